@@ -1,0 +1,184 @@
+/*
+ * pcopt -- GB300 (sm_103a) library for the all-at-once optimality system of
+ * the parabolic optimal-control problem and its eps-circulant rotated
+ * block-diagonal (RBD) preconditioner (Hon, Fung & Lin, arXiv 2410.22686).
+ *
+ * Problem (Eq. Cost_functional_heat, Eq. heat): minimise
+ *   1/2 ||y - g||^2 + gamma/2 ||u||^2   s.t.  y_t - div(a grad y) = f + u,
+ * homogeneous Dirichlet data on the unit square (dim 2) or cube (dim 3).
+ * Backward Euler with tau = T/(n+1) and a conservative finite-difference
+ * stencil (M = I, K = -L_h, face coefficient (a_P + a_Q)/2) give the scaled
+ * all-at-once system A x = b of Eq. main_system / Eq. matrix_A:
+ *
+ *   A = [[alpha I, T^T], [-T, alpha I]],  T = B_n (x) I + tau I_n (x) K,
+ *   x = [sqrt(gamma) y; p],  b = [g_vec; -sqrt(gamma) f_vec],  alpha = tau/sqrt(gamma).
+ *
+ * VECTOR LAYOUT.  Every all-at-once vector (x, b, v, w, lam, c) is a
+ * contiguous FP64 array of 2*n*ms entries, ms = m1^dim, ordered
+ * [half][time block][space]: half 0 is sqrt(gamma) y (resp. the first block
+ * row), half 1 is p; time block j = 1..n is stored at index j-1; space is
+ * C-ordered with x1 fastest, i.e. s = i1 + m1*i2 (+ m1*m1*i3), 0-based
+ * interior indices.  Space-time source/target fields (f, g) are FP64 arrays
+ * [time block][space] of n*ms entries; y0 is one spatial field of ms entries.
+ *
+ * MEMORY.  Vector arguments are DEVICE pointers owned by the caller (for
+ * example torch CUDA tensors), 8-byte aligned, not overlapping unless stated.
+ * The handle owns all workspace; it is allocated in pc_setup and released in
+ * pc_destroy.  No other call allocates device memory.  Calls are asynchronous
+ * on `stream` (a cudaStream_t, NULL = legacy default stream) except where a
+ * host result (iteration count, residual) is returned: those synchronise the
+ * stream before returning.  A handle must not be used from two host threads
+ * at once.
+ *
+ * ERRORS.  Every entry point returns a pc_status; nothing throws across the
+ * boundary.  pc_last_error() gives a human-readable message for the calling
+ * thread's most recent failure.
+ */
+#ifndef PCOPT_H
+#define PCOPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pc_status {
+  PC_OK = 0,
+  PC_ERR_ARG = 1,            /* invalid argument (see pc_last_error) */
+  PC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  PC_ERR_OOM = 3,            /* device allocation failed in pc_setup */
+  PC_ERR_NOT_CONVERGED = 4,  /* Krylov solver hit max_iter; x holds the last iterate */
+  PC_ERR_BREAKDOWN = 5,      /* NaN/Inf in a residual or Arnoldi coefficient */
+  PC_ERR_UNSUPPORTED = 6     /* valid request outside what this build implements */
+} pc_status;
+
+typedef enum pc_spatial {
+  PC_SPATIAL_AUTO = 0,  /* FST when a is constant (a_nodes == NULL), else multigrid */
+  PC_SPATIAL_FST = 1,   /* exact sine-transform solves, constant a only (Example 1) */
+  PC_SPATIAL_MG = 2     /* one V(1,0) multigrid cycle per shifted system (Example 2) */
+} pc_spatial;
+
+typedef enum pc_precision {
+  PC_PREC_FP64 = 0,         /* preconditioner in FP64 */
+  PC_PREC_MIXED_FP32 = 1,   /* preconditioner in FP32 (flexible GMRES keeps FP64 outside) */
+  PC_PREC_MIXED_BF16S = 2   /* as FP32, multigrid smoother iterates stored as BF16 */
+} pc_precision;
+
+typedef enum pc_gmres_mode {
+  PC_GMRES_RIGHT = 0,  /* flexible GMRES, right preconditioning, stops on ||b-Ax||/||b|| */
+  PC_GMRES_LEFT = 1    /* GMRES on P^{-1}A x = P^{-1}b, stops on ||P^{-1}(b-Ax)||/||P^{-1}b|| */
+} pc_gmres_mode;
+
+typedef struct pc_params {
+  int dim;          /* 2 or 3 */
+  int m1;           /* interior grid points per dimension, h = 1/(m1+1); multigrid needs m1 = 2^k-1 */
+  int n;            /* time blocks (FFT length), tau = T/(n+1); power of two in this build */
+  double T;         /* final time > 0 */
+  double gamma;     /* regularisation parameter > 0 */
+  double eps;       /* eps of C_{eps,n}, in (0, 1] */
+  int spatial;      /* pc_spatial */
+  int precision;    /* pc_precision */
+  int max_iter;     /* Krylov capacity: basis storage for this many iterations (1..1000) */
+} pc_params;
+
+typedef struct pc_handle pc_handle;
+
+/* Build a solver for one problem.  Section 1 (discretisation), Eq. matrix_A,
+ * Eq. matrix_P_eps, Eq. decomposition_eps.
+ *   a_nodes: HOST pointer to the coefficient a(x) sampled on all (m1+2)^dim
+ *            grid nodes including the boundary, C-ordered with x1 fastest;
+ *            NULL means a == 1.  Every value must be finite and > 0.
+ *   stream:  stream used for the coefficient upload.
+ *   out:     receives the handle (caller releases it with pc_destroy).
+ * Errors: PC_ERR_ARG (dim not 2/3, m1 < 1, n < 1 or not a power of two,
+ * T <= 0, gamma <= 0, eps outside (0,1], a <= 0, FST with non-constant a,
+ * MG with m1 != 2^k-1), PC_ERR_OOM, PC_ERR_CUDA. */
+int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
+
+/* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
+int pc_destroy(pc_handle* h);
+
+/* y = A x  (Eq. matrix_A, Section 2.1: two block-bidiagonal Toeplitz products, O(mn)).
+ * x, y: device, 2*n*ms FP64, must not overlap. */
+int pc_matvec(pc_handle* h, const double* x, double* y, void* stream);
+
+/* y = A^T x  (block transpose of Eq. matrix_A; equals S A S with S = diag(I, -I)).
+ * x, y: device, 2*n*ms FP64, must not overlap. */
+int pc_matvec_transpose(pc_handle* h, const double* x, double* y, void* stream);
+
+/* w = P_eps^{-1} v by the four steps of Section 2.1: scaled FFT along time,
+ * n independent complex-shifted spatial solves (FST or one V(1,0) cycle),
+ * inverse scaled FFT, and w = [[I,-I],[I,I]] w~.  Computed in the handle's
+ * precision (FP64, or FP32 for the mixed modes); input and output are FP64.
+ * v, w: device, 2*n*ms FP64; v and w may be the same pointer. */
+int pc_apply_precond(pc_handle* h, const double* v, double* w, void* stream);
+
+/* b = [g_vec; -sqrt(gamma) f_vec] of Eq. main_system_before / Eq. main_system:
+ * g_vec_j = tau g^(j) (j = 1..n; the final condition p^(N) = 0 adds nothing),
+ * f_vec_1 = tau f^(1) + y0, f_vec_j = tau f^(j).
+ * f, g: device, n*ms FP64 (time levels t_j = j tau, j = 1..n); y0: device, ms
+ * FP64 (NULL means 0); f may be NULL (means 0).  b: device, 2*n*ms FP64. */
+int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y0,
+                 double* b, void* stream);
+
+/* Solve A x = b by preconditioned GMRES without restarts (Section 3: MATLAB gmres,
+ * zero initial guess, relative tolerance; Lemma 2.1), preconditioner P_eps.
+ *   b: device rhs; x: device, in = initial guess x0, out = solution.
+ *   rtol > 0; maxit in 1..params.max_iter; mode: pc_gmres_mode (LEFT needs PC_PREC_FP64).
+ *   iters, relres: HOST outputs (may be NULL): iterations done and the final
+ *   relative residual (true residual for RIGHT, preconditioned for LEFT).
+ * Arnoldi (classical Gram-Schmidt with one re-orthogonalisation), the Givens
+ * least-squares update, the matvec and the true residual are FP64 in every
+ * precision mode.  Synchronises `stream`.
+ * Errors: PC_ERR_NOT_CONVERGED (x holds the maxit-th iterate), PC_ERR_BREAKDOWN. */
+int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit,
+                   int mode, int* iters, double* relres, void* stream);
+
+/* Solve the adjoint system A^T lam = c with the same preconditioner, using
+ * A^T = S A S, S = diag(I, -I) (from the block form of Eq. matrix_A with K
+ * symmetric): lam = S A^{-1} S c.  Arguments as pc_gmres_solve; lam in/out
+ * (initial guess in). */
+int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, int maxit,
+                     int mode, int* iters, double* relres, void* stream);
+
+/* Stencil derivative for the gradient with respect to the nodal log a:
+ *   grad_P = -tau * sum_j [ lam1_j^T (dK/dlog a_P) x2_j - lam2_j^T (dK/dlog a_P) x1_j ],
+ *   u^T (dK/dlog a_P) v = a_P/(2h^2) sum_{faces (P,Q)} (u_P-u_Q)(v_P-v_Q),
+ * i.e. -lam^T (dA/dlog a_P) x for interior nodes P (boundary nodes fixed).
+ *   x, lam: device all-at-once vectors; grad: device, ms FP64 (interior nodes,
+ *   same spatial ordering), overwritten. */
+int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream);
+
+/* Problem sizes of a handle: ms = m1^dim and the all-at-once length 2*n*ms. */
+int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
+
+/* Instrumentation.  pc_profile(h, 1) starts recording a CUDA-event pair around
+ * every kernel the handle launches (per kernel class); pc_profile(h, 0) stops.
+ * pc_stats fills up to `cap` records (name, launches, summed device ms,
+ * summed algorithmic DRAM bytes) and returns the number of classes; it
+ * synchronises the events.  pc_launch_count returns the number of kernels the
+ * handle has launched since setup or pc_stats_reset. */
+typedef struct pc_kernel_stat {
+  char name[32];
+  int64_t launches;
+  double total_ms;      /* 0 unless profiling was on */
+  double bytes;         /* algorithmic bytes moved (reads + writes of DRAM-resident data) */
+  double flops;         /* algorithmic floating-point operations */
+} pc_kernel_stat;
+
+int pc_profile(pc_handle* h, int on);
+int pc_stats(pc_handle* h, pc_kernel_stat* out, int cap, int* count);
+int pc_stats_reset(pc_handle* h);
+int64_t pc_launch_count(const pc_handle* h);
+
+/* Message of the calling thread's last error (never NULL). */
+const char* pc_last_error(void);
+const char* pc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCOPT_H */

@@ -1,0 +1,100 @@
+"""ctypes binding of libpcopt (include/pcopt.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  Vectors are torch CUDA tensors (float64, contiguous); their device
+pointers and torch's current CUDA stream are handed to the C functions.  If
+the library has not been built, or cannot be loaded, ``load()`` raises: there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpcopt.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pcopt.h")
+
+PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_NOT_CONVERGED, PC_ERR_BREAKDOWN, PC_ERR_UNSUPPORTED = range(7)
+PC_SPATIAL_AUTO, PC_SPATIAL_FST, PC_SPATIAL_MG = 0, 1, 2
+PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S = 0, 1, 2
+PC_GMRES_RIGHT, PC_GMRES_LEFT = 0, 1
+
+
+class pc_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("m1", ctypes.c_int), ("n", ctypes.c_int),
+                ("T", ctypes.c_double), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
+                ("spatial", ctypes.c_int), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
+class pc_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class PCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pcopt status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_ip = ctypes.POINTER(ctypes.c_int)
+_dpp = ctypes.POINTER(ctypes.c_double)
+
+_SIGNATURES = {
+    "pc_setup": (_i, [ctypes.POINTER(pc_params), _vp, _vp, ctypes.POINTER(_vp)]),
+    "pc_destroy": (_i, [_vp]),
+    "pc_matvec": (_i, [_vp, _dp, _dp, _vp]),
+    "pc_matvec_transpose": (_i, [_vp, _dp, _dp, _vp]),
+    "pc_apply_precond": (_i, [_vp, _dp, _dp, _vp]),
+    "pc_build_rhs": (_i, [_vp, _dp, _dp, _dp, _dp, _vp]),
+    "pc_gmres_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
+    "pc_adjoint_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
+    "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
+    "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "pc_profile": (_i, [_vp, _i]),
+    "pc_stats": (_i, [_vp, ctypes.POINTER(pc_kernel_stat), _i, _ip]),
+    "pc_stats_reset": (_i, [_vp]),
+    "pc_launch_count": (ctypes.c_int64, [_vp]),
+    "pc_last_error": (ctypes.c_char_p, []),
+    "pc_status_string": (ctypes.c_char_p, [_i]),
+}
+
+
+def header_functions():
+    """Names of the functions declared in include/pcopt.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pc_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str | None = None):
+    """Load libpcopt.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: the CUDA library must be built (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != PC_OK:
+        lib = load()
+        raise PCError(status, lib.pc_last_error().decode())
+    return status

@@ -1,0 +1,870 @@
+// C ABI of libpcopt (include/pcopt.h): handle set-up, the four-step
+// preconditioner apply (Section 2.1), the all-at-once matvec (Eq. matrix_A),
+// the GMRES driver (Section 3, Lemma 2.1), the adjoint solve and gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pcopt.h"
+#include "common.cuh"
+
+using namespace pcopt;
+
+// ---------------------------------------------------------------------------
+// error state
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error = "no error";
+
+static int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+static int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return PC_ERR_CUDA;
+}
+#define PC_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+namespace pcopt {
+const char* kernel_class_name(int kc) {
+  static const char* names[KC_COUNT] = {"matvec",        "tfft_forward", "tfft_inverse_butterfly",
+                                        "fst_axis",      "fst_divide",   "mg_smooth_rb",
+                                        "mg_resid_restrict", "mg_prolong_correct", "mg_coarsest",
+                                        "arnoldi_dot",   "arnoldi_update_norm", "reduce_partials",
+                                        "normalize",     "givens",       "x_update",
+                                        "axpby",         "build_rhs",    "grad_stencil"};
+  return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
+}
+
+void Launch::begin(int kc) {
+  (void)kc;
+  ev_a = nullptr;
+  if (prof && prof->on) {
+    if (prof->pool.empty()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) == cudaSuccess) prof->pool.push_back(e);
+    }
+    if (!prof->pool.empty()) {
+      ev_a = prof->pool.back();
+      prof->pool.pop_back();
+      cudaEventRecord(ev_a, stream);
+    }
+  }
+}
+
+cudaError_t Launch::end(int kc, double bytes, double flops) {
+  cudaError_t e = cudaGetLastError();
+  if (prof) {
+    prof->launches[kc]++;
+    prof->total++;
+    prof->bytes[kc] += bytes;
+    prof->flops[kc] += flops;
+    if (prof->on && ev_a) {
+      cudaEvent_t b = nullptr;
+      if (prof->pool.empty()) {
+        cudaEvent_t t;
+        if (cudaEventCreate(&t) == cudaSuccess) prof->pool.push_back(t);
+      }
+      if (!prof->pool.empty()) {
+        b = prof->pool.back();
+        prof->pool.pop_back();
+        cudaEventRecord(b, stream);
+        prof->pending.push_back({kc, ev_a, b});
+      } else {
+        prof->pool.push_back(ev_a);
+      }
+    }
+  }
+  ev_a = nullptr;
+  return e;
+}
+
+cudaError_t Prof::flush() {
+  for (auto& p : pending) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e != cudaSuccess) return e;
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, p.a, p.b);
+    if (e != cudaSuccess) return e;
+    ms[p.kc] += t;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+  return cudaSuccess;
+}
+
+void Prof::reset() {
+  for (int k = 0; k < KC_COUNT; ++k) {
+    launches[k] = 0;
+    bytes[k] = 0;
+    flops[k] = 0;
+    ms[k] = 0;
+  }
+  total = 0;
+}
+
+Prof::~Prof() {
+  for (auto& p : pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
+}  // namespace pcopt
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+struct LevelBuf {
+  int m = 0;
+  int64_t np = 0;
+  double* w64 = nullptr;   // [2*dim][np]  tau*a_f/h^2
+  double* d64 = nullptr;   // [np]
+  float* w32 = nullptr;
+  float* d32 = nullptr;
+  void* r = nullptr;       // complex spectral planes (Tc)
+  void* u = nullptr;
+  void* res = nullptr;
+};
+
+struct pc_handle {
+  pc_params prm;
+  int dim = 2, m1 = 0, n = 0, nf = 0, planes = 0, logn = 0;
+  int64_t ms = 0;
+  size_t U = 0;
+  double tau = 0, alpha = 0, sqrtg = 0, h = 0;
+  int spatial = PC_SPATIAL_MG;
+  bool fp32 = false;
+  int cap = 0;
+  double a_const = 1.0;
+
+  std::vector<LevelBuf> lv;
+  // time FFT tables
+  double* dpow64 = nullptr;
+  float* dpow32 = nullptr;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double2* sig64 = nullptr;
+  float2* sig32 = nullptr;
+  // FST tables
+  double* S64 = nullptr;
+  float* S32 = nullptr;
+  double* lamK64 = nullptr;
+  float* lamK32 = nullptr;
+  void* fst_tmp = nullptr;
+  // gradient
+  double* a_int = nullptr;
+  double* grad_partial = nullptr;
+  int grad_tj = 16;
+  // Krylov workspace
+  double* V = nullptr;     // (cap+1) x U
+  void* Z = nullptr;       // cap x U (double or float)
+  double* wbuf = nullptr;  // U
+  double* tbuf = nullptr;  // U
+  double* adjbuf = nullptr;  // U: S c of the adjoint solve
+  double* H = nullptr;     // (cap+1) x cap, column-major, ldh = cap+1
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* gvec = nullptr;
+  double* hcol = nullptr;  // 2 x (cap+1)
+  double* ycoef = nullptr;
+  double* scal = nullptr;  // [0] nrm2, [1] est, [2] ref, [3] tmp
+  double* partial = nullptr;
+  int nblocks = 0;
+  double* host = nullptr;  // pinned: [0] est, [1] ref, [2] nrm2
+  std::vector<void*> allocs;
+  Prof prof;
+};
+
+static int dev_alloc(pc_handle* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  return PC_OK;
+}
+template <typename T>
+static int dev_alloc_t(pc_handle* h, T** p, size_t count) {
+  return dev_alloc(h, (void**)p, count * sizeof(T));
+}
+
+static void release(pc_handle* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->host) cudaFreeHost(h->host);
+  h->host = nullptr;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// per-point face weights tau*a_f/h^2 and their sum for one level (host)
+static void level_stencil(const std::vector<double>& a, int m, int dim, double tau, std::vector<double>& w,
+                          std::vector<double>& d) {
+  const int M = m + 2;
+  const int64_t np = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
+  const double h = 1.0 / (m + 1);
+  const double sc = tau / (h * h);
+  w.assign((size_t)2 * dim * np, 0.0);
+  d.assign((size_t)np, 0.0);
+  auto node = [&](int i1, int i2, int i3) -> double {
+    return dim == 2 ? a[(size_t)i2 * M + i1] : a[((size_t)i3 * M + i2) * M + i1];
+  };
+  for (int64_t s = 0; s < np; ++s) {
+    const int i1 = (int)(s % m) + 1;
+    const int64_t r = s / m;
+    const int i2 = (int)(dim == 2 ? r : r % m) + 1;
+    const int i3 = dim == 3 ? (int)(r / m) + 1 : 0;
+    const double aP = node(i1, i2, i3);
+    double nb[6];
+    nb[0] = node(i1 - 1, i2, i3);
+    nb[1] = node(i1 + 1, i2, i3);
+    nb[2] = node(i1, i2 - 1, i3);
+    nb[3] = node(i1, i2 + 1, i3);
+    if (dim == 3) {
+      nb[4] = node(i1, i2, i3 - 1);
+      nb[5] = node(i1, i2, i3 + 1);
+    }
+    double sum = 0.0;
+    for (int k = 0; k < 2 * dim; ++k) {
+      const double wf = sc * 0.5 * (aP + nb[k]);
+      w[(size_t)k * np + s] = wf;
+      sum += wf;
+    }
+    d[(size_t)s] = sum;
+  }
+}
+
+template <typename T>
+static int upload(pc_handle* h, T** dst, const std::vector<double>& src, cudaStream_t st) {
+  std::vector<T> tmp(src.begin(), src.end());
+  int rc = dev_alloc_t(h, dst, tmp.size());
+  if (rc) return rc;
+  PC_CUDA(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+static int upload_c(pc_handle* h, void** dst, const std::vector<double>& re, const std::vector<double>& im, bool f32,
+                    cudaStream_t st) {
+  const size_t n = re.size();
+  if (f32) {
+    std::vector<float2> t(n);
+    for (size_t i = 0; i < n; ++i) t[i] = make_float2((float)re[i], (float)im[i]);
+    int rc = dev_alloc(h, dst, n * sizeof(float2));
+    if (rc) return rc;
+    PC_CUDA(cudaMemcpyAsync(*dst, t.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+  } else {
+    std::vector<double2> t(n);
+    for (size_t i = 0; i < n; ++i) t[i] = make_double2(re[i], im[i]);
+    int rc = dev_alloc(h, dst, n * sizeof(double2));
+    if (rc) return rc;
+    PC_CUDA(cudaMemcpyAsync(*dst, t.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+  }
+  return PC_OK;
+}
+
+extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream, pc_handle** out) {
+  if (!p || !out) return fail(PC_ERR_ARG, "pc_setup: null params or out pointer");
+  *out = nullptr;
+  if (p->dim != 2 && p->dim != 3) return fail(PC_ERR_ARG, "dim must be 2 or 3");
+  if (p->m1 < 1 || p->m1 > 4095) return fail(PC_ERR_ARG, "m1 must be in [1, 4095]");
+  if (p->n < 1) return fail(PC_ERR_ARG, "n must be >= 1");
+  if (!is_pow2(p->n)) return fail(PC_ERR_ARG, "n must be a power of two in this build");
+  if (p->n > 4096) return fail(PC_ERR_ARG, "n must be <= 4096");
+  if (!(p->T > 0) || !std::isfinite(p->T)) return fail(PC_ERR_ARG, "T must be finite and > 0");
+  if (!(p->gamma > 0) || !std::isfinite(p->gamma)) return fail(PC_ERR_ARG, "gamma must be finite and > 0");
+  if (!(p->eps > 0) || !(p->eps <= 1.0)) return fail(PC_ERR_ARG, "eps must lie in (0, 1]");
+  if (p->precision != PC_PREC_FP64 && p->precision != PC_PREC_MIXED_FP32 && p->precision != PC_PREC_MIXED_BF16S)
+    return fail(PC_ERR_ARG, "unknown precision");
+  if (p->precision == PC_PREC_MIXED_BF16S) return fail(PC_ERR_UNSUPPORTED, "BF16-storage smoother not built yet");
+  if (p->spatial < 0 || p->spatial > 2) return fail(PC_ERR_ARG, "unknown spatial solver");
+  if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
+
+  const int dim = p->dim, m1 = p->m1;
+  const int M = m1 + 2;
+  const size_t nodes = dim == 2 ? (size_t)M * M : (size_t)M * M * M;
+  std::vector<double> a(nodes, 1.0);
+  bool constant = true;
+  if (a_nodes) {
+    for (size_t i = 0; i < nodes; ++i) {
+      const double v = a_nodes[i];
+      if (!(v > 0) || !std::isfinite(v)) return fail(PC_ERR_ARG, "a(x) must be finite and > 0 on every node");
+      a[i] = v;
+      if (v != a_nodes[0]) constant = false;
+    }
+  }
+  int spatial = p->spatial;
+  if (spatial == PC_SPATIAL_AUTO) spatial = constant ? PC_SPATIAL_FST : PC_SPATIAL_MG;
+  if (spatial == PC_SPATIAL_FST && !constant) return fail(PC_ERR_ARG, "FST needs a constant coefficient a");
+  if (spatial == PC_SPATIAL_MG && ((m1 + 1) & m1) != 0) return fail(PC_ERR_ARG, "multigrid needs m1 = 2^k - 1");
+
+  pc_handle* h = new (std::nothrow) pc_handle();
+  if (!h) return fail(PC_ERR_OOM, "host allocation failed");
+  h->prm = *p;
+  h->dim = dim;
+  h->m1 = m1;
+  h->n = p->n;
+  h->nf = p->n / 2 + 1;
+  h->planes = 2 * h->nf;
+  h->logn = 0;
+  while ((1 << h->logn) < h->n) h->logn++;
+  h->ms = dim == 2 ? (int64_t)m1 * m1 : (int64_t)m1 * m1 * m1;
+  h->U = (size_t)2 * h->n * h->ms;
+  h->tau = p->T / (p->n + 1);
+  h->alpha = h->tau / std::sqrt(p->gamma);
+  h->sqrtg = std::sqrt(p->gamma);
+  h->h = 1.0 / (m1 + 1);
+  h->spatial = spatial;
+  h->fp32 = p->precision != PC_PREC_FP64;
+  h->cap = p->max_iter;
+  h->a_const = a[0];
+  h->prof.on = false;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  int rc = PC_OK;
+  const size_t cb = h->fp32 ? sizeof(float2) : sizeof(double2);
+  // ---- level hierarchy: level 0 always (matvec), coarser ones for multigrid
+  {
+    std::vector<double> acur = a;
+    int m = m1;
+    while (true) {
+      LevelBuf L;
+      L.m = m;
+      L.np = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
+      std::vector<double> w, d;
+      level_stencil(acur, m, dim, h->tau, w, d);
+      if ((rc = upload(h, &L.w64, w, st))) goto fail_out;
+      if ((rc = upload(h, &L.d64, d, st))) goto fail_out;
+      if ((rc = upload(h, &L.w32, w, st))) goto fail_out;
+      if ((rc = upload(h, &L.d32, d, st))) goto fail_out;
+      if ((rc = dev_alloc(h, &L.r, (size_t)h->planes * L.np * cb))) goto fail_out;
+      if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * cb))) goto fail_out;
+      const bool more = spatial == PC_SPATIAL_MG && m > 1;
+      if (more && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb))) goto fail_out;
+      h->lv.push_back(L);
+      if (!more) break;
+      // inject the nodal coefficient: a_c[I] = a[2I] over all nodes incl. boundary
+      const int mc = (m - 1) / 2, Mc = mc + 2, Mf = m + 2;
+      std::vector<double> ac(dim == 2 ? (size_t)Mc * Mc : (size_t)Mc * Mc * Mc);
+      for (size_t q = 0; q < ac.size(); ++q) {
+        const int c1 = (int)(q % Mc);
+        const size_t rr = q / Mc;
+        const int c2 = (int)(dim == 2 ? rr : rr % Mc);
+        const int c3 = dim == 3 ? (int)(rr / Mc) : 0;
+        ac[q] = dim == 2 ? acur[(size_t)(2 * c2) * Mf + 2 * c1]
+                         : acur[((size_t)(2 * c3) * Mf + 2 * c2) * Mf + 2 * c1];
+      }
+      acur.swap(ac);
+      m = mc;
+    }
+  }
+  // ---- time FFT tables
+  {
+    const int n = h->n;
+    std::vector<double> dp(n), twr(std::max(1, n / 2)), twi(std::max(1, n / 2));
+    for (int j = 0; j < n; ++j) dp[j] = std::pow(p->eps, (double)j / n);
+    for (int k = 0; k < std::max(1, n / 2); ++k) {
+      const double th = 2.0 * M_PI * (double)k / n;
+      twr[k] = std::cos(th);
+      twi[k] = -std::sin(th);
+    }
+    std::vector<double> sr(h->planes), si(h->planes);
+    const double e1n = std::pow(p->eps, 1.0 / n);
+    for (int q = 0; q < h->planes; ++q) {
+      const int k = q / 2;
+      const double th = 2.0 * M_PI * (double)k / n;
+      // sigma_k = lambda_k + alpha, lambda_k = 1 - eps^{1/n} exp(-2 pi i k / n)
+      sr[q] = 1.0 + h->alpha - e1n * std::cos(th);
+      si[q] = (k == 0 || 2 * k == n) ? 0.0 : e1n * std::sin(th);
+    }
+    if ((rc = upload(h, &h->dpow64, dp, st))) goto fail_out;
+    if ((rc = upload(h, &h->dpow32, dp, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->tw64, twr, twi, false, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->tw32, twr, twi, true, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->sig64, sr, si, false, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->sig32, sr, si, true, st))) goto fail_out;
+  }
+  // ---- FST tables (constant a)
+  if (spatial == PC_SPATIAL_FST) {
+    const int m = m1;
+    std::vector<double> S((size_t)m * m), lam((size_t)h->ms, 0.0), mu(m);
+    const double sc = std::sqrt(2.0 / (m + 1));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = sc * std::sin(M_PI * (double)(i + 1) * (j + 1) / (m + 1));
+    for (int i = 0; i < m; ++i) {
+      const double sv = std::sin(M_PI * (double)(i + 1) / (2.0 * (m + 1)));
+      mu[i] = 4.0 * sv * sv / (h->h * h->h);
+    }
+    for (int64_t s = 0; s < h->ms; ++s) {
+      const int i1 = (int)(s % m);
+      const int64_t r = s / m;
+      const int i2 = (int)(dim == 2 ? r : r % m);
+      const int i3 = dim == 3 ? (int)(r / m) : -1;
+      double v = mu[i1] + mu[i2] + (i3 >= 0 ? mu[i3] : 0.0);
+      lam[(size_t)s] = h->tau * h->a_const * v;
+    }
+    if ((rc = upload(h, &h->S64, S, st))) goto fail_out;
+    if ((rc = upload(h, &h->S32, S, st))) goto fail_out;
+    if ((rc = upload(h, &h->lamK64, lam, st))) goto fail_out;
+    if ((rc = upload(h, &h->lamK32, lam, st))) goto fail_out;
+    if ((rc = dev_alloc(h, &h->fst_tmp, (size_t)h->planes * h->ms * cb))) goto fail_out;
+  }
+  // ---- interior coefficient (gradient) and its scratch
+  {
+    std::vector<double> ai((size_t)h->ms);
+    for (int64_t s = 0; s < h->ms; ++s) {
+      const int i1 = (int)(s % m1) + 1;
+      const int64_t r = s / m1;
+      const int i2 = (int)(dim == 2 ? r : r % m1) + 1;
+      const int i3 = dim == 3 ? (int)(r / m1) + 1 : 0;
+      ai[(size_t)s] = dim == 2 ? a[(size_t)i2 * M + i1] : a[((size_t)i3 * M + i2) * M + i1];
+    }
+    if ((rc = upload(h, &h->a_int, ai, st))) goto fail_out;
+    const int nch = (h->n + h->grad_tj - 1) / h->grad_tj;
+    if ((rc = dev_alloc_t(h, &h->grad_partial, (size_t)nch * h->ms))) goto fail_out;
+  }
+  // ---- Krylov workspace
+  {
+    const size_t U = h->U;
+    const int cap = h->cap;
+    h->nblocks = num_sms() * 4;
+    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * U))) goto fail_out;
+    if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->tbuf, U))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->adjbuf, U))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->H, (size_t)(cap + 1) * cap))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->cs, (size_t)cap + 1))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->sn, (size_t)cap + 1))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->gvec, (size_t)cap + 2))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->hcol, (size_t)2 * (cap + 1)))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->ycoef, (size_t)cap + 1))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->scal, 8))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 1)))) goto fail_out;
+    cudaError_t e = cudaMallocHost((void**)&h->host, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+      rc = fail(PC_ERR_OOM, "cudaMallocHost failed");
+      goto fail_out;
+    }
+  }
+  {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "pc_setup");
+      goto fail_out;
+    }
+  }
+  *out = h;
+  return PC_OK;
+fail_out:
+  release(h);
+  delete h;
+  return rc;
+}
+
+extern "C" int pc_destroy(pc_handle* h) {
+  if (!h) return PC_OK;
+  cudaDeviceSynchronize();
+  release(h);
+  delete h;
+  return PC_OK;
+}
+
+extern "C" int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  if (ms) *ms = h->ms;
+  if (vec_len) *vec_len = (int64_t)h->U;
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// internal operators
+// ---------------------------------------------------------------------------
+static Grid grid_of(const pc_handle* h, int l) {
+  Grid g;
+  g.dim = h->dim;
+  g.m = h->lv[l].m;
+  g.np = h->lv[l].np;
+  return g;
+}
+
+template <typename Tc>
+static const Tc* lvw(const LevelBuf& L);
+template <>
+const double* lvw<double>(const LevelBuf& L) { return L.w64; }
+template <>
+const float* lvw<float>(const LevelBuf& L) { return L.w32; }
+template <typename Tc>
+static const Tc* lvd(const LevelBuf& L);
+template <>
+const double* lvd<double>(const LevelBuf& L) { return L.d64; }
+template <>
+const float* lvd<float>(const LevelBuf& L) { return L.d32; }
+
+template <typename Tc>
+struct Tables;
+template <>
+struct Tables<double> {
+  static const double* dpow(const pc_handle* h) { return h->dpow64; }
+  static const double2* tw(const pc_handle* h) { return h->tw64; }
+  static const double2* sig(const pc_handle* h) { return h->sig64; }
+  static const double* S(const pc_handle* h) { return h->S64; }
+  static const double* lamK(const pc_handle* h) { return h->lamK64; }
+};
+template <>
+struct Tables<float> {
+  static const float* dpow(const pc_handle* h) { return h->dpow32; }
+  static const float2* tw(const pc_handle* h) { return h->tw32; }
+  static const float2* sig(const pc_handle* h) { return h->sig32; }
+  static const float* S(const pc_handle* h) { return h->S32; }
+  static const float* lamK(const pc_handle* h) { return h->lamK32; }
+};
+
+// step 2: every plane of lv[0].r solved into lv[0].u
+template <typename Tc>
+static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
+  typedef typename Cx<Tc>::t C;
+  const int P = h->planes;
+  const C* sig = Tables<Tc>::sig(h);
+  if (h->spatial == PC_SPATIAL_FST) {
+    const Grid g = grid_of(h, 0);
+    C* bufs[2] = {(C*)h->lv[0].r, (C*)h->fst_tmp};
+    int cur = 0;
+    cudaError_t e;
+    for (int ax = 0; ax < h->dim; ++ax) {
+      if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], bufs[1 - cur])) != cudaSuccess) return e;
+      cur = 1 - cur;
+    }
+    if ((e = launch_fst_divide<Tc>(L, g, P, Tables<Tc>::lamK(h), sig, bufs[cur])) != cudaSuccess) return e;
+    for (int ax = h->dim - 1; ax >= 0; --ax) {
+      C* dst = ax == 0 ? (C*)h->lv[0].u : bufs[1 - cur];
+      if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], dst)) != cudaSuccess) return e;
+      cur = 1 - cur;
+    }
+    return cudaSuccess;
+  }
+  // multigrid V(1,0)
+  const int nl = (int)h->lv.size();
+  cudaError_t e;
+  for (int l = 0; l + 1 < nl; ++l) {
+    const LevelBuf& Lb = h->lv[l];
+    Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
+    const Grid g = grid_of(h, l);
+    if ((e = launch_mg_smooth<Tc>(L, g, P, st, sig, (const C*)Lb.r, (C*)Lb.u)) != cudaSuccess) return e;
+    if ((e = launch_mg_resid_restrict<Tc>(L, g, P, st, sig, (const C*)Lb.r, (const C*)Lb.u, (C*)Lb.res,
+                                          (C*)h->lv[l + 1].r)) != cudaSuccess)
+      return e;
+  }
+  {
+    const LevelBuf& Lc = h->lv[nl - 1];
+    if ((e = launch_mg_coarsest<Tc>(L, P, lvd<Tc>(Lc), sig, (const C*)Lc.r, (C*)Lc.u)) != cudaSuccess) return e;
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    if ((e = launch_mg_prolong<Tc>(L, grid_of(h, l), P, (const C*)h->lv[l + 1].u, (C*)h->lv[l].u)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename Tc, typename Tout>
+static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w) {
+  typedef typename Cx<Tc>::t C;
+  cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::tw(h), (C*)h->lv[0].r);
+  if (e != cudaSuccess) return e;
+  if ((e = spatial_solve<Tc>(h, L)) != cudaSuccess) return e;
+  return launch_tfft_inverse<Tc, Tout>(L, h->ms, h->n, (const C*)h->lv[0].u, Tables<Tc>::dpow(h), Tables<Tc>::tw(h),
+                                       w);
+}
+
+// w (FP64) = P^{-1} v in the handle's precision
+static cudaError_t precond64(pc_handle* h, Launch& L, const double* v, double* w) {
+  return h->fp32 ? precond_t<float, double>(h, L, v, w) : precond_t<double, double>(h, L, v, w);
+}
+
+static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32, double* y, bool transpose) {
+  Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
+  const Grid g = grid_of(h, 0);
+  if (x_f32) return launch_matvec<float>(L, g, h->n, st, h->alpha, (const float*)x, y, transpose);
+  return launch_matvec<double>(L, g, h->n, st, h->alpha, (const double*)x, y, transpose);
+}
+
+// ---------------------------------------------------------------------------
+// public operators
+// ---------------------------------------------------------------------------
+extern "C" int pc_matvec(pc_handle* h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec: null argument");
+  if (x == y) return fail(PC_ERR_ARG, "pc_matvec: x and y must not overlap");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  cudaError_t e = matvec_any(h, L, x, false, y, false);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec");
+}
+
+extern "C" int pc_matvec_transpose(pc_handle* h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec_transpose: null argument");
+  if (x == y) return fail(PC_ERR_ARG, "pc_matvec_transpose: x and y must not overlap");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  cudaError_t e = matvec_any(h, L, x, false, y, true);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec_transpose");
+}
+
+extern "C" int pc_apply_precond(pc_handle* h, const double* v, double* w, void* stream) {
+  if (!h || !v || !w) return fail(PC_ERR_ARG, "pc_apply_precond: null argument");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  cudaError_t e = precond64(h, L, v, w);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_apply_precond");
+}
+
+extern "C" int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y0, double* b,
+                            void* stream) {
+  if (!h || !g || !b) return fail(PC_ERR_ARG, "pc_build_rhs: null g or b");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  cudaError_t e = launch_build_rhs(L, h->ms, h->n, h->tau, h->sqrtg, f, g, y0, b);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_build_rhs");
+}
+
+extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream) {
+  if (!h || !x || !lam || !grad) return fail(PC_ERR_ARG, "pc_grad_log_a: null argument");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  // -tau * a_P / (2 h^2) * sum_j sum_faces [...]
+  const double scale = -h->tau * 0.5 / (h->h * h->h);
+  cudaError_t e =
+      launch_grad_chunked(L, grid_of(h, 0), h->n, scale, h->a_int, x, lam, h->grad_partial, h->grad_tj, grad);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_log_a");
+}
+
+// ---------------------------------------------------------------------------
+// GMRES (Section 3: zero initial guess, relative tolerance; Lemma 2.1)
+// ---------------------------------------------------------------------------
+static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref) {
+  PC_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  if (est) *est = h->host[0];
+  if (ref) *ref = h->host[1];
+  return PC_OK;
+}
+
+static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int maxit, int mode, int* iters,
+                      double* relres, cudaStream_t st) {
+  if (!h || !b || !x) return fail(PC_ERR_ARG, "gmres: null argument");
+  if (!(rtol > 0)) return fail(PC_ERR_ARG, "gmres: rtol must be > 0");
+  if (maxit < 1 || maxit > h->cap) return fail(PC_ERR_ARG, "gmres: maxit must be in [1, max_iter]");
+  if (mode != PC_GMRES_RIGHT && mode != PC_GMRES_LEFT) return fail(PC_ERR_ARG, "gmres: unknown mode");
+  if (mode == PC_GMRES_LEFT && h->fp32) return fail(PC_ERR_ARG, "gmres: LEFT mode needs the FP64 preconditioner");
+  Launch L{st, &h->prof};
+  const size_t U = h->U;
+  const int ldh = h->cap + 1;
+  double* nrm2 = h->scal + 0;
+  double* est = h->scal + 1;
+  double* ref = h->scal + 2;
+  double* V = h->V;
+  cudaError_t e;
+#define GM_CUDA(...)                                   \
+  do {                                                 \
+    if ((e = (__VA_ARGS__)) != cudaSuccess) return cuda_fail(e, #__VA_ARGS__); \
+  } while (0)
+
+  // is x0 zero?  (one norm + readback)
+  GM_CUDA(launch_norm2(L, x, U, h->partial, h->nblocks, h->scal + 3));
+  PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  const bool x0_zero = h->host[2] == 0.0;
+
+  // reference norm and r0 (stored unnormalised in V_0)
+  if (mode == PC_GMRES_RIGHT) {
+    GM_CUDA(launch_norm2(L, b, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 1));  // ref = ||b||
+    if (x0_zero) {
+      PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
+      PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, V, U));
+    }
+    GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 0));
+  } else {
+    GM_CUDA(precond64(h, L, b, V));  // P^{-1} b
+    GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 1));  // ref = ||P^{-1} b||
+    if (!x0_zero) {
+      GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
+      PC_CUDA(cudaMemcpyAsync(h->tbuf, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, h->tbuf, U));
+      GM_CUDA(precond64(h, L, h->tbuf, V));
+      GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+      GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 0));
+    }
+  }
+  double est_h = 0, ref_h = 0;
+  if (int rc = read_scalars(h, st, &est_h, &ref_h)) return rc;
+  if (ref_h == 0.0) {
+    // b == 0 (or P^{-1}b == 0): the solution is x = 0
+    PC_CUDA(cudaMemsetAsync(x, 0, U * sizeof(double), st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return PC_OK;
+  }
+  if (!std::isfinite(est_h) || !std::isfinite(ref_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite initial residual");
+  if (est_h <= rtol) {
+    if (iters) *iters = 0;
+    if (relres) *relres = est_h;
+    return PC_OK;
+  }
+  GM_CUDA(launch_scale_by_inv_norm(L, V, V, U, nrm2));
+
+  int k = 0;
+  bool converged = false;
+  for (int j = 0; j < maxit; ++j) {
+    double* vj = V + (size_t)j * U;
+    double* vn = V + (size_t)(j + 1) * U;
+    if (mode == PC_GMRES_RIGHT) {
+      if (h->fp32) {
+        float* zj = (float*)h->Z + (size_t)j * U;
+        GM_CUDA(precond_t<float, float>(h, L, vj, zj));
+        GM_CUDA(matvec_any(h, L, zj, true, vn, false));
+      } else {
+        double* zj = (double*)h->Z + (size_t)j * U;
+        GM_CUDA(precond_t<double, double>(h, L, vj, zj));
+        GM_CUDA(matvec_any(h, L, zj, false, vn, false));
+      }
+    } else {
+      GM_CUDA(matvec_any(h, L, vj, false, h->wbuf, false));
+      GM_CUDA(precond64(h, L, h->wbuf, vn));
+    }
+    // classical Gram-Schmidt, twice
+    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->nblocks, h->hcol));
+    GM_CUDA(launch_update_norm(L, V, U, j + 1, h->hcol, vn, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->nblocks, h->hcol + ldh));
+    GM_CUDA(launch_update_norm(L, V, U, j + 1, h->hcol + ldh, vn, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, nrm2, est, ref));
+    if (int rc = read_scalars(h, st, &est_h, nullptr)) return rc;
+    k = j + 1;
+    if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite residual estimate");
+    if (est_h <= rtol) {
+      converged = true;
+      break;
+    }
+    if (j + 1 < maxit) GM_CUDA(launch_scale_by_inv_norm(L, vn, vn, U, nrm2));
+  }
+  GM_CUDA(launch_backsolve(L, k, ldh, h->H, h->gvec, h->ycoef));
+  if (mode == PC_GMRES_RIGHT) {
+    if (h->fp32)
+      GM_CUDA(launch_xupdate<float>(L, (const float*)h->Z, U, k, h->ycoef, x, U));
+    else
+      GM_CUDA(launch_xupdate<double>(L, (const double*)h->Z, U, k, h->ycoef, x, U));
+    // true residual ||b - A x|| / ||b||
+    GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
+    GM_CUDA(launch_axpby<double>(L, 1.0, b, -1.0, h->wbuf, U));
+    GM_CUDA(launch_norm2(L, h->wbuf, U, h->partial, h->nblocks, h->scal + 3));
+    PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+    est_h = std::sqrt(h->host[2]) / ref_h;
+  } else {
+    GM_CUDA(launch_xupdate<double>(L, V, U, k, h->ycoef, x, U));
+    PC_CUDA(cudaStreamSynchronize(st));
+  }
+#undef GM_CUDA
+  if (iters) *iters = k;
+  if (relres) *relres = est_h;
+  if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite final residual");
+  if (!converged) return fail(PC_ERR_NOT_CONVERGED, "gmres: maxit reached before rtol");
+  return PC_OK;
+}
+
+extern "C" int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit, int mode, int* iters,
+                              double* relres, void* stream) {
+  return gmres_impl(h, b, x, rtol, maxit, mode, iters, relres, (cudaStream_t)stream);
+}
+
+extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, int maxit, int mode,
+                                int* iters, double* relres, void* stream) {
+  if (!h || !c || !lam) return fail(PC_ERR_ARG, "pc_adjoint_solve: null argument");
+  if (c == lam) return fail(PC_ERR_ARG, "pc_adjoint_solve: c and lam must not overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  Launch L{st, &h->prof};
+  const size_t half = h->U / 2;
+  // A^T lam = c  <=>  A (S lam) = S c,  S = diag(I, -I)
+  PC_CUDA(cudaMemcpyAsync(h->adjbuf, c, h->U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  cudaError_t e = launch_axpby<double>(L, -1.0, h->adjbuf + half, 0.0, h->adjbuf + half, half);
+  if (e != cudaSuccess) return cuda_fail(e, "pc_adjoint_solve");
+  if ((e = launch_axpby<double>(L, -1.0, lam + half, 0.0, lam + half, half)) != cudaSuccess)
+    return cuda_fail(e, "pc_adjoint_solve");
+  const int rc = gmres_impl(h, h->adjbuf, lam, rtol, maxit, mode, iters, relres, st);
+  if ((e = launch_axpby<double>(L, -1.0, lam + half, 0.0, lam + half, half)) != cudaSuccess)
+    return cuda_fail(e, "pc_adjoint_solve");
+  cudaError_t se = cudaStreamSynchronize(st);
+  if (se != cudaSuccess) return cuda_fail(se, "pc_adjoint_solve");
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// instrumentation and status
+// ---------------------------------------------------------------------------
+extern "C" int pc_profile(pc_handle* h, int on) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  h->prof.on = on != 0;
+  return PC_OK;
+}
+
+extern "C" int pc_stats(pc_handle* h, pc_kernel_stat* out, int cap, int* count) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  cudaError_t e = h->prof.flush();
+  if (e != cudaSuccess) return cuda_fail(e, "pc_stats");
+  int c = 0;
+  for (int k = 0; k < KC_COUNT && c < cap; ++k) {
+    if (!out) break;
+    std::memset(&out[c], 0, sizeof(pc_kernel_stat));
+    std::snprintf(out[c].name, sizeof(out[c].name), "%s", kernel_class_name(k));
+    out[c].launches = h->prof.launches[k];
+    out[c].total_ms = h->prof.ms[k];
+    out[c].bytes = h->prof.bytes[k];
+    out[c].flops = h->prof.flops[k];
+    ++c;
+  }
+  if (count) *count = KC_COUNT;
+  return PC_OK;
+}
+
+extern "C" int pc_stats_reset(pc_handle* h) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  cudaError_t e = h->prof.flush();
+  h->prof.reset();
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_stats_reset");
+}
+
+extern "C" int64_t pc_launch_count(const pc_handle* h) { return h ? h->prof.total : 0; }
+
+extern "C" const char* pc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* pc_status_string(int s) {
+  switch (s) {
+    case PC_OK: return "ok";
+    case PC_ERR_ARG: return "invalid argument";
+    case PC_ERR_CUDA: return "CUDA error";
+    case PC_ERR_OOM: return "out of device memory";
+    case PC_ERR_NOT_CONVERGED: return "not converged";
+    case PC_ERR_BREAKDOWN: return "breakdown (non-finite value)";
+    case PC_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}

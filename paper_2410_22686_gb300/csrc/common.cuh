@@ -1,0 +1,201 @@
+// Internal declarations shared by the translation units of libpcopt.
+// Nothing here is part of the public C ABI (include/pcopt.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pcopt {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<float> { typedef float2 t; };
+template <> struct Cx<double> { typedef double2 t; };
+
+template <typename T>
+__host__ __device__ __forceinline__ typename Cx<T>::t cmk(T re, T im) {
+  typename Cx<T>::t r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// 1/z = conj(z)/|z|^2
+__host__ __device__ __forceinline__ float2 cinv(float2 z) {
+  float q = 1.0f / (z.x * z.x + z.y * z.y);
+  return make_float2(z.x * q, -z.y * q);
+}
+__host__ __device__ __forceinline__ double2 cinv(double2 z) {
+  double q = 1.0 / (z.x * z.x + z.y * z.y);
+  return make_double2(z.x * q, -z.y * q);
+}
+template <typename T>
+__host__ __device__ __forceinline__ typename Cx<T>::t czero() { return cmk<T>(T(0), T(0)); }
+
+// ---------------------------------------------------------------------------
+// kernel classes (instrumentation buckets)
+// ---------------------------------------------------------------------------
+enum KernelClass {
+  KC_MATVEC = 0,
+  KC_TFFT_FWD,
+  KC_TFFT_INV,
+  KC_FST_AXIS,
+  KC_FST_DIVIDE,
+  KC_MG_SMOOTH,
+  KC_MG_RESID_RESTRICT,
+  KC_MG_PROLONG,
+  KC_MG_COARSEST,
+  KC_DOT,
+  KC_UPDATE,
+  KC_REDUCE,
+  KC_SCALE,
+  KC_GIVENS,
+  KC_XUPDATE,
+  KC_AXPBY,
+  KC_RHS,
+  KC_GRAD,
+  KC_COUNT
+};
+const char* kernel_class_name(int kc);
+
+// ---------------------------------------------------------------------------
+// launch context: stream + launch counting + optional event timing
+// ---------------------------------------------------------------------------
+struct Prof {
+  bool on = false;
+  int64_t launches[KC_COUNT] = {0};
+  double bytes[KC_COUNT] = {0};
+  double flops[KC_COUNT] = {0};
+  double ms[KC_COUNT] = {0};
+  struct Pending {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t total = 0;
+  cudaError_t flush();  // resolve pending event pairs into ms[]
+  void reset();
+  ~Prof();
+};
+
+struct Launch {
+  cudaStream_t stream;
+  Prof* prof;
+  // record around one kernel launch; `bytes`/`flops` are algorithmic figures
+  cudaEvent_t ev_a = nullptr;
+  void begin(int kc);
+  cudaError_t end(int kc, double bytes, double flops);
+};
+
+// ---------------------------------------------------------------------------
+// device-side problem description used by the kernels
+// ---------------------------------------------------------------------------
+struct Grid {
+  int dim;     // 2 or 3
+  int m;       // points per dimension on this level
+  int64_t np;  // m^dim
+};
+
+// stencil of one level: per-point face weights tau*a_f/h^2 towards
+// (-x1, +x1, -x2, +x2[, -x3, +x3]) and their sum (the diagonal of tau K)
+template <typename T>
+struct Stencil {
+  const T* w;     // [2*dim][np]
+  const T* diag;  // [np]
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the k_*.cu files)
+// ---------------------------------------------------------------------------
+// y = A x (transpose=false) or A^T x; x in Tin (double or float), y double.
+template <typename Tin>
+cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>& st, double alpha,
+                          const Tin* x, double* y, bool transpose);
+
+// forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
+template <typename Tc>
+cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow,
+                                const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec);
+// inverse scaled time FFT + butterfly: spectral planes -> w (Tout [2][n][ms])
+template <typename Tc, typename Tout>
+cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const typename Cx<Tc>::t* spec,
+                                const Tc* dpow, const typename Cx<Tc>::t* tw, Tout* w);
+
+// FST: one DST-I along `axis` of every plane (out = S in), and the spectral divide
+template <typename Tc>
+cudaError_t launch_fst_axis(Launch& L, const Grid& g, int planes, int axis, const Tc* S,
+                            const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out);
+template <typename Tc>
+cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK,
+                              const typename Cx<Tc>::t* sigma, typename Cx<Tc>::t* buf);
+
+// multigrid pieces (planes = 2*nfreq, sigma per plane)
+template <typename Tc>
+cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
+                             const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
+                             typename Cx<Tc>::t* u);
+template <typename Tc>
+cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
+                                     const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
+                                     const typename Cx<Tc>::t* u, typename Cx<Tc>::t* res,
+                                     typename Cx<Tc>::t* rc);
+template <typename Tc>
+cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const typename Cx<Tc>::t* ec,
+                              typename Cx<Tc>::t* uf);
+template <typename Tc>
+cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const typename Cx<Tc>::t* sigma,
+                               const typename Cx<Tc>::t* r, typename Cx<Tc>::t* u);
+
+// Krylov (FP64): partial dots of nv vectors (stride ldv) with w, chunked launches
+cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, const double* w, size_t len,
+                            double* partial, int nblocks, double* out);
+// w -= sum_i h[i] V_i (h on device), writes partial sums of the new ||w||^2 and reduces into *nrm2
+cudaError_t launch_update_norm(Launch& L, const double* V, size_t ldv, int nv, const double* h, double* w,
+                               size_t len, double* partial, int nblocks, double* nrm2);
+// partial sums of ||w||^2 -> *nrm2
+cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, int nblocks, double* nrm2);
+// v = w * (1/sqrt(nrm2[0]))
+cudaError_t launch_scale_by_inv_norm(Launch& L, const double* w, double* v, size_t len, const double* nrm2);
+// y = a*x + b*y on [lo, hi) (x may be float)
+template <typename Tx>
+cudaError_t launch_axpby(Launch& L, double a, const Tx* x, double b, double* y, size_t len);
+// Givens update of column j of H, residual estimate
+cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec,
+                          const double* hcol, const double* nrm2, double* est, const double* ref);
+cudaError_t launch_backsolve(Launch& L, int k, int ldh, const double* H, const double* gvec, double* y);
+template <typename Tz>
+cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const double* y, double* x, size_t len);
+// start vector: v0 = r / ||r||, gvec[0] = ||r||, ref := ||r0|| or given
+cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, double* est, double* ref_out,
+                                 int set_ref);
+
+// RHS assembly and gradient
+cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
+                             const double* g, const double* y0, double* b);
+// grad_P = scale * a_P * sum_j sum_faces [(l1_P-l1_Q)(x2_P-x2_Q) - (l2_P-l2_Q)(x1_P-x1_Q)]
+cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, const double* a_int, const double* x,
+                                const double* lam, double* partial, int tj, double* grad);
+
+int num_sms();
+
+}  // namespace pcopt

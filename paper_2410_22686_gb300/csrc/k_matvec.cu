@@ -1,0 +1,127 @@
+// All-at-once matrix-vector product y = A x (Eq. matrix_A, Section 2.1):
+//
+//   y1_j = alpha x1_j + (T^T x2)_j,   (T^T v)_j = v_j - v_{j+1} + tau K v_j,
+//   y2_j = -(T x1)_j + alpha x2_j,     (T v)_j  = v_j - v_{j-1} + tau K v_j,
+//
+// and the transpose A^T = [[alpha I, -T^T], [T, alpha I]].
+//
+// One thread owns one spatial point and marches over a chunk of time blocks:
+// its 2*dim face weights and the diagonal of tau K are loaded once, the time
+// neighbour x1_{j-1} / x2_{j+1} is carried in registers, and the spatial
+// neighbours come through L1/L2 (the rows above/below belong to blocks that
+// run concurrently on the same time chunk).  DRAM traffic is the minimum:
+// read x once, write y once.
+#include "common.cuh"
+
+namespace pcopt {
+
+namespace {
+
+template <typename Tin, int DIM, bool TRANSPOSE>
+__global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, double* __restrict__ y,
+                                                     const double* __restrict__ w,
+                                                     const double* __restrict__ diag, int m, int64_t ms,
+                                                     int n, int tj, double alpha) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ms) return;
+  const int j0 = blockIdx.y * tj;
+  const int j1 = min(n, j0 + tj);
+  if (j0 >= n) return;
+
+  const int i1 = (int)(s % m);
+  const int64_t r = s / m;
+  const int i2 = (int)(DIM == 2 ? r : r % m);
+  const int i3 = (int)(DIM == 3 ? r / m : 0);
+
+  // neighbour offsets (0 when the neighbour is a boundary node -> value 0)
+  int64_t off[2 * DIM];
+  bool ex[2 * DIM];
+  double wv[2 * DIM];
+  const int64_t mm = (int64_t)m * m;
+  off[0] = -1;
+  ex[0] = i1 > 0;
+  off[1] = 1;
+  ex[1] = i1 < m - 1;
+  off[2] = -(int64_t)m;
+  ex[2] = i2 > 0;
+  off[3] = m;
+  ex[3] = i2 < m - 1;
+  if (DIM == 3) {
+    off[4] = -mm;
+    ex[4] = i3 > 0;
+    off[5] = mm;
+    ex[5] = i3 < m - 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * DIM; ++k) wv[k] = w[(int64_t)k * ms + s];
+  const double dg = diag[s];
+
+  const Tin* x1 = x;
+  const Tin* x2 = x + (int64_t)n * ms;
+  double* y1 = y;
+  double* y2 = y + (int64_t)n * ms;
+
+  auto tauK = [&](const Tin* base, double centre) -> double {
+    double acc = dg * centre;
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k) {
+      double nb = ex[k] ? (double)__ldg(base + off[k]) : 0.0;
+      acc = fma(-wv[k], nb, acc);
+    }
+    return acc;
+  };
+
+  double x1prev = (j0 > 0) ? (double)x1[(int64_t)(j0 - 1) * ms + s] : 0.0;
+  double x2c = (double)x2[(int64_t)j0 * ms + s];
+  for (int j = j0; j < j1; ++j) {
+    const int64_t idx = (int64_t)j * ms + s;
+    const double x1c = (double)x1[idx];
+    const double x2n = (j + 1 < n) ? (double)x2[idx + ms] : 0.0;
+    const double k1 = tauK(x1 + idx, x1c);
+    const double k2 = tauK(x2 + idx, x2c);
+    const double tT_x2 = x2c - x2n + k2;     // (T^T x2)_j
+    const double t_x1 = x1c - x1prev + k1;   // (T x1)_j
+    if (!TRANSPOSE) {
+      y1[idx] = fma(alpha, x1c, tT_x2);
+      y2[idx] = fma(alpha, x2c, -t_x1);
+    } else {
+      y1[idx] = fma(alpha, x1c, -tT_x2);
+      y2[idx] = fma(alpha, x2c, t_x1);
+    }
+    x1prev = x1c;
+    x2c = x2n;
+  }
+}
+
+}  // namespace
+
+template <typename Tin>
+cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>& st, double alpha,
+                          const Tin* x, double* y, bool transpose) {
+  const int threads = 256;
+  const int tj = n < 32 ? n : 32;
+  dim3 grid((unsigned)((g.np + threads - 1) / threads), (unsigned)((n + tj - 1) / tj));
+  const double U = 2.0 * (double)n * (double)g.np;
+  const double bytes = U * (sizeof(Tin) + sizeof(double)) + (2.0 * g.dim + 1) * g.np * 8.0;
+  const double flops = U * (4.0 * g.dim + 5.0);
+  L.begin(KC_MATVEC);
+  if (g.dim == 2) {
+    if (transpose)
+      matvec_kernel<Tin, 2, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+    else
+      matvec_kernel<Tin, 2, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+  } else {
+    if (transpose)
+      matvec_kernel<Tin, 3, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+    else
+      matvec_kernel<Tin, 3, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+  }
+  return L.end(KC_MATVEC, bytes, flops);
+}
+
+template cudaError_t launch_matvec<double>(Launch&, const Grid&, int, const Stencil<double>&, double,
+                                           const double*, double*, bool);
+template cudaError_t launch_matvec<float>(Launch&, const Grid&, int, const Stencil<double>&, double,
+                                          const float*, double*, bool);
+
+}  // namespace pcopt

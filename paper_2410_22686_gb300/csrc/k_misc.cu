@@ -1,0 +1,113 @@
+// Right-hand side of the all-at-once system (Eq. main_system_before /
+// Eq. main_system) and the stencil derivative used for dJ/d(log a).
+#include "common.cuh"
+
+namespace pcopt {
+
+namespace {
+
+// b1_j = tau g_j ;  b2_j = -sqrt(gamma) (tau f_j + [j = 1] y0)
+__global__ void build_rhs_kernel(int64_t ms, int n, double tau, double sg, const double* __restrict__ f,
+                                 const double* __restrict__ g, const double* __restrict__ y0, double* __restrict__ b) {
+  const int64_t tot = (int64_t)n * ms;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += stride) {
+    b[e] = tau * g[e];
+    double fv = f ? tau * f[e] : 0.0;
+    if (e < ms && y0) fv += y0[e];
+    b[tot + e] = -sg * fv;
+  }
+}
+
+// partial[c][P] = sum_{j in chunk c} sum_{faces (P,Q)} (l1_P-l1_Q)(x2_P-x2_Q) - (l2_P-l2_Q)(x1_P-x1_Q)
+template <int DIM>
+__global__ void __launch_bounds__(256) grad_partial_kernel(const double* __restrict__ x, const double* __restrict__ lam,
+                                                           double* __restrict__ partial, int m, int64_t ms, int n,
+                                                           int tj) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ms) return;
+  const int j0 = blockIdx.y * tj;
+  const int j1 = min(n, j0 + tj);
+  const int i1 = (int)(s % m);
+  const int64_t r = s / m;
+  const int i2 = (int)(DIM == 2 ? r : r % m);
+  const int i3 = (int)(DIM == 3 ? r / m : 0);
+  int64_t off[2 * DIM];
+  bool ex[2 * DIM];
+  const int64_t mm = (int64_t)m * m;
+  off[0] = -1;
+  ex[0] = i1 > 0;
+  off[1] = 1;
+  ex[1] = i1 < m - 1;
+  off[2] = -(int64_t)m;
+  ex[2] = i2 > 0;
+  off[3] = m;
+  ex[3] = i2 < m - 1;
+  if (DIM == 3) {
+    off[4] = -mm;
+    ex[4] = i3 > 0;
+    off[5] = mm;
+    ex[5] = i3 < m - 1;
+  }
+  const int64_t half = (int64_t)n * ms;
+  double acc = 0.0;
+  for (int j = j0; j < j1; ++j) {
+    const int64_t o = (int64_t)j * ms + s;
+    const double x1 = x[o], x2 = x[half + o], l1 = lam[o], l2 = lam[half + o];
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k) {
+      double dx1 = x1, dx2 = x2, dl1 = l1, dl2 = l2;
+      if (ex[k]) {
+        dx1 -= x[o + off[k]];
+        dx2 -= x[half + o + off[k]];
+        dl1 -= lam[o + off[k]];
+        dl2 -= lam[half + o + off[k]];
+      }
+      acc = fma(dl1, dx2, acc);
+      acc = fma(-dl2, dx1, acc);
+    }
+  }
+  partial[(int64_t)blockIdx.y * ms + s] = acc;
+}
+
+// grad_P = -tau a_P/(2h^2) sum_c partial[c][P]
+__global__ void grad_finish_kernel(const double* __restrict__ partial, int nchunks, int64_t ms, double scale,
+                                   const double* __restrict__ a_int, double* __restrict__ grad) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ms) return;
+  double t = 0.0;
+  for (int c = 0; c < nchunks; ++c) t += partial[(int64_t)c * ms + s];
+  grad[s] = scale * a_int[s] * t;
+}
+
+}  // namespace
+
+cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
+                             const double* g, const double* y0, double* b) {
+  const int64_t tot = (int64_t)n * ms;
+  int64_t blocks = (tot + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  L.begin(KC_RHS);
+  build_rhs_kernel<<<(unsigned)blocks, 256, 0, L.stream>>>(ms, n, tau, sqrt_gamma, f, g, y0, b);
+  return L.end(KC_RHS, tot * (16.0 + (f ? 8.0 : 0.0)) + ms * 8.0, 3.0 * tot);
+}
+
+// grad: ms doubles; partial: ceil(n/tj)*ms doubles of scratch
+cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, const double* a_int, const double* x,
+                                const double* lam, double* partial, int tj, double* grad) {
+  const int nchunks = (n + tj - 1) / tj;
+  dim3 grid((unsigned)((g.np + 255) / 256), (unsigned)nchunks);
+  L.begin(KC_GRAD);
+  if (g.dim == 2)
+    grad_partial_kernel<2><<<grid, 256, 0, L.stream>>>(x, lam, partial, g.m, g.np, n, tj);
+  else
+    grad_partial_kernel<3><<<grid, 256, 0, L.stream>>>(x, lam, partial, g.m, g.np, n, tj);
+  cudaError_t e = L.end(KC_GRAD, 32.0 * n * g.np + 8.0 * nchunks * g.np, 4.0 * g.dim * 7.0 * n * g.np);
+  if (e != cudaSuccess) return e;
+  L.begin(KC_GRAD);
+  grad_finish_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, L.stream>>>(partial, nchunks, g.np, scale, a_int, grad);
+  return L.end(KC_GRAD, 8.0 * (nchunks + 2) * g.np, 1.0 * nchunks * g.np);
+}
+
+}  // namespace pcopt

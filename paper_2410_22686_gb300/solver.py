@@ -1,0 +1,151 @@
+"""Python front end over the C ABI: one ``Solver`` per problem.
+
+Tensors are torch float64 CUDA tensors; all-at-once vectors have shape
+``(2, n) + (m1,)*dim`` (or any shape with ``2*n*m1**dim`` elements) laid out as
+[half][time block][space] with x1 fastest (include/pcopt.h).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+_SPATIAL = {"auto": capi.PC_SPATIAL_AUTO, "fst": capi.PC_SPATIAL_FST, "mg": capi.PC_SPATIAL_MG}
+_PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": capi.PC_PREC_MIXED_FP32,
+         "bf16s": capi.PC_PREC_MIXED_BF16S}
+_MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """Handle for one discrete optimal-control problem (pc_setup ... pc_destroy)."""
+
+    def __init__(self, dim: int, m1: int, n: int, T: float, gamma: float, eps: float,
+                 a_nodes: np.ndarray | None = None, spatial: str = "auto", precision: str = "fp64",
+                 max_iter: int = 60):
+        self.lib = capi.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("pcopt needs a CUDA device")
+        self.dim, self.m1, self.n = dim, m1, n
+        self.T, self.gamma, self.eps = T, gamma, eps
+        self.max_iter = max_iter
+        prm = capi.pc_params(dim, m1, n, T, gamma, eps, _SPATIAL[spatial], _PREC[precision], max_iter)
+        a_ptr = None
+        if a_nodes is not None:
+            self._a = np.ascontiguousarray(a_nodes, dtype=np.float64)
+            if self._a.size != (m1 + 2) ** dim:
+                raise ValueError("a_nodes must have (m1+2)^dim entries")
+            a_ptr = self._a.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        capi.check(self.lib.pc_setup(ctypes.byref(prm), a_ptr, _stream(), ctypes.byref(h)))
+        self.h = h
+        self.ms = m1 ** dim
+        self.vec_len = 2 * n * self.ms
+        self.tau = T / (n + 1)
+
+    # ---------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- helpers
+    def empty_vector(self):
+        return torch.empty((2, self.n) + (self.m1,) * self.dim, dtype=torch.float64, device="cuda")
+
+    def _vec(self, t):
+        if t.numel() != self.vec_len:
+            raise ValueError(f"expected {self.vec_len} entries, got {t.numel()}")
+        return t
+
+    # ---------------------------------------------------------------- operators
+    def matvec(self, x, out=None, transpose=False):
+        self._vec(x)
+        y = torch.empty_like(x) if out is None else out
+        fn = self.lib.pc_matvec_transpose if transpose else self.lib.pc_matvec
+        capi.check(fn(self.h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def apply_precond(self, v, out=None):
+        self._vec(v)
+        w = torch.empty_like(v) if out is None else out
+        capi.check(self.lib.pc_apply_precond(self.h, _ptr(v), _ptr(w), _stream()))
+        return w
+
+    def build_rhs(self, f, g, y0=None, out=None):
+        b = self.empty_vector() if out is None else out
+        capi.check(self.lib.pc_build_rhs(self.h, _ptr(f), _ptr(g), _ptr(y0), _ptr(b), _stream()))
+        return b
+
+    def solve(self, b, x0=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
+        """GMRES on A x = b; returns (x, iterations, relative residual)."""
+        self._vec(b)
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = self.lib.pc_gmres_solve(self.h, _ptr(b), _ptr(x), rtol, maxit or self.max_iter, _MODE[mode],
+                                     ctypes.byref(it), ctypes.byref(rr), _stream())
+        if st != capi.PC_ERR_NOT_CONVERGED or raise_on_nonconv:
+            capi.check(st)
+        return x, it.value, rr.value
+
+    def adjoint_solve(self, c, lam0=None, rtol=1e-8, maxit=None, mode="right"):
+        """GMRES on A^T lam = c; returns (lam, iterations, relative residual)."""
+        self._vec(c)
+        lam = torch.zeros_like(c) if lam0 is None else lam0.clone()
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        capi.check(self.lib.pc_adjoint_solve(self.h, _ptr(c), _ptr(lam), rtol, maxit or self.max_iter,
+                                             _MODE[mode], ctypes.byref(it), ctypes.byref(rr), _stream()))
+        return lam, it.value, rr.value
+
+    def grad_log_a(self, x, lam, out=None):
+        g = torch.empty((self.m1,) * self.dim, dtype=torch.float64, device="cuda") if out is None else out
+        capi.check(self.lib.pc_grad_log_a(self.h, _ptr(x), _ptr(lam), _ptr(g), _stream()))
+        return g
+
+    # ---------------------------------------------------------------- instrumentation
+    def profile(self, on=True):
+        capi.check(self.lib.pc_profile(self.h, 1 if on else 0))
+
+    def stats(self):
+        arr = (capi.pc_kernel_stat * 64)()
+        cnt = ctypes.c_int(0)
+        capi.check(self.lib.pc_stats(self.h, arr, 64, ctypes.byref(cnt)))
+        out = {}
+        for i in range(cnt.value):
+            s = arr[i]
+            out[s.name.decode()] = {"launches": s.launches, "ms": s.total_ms, "bytes": s.bytes, "flops": s.flops}
+        return out
+
+    def stats_reset(self):
+        capi.check(self.lib.pc_stats_reset(self.h))
+
+    def launch_count(self):
+        return int(self.lib.pc_launch_count(self.h))

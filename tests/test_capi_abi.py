@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every function include/pcopt.h
+declares (no GPU needed: nothing here calls into a kernel)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2410_22686_gb300 import build as pbuild, capi
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = pbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = capi.header_functions()
+    for must in ("pc_setup", "pc_destroy", "pc_matvec", "pc_apply_precond", "pc_gmres_solve",
+                 "pc_adjoint_solve", "pc_build_rhs", "pc_grad_log_a"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in capi.header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_function():
+    assert set(capi.header_functions()) <= set(capi._SIGNATURES)
+
+
+def test_exported_symbols_are_plain_c(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pbuild.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    for name in capi.header_functions():
+        assert name in exported, name
+
+
+def test_status_strings_and_argument_errors_without_gpu():
+    l = capi.load()
+    assert l.pc_status_string(capi.PC_OK) == b"ok"
+    assert l.pc_status_string(capi.PC_ERR_ARG) == b"invalid argument"
+    # invalid parameters are rejected on the host before any device work
+    h = ctypes.c_void_p()
+    bad = [
+        capi.pc_params(4, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10),     # dim
+        capi.pc_params(2, 7, 6, 1.0, 1e-2, 0.5, 0, 0, 10),     # n not a power of two
+        capi.pc_params(2, 7, 8, 1.0, 0.0, 0.5, 0, 0, 10),      # gamma
+        capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.0, 0, 0, 10),     # eps
+        capi.pc_params(2, 7, 8, 1.0, 1e-2, 1.5, 0, 0, 10),     # eps
+        capi.pc_params(2, 6, 8, 1.0, 1e-2, 0.5, 2, 0, 10),     # MG needs 2^k - 1
+        capi.pc_params(2, 7, 8, -1.0, 1e-2, 0.5, 0, 0, 10),    # T
+        capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 0),      # max_iter
+    ]
+    for p in bad:
+        assert l.pc_setup(ctypes.byref(p), None, None, ctypes.byref(h)) == capi.PC_ERR_ARG
+        assert len(l.pc_last_error()) > 0
+    # non-positive coefficient
+    import numpy as np
+    a = np.ones((9, 9))
+    a[3, 3] = -1.0
+    p = capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10)
+    assert l.pc_setup(ctypes.byref(p), a.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(h)) == capi.PC_ERR_ARG
+    assert l.pc_destroy(None) == capi.PC_OK

@@ -1,0 +1,268 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative, max-norm over the output unless stated):
+* FP64 operators (A x, A^T x, P_eps^{-1} v, b): 1e-12.  Both sides evaluate the
+  same formulas in FP64; only the summation order differs (~1e-15).
+* FP32 preconditioner: 1e-5.  FP32 unit roundoff 6e-8, times the depth of the
+  FFT (2 log2 n butterflies) and of the multigrid cycle (< 40 operations per
+  level, 8 levels) on well-conditioned shifted systems.
+* Solutions: 1e-10 (FP64 path) and 1e-7 (mixed path) in the 2-norm, with both
+  sides solved far below that (GPU 1e-12 / 1e-11, oracle 1e-13).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import gradient as ogr, krylov as okr, precond as opc, system as osy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_22686_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _solver(d, m1, n, a, spatial, precision="fp64", gamma=1e-3, eps=0.3, T=1.0, max_iter=40):
+    from paper_2410_22686_gb300 import Solver
+    return Solver(d, m1, n, T, gamma, eps, a, spatial=spatial, precision=precision, max_iter=max_iter)
+
+
+def _coef(d, m1, kind, seed=0):
+    if kind == "const":
+        return None
+    return np.exp(0.4 * S.random_vector((m1 + 2,) * d, seed))
+
+
+def _a_or_one(a, d, m1):
+    return a if a is not None else np.ones((m1 + 2,) * d)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _rel(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+MATVEC_CASES = [(2, 7, 4, "var"), (2, 31, 32, "var"), (2, 20, 8, "const"), (3, 7, 8, "var"),
+                (3, 5, 2, "const"), (2, 1, 1, "var"), (2, 15, 64, "var"), (2, 33, 4, "const")]
+
+
+@pytest.mark.parametrize("d,m1,n,kind", MATVEC_CASES)
+def test_matvec_and_transpose_match_oracle(d, m1, n, kind):
+    if kind == "var" and (m1 + 1) & m1:
+        pytest.skip("variable a needs the multigrid grid sizes")
+    a = _coef(d, m1, kind, seed=m1 + n)
+    sol = _solver(d, m1, n, a, "auto", gamma=2e-3)
+    x = S.random_vector((2, n) + (m1,) * d, 7)
+    aa = _a_or_one(a, d, m1)
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, 2e-3)
+    y = sol.matvec(_dev(x)).cpu().numpy()
+    assert _rel(y, osy.apply_A(x, aa, tau, alpha)) <= 1e-12
+    yt = sol.matvec(_dev(x), transpose=True).cpu().numpy()
+    assert _rel(yt, osy.apply_AT(x, aa, tau, alpha)) <= 1e-12
+    sol.close()
+
+
+def test_build_rhs_matches_oracle():
+    prob = S.example1_problem(15, 16, 1e-4)
+    sol = _solver(2, 15, 16, None, "fst", gamma=prob.gamma, eps=prob.eps)
+    b = sol.build_rhs(_dev(prob.f), _dev(prob.g), _dev(prob.y0)).cpu().numpy()
+    ref = osy.build_rhs(prob.f, prob.g, prob.y0, prob.tau, prob.gamma)
+    assert _rel(b, ref) <= 1e-14
+    # NULL f and y0 mean zero fields
+    b2 = sol.build_rhs(None, _dev(prob.g), None).cpu().numpy()
+    ref2 = osy.build_rhs(np.zeros_like(prob.f), prob.g, np.zeros_like(prob.y0), prob.tau, prob.gamma)
+    assert _rel(b2, ref2) <= 1e-14
+    sol.close()
+
+
+PRECOND_CASES = [(2, 31, 32, "const", "fst"), (2, 20, 16, "const", "fst"), (2, 15, 16, "var", "mg"),
+                 (2, 63, 8, "var", "mg"), (3, 7, 8, "var", "mg"), (3, 5, 4, "const", "fst"),
+                 (2, 1, 2, "var", "mg"), (2, 3, 1, "var", "mg"), (2, 7, 128, "var", "mg"),
+                 (2, 31, 256, "var", "mg")]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n,kind,spatial", PRECOND_CASES)
+def test_precond_apply_matches_oracle(d, m1, n, kind, spatial, precision, tol):
+    a = _coef(d, m1, kind, seed=3 * m1 + n)
+    gamma, eps = 1e-4, 0.25
+    sol = _solver(d, m1, n, a, spatial, precision=precision, gamma=gamma, eps=eps)
+    v = S.random_vector((2, n) + (m1,) * d, 11)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    spat = opc.make_spatial_solver(spatial, a, m1, d, tau)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, spat)
+    assert _rel(w, ref) <= tol
+    sol.close()
+
+
+def _oracle_solution(prob, spatial, rtol=1e-13):
+    a = _a_or_one(prob.a_nodes, prob.d, prob.m1)
+    tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, prob.gamma)
+    b = osy.build_rhs(prob.f, prob.g, prob.y0, tau, prob.gamma)
+    spat = opc.make_spatial_solver(spatial, prob.a_nodes, prob.m1, prob.d, tau)
+    A = lambda v: osy.apply_A(v, a, tau, alpha)
+    Pi = lambda v: opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, spat)
+    return b, A, Pi, okr.gmres(A, Pi, b, rtol=rtol, maxit=200, mode="right")
+
+
+@pytest.mark.parametrize("case", ["plain", "variable", "variable3d"])
+def test_fp64_gmres_solution_matches_oracle(case):
+    if case == "plain":
+        prob, spatial = S.plain_fp64_problem(), "fst"
+    elif case == "variable":
+        prob, spatial = S.variable_2d_problem(gamma=1e-4, m1=31, n=32), "mg"
+    else:
+        prob, spatial = S.gaussian_field_3d_problem(m1=7, n=16), "mg"
+    b, A, Pi, ref = _oracle_solution(prob, spatial)
+    sol = _solver(prob.d, prob.m1, prob.n, prob.a_nodes, spatial, gamma=prob.gamma, eps=prob.eps, max_iter=60)
+    x, iters, rel = sol.solve(_dev(b), rtol=1e-12)
+    xg = x.cpu().numpy()
+    assert rel <= 1e-12
+    assert np.linalg.norm(xg - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    # the GPU's own reported residual is the true one
+    r = b - A(xg)
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rel) <= 1e-13
+    sol.close()
+
+
+@pytest.mark.parametrize("gamma", [1e-8, 1e-4, 1e-2])
+def test_iteration_counts_match_oracle_left_and_right(gamma):
+    prob = S.variable_2d_problem(gamma=gamma, m1=31, n=32)
+    a, tau, alpha = prob.a_nodes, prob.tau, osy.alpha_weight(prob.T, prob.n, gamma)
+    b = osy.build_rhs(prob.f, prob.g, prob.y0, tau, gamma)
+    mg = opc.MGSpatialSolver(a, tau)
+    A = lambda v: osy.apply_A(v, a, tau, alpha)
+    Pi = lambda v: opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, mg)
+    sol = _solver(2, 31, 32, a, "mg", gamma=gamma, eps=prob.eps, max_iter=60)
+    for mode in ("left", "right"):
+        ref = okr.gmres(A, Pi, b, rtol=1e-8, maxit=100, mode=mode)
+        x, iters, rel = sol.solve(_dev(b), rtol=1e-8, mode=mode)
+        assert iters == ref.iters, (mode, iters, ref.iters)
+        assert rel <= 1e-8
+    sol.close()
+
+
+def test_gmres_kth_iterate_matches_oracle():
+    # equal fixed iteration count: the iterates agree to 1e-10 (both FP64)
+    prob = S.variable_2d_problem(gamma=1e-4, m1=15, n=16)
+    b, A, Pi, _ = _oracle_solution(prob, "mg")
+    ref = okr.gmres(A, Pi, b, rtol=1e-30, maxit=5, mode="right")
+    sol = _solver(2, 15, 16, prob.a_nodes, "mg", gamma=prob.gamma, eps=prob.eps)
+    x, iters, _ = sol.solve(_dev(b), rtol=1e-30, maxit=5, raise_on_nonconv=False)
+    assert iters == 5
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    sol.close()
+
+
+@pytest.mark.parametrize("case", ["variable", "plain"])
+def test_mixed_precision_fgmres_matches_fp64_oracle(case):
+    if case == "plain":
+        prob, spatial = S.plain_fp64_problem(), "fst"
+    else:
+        prob, spatial = S.variable_2d_problem(gamma=1e-6, m1=63, n=64), "mg"
+    b, A, Pi, ref = _oracle_solution(prob, spatial)
+    sol = _solver(prob.d, prob.m1, prob.n, prob.a_nodes, spatial, precision="fp32", gamma=prob.gamma,
+                  eps=prob.eps, max_iter=60)
+    x, iters, rel = sol.solve(_dev(b), rtol=1e-11)
+    assert rel <= 1e-11
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    sol.close()
+
+
+def test_nonzero_initial_guess_and_zero_rhs():
+    prob = S.variable_2d_problem(gamma=1e-4, m1=15, n=8)
+    b, A, Pi, ref = _oracle_solution(prob, "mg")
+    sol = _solver(2, 15, 8, prob.a_nodes, "mg", gamma=prob.gamma, eps=prob.eps)
+    x0 = _dev(ref.x + 1e-3 * S.random_vector(ref.x.shape, 5))
+    for mode in ("right", "left"):
+        x, iters, rel = sol.solve(_dev(b), x0=x0, rtol=1e-12, mode=mode)
+        assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    z, iters, rel = sol.solve(torch.zeros_like(x0), rtol=1e-8)
+    assert iters == 0 and float(z.abs().max()) == 0.0
+    sol.close()
+
+
+def test_adjoint_solve_matches_oracle():
+    prob = S.variable_2d_problem(gamma=1e-4, m1=31, n=16)
+    a, tau, alpha = prob.a_nodes, prob.tau, osy.alpha_weight(prob.T, prob.n, prob.gamma)
+    c = S.random_vector((2, 16, 31, 31), 21)
+    sol = _solver(2, 31, 16, a, "mg", gamma=prob.gamma, eps=prob.eps, max_iter=150)
+    lam, iters, rel = sol.adjoint_solve(_dev(c), rtol=1e-12)
+    lg = lam.cpu().numpy()
+    resid = c - osy.apply_AT(lg, a, tau, alpha)
+    assert np.linalg.norm(resid) <= 1e-11 * np.linalg.norm(c)
+    sol.close()
+
+
+def test_grad_log_a_matches_oracle_formula():
+    d, m1, n, gamma = 2, 31, 16, 1e-4
+    a = np.exp(0.3 * S.random_vector((m1 + 2,) * d, 31))
+    x = S.random_vector((2, n, m1, m1), 32)
+    lam = S.random_vector((2, n, m1, m1), 33)
+    sol = _solver(d, m1, n, a, "mg", gamma=gamma)
+    g = sol.grad_log_a(_dev(x), _dev(lam)).cpu().numpy()
+    tau = osy.time_step(1.0, n)
+    g_ref, _ = ogr.adjoint_gradient(x, lam, np.zeros((n, m1, m1)), a, tau, gamma)
+    assert _rel(g, g_ref) <= 1e-12
+    sol.close()
+
+
+def test_grad_log_a_3d_matches_oracle_formula():
+    d, m1, n, gamma = 3, 7, 8, 1e-2
+    a = np.exp(0.3 * S.random_vector((m1 + 2,) * d, 34))
+    x = S.random_vector((2, n) + (m1,) * d, 35)
+    lam = S.random_vector((2, n) + (m1,) * d, 36)
+    sol = _solver(d, m1, n, a, "mg", gamma=gamma)
+    g = sol.grad_log_a(_dev(x), _dev(lam)).cpu().numpy()
+    g_ref, _ = ogr.adjoint_gradient(x, lam, np.zeros((n,) + (m1,) * d), a, osy.time_step(1.0, n), gamma)
+    assert _rel(g, g_ref) <= 1e-12
+    sol.close()
+
+
+def test_full_size_bench_configuration_precond_and_matvec():
+    # the 255 x 255, n = 256 workload the benchmark times, in its launch configuration
+    prob = S.variable_2d_problem(gamma=1e-4)
+    tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, prob.gamma)
+    v = S.random_vector((2, prob.n, prob.m1, prob.m1), 41)
+    sol = _solver(2, prob.m1, prob.n, prob.a_nodes, "mg", precision="fp32", gamma=prob.gamma,
+                  eps=prob.eps, max_iter=4)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    y = sol.matvec(_dev(v)).cpu().numpy()
+    mg = opc.MGSpatialSolver(prob.a_nodes, tau)
+    ref = opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, mg)
+    assert _rel(w, ref) <= 1e-5
+    assert _rel(y, osy.apply_A(v, prob.a_nodes, tau, alpha)) <= 1e-12
+    sol.close()
+
+
+def test_invalid_arguments_return_errors_and_context_survives():
+    from paper_2410_22686_gb300 import capi
+    with pytest.raises(capi.PCError) as ei:
+        _solver(2, 6, 8, np.ones((8, 8)), "mg")
+    assert ei.value.status == capi.PC_ERR_ARG
+    with pytest.raises(capi.PCError) as ei:
+        _solver(2, 7, 8, np.ones((9, 9)) * np.linspace(1, 2, 9), "fst")
+    assert ei.value.status == capi.PC_ERR_ARG
+    sol = _solver(2, 7, 8, None, "fst")
+    with pytest.raises(capi.PCError):
+        sol.solve(_dev(np.ones((2, 8, 7, 7))), rtol=1e-8, maxit=1000)
+    with pytest.raises(capi.PCError) as ei:
+        b = np.ones((2, 8, 7, 7))
+        b[0, 0, 0, 0] = np.nan
+        sol.solve(_dev(b), rtol=1e-8)
+    assert ei.value.status == capi.PC_ERR_BREAKDOWN
+    # the context is still usable
+    x, it, rel = sol.solve(_dev(np.ones((2, 8, 7, 7))), rtol=1e-10)
+    assert rel <= 1e-10
+    sol.close()
