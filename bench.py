@@ -1,0 +1,401 @@
+"""Benchmark: preconditioned GMRES solve time on the 2D variable-coefficient
+workload (255 x 255 interior grid, n = 256 time blocks, T = 1,
+a = 1 + 0.5 sin(2 pi x1) cos(2 pi x2), eps = sqrt(tau), 16-mode target, f = 0,
+y0 = 0), gamma in {1e-2, 1e-4, 1e-6, 1e-8}: FP32 preconditioner inside flexible
+GMRES (FP64 Arnoldi, Givens, matvec and true residual) against the plain FP64
+solve, to a relative residual of 1e-8.
+
+One step = the four gamma solves of the mixed-precision path, right-hand
+sides resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (plain numpy FP64) on the machine's host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+# the oracle runs single-threaded (numpy FFT and elementwise code are; pin BLAS too)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+METRIC = "GMRES solve time to 1e-8 rel. residual, mixed vs FP64; precond-apply HBM GB/s"
+GAMMAS = (1e-2, 1e-4, 1e-6, 1e-8)
+M1, NT = 255, 256
+RTOL = 1e-8
+# Iterations reported by the paper for its variable-coefficient example at the same
+# number of unknowns (h = tau = 2^-8, gamma = 1e-4; Table 6): used only to scale the
+# oracle's per-iteration time to a solve in the reference arm.
+PAPER_ITERS_H8 = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cap", type=int, default=60, help="Krylov basis capacity")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases for profiling runs (the default is the benchmark workload)
+    ap.add_argument("--m1", type=int, default=255)
+    ap.add_argument("--nt", type=int, default=256)
+    ap.add_argument("--gammas", default=",".join(str(g) for g in GAMMAS))
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    a = ap.parse_args()
+    a.gammas = tuple(float(x) for x in a.gammas.split(","))
+    return a
+
+
+def workload_config(m1=M1, nt=NT, gammas=GAMMAS):
+    vec_mb = 2 * m1 * m1 * nt * 8 / 1e6
+    return {"workload": f"2D variable-a parabolic control, {m1}x{m1} grid, n={nt} time blocks, "
+                        f"gamma in {{{','.join(f'{g:g}' for g in gammas)}}}, eps=sqrt(tau), rtol 1e-8",
+            "m1": m1, "n": nt, "dim": 2, "unknowns_per_solve": 2 * m1 * m1 * nt,
+            "gammas": list(gammas), "rtol": RTOL,
+            "l2": f"inputs larger than L2 (each all-at-once vector is {vec_mb:.0f} MB)" if vec_mb > 129
+                  else f"vectors of {vec_mb:.0f} MB: not larger than L2"}
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return dist if ws > 1 else None
+
+
+def dist_max(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower() in ("active", "0x1") or v == "1":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_iteration_seconds(gamma=1e-4, m1=M1, nt=NT):
+    """Time one right-preconditioned (flexible) GMRES iteration of the CPU oracle on
+    the full workload: P_eps^{-1} v (FFT, one V-cycle per shifted system, inverse
+    FFT), A z, and the Gram-Schmidt step against the first basis vector."""
+    import synthetic as S
+    from oracle import precond as opc, system as osy
+    prob = S.variable_2d_problem(gamma=gamma, m1=m1, n=nt)
+    tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, gamma)
+    b = osy.build_rhs(prob.f, prob.g, prob.y0, tau, gamma)
+    mg = opc.MGSpatialSolver(prob.a_nodes, tau)
+    t0 = time.perf_counter()
+    v = b / np.linalg.norm(b)
+    z = opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, mg)
+    w = osy.apply_A(z, prob.a_nodes, tau, alpha)
+    h = float(np.vdot(w.ravel(), v.ravel()))
+    w = w - h * v
+    _ = np.linalg.norm(w)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_iteration_seconds(m1=args.m1, nt=args.nt)
+    times = [oracle_iteration_seconds(m1=args.m1, nt=args.nt) for _ in range(args.steps)]
+    per_iter = statistics.median(times)
+    value = per_iter * PAPER_ITERS_H8
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.m1, args.nt, args.gammas),
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": 1, "kind": "oracle",
+                         "sample": f"one oracle GMRES iteration (preconditioner apply, matvec, one Gram-Schmidt "
+                                   f"step) on the full workload at gamma=1e-4 per step, median of {args.steps}, "
+                                   f"times {PAPER_ITERS_H8} iterations (the paper's count at this size)"},
+        "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def _e2e(args, sols, rhs, gammas, torch):
+    """Same metric through the public host-buffer call (copies inside the timed region)."""
+    hb = [torch.empty(b.shape, dtype=torch.float64, pin_memory=True) for b in rhs]
+    for h_, b in zip(hb, rhs):
+        h_.copy_(b)
+    hx = [torch.empty(b.shape, dtype=torch.float64, pin_memory=True) for b in rhs]
+    for s, h_, x_ in zip(sols, hb, hx):
+        s.solve_host(h_, x_host=x_, rtol=RTOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s, h_, x_ in zip(sols, hb, hx):
+            s.solve_host(h_, x_host=x_, rtol=RTOL)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / (args.steps * len(gammas))
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    import synthetic as S
+    from paper_2410_22686_gb300 import Solver
+    from paper_2410_22686_gb300 import build as pbuild
+    pbuild.build()
+
+    GAM = args.gammas
+    probs = [S.variable_2d_problem(gamma=g, m1=args.m1, n=args.nt) for g in GAM]
+    U = probs[0].unknowns
+    f = torch.from_numpy(probs[0].f).to(dev)
+    y0 = torch.from_numpy(probs[0].y0).to(dev)
+
+    def make(precision):
+        sols, rhs = [], []
+        for p in probs:
+            s = Solver(2, args.m1, args.nt, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision=precision,
+                       max_iter=args.cap)
+            rhs.append(s.build_rhs(f, torch.from_numpy(p.g).to(dev), y0))
+            sols.append(s)
+        torch.cuda.synchronize()
+        return sols, rhs
+
+    def step(sols, rhs, record):
+        for s, b in zip(sols, rhs):
+            x, it, rr = s.solve(b, rtol=RTOL, raise_on_nonconv=False)
+            record.append((it, rr))
+
+    def timed(sols, rhs, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(sols, rhs, [])
+        for s in sols:
+            s.stats_reset()
+            s.profile(profile)
+        rec = []
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step(sols, rhs, rec)
+        e1.record()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = clk.stop()
+        ms = dist_max(dist, e0.elapsed_time(e1), dev)
+        for s in sols:
+            s.profile(False)
+        return ms, rec, clocks
+
+    # ---------------- mixed precision (the timed headline)
+    sols, rhs = make("fp32")
+    ms_mixed, rec_mixed, clocks = timed(sols, rhs, args.steps, args.warmup, profile=True)
+    launches = sum(s.launch_count() for s in sols)
+    stats = {}
+    for s in sols:
+        for k, v in s.stats().items():
+            a = stats.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for q in a:
+                a[q] += v[q]
+    iters_mixed = [it for it, _ in rec_mixed[: len(GAM)]]
+    relres_mixed = [rr for _, rr in rec_mixed[: len(GAM)]]
+    value = ms_mixed / 1000.0 / (args.steps * len(GAM))   # per solve; every rank runs its own replica
+
+    # precond-apply GB/s (mixed): the apply alone, on the same handle and launch configuration
+    s0 = sols[min(1, len(sols) - 1)]
+    v = torch.randn(U, dtype=torch.float64, device=dev)
+    w = torch.empty_like(v)
+    for _ in range(3):
+        s0.apply_precond(v, out=w)
+    s0.stats_reset()
+    reps = 10
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ea.record()
+    for _ in range(reps):
+        s0.apply_precond(v, out=w)
+    eb.record()
+    torch.cuda.synchronize()
+    pstats = s0.stats()
+    p_bytes = sum(x["bytes"] for x in pstats.values()) / reps
+    p_ms = ea.elapsed_time(eb) / reps
+    precond_gbs = p_bytes / (p_ms * 1e-3) / 1e9
+
+    # ---------------- end to end through host buffers (same metric)
+    e2e_s = None
+    if not args.skip_e2e:
+        e2e_s = _e2e(args, sols, rhs, GAM, torch)
+    for s in sols:
+        s.close()
+    del sols
+    torch.cuda.empty_cache()
+
+    # ---------------- plain FP64 solve (comparison)
+    fp64_s, iters64 = None, None
+    if not args.skip_fp64:
+        sols64, rhs64 = make("fp64")
+        ms64, rec64, _ = timed(sols64, rhs64, args.steps, 1)
+        iters64 = [it for it, _ in rec64[: len(GAM)]]
+        fp64_s = ms64 / 1000.0 / (args.steps * len(GAM))
+        for s in sols64:
+            s.close()
+        del sols64
+
+    # ---------------- roofline of the dominant kernel class
+    tot_ms = sum(v["ms"] for v in stats.values())
+    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    peaks, peak_src = {}, "fallback 6.8 TB/s (of fallback)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+        peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12     # 2 FP64 FMA/clk/SM at 2070 MHz
+    dom_avg_ms = dom["ms"] / max(dom["launches"], 1)
+    dom_bytes = dom["bytes"] / max(dom["launches"], 1)
+    dom_flops = dom["flops"] / max(dom["launches"], 1)
+    gbs = dom_bytes / (dom_avg_ms * 1e-3) / 1e9
+    tfl = dom_flops / (dom_avg_ms * 1e-3) / 1e12
+    if dom_name in ("arnoldi_dot", "arnoldi_update_norm", "matvec", "x_update") and tfl / fp64_peak_tflops > gbs / hbm_peak:
+        roof = {"bound": "alu", "achieved": tfl, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": tfl / fp64_peak_tflops, "traffic": None, "kernel": dom_name,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
+                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "kernel": dom_name, "peak_source": peak_src}
+    roof["share_of_kernel_time"] = dom["ms"] / tot_ms if tot_ms else None
+    breakdown = {k: {"share": v["ms"] / tot_ms if tot_ms else None, "launches": v["launches"],
+                     "avg_us": 1000 * v["ms"] / v["launches"] if v["launches"] else None,
+                     "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None}
+                 for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": workload_config(args.m1, args.nt, GAM),
+        "fp64_solve_s": fp64_s, "mixed_solve_s": value,
+        "mixed_speedup_vs_fp64": (fp64_s / value) if fp64_s else None,
+        "iters_mixed": iters_mixed, "iters_fp64": iters64, "relres_mixed": relres_mixed,
+        "unknowns_iters_per_s": sum(U * it for it in iters_mixed) / (ms_mixed / 1000.0 / args.steps),
+        "precond_apply": {"gbs": precond_gbs, "ms": p_ms, "frac_of_hbm": precond_gbs / hbm_peak,
+                          "bytes": p_bytes, "precision": "fp32"},
+        "roofline": roof, "kernel_breakdown": breakdown,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 8 * U * len(GAM),
+                "d2h_bytes_per_step": 8 * U * len(GAM),
+                "how": "Solver.solve_host: pinned host b -> device, GMRES, device x -> pinned host, per solve"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        t_iter = oracle_iteration_seconds(m1=args.m1, nt=args.nt)
+        mean_it = sum(iters_mixed) / len(iters_mixed)
+        line["cpu_baseline"] = {"value": t_iter * mean_it, "unit": "s/solve", "cores": 1, "kind": "oracle",
+                                "sample": "one oracle GMRES iteration (preconditioner apply, matvec, one "
+                                          "Gram-Schmidt step) on the full workload at gamma=1e-4, times the "
+                                          f"mean GPU iteration count {mean_it:.1f}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

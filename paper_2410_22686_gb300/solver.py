@@ -115,6 +115,21 @@ class Solver:
             capi.check(st)
         return x, it.value, rr.value
 
+    def solve_host(self, b_host, x_host=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
+        """Solve from a HOST right-hand side: copy b to the device, run GMRES,
+        copy x back into ``x_host`` (pinned CPU tensors give asynchronous copies).
+        Returns (x_host, iterations, relative residual)."""
+        if b_host.is_cuda or b_host.dtype != torch.float64:
+            raise ValueError("b_host must be a float64 CPU tensor")
+        b = torch.empty(b_host.shape, dtype=torch.float64, device="cuda")
+        b.copy_(b_host, non_blocking=True)
+        x, it, rr = self.solve(b, rtol=rtol, maxit=maxit, mode=mode, raise_on_nonconv=raise_on_nonconv)
+        if x_host is None:
+            x_host = torch.empty(b_host.shape, dtype=torch.float64, pin_memory=True)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return x_host, it, rr
+
     def adjoint_solve(self, c, lam0=None, rtol=1e-8, maxit=None, mode="right"):
         """GMRES on A^T lam = c; returns (lam, iterations, relative residual)."""
         self._vec(c)
