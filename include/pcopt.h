@@ -151,6 +151,32 @@ int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, in
  *   same spatial ordering), overwritten. */
 int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream);
 
+/* Allocation-free variant of pc_grad_log_a (the paper has no counterpart: it
+ * is a deployment feature of this library).  For callers that may not
+ * allocate device memory at all -- e.g. code running under another
+ * framework's memory pool or a fixed pre-allocated budget, where cudaMalloc is
+ * forbidden after start-up -- and so cannot create a handle.  It needs no
+ * handle and calls no cudaMalloc, cudaFree or allocating library routine; the
+ * caller passes every input and the output:
+ *   dim, m1, n, T: as in pc_params (tau = T/(n+1), h = 1/(m1+1));
+ *   a_int:  device, ms = m1^dim FP64, the coefficient a at the interior nodes
+ *           (same spatial ordering as the vectors);
+ *   x, lam: device all-at-once vectors (2*n*ms FP64);
+ *   grad:   device, ms FP64, overwritten with the same quantity as pc_grad_log_a.
+ * Scratch: the per-time-chunk partial sums live in one file-scope device array
+ * of PC_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB) that every GPU loading the
+ * library holds until exit.  m1^dim above that size is rejected with
+ * PC_ERR_ARG; larger n only coarsens the time chunks.  All calls on a device
+ * share the array and it keeps the last call's contents (every entry a call
+ * reads it first writes, so nothing needs clearing); calls whose execution
+ * overlaps on the GPU (different streams without ordering) race on it.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. */
+#define PC_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const double* a_int, const double* x,
+                          const double* lam, double* grad, void* stream);
+
 /* Problem sizes of a handle: ms = m1^dim and the all-at-once length 2*n*ms. */
 int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
 

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "pc_gmres_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
     "pc_adjoint_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
+    "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
     "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "pc_profile": (_i, [_vp, _i]),
     "pc_stats": (_i, [_vp, ctypes.POINTER(pc_kernel_stat), _i, _ip]),

@@ -29,6 +29,10 @@ static int cuda_fail(cudaError_t e, const char* where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
   return PC_ERR_CUDA;
 }
+namespace pcopt {
+int set_error(int status, const std::string& msg) { return fail(status, msg); }
+}  // namespace pcopt
+
 #define PC_CUDA(call)                                  \
   do {                                                 \
     cudaError_t _e = (call);                           \

@@ -198,4 +198,7 @@ cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, c
 
 int num_sms();
 
+// record `msg` as the calling thread's last error (pc_last_error) and return `status`
+int set_error(int status, const std::string& msg);
+
 }  // namespace pcopt
