@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--gammas", default=",".join(str(g) for g in GAMMAS))
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-bf16", action="store_true")
     a = ap.parse_args()
     a.gammas = tuple(float(x) for x in a.gammas.split(","))
     return a
@@ -326,6 +327,18 @@ def run_ours(args):
             s.close()
         del sols64
 
+    # ---------------- BF16-storage smoother variant (FP32 arithmetic)
+    bf16_s, iters_bf16 = None, None
+    if not args.skip_bf16:
+        solsb, rhsb = make("bf16s")
+        msb, recb, _ = timed(solsb, rhsb, args.steps, 1)
+        iters_bf16 = [it for it, _ in recb[: len(GAM)]]
+        bf16_s = msb / 1000.0 / (args.steps * len(GAM))
+        for s in solsb:
+            s.close()
+        del solsb
+        torch.cuda.empty_cache()
+
     # ---------------- roofline of the dominant kernel class
     tot_ms = sum(v["ms"] for v in stats.values())
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
@@ -364,6 +377,7 @@ def run_ours(args):
         "config": workload_config(args.m1, args.nt, GAM),
         "fp64_solve_s": fp64_s, "mixed_solve_s": value,
         "mixed_speedup_vs_fp64": (fp64_s / value) if fp64_s else None,
+        "bf16_storage_solve_s": bf16_s, "iters_bf16_storage": iters_bf16,
         "iters_mixed": iters_mixed, "iters_fp64": iters64, "relres_mixed": relres_mixed,
         "unknowns_iters_per_s": sum(U * it for it in iters_mixed) / (ms_mixed / 1000.0 / args.steps),
         "precond_apply": {"gbs": precond_gbs, "ms": p_ms, "frac_of_hbm": precond_gbs / hbm_peak,

@@ -97,6 +97,13 @@ typedef struct pc_handle pc_handle;
  * MG with m1 != 2^k-1), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
 
+/* Replace the coefficient a(x) of an existing handle without reallocating:
+ * the stencil of every level (and the FST eigenvalues) is recomputed on the
+ * host and copied into the handle's buffers.  a_nodes: HOST, (m1+2)^dim values
+ * as in pc_setup (NULL means a == 1).  Synchronises `stream`.
+ * Errors: PC_ERR_ARG (a <= 0 or non-finite; non-constant a on an FST handle). */
+int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
+
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
 int pc_destroy(pc_handle* h);
 

@@ -50,6 +50,7 @@ _dpp = ctypes.POINTER(ctypes.c_double)
 _SIGNATURES = {
     "pc_setup": (_i, [ctypes.POINTER(pc_params), _vp, _vp, ctypes.POINTER(_vp)]),
     "pc_destroy": (_i, [_vp]),
+    "pc_set_coefficient": (_i, [_vp, _vp, _vp]),
     "pc_matvec": (_i, [_vp, _dp, _dp, _vp]),
     "pc_matvec_transpose": (_i, [_vp, _dp, _dp, _vp]),
     "pc_apply_precond": (_i, [_vp, _dp, _dp, _vp]),

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pcopt.h"
@@ -49,7 +50,8 @@ const char* kernel_class_name(int kc) {
                                         "mg_resid_restrict", "mg_prolong_correct", "mg_coarsest",
                                         "arnoldi_dot",   "arnoldi_update_norm", "reduce_partials",
                                         "normalize",     "givens",       "x_update",
-                                        "axpby",         "build_rhs",    "grad_stencil"};
+                                        "axpby",         "build_rhs",    "grad_stencil",
+                                        "arnoldi_reorth"};
   return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
 }
 
@@ -153,6 +155,7 @@ struct pc_handle {
   double tau = 0, alpha = 0, sqrtg = 0, h = 0;
   int spatial = PC_SPATIAL_MG;
   bool fp32 = false;
+  bool bf16s = false;  // multigrid iterates stored as BF16 pairs (FP32 arithmetic)
   int cap = 0;
   double a_const = 1.0;
 
@@ -186,10 +189,11 @@ struct pc_handle {
   double* gvec = nullptr;
   double* hcol = nullptr;  // 2 x (cap+1)
   double* ycoef = nullptr;
-  double* scal = nullptr;  // [0] nrm2, [1] est, [2] ref, [3] tmp
+  double* scal = nullptr;  // [0] nrm2, [1] est, [2] ref, [3] tmp, [4..9] Arnoldi step scalars
   double* partial = nullptr;
-  int nblocks = 0;
-  double* host = nullptr;  // pinned: [0] est, [1] ref, [2] nrm2
+  int nblocks = 0;         // rows of `partial`: SMs x blocks per SM
+  double* host = nullptr;  // pinned: [0] est, [1] ref, [2] nrm2, ... (16 doubles)
+  int64_t reorth_count = 0;
   std::vector<void*> allocs;
   Prof prof;
 };
@@ -255,6 +259,72 @@ static void level_stencil(const std::vector<double>& a, int m, int dim, double t
   }
 }
 
+// stencils of every level: level 0 from `a`, coarser levels (multigrid) from the
+// nodal coefficient injected level by level, a_c[I] = a[2I] (boundary nodes included)
+static void all_level_stencils(const std::vector<double>& a, int m1, int dim, double tau, bool multigrid,
+                               std::vector<std::vector<double>>& ws, std::vector<std::vector<double>>& ds,
+                               std::vector<int>& ms) {
+  std::vector<double> acur = a;
+  int m = m1;
+  ws.clear();
+  ds.clear();
+  ms.clear();
+  while (true) {
+    std::vector<double> w, d;
+    level_stencil(acur, m, dim, tau, w, d);
+    ws.push_back(std::move(w));
+    ds.push_back(std::move(d));
+    ms.push_back(m);
+    if (!multigrid || m <= 1) break;
+    const int mc = (m - 1) / 2, Mc = mc + 2, Mf = m + 2;
+    std::vector<double> ac(dim == 2 ? (size_t)Mc * Mc : (size_t)Mc * Mc * Mc);
+    for (size_t q = 0; q < ac.size(); ++q) {
+      const int c1 = (int)(q % Mc);
+      const size_t rr = q / Mc;
+      const int c2 = (int)(dim == 2 ? rr : rr % Mc);
+      const int c3 = dim == 3 ? (int)(rr / Mc) : 0;
+      ac[q] = dim == 2 ? acur[(size_t)(2 * c2) * Mf + 2 * c1] : acur[((size_t)(2 * c3) * Mf + 2 * c2) * Mf + 2 * c1];
+    }
+    acur.swap(ac);
+    m = mc;
+  }
+}
+
+// interior values of the nodal coefficient, in vector ordering
+static std::vector<double> interior_of(const std::vector<double>& a, int m1, int dim) {
+  const int M = m1 + 2;
+  const int64_t ms = dim == 2 ? (int64_t)m1 * m1 : (int64_t)m1 * m1 * m1;
+  std::vector<double> ai((size_t)ms);
+  for (int64_t s = 0; s < ms; ++s) {
+    const int i1 = (int)(s % m1) + 1;
+    const int64_t r = s / m1;
+    const int i2 = (int)(dim == 2 ? r : r % m1) + 1;
+    const int i3 = dim == 3 ? (int)(r / m1) + 1 : 0;
+    ai[(size_t)s] = dim == 2 ? a[(size_t)i2 * M + i1] : a[((size_t)i3 * M + i2) * M + i1];
+  }
+  return ai;
+}
+
+// FST eigenvalues tau * c * sum_axes 4 sin^2(pi i/(2(m+1)))/h^2 of tau K for a == c
+static std::vector<double> fst_eigenvalues(int m, int dim, double tau, double c) {
+  const double h = 1.0 / (m + 1);
+  std::vector<double> mu(m);
+  for (int i = 0; i < m; ++i) {
+    const double sv = std::sin(M_PI * (double)(i + 1) / (2.0 * (m + 1)));
+    mu[i] = 4.0 * sv * sv / (h * h);
+  }
+  const int64_t ms = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
+  std::vector<double> lam((size_t)ms);
+  for (int64_t s = 0; s < ms; ++s) {
+    const int i1 = (int)(s % m);
+    const int64_t r = s / m;
+    const int i2 = (int)(dim == 2 ? r : r % m);
+    const int i3 = dim == 3 ? (int)(r / m) : -1;
+    lam[(size_t)s] = tau * c * (mu[i1] + mu[i2] + (i3 >= 0 ? mu[i3] : 0.0));
+  }
+  return lam;
+}
+
 template <typename T>
 static int upload(pc_handle* h, T** dst, const std::vector<double>& src, cudaStream_t st) {
   std::vector<T> tmp(src.begin(), src.end());
@@ -299,7 +369,6 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   if (!(p->eps > 0) || !(p->eps <= 1.0)) return fail(PC_ERR_ARG, "eps must lie in (0, 1]");
   if (p->precision != PC_PREC_FP64 && p->precision != PC_PREC_MIXED_FP32 && p->precision != PC_PREC_MIXED_BF16S)
     return fail(PC_ERR_ARG, "unknown precision");
-  if (p->precision == PC_PREC_MIXED_BF16S) return fail(PC_ERR_UNSUPPORTED, "BF16-storage smoother not built yet");
   if (p->spatial < 0 || p->spatial > 2) return fail(PC_ERR_ARG, "unknown spatial solver");
   if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
 
@@ -339,6 +408,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->h = 1.0 / (m1 + 1);
   h->spatial = spatial;
   h->fp32 = p->precision != PC_PREC_FP64;
+  h->bf16s = p->precision == PC_PREC_MIXED_BF16S && spatial == PC_SPATIAL_MG;
   h->cap = p->max_iter;
   h->a_const = a[0];
   h->prof.on = false;
@@ -346,39 +416,24 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
 
   int rc = PC_OK;
   const size_t cb = h->fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t ub = h->bf16s ? sizeof(__nv_bfloat162) : cb;  // storage of the multigrid iterates
   // ---- level hierarchy: level 0 always (matvec), coarser ones for multigrid
   {
-    std::vector<double> acur = a;
-    int m = m1;
-    while (true) {
+    std::vector<std::vector<double>> ws, ds;
+    std::vector<int> mlev;
+    all_level_stencils(a, m1, dim, h->tau, spatial == PC_SPATIAL_MG, ws, ds, mlev);
+    for (size_t l = 0; l < mlev.size(); ++l) {
       LevelBuf L;
-      L.m = m;
-      L.np = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
-      std::vector<double> w, d;
-      level_stencil(acur, m, dim, h->tau, w, d);
-      if ((rc = upload(h, &L.w64, w, st))) goto fail_out;
-      if ((rc = upload(h, &L.d64, d, st))) goto fail_out;
-      if ((rc = upload(h, &L.w32, w, st))) goto fail_out;
-      if ((rc = upload(h, &L.d32, d, st))) goto fail_out;
+      L.m = mlev[l];
+      L.np = dim == 2 ? (int64_t)L.m * L.m : (int64_t)L.m * L.m * L.m;
+      if ((rc = upload(h, &L.w64, ws[l], st))) goto fail_out;
+      if ((rc = upload(h, &L.d64, ds[l], st))) goto fail_out;
+      if ((rc = upload(h, &L.w32, ws[l], st))) goto fail_out;
+      if ((rc = upload(h, &L.d32, ds[l], st))) goto fail_out;
       if ((rc = dev_alloc(h, &L.r, (size_t)h->planes * L.np * cb))) goto fail_out;
-      if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * cb))) goto fail_out;
-      const bool more = spatial == PC_SPATIAL_MG && m > 1;
-      if (more && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb))) goto fail_out;
+      if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * ub))) goto fail_out;
+      if (l + 1 < mlev.size() && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb))) goto fail_out;
       h->lv.push_back(L);
-      if (!more) break;
-      // inject the nodal coefficient: a_c[I] = a[2I] over all nodes incl. boundary
-      const int mc = (m - 1) / 2, Mc = mc + 2, Mf = m + 2;
-      std::vector<double> ac(dim == 2 ? (size_t)Mc * Mc : (size_t)Mc * Mc * Mc);
-      for (size_t q = 0; q < ac.size(); ++q) {
-        const int c1 = (int)(q % Mc);
-        const size_t rr = q / Mc;
-        const int c2 = (int)(dim == 2 ? rr : rr % Mc);
-        const int c3 = dim == 3 ? (int)(rr / Mc) : 0;
-        ac[q] = dim == 2 ? acur[(size_t)(2 * c2) * Mf + 2 * c1]
-                         : acur[((size_t)(2 * c3) * Mf + 2 * c2) * Mf + 2 * c1];
-      }
-      acur.swap(ac);
-      m = mc;
     }
   }
   // ---- time FFT tables
@@ -410,22 +465,11 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   // ---- FST tables (constant a)
   if (spatial == PC_SPATIAL_FST) {
     const int m = m1;
-    std::vector<double> S((size_t)m * m), lam((size_t)h->ms, 0.0), mu(m);
+    std::vector<double> S((size_t)m * m);
     const double sc = std::sqrt(2.0 / (m + 1));
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = sc * std::sin(M_PI * (double)(i + 1) * (j + 1) / (m + 1));
-    for (int i = 0; i < m; ++i) {
-      const double sv = std::sin(M_PI * (double)(i + 1) / (2.0 * (m + 1)));
-      mu[i] = 4.0 * sv * sv / (h->h * h->h);
-    }
-    for (int64_t s = 0; s < h->ms; ++s) {
-      const int i1 = (int)(s % m);
-      const int64_t r = s / m;
-      const int i2 = (int)(dim == 2 ? r : r % m);
-      const int i3 = dim == 3 ? (int)(r / m) : -1;
-      double v = mu[i1] + mu[i2] + (i3 >= 0 ? mu[i3] : 0.0);
-      lam[(size_t)s] = h->tau * h->a_const * v;
-    }
+    const std::vector<double> lam = fst_eigenvalues(m, dim, h->tau, h->a_const);
     if ((rc = upload(h, &h->S64, S, st))) goto fail_out;
     if ((rc = upload(h, &h->S32, S, st))) goto fail_out;
     if ((rc = upload(h, &h->lamK64, lam, st))) goto fail_out;
@@ -434,15 +478,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   }
   // ---- interior coefficient (gradient) and its scratch
   {
-    std::vector<double> ai((size_t)h->ms);
-    for (int64_t s = 0; s < h->ms; ++s) {
-      const int i1 = (int)(s % m1) + 1;
-      const int64_t r = s / m1;
-      const int i2 = (int)(dim == 2 ? r : r % m1) + 1;
-      const int i3 = dim == 3 ? (int)(r / m1) + 1 : 0;
-      ai[(size_t)s] = dim == 2 ? a[(size_t)i2 * M + i1] : a[((size_t)i3 * M + i2) * M + i1];
-    }
-    if ((rc = upload(h, &h->a_int, ai, st))) goto fail_out;
+    if ((rc = upload(h, &h->a_int, interior_of(a, m1, dim), st))) goto fail_out;
     const int nch = (h->n + h->grad_tj - 1) / h->grad_tj;
     if ((rc = dev_alloc_t(h, &h->grad_partial, (size_t)nch * h->ms))) goto fail_out;
   }
@@ -450,7 +486,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   {
     const size_t U = h->U;
     const int cap = h->cap;
-    h->nblocks = num_sms() * 4;
+    h->nblocks = num_sms() * kMaxBlocksPerSM;
     if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * U))) goto fail_out;
     if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
@@ -462,9 +498,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = dev_alloc_t(h, &h->gvec, (size_t)cap + 2))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->hcol, (size_t)2 * (cap + 1)))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->ycoef, (size_t)cap + 1))) goto fail_out;
-    if ((rc = dev_alloc_t(h, &h->scal, 8))) goto fail_out;
-    if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 1)))) goto fail_out;
-    cudaError_t e = cudaMallocHost((void**)&h->host, 8 * sizeof(double));
+    if ((rc = dev_alloc_t(h, &h->scal, 16))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 2)))) goto fail_out;
+    cudaError_t e = cudaMallocHost((void**)&h->host, 16 * sizeof(double));
     if (e != cudaSuccess) {
       rc = fail(PC_ERR_OOM, "cudaMallocHost failed");
       goto fail_out;
@@ -483,6 +519,53 @@ fail_out:
   release(h);
   delete h;
   return rc;
+}
+
+template <typename T>
+static int refill(T* dst, const std::vector<double>& src, cudaStream_t st, std::vector<T>& stage) {
+  stage.assign(src.begin(), src.end());
+  PC_CUDA(cudaMemcpyAsync(dst, stage.data(), stage.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream) {
+  if (!h) return fail(PC_ERR_ARG, "pc_set_coefficient: null handle");
+  const int dim = h->dim, m1 = h->m1, M = m1 + 2;
+  const size_t nodes = dim == 2 ? (size_t)M * M : (size_t)M * M * M;
+  std::vector<double> a(nodes, 1.0);
+  bool constant = true;
+  if (a_nodes) {
+    for (size_t i = 0; i < nodes; ++i) {
+      const double v = a_nodes[i];
+      if (!(v > 0) || !std::isfinite(v)) return fail(PC_ERR_ARG, "a(x) must be finite and > 0 on every node");
+      a[i] = v;
+      if (v != a_nodes[0]) constant = false;
+    }
+  }
+  if (h->spatial == PC_SPATIAL_FST && !constant) return fail(PC_ERR_ARG, "FST handle needs a constant coefficient");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<std::vector<double>> ws, ds;
+  std::vector<int> mlev;
+  all_level_stencils(a, m1, dim, h->tau, h->spatial == PC_SPATIAL_MG, ws, ds, mlev);
+  if (mlev.size() != h->lv.size()) return fail(PC_ERR_ARG, "pc_set_coefficient: level mismatch");
+  std::vector<double> s64;
+  std::vector<float> s32;
+  int rc;
+  for (size_t l = 0; l < mlev.size(); ++l) {
+    if ((rc = refill(h->lv[l].w64, ws[l], st, s64))) return rc;
+    if ((rc = refill(h->lv[l].d64, ds[l], st, s64))) return rc;
+    if ((rc = refill(h->lv[l].w32, ws[l], st, s32))) return rc;
+    if ((rc = refill(h->lv[l].d32, ds[l], st, s32))) return rc;
+  }
+  if ((rc = refill(h->a_int, interior_of(a, m1, dim), st, s64))) return rc;
+  h->a_const = a[0];
+  if (h->spatial == PC_SPATIAL_FST) {
+    const std::vector<double> lam = fst_eigenvalues(m1, dim, h->tau, h->a_const);
+    if ((rc = refill(h->lamK64, lam, st, s64))) return rc;
+    if ((rc = refill(h->lamK32, lam, st, s32))) return rc;
+  }
+  return PC_OK;
 }
 
 extern "C" int pc_destroy(pc_handle* h) {
@@ -543,65 +626,73 @@ struct Tables<float> {
   static const float* lamK(const pc_handle* h) { return h->lamK32; }
 };
 
-// step 2: every plane of lv[0].r solved into lv[0].u
-template <typename Tc>
+// step 2: every plane of lv[0].r solved into lv[0].u (iterates stored as TU)
+template <typename Tc, typename TU>
 static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
   typedef typename Cx<Tc>::t C;
   const int P = h->planes;
   const C* sig = Tables<Tc>::sig(h);
-  if (h->spatial == PC_SPATIAL_FST) {
-    const Grid g = grid_of(h, 0);
-    C* bufs[2] = {(C*)h->lv[0].r, (C*)h->fst_tmp};
-    int cur = 0;
-    cudaError_t e;
-    for (int ax = 0; ax < h->dim; ++ax) {
-      if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], bufs[1 - cur])) != cudaSuccess) return e;
-      cur = 1 - cur;
+  cudaError_t e;
+  if constexpr (std::is_same<TU, C>::value) {
+    if (h->spatial == PC_SPATIAL_FST) {
+      const Grid g = grid_of(h, 0);
+      C* bufs[2] = {(C*)h->lv[0].r, (C*)h->fst_tmp};
+      int cur = 0;
+      for (int ax = 0; ax < h->dim; ++ax) {
+        if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], bufs[1 - cur])) != cudaSuccess) return e;
+        cur = 1 - cur;
+      }
+      if ((e = launch_fst_divide<Tc>(L, g, P, Tables<Tc>::lamK(h), sig, bufs[cur])) != cudaSuccess) return e;
+      for (int ax = h->dim - 1; ax >= 0; --ax) {
+        C* dst = ax == 0 ? (C*)h->lv[0].u : bufs[1 - cur];
+        if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], dst)) != cudaSuccess) return e;
+        cur = 1 - cur;
+      }
+      return cudaSuccess;
     }
-    if ((e = launch_fst_divide<Tc>(L, g, P, Tables<Tc>::lamK(h), sig, bufs[cur])) != cudaSuccess) return e;
-    for (int ax = h->dim - 1; ax >= 0; --ax) {
-      C* dst = ax == 0 ? (C*)h->lv[0].u : bufs[1 - cur];
-      if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], dst)) != cudaSuccess) return e;
-      cur = 1 - cur;
-    }
-    return cudaSuccess;
   }
   // multigrid V(1,0)
   const int nl = (int)h->lv.size();
-  cudaError_t e;
   for (int l = 0; l + 1 < nl; ++l) {
     const LevelBuf& Lb = h->lv[l];
     Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
     const Grid g = grid_of(h, l);
-    if ((e = launch_mg_smooth<Tc>(L, g, P, st, sig, (const C*)Lb.r, (C*)Lb.u)) != cudaSuccess) return e;
-    if ((e = launch_mg_resid_restrict<Tc>(L, g, P, st, sig, (const C*)Lb.r, (const C*)Lb.u, (C*)Lb.res,
-                                          (C*)h->lv[l + 1].r)) != cudaSuccess)
+    if ((e = launch_mg_smooth<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u)) != cudaSuccess) return e;
+    if ((e = launch_mg_resid_restrict<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (const TU*)Lb.u, (C*)Lb.res,
+                                              (C*)h->lv[l + 1].r)) != cudaSuccess)
       return e;
   }
   {
     const LevelBuf& Lc = h->lv[nl - 1];
-    if ((e = launch_mg_coarsest<Tc>(L, P, lvd<Tc>(Lc), sig, (const C*)Lc.r, (C*)Lc.u)) != cudaSuccess) return e;
+    if ((e = launch_mg_coarsest<Tc, TU>(L, P, lvd<Tc>(Lc), sig, (const C*)Lc.r, (TU*)Lc.u)) != cudaSuccess) return e;
   }
   for (int l = nl - 2; l >= 0; --l) {
-    if ((e = launch_mg_prolong<Tc>(L, grid_of(h, l), P, (const C*)h->lv[l + 1].u, (C*)h->lv[l].u)) != cudaSuccess)
+    if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
+        cudaSuccess)
       return e;
   }
   return cudaSuccess;
 }
 
-template <typename Tc, typename Tout>
+template <typename Tc, typename TU, typename Tout>
 static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w) {
   typedef typename Cx<Tc>::t C;
   cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::tw(h), (C*)h->lv[0].r);
   if (e != cudaSuccess) return e;
-  if ((e = spatial_solve<Tc>(h, L)) != cudaSuccess) return e;
-  return launch_tfft_inverse<Tc, Tout>(L, h->ms, h->n, (const C*)h->lv[0].u, Tables<Tc>::dpow(h), Tables<Tc>::tw(h),
-                                       w);
+  if ((e = spatial_solve<Tc, TU>(h, L)) != cudaSuccess) return e;
+  return launch_tfft_inverse<Tc, TU, Tout>(L, h->ms, h->n, (const TU*)h->lv[0].u, Tables<Tc>::dpow(h),
+                                           Tables<Tc>::tw(h), w);
+}
+
+// FP32 preconditioner into Tout, with the handle's iterate storage
+template <typename Tout>
+static cudaError_t precond32(pc_handle* h, Launch& L, const double* v, Tout* w) {
+  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout>(h, L, v, w) : precond_t<float, float2, Tout>(h, L, v, w);
 }
 
 // w (FP64) = P^{-1} v in the handle's precision
 static cudaError_t precond64(pc_handle* h, Launch& L, const double* v, double* w) {
-  return h->fp32 ? precond_t<float, double>(h, L, v, w) : precond_t<double, double>(h, L, v, w);
+  return h->fp32 ? precond32<double>(h, L, v, w) : precond_t<double, double2, double>(h, L, v, w);
 }
 
 static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32, double* y, bool transpose) {
@@ -658,11 +749,13 @@ extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, d
 // ---------------------------------------------------------------------------
 // GMRES (Section 3: zero initial guess, relative tolerance; Lemma 2.1)
 // ---------------------------------------------------------------------------
-static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref) {
-  PC_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+// host[0] = est, host[1] = ref, host[8] = re-orthogonalisation flag of the last step
+static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref, bool* reorth = nullptr) {
+  PC_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
   PC_CUDA(cudaStreamSynchronize(st));
   if (est) *est = h->host[0];
   if (ref) *ref = h->host[1];
+  if (reorth) *reorth = h->host[8] != 0.0;
   return PC_OK;
 }
 
@@ -680,6 +773,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   double* est = h->scal + 1;
   double* ref = h->scal + 2;
   double* V = h->V;
+  const ArnoldiScalars AS{h->scal + 4, h->scal + 5, h->scal + 6, h->scal + 7, h->scal + 8, h->scal + 9};
   cudaError_t e;
 #define GM_CUDA(...)                                   \
   do {                                                 \
@@ -687,14 +781,14 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   } while (0)
 
   // is x0 zero?  (one norm + readback)
-  GM_CUDA(launch_norm2(L, x, U, h->partial, h->nblocks, h->scal + 3));
+  GM_CUDA(launch_norm2(L, x, U, h->partial, h->scal + 3));
   PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
   PC_CUDA(cudaStreamSynchronize(st));
   const bool x0_zero = h->host[2] == 0.0;
 
   // reference norm and r0 (stored unnormalised in V_0)
   if (mode == PC_GMRES_RIGHT) {
-    GM_CUDA(launch_norm2(L, b, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_norm2(L, b, U, h->partial, nrm2));
     GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 1));  // ref = ||b||
     if (x0_zero) {
       PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -703,18 +797,18 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
       GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, V, U));
     }
-    GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_norm2(L, V, U, h->partial, nrm2));
     GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 0));
   } else {
     GM_CUDA(precond64(h, L, b, V));  // P^{-1} b
-    GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+    GM_CUDA(launch_norm2(L, V, U, h->partial, nrm2));
     GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 1));  // ref = ||P^{-1} b||
     if (!x0_zero) {
       GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
       PC_CUDA(cudaMemcpyAsync(h->tbuf, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
       GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, h->tbuf, U));
       GM_CUDA(precond64(h, L, h->tbuf, V));
-      GM_CUDA(launch_norm2(L, V, U, h->partial, h->nblocks, nrm2));
+      GM_CUDA(launch_norm2(L, V, U, h->partial, nrm2));
       GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 0));
     }
   }
@@ -734,7 +828,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     if (relres) *relres = est_h;
     return PC_OK;
   }
-  GM_CUDA(launch_scale_by_inv_norm(L, V, V, U, nrm2));
+  GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr));
 
   int k = 0;
   bool converged = false;
@@ -744,31 +838,40 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     if (mode == PC_GMRES_RIGHT) {
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
-        GM_CUDA(precond_t<float, float>(h, L, vj, zj));
+        GM_CUDA(precond32<float>(h, L, vj, zj));
         GM_CUDA(matvec_any(h, L, zj, true, vn, false));
       } else {
         double* zj = (double*)h->Z + (size_t)j * U;
-        GM_CUDA(precond_t<double, double>(h, L, vj, zj));
+        GM_CUDA(precond_t<double, double2, double>(h, L, vj, zj));
         GM_CUDA(matvec_any(h, L, zj, false, vn, false));
       }
     } else {
       GM_CUDA(matvec_any(h, L, vj, false, h->wbuf, false));
       GM_CUDA(precond64(h, L, h->wbuf, vn));
     }
-    // classical Gram-Schmidt, twice
-    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->nblocks, h->hcol));
-    GM_CUDA(launch_update_norm(L, V, U, j + 1, h->hcol, vn, U, h->partial, h->nblocks, nrm2));
-    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->nblocks, h->hcol + ldh));
-    GM_CUDA(launch_update_norm(L, V, U, j + 1, h->hcol + ldh, vn, U, h->partial, h->nblocks, nrm2));
-    GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, nrm2, est, ref));
-    if (int rc = read_scalars(h, st, &est_h, nullptr)) return rc;
+    // classical Gram-Schmidt with Pythagorean normalisation, re-orthogonalised only
+    // when the check flags cancellation (the gated kernels then do the work)
+    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol, AS.ww, nullptr));
+    GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
+    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol, vn, U, AS.inv, h->partial, AS.q, nullptr));
+    GM_CUDA(launch_arnoldi_check(L, AS));
+    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
+    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol + ldh, vn, U, nullptr, h->partial, AS.rho2, AS.flag));
+    GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag));
+    GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, est, ref));
+    bool reorth = false;
+    if (int rc = read_scalars(h, st, &est_h, nullptr, &reorth)) return rc;
+    if (reorth) {  // book the second Gram-Schmidt pass that ran
+      h->prof.bytes[KC_REORTH] += 8.0 * U * (2.0 * (j + 1) + 6.0);
+      h->prof.flops[KC_REORTH] += 4.0 * U * (j + 1);
+      h->reorth_count++;
+    }
     k = j + 1;
     if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite residual estimate");
     if (est_h <= rtol) {
       converged = true;
       break;
     }
-    if (j + 1 < maxit) GM_CUDA(launch_scale_by_inv_norm(L, vn, vn, U, nrm2));
   }
   GM_CUDA(launch_backsolve(L, k, ldh, h->H, h->gvec, h->ycoef));
   if (mode == PC_GMRES_RIGHT) {
@@ -779,7 +882,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     // true residual ||b - A x|| / ||b||
     GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
     GM_CUDA(launch_axpby<double>(L, 1.0, b, -1.0, h->wbuf, U));
-    GM_CUDA(launch_norm2(L, h->wbuf, U, h->partial, h->nblocks, h->scal + 3));
+    GM_CUDA(launch_norm2(L, h->wbuf, U, h->partial, h->scal + 3));
     PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
     PC_CUDA(cudaStreamSynchronize(st));
     est_h = std::sqrt(h->host[2]) / ref_h;

@@ -2,6 +2,7 @@
 // Nothing here is part of the public C ABI (include/pcopt.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -51,6 +52,15 @@ __host__ __device__ __forceinline__ double2 cinv(double2 z) {
 template <typename T>
 __host__ __device__ __forceinline__ typename Cx<T>::t czero() { return cmk<T>(T(0), T(0)); }
 
+// storage of complex multigrid iterates: the compute type itself, or a BF16 pair
+// (FP32 arithmetic, BF16 storage) for the BF16-storage smoother variant
+__device__ __forceinline__ float2 ldc(const float2* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ double2 ldc(const double2* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p, int64_t i) { return __bfloat1622float2(p[i]); }
+__device__ __forceinline__ void stc(float2* p, int64_t i, float2 v) { p[i] = v; }
+__device__ __forceinline__ void stc(double2* p, int64_t i, double2 v) { p[i] = v; }
+__device__ __forceinline__ void stc(__nv_bfloat162* p, int64_t i, float2 v) { p[i] = __float22bfloat162_rn(v); }
+
 // ---------------------------------------------------------------------------
 // kernel classes (instrumentation buckets)
 // ---------------------------------------------------------------------------
@@ -73,6 +83,7 @@ enum KernelClass {
   KC_AXPBY,
   KC_RHS,
   KC_GRAD,
+  KC_REORTH,  // gated re-orthogonalisation passes (bytes booked only when they ran)
   KC_COUNT
 };
 const char* kernel_class_name(int kc);
@@ -136,10 +147,10 @@ cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>
 template <typename Tc>
 cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow,
                                 const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec);
-// inverse scaled time FFT + butterfly: spectral planes -> w (Tout [2][n][ms])
-template <typename Tc, typename Tout>
-cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const typename Cx<Tc>::t* spec,
-                                const Tc* dpow, const typename Cx<Tc>::t* tw, Tout* w);
+// inverse scaled time FFT + butterfly: spectral planes (stored as TU) -> w (Tout [2][n][ms])
+template <typename Tc, typename TU, typename Tout>
+cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow,
+                                const typename Cx<Tc>::t* tw, Tout* w);
 
 // FST: one DST-I along `axis` of every plane (out = S in), and the spectral divide
 template <typename Tc>
@@ -149,39 +160,48 @@ template <typename Tc>
 cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK,
                               const typename Cx<Tc>::t* sigma, typename Cx<Tc>::t* buf);
 
-// multigrid pieces (planes = 2*nfreq, sigma per plane)
-template <typename Tc>
+// multigrid pieces (planes = 2*nfreq, sigma per plane); iterates u stored as TU
+template <typename Tc, typename TU>
 cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
-                             const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
-                             typename Cx<Tc>::t* u);
-template <typename Tc>
+                             const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u);
+template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
-                                     const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
-                                     const typename Cx<Tc>::t* u, typename Cx<Tc>::t* res,
-                                     typename Cx<Tc>::t* rc);
-template <typename Tc>
-cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const typename Cx<Tc>::t* ec,
-                              typename Cx<Tc>::t* uf);
-template <typename Tc>
+                                     const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
+                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc);
+template <typename Tc, typename TU>
+cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* ec, TU* uf);
+template <typename Tc, typename TU>
 cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const typename Cx<Tc>::t* sigma,
-                               const typename Cx<Tc>::t* r, typename Cx<Tc>::t* u);
+                               const typename Cx<Tc>::t* r, TU* u);
 
-// Krylov (FP64): partial dots of nv vectors (stride ldv) with w, chunked launches
+// Krylov (FP64).  Device scalars of one Arnoldi step.
+struct ArnoldiScalars {
+  double* ww;    // ||w||^2 of the new vector (pass 1)
+  double* c;     // normalisation used in pass 2 (Pythagorean norm, or 1)
+  double* inv;   // 1/c
+  double* q;     // computed ||w - V d||^2
+  double* rho2;  // squared norm after re-orthogonalisation
+  double* flag;  // 1.0 when the step re-orthogonalised
+};
+constexpr int kMaxBlocksPerSM = 8;  // 256-thread blocks: partial-sum buffers hold SMs*8 rows
+// out = V^T w for nv vectors (stride ldv); optionally *ww = ||w||^2; skipped when gate && *gate == 0
+// (gated launches are booked under KC_REORTH with zero bytes; the caller adds them if they ran)
 cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, const double* w, size_t len,
-                            double* partial, int nblocks, double* out);
-// w -= sum_i h[i] V_i (h on device), writes partial sums of the new ||w||^2 and reduces into *nrm2
-cudaError_t launch_update_norm(Launch& L, const double* V, size_t ldv, int nv, const double* h, double* w,
-                               size_t len, double* partial, int nblocks, double* nrm2);
-// partial sums of ||w||^2 -> *nrm2
-cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, int nblocks, double* nrm2);
-// v = w * (1/sqrt(nrm2[0]))
-cudaError_t launch_scale_by_inv_norm(Launch& L, const double* w, double* v, size_t len, const double* nrm2);
-// y = a*x + b*y on [lo, hi) (x may be float)
+                            double* partial, double* out, double* ww, const double* gate);
+// v = (v - sum_i coef_i V_i) * (*scale or 1); *q = ||v - sum_i coef_i V_i||^2 (before scaling); gated
+cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
+                          const double* scale, double* partial, double* q, const double* gate);
+cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, double* nrm2);
+// v *= 1/sqrt(*nrm2); gated
+cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate);
+// y = a*x + b*y (x may be float)
 template <typename Tx>
 cudaError_t launch_axpby(Launch& L, double a, const Tx* x, double b, double* y, size_t len);
-// Givens update of column j of H, residual estimate
-cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec,
-                          const double* hcol, const double* nrm2, double* est, const double* ref);
+cudaError_t launch_arnoldi_prep(Launch& L, int nv, const double* d, ArnoldiScalars s);
+cudaError_t launch_arnoldi_check(Launch& L, ArnoldiScalars s);
+// column j of H from d (and e after re-orthogonalisation), Givens update, residual estimate
+cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec, const double* d,
+                          const double* e, ArnoldiScalars s, double* est, const double* ref);
 cudaError_t launch_backsolve(Launch& L, int k, int ldh, const double* H, const double* gvec, double* y);
 template <typename Tz>
 cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const double* y, double* x, size_t len);

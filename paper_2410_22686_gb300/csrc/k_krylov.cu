@@ -1,12 +1,20 @@
-// Arnoldi / GMRES building blocks, all FP64 (GMRES of Section 3, Lemma 2.1):
-// multi-dot h = V^T w, Gram-Schmidt update w -= V h fused with ||w||^2,
-// normalisation, Givens rotations of the Hessenberg column with the residual
-// estimate, back substitution and the solution update x += Z y.
+// Arnoldi / GMRES building blocks, all FP64 (GMRES of Section 3, Lemma 2.1).
 //
-// Reductions are deterministic: a fixed grid writes per-block partial sums
-// (warp shuffles, then shared memory), and a second kernel adds them in a
-// fixed order.  The multi-dot keeps up to kChunk accumulators per thread so
-// that V is read once and w once per chunk of vectors.
+// One Arnoldi step for the new vector w (stored in place of v_{j+1}):
+//   pass 1  d = V^T w and ||w||^2                       (multidot, one read of V and w)
+//   prep    c = sqrt(||w||^2 - ||d||^2)  (Pythagoras)    (one thread)
+//   pass 2  v_{j+1} = (w - V d) / c, q = ||w - V d||^2   (update, one read of V and w, one write)
+//   check   re-orthogonalise if the projection cancelled most of w or Pythagoras is
+//           inaccurate: then pass 1/2 run again on v_{j+1} and it is renormalised
+//           (the gated kernels return at once when the check passed)
+//   givens  column j of H = d (+ c e), h_{j+1,j} = c (or c rho); rotations; |g_{j+1}|/ref
+// This is classical Gram-Schmidt with selective re-orthogonalisation: two passes
+// over the basis per iteration in the common case instead of four.
+//
+// Reductions are deterministic: an occupancy-sized grid writes per-block partial
+// sums (warp shuffles, then shared memory) and a second kernel adds them in a
+// fixed order.  The multi-dot is instantiated per vector count (1..16) so that
+// every FMA it issues is useful; more vectors take several chunked launches.
 #include "common.cuh"
 
 namespace pcopt {
@@ -15,6 +23,7 @@ namespace {
 
 constexpr int kChunk = 16;
 constexpr int kThreads = 256;
+constexpr int kMaxChunks = 64;   // up to 1024 basis vectors
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -22,43 +31,64 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ldv, int i0, int cnt,
+__device__ __forceinline__ bool gated_off(const double* gate) { return gate && gate[0] == 0.0; }
+
+// partial[b*ld + i0 + c] = sum over block b of V_{i0+c} . w   (c < CNT)
+// partial[b*ld + nv]     = sum over block b of w . w          (WITH_NORM)
+template <int CNT, bool WITH_NORM>
+__global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ldv, int i0,
                                                             const double* __restrict__ w, size_t len,
-                                                            double* __restrict__ partial, int nv) {
-  double acc[kChunk];
+                                                            double* __restrict__ partial, int nv, int ld,
+                                                            const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
+  double acc[CNT];
+  double ww = 0.0;
 #pragma unroll
-  for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
+  for (int c = 0; c < CNT; ++c) acc[c] = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const double* Vb = V + (size_t)i0 * ldv;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
     const double we = w[e];
+    if (WITH_NORM) ww = fma(we, we, ww);
 #pragma unroll
-    for (int c = 0; c < kChunk; ++c)
-      if (c < cnt) acc[c] = fma(Vb[(size_t)c * ldv + e], we, acc[c]);
+    for (int c = 0; c < CNT; ++c) acc[c] = fma(__ldg(Vb + (size_t)c * ldv + e), we, acc[c]);
   }
-  __shared__ double red[kThreads / 32][kChunk];
+  __shared__ double red[kThreads / 32][CNT + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < kChunk; ++c) {
-    if (c < cnt) {
-      const double v = warp_sum(acc[c]);
-      if (lane == 0) red[wid][c] = v;
-    }
+  for (int c = 0; c < CNT; ++c) {
+    const double v = warp_sum(acc[c]);
+    if (lane == 0) red[wid][c] = v;
+  }
+  if (WITH_NORM) {
+    const double v = warp_sum(ww);
+    if (lane == 0) red[wid][CNT] = v;
   }
   __syncthreads();
-  if (threadIdx.x < cnt) {
+  if (threadIdx.x < CNT + (WITH_NORM ? 1 : 0)) {
     double s = 0.0;
     for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
-    partial[(size_t)blockIdx.x * nv + i0 + threadIdx.x] = s;
+    const int col = threadIdx.x < CNT ? i0 + threadIdx.x : nv;
+    partial[(size_t)blockIdx.x * ld + col] = s;
   }
 }
 
-// out[i] = sum_b partial[b*nv + i], one block per i, fixed order
-__global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, int nblocks,
-                                                                   int nv, double* __restrict__ out) {
+// number of blocks that wrote the partial sums of each chunk of kChunk columns
+struct ChunkGrids {
+  unsigned nb[kMaxChunks];
+};
+
+// out[i] = sum_b partial[b*ld + i] for i < nout (column nout goes to *extra), in a
+// fixed order; one block per column
+__global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, ChunkGrids cg,
+                                                                   int ld, double* __restrict__ out,
+                                                                   double* __restrict__ extra, int nout,
+                                                                   const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int i = blockIdx.x;
+  const int nblocks = (int)cg.nb[i < nout ? i / kChunk : 0];
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * nv + i];
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * ld + i];
   __shared__ double red[kThreads / 32];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -66,23 +96,31 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double*
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < kThreads / 32; ++q) t += red[q];
-    out[i] = t;
+    if (i < nout)
+      out[i] = t;
+    else
+      extra[0] = t;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) update_norm_kernel(const double* __restrict__ V, size_t ldv, int nv,
-                                                               const double* __restrict__ h, double* __restrict__ w,
-                                                               size_t len, double* __restrict__ partial) {
+// v = (v - sum_i coef_i V_i) * scale ;  partial[b] = sum over block b of (v - sum)^2 (before scaling)
+__global__ void __launch_bounds__(kThreads) update_kernel(const double* __restrict__ V, size_t ldv, int nv,
+                                                          const double* __restrict__ coef, double* __restrict__ v,
+                                                          size_t len, const double* __restrict__ scale,
+                                                          double* __restrict__ partial,
+                                                          const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
   extern __shared__ double hs[];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = coef[i];
   __syncthreads();
+  const double sc = scale ? scale[0] : 1.0;
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    double we = w[e];
-    for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[(size_t)i * ldv + e], we);
-    w[e] = we;
+    double we = v[e];
+    for (int i = 0; i < nv; ++i) we = fma(-hs[i], __ldg(V + (size_t)i * ldv + e), we);
     acc = fma(we, we, acc);
+    v[e] = we * sc;
   }
   __shared__ double red[kThreads / 32];
   acc = warp_sum(acc);
@@ -111,11 +149,13 @@ __global__ void __launch_bounds__(kThreads) norm2_kernel(const double* __restric
   }
 }
 
-__global__ void scale_kernel(const double* __restrict__ w, double* __restrict__ v, size_t len,
-                             const double* __restrict__ nrm2) {
+// v *= 1/sqrt(nrm2[0])  (gated)
+__global__ void scale_kernel(double* __restrict__ v, size_t len, const double* __restrict__ nrm2,
+                             const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const double q = 1.0 / sqrt(nrm2[0]);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) v[e] = w[e] * q;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) v[e] *= q;
 }
 
 template <typename Tx>
@@ -125,32 +165,63 @@ __global__ void axpby_kernel(double a, const Tx* __restrict__ x, double b, doubl
     y[e] = (b == 0.0) ? a * (double)x[e] : fma(a, (double)x[e], b * y[e]);
 }
 
-// Column j of the Hessenberg matrix: H[0..j][j] = h1 (+ h2), H[j+1][j] = sqrt(nrm2);
-// apply rotations 0..j-1, build rotation j, update g, est = |g[j+1]| / ref.
-__global__ void givens_kernel(int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
-                              const double* h2, const double* nrm2, double* est, const double* ref) {
+// c = sqrt(||w||^2 - ||d||^2) when that is safely positive, else 1 (and force re-orthogonalisation)
+__global__ void arnoldi_prep_kernel(int nv, const double* d, ArnoldiScalars s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double dd = 0.0;
+  for (int i = 0; i < nv; ++i) dd = fma(d[i], d[i], dd);
+  const double ww = s.ww[0];
+  const double r = ww - dd;
+  if (r > 1e-12 * ww && r > 0.0) {
+    s.c[0] = sqrt(r);
+    s.inv[0] = 1.0 / s.c[0];
+    s.flag[0] = 0.0;
+  } else {
+    s.c[0] = 1.0;
+    s.inv[0] = 1.0;
+    s.flag[0] = 1.0;
+  }
+}
+
+// re-orthogonalise when ||w - V d||^2 < 1e-3 ||w||^2 (more than 99.95% cancelled) or the
+// Pythagorean norm disagrees with the computed one by more than 1e-6 (relative, squared)
+__global__ void arnoldi_check_kernel(ArnoldiScalars s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (s.flag[0] != 0.0) return;
+  const double q = s.q[0], ww = s.ww[0], c2 = s.c[0] * s.c[0];
+  const bool bad = !(q >= 1e-3 * ww) || !(fabs(q - c2) <= 1e-6 * q);
+  s.flag[0] = bad ? 1.0 : 0.0;
+}
+
+// Column j of H and its Givens rotation; est = |g_{j+1}| / ref.
+//   no re-orthogonalisation:  w = V d + c v_{j+1}
+//   re-orthogonalisation:     w = V (d + c e) + c rho v_{j+1},  rho^2 = s.rho2
+__global__ void givens_kernel(int j, int ldh, double* H, double* cs, double* sn, double* g, const double* d,
+                              const double* e, ArnoldiScalars s, double* est, const double* ref) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + (size_t)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
-  col[j + 1] = sqrt(nrm2[0]);
+  const bool re = s.flag[0] != 0.0;
+  const double c = s.c[0];
+  for (int i = 0; i <= j; ++i) col[i] = re ? fma(c, e[i], d[i]) : d[i];
+  col[j + 1] = re ? c * sqrt(s.rho2[0]) : c;
   for (int i = 0; i < j; ++i) {
     const double t = cs[i] * col[i] + sn[i] * col[i + 1];
     col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
     col[i] = t;
   }
   const double a = col[j], b = col[j + 1];
-  double c = 1.0, s = 0.0, r = a;
+  double cr = 1.0, sr = 0.0, r = a;
   if (b != 0.0) {
     r = hypot(a, b);
-    c = a / r;
-    s = b / r;
+    cr = a / r;
+    sr = b / r;
   }
-  cs[j] = c;
-  sn[j] = s;
+  cs[j] = cr;
+  sn[j] = sr;
   col[j] = r;
   col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
+  g[j + 1] = -sr * g[j];
+  g[j] = cr * g[j];
   est[0] = fabs(g[j + 1]) / ref[0];
 }
 
@@ -186,54 +257,111 @@ __global__ void arnoldi_start_kernel(double* g, const double* nrm2, double* est,
   est[0] = beta / ref[0];
 }
 
+// blocks that fit the device at once for kernel `fn` (one wave), capped by the work size
+template <typename K>
+unsigned wave_blocks(K fn, size_t smem, size_t len) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  if (per_sm > kMaxBlocksPerSM) per_sm = kMaxBlocksPerSM;
+  size_t b = (size_t)num_sms() * per_sm;
+  const size_t need = (len + kThreads - 1) / kThreads;
+  if (need < b) b = need ? need : 1;
+  return (unsigned)b;
+}
+
 unsigned stream_blocks(size_t len) {
   size_t b = (len + kThreads - 1) / kThreads;
   const size_t cap = (size_t)num_sms() * 8;
   return (unsigned)(b < cap ? (b ? b : 1) : cap);
 }
 
+ChunkGrids one_grid(unsigned nb) {
+  ChunkGrids g;
+  for (int c = 0; c < kMaxChunks; ++c) g.nb[c] = nb;
+  return g;
+}
+
+template <int CNT, bool N>
+cudaError_t multidot_chunk(Launch& L, const double* V, size_t ldv, int i0, const double* w, size_t len,
+                           double* partial, int nv, int ld, const double* gate, unsigned* blocks_out) {
+  const unsigned nb = wave_blocks(multidot_kernel<CNT, N>, 0, len);
+  *blocks_out = nb;
+  const int kc = gate ? KC_REORTH : KC_DOT;
+  L.begin(kc);
+  multidot_kernel<CNT, N><<<nb, kThreads, 0, L.stream>>>(V, ldv, i0, w, len, partial, nv, ld, gate);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * len * (CNT + 1), 2.0 * len * (CNT + (N ? 1 : 0)));
+}
+
+template <bool N>
+cudaError_t multidot_dispatch(int cnt, Launch& L, const double* V, size_t ldv, int i0, const double* w, size_t len,
+                              double* partial, int nv, int ld, const double* gate, unsigned* nb) {
+  switch (cnt) {
+#define PCOPT_CASE(k) \
+  case k: return multidot_chunk<k, N>(L, V, ldv, i0, w, len, partial, nv, ld, gate, nb);
+    PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
+    PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
+    PCOPT_CASE(15) PCOPT_CASE(16)
+#undef PCOPT_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, const double* w, size_t len,
-                            double* partial, int nblocks, double* out) {
-  for (int i0 = 0; i0 < nv; i0 += kChunk) {
+                            double* partial, double* out, double* ww, const double* gate) {
+  if (nv < 1 || nv > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+  const int ld = nv + 1;
+  ChunkGrids cg = one_grid(1);
+  double nb_sum = 0;
+  for (int i0 = 0, c = 0; i0 < nv; i0 += kChunk, ++c) {
     const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
-    L.begin(KC_DOT);
-    multidot_kernel<<<nblocks, kThreads, 0, L.stream>>>(V, ldv, i0, cnt, w, len, partial, nv);
-    cudaError_t e = L.end(KC_DOT, 8.0 * len * (cnt + 1), 2.0 * len * cnt);
+    unsigned nb = 0;
+    cudaError_t e = (i0 == 0 && ww) ? multidot_dispatch<true>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb)
+                                    : multidot_dispatch<false>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb);
     if (e != cudaSuccess) return e;
+    cg.nb[c] = nb;
+    nb_sum += nb * (double)cnt;
   }
-  L.begin(KC_REDUCE);
-  reduce_partials_kernel<<<nv, kThreads, 0, L.stream>>>(partial, nblocks, nv, out);
-  return L.end(KC_REDUCE, 8.0 * nblocks * nv, 1.0 * nblocks * nv);
+  const int ncols = nv + (ww ? 1 : 0);
+  const int kc = gate ? KC_REORTH : KC_REDUCE;
+  L.begin(kc);
+  reduce_partials_kernel<<<ncols, kThreads, 0, L.stream>>>(partial, cg, ld, out, ww, nv, gate);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * nb_sum, nb_sum);
 }
 
-cudaError_t launch_update_norm(Launch& L, const double* V, size_t ldv, int nv, const double* h, double* w, size_t len,
-                               double* partial, int nblocks, double* nrm2) {
-  L.begin(KC_UPDATE);
-  update_norm_kernel<<<nblocks, kThreads, sizeof(double) * (nv > 0 ? nv : 1), L.stream>>>(V, ldv, nv, h, w, len,
-                                                                                         partial);
-  cudaError_t e = L.end(KC_UPDATE, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
+cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
+                          const double* scale, double* partial, double* q, const double* gate) {
+  const size_t smem = sizeof(double) * (nv > 0 ? nv : 1);
+  const unsigned nb = wave_blocks(update_kernel, smem, len);
+  const int kc = gate ? KC_REORTH : KC_UPDATE;
+  L.begin(kc);
+  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate);
+  cudaError_t e = gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
   if (e != cudaSuccess) return e;
-  L.begin(KC_REDUCE);
-  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, nblocks, 1, nrm2);
-  return L.end(KC_REDUCE, 8.0 * nblocks, 1.0 * nblocks);
+  const int kr = gate ? KC_REORTH : KC_REDUCE;
+  L.begin(kr);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate);
+  return gate ? L.end(kr, 0.0, 0.0) : L.end(kr, 8.0 * nb, 1.0 * nb);
 }
 
-cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, int nblocks, double* nrm2) {
+cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, double* nrm2) {
+  const unsigned nb = wave_blocks(norm2_kernel, 0, len);
   L.begin(KC_DOT);
-  norm2_kernel<<<nblocks, kThreads, 0, L.stream>>>(w, len, partial);
+  norm2_kernel<<<nb, kThreads, 0, L.stream>>>(w, len, partial);
   cudaError_t e = L.end(KC_DOT, 8.0 * len, 2.0 * len);
   if (e != cudaSuccess) return e;
   L.begin(KC_REDUCE);
-  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, nblocks, 1, nrm2);
-  return L.end(KC_REDUCE, 8.0 * nblocks, 1.0 * nblocks);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, nrm2, nrm2, 1, nullptr);
+  return L.end(KC_REDUCE, 8.0 * nb, 1.0 * nb);
 }
 
-cudaError_t launch_scale_by_inv_norm(Launch& L, const double* w, double* v, size_t len, const double* nrm2) {
-  L.begin(KC_SCALE);
-  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(w, v, len, nrm2);
-  return L.end(KC_SCALE, 16.0 * len, 1.0 * len);
+cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate) {
+  const int kc = gate ? KC_REORTH : KC_SCALE;
+  L.begin(kc);
+  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, len, nrm2, gate);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len, 1.0 * len);
 }
 
 template <typename Tx>
@@ -245,11 +373,22 @@ cudaError_t launch_axpby(Launch& L, double a, const Tx* x, double b, double* y, 
 template cudaError_t launch_axpby<double>(Launch&, double, const double*, double, double*, size_t);
 template cudaError_t launch_axpby<float>(Launch&, double, const float*, double, double*, size_t);
 
-cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec,
-                          const double* hcol, const double* nrm2, double* est, const double* ref) {
-  // hcol holds two consecutive arrays of ldh entries: first and second Gram-Schmidt pass
+cudaError_t launch_arnoldi_prep(Launch& L, int nv, const double* d, ArnoldiScalars s) {
   L.begin(KC_GIVENS);
-  givens_kernel<<<1, 32, 0, L.stream>>>(j, ldh, H, cs, sn, gvec, hcol, hcol + ldh, nrm2, est, ref);
+  arnoldi_prep_kernel<<<1, 32, 0, L.stream>>>(nv, d, s);
+  return L.end(KC_GIVENS, 0.0, 2.0 * nv);
+}
+
+cudaError_t launch_arnoldi_check(Launch& L, ArnoldiScalars s) {
+  L.begin(KC_GIVENS);
+  arnoldi_check_kernel<<<1, 32, 0, L.stream>>>(s);
+  return L.end(KC_GIVENS, 0.0, 4.0);
+}
+
+cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec, const double* d,
+                          const double* e, ArnoldiScalars s, double* est, const double* ref) {
+  L.begin(KC_GIVENS);
+  givens_kernel<<<1, 32, 0, L.stream>>>(j, ldh, H, cs, sn, gvec, d, e, s, est, ref);
   return L.end(KC_GIVENS, 0.0, 10.0 * (j + 1));
 }
 
@@ -261,9 +400,9 @@ cudaError_t launch_backsolve(Launch& L, int k, int ldh, const double* H, const d
 
 template <typename Tz>
 cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const double* y, double* x, size_t len) {
+  const size_t smem = sizeof(double) * (k > 0 ? k : 1);
   L.begin(KC_XUPDATE);
-  xupdate_kernel<Tz><<<stream_blocks(len), kThreads, sizeof(double) * (k > 0 ? k : 1), L.stream>>>(Z, ldz, k, y, x,
-                                                                                                  len);
+  xupdate_kernel<Tz><<<wave_blocks(xupdate_kernel<Tz>, smem, len), kThreads, smem, L.stream>>>(Z, ldz, k, y, x, len);
   return L.end(KC_XUPDATE, (double)len * (k * sizeof(Tz) + 16.0), 2.0 * len * k);
 }
 template cudaError_t launch_xupdate<double>(Launch&, const double*, size_t, int, const double*, double*, size_t);

@@ -79,9 +79,9 @@ __global__ void fst_divide_kernel(typename Cx<Tc>::t* __restrict__ buf, const Tc
 // One red-black Gauss-Seidel sweep from u = 0, fused: a red point takes
 // r/d; a black point takes (r + sum_k w_k u_red(nb_k))/d, where the red
 // neighbour values are recomputed from r on the fly.
-template <typename Tc, int DIM>
+template <typename Tc, typename TU, int DIM>
 __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t* __restrict__ r,
-                                                        typename Cx<Tc>::t* __restrict__ u,
+                                                        TU* __restrict__ u,
                                                         const Tc* __restrict__ w, const Tc* __restrict__ diag,
                                                         const typename Cx<Tc>::t* __restrict__ sigma, int m,
                                                         int64_t np, int planes) {
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
   if (red) {
     for (int p = p0; p < p1; ++p) {
       const int64_t o = (int64_t)p * np + s;
-      u[o] = cmul(r[o], inv_diag<Tc>(sigma[p], dg));
+      stc(u, o, cmul(r[o], inv_diag<Tc>(sigma[p], dg)));
     }
     return;
   }
@@ -135,14 +135,14 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
         acc.y = fma(wv[k], ured.y, acc.y);
       }
     }
-    u[o] = cmul(acc, inv_diag<Tc>(sig, dg));
+    stc(u, o, cmul(acc, inv_diag<Tc>(sig, dg)));
   }
 }
 
 // res = r - (sigma u + tau K u)
-template <typename Tc, int DIM>
+template <typename Tc, typename TU, int DIM>
 __global__ void __launch_bounds__(256) mg_residual_kernel(const typename Cx<Tc>::t* __restrict__ r,
-                                                          const typename Cx<Tc>::t* __restrict__ u,
+                                                          const TU* __restrict__ u,
                                                           typename Cx<Tc>::t* __restrict__ res,
                                                           const Tc* __restrict__ w, const Tc* __restrict__ diag,
                                                           const typename Cx<Tc>::t* __restrict__ sigma, int m,
@@ -177,13 +177,13 @@ __global__ void __launch_bounds__(256) mg_residual_kernel(const typename Cx<Tc>:
   for (int p = p0; p < p1; ++p) {
     const int64_t o = (int64_t)p * np + s;
     const C sig = sigma[p];
-    const C uc = u[o];
+    const C uc = ldc(u, o);
     // L u = (sigma + dg) u - sum_k w_k u_nb
     C lu = cmul(cmk<Tc>(sig.x + dg, sig.y), uc);
 #pragma unroll
     for (int k = 0; k < 2 * DIM; ++k) {
       if (ex[k]) {
-        const C un = u[o + off[k]];
+        const C un = ldc(u, o + off[k]);
         lu.x = fma(-wv[k], un.x, lu.x);
         lu.y = fma(-wv[k], un.y, lu.y);
       }
@@ -227,9 +227,8 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(const typename Cx<Tc>:
 }
 
 // u_f += P e_c, P = tensor product of 1D linear interpolation
-template <typename Tc, int DIM>
-__global__ void __launch_bounds__(256) mg_prolong_kernel(const typename Cx<Tc>::t* __restrict__ ec,
-                                                         typename Cx<Tc>::t* __restrict__ uf, int mf, int mc,
+template <typename Tc, typename TU, int DIM>
+__global__ void __launch_bounds__(256) mg_prolong_kernel(const TU* __restrict__ ec, TU* __restrict__ uf, int mf, int mc,
                                                          int64_t npf, int64_t npc, int planes) {
   typedef typename Cx<Tc>::t C;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,29 +268,28 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(const typename Cx<Tc>::
     cw[2][0] = Tc(1);
   }
   for (int p = p0; p < p1; ++p) {
-    const C* ep = ec + (int64_t)p * npc;
+    const TU* ep = ec + (int64_t)p * npc;
     C acc = czero<Tc>();
     for (int a3 = 0; a3 < cnt[2]; ++a3)
       for (int a2 = 0; a2 < cnt[1]; ++a2)
         for (int a1 = 0; a1 < cnt[0]; ++a1) {
           const Tc wgt = cw[0][a1] * cw[1][a2] * cw[2][a3];
           const int64_t q = ((int64_t)ci[2][a3] * mc + ci[1][a2]) * mc + ci[0][a1];
-          const C v = ep[q];
+          const C v = ldc(ep, q);
           acc.x = fma(wgt, v.x, acc.x);
           acc.y = fma(wgt, v.y, acc.y);
         }
     const int64_t o = (int64_t)p * npf + s;
-    uf[o] = uf[o] + acc;
+    stc(uf, o, ldc(uf, o) + acc);
   }
 }
 
-template <typename Tc>
+template <typename Tc, typename TU>
 __global__ void mg_coarsest_kernel(const Tc* __restrict__ diag, const typename Cx<Tc>::t* __restrict__ sigma,
-                                   const typename Cx<Tc>::t* __restrict__ r, typename Cx<Tc>::t* __restrict__ u,
-                                   int planes) {
+                                   const typename Cx<Tc>::t* __restrict__ r, TU* __restrict__ u, int planes) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= planes) return;
-  u[p] = cmul(r[p], inv_diag<Tc>(sigma[p], diag[0]));
+  stc(u, p, cmul(r[p], inv_diag<Tc>(sigma[p], diag[0])));
 }
 
 dim3 plane_grid(int64_t np, int planes) {
@@ -320,36 +318,35 @@ cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* la
   return L.end(KC_FST_DIVIDE, 2.0 * tot * cs, 12.0 * tot);
 }
 
-template <typename Tc>
+template <typename Tc, typename TU>
 cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
-                             const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, typename Cx<Tc>::t* u) {
-  const double cs = sizeof(typename Cx<Tc>::t);
+                             const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u) {
+  const double cs = 0.5 * (sizeof(typename Cx<Tc>::t) + sizeof(TU));
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_SMOOTH);
   if (g.dim == 2)
-    mg_smooth_kernel<Tc, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
+    mg_smooth_kernel<Tc, TU, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
                                                                             planes);
   else
-    mg_smooth_kernel<Tc, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
+    mg_smooth_kernel<Tc, TU, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
                                                                             planes);
   return L.end(KC_MG_SMOOTH, 2.0 * tot * cs, tot * (12.0 + 10.0 * g.dim));
 }
 
-template <typename Tc>
+template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
-                                     const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
-                                     const typename Cx<Tc>::t* u, typename Cx<Tc>::t* res,
-                                     typename Cx<Tc>::t* rc) {
+                                     const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
+                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc) {
   const double cs = sizeof(typename Cx<Tc>::t);
   const int mc = (g.m - 1) / 2;
   const int64_t npc = g.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_RESID_RESTRICT);
   if (g.dim == 2)
-    mg_residual_kernel<Tc, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
+    mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
                                                                               g.np, planes);
   else
-    mg_residual_kernel<Tc, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
+    mg_residual_kernel<Tc, TU, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
                                                                               g.np, planes);
   cudaError_t e = L.end(KC_MG_RESID_RESTRICT, 3.0 * tot * cs, tot * (8.0 + 4.0 * g.dim));
   if (e != cudaSuccess) return e;
@@ -361,44 +358,48 @@ cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const
   return L.end(KC_MG_RESID_RESTRICT, tot * cs + (double)npc * planes * cs, (double)npc * planes * (g.dim == 2 ? 36 : 108));
 }
 
-template <typename Tc>
-cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const typename Cx<Tc>::t* ec,
-                              typename Cx<Tc>::t* uf) {
-  const double cs = sizeof(typename Cx<Tc>::t);
+template <typename Tc, typename TU>
+cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* ec, TU* uf) {
+  const double cs = sizeof(TU);
   const int mc = (gf.m - 1) / 2;
   const int64_t npc = gf.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
   const double tot = (double)gf.np * planes;
   L.begin(KC_MG_PROLONG);
   if (gf.dim == 2)
-    mg_prolong_kernel<Tc, 2><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
+    mg_prolong_kernel<Tc, TU, 2><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
   else
-    mg_prolong_kernel<Tc, 3><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
+    mg_prolong_kernel<Tc, TU, 3><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
   return L.end(KC_MG_PROLONG, 2.0 * tot * cs + (double)npc * planes * cs, tot * 8.0);
 }
 
-template <typename Tc>
+template <typename Tc, typename TU>
 cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const typename Cx<Tc>::t* sigma,
-                               const typename Cx<Tc>::t* r, typename Cx<Tc>::t* u) {
+                               const typename Cx<Tc>::t* r, TU* u) {
   const double cs = sizeof(typename Cx<Tc>::t);
   L.begin(KC_MG_COARSEST);
-  mg_coarsest_kernel<Tc><<<(planes + 255) / 256, 256, 0, L.stream>>>(diag, sigma, r, u, planes);
+  mg_coarsest_kernel<Tc, TU><<<(planes + 255) / 256, 256, 0, L.stream>>>(diag, sigma, r, u, planes);
   return L.end(KC_MG_COARSEST, 2.0 * planes * cs, 12.0 * planes);
 }
 
-#define PCOPT_INST(Tc)                                                                                              \
+#define PCOPT_INST_FST(Tc)                                                                                   \
   template cudaError_t launch_fst_axis<Tc>(Launch&, const Grid&, int, int, const Tc*, const Cx<Tc>::t*,          \
                                            Cx<Tc>::t*);                                                             \
-  template cudaError_t launch_fst_divide<Tc>(Launch&, const Grid&, int, const Tc*, const Cx<Tc>::t*, Cx<Tc>::t*); \
-  template cudaError_t launch_mg_smooth<Tc>(Launch&, const Grid&, int, const Stencil<Tc>&, const Cx<Tc>::t*,     \
-                                            const Cx<Tc>::t*, Cx<Tc>::t*);                                          \
-  template cudaError_t launch_mg_resid_restrict<Tc>(Launch&, const Grid&, int, const Stencil<Tc>&,               \
-                                                    const Cx<Tc>::t*, const Cx<Tc>::t*, const Cx<Tc>::t*,          \
-                                                    Cx<Tc>::t*, Cx<Tc>::t*);                                        \
-  template cudaError_t launch_mg_prolong<Tc>(Launch&, const Grid&, int, const Cx<Tc>::t*, Cx<Tc>::t*);           \
-  template cudaError_t launch_mg_coarsest<Tc>(Launch&, int, const Tc*, const Cx<Tc>::t*, const Cx<Tc>::t*,       \
-                                              Cx<Tc>::t*);
-PCOPT_INST(float)
-PCOPT_INST(double)
-#undef PCOPT_INST
+  template cudaError_t launch_fst_divide<Tc>(Launch&, const Grid&, int, const Tc*, const Cx<Tc>::t*, Cx<Tc>::t*);
+#define PCOPT_INST_MG(Tc, TU)                                                                                    \
+  template cudaError_t launch_mg_smooth<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&, const Cx<Tc>::t*, \
+                                                const Cx<Tc>::t*, TU*);                                             \
+  template cudaError_t launch_mg_resid_restrict<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&,           \
+                                                        const Cx<Tc>::t*, const Cx<Tc>::t*, const TU*, Cx<Tc>::t*, \
+                                                        Cx<Tc>::t*);                                                \
+  template cudaError_t launch_mg_prolong<Tc, TU>(Launch&, const Grid&, int, const TU*, TU*);                     \
+  template cudaError_t launch_mg_coarsest<Tc, TU>(Launch&, int, const Tc*, const Cx<Tc>::t*, const Cx<Tc>::t*,   \
+                                                  TU*);
+PCOPT_INST_FST(float)
+PCOPT_INST_FST(double)
+PCOPT_INST_MG(float, float2)
+PCOPT_INST_MG(double, double2)
+PCOPT_INST_MG(float, __nv_bfloat162)
+#undef PCOPT_INST_FST
+#undef PCOPT_INST_MG
 
 }  // namespace pcopt

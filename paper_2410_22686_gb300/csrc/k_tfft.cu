@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(256) tfft_forward_kernel(const double* __restr
   }
 }
 
-template <typename Tc, typename Tout>
-__global__ void __launch_bounds__(256) tfft_inverse_kernel(const typename Cx<Tc>::t* __restrict__ spec,
+template <typename Tc, typename TU, typename Tout>
+__global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict__ spec,
                                                            const Tc* __restrict__ dpow,
                                                            const typename Cx<Tc>::t* __restrict__ tw,
                                                            Tout* __restrict__ w, int64_t ms, int n, int logn,
@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const typename Cx<Tc>
     const int64_t s = s0 + c;
     C sa = czero<Tc>(), sb = czero<Tc>();
     if (s < ms) {
-      sa = spec[(int64_t)(2 * k) * ms + s];      // hat w2[k]
-      sb = spec[(int64_t)(2 * k + 1) * ms + s];  // hat w1[n-k] = conj(hat w1[k])
+      sa = ldc(spec, (int64_t)(2 * k) * ms + s);      // hat w2[k]
+      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);  // hat w1[n-k] = conj(hat w1[k])
     }
     // Y[k] = hat w1[k] + i hat w2[k] with hat w1[k] = conj(sb), hat w2[k] = sa
     z[bitrev(k, logn) * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
@@ -167,20 +167,20 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
   return L.end(KC_TFFT_FWD, bytes, flops);
 }
 
-template <typename Tc, typename Tout>
-cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const typename Cx<Tc>::t* spec, const Tc* dpow,
+template <typename Tc, typename TU, typename Tout>
+cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow,
                                 const typename Cx<Tc>::t* tw, Tout* w) {
   const int TS = pick_ts<Tc>(n);
   const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
   cudaError_t e =
-      cudaFuncSetAttribute(tfft_inverse_kernel<Tc, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(tfft_inverse_kernel<Tc, TU, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ms + TS - 1) / TS);
   const int nf = n / 2 + 1;
-  const double bytes = 2.0 * nf * ms * sizeof(typename Cx<Tc>::t) + 2.0 * n * ms * sizeof(Tout);
+  const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout);
   const double flops = (double)ms * (5.0 * n * ilog2(n) + 4.0 * n);
   L.begin(KC_TFFT_INV);
-  tfft_inverse_kernel<Tc, Tout><<<blocks, 256, smem, L.stream>>>(spec, dpow, tw, w, ms, n, ilog2(n), TS);
+  tfft_inverse_kernel<Tc, TU, Tout><<<blocks, 256, smem, L.stream>>>(spec, dpow, tw, w, ms, n, ilog2(n), TS);
   return L.end(KC_TFFT_INV, bytes, flops);
 }
 
@@ -188,11 +188,16 @@ template cudaError_t launch_tfft_forward<double>(Launch&, int64_t, int, const do
                                                  double2*);
 template cudaError_t launch_tfft_forward<float>(Launch&, int64_t, int, const double*, const float*, const float2*,
                                                 float2*);
-template cudaError_t launch_tfft_inverse<double, double>(Launch&, int64_t, int, const double2*, const double*,
-                                                         const double2*, double*);
-template cudaError_t launch_tfft_inverse<float, double>(Launch&, int64_t, int, const float2*, const float*,
-                                                        const float2*, double*);
-template cudaError_t launch_tfft_inverse<float, float>(Launch&, int64_t, int, const float2*, const float*,
-                                                       const float2*, float*);
+template cudaError_t launch_tfft_inverse<double, double2, double>(Launch&, int64_t, int, const double2*,
+                                                                  const double*, const double2*, double*);
+template cudaError_t launch_tfft_inverse<float, float2, double>(Launch&, int64_t, int, const float2*, const float*,
+                                                                const float2*, double*);
+template cudaError_t launch_tfft_inverse<float, float2, float>(Launch&, int64_t, int, const float2*, const float*,
+                                                               const float2*, float*);
+template cudaError_t launch_tfft_inverse<float, __nv_bfloat162, double>(Launch&, int64_t, int,
+                                                                        const __nv_bfloat162*, const float*,
+                                                                        const float2*, double*);
+template cudaError_t launch_tfft_inverse<float, __nv_bfloat162, float>(Launch&, int64_t, int, const __nv_bfloat162*,
+                                                                       const float*, const float2*, float*);
 
 }  // namespace pcopt

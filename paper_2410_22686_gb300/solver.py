@@ -75,6 +75,16 @@ class Solver:
     def __exit__(self, *exc):
         self.close()
 
+    def set_coefficient(self, a_nodes: np.ndarray | None):
+        """Replace a(x) (host array of (m1+2)^dim nodal values) without reallocating."""
+        ptr = None
+        if a_nodes is not None:
+            self._a = np.ascontiguousarray(a_nodes, dtype=np.float64)
+            if self._a.size != (self.m1 + 2) ** self.dim:
+                raise ValueError("a_nodes must have (m1+2)^dim entries")
+            ptr = self._a.ctypes.data_as(ctypes.c_void_p)
+        capi.check(self.lib.pc_set_coefficient(self.h, ptr, _stream()))
+
     # ---------------------------------------------------------------- helpers
     def empty_vector(self):
         return torch.empty((2, self.n) + (self.m1,) * self.dim, dtype=torch.float64, device="cuda")

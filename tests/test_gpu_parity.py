@@ -266,3 +266,31 @@ def test_invalid_arguments_return_errors_and_context_survives():
     x, it, rel = sol.solve(_dev(np.ones((2, 8, 7, 7))), rtol=1e-10)
     assert rel <= 1e-10
     sol.close()
+
+
+@pytest.mark.parametrize("d,m1,n", [(2, 63, 8), (3, 7, 8), (2, 255, 16)])
+def test_bf16_storage_precond_apply_close_to_oracle(d, m1, n):
+    # multigrid iterates stored as BF16 (8-bit significand, relative rounding 2^-9 per
+    # stored value), FP32 arithmetic: each of the <= 8 levels stores u after smoothing
+    # and after the coarse correction, so the output carries < 16 * 2^-9 ~ 3e-2 relative error
+    a = _coef(d, m1, "var", seed=5 * m1 + n)
+    gamma, eps = 1e-4, 0.25
+    sol = _solver(d, m1, n, a, "mg", precision="bf16s", gamma=gamma, eps=eps)
+    v = S.random_vector((2, n) + (m1,) * d, 12)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, opc.MGSpatialSolver(a, tau))
+    assert _rel(w, ref) <= 3e-2
+    assert np.linalg.norm(w - ref) <= 1e-2 * np.linalg.norm(ref)
+    sol.close()
+
+
+def test_bf16_storage_fgmres_matches_fp64_oracle():
+    prob, spatial = S.variable_2d_problem(gamma=1e-6, m1=63, n=64), "mg"
+    b, A, Pi, ref = _oracle_solution(prob, spatial)
+    sol = _solver(2, 63, 64, prob.a_nodes, spatial, precision="bf16s", gamma=prob.gamma, eps=prob.eps,
+                  max_iter=80)
+    x, iters, rel = sol.solve(_dev(b), rtol=1e-11)
+    assert rel <= 1e-11
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    sol.close()
