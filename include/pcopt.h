@@ -143,6 +143,33 @@ int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y
 int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit,
                    int mode, int* iters, double* relres, void* stream);
 
+/* The same right-preconditioned (flexible) GMRES solve from a zero initial
+ * guess, run as ONE CUDA-graph launch: the iteration is the body of a graph
+ * WHILE node whose condition a kernel sets on the device from the residual
+ * estimate, so no host round trip happens per iteration.  The graph is built
+ * on the first call and reused while (b, x, rtol, maxit) are unchanged.
+ *   x: device, overwritten (the initial guess is zero).  iters/relres as in
+ *   pc_gmres_solve (relres is the true relative residual).  Synchronises `stream`.
+ * Errors: as pc_gmres_solve; PC_ERR_UNSUPPORTED for n > 1024 (FP32
+ * preconditioner) or n > 256 (FP64 preconditioner). */
+int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, int maxit, int* iters,
+                         double* relres, void* stream);
+
+/* Batched solve of independent problems of uneven size (each with its own
+ * handle: grid, n, gamma and a may all differ): pc_batch_create captures one
+ * graph in which every problem is a parallel branch running its own device-
+ * controlled FGMRES loop (as pc_gmres_solve_graph); pc_batch_solve runs the
+ * whole batch with ONE graph launch and fills iters[count], relres[count]
+ * (HOST arrays, may be NULL).  hs: distinct handles; b[i], x[i]: device
+ * vectors of handle i (x overwritten, zero initial guess).  The batch keeps
+ * pointers to everything it was created with; destroy it before those.
+ * pc_batch_solve returns the worst status over the problems. */
+typedef struct pc_batch pc_batch;
+int pc_batch_create(pc_handle* const* hs, int count, const double* const* b, double* const* x, double rtol,
+                    int maxit, pc_batch** out);
+int pc_batch_solve(pc_batch* batch, int* iters, double* relres, void* stream);
+int pc_batch_destroy(pc_batch* batch);
+
 /* Solve the adjoint system A^T lam = c with the same preconditioner, using
  * A^T = S A S, S = diag(I, -I) (from the block form of Eq. matrix_A with K
  * symmetric): lam = S A^{-1} S c.  Arguments as pc_gmres_solve; lam in/out
@@ -191,7 +218,9 @@ int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
  * every kernel the handle launches (per kernel class); pc_profile(h, 0) stops.
  * pc_stats fills up to `cap` records (name, launches, summed device ms,
  * summed algorithmic DRAM bytes) and returns the number of classes; it
- * synchronises the events.  pc_launch_count returns the number of kernels the
+ * synchronises the events.  For the class "arnoldi_reorth" (the second
+ * Gram-Schmidt pass, launched flag-gated every iteration) `launches` counts the
+ * iterations in which it actually ran and `bytes` only their traffic.  pc_launch_count returns the number of kernels the
  * handle has launched since setup or pc_stats_reset. */
 typedef struct pc_kernel_stat {
   char name[32];

@@ -56,6 +56,11 @@ _SIGNATURES = {
     "pc_apply_precond": (_i, [_vp, _dp, _dp, _vp]),
     "pc_build_rhs": (_i, [_vp, _dp, _dp, _dp, _dp, _vp]),
     "pc_gmres_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
+    "pc_gmres_solve_graph": (_i, [_vp, _dp, _dp, _d, _i, _ip, _dpp, _vp]),
+    "pc_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
+                             ctypes.POINTER(_vp)]),
+    "pc_batch_solve": (_i, [_vp, _ip, _dpp, _vp]),
+    "pc_batch_destroy": (_i, [_vp]),
     "pc_adjoint_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),

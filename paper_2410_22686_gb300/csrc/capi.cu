@@ -74,7 +74,7 @@ void Launch::begin(int kc) {
 cudaError_t Launch::end(int kc, double bytes, double flops) {
   cudaError_t e = cudaGetLastError();
   if (prof) {
-    prof->launches[kc]++;
+    if (kc != KC_REORTH) prof->launches[kc]++;  // re-orthogonalisations are counted when they ran
     prof->total++;
     prof->bytes[kc] += bytes;
     prof->flops[kc] += flops;
@@ -161,8 +161,10 @@ struct pc_handle {
 
   std::vector<LevelBuf> lv;
   // time FFT tables
-  double* dpow64 = nullptr;
+  double* dpow64 = nullptr;  // eps^{j/n}
   float* dpow32 = nullptr;
+  double* dinv64 = nullptr;  // eps^{-j/n}
+  float* dinv32 = nullptr;
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   double2* sig64 = nullptr;
@@ -193,9 +195,17 @@ struct pc_handle {
   double* partial = nullptr;
   int nblocks = 0;         // rows of `partial`: SMs x blocks per SM
   double* host = nullptr;  // pinned: [0] est, [1] ref, [2] nrm2, ... (16 doubles)
-  int64_t reorth_count = 0;
   std::vector<void*> allocs;
   Prof prof;
+  // graph-captured solve
+  int* idx = nullptr;                 // device: [0] Arnoldi index j, [1] iterations done k
+  cudaStream_t cap_stream = nullptr;  // capture streams (a batch captures each problem on its own)
+  cudaStream_t aux_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;    // single-problem solve graph and what it was built for
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  double g_rtol = 0.0;
+  int g_maxit = 0;
 };
 
 static int dev_alloc(pc_handle* h, void** p, size_t bytes) {
@@ -214,6 +224,11 @@ static int dev_alloc_t(pc_handle* h, T** p, size_t count) {
 }
 
 static void release(pc_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+  h->cap_stream = h->aux_stream = nullptr;
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->host) cudaFreeHost(h->host);
@@ -439,9 +454,13 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   // ---- time FFT tables
   {
     const int n = h->n;
-    std::vector<double> dp(n), twr(std::max(1, n / 2)), twi(std::max(1, n / 2));
-    for (int j = 0; j < n; ++j) dp[j] = std::pow(p->eps, (double)j / n);
-    for (int k = 0; k < std::max(1, n / 2); ++k) {
+    // full circle of twiddles exp(-2 pi i k / n), k = 0..n-1
+    std::vector<double> dp(n), di(n), twr(n), twi(n);
+    for (int j = 0; j < n; ++j) {
+      dp[j] = std::pow(p->eps, (double)j / n);
+      di[j] = std::pow(p->eps, -(double)j / n);
+    }
+    for (int k = 0; k < n; ++k) {
       const double th = 2.0 * M_PI * (double)k / n;
       twr[k] = std::cos(th);
       twi[k] = -std::sin(th);
@@ -457,6 +476,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     }
     if ((rc = upload(h, &h->dpow64, dp, st))) goto fail_out;
     if ((rc = upload(h, &h->dpow32, dp, st))) goto fail_out;
+    if ((rc = upload(h, &h->dinv64, di, st))) goto fail_out;
+    if ((rc = upload(h, &h->dinv32, di, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->tw64, twr, twi, false, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->tw32, twr, twi, true, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->sig64, sr, si, false, st))) goto fail_out;
@@ -500,6 +521,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = dev_alloc_t(h, &h->ycoef, (size_t)cap + 1))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->scal, 16))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 2)))) goto fail_out;
+    if ((rc = dev_alloc_t(h, &h->idx, 4))) goto fail_out;
     cudaError_t e = cudaMallocHost((void**)&h->host, 16 * sizeof(double));
     if (e != cudaSuccess) {
       rc = fail(PC_ERR_OOM, "cudaMallocHost failed");
@@ -507,7 +529,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     }
   }
   {
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "pc_setup");
       goto fail_out;
@@ -612,6 +636,7 @@ struct Tables;
 template <>
 struct Tables<double> {
   static const double* dpow(const pc_handle* h) { return h->dpow64; }
+  static const double* dinv(const pc_handle* h) { return h->dinv64; }
   static const double2* tw(const pc_handle* h) { return h->tw64; }
   static const double2* sig(const pc_handle* h) { return h->sig64; }
   static const double* S(const pc_handle* h) { return h->S64; }
@@ -620,6 +645,7 @@ struct Tables<double> {
 template <>
 struct Tables<float> {
   static const float* dpow(const pc_handle* h) { return h->dpow32; }
+  static const float* dinv(const pc_handle* h) { return h->dinv32; }
   static const float2* tw(const pc_handle* h) { return h->tw32; }
   static const float2* sig(const pc_handle* h) { return h->sig32; }
   static const float* S(const pc_handle* h) { return h->S32; }
@@ -674,20 +700,25 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
   return cudaSuccess;
 }
 
+// w = P^{-1} v; with jdev != nullptr the input is v + j*stride and the output w + j*stride
 template <typename Tc, typename TU, typename Tout>
-static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w) {
+static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w, size_t stride = 0,
+                             const int* jdev = nullptr) {
   typedef typename Cx<Tc>::t C;
-  cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::tw(h), (C*)h->lv[0].r);
+  cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::dinv(h),
+                                          Tables<Tc>::tw(h), (C*)h->lv[0].r, stride, jdev);
   if (e != cudaSuccess) return e;
   if ((e = spatial_solve<Tc, TU>(h, L)) != cudaSuccess) return e;
   return launch_tfft_inverse<Tc, TU, Tout>(L, h->ms, h->n, (const TU*)h->lv[0].u, Tables<Tc>::dpow(h),
-                                           Tables<Tc>::tw(h), w);
+                                           Tables<Tc>::dinv(h), Tables<Tc>::tw(h), w, stride, jdev);
 }
 
 // FP32 preconditioner into Tout, with the handle's iterate storage
 template <typename Tout>
-static cudaError_t precond32(pc_handle* h, Launch& L, const double* v, Tout* w) {
-  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout>(h, L, v, w) : precond_t<float, float2, Tout>(h, L, v, w);
+static cudaError_t precond32(pc_handle* h, Launch& L, const double* v, Tout* w, size_t stride = 0,
+                             const int* jdev = nullptr) {
+  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout>(h, L, v, w, stride, jdev)
+                  : precond_t<float, float2, Tout>(h, L, v, w, stride, jdev);
 }
 
 // w (FP64) = P^{-1} v in the handle's precision
@@ -864,7 +895,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     if (reorth) {  // book the second Gram-Schmidt pass that ran
       h->prof.bytes[KC_REORTH] += 8.0 * U * (2.0 * (j + 1) + 6.0);
       h->prof.flops[KC_REORTH] += 4.0 * U * (j + 1);
-      h->reorth_count++;
+      h->prof.launches[KC_REORTH]++;
     }
     k = j + 1;
     if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite residual estimate");
@@ -922,6 +953,266 @@ extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, doub
   cudaError_t se = cudaStreamSynchronize(st);
   if (se != cudaSuccess) return cuda_fail(se, "pc_adjoint_solve");
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Graph-captured solve (right-preconditioned FGMRES, zero initial guess): the
+// whole solve is one graph; the iteration is the body of a WHILE conditional
+// node whose condition the loop-control kernel sets on the device, so no host
+// round trip happens per iteration.  Every launch of the body reads the Arnoldi
+// index from h->idx, so one captured iteration serves all of them.
+// ---------------------------------------------------------------------------
+#define GR_CUDA(...)                                                             \
+  do {                                                                           \
+    cudaError_t _e = (__VA_ARGS__);                                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #__VA_ARGS__);                   \
+  } while (0)
+
+static int graph_supported(const pc_handle* h, int maxit) {
+  if (maxit < 1 || maxit > h->cap) return fail(PC_ERR_ARG, "graph solve: maxit must be in [1, max_iter]");
+  const int nmax = h->fp32 ? 1024 : 256;
+  if (h->n > nmax) return fail(PC_ERR_UNSUPPORTED, "graph solve: n too large for the register FFT");
+  return PC_OK;
+}
+
+// x = 0, r0 = b, ref = ||b||, g0 = beta, v0 = b / beta, enter the loop iff est > rtol
+static int enqueue_pre(pc_handle* h, Launch& L, const double* b, double* x, double rtol,
+                       cudaGraphConditionalHandle hc) {
+  const size_t U = h->U;
+  double* nrm2 = h->scal + 0;
+  GR_CUDA(cudaMemsetAsync(x, 0, U * sizeof(double), L.stream));
+  GR_CUDA(launch_norm2(L, b, U, h->partial, nrm2));
+  GR_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, h->scal + 1, h->scal + 2, 1));
+  GR_CUDA(cudaMemcpyAsync(h->V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, L.stream));
+  GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr));
+  GR_CUDA(launch_loop_start(L, h->idx, h->idx + 1, h->scal + 1, rtol, hc));
+  return PC_OK;
+}
+
+// one FGMRES iteration with device-resident index j = h->idx[0]
+static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGraphConditionalHandle hc) {
+  const size_t U = h->U;
+  const int ldh = h->cap + 1;
+  const int* j = h->idx;
+  const ArnoldiScalars AS{h->scal + 4, h->scal + 5, h->scal + 6, h->scal + 7, h->scal + 8, h->scal + 9};
+  Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
+  const Grid g = grid_of(h, 0);
+  if (h->fp32) {
+    float* Z = (float*)h->Z;
+    GR_CUDA(precond32<float>(h, L, h->V, Z, U, j));
+    GR_CUDA(launch_matvec<float>(L, g, h->n, st, h->alpha, Z, h->V, false, U, U, j));
+  } else {
+    double* Z = (double*)h->Z;
+    GR_CUDA((precond_t<double, double2, double>(h, L, h->V, Z, U, j)));
+    GR_CUDA(launch_matvec<double>(L, g, h->n, st, h->alpha, Z, h->V, false, U, U, j));
+  }
+  GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol, AS.ww, nullptr));
+  GR_CUDA(launch_arnoldi_prep_dev(L, j, h->hcol, AS));
+  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol, h->V, U, U, AS.inv, h->partial, AS.q, nullptr));
+  GR_CUDA(launch_arnoldi_check(L, AS));
+  GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
+  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol + ldh, h->V, U, U, nullptr, h->partial, AS.rho2, AS.flag));
+  GR_CUDA(launch_scale_dev(L, h->V, U, j, U, AS.rho2, AS.flag));
+  GR_CUDA(launch_givens_dev(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, h->scal + 1,
+                            h->scal + 2));
+  GR_CUDA(launch_loop_control(L, h->idx, h->idx + 1, h->scal + 1, rtol, maxit, hc));
+  return PC_OK;
+}
+
+// x = Z y (k = h->idx[1] columns), true residual ||b - A x||^2 -> scal[3]
+static int enqueue_post(pc_handle* h, Launch& L, const double* b, double* x, int maxit) {
+  const size_t U = h->U;
+  const int ldh = h->cap + 1;
+  GR_CUDA(launch_backsolve_dev(L, h->idx + 1, ldh, h->H, h->gvec, h->ycoef));
+  if (h->fp32)
+    GR_CUDA(launch_xupdate_dev<float>(L, (const float*)h->Z, U, maxit, h->idx + 1, h->ycoef, x, U));
+  else
+    GR_CUDA(launch_xupdate_dev<double>(L, (const double*)h->Z, U, maxit, h->idx + 1, h->ycoef, x, U));
+  GR_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
+  GR_CUDA(launch_axpby<double>(L, 1.0, b, -1.0, h->wbuf, U));
+  GR_CUDA(launch_norm2(L, h->wbuf, U, h->partial, h->scal + 3));
+  return PC_OK;
+}
+
+// Enqueue one complete solve into `st`, which must be capturing; the loop body is
+// captured on the handle's auxiliary stream into the conditional node's graph.
+static int capture_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit, cudaStream_t st) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t G = nullptr;
+  GR_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive || !G) return fail(PC_ERR_CUDA, "capture_solve: stream is not capturing");
+  cudaGraphConditionalHandle hc;
+  GR_CUDA(cudaGraphConditionalHandleCreate(&hc, G, 0, cudaGraphCondAssignDefault));
+  Launch L{st, nullptr};
+  int rc;
+  if ((rc = enqueue_pre(h, L, b, x, rtol, hc))) return rc;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  GR_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+  std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+  // cudaGraphNodeParams holds a union without a default constructor: zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_storage, 0, sizeof(cp_storage));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  GR_CUDA(cudaGraphAddNode(&cnode, G, dv.data(), nullptr, nd, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  GR_CUDA(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  GR_CUDA(cudaStreamBeginCaptureToGraph(h->aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  Launch LB{h->aux_stream, nullptr};
+  rc = enqueue_body(h, LB, rtol, maxit, hc);
+  cudaGraph_t body_out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->aux_stream, &body_out);
+  if (rc) return rc;
+  GR_CUDA(e);
+  return enqueue_post(h, L, b, x, maxit);
+}
+
+// read iterations and the true relative residual of a finished graph solve
+static int graph_results(pc_handle* h, cudaStream_t st, double rtol, int* iters, double* relres) {
+  int kdone = 0;
+  GR_CUDA(cudaMemcpyAsync(&kdone, h->idx + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GR_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GR_CUDA(cudaStreamSynchronize(st));
+  const double ref = h->host[1], r2 = h->host[2];
+  const double rr = ref > 0 ? std::sqrt(r2) / ref : 0.0;
+  if (iters) *iters = kdone;
+  if (relres) *relres = rr;
+  if (ref == 0.0) return PC_OK;  // b = 0: x = 0 is exact
+  if (!std::isfinite(rr) || !std::isfinite(h->host[0])) return fail(PC_ERR_BREAKDOWN, "graph solve: non-finite residual");
+  if (h->host[0] > rtol) return fail(PC_ERR_NOT_CONVERGED, "graph solve: maxit reached before rtol");
+  return PC_OK;
+}
+
+extern "C" int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, int maxit, int* iters,
+                                    double* relres, void* stream) {
+  if (!h || !b || !x) return fail(PC_ERR_ARG, "pc_gmres_solve_graph: null argument");
+  if (!(rtol > 0)) return fail(PC_ERR_ARG, "pc_gmres_solve_graph: rtol must be > 0");
+  if (int rc = graph_supported(h, maxit)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!h->gexec || h->g_b != b || h->g_x != x || h->g_rtol != rtol || h->g_maxit != maxit) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    GR_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+    int rc = capture_solve(h, b, x, rtol, maxit, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    GR_CUDA(e);
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    GR_CUDA(e);
+    h->g_b = b;
+    h->g_x = x;
+    h->g_rtol = rtol;
+    h->g_maxit = maxit;
+  }
+  GR_CUDA(cudaGraphLaunch(h->gexec, st));
+  return graph_results(h, st, rtol, iters, relres);
+}
+
+// ---------------------------------------------------------------------------
+// Batch: many independent problems (uneven m1, n, gamma, a) solved by ONE graph
+// launch; each problem is a parallel branch with its own WHILE loop.
+// ---------------------------------------------------------------------------
+struct pc_batch {
+  std::vector<pc_handle*> hs;
+  double rtol = 0.0;
+  int maxit = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaEvent_t> events;
+};
+
+static void batch_release(pc_batch* bt) {
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  for (auto e : bt->events) cudaEventDestroy(e);
+  if (bt->origin) cudaStreamDestroy(bt->origin);
+}
+
+extern "C" int pc_batch_create(pc_handle* const* hs, int count, const double* const* b, double* const* x, double rtol,
+                               int maxit, pc_batch** out) {
+  if (!hs || !b || !x || !out || count < 1) return fail(PC_ERR_ARG, "pc_batch_create: bad arguments");
+  if (!(rtol > 0)) return fail(PC_ERR_ARG, "pc_batch_create: rtol must be > 0");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !b[i] || !x[i]) return fail(PC_ERR_ARG, "pc_batch_create: null handle or vector");
+    if (int rc = graph_supported(hs[i], maxit)) return rc;
+    for (int q = 0; q < i; ++q)
+      if (hs[q] == hs[i]) return fail(PC_ERR_ARG, "pc_batch_create: a handle appears twice");
+  }
+  pc_batch* bt = new (std::nothrow) pc_batch();
+  if (!bt) return fail(PC_ERR_OOM, "host allocation failed");
+  bt->hs.assign(hs, hs + count);
+  bt->rtol = rtol;
+  bt->maxit = maxit;
+  int rc = PC_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&bt->origin, cudaStreamNonBlocking);
+  for (int i = 0; e == cudaSuccess && i < 2 * count + 1; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) bt->events.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    batch_release(bt);
+    delete bt;
+    return cuda_fail(e, "pc_batch_create");
+  }
+  e = cudaStreamBeginCapture(bt->origin, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) e = cudaEventRecord(bt->events[0], bt->origin);
+  for (int i = 0; e == cudaSuccess && rc == PC_OK && i < count; ++i) {
+    // fork: the problem's capture stream joins the capture, then runs its own solve
+    e = cudaStreamWaitEvent(hs[i]->cap_stream, bt->events[0], 0);
+    if (e != cudaSuccess) break;
+    rc = capture_solve(hs[i], b[i], x[i], rtol, maxit, hs[i]->cap_stream);
+    if (rc) break;
+    e = cudaEventRecord(bt->events[1 + i], hs[i]->cap_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->origin, bt->events[1 + i], 0);  // join
+  }
+  cudaError_t ee = cudaStreamEndCapture(bt->origin, &g);
+  if (rc == PC_OK && e != cudaSuccess) rc = cuda_fail(e, "pc_batch_create: capture");
+  if (rc == PC_OK && ee != cudaSuccess) rc = cuda_fail(ee, "pc_batch_create: end capture");
+  if (rc == PC_OK) {
+    e = cudaGraphInstantiate(&bt->exec, g, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "pc_batch_create: instantiate");
+  }
+  if (g) cudaGraphDestroy(g);
+  if (rc != PC_OK) {
+    batch_release(bt);
+    delete bt;
+    return rc;
+  }
+  *out = bt;
+  return PC_OK;
+}
+
+extern "C" int pc_batch_solve(pc_batch* bt, int* iters, double* relres, void* stream) {
+  if (!bt) return fail(PC_ERR_ARG, "pc_batch_solve: null batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  GR_CUDA(cudaGraphLaunch(bt->exec, st));
+  int worst = PC_OK;
+  for (size_t i = 0; i < bt->hs.size(); ++i) {
+    const int rc = graph_results(bt->hs[i], st, bt->rtol, iters ? iters + i : nullptr, relres ? relres + i : nullptr);
+    if (rc == PC_ERR_CUDA) return rc;
+    if (rc != PC_OK && worst == PC_OK) worst = rc;
+  }
+  return worst;
+}
+
+extern "C" int pc_batch_destroy(pc_batch* bt) {
+  if (!bt) return PC_OK;
+  cudaDeviceSynchronize();
+  batch_release(bt);
+  delete bt;
+  return PC_OK;
 }
 
 // ---------------------------------------------------------------------------

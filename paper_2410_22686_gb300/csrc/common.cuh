@@ -52,6 +52,54 @@ __host__ __device__ __forceinline__ double2 cinv(double2 z) {
 template <typename T>
 __host__ __device__ __forceinline__ typename Cx<T>::t czero() { return cmk<T>(T(0), T(0)); }
 
+// FP64 <-> FP32 conversions on the integer pipes.  GB300 executes F2F
+// conversions on its FP64 unit, whose rate is 1/64 of FP32, which made plain
+// casts the bottleneck of the FP32 kernels that read FP64 vectors.  Both follow
+// the IEEE-754 binary64/binary32 layouts.  FP64 -> FP32 rounds half up on the
+// magnitude (ties away from zero; differs from round-to-nearest-even only on
+// exact ties), flushes results below the FP32 normal range to a signed zero and
+// saturates larger magnitudes, infinities and NaNs to infinity: it feeds FP32
+// preconditioner inputs only.  FP32 -> FP64 is exact; FP32 subnormals flush to
+// zero, infinities and NaNs are kept.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mag = hi & 0x7FFFFFFFu;  // exponent (11 bits) and top 20 mantissa bits
+  // rebias 1023 -> 127, keep 23 mantissa bits, round half up on the magnitude (a carry
+  // moves into the exponent); magnitudes below the FP32 normal range flush to zero,
+  // above it (and infinities, NaNs) saturate to infinity
+  unsigned f = ((mag - (896u << 20)) << 3) | (lo >> 29);
+  f += (lo >> 28) & 1u;
+  f = mag < (897u << 20) ? 0u : f;
+  f = mag >= (1151u << 20) ? 0x7F800000u : f;
+  return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  unsigned hi, lo;
+  if (e == 0) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    lo = m << 29;
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+// generic casts used by templated kernels
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From x) { return (To)x; }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) { return f64_to_f32(x); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) { return f32_to_f64(x); }
+
 // storage of complex multigrid iterates: the compute type itself, or a BF16 pair
 // (FP32 arithmetic, BF16 storage) for the BF16-storage smoother variant
 __device__ __forceinline__ float2 ldc(const float2* p, int64_t i) { return p[i]; }
@@ -139,18 +187,25 @@ struct Stencil {
 // launchers (defined in the k_*.cu files)
 // ---------------------------------------------------------------------------
 // y = A x (transpose=false) or A^T x; x in Tin (double or float), y double.
+// With jdev != nullptr: x += (*jdev) * xstride and y += (*jdev + 1) * ystride.
 template <typename Tin>
 cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>& st, double alpha,
-                          const Tin* x, double* y, bool transpose);
+                          const Tin* x, double* y, bool transpose, size_t xstride = 0, size_t ystride = 0,
+                          const int* jdev = nullptr);
 
 // forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
+// dpow[j] = eps^{j/n}, dinv[j] = eps^{-j/n}, tw[k] = exp(-2 pi i k/n) for k = 0..n-1
+// With jdev != nullptr the input is v + (*jdev) * vstride (device-resident Arnoldi index).
 template <typename Tc>
-cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow,
-                                const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec);
+cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow, const Tc* dinv,
+                                const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride = 0,
+                                const int* jdev = nullptr);
 // inverse scaled time FFT + butterfly: spectral planes (stored as TU) -> w (Tout [2][n][ms])
+// With jdev != nullptr the output is w + (*jdev) * wstride.
 template <typename Tc, typename TU, typename Tout>
-cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow,
-                                const typename Cx<Tc>::t* tw, Tout* w);
+cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
+                                const typename Cx<Tc>::t* tw, Tout* w, size_t wstride = 0,
+                                const int* jdev = nullptr);
 
 // FST: one DST-I along `axis` of every plane (out = S in), and the spectral divide
 template <typename Tc>
@@ -205,6 +260,31 @@ cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, doub
 cudaError_t launch_backsolve(Launch& L, int k, int ldh, const double* H, const double* gvec, double* y);
 template <typename Tz>
 cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const double* y, double* x, size_t len);
+// Device-index variants for graph-captured iterations: the Arnoldi index j is read
+// from jdev (nv = j + 1 basis vectors, the new vector is base + (j + 1) * stride),
+// launch shapes are sized for nv_max, and their traffic is not booked (no events
+// can be recorded inside a conditional graph body).
+cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev,
+                                const double* wbase, size_t wstride, size_t len, double* partial, double* out,
+                                double* ww, const double* gate);
+cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
+                              double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
+                              double* q, const double* gate);
+cudaError_t launch_scale_dev(Launch& L, double* vbase, size_t vstride, const int* jdev, size_t len,
+                             const double* nrm2, const double* gate);
+cudaError_t launch_arnoldi_prep_dev(Launch& L, const int* jdev, const double* d, ArnoldiScalars s);
+cudaError_t launch_givens_dev(Launch& L, const int* jdev, int ldh, double* H, double* cs, double* sn, double* gvec,
+                              const double* d, const double* e, ArnoldiScalars s, double* est, const double* ref);
+// loop control of the captured iteration (sets the WHILE condition; k = iterations done)
+cudaError_t launch_loop_control(Launch& L, int* jdev, int* kdev, const double* est, double rtol, int maxit,
+                                cudaGraphConditionalHandle hc);
+cudaError_t launch_loop_start(Launch& L, int* jdev, int* kdev, const double* est, double rtol,
+                              cudaGraphConditionalHandle hc);
+cudaError_t launch_backsolve_dev(Launch& L, const int* kdev, int ldh, const double* H, const double* gvec, double* y);
+template <typename Tz>
+cudaError_t launch_xupdate_dev(Launch& L, const Tz* Z, size_t ldz, int kmax, const int* kdev, const double* y,
+                               double* x, size_t len);
+
 // start vector: v0 = r / ||r||, gvec[0] = ||r||, ref := ||r0|| or given
 cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, double* est, double* ref_out,
                                  int set_ref);

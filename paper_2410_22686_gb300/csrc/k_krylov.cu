@@ -36,11 +36,9 @@ __device__ __forceinline__ bool gated_off(const double* gate) { return gate && g
 // partial[b*ld + i0 + c] = sum over block b of V_{i0+c} . w   (c < CNT)
 // partial[b*ld + nv]     = sum over block b of w . w          (WITH_NORM)
 template <int CNT, bool WITH_NORM>
-__global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ldv, int i0,
-                                                            const double* __restrict__ w, size_t len,
-                                                            double* __restrict__ partial, int nv, int ld,
-                                                            const double* __restrict__ gate) {
-  if (gated_off(gate)) return;
+__device__ __forceinline__ void multidot_body(const double* __restrict__ V, size_t ldv, int i0,
+                                              const double* __restrict__ w, size_t len,
+                                              double* __restrict__ partial, int ncol_norm, int ld) {
   double acc[CNT];
   double ww = 0.0;
 #pragma unroll
@@ -68,8 +66,41 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __rest
   if (threadIdx.x < CNT + (WITH_NORM ? 1 : 0)) {
     double s = 0.0;
     for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
-    const int col = threadIdx.x < CNT ? i0 + threadIdx.x : nv;
+    const int col = threadIdx.x < CNT ? i0 + threadIdx.x : ncol_norm;
     partial[(size_t)blockIdx.x * ld + col] = s;
+  }
+}
+
+template <int CNT, bool WITH_NORM>
+__global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ldv, int i0,
+                                                            const double* __restrict__ w, size_t len,
+                                                            double* __restrict__ partial, int nv, int ld,
+                                                            const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
+  multidot_body<CNT, WITH_NORM>(V, ldv, i0, w, len, partial, nv, ld);
+}
+
+// Device-resident Arnoldi index: nv = *jdev + 1 vectors, w = wbase + (*jdev + 1) wstride;
+// the chunk [i0, i0 + 16) exits when it lies beyond nv, otherwise dispatches on its count.
+// The norm column is ld - 1.
+template <bool WITH_NORM>
+__global__ void __launch_bounds__(kThreads) multidot_dyn_kernel(const double* __restrict__ V, size_t ldv, int i0,
+                                                                const double* __restrict__ wbase, size_t wstride,
+                                                                const int* __restrict__ jdev, size_t len,
+                                                                double* __restrict__ partial, int ld,
+                                                                const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
+  const int nv = *jdev + 1;
+  if (i0 >= nv) return;
+  const double* w = wbase + (size_t)nv * wstride;
+  const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
+  switch (cnt) {
+#define PCOPT_DYN(k) \
+  case k: multidot_body<k, WITH_NORM>(V, ldv, i0, w, len, partial, ld - 1, ld); break;
+    PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
+    PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
+#undef PCOPT_DYN
+    default: break;
   }
 }
 
@@ -80,12 +111,23 @@ struct ChunkGrids {
 
 // out[i] = sum_b partial[b*ld + i] for i < nout (column nout goes to *extra), in a
 // fixed order; one block per column
+// With jdev != nullptr: nout = *jdev + 1, the grid covers the largest count, blocks
+// beyond nout exit, and the last block reduces the extra column ld - 1.
 __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, ChunkGrids cg,
                                                                    int ld, double* __restrict__ out,
                                                                    double* __restrict__ extra, int nout,
-                                                                   const double* __restrict__ gate) {
+                                                                   const double* __restrict__ gate,
+                                                                   const int* __restrict__ jdev) {
   if (gated_off(gate)) return;
-  const int i = blockIdx.x;
+  int i = blockIdx.x;
+  if (jdev) {
+    nout = *jdev + 1;
+    if (extra && i == (int)gridDim.x - 1) {
+      i = ld - 1;
+    } else if (i >= nout) {
+      return;
+    }
+  }
   const int nblocks = (int)cg.nb[i < nout ? i / kChunk : 0];
   double s = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * ld + i];
@@ -104,12 +146,18 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double*
 }
 
 // v = (v - sum_i coef_i V_i) * scale ;  partial[b] = sum over block b of (v - sum)^2 (before scaling)
+// with jdev != nullptr: nv = *jdev + 1 and v = vbase + nv * vstride
 __global__ void __launch_bounds__(kThreads) update_kernel(const double* __restrict__ V, size_t ldv, int nv,
                                                           const double* __restrict__ coef, double* __restrict__ v,
                                                           size_t len, const double* __restrict__ scale,
                                                           double* __restrict__ partial,
-                                                          const double* __restrict__ gate) {
+                                                          const double* __restrict__ gate,
+                                                          const int* __restrict__ jdev, size_t vstride) {
   if (gated_off(gate)) return;
+  if (jdev) {
+    nv = *jdev + 1;
+    v += (size_t)nv * vstride;
+  }
   extern __shared__ double hs[];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = coef[i];
   __syncthreads();
@@ -151,8 +199,10 @@ __global__ void __launch_bounds__(kThreads) norm2_kernel(const double* __restric
 
 // v *= 1/sqrt(nrm2[0])  (gated)
 __global__ void scale_kernel(double* __restrict__ v, size_t len, const double* __restrict__ nrm2,
-                             const double* __restrict__ gate) {
+                             const double* __restrict__ gate, const int* __restrict__ jdev, size_t vstride) {
   if (gated_off(gate)) return;
+  if (jdev) v += (size_t)(*jdev + 1) * vstride;
+  if (!(nrm2[0] > 0.0)) return;  // zero vector: nothing to normalise
   const double q = 1.0 / sqrt(nrm2[0]);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) v[e] *= q;
@@ -162,12 +212,13 @@ template <typename Tx>
 __global__ void axpby_kernel(double a, const Tx* __restrict__ x, double b, double* __restrict__ y, size_t len) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride)
-    y[e] = (b == 0.0) ? a * (double)x[e] : fma(a, (double)x[e], b * y[e]);
+    y[e] = (b == 0.0) ? a * cvt<double>(x[e]) : fma(a, cvt<double>(x[e]), b * y[e]);
 }
 
 // c = sqrt(||w||^2 - ||d||^2) when that is safely positive, else 1 (and force re-orthogonalisation)
-__global__ void arnoldi_prep_kernel(int nv, const double* d, ArnoldiScalars s) {
+__global__ void arnoldi_prep_kernel(int nv, const double* d, ArnoldiScalars s, const int* jdev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (jdev) nv = *jdev + 1;
   double dd = 0.0;
   for (int i = 0; i < nv; ++i) dd = fma(d[i], d[i], dd);
   const double ww = s.ww[0];
@@ -183,13 +234,16 @@ __global__ void arnoldi_prep_kernel(int nv, const double* d, ArnoldiScalars s) {
   }
 }
 
-// re-orthogonalise when ||w - V d||^2 < 1e-3 ||w||^2 (more than 99.95% cancelled) or the
-// Pythagorean norm disagrees with the computed one by more than 1e-6 (relative, squared)
+// re-orthogonalise when ||w - V d||^2 < 1e-10 ||w||^2 (one pass then leaves a loss
+// of orthogonality of about eps ||w|| / ||w - V d|| > 1e-11) or when the Pythagorean
+// norm disagrees with the computed one by more than 1e-6 (relative, squared).  With
+// a strong preconditioner A P^{-1} v_j is close to v_j, so strong cancellation is the
+// normal case and a tighter trigger would re-orthogonalise in many iterations.
 __global__ void arnoldi_check_kernel(ArnoldiScalars s) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (s.flag[0] != 0.0) return;
   const double q = s.q[0], ww = s.ww[0], c2 = s.c[0] * s.c[0];
-  const bool bad = !(q >= 1e-3 * ww) || !(fabs(q - c2) <= 1e-6 * q);
+  const bool bad = !(q >= 1e-10 * ww) || !(fabs(q - c2) <= 1e-6 * q);
   s.flag[0] = bad ? 1.0 : 0.0;
 }
 
@@ -197,8 +251,9 @@ __global__ void arnoldi_check_kernel(ArnoldiScalars s) {
 //   no re-orthogonalisation:  w = V d + c v_{j+1}
 //   re-orthogonalisation:     w = V (d + c e) + c rho v_{j+1},  rho^2 = s.rho2
 __global__ void givens_kernel(int j, int ldh, double* H, double* cs, double* sn, double* g, const double* d,
-                              const double* e, ArnoldiScalars s, double* est, const double* ref) {
+                              const double* e, ArnoldiScalars s, double* est, const double* ref, const int* jdev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (jdev) j = *jdev;
   double* col = H + (size_t)j * ldh;
   const bool re = s.flag[0] != 0.0;
   const double c = s.c[0];
@@ -225,8 +280,9 @@ __global__ void givens_kernel(int j, int ldh, double* H, double* cs, double* sn,
   est[0] = fabs(g[j + 1]) / ref[0];
 }
 
-__global__ void backsolve_kernel(int k, int ldh, const double* H, const double* g, double* y) {
+__global__ void backsolve_kernel(int k, int ldh, const double* H, const double* g, double* y, const int* kdev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (kdev) k = *kdev;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
     for (int q = i + 1; q < k; ++q) s -= H[(size_t)q * ldh + i] * y[q];
@@ -237,14 +293,15 @@ __global__ void backsolve_kernel(int k, int ldh, const double* H, const double* 
 template <typename Tz>
 __global__ void __launch_bounds__(kThreads) xupdate_kernel(const Tz* __restrict__ Z, size_t ldz, int k,
                                                            const double* __restrict__ y, double* __restrict__ x,
-                                                           size_t len) {
+                                                           size_t len, const int* __restrict__ kdev) {
+  if (kdev) k = *kdev;
   extern __shared__ double ys[];
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
   __syncthreads();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
     double xe = x[e];
-    for (int i = 0; i < k; ++i) xe = fma(ys[i], (double)Z[(size_t)i * ldz + e], xe);
+    for (int i = 0; i < k; ++i) xe = fma(ys[i], cvt<double>(Z[(size_t)i * ldz + e]), xe);
     x[e] = xe;
   }
 }
@@ -255,6 +312,30 @@ __global__ void arnoldi_start_kernel(double* g, const double* nrm2, double* est,
   g[0] = beta;
   if (set_ref) ref[0] = beta;
   est[0] = beta / ref[0];
+}
+
+// Loop control of a graph-captured FGMRES iteration: k = j + 1 iterations are done;
+// continue (condition 1) while the estimate is finite, above rtol and j + 1 < maxit.
+__global__ void loop_control_kernel(int* jdev, int* kdev, const double* est, double rtol, int maxit,
+                                    cudaGraphConditionalHandle hc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = *jdev;
+  const double e = est[0];
+  const bool cont = isfinite(e) && e > rtol && j + 1 < maxit;
+  *kdev = j + 1;
+  if (cont) *jdev = j + 1;
+  cudaGraphSetConditional(hc, cont ? 1u : 0u);
+}
+
+// Before the loop: j = k = 0, and enter the loop only when the initial estimate is
+// finite and above rtol.
+__global__ void loop_start_kernel(int* jdev, int* kdev, const double* est, double rtol,
+                                  cudaGraphConditionalHandle hc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *jdev = 0;
+  *kdev = 0;
+  const double e = est[0];
+  cudaGraphSetConditional(hc, (isfinite(e) && e > rtol) ? 1u : 0u);
 }
 
 // blocks that fit the device at once for kernel `fn` (one wave), capped by the work size
@@ -327,7 +408,7 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
   const int ncols = nv + (ww ? 1 : 0);
   const int kc = gate ? KC_REORTH : KC_REDUCE;
   L.begin(kc);
-  reduce_partials_kernel<<<ncols, kThreads, 0, L.stream>>>(partial, cg, ld, out, ww, nv, gate);
+  reduce_partials_kernel<<<ncols, kThreads, 0, L.stream>>>(partial, cg, ld, out, ww, nv, gate, nullptr);
   return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * nb_sum, nb_sum);
 }
 
@@ -337,12 +418,12 @@ cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const 
   const unsigned nb = wave_blocks(update_kernel, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
-  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate);
+  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate, nullptr, 0);
   cudaError_t e = gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
   if (e != cudaSuccess) return e;
   const int kr = gate ? KC_REORTH : KC_REDUCE;
   L.begin(kr);
-  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate, nullptr);
   return gate ? L.end(kr, 0.0, 0.0) : L.end(kr, 8.0 * nb, 1.0 * nb);
 }
 
@@ -353,14 +434,15 @@ cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial
   cudaError_t e = L.end(KC_DOT, 8.0 * len, 2.0 * len);
   if (e != cudaSuccess) return e;
   L.begin(KC_REDUCE);
-  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, nrm2, nrm2, 1, nullptr);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, nrm2, nrm2, 1, nullptr,
+                                                       nullptr);
   return L.end(KC_REDUCE, 8.0 * nb, 1.0 * nb);
 }
 
 cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate) {
   const int kc = gate ? KC_REORTH : KC_SCALE;
   L.begin(kc);
-  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, len, nrm2, gate);
+  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, len, nrm2, gate, nullptr, 0);
   return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len, 1.0 * len);
 }
 
@@ -375,7 +457,7 @@ template cudaError_t launch_axpby<float>(Launch&, double, const float*, double, 
 
 cudaError_t launch_arnoldi_prep(Launch& L, int nv, const double* d, ArnoldiScalars s) {
   L.begin(KC_GIVENS);
-  arnoldi_prep_kernel<<<1, 32, 0, L.stream>>>(nv, d, s);
+  arnoldi_prep_kernel<<<1, 32, 0, L.stream>>>(nv, d, s, nullptr);
   return L.end(KC_GIVENS, 0.0, 2.0 * nv);
 }
 
@@ -388,13 +470,13 @@ cudaError_t launch_arnoldi_check(Launch& L, ArnoldiScalars s) {
 cudaError_t launch_givens(Launch& L, int j, int ldh, double* H, double* cs, double* sn, double* gvec, const double* d,
                           const double* e, ArnoldiScalars s, double* est, const double* ref) {
   L.begin(KC_GIVENS);
-  givens_kernel<<<1, 32, 0, L.stream>>>(j, ldh, H, cs, sn, gvec, d, e, s, est, ref);
+  givens_kernel<<<1, 32, 0, L.stream>>>(j, ldh, H, cs, sn, gvec, d, e, s, est, ref, nullptr);
   return L.end(KC_GIVENS, 0.0, 10.0 * (j + 1));
 }
 
 cudaError_t launch_backsolve(Launch& L, int k, int ldh, const double* H, const double* gvec, double* y) {
   L.begin(KC_GIVENS);
-  backsolve_kernel<<<1, 32, 0, L.stream>>>(k, ldh, H, gvec, y);
+  backsolve_kernel<<<1, 32, 0, L.stream>>>(k, ldh, H, gvec, y, nullptr);
   return L.end(KC_GIVENS, 0.0, 1.0 * k * k);
 }
 
@@ -402,7 +484,8 @@ template <typename Tz>
 cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const double* y, double* x, size_t len) {
   const size_t smem = sizeof(double) * (k > 0 ? k : 1);
   L.begin(KC_XUPDATE);
-  xupdate_kernel<Tz><<<wave_blocks(xupdate_kernel<Tz>, smem, len), kThreads, smem, L.stream>>>(Z, ldz, k, y, x, len);
+  xupdate_kernel<Tz><<<wave_blocks(xupdate_kernel<Tz>, smem, len), kThreads, smem, L.stream>>>(Z, ldz, k, y, x, len,
+                                                                                               nullptr);
   return L.end(KC_XUPDATE, (double)len * (k * sizeof(Tz) + 16.0), 2.0 * len * k);
 }
 template cudaError_t launch_xupdate<double>(Launch&, const double*, size_t, int, const double*, double*, size_t);
@@ -414,6 +497,107 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
   arnoldi_start_kernel<<<1, 32, 0, L.stream>>>(gvec, nrm2, est, ref_out, set_ref);
   return L.end(KC_GIVENS, 0.0, 2.0);
 }
+
+// ---------------------------------------------------------------------------
+// device-index launchers: every launch below is independent of the iteration
+// index, which the kernels read from `jdev`, so one captured iteration serves all
+cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev,
+                                const double* wbase, size_t wstride, size_t len, double* partial, double* out,
+                                double* ww, const double* gate) {
+  if (nv_max < 1 || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+  const int ld = nv_max + 1;
+  const unsigned nb_norm = wave_blocks(multidot_dyn_kernel<true>, 0, len);
+  const unsigned nb_plain = wave_blocks(multidot_dyn_kernel<false>, 0, len);
+  ChunkGrids cg = one_grid(nb_plain);
+  const int kc = gate ? KC_REORTH : KC_DOT;
+  for (int i0 = 0, c = 0; i0 < nv_max; i0 += kChunk, ++c) {
+    L.begin(kc);
+    if (i0 == 0 && ww) {
+      cg.nb[0] = nb_norm;
+      multidot_dyn_kernel<true><<<nb_norm, kThreads, 0, L.stream>>>(V, ldv, i0, wbase, wstride, jdev, len, partial,
+                                                                   ld, gate);
+    } else {
+      multidot_dyn_kernel<false><<<nb_plain, kThreads, 0, L.stream>>>(V, ldv, i0, wbase, wstride, jdev, len,
+                                                                     partial, ld, gate);
+    }
+    cudaError_t e = L.end(kc, 0.0, 0.0);
+    if (e != cudaSuccess) return e;
+  }
+  L.begin(kc);
+  reduce_partials_kernel<<<nv_max + (ww ? 1 : 0), kThreads, 0, L.stream>>>(partial, cg, ld, out, ww, nv_max, gate,
+                                                                          jdev);
+  return L.end(kc, 0.0, 0.0);
+}
+
+cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
+                              double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
+                              double* q, const double* gate) {
+  const size_t smem = sizeof(double) * nv_max;
+  const unsigned nb = wave_blocks(update_kernel, smem, len);
+  const int kc = gate ? KC_REORTH : KC_UPDATE;
+  L.begin(kc);
+  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv_max, coef, vbase, len, scale, partial, gate, jdev,
+                                                  vstride);
+  cudaError_t e = L.end(kc, 0.0, 0.0);
+  if (e != cudaSuccess) return e;
+  L.begin(kc);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate, nullptr);
+  return L.end(kc, 0.0, 0.0);
+}
+
+cudaError_t launch_scale_dev(Launch& L, double* vbase, size_t vstride, const int* jdev, size_t len,
+                             const double* nrm2, const double* gate) {
+  L.begin(KC_REORTH);
+  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(vbase, len, nrm2, gate, jdev, vstride);
+  return L.end(KC_REORTH, 0.0, 0.0);
+}
+
+cudaError_t launch_arnoldi_prep_dev(Launch& L, const int* jdev, const double* d, ArnoldiScalars s) {
+  L.begin(KC_GIVENS);
+  arnoldi_prep_kernel<<<1, 32, 0, L.stream>>>(0, d, s, jdev);
+  return L.end(KC_GIVENS, 0.0, 0.0);
+}
+
+cudaError_t launch_givens_dev(Launch& L, const int* jdev, int ldh, double* H, double* cs, double* sn, double* gvec,
+                              const double* d, const double* e, ArnoldiScalars s, double* est, const double* ref) {
+  L.begin(KC_GIVENS);
+  givens_kernel<<<1, 32, 0, L.stream>>>(0, ldh, H, cs, sn, gvec, d, e, s, est, ref, jdev);
+  return L.end(KC_GIVENS, 0.0, 0.0);
+}
+
+cudaError_t launch_loop_control(Launch& L, int* jdev, int* kdev, const double* est, double rtol, int maxit,
+                                cudaGraphConditionalHandle hc) {
+  L.begin(KC_GIVENS);
+  loop_control_kernel<<<1, 32, 0, L.stream>>>(jdev, kdev, est, rtol, maxit, hc);
+  return L.end(KC_GIVENS, 0.0, 0.0);
+}
+
+cudaError_t launch_loop_start(Launch& L, int* jdev, int* kdev, const double* est, double rtol,
+                              cudaGraphConditionalHandle hc) {
+  L.begin(KC_GIVENS);
+  loop_start_kernel<<<1, 32, 0, L.stream>>>(jdev, kdev, est, rtol, hc);
+  return L.end(KC_GIVENS, 0.0, 0.0);
+}
+
+cudaError_t launch_backsolve_dev(Launch& L, const int* kdev, int ldh, const double* H, const double* gvec, double* y) {
+  L.begin(KC_GIVENS);
+  backsolve_kernel<<<1, 32, 0, L.stream>>>(0, ldh, H, gvec, y, kdev);
+  return L.end(KC_GIVENS, 0.0, 0.0);
+}
+
+template <typename Tz>
+cudaError_t launch_xupdate_dev(Launch& L, const Tz* Z, size_t ldz, int kmax, const int* kdev, const double* y,
+                               double* x, size_t len) {
+  const size_t smem = sizeof(double) * (kmax > 0 ? kmax : 1);
+  L.begin(KC_XUPDATE);
+  xupdate_kernel<Tz><<<wave_blocks(xupdate_kernel<Tz>, smem, len), kThreads, smem, L.stream>>>(Z, ldz, kmax, y, x,
+                                                                                               len, kdev);
+  return L.end(KC_XUPDATE, 0.0, 0.0);
+}
+template cudaError_t launch_xupdate_dev<double>(Launch&, const double*, size_t, int, const int*, const double*,
+                                                double*, size_t);
+template cudaError_t launch_xupdate_dev<float>(Launch&, const float*, size_t, int, const int*, const double*, double*,
+                                               size_t);
 
 int num_sms() {
   static int cached = 0;

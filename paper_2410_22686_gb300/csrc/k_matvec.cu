@@ -21,7 +21,12 @@ template <typename Tin, int DIM, bool TRANSPOSE>
 __global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, double* __restrict__ y,
                                                      const double* __restrict__ w,
                                                      const double* __restrict__ diag, int m, int64_t ms,
-                                                     int n, int tj, double alpha) {
+                                                     int n, int tj, double alpha, size_t xstride, size_t ystride,
+                                                     const int* __restrict__ jdev) {
+  if (jdev) {  // device-resident Arnoldi index: x = Z_j, y = V_{j+1}
+    x += (size_t)(*jdev) * xstride;
+    y += (size_t)(*jdev + 1) * ystride;
+  }
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ms) return;
   const int j0 = blockIdx.y * tj;
@@ -65,18 +70,18 @@ __global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, 
     double acc = dg * centre;
 #pragma unroll
     for (int k = 0; k < 2 * DIM; ++k) {
-      double nb = ex[k] ? (double)__ldg(base + off[k]) : 0.0;
+      double nb = ex[k] ? cvt<double>(__ldg(base + off[k])) : 0.0;
       acc = fma(-wv[k], nb, acc);
     }
     return acc;
   };
 
-  double x1prev = (j0 > 0) ? (double)x1[(int64_t)(j0 - 1) * ms + s] : 0.0;
-  double x2c = (double)x2[(int64_t)j0 * ms + s];
+  double x1prev = (j0 > 0) ? cvt<double>(x1[(int64_t)(j0 - 1) * ms + s]) : 0.0;
+  double x2c = cvt<double>(x2[(int64_t)j0 * ms + s]);
   for (int j = j0; j < j1; ++j) {
     const int64_t idx = (int64_t)j * ms + s;
-    const double x1c = (double)x1[idx];
-    const double x2n = (j + 1 < n) ? (double)x2[idx + ms] : 0.0;
+    const double x1c = cvt<double>(x1[idx]);
+    const double x2n = (j + 1 < n) ? cvt<double>(x2[idx + ms]) : 0.0;
     const double k1 = tauK(x1 + idx, x1c);
     const double k2 = tauK(x2 + idx, x2c);
     const double tT_x2 = x2c - x2n + k2;     // (T^T x2)_j
@@ -97,7 +102,8 @@ __global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, 
 
 template <typename Tin>
 cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>& st, double alpha,
-                          const Tin* x, double* y, bool transpose) {
+                          const Tin* x, double* y, bool transpose, size_t xstride, size_t ystride,
+                          const int* jdev) {
   const int threads = 256;
   const int tj = n < 32 ? n : 32;
   dim3 grid((unsigned)((g.np + threads - 1) / threads), (unsigned)((n + tj - 1) / tj));
@@ -107,21 +113,21 @@ cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>
   L.begin(KC_MATVEC);
   if (g.dim == 2) {
     if (transpose)
-      matvec_kernel<Tin, 2, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+      matvec_kernel<Tin, 2, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha, xstride, ystride, jdev);
     else
-      matvec_kernel<Tin, 2, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+      matvec_kernel<Tin, 2, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha, xstride, ystride, jdev);
   } else {
     if (transpose)
-      matvec_kernel<Tin, 3, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+      matvec_kernel<Tin, 3, true><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha, xstride, ystride, jdev);
     else
-      matvec_kernel<Tin, 3, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha);
+      matvec_kernel<Tin, 3, false><<<grid, threads, 0, L.stream>>>(x, y, st.w, st.diag, g.m, g.np, n, tj, alpha, xstride, ystride, jdev);
   }
   return L.end(KC_MATVEC, bytes, flops);
 }
 
 template cudaError_t launch_matvec<double>(Launch&, const Grid&, int, const Stencil<double>&, double,
-                                           const double*, double*, bool);
+                                           const double*, double*, bool, size_t, size_t, const int*);
 template cudaError_t launch_matvec<float>(Launch&, const Grid&, int, const Stencil<double>&, double,
-                                          const float*, double*, bool);
+                                          const float*, double*, bool, size_t, size_t, const int*);
 
 }  // namespace pcopt

@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(256) tfft_forward_kernel(const double* __restr
     Tc a = Tc(0), b = Tc(0);
     if (s < ms) {
       const Tc d = dpow[j];
-      a = (Tc)v1[(int64_t)j * ms + s] / d;   // D^{-1} v1
-      b = (Tc)v2[(int64_t)j * ms + s] * d;   // D v2
+      a = cvt<Tc>(v1[(int64_t)j * ms + s]) / d;   // D^{-1} v1
+      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * d;   // D v2
     }
     z[bitrev(j, logn) * TS + c] = cmk<Tc>(a, b);
   }
@@ -129,8 +129,179 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
     const Tc d = dpow[j];
     const Tc wt1 = d * (y.x * inv_n);   // D ifft(hat w1)
     const Tc wt2 = (y.y * inv_n) / d;   // D^{-1} ifft(hat w2)
-    w1[(int64_t)j * ms + s] = (Tout)(wt1 - wt2);   // step 4: [[I, -I], [I, I]]
-    w2[(int64_t)j * ms + s] = (Tout)(wt1 + wt2);
+    w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);   // step 4: [[I, -I], [I, I]]
+    w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Four-step FFT in registers (n = N1 * N2 <= 1024): the kernels used in practice.
+// Forward X[k] = sum_j x[j] w^{jk}, w = exp(-2 pi i / n), j = j1 + N1 j2,
+// k = k2 + N2 k1:  (A) an N2-point DFT over j2 per j1, (B) the twiddle
+// w^{j1 k2}, (C) an N1-point DFT over j1 per k2.  The inverse uses the same
+// split with k = k1 + N1 k2, j = j2 + N2 j1 and conjugate twiddles.  Each of
+// the N1 thread rows of a CTA owns one j1 (then one k2) of COLS = 256/N1
+// spatial columns: two register FFTs and one shared-memory exchange instead of
+// log2(n) shared-memory radix-2 stages.
+template <int R>
+__device__ __forceinline__ constexpr int brev_ct(int i) {
+  int r = 0;
+  for (int b = 1, rb = R >> 1; b < R; b <<= 1, rb >>= 1)
+    if (i & b) r |= rb;
+  return r;
+}
+
+// in-place R-point DFT of registers x (DIT, radix 2); twiddles exp(-+2 pi i q/R)
+// are tw[q * tstride] from the full-circle table of length n = R * tstride
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void reg_fft(C (&x)[R], const C* __restrict__ tw, int tstride) {
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = brev_ct<R>(i);
+    if (j > i) {
+      const C t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < R; half <<= 1) {
+#pragma unroll
+    for (int g = 0; g < R; g += 2 * half) {
+#pragma unroll
+      for (int p = 0; p < half; ++p) {
+        const C a = x[g + p];
+        C b = x[g + p + half];
+        if (p != 0) {
+          C w = tw[p * (R / (2 * half)) * tstride];
+          if (INV) w.y = -w.y;
+          b = cmul(w, b);
+        }
+        x[g + p] = a + b;
+        x[g + p + half] = a - b;
+      }
+    }
+  }
+}
+
+template <typename Tin, typename Tc, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
+                                                            const Tc* __restrict__ dinv,
+                                                            const typename Cx<Tc>::t* __restrict__ tw,
+                                                            typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
+                                                            size_t vstride, const int* __restrict__ jdev) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;  // 0..N1-1
+  const int64_t s = (int64_t)blockIdx.x * COLS + c;
+  const bool valid = s < ms;
+  if (jdev) v += (size_t)(*jdev) * vstride;  // input = basis vector j (device-resident index)
+  const Tin* v1 = v;
+  const Tin* v2 = v + (int64_t)n * ms;
+  // (A) rows j = r + N1 j2: z = D^{-1} v1 + i D v2, N2-point DFT over j2
+  C x[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    const int j = r + N1 * j2;
+    Tc a = Tc(0), b = Tc(0);
+    if (valid) {
+      a = cvt<Tc>(v1[(int64_t)j * ms + s]) * dinv[j];
+      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * dpow[j];
+    }
+    x[j2] = cmk<Tc>(a, b);
+  }
+  reg_fft<N2, false>(x, tw, N1);
+  // (B) twiddle w^{j1 k2}, stored as Y[k2][j1]
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const C y = (k2 == 0 || r == 0) ? x[k2] : cmul(tw[r * k2], x[k2]);
+    sm[(k2 * N1 + r) * COLS + c] = y;
+  }
+  __syncthreads();
+  // (C) row k2 = r (< N2): N1-point DFT over j1, X[k2 + N2 k1]
+  C y[N1];
+  if (r < N2) {
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) y[j1] = sm[(r * N1 + j1) * COLS + c];
+  }
+  __syncthreads();
+  if (r < N2) {
+    reg_fft<N1, false>(y, tw, N2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) sm[(r + N2 * k1) * COLS + c] = y[k1];
+  }
+  __syncthreads();
+  if (!valid) return;
+  // Hermitian split of the two-for-one spectrum, k = 0..n/2
+  const Tc hf = Tc(0.5);
+  for (int k = r; k <= n / 2; k += N1) {
+    const C Z = sm[k * COLS + c];
+    const C W = sm[((n - k) & (n - 1)) * COLS + c];
+    spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
+    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+  }
+}
+
+template <typename Tc, typename TU, typename Tout, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+                                                            const Tc* __restrict__ dinv,
+                                                            const typename Cx<Tc>::t* __restrict__ tw,
+                                                            Tout* __restrict__ w, int64_t ms, size_t wstride,
+                                                            const int* __restrict__ jdev) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;
+  const int64_t s = (int64_t)blockIdx.x * COLS + c;
+  const bool valid = s < ms;
+  if (jdev) w += (size_t)(*jdev) * wstride;  // output = basis vector j
+  // Y[k] = hat w1[k] + i hat w2[k] for all k from the half spectrum
+  for (int k = r; k <= n / 2; k += N1) {
+    C sa = czero<Tc>(), sb = czero<Tc>();
+    if (valid) {
+      sa = ldc(spec, (int64_t)(2 * k) * ms + s);
+      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
+    }
+    sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
+    if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+  }
+  __syncthreads();
+  // (A) row k1 = r: N2-point inverse DFT over k2 of Y[k1 + N1 k2], twiddle w^{-k1 j2}
+  C x[N2];
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) x[k2] = sm[(r + N1 * k2) * COLS + c];
+  __syncthreads();
+  reg_fft<N2, true>(x, tw, N1);
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    C t = tw[r * j2];
+    t.y = -t.y;
+    sm[(j2 * N1 + r) * COLS + c] = (j2 == 0 || r == 0) ? x[j2] : cmul(t, x[j2]);
+  }
+  __syncthreads();
+  if (r >= N2 || !valid) return;
+  // (C) row j2 = r: N1-point inverse DFT over k1 -> x[j2 + N2 j1]
+  C y[N1];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) y[k1] = sm[(r * N1 + k1) * COLS + c];
+  reg_fft<N1, true>(y, tw, N2);
+  const Tc inv_n = Tc(1) / Tc(n);
+  Tout* w1 = w;
+  Tout* w2 = w + (int64_t)n * ms;
+#pragma unroll
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int j = r + N2 * j1;
+    const Tc wt1 = dpow[j] * (y[j1].x * inv_n);  // D ifft(hat w1)
+    const Tc wt2 = dinv[j] * (y[j1].y * inv_n);  // D^{-1} ifft(hat w2)
+    w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);  // step 4: [[I, -I], [I, I]]
+    w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
   }
 }
 
@@ -151,9 +322,98 @@ int ilog2(int n) {
 
 }  // namespace
 
+template <typename Tin, typename Tc, int N1, int N2>
+cudaError_t fwd4(Launch& L, int64_t ms, const Tin* v, const Tc* dpow, const Tc* dinv, const typename Cx<Tc>::t* tw,
+                 typename Cx<Tc>::t* spec, size_t vstride, const int* jdev) {
+  constexpr int COLS = 256 / N1;
+  const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
+  cudaError_t e = cudaFuncSetAttribute(tfft4_forward_kernel<Tin, Tc, N1, N2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tfft4_forward_kernel<Tin, Tc, N1, N2><<<(unsigned)((ms + COLS - 1) / COLS), 256, smem, L.stream>>>(v, dpow, dinv,
+                                                                                                    tw, spec, ms,
+                                                                                                    vstride, jdev);
+  return cudaGetLastError();
+}
+
+template <typename Tc, typename TU, typename Tout, int N1, int N2>
+cudaError_t inv4(Launch& L, int64_t ms, const TU* spec, const Tc* dpow, const Tc* dinv, const typename Cx<Tc>::t* tw,
+                 Tout* w, size_t wstride, const int* jdev) {
+  constexpr int COLS = 256 / N1;
+  const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
+  cudaError_t e = cudaFuncSetAttribute(tfft4_inverse_kernel<Tc, TU, Tout, N1, N2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tfft4_inverse_kernel<Tc, TU, Tout, N1, N2><<<(unsigned)((ms + COLS - 1) / COLS), 256, smem, L.stream>>>(
+      spec, dpow, dinv, tw, w, ms, wstride, jdev);
+  return cudaGetLastError();
+}
+
+// largest n handled by the four-step kernels (register pressure bounds FP64)
 template <typename Tc>
-cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow,
-                                const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec) {
+constexpr int four_step_max() {
+  return sizeof(Tc) == 4 ? 1024 : 256;
+}
+
+template <typename Tin, typename Tc>
+cudaError_t fwd4_dispatch(Launch& L, int64_t ms, int n, const Tin* v, const Tc* dpow, const Tc* dinv,
+                          const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride, const int* jdev) {
+  switch (n) {
+    case 1: return fwd4<Tin, Tc, 1, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 2: return fwd4<Tin, Tc, 2, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 4: return fwd4<Tin, Tc, 2, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 8: return fwd4<Tin, Tc, 4, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 16: return fwd4<Tin, Tc, 4, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 32: return fwd4<Tin, Tc, 8, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 64: return fwd4<Tin, Tc, 8, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 128: return fwd4<Tin, Tc, 16, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 256: return fwd4<Tin, Tc, 16, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 512:
+      if constexpr (sizeof(Tc) == 4) return fwd4<Tin, Tc, 32, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+      break;
+    case 1024:
+      if constexpr (sizeof(Tc) == 4) return fwd4<Tin, Tc, 32, 32>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename Tc, typename TU, typename Tout>
+cudaError_t inv4_dispatch(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
+                          const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev) {
+  switch (n) {
+    case 1: return inv4<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 2: return inv4<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 4: return inv4<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 8: return inv4<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 16: return inv4<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 32: return inv4<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 64: return inv4<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 128: return inv4<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 256: return inv4<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 512:
+      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+      break;
+    case 1024:
+      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename Tc>
+cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow, const Tc* dinv,
+                                const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride,
+                                const int* jdev) {
+  if (jdev && n > four_step_max<Tc>()) return cudaErrorNotSupported;
+  if (n <= four_step_max<Tc>()) {
+    const int nf = n / 2 + 1;
+    const double bytes = 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
+    const double flops = (double)ms * (5.0 * n * ilog2(n) + 2.0 * n);
+    L.begin(KC_TFFT_FWD);
+    fwd4_dispatch<double, Tc>(L, ms, n, v, dpow, dinv, tw, spec, vstride, jdev);
+    return L.end(KC_TFFT_FWD, bytes, flops);
+  }
   const int TS = pick_ts<Tc>(n);
   const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
   cudaError_t e = cudaFuncSetAttribute(tfft_forward_kernel<Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -168,8 +428,17 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
 }
 
 template <typename Tc, typename TU, typename Tout>
-cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow,
-                                const typename Cx<Tc>::t* tw, Tout* w) {
+cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
+                                const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev) {
+  if (jdev && n > four_step_max<Tc>()) return cudaErrorNotSupported;
+  if (n <= four_step_max<Tc>()) {
+    const int nf = n / 2 + 1;
+    const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout);
+    const double flops = (double)ms * (5.0 * n * ilog2(n) + 4.0 * n);
+    L.begin(KC_TFFT_INV);
+    inv4_dispatch<Tc, TU, Tout>(L, ms, n, spec, dpow, dinv, tw, w, wstride, jdev);
+    return L.end(KC_TFFT_INV, bytes, flops);
+  }
   const int TS = pick_ts<Tc>(n);
   const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
   cudaError_t e =
@@ -184,20 +453,18 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
   return L.end(KC_TFFT_INV, bytes, flops);
 }
 
-template cudaError_t launch_tfft_forward<double>(Launch&, int64_t, int, const double*, const double*, const double2*,
-                                                 double2*);
-template cudaError_t launch_tfft_forward<float>(Launch&, int64_t, int, const double*, const float*, const float2*,
-                                                float2*);
-template cudaError_t launch_tfft_inverse<double, double2, double>(Launch&, int64_t, int, const double2*,
-                                                                  const double*, const double2*, double*);
-template cudaError_t launch_tfft_inverse<float, float2, double>(Launch&, int64_t, int, const float2*, const float*,
-                                                                const float2*, double*);
-template cudaError_t launch_tfft_inverse<float, float2, float>(Launch&, int64_t, int, const float2*, const float*,
-                                                               const float2*, float*);
-template cudaError_t launch_tfft_inverse<float, __nv_bfloat162, double>(Launch&, int64_t, int,
-                                                                        const __nv_bfloat162*, const float*,
-                                                                        const float2*, double*);
-template cudaError_t launch_tfft_inverse<float, __nv_bfloat162, float>(Launch&, int64_t, int, const __nv_bfloat162*,
-                                                                       const float*, const float2*, float*);
+template cudaError_t launch_tfft_forward<double>(Launch&, int64_t, int, const double*, const double*, const double*,
+                                                 const double2*, double2*, size_t, const int*);
+template cudaError_t launch_tfft_forward<float>(Launch&, int64_t, int, const double*, const float*, const float*,
+                                                const float2*, float2*, size_t, const int*);
+#define PCOPT_INV(Tc, TU, Tout)                                                                                  \
+  template cudaError_t launch_tfft_inverse<Tc, TU, Tout>(Launch&, int64_t, int, const TU*, const Tc*, const Tc*, \
+                                                         const Cx<Tc>::t*, Tout*, size_t, const int*);
+PCOPT_INV(double, double2, double)
+PCOPT_INV(float, float2, double)
+PCOPT_INV(float, float2, float)
+PCOPT_INV(float, __nv_bfloat162, double)
+PCOPT_INV(float, __nv_bfloat162, float)
+#undef PCOPT_INV
 
 }  // namespace pcopt

@@ -125,6 +125,19 @@ class Solver:
             capi.check(st)
         return x, it.value, rr.value
 
+    def solve_graph(self, b, x=None, rtol=1e-8, maxit=None, raise_on_nonconv=True):
+        """The same FGMRES solve (zero initial guess) as one CUDA-graph launch with
+        device-side convergence control; returns (x, iterations, relative residual)."""
+        self._vec(b)
+        x = torch.empty_like(b) if x is None else x
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = self.lib.pc_gmres_solve_graph(self.h, _ptr(b), _ptr(x), rtol, maxit or self.max_iter,
+                                           ctypes.byref(it), ctypes.byref(rr), _stream())
+        if st != capi.PC_ERR_NOT_CONVERGED or raise_on_nonconv:
+            capi.check(st)
+        return x, it.value, rr.value
+
     def solve_host(self, b_host, x_host=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
         """Solve from a HOST right-hand side: copy b to the device, run GMRES,
         copy x back into ``x_host`` (pinned CPU tensors give asynchronous copies).
@@ -174,3 +187,44 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.pc_launch_count(self.h))
+
+
+class Batch:
+    """Independent problems solved by one graph launch (pc_batch_*).  ``solvers``
+    are distinct Solver objects; ``bs`` their right-hand sides; ``xs`` receive the
+    solutions (allocated if None).  Keep the solvers and tensors alive while the
+    batch exists."""
+
+    def __init__(self, solvers, bs, xs=None, rtol=1e-8, maxit=None):
+        self.lib = capi.load()
+        self.solvers = list(solvers)
+        self.bs = list(bs)
+        self.xs = [torch.empty_like(b) for b in self.bs] if xs is None else list(xs)
+        n = len(self.solvers)
+        hs = (ctypes.c_void_p * n)(*[s.h for s in self.solvers])
+        bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in self.bs])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in self.xs])
+        maxit = maxit or min(s.max_iter for s in self.solvers)
+        bt = ctypes.c_void_p()
+        capi.check(self.lib.pc_batch_create(hs, n, bp, xp, rtol, maxit, ctypes.byref(bt)))
+        self.bt = bt
+
+    def solve(self, raise_on_nonconv=True):
+        n = len(self.solvers)
+        it = (ctypes.c_int * n)()
+        rr = (ctypes.c_double * n)()
+        st = self.lib.pc_batch_solve(self.bt, it, rr, _stream())
+        if st != capi.PC_ERR_NOT_CONVERGED or raise_on_nonconv:
+            capi.check(st)
+        return list(it), list(rr)
+
+    def close(self):
+        if getattr(self, "bt", None):
+            self.lib.pc_batch_destroy(self.bt)
+            self.bt = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

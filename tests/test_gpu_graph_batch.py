@@ -1,0 +1,83 @@
+"""Graph-captured solves (device-controlled WHILE loop) and batched solves of
+uneven problems in one graph launch, against the host-driven solve and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import krylov as okr, precond as opc, system as osy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_22686_gb300 import build
+    build.build()
+
+
+def _make(prob, precision, max_iter=60):
+    from paper_2410_22686_gb300 import Solver
+    sol = Solver(2, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg",
+                 precision=precision, max_iter=max_iter)
+    b = sol.build_rhs(torch.from_numpy(prob.f).cuda(), torch.from_numpy(prob.g).cuda(),
+                      torch.from_numpy(prob.y0).cuda())
+    return sol, b
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_solve_equals_host_driven_solve(precision):
+    prob = S.variable_2d_problem(gamma=1e-4, m1=63, n=64)
+    sol, b = _make(prob, precision)
+    x_ref, it_ref, rr_ref = sol.solve(b, rtol=1e-10)
+    for _ in range(2):  # second call replays the cached graph
+        x, it, rr = sol.solve_graph(b, rtol=1e-10)
+        assert it == it_ref
+        assert rr <= 1e-10
+        assert (x - x_ref).norm().item() <= 1e-12 * x_ref.norm().item()
+    sol.close()
+
+
+def test_batch_of_uneven_problems_matches_individual_solves_and_oracle():
+    from paper_2410_22686_gb300 import Batch
+    probs = [S.variable_2d_problem(gamma=1e-2, m1=15, n=16), S.variable_2d_problem(gamma=1e-6, m1=31, n=64),
+             S.variable_2d_problem(gamma=1e-4, m1=63, n=32), S.gradient_problem(m1=31, n=16, gamma=1e-8)]
+    precs = ["fp64", "fp32", "fp64", "bf16s"]
+    made = [_make(p, q, max_iter=80) for p, q in zip(probs, precs)]
+    sols, bs = [m[0] for m in made], [m[1] for m in made]
+    singles = [s.solve(b, rtol=1e-10) for s, b in zip(sols, bs)]
+    batch = Batch(sols, bs, rtol=1e-10, maxit=80)
+    for _ in range(2):
+        iters, rel = batch.solve()
+        for k in range(len(probs)):
+            x_ref, it_ref, _ = singles[k]
+            assert iters[k] == it_ref
+            assert rel[k] <= 1e-10
+            assert (batch.xs[k] - x_ref).norm().item() <= 1e-12 * x_ref.norm().item()
+    # the FP64 members against the oracle
+    for k in (0, 2):
+        p = probs[k]
+        tau, alpha = p.tau, osy.alpha_weight(p.T, p.n, p.gamma)
+        bo = osy.build_rhs(p.f, p.g, p.y0, tau, p.gamma)
+        mg = opc.MGSpatialSolver(p.a_nodes, tau)
+        ref = okr.gmres(lambda v: osy.apply_A(v, p.a_nodes, tau, alpha),
+                        lambda v: opc.apply_Peps_inv(v, p.n, alpha, p.eps, mg), bo, rtol=1e-13, maxit=200)
+        xg = batch.xs[k].cpu().numpy()
+        assert np.linalg.norm(xg - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    batch.close()
+    for s in sols:
+        s.close()
+
+
+def test_graph_solve_zero_rhs_and_maxit():
+    from paper_2410_22686_gb300 import capi
+    prob = S.variable_2d_problem(gamma=1e-4, m1=15, n=16)
+    sol, b = _make(prob, "fp32")
+    x, it, rr = sol.solve_graph(torch.zeros_like(b), rtol=1e-8)
+    assert it == 0 and float(x.abs().max()) == 0.0
+    x, it, rr = sol.solve_graph(b, rtol=1e-14, maxit=3, raise_on_nonconv=False)
+    assert it == 3
+    with pytest.raises(capi.PCError) as ei:
+        sol.solve_graph(b, rtol=1e-14, maxit=3)
+    assert ei.value.status == capi.PC_ERR_NOT_CONVERGED
+    sol.close()
