@@ -111,6 +111,13 @@ int pc_destroy(pc_handle* h);
  * x, y: device, 2*n*ms FP64, must not overlap. */
 int pc_matvec(pc_handle* h, const double* x, double* y, void* stream);
 
+/* y = A x for an FP32 vector x (Eq. matrix_A): the product flexible GMRES forms
+ * with its FP32 basis Z.  Evaluated in double-float arithmetic on the FP32 units
+ * (each FP64 coefficient split into two floats, FMA error terms, TwoSum
+ * accumulation); relative error of order 2^-46 of the largest term; FP64 output.
+ * x: device, 2*n*ms FP32; y: device, 2*n*ms FP64. */
+int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream);
+
 /* y = A^T x  (block transpose of Eq. matrix_A; equals S A S with S = diag(I, -I)).
  * x, y: device, 2*n*ms FP64, must not overlap. */
 int pc_matvec_transpose(pc_handle* h, const double* x, double* y, void* stream);

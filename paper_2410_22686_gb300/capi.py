@@ -53,6 +53,7 @@ _SIGNATURES = {
     "pc_set_coefficient": (_i, [_vp, _vp, _vp]),
     "pc_matvec": (_i, [_vp, _dp, _dp, _vp]),
     "pc_matvec_transpose": (_i, [_vp, _dp, _dp, _vp]),
+    "pc_matvec_f32": (_i, [_vp, _vp, _dp, _vp]),
     "pc_apply_precond": (_i, [_vp, _dp, _dp, _vp]),
     "pc_build_rhs": (_i, [_vp, _dp, _dp, _dp, _dp, _vp]),
     "pc_gmres_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),

@@ -51,7 +51,7 @@ const char* kernel_class_name(int kc) {
                                         "arnoldi_dot",   "arnoldi_update_norm", "reduce_partials",
                                         "normalize",     "givens",       "x_update",
                                         "axpby",         "build_rhs",    "grad_stencil",
-                                        "arnoldi_reorth"};
+                                        "arnoldi_reorth", "mg_coarse_cycle"};
   return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
 }
 
@@ -160,6 +160,12 @@ struct pc_handle {
   double a_const = 1.0;
 
   std::vector<LevelBuf> lv;
+  int coarse_l0 = 0;                 // first level run by the fused coarse-cycle kernel
+  float2* wdf = nullptr;             // level-0 face weights and diagonal as (hi, lo) float pairs
+  float2* ddf = nullptr;
+  float2 alpha_df{0.f, 0.f};
+  CoarseLevels<float> coarse32{};
+  CoarseLevels<double> coarse64{};
   // time FFT tables
   double* dpow64 = nullptr;  // eps^{j/n}
   float* dpow32 = nullptr;
@@ -450,6 +456,46 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       if (l + 1 < mlev.size() && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb))) goto fail_out;
       h->lv.push_back(L);
     }
+    // double-float copies of the level-0 stencil for the inner matvec of flexible GMRES
+    {
+      auto split = [](const std::vector<double>& v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+          const float hi = (float)v[i];
+          o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+        return o;
+      };
+      const std::vector<float2> wsp = split(ws[0]), dsp = split(ds[0]);
+      if ((rc = dev_alloc_t(h, &h->wdf, wsp.size()))) goto fail_out;
+      if ((rc = dev_alloc_t(h, &h->ddf, dsp.size()))) goto fail_out;
+      cudaError_t ce = cudaMemcpyAsync(h->wdf, wsp.data(), wsp.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(h->ddf, dsp.data(), dsp.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) {
+        rc = cuda_fail(ce, "pc_setup: double-float stencil");
+        goto fail_out;
+      }
+      const float ah = (float)h->alpha;
+      h->alpha_df = make_float2(ah, (float)(h->alpha - (double)ah));
+    }
+    // the fused coarse cycle takes every level from the first with m <= 31 (2D) / 15 (3D)
+    const int mthr = dim == 2 ? 31 : 15;
+    int l0 = (int)h->lv.size() - 1;
+    while (l0 > 0 && h->lv[l0 - 1].m <= mthr) --l0;
+    if ((int)h->lv.size() - l0 > kMaxCoarseLevels) l0 = (int)h->lv.size() - kMaxCoarseLevels;
+    h->coarse_l0 = l0;
+    h->coarse32.count = h->coarse64.count = (int)h->lv.size() - l0;
+    for (int l = l0; l < (int)h->lv.size(); ++l) {
+      const int q = l - l0;
+      h->coarse32.m[q] = h->coarse64.m[q] = h->lv[l].m;
+      h->coarse32.np[q] = h->coarse64.np[q] = h->lv[l].np;
+      h->coarse32.w[q] = h->lv[l].w32;
+      h->coarse32.diag[q] = h->lv[l].d32;
+      h->coarse64.w[q] = h->lv[l].w64;
+      h->coarse64.diag[q] = h->lv[l].d64;
+    }
   }
   // ---- time FFT tables
   {
@@ -582,6 +628,20 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
     if ((rc = refill(h->lv[l].w32, ws[l], st, s32))) return rc;
     if ((rc = refill(h->lv[l].d32, ds[l], st, s32))) return rc;
   }
+  {
+    std::vector<float2> wsp(ws[0].size()), dsp(ds[0].size());
+    for (size_t i = 0; i < wsp.size(); ++i) {
+      const float hi = (float)ws[0][i];
+      wsp[i] = make_float2(hi, (float)(ws[0][i] - (double)hi));
+    }
+    for (size_t i = 0; i < dsp.size(); ++i) {
+      const float hi = (float)ds[0][i];
+      dsp[i] = make_float2(hi, (float)(ds[0][i] - (double)hi));
+    }
+    PC_CUDA(cudaMemcpyAsync(h->wdf, wsp.data(), wsp.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(h->ddf, dsp.data(), dsp.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+  }
   if ((rc = refill(h->a_int, interior_of(a, m1, dim), st, s64))) return rc;
   h->a_const = a[0];
   if (h->spatial == PC_SPATIAL_FST) {
@@ -652,6 +712,13 @@ struct Tables<float> {
   static const float* lamK(const pc_handle* h) { return h->lamK32; }
 };
 
+template <typename Tc>
+static const CoarseLevels<Tc>& coarse_of(const pc_handle* h);
+template <>
+const CoarseLevels<float>& coarse_of<float>(const pc_handle* h) { return h->coarse32; }
+template <>
+const CoarseLevels<double>& coarse_of<double>(const pc_handle* h) { return h->coarse64; }
+
 // step 2: every plane of lv[0].r solved into lv[0].u (iterates stored as TU)
 template <typename Tc, typename TU>
 static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
@@ -677,9 +744,10 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
       return cudaSuccess;
     }
   }
-  // multigrid V(1,0)
+  // multigrid V(1,0): per-level kernels on the fine levels, one fused kernel for the rest
   const int nl = (int)h->lv.size();
-  for (int l = 0; l + 1 < nl; ++l) {
+  const int l0 = h->coarse_l0;
+  for (int l = 0; l < l0; ++l) {
     const LevelBuf& Lb = h->lv[l];
     Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
     const Grid g = grid_of(h, l);
@@ -689,10 +757,12 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
       return e;
   }
   {
-    const LevelBuf& Lc = h->lv[nl - 1];
-    if ((e = launch_mg_coarsest<Tc, TU>(L, P, lvd<Tc>(Lc), sig, (const C*)Lc.r, (TU*)Lc.u)) != cudaSuccess) return e;
+    const CoarseLevels<Tc>& cl = coarse_of<Tc>(h);
+    if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r, (TU*)h->lv[l0].u)) !=
+        cudaSuccess)
+      return e;
   }
-  for (int l = nl - 2; l >= 0; --l) {
+  for (int l = l0 - 1; l >= 0; --l) {
     if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
         cudaSuccess)
       return e;
@@ -742,6 +812,13 @@ extern "C" int pc_matvec(pc_handle* h, const double* x, double* y, void* stream)
   Launch L{(cudaStream_t)stream, &h->prof};
   cudaError_t e = matvec_any(h, L, x, false, y, false);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec");
+}
+
+extern "C" int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec_f32: null argument");
+  Launch L{(cudaStream_t)stream, &h->prof};
+  cudaError_t e = launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, x, y);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec_f32");
 }
 
 extern "C" int pc_matvec_transpose(pc_handle* h, const double* x, double* y, void* stream) {
@@ -870,7 +947,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
         GM_CUDA(precond32<float>(h, L, vj, zj));
-        GM_CUDA(matvec_any(h, L, zj, true, vn, false));
+        GM_CUDA(launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, zj, vn));
       } else {
         double* zj = (double*)h->Z + (size_t)j * U;
         GM_CUDA(precond_t<double, double2, double>(h, L, vj, zj));
@@ -1000,7 +1077,7 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   if (h->fp32) {
     float* Z = (float*)h->Z;
     GR_CUDA(precond32<float>(h, L, h->V, Z, U, j));
-    GR_CUDA(launch_matvec<float>(L, g, h->n, st, h->alpha, Z, h->V, false, U, U, j));
+    GR_CUDA(launch_matvec_df(L, g, h->n, h->wdf, h->ddf, h->alpha_df, Z, h->V, U, U, j));
   } else {
     double* Z = (double*)h->Z;
     GR_CUDA((precond_t<double, double2, double>(h, L, h->V, Z, U, j)));

@@ -132,6 +132,7 @@ enum KernelClass {
   KC_RHS,
   KC_GRAD,
   KC_REORTH,  // gated re-orthogonalisation passes (bytes booked only when they ran)
+  KC_MG_COARSE,
   KC_COUNT
 };
 const char* kernel_class_name(int kc);
@@ -193,6 +194,12 @@ cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>
                           const Tin* x, double* y, bool transpose, size_t xstride = 0, size_t ystride = 0,
                           const int* jdev = nullptr);
 
+// y = A x for an FP32 x in double-float arithmetic (FP64 output): the inner matvec
+// of flexible GMRES.  w/diag hold tau a_f / h^2 and its sum as (hi, lo) float pairs.
+cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, const float2* diag, float2 alpha,
+                             const float* x, double* y, size_t xstride = 0, size_t ystride = 0,
+                             const int* jdev = nullptr);
+
 // forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
 // dpow[j] = eps^{j/n}, dinv[j] = eps^{-j/n}, tw[k] = exp(-2 pi i k/n) for k = 0..n-1
 // With jdev != nullptr the input is v + (*jdev) * vstride (device-resident Arnoldi index).
@@ -228,6 +235,23 @@ cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* e
 template <typename Tc, typename TU>
 cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const typename Cx<Tc>::t* sigma,
                                const typename Cx<Tc>::t* r, TU* u);
+
+// Coarse part of the multigrid cycle run by one kernel (levels l0..last):
+// sizes and per-level stencils, passed by value.
+constexpr int kMaxCoarseLevels = 8;
+template <typename T>
+struct CoarseLevels {
+  int count;
+  int m[kMaxCoarseLevels];
+  int64_t np[kMaxCoarseLevels];
+  const T* w[kMaxCoarseLevels];
+  const T* diag[kMaxCoarseLevels];
+};
+template <typename Tc, typename TU>
+size_t mg_coarse_cycle_smem(const CoarseLevels<Tc>& lv);
+template <typename Tc, typename TU>
+cudaError_t launch_mg_coarse_cycle(Launch& L, int dim, int planes, const CoarseLevels<Tc>& lv,
+                                   const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r0, TU* u0);
 
 // Krylov (FP64).  Device scalars of one Arnoldi step.
 struct ArnoldiScalars {

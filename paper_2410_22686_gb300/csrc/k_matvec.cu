@@ -131,3 +131,138 @@ template cudaError_t launch_matvec<float>(Launch&, const Grid&, int, const Stenc
                                           const float*, double*, bool, size_t, size_t, const int*);
 
 }  // namespace pcopt
+
+// ---------------------------------------------------------------------------
+// The same product for an FP32 input z (the flexible-GMRES basis Z), evaluated in
+// double-float arithmetic on the FP32 units: every FP64 coefficient c is held as
+// c_hi + c_lo (two floats), c*z is formed exactly up to c_lo*z by an FMA error
+// term (p = c_hi z, e = fma(c_hi, z, -p)), terms are added with Knuth's TwoSum,
+// and only the final hi + lo becomes an FP64 value (one FP64 addition per output).
+// The relative error is of order 2^-46 of the largest term, far below what the
+// Arnoldi relation needs, while GB300's FP64 unit (1/57 of the FP32 rate) would
+// otherwise bound this kernel.
+namespace pcopt {
+namespace {
+
+struct DF {
+  float hi, lo;
+};
+// a + b exactly as hi + err (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+}
+// accumulate the exact float x into (acc.hi, acc.lo)
+__device__ __forceinline__ void df_add_f(DF& acc, float x) {
+  float s, e;
+  two_sum(acc.hi, x, s, e);
+  acc.hi = s;
+  acc.lo += e;
+}
+// accumulate c * x (c = c.hi + c.lo, x exact float)
+__device__ __forceinline__ void df_add_prod(DF& acc, float2 c, float x) {
+  const float p = c.x * x;
+  const float pe = fmaf(c.x, x, -p) + c.y * x;
+  float s, e;
+  two_sum(acc.hi, p, s, e);
+  acc.hi = s;
+  acc.lo += e + pe;
+}
+__device__ __forceinline__ double df_to_f64(const DF& a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+
+template <int DIM>
+__global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict__ x, double* __restrict__ y,
+                                                        const float2* __restrict__ w, const float2* __restrict__ dg,
+                                                        float2 alpha, int m, int64_t ms, int n, int tj,
+                                                        size_t xstride, size_t ystride, const int* __restrict__ jdev) {
+  if (jdev) {
+    x += (size_t)(*jdev) * xstride;
+    y += (size_t)(*jdev + 1) * ystride;
+  }
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ms) return;
+  const int j0 = blockIdx.y * tj;
+  const int j1 = min(n, j0 + tj);
+  if (j0 >= n) return;
+  const int i1 = (int)(s % m);
+  const int64_t r = s / m;
+  const int i2 = (int)(DIM == 2 ? r : r % m);
+  const int i3 = (int)(DIM == 3 ? r / m : 0);
+  int64_t off[2 * DIM];
+  bool ex[2 * DIM];
+  float2 wv[2 * DIM];
+  const int64_t mm = (int64_t)m * m;
+  off[0] = -1;
+  ex[0] = i1 > 0;
+  off[1] = 1;
+  ex[1] = i1 < m - 1;
+  off[2] = -(int64_t)m;
+  ex[2] = i2 > 0;
+  off[3] = m;
+  ex[3] = i2 < m - 1;
+  if (DIM == 3) {
+    off[4] = -mm;
+    ex[4] = i3 > 0;
+    off[5] = mm;
+    ex[5] = i3 < m - 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * DIM; ++k) {
+    const float2 c = w[(int64_t)k * ms + s];
+    wv[k] = make_float2(-c.x, -c.y);  // off-diagonal entries of tau K are -w
+  }
+  const float2 d = dg[s];
+  const float* x1 = x;
+  const float* x2 = x + (int64_t)n * ms;
+  double* y1 = y;
+  double* y2 = y + (int64_t)n * ms;
+  float x1prev = (j0 > 0) ? x1[(int64_t)(j0 - 1) * ms + s] : 0.0f;
+  float x2c = x2[(int64_t)j0 * ms + s];
+  for (int j = j0; j < j1; ++j) {
+    const int64_t idx = (int64_t)j * ms + s;
+    const float x1c = x1[idx];
+    const float x2n = (j + 1 < n) ? x2[idx + ms] : 0.0f;
+    // y1 = alpha x1 + x2_j - x2_{j+1} + tau K x2_j
+    DF a{0.0f, 0.0f};
+    df_add_prod(a, d, x2c);
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k)
+      if (ex[k]) df_add_prod(a, wv[k], __ldg(x2 + idx + off[k]));
+    df_add_f(a, x2c);
+    df_add_f(a, -x2n);
+    df_add_prod(a, alpha, x1c);
+    // y2 = alpha x2 - (x1_j - x1_{j-1} + tau K x1_j)
+    DF b{0.0f, 0.0f};
+    df_add_prod(b, make_float2(-d.x, -d.y), x1c);
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k)
+      if (ex[k]) df_add_prod(b, make_float2(-wv[k].x, -wv[k].y), __ldg(x1 + idx + off[k]));
+    df_add_f(b, -x1c);
+    df_add_f(b, x1prev);
+    df_add_prod(b, alpha, x2c);
+    y1[idx] = df_to_f64(a);
+    y2[idx] = df_to_f64(b);
+    x1prev = x1c;
+    x2c = x2n;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, const float2* diag, float2 alpha,
+                             const float* x, double* y, size_t xstride, size_t ystride, const int* jdev) {
+  const int threads = 256;
+  const int tj = n < 32 ? n : 32;
+  dim3 grid((unsigned)((g.np + threads - 1) / threads), (unsigned)((n + tj - 1) / tj));
+  const double U = 2.0 * (double)n * (double)g.np;
+  const double bytes = U * (sizeof(float) + sizeof(double)) + (2.0 * g.dim + 1) * g.np * 8.0;
+  L.begin(KC_MATVEC);
+  if (g.dim == 2)
+    matvec_df_kernel<2><<<grid, threads, 0, L.stream>>>(x, y, w, diag, alpha, g.m, g.np, n, tj, xstride, ystride, jdev);
+  else
+    matvec_df_kernel<3><<<grid, threads, 0, L.stream>>>(x, y, w, diag, alpha, g.m, g.np, n, tj, xstride, ystride, jdev);
+  return L.end(KC_MATVEC, jdev ? 0.0 : bytes, jdev ? 0.0 : U * (4.0 * g.dim + 5.0));
+}
+
+}  // namespace pcopt

@@ -403,3 +403,222 @@ PCOPT_INST_MG(float, __nv_bfloat162)
 #undef PCOPT_INST_MG
 
 }  // namespace pcopt
+
+// ---------------------------------------------------------------------------
+// Coarse part of the V(1,0) cycle in one kernel.  From level l0 (the first one
+// with few enough points) down to the one-point level and back, the cycle is
+// launch- and latency-bound when run level by level; here one CTA owns one
+// spectral plane and keeps every coarse level in shared memory.  The
+// arithmetic is that of the per-level kernels above: red-black sweep from zero,
+// residual, full weighting, exact one-point solve, linear prolongation.
+// ---------------------------------------------------------------------------
+namespace pcopt {
+namespace {
+
+template <int DIM>
+__device__ __forceinline__ int64_t lin(int i1, int i2, int i3, int m) {
+  return DIM == 2 ? (int64_t)i2 * m + i1 : ((int64_t)i3 * m + i2) * m + i1;
+}
+
+template <typename Tc, typename TU, int DIM>
+__global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels<Tc> lv,
+                                                              const typename Cx<Tc>::t* __restrict__ r0,
+                                                              TU* __restrict__ u0,
+                                                              const typename Cx<Tc>::t* __restrict__ sigma) {
+  typedef typename Cx<Tc>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x;
+  const C sig = sigma[p];
+  // carve: per level r, u (as TU), res
+  C* rl[kMaxCoarseLevels];
+  TU* ul[kMaxCoarseLevels];
+  C* resl[kMaxCoarseLevels];
+  {
+    unsigned char* q = smem_raw;
+    for (int l = 0; l < lv.count; ++l) {
+      const int64_t np = lv.np[l];
+      rl[l] = reinterpret_cast<C*>(q);
+      q += np * sizeof(C);
+      resl[l] = reinterpret_cast<C*>(q);
+      q += np * sizeof(C);
+      ul[l] = reinterpret_cast<TU*>(q);
+      q += ((np * sizeof(TU) + 15) / 16) * 16;
+    }
+  }
+  // level 0 of the coarse part comes from global memory
+  for (int64_t s = threadIdx.x; s < lv.np[0]; s += blockDim.x) rl[0][s] = r0[(int64_t)p * lv.np[0] + s];
+  __syncthreads();
+  const Tc wt[3] = {Tc(0.25), Tc(0.5), Tc(0.25)};
+  for (int l = 0; l + 1 < lv.count; ++l) {
+    const int m = lv.m[l];
+    const int64_t np = lv.np[l];
+    const Tc* w = lv.w[l];
+    const Tc* dg = lv.diag[l];
+    // red points: u = r / d ; black points wait for them
+    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
+      const int i1 = (int)(s % m);
+      const int64_t rr = s / m;
+      const int i2 = (int)(DIM == 2 ? rr : rr % m);
+      const int i3 = (int)(DIM == 3 ? rr / m : 0);
+      if (((i1 + i2 + i3 + DIM) & 1) == 0) stc(ul[l], s, cmul(rl[l][s], inv_diag<Tc>(sig, dg[s])));
+    }
+    __syncthreads();
+    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
+      const int i1 = (int)(s % m);
+      const int64_t rr = s / m;
+      const int i2 = (int)(DIM == 2 ? rr : rr % m);
+      const int i3 = (int)(DIM == 3 ? rr / m : 0);
+      if (((i1 + i2 + i3 + DIM) & 1) == 0) continue;
+      const int64_t off[6] = {-1, 1, -(int64_t)m, (int64_t)m, -(int64_t)m * m, (int64_t)m * m};
+      const bool ex[6] = {i1 > 0, i1 < m - 1, i2 > 0, i2 < m - 1, i3 > 0, i3 < m - 1};
+      C acc = rl[l][s];
+#pragma unroll
+      for (int k = 0; k < 2 * DIM; ++k) {
+        if (ex[k]) {
+          const C ured = ldc(ul[l], s + off[k]);
+          const Tc wk = w[(int64_t)k * np + s];
+          acc.x = fma(wk, ured.x, acc.x);
+          acc.y = fma(wk, ured.y, acc.y);
+        }
+      }
+      stc(ul[l], s, cmul(acc, inv_diag<Tc>(sig, dg[s])));
+    }
+    __syncthreads();
+    // residual res = r - (sigma u + tau K u)
+    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
+      const int i1 = (int)(s % m);
+      const int64_t rr = s / m;
+      const int i2 = (int)(DIM == 2 ? rr : rr % m);
+      const int i3 = (int)(DIM == 3 ? rr / m : 0);
+      const int64_t off[6] = {-1, 1, -(int64_t)m, (int64_t)m, -(int64_t)m * m, (int64_t)m * m};
+      const bool ex[6] = {i1 > 0, i1 < m - 1, i2 > 0, i2 < m - 1, i3 > 0, i3 < m - 1};
+      const C uc = ldc(ul[l], s);
+      C lu = cmul(cmk<Tc>(sig.x + dg[s], sig.y), uc);
+#pragma unroll
+      for (int k = 0; k < 2 * DIM; ++k) {
+        if (ex[k]) {
+          const C un = ldc(ul[l], s + off[k]);
+          const Tc wk = w[(int64_t)k * np + s];
+          lu.x = fma(-wk, un.x, lu.x);
+          lu.y = fma(-wk, un.y, lu.y);
+        }
+      }
+      resl[l][s] = rl[l][s] - lu;
+    }
+    __syncthreads();
+    // full weighting onto level l + 1
+    const int mc = lv.m[l + 1];
+    for (int64_t sc = threadIdx.x; sc < lv.np[l + 1]; sc += blockDim.x) {
+      const int c1 = (int)(sc % mc);
+      const int64_t rr = sc / mc;
+      const int c2 = (int)(DIM == 2 ? rr : rr % mc);
+      const int c3 = (int)(DIM == 3 ? rr / mc : 0);
+      const int f1 = 2 * c1 + 1, f2 = 2 * c2 + 1, f3 = 2 * c3 + 1;
+      C acc = czero<Tc>();
+      for (int o3 = (DIM == 3 ? -1 : 0); o3 <= (DIM == 3 ? 1 : 0); ++o3)
+        for (int o2 = -1; o2 <= 1; ++o2)
+          for (int o1 = -1; o1 <= 1; ++o1) {
+            Tc wgt = wt[o1 + 1] * wt[o2 + 1];
+            if (DIM == 3) wgt *= wt[o3 + 1];
+            const C v = resl[l][lin<DIM>(f1 + o1, f2 + o2, f3 + o3, m)];
+            acc.x = fma(wgt, v.x, acc.x);
+            acc.y = fma(wgt, v.y, acc.y);
+          }
+      rl[l + 1][sc] = acc;
+    }
+    __syncthreads();
+  }
+  // one-point level
+  {
+    const int l = lv.count - 1;
+    if (threadIdx.x == 0) stc(ul[l], 0, cmul(rl[l][0], inv_diag<Tc>(sig, lv.diag[l][0])));
+    __syncthreads();
+  }
+  // prolongation and correction back up
+  for (int l = lv.count - 2; l >= 0; --l) {
+    const int mf = lv.m[l], mc = lv.m[l + 1];
+    for (int64_t s = threadIdx.x; s < lv.np[l]; s += blockDim.x) {
+      const int fi[3] = {(int)(s % mf), (int)(DIM == 2 ? s / mf : (s / mf) % mf), (int)(DIM == 3 ? s / mf / mf : 0)};
+      int ci[3][2];
+      Tc cw[3][2];
+      int cnt[3] = {1, 1, 1};
+      ci[2][0] = 0;
+      cw[2][0] = Tc(1);
+      for (int a = 0; a < DIM; ++a) {
+        const int f = fi[a];
+        if (f & 1) {
+          ci[a][0] = (f - 1) >> 1;
+          cw[a][0] = Tc(1);
+          cnt[a] = 1;
+        } else {
+          cnt[a] = 0;
+          const int lo = (f >> 1) - 1, hi = f >> 1;
+          if (lo >= 0) {
+            ci[a][cnt[a]] = lo;
+            cw[a][cnt[a]] = Tc(0.5);
+            cnt[a]++;
+          }
+          if (hi < mc) {
+            ci[a][cnt[a]] = hi;
+            cw[a][cnt[a]] = Tc(0.5);
+            cnt[a]++;
+          }
+        }
+      }
+      C acc = czero<Tc>();
+      for (int a3 = 0; a3 < cnt[2]; ++a3)
+        for (int a2 = 0; a2 < cnt[1]; ++a2)
+          for (int a1 = 0; a1 < cnt[0]; ++a1) {
+            const Tc wgt = cw[0][a1] * cw[1][a2] * cw[2][a3];
+            const C v = ldc(ul[l + 1], lin<DIM>(ci[0][a1], ci[1][a2], ci[2][a3], mc));
+            acc.x = fma(wgt, v.x, acc.x);
+            acc.y = fma(wgt, v.y, acc.y);
+          }
+      stc(ul[l], s, ldc(ul[l], s) + acc);
+    }
+    __syncthreads();
+  }
+  for (int64_t s = threadIdx.x; s < lv.np[0]; s += blockDim.x) stc(u0, (int64_t)p * lv.np[0] + s, ldc(ul[0], s));
+}
+
+}  // namespace
+
+template <typename Tc, typename TU>
+size_t mg_coarse_cycle_smem(const CoarseLevels<Tc>& lv) {
+  size_t b = 0;
+  for (int l = 0; l < lv.count; ++l)
+    b += 2 * (size_t)lv.np[l] * sizeof(typename Cx<Tc>::t) + (((size_t)lv.np[l] * sizeof(TU) + 15) / 16) * 16;
+  return b;
+}
+
+template <typename Tc, typename TU>
+cudaError_t launch_mg_coarse_cycle(Launch& L, int dim, int planes, const CoarseLevels<Tc>& lv,
+                                   const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r0, TU* u0) {
+  const size_t smem = mg_coarse_cycle_smem<Tc, TU>(lv);
+  cudaError_t e;
+  if (dim == 2)
+    e = cudaFuncSetAttribute(mg_coarse_cycle_kernel<Tc, TU, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else
+    e = cudaFuncSetAttribute(mg_coarse_cycle_kernel<Tc, TU, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  double pts = 0;
+  for (int l = 0; l < lv.count; ++l) pts += (double)lv.np[l];
+  const double cs = sizeof(typename Cx<Tc>::t);
+  L.begin(KC_MG_COARSE);
+  if (dim == 2)
+    mg_coarse_cycle_kernel<Tc, TU, 2><<<planes, 256, smem, L.stream>>>(lv, r0, u0, sigma);
+  else
+    mg_coarse_cycle_kernel<Tc, TU, 3><<<planes, 256, smem, L.stream>>>(lv, r0, u0, sigma);
+  return L.end(KC_MG_COARSE, (double)planes * lv.np[0] * (cs + sizeof(TU)), (double)planes * pts * 60.0);
+}
+
+#define PCOPT_INST_CC(Tc, TU)                                                                              \
+  template cudaError_t launch_mg_coarse_cycle<Tc, TU>(Launch&, int, int, const CoarseLevels<Tc>&,         \
+                                                      const Cx<Tc>::t*, const Cx<Tc>::t*, TU*);            \
+  template size_t mg_coarse_cycle_smem<Tc, TU>(const CoarseLevels<Tc>&);
+PCOPT_INST_CC(float, float2)
+PCOPT_INST_CC(double, double2)
+PCOPT_INST_CC(float, __nv_bfloat162)
+#undef PCOPT_INST_CC
+
+}  // namespace pcopt

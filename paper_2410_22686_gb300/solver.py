@@ -102,6 +102,14 @@ class Solver:
         capi.check(fn(self.h, _ptr(x), _ptr(y), _stream()))
         return y
 
+    def matvec_f32(self, x32, out=None):
+        """y = A x for an FP32 tensor x (double-float arithmetic, FP64 result)."""
+        if not x32.is_cuda or x32.dtype != torch.float32 or not x32.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        y = torch.empty(x32.shape, dtype=torch.float64, device="cuda") if out is None else out
+        capi.check(self.lib.pc_matvec_f32(self.h, ctypes.c_void_p(x32.data_ptr()), _ptr(y), _stream()))
+        return y
+
     def apply_precond(self, v, out=None):
         self._vec(v)
         w = torch.empty_like(v) if out is None else out

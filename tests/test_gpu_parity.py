@@ -294,3 +294,18 @@ def test_bf16_storage_fgmres_matches_fp64_oracle():
     assert rel <= 1e-11
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
     sol.close()
+
+
+@pytest.mark.parametrize("d,m1,n", [(2, 31, 32), (3, 7, 8), (2, 255, 8)])
+def test_double_float_matvec_of_fp32_vector_matches_oracle(d, m1, n):
+    # FP32 input is exact in FP64; the double-float evaluation must agree with the
+    # FP64 oracle to ~2^-46 of the largest term (stencil terms are up to ~4 tau/h^2
+    # times the vector): bar 1e-11 relative to max |A x|
+    a = _coef(d, m1, "var", seed=m1 + 7 * n)
+    sol = _solver(d, m1, n, a, "mg", gamma=1e-4)
+    x32 = S.random_vector((2, n) + (m1,) * d, 17).astype(np.float32)
+    y = sol.matvec_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, 1e-4)
+    ref = osy.apply_A(x32.astype(np.float64), a, tau, alpha)
+    assert _rel(y, ref) <= 1e-11
+    sol.close()
