@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-bf16", action="store_true")
+    ap.add_argument("--skip-3d", action="store_true")
+    ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--batch-gb", type=float, default=110.0, help="device memory per batched wave (GB)")
     a = ap.parse_args()
     a.gammas = tuple(float(x) for x in a.gammas.split(","))
     return a
@@ -215,6 +219,109 @@ def _e2e(args, sols, rhs, gammas, torch):
     return (time.perf_counter() - t0) / (args.steps * len(gammas))
 
 
+def _extra_workloads(args, torch, dev):
+    """Timed extras on the other workloads of the path (not part of `value`)."""
+    import synthetic as S
+    from paper_2410_22686_gb300 import Batch, Solver
+    from paper_2410_22686_gb300 import autograd as pag
+    out = {}
+
+    def sync_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = None
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0 / reps, r
+
+    if not args.skip_3d:
+        p = S.gaussian_field_3d_problem()
+        res = {}
+        for prec in ("fp32", "bf16s", "fp64"):
+            sol = Solver(3, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision=prec, max_iter=60)
+            b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
+                              torch.from_numpy(p.y0).to(dev))
+            t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
+            res[prec] = {"solve_s": t, "iters": r[1], "relres": r[2]}
+            sol.close()
+            del b
+            torch.cuda.empty_cache()
+        out["grf_3d_63cubed_n128"] = {"unknowns": p.unknowns, "gamma": p.gamma, **res}
+
+    if not args.skip_grad:
+        p = S.gradient_problem()
+        sol = Solver(2, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision="fp64", max_iter=80)
+        g = torch.from_numpy(p.g).to(dev)
+
+        def grad_once():
+            la = torch.from_numpy(np.log(p.a_nodes[1:-1, 1:-1]).copy()).to(dev).requires_grad_(True)
+            gg = g.clone().requires_grad_(True)
+            x = pag.solve(sol, la, gg, p.a_nodes, rtol=1e-10)
+            J = pag.objective(x, gg, sol)
+            J.backward()
+            return J.item()
+
+        t, _ = sync_time(grad_once, 2)
+        out["gradient_127sq_n128"] = {"seconds_per_gradient": t, "params": p.m1 * p.m1 + p.g.size,
+                                      "includes": "set_coefficient, forward solve (1e-10), adjoint solve, "
+                                                  "stencil derivative, objective"}
+        sol.close()
+        torch.cuda.empty_cache()
+
+    if not args.skip_batched:
+        probs = S.batched_problems(64)
+        cap = 48
+        waves, cur, cur_b = [], [], 0.0
+        for q in probs:
+            need = q.unknowns * (12.0 * cap + 60.0) / 1e9
+            if cur and cur_b + need > args.batch_gb:
+                waves.append(cur)
+                cur, cur_b = [], 0.0
+            cur.append(q)
+            cur_b += need
+        if cur:
+            waves.append(cur)
+        t_batch, t_seq, iters, rels, unk_it = 0.0, 0.0, [], [], 0.0
+        for wave in waves:
+            sols, bs = [], []
+            for q in wave:
+                so = Solver(2, q.m1, q.n, q.T, q.gamma, q.eps, q.a_nodes, spatial="mg", precision="fp32",
+                            max_iter=cap)
+                bs.append(so.build_rhs(torch.from_numpy(q.f).to(dev), torch.from_numpy(q.g).to(dev),
+                                       torch.from_numpy(q.y0).to(dev)))
+                sols.append(so)
+            bt = Batch(sols, bs, rtol=RTOL, maxit=cap)
+            tb, r = sync_time(lambda: bt.solve(raise_on_nonconv=False), 2)
+            t_batch += tb
+            iters += r[0]
+            rels += r[1]
+            unk_it += sum(q.unknowns * it for q, it in zip(wave, r[0]))
+
+            def seq():
+                for so, bb in zip(sols, bs):
+                    so.solve(bb, rtol=RTOL, raise_on_nonconv=False)
+
+            ts, _ = sync_time(seq, 1)
+            t_seq += ts
+            bt.close()
+            for so in sols:
+                so.close()
+            del bs, sols
+            torch.cuda.empty_cache()
+        out["batched_64"] = {"problems": len(probs), "waves": len(waves), "batch_seconds": t_batch,
+                             "sequential_seconds": t_seq, "speedup": t_seq / t_batch if t_batch else None,
+                             "unknowns_iters_per_s": unk_it / t_batch if t_batch else None,
+                             "total_unknowns": sum(q.unknowns for q in probs), "max_iters": max(iters),
+                             "converged": int(sum(1 for r in rels if r <= RTOL)),
+                             "how": "each wave is one graph launch (pc_batch_solve), FP32 preconditioner; "
+                                    "sequential = the same problems one host-driven solve after another"}
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -339,6 +446,9 @@ def run_ours(args):
         del solsb
         torch.cuda.empty_cache()
 
+    # ---------------- the other workloads of the path
+    extras = _extra_workloads(args, torch, dev)
+
     # ---------------- roofline of the dominant kernel class
     tot_ms = sum(v["ms"] for v in stats.values())
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
@@ -382,7 +492,7 @@ def run_ours(args):
         "unknowns_iters_per_s": sum(U * it for it in iters_mixed) / (ms_mixed / 1000.0 / args.steps),
         "precond_apply": {"gbs": precond_gbs, "ms": p_ms, "frac_of_hbm": precond_gbs / hbm_peak,
                           "bytes": p_bytes, "precision": "fp32"},
-        "roofline": roof, "kernel_breakdown": breakdown,
+        "roofline": roof, "kernel_breakdown": breakdown, "other_workloads": extras,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 8 * U * len(GAM),
