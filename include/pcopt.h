@@ -74,7 +74,8 @@ typedef enum pc_gmres_mode {
 typedef struct pc_params {
   int dim;          /* 2 or 3 */
   int m1;           /* interior grid points per dimension, h = 1/(m1+1); multigrid needs m1 = 2^k-1 */
-  int n;            /* time blocks (FFT length), tau = T/(n+1); power of two in this build */
+  int n;            /* time blocks (FFT length), tau = T/(n+1); 1..4096.  Powers of two use the
+                       register FFT; other lengths (the paper's n = 2^k - 1) a direct DFT */
   double T;         /* final time > 0 */
   double gamma;     /* regularisation parameter > 0 */
   double eps;       /* eps of C_{eps,n}, in (0, 1] */
@@ -89,11 +90,12 @@ typedef struct pc_handle pc_handle;
  * Eq. matrix_P_eps, Eq. decomposition_eps.
  *   a_nodes: HOST pointer to the coefficient a(x) sampled on all (m1+2)^dim
  *            grid nodes including the boundary, C-ordered with x1 fastest;
- *            NULL means a == 1.  Every value must be finite and > 0.
+ *            NULL means a == 1.  Values must be finite, > 0 at interior nodes
+ *            and >= 0 at boundary nodes.
  *   stream:  stream used for the coefficient upload.
  *   out:     receives the handle (caller releases it with pc_destroy).
- * Errors: PC_ERR_ARG (dim not 2/3, m1 < 1, n < 1 or not a power of two,
- * T <= 0, gamma <= 0, eps outside (0,1], a <= 0, FST with non-constant a,
+ * Errors: PC_ERR_ARG (dim not 2/3, m1 < 1, n outside 1..4096,
+ * T <= 0, gamma <= 0, eps outside (0,1], a not as above, FST with non-constant a,
  * MG with m1 != 2^k-1), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
 
@@ -101,7 +103,7 @@ int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_ha
  * the stencil of every level (and the FST eigenvalues) is recomputed on the
  * host and copied into the handle's buffers.  a_nodes: HOST, (m1+2)^dim values
  * as in pc_setup (NULL means a == 1).  Synchronises `stream`.
- * Errors: PC_ERR_ARG (a <= 0 or non-finite; non-constant a on an FST handle). */
+ * Errors: PC_ERR_ARG (a not as in pc_setup; non-constant a on an FST handle). */
 int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
 
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
@@ -157,8 +159,8 @@ int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int ma
  * on the first call and reused while (b, x, rtol, maxit) are unchanged.
  *   x: device, overwritten (the initial guess is zero).  iters/relres as in
  *   pc_gmres_solve (relres is the true relative residual).  Synchronises `stream`.
- * Errors: as pc_gmres_solve; PC_ERR_UNSUPPORTED for n > 1024 (FP32
- * preconditioner) or n > 256 (FP64 preconditioner). */
+ * Errors: as pc_gmres_solve; PC_ERR_UNSUPPORTED for n not a power of two,
+ * n > 1024 (FP32 preconditioner) or n > 256 (FP64 preconditioner). */
 int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, int maxit, int* iters,
                          double* relres, void* stream);
 

@@ -243,6 +243,24 @@ static void release(pc_handle* h) {
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// a must be finite, > 0 at interior nodes and >= 0 at boundary nodes (faces to the
+// boundary then carry a_f = (a_P + a_Q)/2 > 0, so K stays symmetric positive definite)
+static int check_coefficient(const double* a, int m1, int dim) {
+  const int M = m1 + 2;
+  const size_t nodes = dim == 2 ? (size_t)M * M : (size_t)M * M * M;
+  for (size_t i = 0; i < nodes; ++i) {
+    const int i1 = (int)(i % M);
+    const size_t r = i / M;
+    const int i2 = (int)(dim == 2 ? r : r % M);
+    const int i3 = dim == 3 ? (int)(r / M) : 1;
+    const bool interior = i1 > 0 && i1 < M - 1 && i2 > 0 && i2 < M - 1 && i3 > 0 && i3 < M - 1;
+    const double v = a[i];
+    if (!std::isfinite(v) || !(interior ? v > 0 : v >= 0))
+      return fail(PC_ERR_ARG, "a(x) must be finite, > 0 at interior nodes and >= 0 on the boundary");
+  }
+  return PC_OK;
+}
+
 // per-point face weights tau*a_f/h^2 and their sum for one level (host)
 static void level_stencil(const std::vector<double>& a, int m, int dim, double tau, std::vector<double>& w,
                           std::vector<double>& d) {
@@ -383,7 +401,6 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   if (p->dim != 2 && p->dim != 3) return fail(PC_ERR_ARG, "dim must be 2 or 3");
   if (p->m1 < 1 || p->m1 > 4095) return fail(PC_ERR_ARG, "m1 must be in [1, 4095]");
   if (p->n < 1) return fail(PC_ERR_ARG, "n must be >= 1");
-  if (!is_pow2(p->n)) return fail(PC_ERR_ARG, "n must be a power of two in this build");
   if (p->n > 4096) return fail(PC_ERR_ARG, "n must be <= 4096");
   if (!(p->T > 0) || !std::isfinite(p->T)) return fail(PC_ERR_ARG, "T must be finite and > 0");
   if (!(p->gamma > 0) || !std::isfinite(p->gamma)) return fail(PC_ERR_ARG, "gamma must be finite and > 0");
@@ -399,11 +416,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   std::vector<double> a(nodes, 1.0);
   bool constant = true;
   if (a_nodes) {
+    if (int rc = check_coefficient(a_nodes, m1, dim)) return rc;
     for (size_t i = 0; i < nodes; ++i) {
-      const double v = a_nodes[i];
-      if (!(v > 0) || !std::isfinite(v)) return fail(PC_ERR_ARG, "a(x) must be finite and > 0 on every node");
-      a[i] = v;
-      if (v != a_nodes[0]) constant = false;
+      a[i] = a_nodes[i];
+      if (a_nodes[i] != a_nodes[0]) constant = false;
     }
   }
   int spatial = p->spatial;
@@ -606,11 +622,10 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
   std::vector<double> a(nodes, 1.0);
   bool constant = true;
   if (a_nodes) {
+    if (int rc = check_coefficient(a_nodes, m1, dim)) return rc;
     for (size_t i = 0; i < nodes; ++i) {
-      const double v = a_nodes[i];
-      if (!(v > 0) || !std::isfinite(v)) return fail(PC_ERR_ARG, "a(x) must be finite and > 0 on every node");
-      a[i] = v;
-      if (v != a_nodes[0]) constant = false;
+      a[i] = a_nodes[i];
+      if (a_nodes[i] != a_nodes[0]) constant = false;
     }
   }
   if (h->spatial == PC_SPATIAL_FST && !constant) return fail(PC_ERR_ARG, "FST handle needs a constant coefficient");
@@ -1047,6 +1062,7 @@ extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, doub
 
 static int graph_supported(const pc_handle* h, int maxit) {
   if (maxit < 1 || maxit > h->cap) return fail(PC_ERR_ARG, "graph solve: maxit must be in [1, max_iter]");
+  if (!is_pow2(h->n)) return fail(PC_ERR_UNSUPPORTED, "graph solve: n must be a power of two");
   const int nmax = h->fp32 ? 1024 : 256;
   if (h->n > nmax) return fail(PC_ERR_UNSUPPORTED, "graph solve: n too large for the register FFT");
   return PC_OK;

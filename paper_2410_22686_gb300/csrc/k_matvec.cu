@@ -136,40 +136,23 @@ template cudaError_t launch_matvec<float>(Launch&, const Grid&, int, const Stenc
 // The same product for an FP32 input z (the flexible-GMRES basis Z), evaluated in
 // double-float arithmetic on the FP32 units: every FP64 coefficient c is held as
 // c_hi + c_lo (two floats), c*z is formed exactly up to c_lo*z by an FMA error
-// term (p = c_hi z, e = fma(c_hi, z, -p)), terms are added with Knuth's TwoSum,
-// and only the final hi + lo becomes an FP64 value (one FP64 addition per output).
+// term (p = c_hi z, e = fma(c_hi, z, -p)), the leading parts are added by a
+// pairwise tree of Knuth's TwoSum (depth log2 of the term count, so the chains stay
+// short), and only the final hi + lo becomes an FP64 value (one FP64 addition).
 // The relative error is of order 2^-46 of the largest term, far below what the
 // Arnoldi relation needs, while GB300's FP64 unit (1/57 of the FP32 rate) would
 // otherwise bound this kernel.
 namespace pcopt {
 namespace {
 
-struct DF {
-  float hi, lo;
-};
-// a + b exactly as hi + err (Knuth)
+// a + b exactly as hi + err (Knuth).  The _rn intrinsics keep every operation a
+// separately rounded IEEE operation: with FMA contraction the compiler could fuse a
+// rounded product feeding `a + b` into an FMA, which breaks the exactness.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
-  s = a + b;
-  const float bb = s - a;
-  err = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-// accumulate the exact float x into (acc.hi, acc.lo)
-__device__ __forceinline__ void df_add_f(DF& acc, float x) {
-  float s, e;
-  two_sum(acc.hi, x, s, e);
-  acc.hi = s;
-  acc.lo += e;
-}
-// accumulate c * x (c = c.hi + c.lo, x exact float)
-__device__ __forceinline__ void df_add_prod(DF& acc, float2 c, float x) {
-  const float p = c.x * x;
-  const float pe = fmaf(c.x, x, -p) + c.y * x;
-  float s, e;
-  two_sum(acc.hi, p, s, e);
-  acc.hi = s;
-  acc.lo += e + pe;
-}
-__device__ __forceinline__ double df_to_f64(const DF& a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 
 template <int DIM>
 __global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict__ x, double* __restrict__ y,
@@ -219,30 +202,50 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict_
   double* y2 = y + (int64_t)n * ms;
   float x1prev = (j0 > 0) ? x1[(int64_t)(j0 - 1) * ms + s] : 0.0f;
   float x2c = x2[(int64_t)j0 * ms + s];
+  constexpr int NT = 2 * DIM + 4;  // terms per output
   for (int j = j0; j < j1; ++j) {
     const int64_t idx = (int64_t)j * ms + s;
     const float x1c = x1[idx];
     const float x2n = (j + 1 < n) ? x2[idx + ms] : 0.0f;
-    // y1 = alpha x1 + x2_j - x2_{j+1} + tau K x2_j
-    DF a{0.0f, 0.0f};
-    df_add_prod(a, d, x2c);
+    // y1 = alpha x1 + x2_j - x2_{j+1} + tau K x2_j ; y2 = alpha x2 - (x1_j - x1_{j-1} + tau K x1_j).
+    // Leading parts of all terms are summed by a pairwise TwoSum tree; every rounding
+    // error (products and sums) is gathered in a separate float.
+    float ta[NT], tb[NT];
+    float ea = 0.0f, eb = 0.0f;
+    auto prod = [&](float2 c, float x, float& t, float& e) {
+      t = __fmul_rn(c.x, x);  // rounded product, never fused downstream
+      e += fmaf(c.x, x, -t) + c.y * x;
+    };
+    prod(d, x2c, ta[0], ea);
+    prod(make_float2(-d.x, -d.y), x1c, tb[0], eb);
 #pragma unroll
-    for (int k = 0; k < 2 * DIM; ++k)
-      if (ex[k]) df_add_prod(a, wv[k], __ldg(x2 + idx + off[k]));
-    df_add_f(a, x2c);
-    df_add_f(a, -x2n);
-    df_add_prod(a, alpha, x1c);
-    // y2 = alpha x2 - (x1_j - x1_{j-1} + tau K x1_j)
-    DF b{0.0f, 0.0f};
-    df_add_prod(b, make_float2(-d.x, -d.y), x1c);
+    for (int k = 0; k < 2 * DIM; ++k) {
+      const float n2 = ex[k] ? __ldg(x2 + idx + off[k]) : 0.0f;
+      const float n1 = ex[k] ? __ldg(x1 + idx + off[k]) : 0.0f;
+      prod(wv[k], n2, ta[1 + k], ea);
+      prod(make_float2(-wv[k].x, -wv[k].y), n1, tb[1 + k], eb);
+    }
+    ta[2 * DIM + 1] = x2c;
+    ta[2 * DIM + 2] = -x2n;
+    prod(alpha, x1c, ta[2 * DIM + 3], ea);
+    tb[2 * DIM + 1] = -x1c;
+    tb[2 * DIM + 2] = x1prev;
+    prod(alpha, x2c, tb[2 * DIM + 3], eb);
 #pragma unroll
-    for (int k = 0; k < 2 * DIM; ++k)
-      if (ex[k]) df_add_prod(b, make_float2(-wv[k].x, -wv[k].y), __ldg(x1 + idx + off[k]));
-    df_add_f(b, -x1c);
-    df_add_f(b, x1prev);
-    df_add_prod(b, alpha, x2c);
-    y1[idx] = df_to_f64(a);
-    y2[idx] = df_to_f64(b);
+    for (int step = 1; step < NT; step <<= 1) {
+#pragma unroll
+      for (int i = 0; i + step < NT; i += 2 * step) {
+        float s1, r1, s2, r2;
+        two_sum(ta[i], ta[i + step], s1, r1);
+        two_sum(tb[i], tb[i + step], s2, r2);
+        ta[i] = s1;
+        ea += r1;
+        tb[i] = s2;
+        eb += r2;
+      }
+    }
+    y1[idx] = f32_to_f64(ta[0]) + f32_to_f64(ea);
+    y2[idx] = f32_to_f64(tb[0]) + f32_to_f64(eb);
     x1prev = x1c;
     x2c = x2n;
   }

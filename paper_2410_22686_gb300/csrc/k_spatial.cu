@@ -284,6 +284,79 @@ __global__ void __launch_bounds__(256) mg_prolong_kernel(const TU* __restrict__ 
   }
 }
 
+// The same correction, one thread per coarse cell: cell (I[,J[,K]]), each index in
+// [-1, mc-1], owns the fine points 2I+1 and 2I+2 per axis (0-based; 2I+1 sits on
+// coarse point I, 2I+2 halfway between I and I+1), so every fine point is written
+// exactly once; the 2^d corner values are loaded once and coarse values outside
+// [0, mc) are the zero boundary.
+template <typename Tc, typename TU, int DIM>
+__global__ void __launch_bounds__(256) mg_prolong_cell_kernel(const TU* __restrict__ ec, TU* __restrict__ uf, int mf,
+                                                              int mc, int64_t npf, int64_t npc, int planes) {
+  typedef typename Cx<Tc>::t C;
+  const int mc1 = mc + 1;
+  const int64_t ncell = DIM == 2 ? (int64_t)mc1 * mc1 : (int64_t)mc1 * mc1 * mc1;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= ncell) return;
+  const int p0 = blockIdx.y * kPlaneChunk;
+  const int p1 = min(planes, p0 + kPlaneChunk);
+  const int I = (int)(cell % mc1) - 1;
+  const int J = (int)((cell / mc1) % mc1) - 1;
+  const int K = DIM == 3 ? (int)(cell / ((int64_t)mc1 * mc1)) - 1 : 0;
+  const Tc hf = Tc(0.5);
+  for (int p = p0; p < p1; ++p) {
+    const TU* ep = ec + (int64_t)p * npc;
+    TU* up = uf + (int64_t)p * npf;
+    C c[2][2][2];
+#pragma unroll
+    for (int a3 = 0; a3 < (DIM == 3 ? 2 : 1); ++a3)
+#pragma unroll
+      for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int a1 = 0; a1 < 2; ++a1) {
+          const int i1 = I + a1, i2 = J + a2, i3 = K + a3;
+          const bool in = i1 >= 0 && i1 < mc && i2 >= 0 && i2 < mc && (DIM == 2 || (i3 >= 0 && i3 < mc));
+          c[a3][a2][a1] = in ? ldc(ep, DIM == 2 ? (int64_t)i2 * mc + i1 : ((int64_t)i3 * mc + i2) * mc + i1)
+                             : czero<Tc>();
+        }
+    // interpolate along x1, then x2, then x3: e[o3][o2][o1], o = 0 -> coincident, 1 -> midpoint
+    C e1[2][2][2];
+#pragma unroll
+    for (int a3 = 0; a3 < (DIM == 3 ? 2 : 1); ++a3)
+#pragma unroll
+      for (int a2 = 0; a2 < 2; ++a2) {
+        e1[a3][a2][0] = c[a3][a2][0];
+        e1[a3][a2][1] = cscale(c[a3][a2][0] + c[a3][a2][1], hf);
+      }
+    C e2[2][2][2];
+#pragma unroll
+    for (int a3 = 0; a3 < (DIM == 3 ? 2 : 1); ++a3)
+#pragma unroll
+      for (int o1 = 0; o1 < 2; ++o1) {
+        e2[a3][0][o1] = e1[a3][0][o1];
+        e2[a3][1][o1] = cscale(e1[a3][0][o1] + e1[a3][1][o1], hf);
+      }
+#pragma unroll
+    for (int o3 = 0; o3 < (DIM == 3 ? 2 : 1); ++o3) {
+      const int f3 = DIM == 3 ? 2 * K + 1 + o3 : 0;
+      if (DIM == 3 && f3 < 0) continue;
+#pragma unroll
+      for (int o2 = 0; o2 < 2; ++o2) {
+        const int f2 = 2 * J + 1 + o2;
+        if (f2 < 0) continue;
+#pragma unroll
+        for (int o1 = 0; o1 < 2; ++o1) {
+          const int f1 = 2 * I + 1 + o1;
+          if (f1 < 0) continue;
+          C v = e2[0][o2][o1];
+          if (DIM == 3) v = o3 == 0 ? e2[0][o2][o1] : cscale(e2[0][o2][o1] + e2[1][o2][o1], hf);
+          const int64_t q = DIM == 2 ? (int64_t)f2 * mf + f1 : ((int64_t)f3 * mf + f2) * mf + f1;
+          stc(up, q, ldc(up, q) + v);
+        }
+      }
+    }
+  }
+}
+
 template <typename Tc, typename TU>
 __global__ void mg_coarsest_kernel(const Tc* __restrict__ diag, const typename Cx<Tc>::t* __restrict__ sigma,
                                    const typename Cx<Tc>::t* __restrict__ r, TU* __restrict__ u, int planes) {
@@ -364,11 +437,14 @@ cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* e
   const int mc = (gf.m - 1) / 2;
   const int64_t npc = gf.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
   const double tot = (double)gf.np * planes;
+  const int64_t ncell = gf.dim == 2 ? (int64_t)(mc + 1) * (mc + 1) : (int64_t)(mc + 1) * (mc + 1) * (mc + 1);
   L.begin(KC_MG_PROLONG);
   if (gf.dim == 2)
-    mg_prolong_kernel<Tc, TU, 2><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
+    mg_prolong_cell_kernel<Tc, TU, 2><<<plane_grid(ncell, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
+                                                                                      planes);
   else
-    mg_prolong_kernel<Tc, TU, 3><<<plane_grid(gf.np, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc, planes);
+    mg_prolong_cell_kernel<Tc, TU, 3><<<plane_grid(ncell, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
+                                                                                      planes);
   return L.end(KC_MG_PROLONG, 2.0 * tot * cs + (double)npc * planes * cs, tot * 8.0);
 }
 

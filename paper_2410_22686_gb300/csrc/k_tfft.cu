@@ -305,6 +305,115 @@ __global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Direct DFT along time for lengths that are not powers of two (the paper's own
+// runs use n = 2^k - 1): a CTA holds TS columns of all n time samples in shared
+// memory and forms each needed frequency as a plain sum with the twiddle index
+// advanced incrementally modulo n.  n^2 work per column.
+template <typename Tc>
+__global__ void __launch_bounds__(256) tdft_forward_kernel(const double* __restrict__ v, const Tc* __restrict__ dpow,
+                                                           const Tc* __restrict__ dinv,
+                                                           const typename Cx<Tc>::t* __restrict__ tw,
+                                                           typename Cx<Tc>::t* __restrict__ spec, int64_t ms, int n,
+                                                           int TS) {
+  typedef typename Cx<Tc>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* z = reinterpret_cast<C*>(smem_raw);  // [n][TS]
+  const int64_t s0 = (int64_t)blockIdx.x * TS;
+  const double* v1 = v;
+  const double* v2 = v + (int64_t)n * ms;
+  for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
+    const int j = e / TS, c = e - (e / TS) * TS;
+    const int64_t s = s0 + c;
+    Tc a = Tc(0), b = Tc(0);
+    if (s < ms) {
+      a = cvt<Tc>(v1[(int64_t)j * ms + s]) * dinv[j];
+      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * dpow[j];
+    }
+    z[j * TS + c] = cmk<Tc>(a, b);
+  }
+  __syncthreads();
+  const int nf = n / 2 + 1;
+  const Tc hf = Tc(0.5);
+  for (int e = threadIdx.x; e < nf * TS; e += blockDim.x) {
+    const int k = e / TS, c = e - (e / TS) * TS;
+    const int64_t s = s0 + c;
+    const int kn = (n - k) % n;
+    C Z = czero<Tc>(), W = czero<Tc>();
+    int ik = 0, ikn = 0;  // (j k) mod n and (j (n-k)) mod n
+    for (int j = 0; j < n; ++j) {
+      const C x = z[j * TS + c];
+      const C a = tw[ik], b = tw[ikn];
+      Z.x = fma(a.x, x.x, fma(-a.y, x.y, Z.x));
+      Z.y = fma(a.x, x.y, fma(a.y, x.x, Z.y));
+      W.x = fma(b.x, x.x, fma(-b.y, x.y, W.x));
+      W.y = fma(b.x, x.y, fma(b.y, x.x, W.y));
+      ik += k;
+      if (ik >= n) ik -= n;
+      ikn += kn;
+      if (ikn >= n) ikn -= n;
+    }
+    if (s >= ms) continue;
+    spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
+    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+  }
+}
+
+template <typename Tc, typename TU, typename Tout>
+__global__ void __launch_bounds__(256) tdft_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+                                                           const Tc* __restrict__ dinv,
+                                                           const typename Cx<Tc>::t* __restrict__ tw,
+                                                           Tout* __restrict__ w, int64_t ms, int n, int TS) {
+  typedef typename Cx<Tc>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* z = reinterpret_cast<C*>(smem_raw);  // [n][TS]
+  const int64_t s0 = (int64_t)blockIdx.x * TS;
+  const int nf = n / 2 + 1;
+  for (int e = threadIdx.x; e < nf * TS; e += blockDim.x) {
+    const int k = e / TS, c = e - (e / TS) * TS;
+    const int64_t s = s0 + c;
+    C sa = czero<Tc>(), sb = czero<Tc>();
+    if (s < ms) {
+      sa = ldc(spec, (int64_t)(2 * k) * ms + s);
+      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
+    }
+    z[k * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
+    if (k > 0 && 2 * k < n) z[(n - k) * TS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+  }
+  __syncthreads();
+  const Tc inv_n = Tc(1) / Tc(n);
+  Tout* w1 = w;
+  Tout* w2 = w + (int64_t)n * ms;
+  for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
+    const int j = e / TS, c = e - (e / TS) * TS;
+    const int64_t s = s0 + c;
+    C y = czero<Tc>();
+    int ij = 0;  // (j k) mod n, conjugate twiddles
+    for (int k = 0; k < n; ++k) {
+      const C x = z[k * TS + c];
+      const C a = tw[ij];
+      y.x = fma(a.x, x.x, fma(a.y, x.y, y.x));
+      y.y = fma(a.x, x.y, fma(-a.y, x.x, y.y));
+      ij += j;
+      if (ij >= n) ij -= n;
+    }
+    if (s >= ms) continue;
+    const Tc wt1 = dpow[j] * (y.x * inv_n);
+    const Tc wt2 = dinv[j] * (y.y * inv_n);
+    w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);
+    w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+  }
+}
+
+template <typename Tc>
+int pick_ts_dft(int n) {
+  // n*TS complex values within 96 KB of shared memory, TS a power of two in [1, 64]
+  const int budget = 98304 / (int)sizeof(typename Cx<Tc>::t);
+  int ts = 64;
+  while (ts > 1 && n * ts > budget) ts >>= 1;
+  return ts;
+}
+
 template <typename Tc>
 int pick_ts(int n) {
   // keep n*TS complex values within 64 KB of shared memory, TS a power of two in [1, 256]
@@ -405,7 +514,19 @@ template <typename Tc>
 cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow, const Tc* dinv,
                                 const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride,
                                 const int* jdev) {
-  if (jdev && n > four_step_max<Tc>()) return cudaErrorNotSupported;
+  const bool pow2 = (n & (n - 1)) == 0;
+  if (jdev && (n > four_step_max<Tc>() || !pow2)) return cudaErrorNotSupported;
+  if (!pow2) {
+    const int TS = pick_ts_dft<Tc>(n);
+    const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
+    cudaError_t e = cudaFuncSetAttribute(tdft_forward_kernel<Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nf = n / 2 + 1;
+    L.begin(KC_TFFT_FWD);
+    tdft_forward_kernel<Tc><<<(unsigned)((ms + TS - 1) / TS), 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, n, TS);
+    return L.end(KC_TFFT_FWD, 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t),
+                 16.0 * (double)nf * n * ms);
+  }
   if (n <= four_step_max<Tc>()) {
     const int nf = n / 2 + 1;
     const double bytes = 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
@@ -430,7 +551,20 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
 template <typename Tc, typename TU, typename Tout>
 cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
                                 const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev) {
-  if (jdev && n > four_step_max<Tc>()) return cudaErrorNotSupported;
+  const bool pow2 = (n & (n - 1)) == 0;
+  if (jdev && (n > four_step_max<Tc>() || !pow2)) return cudaErrorNotSupported;
+  if (!pow2) {
+    const int TS = pick_ts_dft<Tc>(n);
+    const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
+    cudaError_t e =
+        cudaFuncSetAttribute(tdft_inverse_kernel<Tc, TU, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nf = n / 2 + 1;
+    L.begin(KC_TFFT_INV);
+    tdft_inverse_kernel<Tc, TU, Tout><<<(unsigned)((ms + TS - 1) / TS), 256, smem, L.stream>>>(spec, dpow, dinv, tw, w,
+                                                                                            ms, n, TS);
+    return L.end(KC_TFFT_INV, 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout), 8.0 * (double)n * n * ms);
+  }
   if (n <= four_step_max<Tc>()) {
     const int nf = n / 2 + 1;
     const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout);

@@ -45,7 +45,7 @@ def test_status_strings_and_argument_errors_without_gpu():
     h = ctypes.c_void_p()
     bad = [
         capi.pc_params(4, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10),     # dim
-        capi.pc_params(2, 7, 6, 1.0, 1e-2, 0.5, 0, 0, 10),     # n not a power of two
+        capi.pc_params(2, 7, 5000, 1.0, 1e-2, 0.5, 0, 0, 10),  # n too large
         capi.pc_params(2, 7, 8, 1.0, 0.0, 0.5, 0, 0, 10),      # gamma
         capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.0, 0, 0, 10),     # eps
         capi.pc_params(2, 7, 8, 1.0, 1e-2, 1.5, 0, 0, 10),     # eps
@@ -56,10 +56,13 @@ def test_status_strings_and_argument_errors_without_gpu():
     for p in bad:
         assert l.pc_setup(ctypes.byref(p), None, None, ctypes.byref(h)) == capi.PC_ERR_ARG
         assert len(l.pc_last_error()) > 0
-    # non-positive coefficient
+    # coefficient: > 0 inside, >= 0 on the boundary, finite everywhere
     import numpy as np
-    a = np.ones((9, 9))
-    a[3, 3] = -1.0
-    p = capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10)
-    assert l.pc_setup(ctypes.byref(p), a.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(h)) == capi.PC_ERR_ARG
+    p = capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 2, 0, 10)
+    for (i, j, v) in [(3, 3, -1.0), (3, 3, 0.0), (0, 4, -1e-9), (8, 8, np.inf), (4, 0, np.nan)]:
+        a = np.ones((9, 9))
+        a[i, j] = v
+        assert l.pc_setup(ctypes.byref(p), a.ctypes.data_as(ctypes.c_void_p), None,
+                          ctypes.byref(h)) == capi.PC_ERR_ARG, (i, j, v)
+        assert b"boundary" in l.pc_last_error()
     assert l.pc_destroy(None) == capi.PC_OK

@@ -309,3 +309,22 @@ def test_double_float_matvec_of_fp32_vector_matches_oracle(d, m1, n):
     ref = osy.apply_A(x32.astype(np.float64), a, tau, alpha)
     assert _rel(y, ref) <= 1e-11
     sol.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n,kind,spatial", [(2, 15, 3, "var", "mg"), (2, 20, 5, "const", "fst"),
+                                                (2, 31, 31, "const", "fst"), (2, 31, 63, "var", "mg"),
+                                                (3, 7, 7, "var", "mg"), (2, 7, 100, "var", "mg")])
+def test_precond_apply_general_n_matches_oracle(d, m1, n, kind, spatial, precision, tol):
+    # lengths that are not powers of two go through the direct-DFT kernels
+    a = _coef(d, m1, kind, seed=11 * m1 + n)
+    gamma, eps = 1e-3, 0.4
+    sol = _solver(d, m1, n, a, spatial, precision=precision, gamma=gamma, eps=eps)
+    v = S.random_vector((2, n) + (m1,) * d, 13)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, opc.make_spatial_solver(spatial, a, m1, d, tau))
+    assert _rel(w, ref) <= tol
+    y = sol.matvec(_dev(v)).cpu().numpy()
+    assert _rel(y, osy.apply_A(v, _a_or_one(a, d, m1), tau, alpha)) <= 1e-12
+    sol.close()
