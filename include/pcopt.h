@@ -223,6 +223,35 @@ int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const double* a_int,
 /* Problem sizes of a handle: ms = m1^dim and the all-at-once length 2*n*ms. */
 int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
 
+/* Tile shapes of the tunable kernels (an implementation choice: the paper has no
+ * counterpart).  0 in any field means the built-in default.
+ *   mg_cx:   fused 2D multigrid down leg (red-black sweep, residual and
+ *            restriction of one level in one launch): coarse points per tile
+ *            axis, 8 or 16 (default 16 in FP32, 8 in FP64).
+ *   mg_ctas: CTAs per SM the fused down leg's grid is sized for, 1..64; it sets
+ *            the spectral planes each CTA sweeps on every level (default 8).
+ *   mv_tj:   time blocks per thread of the all-at-once matvec, 1..4096 (default 32).
+ *   pro_pch: spectral planes per CTA of the prolongation and the 3D per-level
+ *            multigrid kernels, 1..64 (default 8).
+ * pc_set_tiles validates (PC_ERR_ARG), applies the shapes to every later call on
+ * the handle and drops its cached solve graph.  pc_autotune times candidate
+ * shapes on the handle's own workspace (the multigrid spatial step for each
+ * (mg_cx, mg_ctas), then pro_pch; the matvec for each mv_tj), `reps` timed calls
+ * each (1..100) after one untimed call, keeps the fastest, applies it and copies
+ * it to *chosen (may be NULL).  It synchronises `stream`, overwrites the
+ * handle's Krylov and spectral workspace (not the caller's vectors) and must not
+ * run while `stream` is capturing or another call on the handle is in flight. */
+typedef struct pc_tiles {
+  int mg_cx;
+  int mg_ctas;
+  int mv_tj;
+  int pro_pch;
+} pc_tiles;
+
+int pc_get_tiles(const pc_handle* h, pc_tiles* out);
+int pc_set_tiles(pc_handle* h, const pc_tiles* tiles);
+int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* stream);
+
 /* Instrumentation.  pc_profile(h, 1) starts recording a CUDA-event pair around
  * every kernel the handle launches (per kernel class); pc_profile(h, 0) stops.
  * pc_stats fills up to `cap` records (name, launches, summed device ms,

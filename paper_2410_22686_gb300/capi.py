@@ -28,6 +28,11 @@ class pc_params(ctypes.Structure):
                 ("spatial", ctypes.c_int), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
 
 
+class pc_tiles(ctypes.Structure):
+    _fields_ = [("mg_cx", ctypes.c_int), ("mg_ctas", ctypes.c_int), ("mv_tj", ctypes.c_int),
+                ("pro_pch", ctypes.c_int)]
+
+
 class pc_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
@@ -66,6 +71,9 @@ _SIGNATURES = {
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
     "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "pc_get_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
+    "pc_set_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
+    "pc_autotune": (_i, [_vp, _i, ctypes.POINTER(pc_tiles), _vp]),
     "pc_profile": (_i, [_vp, _i]),
     "pc_stats": (_i, [_vp, ctypes.POINTER(pc_kernel_stat), _i, _ip]),
     "pc_stats_reset": (_i, [_vp]),

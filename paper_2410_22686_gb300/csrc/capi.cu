@@ -51,7 +51,7 @@ const char* kernel_class_name(int kc) {
                                         "arnoldi_dot",   "arnoldi_update_norm", "reduce_partials",
                                         "normalize",     "givens",       "x_update",
                                         "axpby",         "build_rhs",    "grad_stencil",
-                                        "arnoldi_reorth", "mg_coarse_cycle"};
+                                        "arnoldi_reorth", "mg_coarse_cycle", "mg_down"};
   return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
 }
 
@@ -161,6 +161,7 @@ struct pc_handle {
 
   std::vector<LevelBuf> lv;
   int coarse_l0 = 0;                 // first level run by the fused coarse-cycle kernel
+  Tiles tiles;                       // tile shapes of the tunable kernels (0 = default)
   float2* wdf = nullptr;             // level-0 face weights and diagonal as (hi, lo) float pairs
   float2* ddf = nullptr;
   float2 alpha_df{0.f, 0.f};
@@ -469,7 +470,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       if ((rc = upload(h, &L.d32, ds[l], st))) goto fail_out;
       if ((rc = dev_alloc(h, &L.r, (size_t)h->planes * L.np * cb))) goto fail_out;
       if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * ub))) goto fail_out;
-      if (l + 1 < mlev.size() && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb))) goto fail_out;
+      // per-level residual planes: only the 3D path writes them (2D fuses the residual away)
+      if (dim == 3 && l + 1 < mlev.size() && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb)))
+        goto fail_out;
       h->lv.push_back(L);
     }
     // double-float copies of the level-0 stencil for the inner matvec of flexible GMRES
@@ -591,6 +594,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     }
   }
   {
+    {
+      int dev = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->tiles.sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -766,6 +773,12 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
     const LevelBuf& Lb = h->lv[l];
     Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
     const Grid g = grid_of(h, l);
+    if (g.dim == 2) {
+      if ((e = launch_mg_down<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u, (C*)h->lv[l + 1].r)) !=
+          cudaSuccess)
+        return e;
+      continue;
+    }
     if ((e = launch_mg_smooth<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u)) != cudaSuccess) return e;
     if ((e = launch_mg_resid_restrict<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (const TU*)Lb.u, (C*)Lb.res,
                                               (C*)h->lv[l + 1].r)) != cudaSuccess)
@@ -777,12 +790,27 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
         cudaSuccess)
       return e;
   }
-  for (int l = l0 - 1; l >= 0; --l) {
+  // the finest level's correction is added by the inverse time transform (fine_correction)
+  for (int l = l0 - 1; l >= 1; --l) {
     if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
         cudaSuccess)
       return e;
   }
   return cudaSuccess;
+}
+
+// correction u_0 += P u_1 still owed by spatial_solve (multigrid with at least one fine level)
+template <typename TU>
+static FineCorrection<TU> fine_correction(const pc_handle* h) {
+  FineCorrection<TU> fc;
+  if (h->spatial == PC_SPATIAL_FST || h->coarse_l0 < 1) return fc;
+  const Grid g0 = grid_of(h, 0), g1 = grid_of(h, 1);
+  fc.ec = (const TU*)h->lv[1].u;
+  fc.dim = h->dim;
+  fc.mf = g0.m;
+  fc.mc = g1.m;
+  fc.npc = g1.np;
+  return fc;
 }
 
 // w = P^{-1} v; with jdev != nullptr the input is v + j*stride and the output w + j*stride
@@ -795,7 +823,8 @@ static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w, 
   if (e != cudaSuccess) return e;
   if ((e = spatial_solve<Tc, TU>(h, L)) != cudaSuccess) return e;
   return launch_tfft_inverse<Tc, TU, Tout>(L, h->ms, h->n, (const TU*)h->lv[0].u, Tables<Tc>::dpow(h),
-                                           Tables<Tc>::dinv(h), Tables<Tc>::tw(h), w, stride, jdev);
+                                           Tables<Tc>::dinv(h), Tables<Tc>::tw(h), w, stride, jdev,
+                                           fine_correction<TU>(h));
 }
 
 // FP32 preconditioner into Tout, with the handle's iterate storage
@@ -824,14 +853,14 @@ static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32
 extern "C" int pc_matvec(pc_handle* h, const double* x, double* y, void* stream) {
   if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec: null argument");
   if (x == y) return fail(PC_ERR_ARG, "pc_matvec: x and y must not overlap");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = matvec_any(h, L, x, false, y, false);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec");
 }
 
 extern "C" int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream) {
   if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec_f32: null argument");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, x, y);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec_f32");
 }
@@ -839,14 +868,14 @@ extern "C" int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stre
 extern "C" int pc_matvec_transpose(pc_handle* h, const double* x, double* y, void* stream) {
   if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec_transpose: null argument");
   if (x == y) return fail(PC_ERR_ARG, "pc_matvec_transpose: x and y must not overlap");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = matvec_any(h, L, x, false, y, true);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec_transpose");
 }
 
 extern "C" int pc_apply_precond(pc_handle* h, const double* v, double* w, void* stream) {
   if (!h || !v || !w) return fail(PC_ERR_ARG, "pc_apply_precond: null argument");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = precond64(h, L, v, w);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_apply_precond");
 }
@@ -854,14 +883,14 @@ extern "C" int pc_apply_precond(pc_handle* h, const double* v, double* w, void* 
 extern "C" int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y0, double* b,
                             void* stream) {
   if (!h || !g || !b) return fail(PC_ERR_ARG, "pc_build_rhs: null g or b");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = launch_build_rhs(L, h->ms, h->n, h->tau, h->sqrtg, f, g, y0, b);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_build_rhs");
 }
 
 extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream) {
   if (!h || !x || !lam || !grad) return fail(PC_ERR_ARG, "pc_grad_log_a: null argument");
-  Launch L{(cudaStream_t)stream, &h->prof};
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   // -tau * a_P / (2 h^2) * sum_j sum_faces [...]
   const double scale = -h->tau * 0.5 / (h->h * h->h);
   cudaError_t e =
@@ -889,7 +918,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   if (maxit < 1 || maxit > h->cap) return fail(PC_ERR_ARG, "gmres: maxit must be in [1, max_iter]");
   if (mode != PC_GMRES_RIGHT && mode != PC_GMRES_LEFT) return fail(PC_ERR_ARG, "gmres: unknown mode");
   if (mode == PC_GMRES_LEFT && h->fp32) return fail(PC_ERR_ARG, "gmres: LEFT mode needs the FP64 preconditioner");
-  Launch L{st, &h->prof};
+  Launch L{st, &h->prof, &h->tiles};
   const size_t U = h->U;
   const int ldh = h->cap + 1;
   double* nrm2 = h->scal + 0;
@@ -1031,7 +1060,7 @@ extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, doub
   if (!h || !c || !lam) return fail(PC_ERR_ARG, "pc_adjoint_solve: null argument");
   if (c == lam) return fail(PC_ERR_ARG, "pc_adjoint_solve: c and lam must not overlap");
   cudaStream_t st = (cudaStream_t)stream;
-  Launch L{st, &h->prof};
+  Launch L{st, &h->prof, &h->tiles};
   const size_t half = h->U / 2;
   // A^T lam = c  <=>  A (S lam) = S c,  S = diag(I, -I)
   PC_CUDA(cudaMemcpyAsync(h->adjbuf, c, h->U * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1136,7 +1165,7 @@ static int capture_solve(pc_handle* h, const double* b, double* x, double rtol, 
   if (cs != cudaStreamCaptureStatusActive || !G) return fail(PC_ERR_CUDA, "capture_solve: stream is not capturing");
   cudaGraphConditionalHandle hc;
   GR_CUDA(cudaGraphConditionalHandleCreate(&hc, G, 0, cudaGraphCondAssignDefault));
-  Launch L{st, nullptr};
+  Launch L{st, nullptr, &h->tiles};
   int rc;
   if ((rc = enqueue_pre(h, L, b, x, rtol, hc))) return rc;
   const cudaGraphNode_t* deps = nullptr;
@@ -1156,7 +1185,7 @@ static int capture_solve(pc_handle* h, const double* b, double* x, double rtol, 
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   GR_CUDA(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   GR_CUDA(cudaStreamBeginCaptureToGraph(h->aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  Launch LB{h->aux_stream, nullptr};
+  Launch LB{h->aux_stream, nullptr, &h->tiles};
   rc = enqueue_body(h, LB, rtol, maxit, hc);
   cudaGraph_t body_out = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->aux_stream, &body_out);
@@ -1358,4 +1387,148 @@ extern "C" const char* pc_status_string(int s) {
     case PC_ERR_UNSUPPORTED: return "unsupported";
     default: return "unknown status";
   }
+}
+
+// ---------------------------------------------------------------------------
+// tile shapes of the tunable kernels
+// ---------------------------------------------------------------------------
+static int check_tiles(const pc_tiles* t) {
+  if (t->mg_cx != 0 && t->mg_cx != 8 && t->mg_cx != 16) return fail(PC_ERR_ARG, "mg_cx must be 0, 8 or 16");
+  if (t->mg_ctas < 0 || t->mg_ctas > 64) return fail(PC_ERR_ARG, "mg_ctas must be in [0, 64]");
+  if (t->mv_tj < 0 || t->mv_tj > 4096) return fail(PC_ERR_ARG, "mv_tj must be in [0, 4096]");
+  if (t->pro_pch < 0 || t->pro_pch > 64) return fail(PC_ERR_ARG, "pro_pch must be in [0, 64]");
+  return PC_OK;
+}
+
+static void drop_graphs(pc_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+extern "C" int pc_get_tiles(const pc_handle* h, pc_tiles* out) {
+  if (!h || !out) return fail(PC_ERR_ARG, "pc_get_tiles: null argument");
+  out->mg_cx = h->tiles.mg_cx;
+  out->mg_ctas = h->tiles.mg_ctas;
+  out->mv_tj = h->tiles.mv_tj;
+  out->pro_pch = h->tiles.pro_pch;
+  return PC_OK;
+}
+
+extern "C" int pc_set_tiles(pc_handle* h, const pc_tiles* t) {
+  if (!h || !t) return fail(PC_ERR_ARG, "pc_set_tiles: null argument");
+  if (int rc = check_tiles(t)) return rc;
+  h->tiles.mg_cx = t->mg_cx;
+  h->tiles.mg_ctas = t->mg_ctas;
+  h->tiles.mv_tj = t->mv_tj;
+  h->tiles.pro_pch = t->pro_pch;
+  drop_graphs(h);  // a cached solve graph holds the old launch shapes
+  return PC_OK;
+}
+
+// mean device time of `reps` calls of f (after one untimed call); +inf on error
+template <typename F>
+static double time_reps(cudaStream_t st, int reps, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double out = HUGE_VAL;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) goto done;
+  if (f() != cudaSuccess) goto done;
+  if (cudaEventRecord(a, st) != cudaSuccess) goto done;
+  for (int i = 0; i < reps; ++i)
+    if (f() != cudaSuccess) goto done;
+  if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) goto done;
+  {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) out = ms / reps;
+  }
+done:
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return out;
+}
+
+template <typename Tc, typename TU>
+static cudaError_t spatial_any(pc_handle* h, Launch& L) {
+  return spatial_solve<Tc, TU>(h, L);
+}
+
+static cudaError_t spatial_for(pc_handle* h, Launch& L) {
+  if (!h->fp32) return spatial_any<double, double2>(h, L);
+  return h->bf16s ? spatial_any<float, __nv_bfloat162>(h, L) : spatial_any<float, float2>(h, L);
+}
+
+extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* stream) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  if (reps < 1 || reps > 100) return fail(PC_ERR_ARG, "reps must be in [1, 100]");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  GR_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(PC_ERR_ARG, "pc_autotune: stream is capturing");
+  // deterministic, finite contents for the workspace the candidates read
+  const size_t cb = h->fp32 ? sizeof(float2) : sizeof(double2);
+  GR_CUDA(cudaMemsetAsync(h->lv[0].r, 0x3e, (size_t)h->planes * h->lv[0].np * cb, st));
+  GR_CUDA(cudaMemsetAsync(h->V, 0x3e, h->U * sizeof(double), st));
+  GR_CUDA(cudaMemsetAsync(h->Z, 0x3e, h->U * (h->fp32 ? sizeof(float) : sizeof(double)), st));
+  Tiles best = h->tiles;
+  // spatial step: fused down-leg tile and grid, then the per-level plane chunk
+  if (h->spatial != PC_SPATIAL_FST) {
+    double tbest = HUGE_VAL;
+    const bool fused = h->dim == 2 && h->coarse_l0 >= 1;
+    const int cxs[2] = {8, 16};
+    const int ctas[5] = {2, 4, 8, 16, 32};
+    for (int ci = 0; ci < (fused ? 2 : 1); ++ci)
+      for (int ki = 0; ki < (fused ? 5 : 1); ++ki) {
+        Tiles t = best;
+        if (fused) {
+          t.mg_cx = cxs[ci];
+          t.mg_ctas = ctas[ki];
+        }
+        Launch L{st, nullptr, &t};
+        const double ms = time_reps(st, reps, [&] { return spatial_for(h, L); });
+        if (ms < tbest) {
+          tbest = ms;
+          best.mg_cx = t.mg_cx;
+          best.mg_ctas = t.mg_ctas;
+        }
+      }
+    const int pchs[5] = {2, 4, 8, 16, 32};
+    if (h->coarse_l0 >= 2 || (h->dim == 3 && h->coarse_l0 >= 1)) {
+      tbest = HUGE_VAL;
+      for (int pi = 0; pi < 5; ++pi) {
+        Tiles t = best;
+        t.pro_pch = pchs[pi];
+        Launch L{st, nullptr, &t};
+        const double ms = time_reps(st, reps, [&] { return spatial_for(h, L); });
+        if (ms < tbest) {
+          tbest = ms;
+          best.pro_pch = t.pro_pch;
+        }
+      }
+    }
+  }
+  // the all-at-once matvec of the Arnoldi step: time blocks per thread
+  {
+    double tbest = HUGE_VAL;
+    const int tjs[5] = {8, 16, 32, 64, 128};
+    for (int ti = 0; ti < 5; ++ti) {
+      if (tjs[ti] > h->n && ti > 0) break;
+      Tiles t = best;
+      t.mv_tj = tjs[ti];
+      Launch L{st, nullptr, &t};
+      const double ms = time_reps(st, reps, [&] {
+        return h->fp32 ? launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, (const float*)h->Z,
+                                          h->V + h->U)
+                       : launch_matvec<double>(L, grid_of(h, 0), h->n, Stencil<double>{h->lv[0].w64, h->lv[0].d64},
+                                               h->alpha, (const double*)h->Z, h->V + h->U, false);
+      });
+      if (ms < tbest) {
+        tbest = ms;
+        best.mv_tj = t.mv_tj;
+      }
+    }
+  }
+  GR_CUDA(cudaGetLastError());
+  h->tiles = best;
+  drop_graphs(h);
+  if (chosen) pc_get_tiles(h, chosen);
+  return PC_OK;
 }

@@ -133,6 +133,7 @@ enum KernelClass {
   KC_GRAD,
   KC_REORTH,  // gated re-orthogonalisation passes (bytes booked only when they ran)
   KC_MG_COARSE,
+  KC_MG_DOWN,  // fused smooth + residual + restriction of one level
   KC_COUNT
 };
 const char* kernel_class_name(int kc);
@@ -158,9 +159,20 @@ struct Prof {
   ~Prof();
 };
 
+// Tile shapes of the tunable kernels, 0 = the built-in default.  Chosen per
+// problem by pc_autotune (timed candidates) or set from a stored table.
+struct Tiles {
+  int mg_cx = 0;    // fused 2D down leg: coarse points per tile axis (8 or 16)
+  int mg_ctas = 0;  // fused 2D down leg: CTAs per SM its grid is sized for (sets planes per CTA per level)
+  int mv_tj = 0;    // matvec kernels: time blocks per thread
+  int pro_pch = 0;  // prolongation and per-level (3D) multigrid kernels: planes per CTA
+  int sms = 0;      // SMs of the device (set at setup)
+};
+
 struct Launch {
   cudaStream_t stream;
   Prof* prof;
+  const Tiles* tiles = nullptr;
   // record around one kernel launch; `bytes`/`flops` are algorithmic figures
   cudaEvent_t ev_a = nullptr;
   void begin(int kc);
@@ -209,10 +221,21 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
                                 const int* jdev = nullptr);
 // inverse scaled time FFT + butterfly: spectral planes (stored as TU) -> w (Tout [2][n][ms])
 // With jdev != nullptr the output is w + (*jdev) * wstride.
+// Last step of the multigrid up leg, done while the inverse time transform loads
+// the finest level: u_f + P e_c, P the (bi/tri)linear prolongation from the next
+// coarser level (mc = (mf - 1) / 2 points per axis, zero outside).  ec == nullptr:
+// the planes are used as they are.
+template <typename TU>
+struct FineCorrection {
+  const TU* ec = nullptr;
+  int dim = 0, mf = 0, mc = 0;
+  int64_t npc = 0;
+};
+
 template <typename Tc, typename TU, typename Tout>
 cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
                                 const typename Cx<Tc>::t* tw, Tout* w, size_t wstride = 0,
-                                const int* jdev = nullptr);
+                                const int* jdev = nullptr, FineCorrection<TU> fc = FineCorrection<TU>());
 
 // FST: one DST-I along `axis` of every plane (out = S in), and the spectral divide
 template <typename Tc>
@@ -230,6 +253,12 @@ template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                                      const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
                                      typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc);
+template <typename Tc, typename TU>
+cudaError_t launch_mg_down(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
+                           const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u,
+                           typename Cx<Tc>::t* rc, int cx = 0, int pch = 0);
+int mg_down_default_cx(int tc_bytes);
+int mg_down_default_pch(int m, int planes, int cx, int ctas_per_sm, int sms);
 template <typename Tc, typename TU>
 cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* ec, TU* uf);
 template <typename Tc, typename TU>

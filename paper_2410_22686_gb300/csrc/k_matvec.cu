@@ -100,12 +100,19 @@ __global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, 
 
 }  // namespace
 
+// time blocks per thread: the tuned value, else 32 (a thread carries its time
+// neighbour in registers, so longer chunks re-read fewer x values)
+static int time_chunk(const Launch& L, int n) {
+  int tj = L.tiles && L.tiles->mv_tj > 0 ? L.tiles->mv_tj : 32;
+  return tj < n ? tj : n;
+}
+
 template <typename Tin>
 cudaError_t launch_matvec(Launch& L, const Grid& g, int n, const Stencil<double>& st, double alpha,
                           const Tin* x, double* y, bool transpose, size_t xstride, size_t ystride,
                           const int* jdev) {
   const int threads = 256;
-  const int tj = n < 32 ? n : 32;
+  const int tj = time_chunk(L, n);
   dim3 grid((unsigned)((g.np + threads - 1) / threads), (unsigned)((n + tj - 1) / tj));
   const double U = 2.0 * (double)n * (double)g.np;
   const double bytes = U * (sizeof(Tin) + sizeof(double)) + (2.0 * g.dim + 1) * g.np * 8.0;
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict_
 cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, const float2* diag, float2 alpha,
                              const float* x, double* y, size_t xstride, size_t ystride, const int* jdev) {
   const int threads = 256;
-  const int tj = n < 32 ? n : 32;
+  const int tj = time_chunk(L, n);
   dim3 grid((unsigned)((g.np + threads - 1) / threads), (unsigned)((n + tj - 1) / tj));
   const double U = 2.0 * (double)n * (double)g.np;
   const double bytes = U * (sizeof(float) + sizeof(double)) + (2.0 * g.dim + 1) * g.np * 8.0;

@@ -17,7 +17,7 @@ namespace pcopt {
 
 namespace {
 
-constexpr int kPlaneChunk = 8;
+constexpr int kPlaneChunk = 8;  // default planes per CTA
 
 template <typename Tc>
 __device__ __forceinline__ typename Cx<Tc>::t inv_diag(typename Cx<Tc>::t sig, Tc dg) {
@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
                                                         TU* __restrict__ u,
                                                         const Tc* __restrict__ w, const Tc* __restrict__ diag,
                                                         const typename Cx<Tc>::t* __restrict__ sigma, int m,
-                                                        int64_t np, int planes) {
+                                                        int64_t np, int planes, int pch) {
   typedef typename Cx<Tc>::t C;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= np) return;
-  const int p0 = blockIdx.y * kPlaneChunk;
-  const int p1 = min(planes, p0 + kPlaneChunk);
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
   const Coord c = coord_of(s, m, DIM);
   const bool red = ((c.i1 + c.i2 + c.i3 + DIM) & 1) == 0;
   const Tc dg = diag[s];
@@ -146,12 +146,12 @@ __global__ void __launch_bounds__(256) mg_residual_kernel(const typename Cx<Tc>:
                                                           typename Cx<Tc>::t* __restrict__ res,
                                                           const Tc* __restrict__ w, const Tc* __restrict__ diag,
                                                           const typename Cx<Tc>::t* __restrict__ sigma, int m,
-                                                          int64_t np, int planes) {
+                                                          int64_t np, int planes, int pch) {
   typedef typename Cx<Tc>::t C;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= np) return;
-  const int p0 = blockIdx.y * kPlaneChunk;
-  const int p1 = min(planes, p0 + kPlaneChunk);
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
   const Coord c = coord_of(s, m, DIM);
   int64_t off[2 * DIM];
   bool ex[2 * DIM];
@@ -197,12 +197,12 @@ __global__ void __launch_bounds__(256) mg_residual_kernel(const typename Cx<Tc>:
 template <typename Tc, int DIM>
 __global__ void __launch_bounds__(256) mg_restrict_kernel(const typename Cx<Tc>::t* __restrict__ res,
                                                           typename Cx<Tc>::t* __restrict__ rc, int mf, int mc,
-                                                          int64_t npf, int64_t npc, int planes) {
+                                                          int64_t npf, int64_t npc, int planes, int pch) {
   typedef typename Cx<Tc>::t C;
   const int64_t sc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sc >= npc) return;
-  const int p0 = blockIdx.y * kPlaneChunk;
-  const int p1 = min(planes, p0 + kPlaneChunk);
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
   const Coord c = coord_of(sc, mc, DIM);
   // 0-based fine centre of coarse (0-based) c is 2c+1
   const int f1 = 2 * c.i1 + 1, f2 = 2 * c.i2 + 1, f3 = 2 * c.i3 + 1;
@@ -226,79 +226,22 @@ __global__ void __launch_bounds__(256) mg_restrict_kernel(const typename Cx<Tc>:
   }
 }
 
-// u_f += P e_c, P = tensor product of 1D linear interpolation
-template <typename Tc, typename TU, int DIM>
-__global__ void __launch_bounds__(256) mg_prolong_kernel(const TU* __restrict__ ec, TU* __restrict__ uf, int mf, int mc,
-                                                         int64_t npf, int64_t npc, int planes) {
-  typedef typename Cx<Tc>::t C;
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= npf) return;
-  const int p0 = blockIdx.y * kPlaneChunk;
-  const int p1 = min(planes, p0 + kPlaneChunk);
-  const Coord c = coord_of(s, mf, DIM);
-  // per axis: up to two coarse indices with weights
-  int ci[3][2];
-  Tc cw[3][2];
-  int cnt[3];
-  const int fi[3] = {c.i1, c.i2, c.i3};
-  for (int a = 0; a < DIM; ++a) {
-    const int f = fi[a];
-    if (f & 1) {
-      ci[a][0] = (f - 1) >> 1;
-      cw[a][0] = Tc(1);
-      cnt[a] = 1;
-    } else {
-      cnt[a] = 0;
-      const int lo = (f >> 1) - 1, hi = f >> 1;
-      if (lo >= 0) {
-        ci[a][cnt[a]] = lo;
-        cw[a][cnt[a]] = Tc(0.5);
-        cnt[a]++;
-      }
-      if (hi < mc) {
-        ci[a][cnt[a]] = hi;
-        cw[a][cnt[a]] = Tc(0.5);
-        cnt[a]++;
-      }
-    }
-  }
-  if (DIM == 2) {
-    cnt[2] = 1;
-    ci[2][0] = 0;
-    cw[2][0] = Tc(1);
-  }
-  for (int p = p0; p < p1; ++p) {
-    const TU* ep = ec + (int64_t)p * npc;
-    C acc = czero<Tc>();
-    for (int a3 = 0; a3 < cnt[2]; ++a3)
-      for (int a2 = 0; a2 < cnt[1]; ++a2)
-        for (int a1 = 0; a1 < cnt[0]; ++a1) {
-          const Tc wgt = cw[0][a1] * cw[1][a2] * cw[2][a3];
-          const int64_t q = ((int64_t)ci[2][a3] * mc + ci[1][a2]) * mc + ci[0][a1];
-          const C v = ldc(ep, q);
-          acc.x = fma(wgt, v.x, acc.x);
-          acc.y = fma(wgt, v.y, acc.y);
-        }
-    const int64_t o = (int64_t)p * npf + s;
-    stc(uf, o, ldc(uf, o) + acc);
-  }
-}
-
-// The same correction, one thread per coarse cell: cell (I[,J[,K]]), each index in
+// u_f += P e_c (P = tensor product of 1D linear interpolation), one thread per coarse cell: cell (I[,J[,K]]), each index in
 // [-1, mc-1], owns the fine points 2I+1 and 2I+2 per axis (0-based; 2I+1 sits on
 // coarse point I, 2I+2 halfway between I and I+1), so every fine point is written
 // exactly once; the 2^d corner values are loaded once and coarse values outside
 // [0, mc) are the zero boundary.
 template <typename Tc, typename TU, int DIM>
 __global__ void __launch_bounds__(256) mg_prolong_cell_kernel(const TU* __restrict__ ec, TU* __restrict__ uf, int mf,
-                                                              int mc, int64_t npf, int64_t npc, int planes) {
+                                                              int mc, int64_t npf, int64_t npc, int planes,
+                                                              int pch) {
   typedef typename Cx<Tc>::t C;
   const int mc1 = mc + 1;
   const int64_t ncell = DIM == 2 ? (int64_t)mc1 * mc1 : (int64_t)mc1 * mc1 * mc1;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncell) return;
-  const int p0 = blockIdx.y * kPlaneChunk;
-  const int p1 = min(planes, p0 + kPlaneChunk);
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
   const int I = (int)(cell % mc1) - 1;
   const int J = (int)((cell / mc1) % mc1) - 1;
   const int K = DIM == 3 ? (int)(cell / ((int64_t)mc1 * mc1)) - 1 : 0;
@@ -365,8 +308,13 @@ __global__ void mg_coarsest_kernel(const Tc* __restrict__ diag, const typename C
   stc(u, p, cmul(r[p], inv_diag<Tc>(sigma[p], diag[0])));
 }
 
-dim3 plane_grid(int64_t np, int planes) {
-  return dim3((unsigned)((np + 255) / 256), (unsigned)((planes + kPlaneChunk - 1) / kPlaneChunk));
+dim3 plane_grid(int64_t np, int planes, int pch) {
+  return dim3((unsigned)((np + 255) / 256), (unsigned)((planes + pch - 1) / pch));
+}
+
+int plane_chunk(const Launch& L) {
+  const int v = L.tiles ? L.tiles->pro_pch : 0;
+  return v > 0 ? v : kPlaneChunk;
 }
 
 }  // namespace
@@ -394,15 +342,16 @@ cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* la
 template <typename Tc, typename TU>
 cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                              const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u) {
+  const int pch = plane_chunk(L);
   const double cs = 0.5 * (sizeof(typename Cx<Tc>::t) + sizeof(TU));
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_SMOOTH);
   if (g.dim == 2)
-    mg_smooth_kernel<Tc, TU, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
-                                                                            planes);
+    mg_smooth_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
+                                                                            planes, pch);
   else
-    mg_smooth_kernel<Tc, TU, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
-                                                                            planes);
+    mg_smooth_kernel<Tc, TU, 3><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
+                                                                            planes, pch);
   return L.end(KC_MG_SMOOTH, 2.0 * tot * cs, tot * (12.0 + 10.0 * g.dim));
 }
 
@@ -410,29 +359,31 @@ template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                                      const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
                                      typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc) {
+  const int pch = plane_chunk(L);
   const double cs = sizeof(typename Cx<Tc>::t);
   const int mc = (g.m - 1) / 2;
   const int64_t npc = g.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_RESID_RESTRICT);
   if (g.dim == 2)
-    mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
-                                                                              g.np, planes);
+    mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
+                                                                              g.np, planes, pch);
   else
-    mg_residual_kernel<Tc, TU, 3><<<plane_grid(g.np, planes), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
-                                                                              g.np, planes);
+    mg_residual_kernel<Tc, TU, 3><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
+                                                                              g.np, planes, pch);
   cudaError_t e = L.end(KC_MG_RESID_RESTRICT, 3.0 * tot * cs, tot * (8.0 + 4.0 * g.dim));
   if (e != cudaSuccess) return e;
   L.begin(KC_MG_RESID_RESTRICT);
   if (g.dim == 2)
-    mg_restrict_kernel<Tc, 2><<<plane_grid(npc, planes), 256, 0, L.stream>>>(res, rc, g.m, mc, g.np, npc, planes);
+    mg_restrict_kernel<Tc, 2><<<plane_grid(npc, planes, pch), 256, 0, L.stream>>>(res, rc, g.m, mc, g.np, npc, planes, pch);
   else
-    mg_restrict_kernel<Tc, 3><<<plane_grid(npc, planes), 256, 0, L.stream>>>(res, rc, g.m, mc, g.np, npc, planes);
+    mg_restrict_kernel<Tc, 3><<<plane_grid(npc, planes, pch), 256, 0, L.stream>>>(res, rc, g.m, mc, g.np, npc, planes, pch);
   return L.end(KC_MG_RESID_RESTRICT, tot * cs + (double)npc * planes * cs, (double)npc * planes * (g.dim == 2 ? 36 : 108));
 }
 
 template <typename Tc, typename TU>
 cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* ec, TU* uf) {
+  const int pch = plane_chunk(L);
   const double cs = sizeof(TU);
   const int mc = (gf.m - 1) / 2;
   const int64_t npc = gf.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
@@ -440,11 +391,11 @@ cudaError_t launch_mg_prolong(Launch& L, const Grid& gf, int planes, const TU* e
   const int64_t ncell = gf.dim == 2 ? (int64_t)(mc + 1) * (mc + 1) : (int64_t)(mc + 1) * (mc + 1) * (mc + 1);
   L.begin(KC_MG_PROLONG);
   if (gf.dim == 2)
-    mg_prolong_cell_kernel<Tc, TU, 2><<<plane_grid(ncell, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
-                                                                                      planes);
+    mg_prolong_cell_kernel<Tc, TU, 2><<<plane_grid(ncell, planes, pch), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
+                                                                                      planes, pch);
   else
-    mg_prolong_cell_kernel<Tc, TU, 3><<<plane_grid(ncell, planes), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
-                                                                                      planes);
+    mg_prolong_cell_kernel<Tc, TU, 3><<<plane_grid(ncell, planes, pch), 256, 0, L.stream>>>(ec, uf, gf.m, mc, gf.np, npc,
+                                                                                      planes, pch);
   return L.end(KC_MG_PROLONG, 2.0 * tot * cs + (double)npc * planes * cs, tot * 8.0);
 }
 

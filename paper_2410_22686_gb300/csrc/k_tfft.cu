@@ -25,6 +25,64 @@ namespace {
 
 __device__ __forceinline__ int bitrev(int j, int logn) { return logn ? (int)(__brev((unsigned)j) >> (32 - logn)) : 0; }
 
+// Parents of fine point s in the next coarser level and their linear weights,
+// per axis: odd f sits on coarse point (f-1)/2 (weight 1), even f halfway between
+// f/2-1 and f/2 (1/2 each, a parent outside [0, mc) is the zero boundary).
+template <typename Tc, typename TU>
+struct Parents {
+  int o[3][2];
+  Tc wt[3][2];
+  __device__ __forceinline__ void init(const FineCorrection<TU>& fc, int64_t s) {
+    int f[3];
+    f[0] = (int)(s % fc.mf);
+    const int64_t r = s / fc.mf;
+    f[1] = (int)(fc.dim == 2 ? r : r % fc.mf);
+    f[2] = fc.dim == 3 ? (int)(r / fc.mf) : 0;
+    int stride = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= fc.dim) {
+        o[a][0] = o[a][1] = 0;
+        wt[a][0] = Tc(1);
+        wt[a][1] = Tc(0);
+        continue;
+      }
+      if (f[a] & 1) {
+        o[a][0] = o[a][1] = ((f[a] - 1) >> 1) * stride;
+        wt[a][0] = Tc(1);
+        wt[a][1] = Tc(0);
+      } else {
+        int lo = (f[a] >> 1) - 1, hi = f[a] >> 1;
+        wt[a][0] = lo >= 0 ? Tc(0.5) : Tc(0);
+        wt[a][1] = hi < fc.mc ? Tc(0.5) : Tc(0);
+        if (lo < 0) lo = hi;
+        if (hi >= fc.mc) hi = lo;
+        o[a][0] = lo * stride;
+        o[a][1] = hi * stride;
+      }
+      stride *= fc.mc;
+    }
+  }
+  __device__ __forceinline__ typename Cx<Tc>::t at(const FineCorrection<TU>& fc, int p) const {
+    typedef typename Cx<Tc>::t C;
+    const TU* e = fc.ec + (int64_t)p * fc.npc;
+    C acc = czero<Tc>();
+    for (int c2 = 0; c2 < (fc.dim == 3 ? 2 : 1); ++c2)
+#pragma unroll
+      for (int c1 = 0; c1 < 2; ++c1)
+#pragma unroll
+        for (int c0 = 0; c0 < 2; ++c0) {
+          const Tc w = wt[2][c2] * wt[1][c1] * wt[0][c0];
+          if (w != Tc(0)) {
+            const C v = ldc(e, o[2][c2] + o[1][c1] + o[0][c0]);
+            acc.x = fma(w, v.x, acc.x);
+            acc.y = fma(w, v.y, acc.y);
+          }
+        }
+    return acc;
+  }
+};
+
 template <typename Tc, bool INVERSE>
 __device__ __forceinline__ void fft_columns(typename Cx<Tc>::t* z, const typename Cx<Tc>::t* __restrict__ tw, int n,
                                             int TS) {
@@ -93,7 +151,7 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
                                                            const Tc* __restrict__ dpow,
                                                            const typename Cx<Tc>::t* __restrict__ tw,
                                                            Tout* __restrict__ w, int64_t ms, int n, int logn,
-                                                           int TS) {
+                                                           int TS, FineCorrection<TU> fc) {
   typedef typename Cx<Tc>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* z = reinterpret_cast<C*>(smem_raw);
@@ -107,6 +165,12 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
     if (s < ms) {
       sa = ldc(spec, (int64_t)(2 * k) * ms + s);      // hat w2[k]
       sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);  // hat w1[n-k] = conj(hat w1[k])
+      if (fc.ec) {
+        Parents<Tc, TU> par;
+        par.init(fc, s);
+        sa = sa + par.at(fc, 2 * k);
+        sb = sb + par.at(fc, 2 * k + 1);
+      }
     }
     // Y[k] = hat w1[k] + i hat w2[k] with hat w1[k] = conj(sb), hat w2[k] = sa
     z[bitrev(k, logn) * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
@@ -251,7 +315,7 @@ __global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict
                                                             const Tc* __restrict__ dinv,
                                                             const typename Cx<Tc>::t* __restrict__ tw,
                                                             Tout* __restrict__ w, int64_t ms, size_t wstride,
-                                                            const int* __restrict__ jdev) {
+                                                            const int* __restrict__ jdev, FineCorrection<TU> fc) {
   typedef typename Cx<Tc>::t C;
   constexpr int n = N1 * N2;
   constexpr int COLS = 256 / N1;
@@ -263,11 +327,17 @@ __global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict
   const bool valid = s < ms;
   if (jdev) w += (size_t)(*jdev) * wstride;  // output = basis vector j
   // Y[k] = hat w1[k] + i hat w2[k] for all k from the half spectrum
+  Parents<Tc, TU> par;
+  if (fc.ec && valid) par.init(fc, s);
   for (int k = r; k <= n / 2; k += N1) {
     C sa = czero<Tc>(), sb = czero<Tc>();
     if (valid) {
       sa = ldc(spec, (int64_t)(2 * k) * ms + s);
       sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
+      if (fc.ec) {
+        sa = sa + par.at(fc, 2 * k);
+        sb = sb + par.at(fc, 2 * k + 1);
+      }
     }
     sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
     if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
@@ -363,7 +433,8 @@ template <typename Tc, typename TU, typename Tout>
 __global__ void __launch_bounds__(256) tdft_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
                                                            const Tc* __restrict__ dinv,
                                                            const typename Cx<Tc>::t* __restrict__ tw,
-                                                           Tout* __restrict__ w, int64_t ms, int n, int TS) {
+                                                           Tout* __restrict__ w, int64_t ms, int n, int TS,
+                                                           FineCorrection<TU> fc) {
   typedef typename Cx<Tc>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* z = reinterpret_cast<C*>(smem_raw);  // [n][TS]
@@ -376,6 +447,12 @@ __global__ void __launch_bounds__(256) tdft_inverse_kernel(const TU* __restrict_
     if (s < ms) {
       sa = ldc(spec, (int64_t)(2 * k) * ms + s);
       sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
+      if (fc.ec) {
+        Parents<Tc, TU> par;
+        par.init(fc, s);
+        sa = sa + par.at(fc, 2 * k);
+        sb = sb + par.at(fc, 2 * k + 1);
+      }
     }
     z[k * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
     if (k > 0 && 2 * k < n) z[(n - k) * TS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
@@ -447,14 +524,14 @@ cudaError_t fwd4(Launch& L, int64_t ms, const Tin* v, const Tc* dpow, const Tc* 
 
 template <typename Tc, typename TU, typename Tout, int N1, int N2>
 cudaError_t inv4(Launch& L, int64_t ms, const TU* spec, const Tc* dpow, const Tc* dinv, const typename Cx<Tc>::t* tw,
-                 Tout* w, size_t wstride, const int* jdev) {
+                 Tout* w, size_t wstride, const int* jdev, const FineCorrection<TU>& fc) {
   constexpr int COLS = 256 / N1;
   const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
   cudaError_t e = cudaFuncSetAttribute(tfft4_inverse_kernel<Tc, TU, Tout, N1, N2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   tfft4_inverse_kernel<Tc, TU, Tout, N1, N2><<<(unsigned)((ms + COLS - 1) / COLS), 256, smem, L.stream>>>(
-      spec, dpow, dinv, tw, w, ms, wstride, jdev);
+      spec, dpow, dinv, tw, w, ms, wstride, jdev, fc);
   return cudaGetLastError();
 }
 
@@ -489,22 +566,23 @@ cudaError_t fwd4_dispatch(Launch& L, int64_t ms, int n, const Tin* v, const Tc* 
 
 template <typename Tc, typename TU, typename Tout>
 cudaError_t inv4_dispatch(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
-                          const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev) {
+                          const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev,
+                          const FineCorrection<TU>& fc) {
   switch (n) {
-    case 1: return inv4<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 2: return inv4<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 4: return inv4<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 8: return inv4<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 16: return inv4<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 32: return inv4<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 64: return inv4<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 128: return inv4<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
-    case 256: return inv4<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+    case 1: return inv4<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 2: return inv4<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 4: return inv4<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 8: return inv4<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 16: return inv4<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 32: return inv4<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 64: return inv4<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 128: return inv4<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 256: return inv4<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
     case 512:
-      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
       break;
     case 1024:
-      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev);
+      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
       break;
   }
   return cudaErrorInvalidValue;
@@ -550,7 +628,10 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
 
 template <typename Tc, typename TU, typename Tout>
 cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
-                                const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev) {
+                                const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev,
+                                FineCorrection<TU> fc) {
+  // bytes of the fused correction: the coarse planes once
+  const double cbytes = fc.ec ? (double)(n / 2 + 1) * 2.0 * fc.npc * sizeof(TU) : 0.0;
   const bool pow2 = (n & (n - 1)) == 0;
   if (jdev && (n > four_step_max<Tc>() || !pow2)) return cudaErrorNotSupported;
   if (!pow2) {
@@ -562,15 +643,16 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
     const int nf = n / 2 + 1;
     L.begin(KC_TFFT_INV);
     tdft_inverse_kernel<Tc, TU, Tout><<<(unsigned)((ms + TS - 1) / TS), 256, smem, L.stream>>>(spec, dpow, dinv, tw, w,
-                                                                                            ms, n, TS);
-    return L.end(KC_TFFT_INV, 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout), 8.0 * (double)n * n * ms);
+                                                                                            ms, n, TS, fc);
+    return L.end(KC_TFFT_INV, 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout) + cbytes,
+                 8.0 * (double)n * n * ms);
   }
   if (n <= four_step_max<Tc>()) {
     const int nf = n / 2 + 1;
-    const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout);
+    const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout) + cbytes;
     const double flops = (double)ms * (5.0 * n * ilog2(n) + 4.0 * n);
     L.begin(KC_TFFT_INV);
-    inv4_dispatch<Tc, TU, Tout>(L, ms, n, spec, dpow, dinv, tw, w, wstride, jdev);
+    inv4_dispatch<Tc, TU, Tout>(L, ms, n, spec, dpow, dinv, tw, w, wstride, jdev, fc);
     return L.end(KC_TFFT_INV, bytes, flops);
   }
   const int TS = pick_ts<Tc>(n);
@@ -580,10 +662,10 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ms + TS - 1) / TS);
   const int nf = n / 2 + 1;
-  const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout);
+  const double bytes = 2.0 * nf * ms * sizeof(TU) + 2.0 * n * ms * sizeof(Tout) + cbytes;
   const double flops = (double)ms * (5.0 * n * ilog2(n) + 4.0 * n);
   L.begin(KC_TFFT_INV);
-  tfft_inverse_kernel<Tc, TU, Tout><<<blocks, 256, smem, L.stream>>>(spec, dpow, tw, w, ms, n, ilog2(n), TS);
+  tfft_inverse_kernel<Tc, TU, Tout><<<blocks, 256, smem, L.stream>>>(spec, dpow, tw, w, ms, n, ilog2(n), TS, fc);
   return L.end(KC_TFFT_INV, bytes, flops);
 }
 
@@ -593,7 +675,8 @@ template cudaError_t launch_tfft_forward<float>(Launch&, int64_t, int, const dou
                                                 const float2*, float2*, size_t, const int*);
 #define PCOPT_INV(Tc, TU, Tout)                                                                                  \
   template cudaError_t launch_tfft_inverse<Tc, TU, Tout>(Launch&, int64_t, int, const TU*, const Tc*, const Tc*, \
-                                                         const Cx<Tc>::t*, Tout*, size_t, const int*);
+                                                         const Cx<Tc>::t*, Tout*, size_t, const int*,         \
+                                                         FineCorrection<TU>);
 PCOPT_INV(double, double2, double)
 PCOPT_INV(float, float2, double)
 PCOPT_INV(float, float2, float)

@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 import torch
 
-from . import capi
+from . import capi, tuning
 
 _SPATIAL = {"auto": capi.PC_SPATIAL_AUTO, "fst": capi.PC_SPATIAL_FST, "mg": capi.PC_SPATIAL_MG}
 _PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": capi.PC_PREC_MIXED_FP32,
@@ -36,7 +36,10 @@ class Solver:
 
     def __init__(self, dim: int, m1: int, n: int, T: float, gamma: float, eps: float,
                  a_nodes: np.ndarray | None = None, spatial: str = "auto", precision: str = "fp64",
-                 max_iter: int = 60):
+                 max_iter: int = 60, tiles: str | dict | None = "table"):
+        """tiles: "table" applies the stored autotune table's entry for this shape
+        (if any), "auto" runs the autotuner now, a dict sets the shapes, None keeps
+        the built-in defaults."""
         self.lib = capi.load()
         if not torch.cuda.is_available():
             raise RuntimeError("pcopt needs a CUDA device")
@@ -56,6 +59,18 @@ class Solver:
         self.ms = m1 ** dim
         self.vec_len = 2 * n * self.ms
         self.tau = T / (n + 1)
+        self.precision = precision
+        self.spatial = spatial
+        if tiles == "table":
+            entry = tuning.lookup(dim, m1, n, precision, spatial)
+            if entry:
+                self.set_tiles(**entry)
+        elif tiles == "auto":
+            self.autotune()
+        elif isinstance(tiles, dict):
+            self.set_tiles(**tiles)
+        elif tiles is not None:
+            raise ValueError("tiles must be 'table', 'auto', a dict or None")
 
     # ---------------------------------------------------------------- lifetime
     def close(self):
@@ -175,6 +190,27 @@ class Solver:
         g = torch.empty((self.m1,) * self.dim, dtype=torch.float64, device="cuda") if out is None else out
         capi.check(self.lib.pc_grad_log_a(self.h, _ptr(x), _ptr(lam), _ptr(g), _stream()))
         return g
+
+    # ---------------------------------------------------------------- tile shapes
+    def get_tiles(self) -> dict:
+        t = capi.pc_tiles()
+        capi.check(self.lib.pc_get_tiles(self.h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in capi.pc_tiles._fields_}
+
+    def set_tiles(self, **shape):
+        cur = self.get_tiles()
+        unknown = set(shape) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown tile fields {sorted(unknown)}")
+        cur.update(shape)
+        t = capi.pc_tiles(**cur)
+        capi.check(self.lib.pc_set_tiles(self.h, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Time candidate tile shapes on this handle and keep the fastest (pc_autotune)."""
+        t = capi.pc_tiles()
+        capi.check(self.lib.pc_autotune(self.h, reps, ctypes.byref(t), _stream()))
+        return {f: getattr(t, f) for f, _ in capi.pc_tiles._fields_}
 
     # ---------------------------------------------------------------- instrumentation
     def profile(self, on=True):

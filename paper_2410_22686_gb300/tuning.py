@@ -1,0 +1,120 @@
+"""Stored tile shapes per problem shape, written by the autotuner.
+
+``pc_autotune`` times candidate tile shapes of the tunable kernels on one handle
+(fused multigrid down leg: tile width and CTAs per SM; prolongation planes per
+CTA; matvec time blocks per thread) and keeps the fastest.  This module keeps
+the chosen shapes in a JSON table next to the package, keyed by
+(dim, m1, n, precision), so that ``Solver(..., tiles="table")`` (the default)
+starts with the tuned shapes without re-timing.  Shapes missing from the table
+run with the built-in defaults.
+
+Regenerate the table on the target GPU with
+
+    python -m paper_2410_22686_gb300.tuning --write [--reps 5] [--out PATH]
+
+which autotunes every workload shape listed in ``WORKLOADS``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiles_gb300.json")
+FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch")
+
+# (dim, m1, n, precision): the bench and test workloads
+WORKLOADS = (
+    [(2, 255, 256, p) for p in ("mixed", "bf16s", "fp64")]
+    + [(3, 63, 128, p) for p in ("mixed", "bf16s", "fp64")]
+    + [(2, 127, 128, p) for p in ("fp64", "mixed")]
+    + [(2, 31, 32, "fp64")]
+    + [(2, m, n, "mixed") for m in (31, 63, 127, 255) for n in (16, 64, 256, 512)]
+)
+
+_cache: dict | None = None
+
+
+_PREC_ALIAS = {"fp32": "mixed"}
+
+
+def key(dim: int, m1: int, n: int, precision: str) -> str:
+    return f"{dim}d_m{m1}_n{n}_{_PREC_ALIAS.get(precision, precision)}"
+
+
+def load(path: str = TABLE) -> dict:
+    """The table as {key: {field: value}} (empty when there is no file)."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        data = json.load(fh)
+    return data.get("entries", {})
+
+
+def lookup(dim: int, m1: int, n: int, precision: str, spatial: str | None = None) -> dict | None:
+    """Tile shapes stored for this problem shape, or None."""
+    global _cache
+    if _cache is None:
+        _cache = load()
+    e = _cache.get(key(dim, m1, n, precision))
+    if not e:
+        return None
+    return {f: int(e[f]) for f in FIELDS if f in e}
+
+
+def _tune_one(dim, m1, n, precision, reps):
+    import numpy as np
+    import torch
+
+    from .solver import Solver
+
+    tau = 1.0 / (n + 1)
+    M = m1 + 2
+    x = np.linspace(0.0, 1.0, M)
+    if dim == 2:
+        X1, X2 = np.meshgrid(x, x, indexing="xy")
+        a = 1.0 + 0.5 * np.sin(2 * np.pi * X1) * np.cos(2 * np.pi * X2)
+    else:
+        X1, X2, X3 = np.meshgrid(x, x, x, indexing="ij")
+        a = np.exp(0.25 * np.sin(2 * np.pi * X1) * np.cos(2 * np.pi * X2) * np.sin(np.pi * X3))
+    spatial = "fst" if (dim == 2 and m1 == 31 and n == 32) else "mg"
+    s = Solver(dim, m1, n, 1.0, 1e-4, float(np.sqrt(tau)), a_nodes=None if spatial == "fst" else a,
+               spatial=spatial, precision=precision, max_iter=2, tiles=None)
+    try:
+        t = s.autotune(reps)
+        torch.cuda.synchronize()
+        return t
+    finally:
+        s.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--write", action="store_true", help="autotune every workload shape and write the table")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--out", default=TABLE)
+    args = ap.parse_args(argv)
+    if not args.write:
+        print(json.dumps(load(args.out), indent=1, sort_keys=True))
+        return 0
+    import torch
+
+    entries = {}
+    for (dim, m1, n, prec) in WORKLOADS:
+        t = _tune_one(dim, m1, n, prec, args.reps)
+        entries[key(dim, m1, n, prec)] = t
+        print(key(dim, m1, n, prec), t, flush=True)
+    doc = {"device": torch.cuda.get_device_name(0), "reps": args.reps,
+           "fields": {"mg_cx": "fused 2D down-leg tile (coarse points per axis)",
+                      "mg_ctas": "fused down-leg CTAs per SM",
+                      "mv_tj": "matvec time blocks per thread",
+                      "pro_pch": "prolongation / 3D per-level planes per CTA"},
+           "entries": entries}
+    with open(args.out, "w") as fh:
+        json.dump(doc, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -1,0 +1,41 @@
+"""The stored autotune table (host logic only; no GPU)."""
+import json
+
+from paper_2410_22686_gb300 import capi, tuning
+
+
+def test_fields_match_the_c_struct():
+    assert tuple(f for f, _ in capi.pc_tiles._fields_) == tuning.FIELDS
+
+
+def test_key_normalises_precision_aliases():
+    assert tuning.key(2, 255, 256, "fp32") == tuning.key(2, 255, 256, "mixed") == "2d_m255_n256_mixed"
+    assert tuning.key(3, 63, 128, "bf16s") == "3d_m63_n128_bf16s"
+
+
+def test_lookup_reads_entries(tmp_path, monkeypatch):
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"entries": {"2d_m15_n16_fp64": {"mg_cx": 8, "mg_ctas": 4, "mv_tj": 16,
+                                                                  "pro_pch": 2}}}))
+    monkeypatch.setattr(tuning, "_cache", tuning.load(str(path)))
+    assert tuning.lookup(2, 15, 16, "fp64") == {"mg_cx": 8, "mg_ctas": 4, "mv_tj": 16, "pro_pch": 2}
+    assert tuning.lookup(2, 15, 32, "fp64") is None
+
+
+def test_missing_table_is_empty(tmp_path):
+    assert tuning.load(str(tmp_path / "none.json")) == {}
+
+
+def test_workloads_cover_the_bench_shapes():
+    keys = {tuning.key(*w) for w in tuning.WORKLOADS}
+    for k in ("2d_m255_n256_mixed", "2d_m255_n256_fp64", "2d_m255_n256_bf16s", "3d_m63_n128_mixed",
+              "2d_m127_n128_fp64"):
+        assert k in keys
+
+
+def test_stored_table_is_well_formed():
+    entries = tuning.load()
+    for k, e in entries.items():
+        assert set(e) == set(tuning.FIELDS), k
+        assert e["mg_cx"] in (0, 8, 16)
+        assert 0 <= e["mg_ctas"] <= 64 and 0 <= e["mv_tj"] <= 4096 and 0 <= e["pro_pch"] <= 64
