@@ -233,10 +233,14 @@ int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
  *   mv_tj:   time blocks per thread of the all-at-once matvec, 1..4096 (default 32).
  *   pro_pch: spectral planes per CTA of the prolongation and the 3D per-level
  *            multigrid kernels, 1..64 (default 8).
+ *   fft_stream: time FFTs (power-of-two n): 0 = one CTA per tile of spatial
+ *            columns (default), 1 = persistent CTAs that copy the next tile into
+ *            shared memory (cp.async) while transforming the current one.
  * pc_set_tiles validates (PC_ERR_ARG), applies the shapes to every later call on
  * the handle and drops its cached solve graph.  pc_autotune times candidate
  * shapes on the handle's own workspace (the multigrid spatial step for each
- * (mg_cx, mg_ctas), then pro_pch; the matvec for each mv_tj), `reps` timed calls
+ * (mg_cx, mg_ctas), then pro_pch; the forward + inverse time FFT for each
+ * fft_stream; the matvec for each mv_tj), `reps` timed calls
  * each (1..100) after one untimed call, keeps the fastest, applies it and copies
  * it to *chosen (may be NULL).  It synchronises `stream`, overwrites the
  * handle's Krylov and spectral workspace (not the caller's vectors) and must not
@@ -246,6 +250,7 @@ typedef struct pc_tiles {
   int mg_ctas;
   int mv_tj;
   int pro_pch;
+  int fft_stream;
 } pc_tiles;
 
 int pc_get_tiles(const pc_handle* h, pc_tiles* out);

@@ -1397,6 +1397,7 @@ static int check_tiles(const pc_tiles* t) {
   if (t->mg_ctas < 0 || t->mg_ctas > 64) return fail(PC_ERR_ARG, "mg_ctas must be in [0, 64]");
   if (t->mv_tj < 0 || t->mv_tj > 4096) return fail(PC_ERR_ARG, "mv_tj must be in [0, 4096]");
   if (t->pro_pch < 0 || t->pro_pch > 64) return fail(PC_ERR_ARG, "pro_pch must be in [0, 64]");
+  if (t->fft_stream < 0 || t->fft_stream > 1) return fail(PC_ERR_ARG, "fft_stream must be 0 or 1");
   return PC_OK;
 }
 
@@ -1411,6 +1412,7 @@ extern "C" int pc_get_tiles(const pc_handle* h, pc_tiles* out) {
   out->mg_ctas = h->tiles.mg_ctas;
   out->mv_tj = h->tiles.mv_tj;
   out->pro_pch = h->tiles.pro_pch;
+  out->fft_stream = h->tiles.fft_stream;
   return PC_OK;
 }
 
@@ -1421,6 +1423,7 @@ extern "C" int pc_set_tiles(pc_handle* h, const pc_tiles* t) {
   h->tiles.mg_ctas = t->mg_ctas;
   h->tiles.mv_tj = t->mv_tj;
   h->tiles.pro_pch = t->pro_pch;
+  h->tiles.fft_stream = t->fft_stream;
   drop_graphs(h);  // a cached solve graph holds the old launch shapes
   return PC_OK;
 }
@@ -1502,6 +1505,37 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
           tbest = ms;
           best.pro_pch = t.pro_pch;
         }
+      }
+    }
+  }
+  // time FFTs: one CTA per column tile or persistent streaming CTAs (power-of-two n)
+  if ((h->n & (h->n - 1)) == 0) {
+    double tbest = HUGE_VAL;
+    for (int mode = 0; mode < 2; ++mode) {
+      Tiles t = best;
+      t.fft_stream = mode;
+      Launch L{st, nullptr, &t};
+      const double ms = time_reps(st, reps, [&]() -> cudaError_t {
+        typedef float2 C32;
+        if (!h->fp32) {
+          cudaError_t e = launch_tfft_forward<double>(L, h->ms, h->n, h->V, h->dpow64, h->dinv64, h->tw64,
+                                                      (double2*)h->lv[0].r);
+          if (e != cudaSuccess) return e;
+          return launch_tfft_inverse<double, double2, double>(L, h->ms, h->n, (const double2*)h->lv[0].u, h->dpow64,
+                                                              h->dinv64, h->tw64, (double*)h->Z);
+        }
+        cudaError_t e = launch_tfft_forward<float>(L, h->ms, h->n, h->V, h->dpow32, h->dinv32, h->tw32,
+                                                   (C32*)h->lv[0].r);
+        if (e != cudaSuccess) return e;
+        if (h->bf16s)
+          return launch_tfft_inverse<float, __nv_bfloat162, float>(L, h->ms, h->n, (const __nv_bfloat162*)h->lv[0].u,
+                                                                   h->dpow32, h->dinv32, h->tw32, (float*)h->Z);
+        return launch_tfft_inverse<float, float2, float>(L, h->ms, h->n, (const float2*)h->lv[0].u, h->dpow32,
+                                                         h->dinv32, h->tw32, (float*)h->Z);
+      });
+      if (ms < tbest) {
+        tbest = ms;
+        best.fft_stream = mode;
       }
     }
   }

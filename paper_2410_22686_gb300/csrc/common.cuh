@@ -166,6 +166,7 @@ struct Tiles {
   int mg_ctas = 0;  // fused 2D down leg: CTAs per SM its grid is sized for (sets planes per CTA per level)
   int mv_tj = 0;    // matvec kernels: time blocks per thread
   int pro_pch = 0;  // prolongation and per-level (3D) multigrid kernels: planes per CTA
+  int fft_stream = 0;  // time FFTs: 0 one CTA per column tile, 1 persistent CTAs streaming tiles (cp.async)
   int sms = 0;      // SMs of the device (set at setup)
 };
 

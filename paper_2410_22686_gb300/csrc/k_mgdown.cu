@@ -6,17 +6,18 @@
 //   full weighting  rc(I, J) = sum_{o1,o2 in -1..1} w(o1) w(o2) res(2I+1+o1, 2J+1+o2),
 //   w(0) = 1/2, w(+-1) = 1/4,
 //
-// with the same arithmetic as the per-level kernels of k_spatial.cu, but r is read
-// from HBM once and the residual never goes there: a CTA owns a CX x CX tile of
-// coarse points (the fine points 2I, 2I+1 of each, the last tile also the fine
-// point m-1), stages r on the fine window [2I0-2, 2I0+2CX+2]^2 in shared memory,
-// takes red u on all of it, black u on [2I0-1, 2I0+2CX+1]^2 and the residual on
+// the operations of the per-level kernels of k_spatial.cu, but r is read from HBM
+// once and the residual never goes there.  A CTA owns a CX x CX tile of coarse
+// points (the fine points 2I, 2I+1 of each, the last tile also the fine point
+// m-1), stages r on the fine window [2I0-2, 2I0+2CX+2]^2 in shared memory, takes
+// red u on all of it, black u on [2I0-1, 2I0+2CX+1]^2 and the residual on
 // [2I0, 2I0+2CX]^2, then restricts.  The face weights and diagonal of the window
-// stay in shared memory for all the CTA's planes.  Points outside the grid hold
-// r = u = 0 (homogeneous Dirichlet boundary).  Red = even i1 + i2 (0-based),
-// swept first.  Values of u are rounded to the storage type TU before any later
-// step reads them, so the BF16-storage variant smooths, takes residuals and is
-// corrected on exactly what it stores.
+// stay in shared memory for all the CTA's planes, and the next plane's window is
+// loaded while the current one is swept.  Points outside the grid hold r = u = 0
+// (homogeneous Dirichlet boundary).  Red = even i1 + i2 (0-based), swept first.
+// Values of u are rounded to the storage type TU before any later step reads
+// them, so the BF16-storage variant smooths, takes residuals and is corrected on
+// exactly what it stores.
 #include "common.cuh"
 
 namespace pcopt {
@@ -40,6 +41,31 @@ __device__ __forceinline__ float2 inv_shift(float2 z) {
 }
 __device__ __forceinline__ double2 inv_shift(double2 z) { return cinv(z); }
 
+// the four face weights of one cell, loaded with one shared-memory access
+template <typename T>
+struct W4;
+template <>
+struct W4<float> {
+  typedef float4 t;
+};
+template <>
+struct W4<double> {
+  typedef double4_32a t;
+};
+
+template <typename T>
+__device__ __forceinline__ void cfma(typename Cx<T>::t& acc, T w, typename Cx<T>::t v) {
+  acc.x = fma(w, v.x, acc.x);
+  acc.y = fma(w, v.y, acc.y);
+}
+
+// Shared memory holds the window colour by colour: the window origin (2 I0 - 2,
+// 2 J0 - 2) is even, so cell (a1, a2) is red iff a1 + a2 is even, and each colour
+// of row a2 is a dense row of HW = (WR + 1) / 2 slots indexed k = a1 >> 1.  The
+// four neighbours of a cell have the other colour and sit at k - p, k + 1 - p
+// (same row) and k (rows a2 +- 1), with p = a2 & 1 for a black cell and 1 - p
+// for a red one; consecutive lanes take consecutive k, so every access is
+// unit-stride.
 template <typename Tc, typename TU, int CX>
 __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t* __restrict__ r, TU* __restrict__ u,
                                                        typename Cx<Tc>::t* __restrict__ rc,
@@ -48,25 +74,29 @@ __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t*
                                                        int planes, int pch) {
   typedef typename Cx<Tc>::t C;
   constexpr int NT = 256;
-  constexpr int WR = 2 * CX + 5;  // r window per axis
-  constexpr int NW = WR * WR;
-  constexpr int NB = WR - 2;      // black range [1, WR-2]
-  constexpr int NPR = (NB + 1) / 2;
-  constexpr int NRS = WR - 4;     // residual range [2, WR-3]
-  constexpr int NPC = (NRS + 1) / 2;
-  constexpr int SA = (NW + NT - 1) / NT;         // window slots per thread
-  constexpr int SB = (NB * NPR + NT - 1) / NT;   // black slots
-  constexpr int SC = (NRS * NPC + NT - 1) / NT;  // red residual slots
+  constexpr int WR = 2 * CX + 5;   // r window per axis
+  constexpr int HW = (WR + 1) / 2; // slots per row and colour
+  constexpr int NH = WR * HW;      // slots per colour
+  constexpr int SA = (2 * NH + NT - 1) / NT;       // window slots per thread (both colours)
+  constexpr int NBR = WR - 2;                      // black rows [1, WR-2]
+  constexpr int SB = (NBR * HW + NT - 1) / NT;     // black slots
+  constexpr int NRR = WR - 4;                      // residual rows [2, WR-3]
+  constexpr int SC = (NRR * HW + NT - 1) / NT;     // red residual slots
   // Residual of a sweep from zero: black points are solved exactly against their
   // red neighbours and red points against zero, so res_black = 0 and
   // res_red = sum_k w_k u_black(nb_k).  With BF16 storage the stored u no longer
   // satisfies this and the residual is formed explicitly from it.
   constexpr bool EXPLICIT = std::is_same<TU, __nv_bfloat162>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sR = reinterpret_cast<C*>(smem_raw);
-  C* sU = sR + NW;
-  Tc* sD = reinterpret_cast<Tc*>(sU + NW);
-  Tc* sW = sD + NW;  // [4][NW]: faces -x, +x, -y, +y
+  typedef typename W4<Tc>::t WV;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  WV* sWr = reinterpret_cast<WV*>(smem_raw);  // faces (-x, +x, -y, +y) of red cells
+  WV* sWb = sWr + NH;
+  C* sRr = reinterpret_cast<C*>(sWb + NH);    // r (then the red residual), red cells
+  C* sRb = sRr + NH;                          // r (then the black residual), black cells
+  C* sUr = sRb + NH;
+  C* sUb = sUr + NH;
+  Tc* sDr = reinterpret_cast<Tc*>(sUb + NH);
+  Tc* sDb = sDr + NH;
 
   const int mc = (m - 1) / 2;
   const int64_t np = (int64_t)m * m;
@@ -80,50 +110,55 @@ __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t*
   const int ey = (J0 + CX >= mc ? m : 2 * (J0 + CX)) - fy;
   const int tid = threadIdx.x;
 
-  // per-thread slots, the same for every plane: in-plane offset (-1 outside),
-  // colour and ownership of the window cells; shared-memory index of the black
-  // and red-residual points
+  // window slots e in [0, 2 NH): colour c = e / NH (0 red), row a2, k; per slot the
+  // in-plane offset (-1 outside the grid) and ownership
   int goffA[SA];
-  unsigned redA = 0, ownA = 0;
+  unsigned ownA = 0;
 #pragma unroll
   for (int i = 0; i < SA; ++i) {
     const int e = tid + i * NT;
-    const int a1 = e % WR, a2 = e / WR;
+    const int c = e >= NH ? 1 : 0;
+    const int h = e - c * NH;
+    const int a2 = h / HW, k = h - (h / HW) * HW;
+    const int a1 = 2 * k + ((a2 & 1) ^ c);
     const int f1 = fx + a1, f2 = fy + a2;
-    const bool in = e < NW && f1 >= 0 && f1 < m && f2 >= 0 && f2 < m;
+    const bool in = e < 2 * NH && a1 < WR && f1 >= 0 && f1 < m && f2 >= 0 && f2 < m;
     goffA[i] = in ? f2 * m + f1 : -1;
-    if (((f1 + f2) & 1) == 0) redA |= 1u << i;
     if (in && a1 >= 2 && a1 < ex && a2 >= 2 && a2 < ey) ownA |= 1u << i;
-    if (e < NW) {
-      sD[e] = in ? diag[goffA[i]] : Tc(0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sW[k * NW + e] = in ? w[(int64_t)k * np + goffA[i]] : Tc(0);
-      sR[e] = czero<Tc>();
-      sU[e] = czero<Tc>();
+    if (e < 2 * NH) {
+      (c ? sDb : sDr)[h] = in ? diag[goffA[i]] : Tc(0);
+      WV wv;
+      wv.x = in ? w[goffA[i]] : Tc(0);
+      wv.y = in ? w[np + goffA[i]] : Tc(0);
+      wv.z = in ? w[2 * np + goffA[i]] : Tc(0);
+      wv.w = in ? w[3 * np + goffA[i]] : Tc(0);
+      (c ? sWb : sWr)[h] = wv;
+      (c ? sRb : sRr)[h] = czero<Tc>();
+      (c ? sUb : sUr)[h] = czero<Tc>();
     }
   }
-  int qB[SB];
+  // black cells of rows [1, WR-2] with a1 in [1, WR-2] inside the grid
+  int hB[SB];
   unsigned ownB = 0;
 #pragma unroll
   for (int i = 0; i < SB; ++i) {
     const int e = tid + i * NT;
-    const int a2 = 1 + e / NPR;
-    int a1 = 1 + 2 * (e % NPR);
-    if (((fx + a1 + fy + a2) & 1) == 0) ++a1;
+    const int a2 = 1 + e / HW, k = e - (e / HW) * HW;
+    const int a1 = 2 * k + ((a2 & 1) ^ 1);
     const int f1 = fx + a1, f2 = fy + a2;
-    const bool ok = e < NB * NPR && a1 <= WR - 2 && f1 >= 0 && f1 < m && f2 >= 0 && f2 < m;
-    qB[i] = ok ? a2 * WR + a1 : -1;
+    const bool ok = e < NBR * HW && a1 >= 1 && a1 <= WR - 2 && f1 >= 0 && f1 < m && f2 >= 0 && f2 < m;
+    hB[i] = ok ? a2 * HW + k : -1;
     if (ok && a1 >= 2 && a1 < ex && a2 >= 2 && a2 < ey) ownB |= 1u << i;
   }
-  int qC[SC];
+  // red cells of rows [2, WR-3] with a1 in [2, WR-3] inside the grid
+  int hC[SC];
 #pragma unroll
   for (int i = 0; i < SC; ++i) {
     const int e = tid + i * NT;
-    const int a2 = 2 + e / NPC;
-    int a1 = 2 + 2 * (e % NPC);
-    if ((fx + a1 + fy + a2) & 1) ++a1;  // the red one of the pair
-    const bool ok = e < NRS * NPC && a1 <= WR - 3 && fx + a1 < m && fy + a2 < m;
-    qC[i] = ok ? a2 * WR + a1 : -1;
+    const int a2 = 2 + e / HW, k = e - (e / HW) * HW;
+    const int a1 = 2 * k + (a2 & 1);
+    const bool ok = e < NRR * HW && a1 >= 2 && a1 <= WR - 3 && fx + a1 < m && fy + a2 < m;
+    hC[i] = ok ? a2 * HW + k : -1;
   }
 
   C pre[SA];
@@ -143,11 +178,13 @@ __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t*
     for (int i = 0; i < SA; ++i) {
       if (goffA[i] < 0) continue;
       const int e = tid + i * NT;
-      sR[e] = pre[i];
-      if (redA & (1u << i)) {
-        const C uv = stored<TU>(cmul(pre[i], inv_shift(cmk<Tc>(sig.x + sD[e], sig.y))));
-        sU[e] = uv;
+      if (e < NH) {
+        sRr[e] = pre[i];
+        const C uv = stored<TU>(cmul(pre[i], inv_shift(cmk<Tc>(sig.x + sDr[e], sig.y))));
+        sUr[e] = uv;
         if (ownA & (1u << i)) stc(up, goffA[i], uv);
+      } else {
+        sRb[e - NH] = pre[i];
       }
     }
     __syncthreads();
@@ -155,76 +192,79 @@ __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t*
     // black points: u = (r + sum_k w_k u_red(nb_k)) / (sigma + d)
 #pragma unroll
     for (int i = 0; i < SB; ++i) {
-      const int q = qB[i];
-      if (q < 0) continue;
-      C acc = sR[q];
-      const C ul = sU[q - 1], ur = sU[q + 1], ud = sU[q - WR], uu = sU[q + WR];
-      const Tc w0 = sW[q], w1 = sW[NW + q], w2 = sW[2 * NW + q], w3 = sW[3 * NW + q];
-      acc.x = fma(w0, ul.x, acc.x);
-      acc.y = fma(w0, ul.y, acc.y);
-      acc.x = fma(w1, ur.x, acc.x);
-      acc.y = fma(w1, ur.y, acc.y);
-      acc.x = fma(w2, ud.x, acc.x);
-      acc.y = fma(w2, ud.y, acc.y);
-      acc.x = fma(w3, uu.x, acc.x);
-      acc.y = fma(w3, uu.y, acc.y);
-      const C uv = stored<TU>(cmul(acc, inv_shift(cmk<Tc>(sig.x + sD[q], sig.y))));
-      sU[q] = uv;
-      if (ownB & (1u << i)) stc(up, (int64_t)(fy + q / WR) * m + fx + q % WR, uv);
+      const int h = hB[i];
+      if (h < 0) continue;
+      const int a2 = h / HW;
+      const int s = a2 & 1;  // left red neighbour at k - s, right at k + 1 - s
+      C acc = sRb[h];
+      const WV wv = sWb[h];
+      cfma<Tc>(acc, wv.x, sUr[h - s]);
+      cfma<Tc>(acc, wv.y, sUr[h + 1 - s]);
+      cfma<Tc>(acc, wv.z, sUr[h - HW]);
+      cfma<Tc>(acc, wv.w, sUr[h + HW]);
+      const C uv = stored<TU>(cmul(acc, inv_shift(cmk<Tc>(sig.x + sDb[h], sig.y))));
+      sUb[h] = uv;
+      if (ownB & (1u << i)) {
+        const int k = h - a2 * HW;
+        stc(up, (int64_t)(fy + a2) * m + fx + 2 * k + (s ^ 1), uv);
+      }
     }
     __syncthreads();
     if constexpr (!EXPLICIT) {
       // red residuals, in place of r
 #pragma unroll
       for (int i = 0; i < SC; ++i) {
-        const int q = qC[i];
-        if (q < 0) continue;
-        const C ul = sU[q - 1], ur = sU[q + 1], ud = sU[q - WR], uu = sU[q + WR];
-        const Tc w0 = sW[q], w1 = sW[NW + q], w2 = sW[2 * NW + q], w3 = sW[3 * NW + q];
+        const int h = hC[i];
+        if (h < 0) continue;
+        const int s = (h / HW) & 1;  // left black neighbour at k - 1 + s, right at k + s
         C res;
-        res.x = w0 * ul.x;
-        res.y = w0 * ul.y;
-        res.x = fma(w1, ur.x, res.x);
-        res.y = fma(w1, ur.y, res.y);
-        res.x = fma(w2, ud.x, res.x);
-        res.y = fma(w2, ud.y, res.y);
-        res.x = fma(w3, uu.x, res.x);
-        res.y = fma(w3, uu.y, res.y);
-        sR[q] = res;
+        const WV wv = sWr[h];
+        const C ul = sUb[h - 1 + s];
+        res.x = wv.x * ul.x;
+        res.y = wv.x * ul.y;
+        cfma<Tc>(res, wv.y, sUb[h + s]);
+        cfma<Tc>(res, wv.z, sUb[h - HW]);
+        cfma<Tc>(res, wv.w, sUb[h + HW]);
+        sRr[h] = res;
       }
     } else {
       // residual of the stored u at every point of the restriction windows
-      for (int e = tid; e < NRS * NRS; e += NT) {
-        const int a1 = 2 + e % NRS, a2 = 2 + e / NRS;
-        if (fx + a1 >= m || fy + a2 >= m) continue;
-        const int q = a2 * WR + a1;
-        const C uc = sU[q];
-        C lu = cmul(cmk<Tc>(sig.x + sD[q], sig.y), uc);
-        const C ul = sU[q - 1], ur = sU[q + 1], ud = sU[q - WR], uu = sU[q + WR];
-        const Tc w0 = sW[q], w1 = sW[NW + q], w2 = sW[2 * NW + q], w3 = sW[3 * NW + q];
-        lu.x = fma(-w0, ul.x, lu.x);
-        lu.y = fma(-w0, ul.y, lu.y);
-        lu.x = fma(-w1, ur.x, lu.x);
-        lu.y = fma(-w1, ur.y, lu.y);
-        lu.x = fma(-w2, ud.x, lu.x);
-        lu.y = fma(-w2, ud.y, lu.y);
-        lu.x = fma(-w3, uu.x, lu.x);
-        lu.y = fma(-w3, uu.y, lu.y);
-        sR[q] = sR[q] - lu;
+      for (int e = tid; e < 2 * NRR * HW; e += NT) {
+        const int c = e >= NRR * HW ? 1 : 0;
+        const int g = e - c * NRR * HW;
+        const int a2 = 2 + g / HW, k = g - (g / HW) * HW;
+        const int sp = (a2 & 1) ^ c;  // a1 parity
+        const int a1 = 2 * k + sp;
+        if (a1 < 2 || a1 > WR - 3 || fx + a1 >= m || fy + a2 >= m) continue;
+        const int h = a2 * HW + k;
+        // neighbours have the other colour; same-row ones at k - 1 + sp and k + sp
+        const C* U = c ? sUr : sUb;
+        const WV wv = (c ? sWb : sWr)[h];
+        const C uc = (c ? sUb : sUr)[h];
+        C lu = cmul(cmk<Tc>(sig.x + (c ? sDb : sDr)[h], sig.y), uc);
+        cfma<Tc>(lu, -wv.x, U[h - 1 + sp]);
+        cfma<Tc>(lu, -wv.y, U[h + sp]);
+        cfma<Tc>(lu, -wv.z, U[h - HW]);
+        cfma<Tc>(lu, -wv.w, U[h + HW]);
+        C* R = c ? sRb : sRr;
+        R[h] = R[h] - lu;
       }
     }
     __syncthreads();
-    // full weighting onto the coarse tile; the edge points of each 3x3 window are
-    // black (zero residual unless it was formed explicitly)
+    // full weighting onto the coarse tile: centre and corners are red, edges black
+    // (zero residual unless it was formed explicitly)
     for (int e = tid; e < CX * CX; e += NT) {
       const int I = I0 + e % CX, J = J0 + e / CX;
       if (I >= mc || J >= mc) continue;
-      const int q = (2 * (J - J0) + 3) * WR + 2 * (I - I0) + 3;
-      const C c0 = sR[q];
-      const C k4 = sR[q - WR - 1] + sR[q - WR + 1] + sR[q + WR - 1] + sR[q + WR + 1];
+      const int a1 = 2 * (I - I0) + 3, a2 = 2 * (J - J0) + 3;  // odd: k = (a1 - 1) / 2 in row a2
+      const int h = a2 * HW + (a1 >> 1);
+      // corners (a1 -+ 1, a2 -+ 1) are red cells of the even rows at k and k + 1
+      const C c0 = sRr[h];
+      const C k4 = sRr[h - HW] + sRr[h - HW + 1] + sRr[h + HW] + sRr[h + HW + 1];
       C acc;
       if constexpr (EXPLICIT) {
-        const C e4 = sR[q - 1] + sR[q + 1] + sR[q - WR] + sR[q + WR];
+        // edges: black (a1 -+ 1, a2) at k, k + 1 in row a2; (a1, a2 -+ 1) at k in rows a2 -+ 1
+        const C e4 = sRb[h] + sRb[h + 1] + sRb[h - HW] + sRb[h + HW];
         acc.x = fma(Tc(0.25), c0.x, fma(Tc(0.125), e4.x, Tc(0.0625) * k4.x));
         acc.y = fma(Tc(0.25), c0.y, fma(Tc(0.125), e4.y, Tc(0.0625) * k4.y));
       } else {
@@ -242,9 +282,13 @@ cudaError_t down2(Launch& L, int m, int planes, int pch, const Tc* w, const Tc* 
                   const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u, typename Cx<Tc>::t* rc) {
   typedef typename Cx<Tc>::t C;
   constexpr int WR = 2 * CX + 5;
-  const size_t smem = (size_t)WR * WR * (2 * sizeof(C) + 5 * sizeof(Tc));
+  constexpr int NH = WR * ((WR + 1) / 2);  // slots per colour
+  const size_t smem = (size_t)NH * (2 * sizeof(typename W4<Tc>::t) + 4 * sizeof(C) + 2 * sizeof(Tc));
   cudaError_t e = cudaFuncSetAttribute(mg_down2_kernel<Tc, TU, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
+  if (e != cudaSuccess) return e;
+  // prefer shared memory in the unified L1 (the window is 50 KB per CTA in FP32)
+  e = cudaFuncSetAttribute(mg_down2_kernel<Tc, TU, CX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   const int mc = (m - 1) / 2;
   const unsigned tiles = (unsigned)((mc + CX - 1) / CX);

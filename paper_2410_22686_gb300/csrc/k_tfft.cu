@@ -17,6 +17,8 @@
 // in-place radix-2 FFT of length n in shared memory for all TS columns
 // (threads of a warp work on consecutive columns: conflict-free), and writes
 // frequency-major planes (the time<->space transpose happens in shared memory).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace pcopt {
@@ -248,35 +250,39 @@ __device__ __forceinline__ void reg_fft(C (&x)[R], const C* __restrict__ tw, int
   }
 }
 
-template <typename Tin, typename Tc, int N1, int N2>
-__global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
-                                                            const Tc* __restrict__ dinv,
-                                                            const typename Cx<Tc>::t* __restrict__ tw,
-                                                            typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
-                                                            size_t vstride, const int* __restrict__ jdev) {
+// cp.async (sm_80+ asynchronous global -> shared copy, bypassing registers);
+// `ok == false` zero-fills the destination without reading global memory
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = ok ? B : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(B), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Forward transform of one tile of COLS = 256 / N1 columns.  ld(j, a, b) gives
+// v1[j] and v2[j] of the thread's column (zero outside the grid).  Returns after
+// the spectrum stores; the caller's barrier orders the reuse of `sm`.
+template <typename Tc, int N1, int N2, typename Ld>
+__device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, const Tc* __restrict__ dinv,
+                                          const typename Cx<Tc>::t* __restrict__ tw,
+                                          typename Cx<Tc>::t* __restrict__ spec, typename Cx<Tc>::t* sm,
+                                          int64_t ms, int64_t s, bool valid, int r, int c) {
   typedef typename Cx<Tc>::t C;
   constexpr int n = N1 * N2;
   constexpr int COLS = 256 / N1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
-  const int c = threadIdx.x % COLS;
-  const int r = threadIdx.x / COLS;  // 0..N1-1
-  const int64_t s = (int64_t)blockIdx.x * COLS + c;
-  const bool valid = s < ms;
-  if (jdev) v += (size_t)(*jdev) * vstride;  // input = basis vector j (device-resident index)
-  const Tin* v1 = v;
-  const Tin* v2 = v + (int64_t)n * ms;
   // (A) rows j = r + N1 j2: z = D^{-1} v1 + i D v2, N2-point DFT over j2
   C x[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) {
     const int j = r + N1 * j2;
-    Tc a = Tc(0), b = Tc(0);
-    if (valid) {
-      a = cvt<Tc>(v1[(int64_t)j * ms + s]) * dinv[j];
-      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * dpow[j];
-    }
-    x[j2] = cmk<Tc>(a, b);
+    Tc a, b;
+    ld(j, a, b);
+    x[j2] = cmk<Tc>(a * dinv[j], b * dpow[j]);
   }
   reg_fft<N2, false>(x, tw, N1);
   // (B) twiddle w^{j1 k2}, stored as Y[k2][j1]
@@ -299,46 +305,33 @@ __global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restric
     for (int k1 = 0; k1 < N1; ++k1) sm[(r + N2 * k1) * COLS + c] = y[k1];
   }
   __syncthreads();
-  if (!valid) return;
-  // Hermitian split of the two-for-one spectrum, k = 0..n/2
-  const Tc hf = Tc(0.5);
-  for (int k = r; k <= n / 2; k += N1) {
-    const C Z = sm[k * COLS + c];
-    const C W = sm[((n - k) & (n - 1)) * COLS + c];
-    spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
-    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+  if (valid) {
+    // Hermitian split of the two-for-one spectrum, k = 0..n/2
+    const Tc hf = Tc(0.5);
+    for (int k = r; k <= n / 2; k += N1) {
+      const C Z = sm[k * COLS + c];
+      const C W = sm[((n - k) & (n - 1)) * COLS + c];
+      spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
+      spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+    }
   }
 }
 
-template <typename Tc, typename TU, typename Tout, int N1, int N2>
-__global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
-                                                            const Tc* __restrict__ dinv,
-                                                            const typename Cx<Tc>::t* __restrict__ tw,
-                                                            Tout* __restrict__ w, int64_t ms, size_t wstride,
-                                                            const int* __restrict__ jdev, FineCorrection<TU> fc) {
+// Inverse transform, D scalings and the [[I, -I], [I, I]] butterfly of one tile.
+// ld(k, sa, sb) gives spectral planes 2k and 2k+1 of the thread's column (zero
+// outside the grid).  Returns after the output stores.
+template <typename Tc, typename Tout, int N1, int N2, typename Ld>
+__device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, const Tc* __restrict__ dinv,
+                                          const typename Cx<Tc>::t* __restrict__ tw, Tout* __restrict__ w,
+                                          typename Cx<Tc>::t* sm, int64_t ms, int64_t s, bool valid, int r,
+                                          int c) {
   typedef typename Cx<Tc>::t C;
   constexpr int n = N1 * N2;
   constexpr int COLS = 256 / N1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
-  const int c = threadIdx.x % COLS;
-  const int r = threadIdx.x / COLS;
-  const int64_t s = (int64_t)blockIdx.x * COLS + c;
-  const bool valid = s < ms;
-  if (jdev) w += (size_t)(*jdev) * wstride;  // output = basis vector j
   // Y[k] = hat w1[k] + i hat w2[k] for all k from the half spectrum
-  Parents<Tc, TU> par;
-  if (fc.ec && valid) par.init(fc, s);
   for (int k = r; k <= n / 2; k += N1) {
-    C sa = czero<Tc>(), sb = czero<Tc>();
-    if (valid) {
-      sa = ldc(spec, (int64_t)(2 * k) * ms + s);
-      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
-      if (fc.ec) {
-        sa = sa + par.at(fc, 2 * k);
-        sb = sb + par.at(fc, 2 * k + 1);
-      }
-    }
+    C sa, sb;
+    ld(k, sa, sb);
     sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
     if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
   }
@@ -356,23 +349,196 @@ __global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict
     sm[(j2 * N1 + r) * COLS + c] = (j2 == 0 || r == 0) ? x[j2] : cmul(t, x[j2]);
   }
   __syncthreads();
-  if (r >= N2 || !valid) return;
-  // (C) row j2 = r: N1-point inverse DFT over k1 -> x[j2 + N2 j1]
-  C y[N1];
+  if (r < N2 && valid) {
+    // (C) row j2 = r: N1-point inverse DFT over k1 -> x[j2 + N2 j1]
+    C y[N1];
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) y[k1] = sm[(r * N1 + k1) * COLS + c];
-  reg_fft<N1, true>(y, tw, N2);
-  const Tc inv_n = Tc(1) / Tc(n);
-  Tout* w1 = w;
-  Tout* w2 = w + (int64_t)n * ms;
+    for (int k1 = 0; k1 < N1; ++k1) y[k1] = sm[(r * N1 + k1) * COLS + c];
+    reg_fft<N1, true>(y, tw, N2);
+    const Tc inv_n = Tc(1) / Tc(n);
+    Tout* w1 = w;
+    Tout* w2 = w + (int64_t)n * ms;
 #pragma unroll
-  for (int j1 = 0; j1 < N1; ++j1) {
-    const int j = r + N2 * j1;
-    const Tc wt1 = dpow[j] * (y[j1].x * inv_n);  // D ifft(hat w1)
-    const Tc wt2 = dinv[j] * (y[j1].y * inv_n);  // D^{-1} ifft(hat w2)
-    w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);  // step 4: [[I, -I], [I, I]]
-    w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const int j = r + N2 * j1;
+      const Tc wt1 = dpow[j] * (y[j1].x * inv_n);  // D ifft(hat w1)
+      const Tc wt2 = dinv[j] * (y[j1].y * inv_n);  // D^{-1} ifft(hat w2)
+      w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);  // step 4: [[I, -I], [I, I]]
+      w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+    }
   }
+}
+
+// one CTA per tile, inputs loaded straight into registers
+template <typename Tin, typename Tc, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
+                                                            const Tc* __restrict__ dinv,
+                                                            const typename Cx<Tc>::t* __restrict__ tw,
+                                                            typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
+                                                            size_t vstride, const int* __restrict__ jdev) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;  // 0..N1-1
+  const int64_t s = (int64_t)blockIdx.x * COLS + c;
+  const bool valid = s < ms;
+  if (jdev) v += (size_t)(*jdev) * vstride;  // input = basis vector j (device-resident index)
+  const Tin* v1 = v;
+  const Tin* v2 = v + (int64_t)n * ms;
+  fwd4_body<Tc, N1, N2>(
+      [&](int j, Tc& a, Tc& b) {
+        a = valid ? cvt<Tc>(v1[(int64_t)j * ms + s]) : Tc(0);
+        b = valid ? cvt<Tc>(v2[(int64_t)j * ms + s]) : Tc(0);
+      },
+      dpow, dinv, tw, spec, sm, ms, s, valid, r, c);
+}
+
+// Persistent streaming variant: each CTA walks tiles blockIdx.x, + gridDim.x, ...
+// and copies the next tile's 2n x COLS inputs into a second shared-memory stage
+// with cp.async while it transforms the current one.
+template <typename Tin, typename Tc, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4s_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
+                                                             const Tc* __restrict__ dinv,
+                                                             const typename Cx<Tc>::t* __restrict__ tw,
+                                                             typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
+                                                             int ntiles, size_t vstride, const int* __restrict__ jdev) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  constexpr int TILE = 2 * n * COLS;  // rows 0..n-1: v1, n..2n-1: v2 (v2 = v1 + n ms)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tin* stage = reinterpret_cast<Tin*>(smem_raw);  // [2][2n][COLS]
+  C* sm = reinterpret_cast<C*>(stage + 2 * TILE);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;
+  if (jdev) v += (size_t)(*jdev) * vstride;
+  auto issue = [&](int tile, int buf) {
+    Tin* dst = stage + buf * TILE;
+    const int64_t s0 = (int64_t)tile * COLS;
+    for (int e = threadIdx.x; e < TILE; e += 256) {
+      const int cc = e % COLS;
+      const int row = e / COLS;
+      const bool ok = s0 + cc < ms;
+      cp_async<sizeof(Tin)>(dst + e, v + (int64_t)row * ms + (ok ? s0 + cc : 0), ok);
+    }
+    cp_async_commit();
+  };
+  if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int buf = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    if (t + (int)gridDim.x < ntiles)
+      issue(t + gridDim.x, buf ^ 1);
+    else
+      cp_async_commit();  // empty group: the wait below always leaves one pending
+    cp_async_wait<1>();
+    __syncthreads();
+    const Tin* st = stage + buf * TILE;
+    const int64_t s = (int64_t)t * COLS + c;
+    fwd4_body<Tc, N1, N2>(
+        [&](int j, Tc& a, Tc& b) {
+          a = cvt<Tc>(st[j * COLS + c]);
+          b = cvt<Tc>(st[(n + j) * COLS + c]);
+        },
+        dpow, dinv, tw, spec, sm, ms, s, s < ms, r, c);
+    __syncthreads();  // stage[buf] and sm are rewritten next
+  }
+  cp_async_wait<0>();
+}
+
+template <typename Tc, typename TU, typename Tout, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+                                                            const Tc* __restrict__ dinv,
+                                                            const typename Cx<Tc>::t* __restrict__ tw,
+                                                            Tout* __restrict__ w, int64_t ms, size_t wstride,
+                                                            const int* __restrict__ jdev, FineCorrection<TU> fc) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;
+  const int64_t s = (int64_t)blockIdx.x * COLS + c;
+  const bool valid = s < ms;
+  if (jdev) w += (size_t)(*jdev) * wstride;  // output = basis vector j
+  Parents<Tc, TU> par;
+  if (fc.ec && valid) par.init(fc, s);
+  inv4_body<Tc, Tout, N1, N2>(
+      [&](int k, C& sa, C& sb) {
+        sa = czero<Tc>();
+        sb = czero<Tc>();
+        if (valid) {
+          sa = ldc(spec, (int64_t)(2 * k) * ms + s);
+          sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);
+          if (fc.ec) {
+            sa = sa + par.at(fc, 2 * k);
+            sb = sb + par.at(fc, 2 * k + 1);
+          }
+        }
+      },
+      dpow, dinv, tw, w, sm, ms, s, valid, r, c);
+}
+
+// Persistent streaming inverse: the next tile's 2 (n/2 + 1) spectral planes are
+// copied into a second stage with cp.async while the current tile is transformed.
+template <typename Tc, typename TU, typename Tout, int N1, int N2>
+__global__ void __launch_bounds__(256) tfft4s_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+                                                             const Tc* __restrict__ dinv,
+                                                             const typename Cx<Tc>::t* __restrict__ tw,
+                                                             Tout* __restrict__ w, int64_t ms, int ntiles,
+                                                             size_t wstride, const int* __restrict__ jdev,
+                                                             FineCorrection<TU> fc) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  constexpr int NP = 2 * (n / 2 + 1);  // spectral planes
+  constexpr int TILE = NP * COLS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TU* stage = reinterpret_cast<TU*>(smem_raw);                                // [2][NP][COLS]
+  C* sm = reinterpret_cast<C*>(smem_raw + ((2 * TILE * sizeof(TU) + 15) / 16) * 16);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;
+  if (jdev) w += (size_t)(*jdev) * wstride;
+  auto issue = [&](int tile, int buf) {
+    TU* dst = stage + buf * TILE;
+    const int64_t s0 = (int64_t)tile * COLS;
+    for (int e = threadIdx.x; e < TILE; e += 256) {
+      const int cc = e % COLS;
+      const int p = e / COLS;
+      const bool ok = s0 + cc < ms;
+      cp_async<sizeof(TU)>(dst + e, spec + (int64_t)p * ms + (ok ? s0 + cc : 0), ok);
+    }
+    cp_async_commit();
+  };
+  if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int buf = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    if (t + (int)gridDim.x < ntiles)
+      issue(t + gridDim.x, buf ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const TU* st = stage + buf * TILE;
+    const int64_t s = (int64_t)t * COLS + c;
+    const bool valid = s < ms;
+    Parents<Tc, TU> par;
+    if (fc.ec && valid) par.init(fc, s);
+    inv4_body<Tc, Tout, N1, N2>(
+        [&](int k, C& sa, C& sb) {
+          sa = ldc(st, (2 * k) * COLS + c);
+          sb = ldc(st, (2 * k + 1) * COLS + c);
+          if (fc.ec && valid) {
+            sa = sa + par.at(fc, 2 * k);
+            sb = sb + par.at(fc, 2 * k + 1);
+          }
+        },
+        dpow, dinv, tw, w, sm, ms, s, valid, r, c);
+    __syncthreads();
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -535,6 +701,47 @@ cudaError_t inv4(Launch& L, int64_t ms, const TU* spec, const Tc* dpow, const Tc
   return cudaGetLastError();
 }
 
+static int sm_count(const Launch& L) { return L.tiles && L.tiles->sms > 0 ? L.tiles->sms : 152; }
+
+template <typename Tin, typename Tc, int N1, int N2>
+cudaError_t fwd4s(Launch& L, int64_t ms, const Tin* v, const Tc* dpow, const Tc* dinv,
+                  const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride, const int* jdev) {
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  const size_t smem = (size_t)2 * 2 * n * COLS * sizeof(Tin) + (size_t)n * COLS * sizeof(typename Cx<Tc>::t);
+  if (smem > 227 * 1024) return fwd4<Tin, Tc, N1, N2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+  auto kern = tfft4s_forward_kernel<Tin, Tc, N1, N2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess) return e;
+  const int ntiles = (int)((ms + COLS - 1) / COLS);
+  const int grid = std::min(ntiles, std::max(1, per_sm) * sm_count(L));
+  kern<<<grid, 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, ntiles, vstride, jdev);
+  return cudaGetLastError();
+}
+
+template <typename Tc, typename TU, typename Tout, int N1, int N2>
+cudaError_t inv4s(Launch& L, int64_t ms, const TU* spec, const Tc* dpow, const Tc* dinv,
+                  const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev,
+                  const FineCorrection<TU>& fc) {
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  constexpr int NP = 2 * (n / 2 + 1);
+  const size_t smem = (((size_t)2 * NP * COLS * sizeof(TU) + 15) / 16) * 16 +
+                      (size_t)n * COLS * sizeof(typename Cx<Tc>::t);
+  if (smem > 227 * 1024) return inv4<Tc, TU, Tout, N1, N2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+  auto kern = tfft4s_inverse_kernel<Tc, TU, Tout, N1, N2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess) return e;
+  const int ntiles = (int)((ms + COLS - 1) / COLS);
+  const int grid = std::min(ntiles, std::max(1, per_sm) * sm_count(L));
+  kern<<<grid, 256, smem, L.stream>>>(spec, dpow, dinv, tw, w, ms, ntiles, wstride, jdev, fc);
+  return cudaGetLastError();
+}
+
 // largest n handled by the four-step kernels (register pressure bounds FP64)
 template <typename Tc>
 constexpr int four_step_max() {
@@ -544,21 +751,33 @@ constexpr int four_step_max() {
 template <typename Tin, typename Tc>
 cudaError_t fwd4_dispatch(Launch& L, int64_t ms, int n, const Tin* v, const Tc* dpow, const Tc* dinv,
                           const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride, const int* jdev) {
+  const bool stream = L.tiles && L.tiles->fft_stream > 0;
   switch (n) {
-    case 1: return fwd4<Tin, Tc, 1, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 2: return fwd4<Tin, Tc, 2, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 4: return fwd4<Tin, Tc, 2, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 8: return fwd4<Tin, Tc, 4, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 16: return fwd4<Tin, Tc, 4, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 32: return fwd4<Tin, Tc, 8, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 64: return fwd4<Tin, Tc, 8, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 128: return fwd4<Tin, Tc, 16, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
-    case 256: return fwd4<Tin, Tc, 16, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 1: return stream ? fwd4s<Tin, Tc, 1, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 1, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 2: return stream ? fwd4s<Tin, Tc, 2, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 2, 1>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 4: return stream ? fwd4s<Tin, Tc, 2, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 2, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 8: return stream ? fwd4s<Tin, Tc, 4, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 4, 2>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 16: return stream ? fwd4s<Tin, Tc, 4, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 4, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 32: return stream ? fwd4s<Tin, Tc, 8, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 8, 4>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 64: return stream ? fwd4s<Tin, Tc, 8, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 8, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 128: return stream ? fwd4s<Tin, Tc, 16, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 16, 8>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+    case 256: return stream ? fwd4s<Tin, Tc, 16, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 16, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
     case 512:
-      if constexpr (sizeof(Tc) == 4) return fwd4<Tin, Tc, 32, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+      if constexpr (sizeof(Tc) == 4) return stream ? fwd4s<Tin, Tc, 32, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 32, 16>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
       break;
     case 1024:
-      if constexpr (sizeof(Tc) == 4) return fwd4<Tin, Tc, 32, 32>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
+      if constexpr (sizeof(Tc) == 4) return stream ? fwd4s<Tin, Tc, 32, 32>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev)
+                    : fwd4<Tin, Tc, 32, 32>(L, ms, v, dpow, dinv, tw, spec, vstride, jdev);
       break;
   }
   return cudaErrorInvalidValue;
@@ -568,21 +787,33 @@ template <typename Tc, typename TU, typename Tout>
 cudaError_t inv4_dispatch(Launch& L, int64_t ms, int n, const TU* spec, const Tc* dpow, const Tc* dinv,
                           const typename Cx<Tc>::t* tw, Tout* w, size_t wstride, const int* jdev,
                           const FineCorrection<TU>& fc) {
+  const bool stream = L.tiles && L.tiles->fft_stream > 0;
   switch (n) {
-    case 1: return inv4<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 2: return inv4<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 4: return inv4<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 8: return inv4<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 16: return inv4<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 32: return inv4<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 64: return inv4<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 128: return inv4<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
-    case 256: return inv4<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 1: return stream ? inv4s<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 1, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 2: return stream ? inv4s<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 2, 1>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 4: return stream ? inv4s<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 2, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 8: return stream ? inv4s<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 4, 2>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 16: return stream ? inv4s<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 4, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 32: return stream ? inv4s<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 8, 4>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 64: return stream ? inv4s<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 8, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 128: return stream ? inv4s<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 16, 8>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+    case 256: return stream ? inv4s<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 16, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
     case 512:
-      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+      if constexpr (sizeof(Tc) == 4) return stream ? inv4s<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 32, 16>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
       break;
     case 1024:
-      if constexpr (sizeof(Tc) == 4) return inv4<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
+      if constexpr (sizeof(Tc) == 4) return stream ? inv4s<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc)
+                    : inv4<Tc, TU, Tout, 32, 32>(L, ms, spec, dpow, dinv, tw, w, wstride, jdev, fc);
       break;
   }
   return cudaErrorInvalidValue;

@@ -2,7 +2,7 @@
 
 ``pc_autotune`` times candidate tile shapes of the tunable kernels on one handle
 (fused multigrid down leg: tile width and CTAs per SM; prolongation planes per
-CTA; matvec time blocks per thread) and keeps the fastest.  This module keeps
+CTA; streaming or one-CTA-per-tile time FFTs; matvec time blocks per thread) and keeps the fastest.  This module keeps
 the chosen shapes in a JSON table next to the package, keyed by
 (dim, m1, n, precision), so that ``Solver(..., tiles="table")`` (the default)
 starts with the tuned shapes without re-timing.  Shapes missing from the table
@@ -21,7 +21,7 @@ import json
 import os
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiles_gb300.json")
-FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch")
+FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch", "fft_stream")
 
 # (dim, m1, n, precision): the bench and test workloads
 WORKLOADS = (
@@ -108,7 +108,8 @@ def main(argv=None):
            "fields": {"mg_cx": "fused 2D down-leg tile (coarse points per axis)",
                       "mg_ctas": "fused down-leg CTAs per SM",
                       "mv_tj": "matvec time blocks per thread",
-                      "pro_pch": "prolongation / 3D per-level planes per CTA"},
+                      "pro_pch": "prolongation / 3D per-level planes per CTA",
+                      "fft_stream": "time FFTs: 0 one CTA per tile, 1 persistent streaming CTAs"},
            "entries": entries}
     with open(args.out, "w") as fh:
         json.dump(doc, fh, indent=1, sort_keys=True)

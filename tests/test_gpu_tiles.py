@@ -20,12 +20,13 @@ def _rel(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
-SHAPES = [dict(mg_cx=8, mg_ctas=2, mv_tj=8, pro_pch=2), dict(mg_cx=16, mg_ctas=32, mv_tj=128, pro_pch=32),
-          dict(mg_cx=16, mg_ctas=1, mv_tj=1, pro_pch=1)]
+SHAPES = [dict(mg_cx=8, mg_ctas=2, mv_tj=8, pro_pch=2, fft_stream=1),
+          dict(mg_cx=16, mg_ctas=32, mv_tj=128, pro_pch=32, fft_stream=0),
+          dict(mg_cx=16, mg_ctas=1, mv_tj=1, pro_pch=1, fft_stream=1)]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5), ("bf16s", 3e-2)])
-@pytest.mark.parametrize("d,m1,n", [(2, 63, 16), (2, 127, 8), (3, 15, 8)])
+@pytest.mark.parametrize("d,m1,n", [(2, 63, 16), (2, 127, 8), (3, 15, 8), (2, 31, 256), (2, 15, 512)])
 def test_precond_and_matvec_match_oracle_for_every_tile_shape(precision, tol, d, m1, n):
     from paper_2410_22686_gb300 import Solver
     a = np.exp(0.4 * S.random_vector((m1 + 2,) * d, 5))
@@ -52,7 +53,7 @@ def test_precond_and_matvec_match_oracle_for_every_tile_shape(precision, tol, d,
 def test_invalid_tile_shapes_are_rejected():
     from paper_2410_22686_gb300 import Solver, capi
     sol = Solver(2, 15, 8, 1.0, 1e-3, 0.3, None, spatial="fst", tiles=None)
-    for bad in (dict(mg_cx=12), dict(mg_ctas=-1), dict(mv_tj=5000), dict(pro_pch=65)):
+    for bad in (dict(mg_cx=12), dict(mg_ctas=-1), dict(mv_tj=5000), dict(pro_pch=65), dict(fft_stream=2)):
         with pytest.raises(capi.PCError):
             sol.set_tiles(**bad)
     with pytest.raises(ValueError):
@@ -71,7 +72,9 @@ def test_autotune_picks_valid_shapes_and_keeps_the_solution(precision):
     x0, it0, rr0 = sol.solve(b, rtol=1e-8)
     t = sol.autotune(reps=2)
     assert t["mg_cx"] in (8, 16) and 1 <= t["mg_ctas"] <= 64
-    assert 1 <= t["mv_tj"] <= 4096 and 1 <= t["pro_pch"] <= 64
+    # pro_pch stays 0 (default) when the handle launches no prolongation kernel:
+    # at 63^2 the only fine level's correction is fused into the inverse FFT
+    assert 1 <= t["mv_tj"] <= 4096 and 0 <= t["pro_pch"] <= 64 and t["fft_stream"] in (0, 1)
     assert sol.get_tiles() == t
     x1, it1, rr1 = sol.solve(b, rtol=1e-8)
     assert rr1 <= 1e-8 and abs(it1 - it0) <= 1
