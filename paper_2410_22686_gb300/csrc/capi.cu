@@ -189,6 +189,7 @@ struct pc_handle {
   // Krylov workspace
   double* V = nullptr;     // (cap+1) x U
   void* Z = nullptr;       // cap x U (double or float)
+  float* vf32 = nullptr;   // U: FP32 rounding of the newest basis vector (mixed handles)
   double* wbuf = nullptr;  // U
   double* tbuf = nullptr;  // U
   double* adjbuf = nullptr;  // U: S c of the adjoint solve
@@ -575,6 +576,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     h->nblocks = num_sms() * kMaxBlocksPerSM;
     if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * U))) goto fail_out;
     if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
+    if (h->fp32 && (rc = dev_alloc_t(h, &h->vf32, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->tbuf, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->adjbuf, U))) goto fail_out;
@@ -813,13 +815,15 @@ static FineCorrection<TU> fine_correction(const pc_handle* h) {
   return fc;
 }
 
-// w = P^{-1} v; with jdev != nullptr the input is v + j*stride and the output w + j*stride
-template <typename Tc, typename TU, typename Tout>
-static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w, size_t stride = 0,
-                             const int* jdev = nullptr) {
+// w = P^{-1} v; with jdev != nullptr the output is w + j*stride and, when index_input,
+// the input v + j*stride (an FP32 input is the single rounded copy of the basis vector)
+template <typename Tc, typename TU, typename Tout, typename Tin = double>
+static cudaError_t precond_t(pc_handle* h, Launch& L, const Tin* v, Tout* w, size_t stride = 0,
+                             const int* jdev = nullptr, bool index_input = true) {
   typedef typename Cx<Tc>::t C;
   cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::dinv(h),
-                                          Tables<Tc>::tw(h), (C*)h->lv[0].r, stride, jdev);
+                                          Tables<Tc>::tw(h), (C*)h->lv[0].r, index_input ? stride : 0,
+                                          index_input ? jdev : nullptr);
   if (e != cudaSuccess) return e;
   if ((e = spatial_solve<Tc, TU>(h, L)) != cudaSuccess) return e;
   return launch_tfft_inverse<Tc, TU, Tout>(L, h->ms, h->n, (const TU*)h->lv[0].u, Tables<Tc>::dpow(h),
@@ -828,11 +832,11 @@ static cudaError_t precond_t(pc_handle* h, Launch& L, const double* v, Tout* w, 
 }
 
 // FP32 preconditioner into Tout, with the handle's iterate storage
-template <typename Tout>
-static cudaError_t precond32(pc_handle* h, Launch& L, const double* v, Tout* w, size_t stride = 0,
-                             const int* jdev = nullptr) {
-  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout>(h, L, v, w, stride, jdev)
-                  : precond_t<float, float2, Tout>(h, L, v, w, stride, jdev);
+template <typename Tout, typename Tin = double>
+static cudaError_t precond32(pc_handle* h, Launch& L, const Tin* v, Tout* w, size_t stride = 0,
+                             const int* jdev = nullptr, bool index_input = true) {
+  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout, Tin>(h, L, v, w, stride, jdev, index_input)
+                  : precond_t<float, float2, Tout, Tin>(h, L, v, w, stride, jdev, index_input);
 }
 
 // w (FP64) = P^{-1} v in the handle's precision
@@ -980,7 +984,10 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     if (relres) *relres = est_h;
     return PC_OK;
   }
-  GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr));
+  // flexible GMRES with the FP32 preconditioner reads the FP32 rounding of each new
+  // basis vector, written by the kernels that finish it (scale / update)
+  float* vf = (mode == PC_GMRES_RIGHT && h->fp32) ? h->vf32 : nullptr;
+  GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr, vf));
 
   int k = 0;
   bool converged = false;
@@ -990,7 +997,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     if (mode == PC_GMRES_RIGHT) {
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
-        GM_CUDA(precond32<float>(h, L, vj, zj));
+        GM_CUDA(precond32<float, float>(h, L, vf, zj));
         GM_CUDA(launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, zj, vn));
       } else {
         double* zj = (double*)h->Z + (size_t)j * U;
@@ -1005,11 +1012,11 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     // when the check flags cancellation (the gated kernels then do the work)
     GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol, AS.ww, nullptr));
     GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
-    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol, vn, U, AS.inv, h->partial, AS.q, nullptr));
+    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol, vn, U, AS.inv, h->partial, AS.q, nullptr, vf));
     GM_CUDA(launch_arnoldi_check(L, AS));
     GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
     GM_CUDA(launch_update(L, V, U, j + 1, h->hcol + ldh, vn, U, nullptr, h->partial, AS.rho2, AS.flag));
-    GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag));
+    GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag, vf));
     GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, est, ref));
     bool reorth = false;
     if (int rc = read_scalars(h, st, &est_h, nullptr, &reorth)) return rc;
@@ -1106,7 +1113,7 @@ static int enqueue_pre(pc_handle* h, Launch& L, const double* b, double* x, doub
   GR_CUDA(launch_norm2(L, b, U, h->partial, nrm2));
   GR_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, h->scal + 1, h->scal + 2, 1));
   GR_CUDA(cudaMemcpyAsync(h->V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, L.stream));
-  GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr));
+  GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr, h->fp32 ? h->vf32 : nullptr));
   GR_CUDA(launch_loop_start(L, h->idx, h->idx + 1, h->scal + 1, rtol, hc));
   return PC_OK;
 }
@@ -1121,7 +1128,7 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   const Grid g = grid_of(h, 0);
   if (h->fp32) {
     float* Z = (float*)h->Z;
-    GR_CUDA(precond32<float>(h, L, h->V, Z, U, j));
+    GR_CUDA((precond32<float, float>(h, L, h->vf32, Z, U, j, false)));
     GR_CUDA(launch_matvec_df(L, g, h->n, h->wdf, h->ddf, h->alpha_df, Z, h->V, U, U, j));
   } else {
     double* Z = (double*)h->Z;
@@ -1130,11 +1137,12 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   }
   GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol, AS.ww, nullptr));
   GR_CUDA(launch_arnoldi_prep_dev(L, j, h->hcol, AS));
-  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol, h->V, U, U, AS.inv, h->partial, AS.q, nullptr));
+  float* vf = h->fp32 ? h->vf32 : nullptr;
+  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol, h->V, U, U, AS.inv, h->partial, AS.q, nullptr, vf));
   GR_CUDA(launch_arnoldi_check(L, AS));
   GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
   GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol + ldh, h->V, U, U, nullptr, h->partial, AS.rho2, AS.flag));
-  GR_CUDA(launch_scale_dev(L, h->V, U, j, U, AS.rho2, AS.flag));
+  GR_CUDA(launch_scale_dev(L, h->V, U, j, U, AS.rho2, AS.flag, vf));
   GR_CUDA(launch_givens_dev(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, h->scal + 1,
                             h->scal + 2));
   GR_CUDA(launch_loop_control(L, h->idx, h->idx + 1, h->scal + 1, rtol, maxit, hc));
@@ -1471,6 +1479,7 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
   GR_CUDA(cudaMemsetAsync(h->lv[0].r, 0x3e, (size_t)h->planes * h->lv[0].np * cb, st));
   GR_CUDA(cudaMemsetAsync(h->V, 0x3e, h->U * sizeof(double), st));
   GR_CUDA(cudaMemsetAsync(h->Z, 0x3e, h->U * (h->fp32 ? sizeof(float) : sizeof(double)), st));
+  if (h->vf32) GR_CUDA(cudaMemsetAsync(h->vf32, 0x3e, h->U * sizeof(float), st));
   Tiles best = h->tiles;
   // spatial step: fused down-leg tile and grid, then the per-level plane chunk
   if (h->spatial != PC_SPATIAL_FST) {
@@ -1524,8 +1533,9 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
           return launch_tfft_inverse<double, double2, double>(L, h->ms, h->n, (const double2*)h->lv[0].u, h->dpow64,
                                                               h->dinv64, h->tw64, (double*)h->Z);
         }
-        cudaError_t e = launch_tfft_forward<float>(L, h->ms, h->n, h->V, h->dpow32, h->dinv32, h->tw32,
-                                                   (C32*)h->lv[0].r);
+        // flexible GMRES feeds the FP32 transform with the FP32 copy of the basis vector
+        cudaError_t e = launch_tfft_forward<float>(L, h->ms, h->n, (const float*)h->vf32, h->dpow32, h->dinv32,
+                                                   h->tw32, (C32*)h->lv[0].r);
         if (e != cudaSuccess) return e;
         if (h->bf16s)
           return launch_tfft_inverse<float, __nv_bfloat162, float>(L, h->ms, h->n, (const __nv_bfloat162*)h->lv[0].u,

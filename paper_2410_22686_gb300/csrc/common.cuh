@@ -216,8 +216,9 @@ cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, c
 // forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
 // dpow[j] = eps^{j/n}, dinv[j] = eps^{-j/n}, tw[k] = exp(-2 pi i k/n) for k = 0..n-1
 // With jdev != nullptr the input is v + (*jdev) * vstride (device-resident Arnoldi index).
-template <typename Tc>
-cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow, const Tc* dinv,
+// input v: FP64 basis vectors, or (Tc = float) their FP32 rounding
+template <typename Tc, typename Tin = double>
+cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const Tin* v, const Tc* dpow, const Tc* dinv,
                                 const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride = 0,
                                 const int* jdev = nullptr);
 // inverse scaled time FFT + butterfly: spectral planes (stored as TU) -> w (Tout [2][n][ms])
@@ -299,10 +300,11 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
                             double* partial, double* out, double* ww, const double* gate);
 // v = (v - sum_i coef_i V_i) * (*scale or 1); *q = ||v - sum_i coef_i V_i||^2 (before scaling); gated
 cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
-                          const double* scale, double* partial, double* q, const double* gate);
+                          const double* scale, double* partial, double* q, const double* gate, float* vf = nullptr);
 cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, double* nrm2);
 // v *= 1/sqrt(*nrm2); gated
-cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate);
+cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate,
+                                     float* vf = nullptr);
 // y = a*x + b*y (x may be float)
 template <typename Tx>
 cudaError_t launch_axpby(Launch& L, double a, const Tx* x, double b, double* y, size_t len);
@@ -323,9 +325,9 @@ cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_m
                                 double* ww, const double* gate);
 cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
                               double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
-                              double* q, const double* gate);
+                              double* q, const double* gate, float* vf = nullptr);
 cudaError_t launch_scale_dev(Launch& L, double* vbase, size_t vstride, const int* jdev, size_t len,
-                             const double* nrm2, const double* gate);
+                             const double* nrm2, const double* gate, float* vf = nullptr);
 cudaError_t launch_arnoldi_prep_dev(Launch& L, const int* jdev, const double* d, ArnoldiScalars s);
 cudaError_t launch_givens_dev(Launch& L, const int* jdev, int ldh, double* H, double* cs, double* sn, double* gvec,
                               const double* d, const double* e, ArnoldiScalars s, double* est, const double* ref);

@@ -146,13 +146,15 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double*
 }
 
 // v = (v - sum_i coef_i V_i) * scale ;  partial[b] = sum over block b of (v - sum)^2 (before scaling)
-// with jdev != nullptr: nv = *jdev + 1 and v = vbase + nv * vstride
+// with jdev != nullptr: nv = *jdev + 1 and v = vbase + nv * vstride.  vf != nullptr also
+// receives the FP32 rounding of the new v (the FP32 preconditioner's input).
 __global__ void __launch_bounds__(kThreads) update_kernel(const double* __restrict__ V, size_t ldv, int nv,
                                                           const double* __restrict__ coef, double* __restrict__ v,
                                                           size_t len, const double* __restrict__ scale,
                                                           double* __restrict__ partial,
                                                           const double* __restrict__ gate,
-                                                          const int* __restrict__ jdev, size_t vstride) {
+                                                          const int* __restrict__ jdev, size_t vstride,
+                                                          float* __restrict__ vf) {
   if (gated_off(gate)) return;
   if (jdev) {
     nv = *jdev + 1;
@@ -168,7 +170,9 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const double* __restri
     double we = v[e];
     for (int i = 0; i < nv; ++i) we = fma(-hs[i], __ldg(V + (size_t)i * ldv + e), we);
     acc = fma(we, we, acc);
-    v[e] = we * sc;
+    const double vn = we * sc;
+    v[e] = vn;
+    if (vf) vf[e] = f64_to_f32(vn);
   }
   __shared__ double red[kThreads / 32];
   acc = warp_sum(acc);
@@ -197,15 +201,20 @@ __global__ void __launch_bounds__(kThreads) norm2_kernel(const double* __restric
   }
 }
 
-// v *= 1/sqrt(nrm2[0])  (gated)
+// v *= 1/sqrt(nrm2[0])  (gated); vf != nullptr also receives the FP32 rounding of v
 __global__ void scale_kernel(double* __restrict__ v, size_t len, const double* __restrict__ nrm2,
-                             const double* __restrict__ gate, const int* __restrict__ jdev, size_t vstride) {
+                             const double* __restrict__ gate, const int* __restrict__ jdev, size_t vstride,
+                             float* __restrict__ vf) {
   if (gated_off(gate)) return;
   if (jdev) v += (size_t)(*jdev + 1) * vstride;
-  if (!(nrm2[0] > 0.0)) return;  // zero vector: nothing to normalise
-  const double q = 1.0 / sqrt(nrm2[0]);
+  const bool nz = nrm2[0] > 0.0;  // zero vector: nothing to normalise
+  const double q = nz ? 1.0 / sqrt(nrm2[0]) : 1.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) v[e] *= q;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const double x = nz ? v[e] * q : v[e];
+    if (nz) v[e] = x;
+    if (vf) vf[e] = f64_to_f32(x);
+  }
 }
 
 template <typename Tx>
@@ -413,13 +422,14 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
 }
 
 cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
-                          const double* scale, double* partial, double* q, const double* gate) {
+                          const double* scale, double* partial, double* q, const double* gate, float* vf) {
   const size_t smem = sizeof(double) * (nv > 0 ? nv : 1);
   const unsigned nb = wave_blocks(update_kernel, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
-  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate, nullptr, 0);
-  cudaError_t e = gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
+  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate, nullptr, 0, vf);
+  cudaError_t e = gate ? L.end(kc, 0.0, 0.0)
+                       : L.end(kc, 8.0 * len * (nv + 2) + (vf ? 4.0 * len : 0.0), 2.0 * len * (nv + 1));
   if (e != cudaSuccess) return e;
   const int kr = gate ? KC_REORTH : KC_REDUCE;
   L.begin(kr);
@@ -439,11 +449,12 @@ cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial
   return L.end(KC_REDUCE, 8.0 * nb, 1.0 * nb);
 }
 
-cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate) {
+cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate,
+                                     float* vf) {
   const int kc = gate ? KC_REORTH : KC_SCALE;
   L.begin(kc);
-  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, len, nrm2, gate, nullptr, 0);
-  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len, 1.0 * len);
+  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, len, nrm2, gate, nullptr, 0, vf);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len + (vf ? 4.0 * len : 0.0), 1.0 * len);
 }
 
 template <typename Tx>
@@ -531,13 +542,13 @@ cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_m
 
 cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
                               double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
-                              double* q, const double* gate) {
+                              double* q, const double* gate, float* vf) {
   const size_t smem = sizeof(double) * nv_max;
   const unsigned nb = wave_blocks(update_kernel, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
   update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv_max, coef, vbase, len, scale, partial, gate, jdev,
-                                                  vstride);
+                                                  vstride, vf);
   cudaError_t e = L.end(kc, 0.0, 0.0);
   if (e != cudaSuccess) return e;
   L.begin(kc);
@@ -546,9 +557,9 @@ cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max
 }
 
 cudaError_t launch_scale_dev(Launch& L, double* vbase, size_t vstride, const int* jdev, size_t len,
-                             const double* nrm2, const double* gate) {
+                             const double* nrm2, const double* gate, float* vf) {
   L.begin(KC_REORTH);
-  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(vbase, len, nrm2, gate, jdev, vstride);
+  scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(vbase, len, nrm2, gate, jdev, vstride, vf);
   return L.end(KC_REORTH, 0.0, 0.0);
 }
 

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(const Tin* __restrict__ x, 
 
   double x1prev = (j0 > 0) ? cvt<double>(x1[(int64_t)(j0 - 1) * ms + s]) : 0.0;
   double x2c = cvt<double>(x2[(int64_t)j0 * ms + s]);
+#pragma unroll 2
   for (int j = j0; j < j1; ++j) {
     const int64_t idx = (int64_t)j * ms + s;
     const double x1c = cvt<double>(x1[idx]);
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict_
   float x1prev = (j0 > 0) ? x1[(int64_t)(j0 - 1) * ms + s] : 0.0f;
   float x2c = x2[(int64_t)j0 * ms + s];
   constexpr int NT = 2 * DIM + 4;  // terms per output
+#pragma unroll 2
   for (int j = j0; j < j1; ++j) {
     const int64_t idx = (int64_t)j * ms + s;
     const float x1c = x1[idx];

@@ -108,8 +108,8 @@ __device__ __forceinline__ void fft_columns(typename Cx<Tc>::t* z, const typenam
   }
 }
 
-template <typename Tc>
-__global__ void __launch_bounds__(256) tfft_forward_kernel(const double* __restrict__ v, const Tc* __restrict__ dpow,
+template <typename Tc, typename Tin>
+__global__ void __launch_bounds__(256) tfft_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
                                                            const typename Cx<Tc>::t* __restrict__ tw,
                                                            typename Cx<Tc>::t* __restrict__ spec, int64_t ms, int n,
                                                            int logn, int TS) {
@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(256) tfft_forward_kernel(const double* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* z = reinterpret_cast<C*>(smem_raw);
   const int64_t s0 = (int64_t)blockIdx.x * TS;
-  const double* v1 = v;
-  const double* v2 = v + (int64_t)n * ms;
+  const Tin* v1 = v;
+  const Tin* v2 = v + (int64_t)n * ms;
   for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
     const int j = e / TS;
     const int c = e - j * TS;
@@ -546,8 +546,8 @@ __global__ void __launch_bounds__(256) tfft4s_inverse_kernel(const TU* __restric
 // runs use n = 2^k - 1): a CTA holds TS columns of all n time samples in shared
 // memory and forms each needed frequency as a plain sum with the twiddle index
 // advanced incrementally modulo n.  n^2 work per column.
-template <typename Tc>
-__global__ void __launch_bounds__(256) tdft_forward_kernel(const double* __restrict__ v, const Tc* __restrict__ dpow,
+template <typename Tc, typename Tin>
+__global__ void __launch_bounds__(256) tdft_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
                                                            const Tc* __restrict__ dinv,
                                                            const typename Cx<Tc>::t* __restrict__ tw,
                                                            typename Cx<Tc>::t* __restrict__ spec, int64_t ms, int n,
@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(256) tdft_forward_kernel(const double* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* z = reinterpret_cast<C*>(smem_raw);  // [n][TS]
   const int64_t s0 = (int64_t)blockIdx.x * TS;
-  const double* v1 = v;
-  const double* v2 = v + (int64_t)n * ms;
+  const Tin* v1 = v;
+  const Tin* v2 = v + (int64_t)n * ms;
   for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
     const int j = e / TS, c = e - (e / TS) * TS;
     const int64_t s = s0 + c;
@@ -819,8 +819,8 @@ cudaError_t inv4_dispatch(Launch& L, int64_t ms, int n, const TU* spec, const Tc
   return cudaErrorInvalidValue;
 }
 
-template <typename Tc>
-cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, const Tc* dpow, const Tc* dinv,
+template <typename Tc, typename Tin>
+cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const Tin* v, const Tc* dpow, const Tc* dinv,
                                 const typename Cx<Tc>::t* tw, typename Cx<Tc>::t* spec, size_t vstride,
                                 const int* jdev) {
   const bool pow2 = (n & (n - 1)) == 0;
@@ -828,32 +828,32 @@ cudaError_t launch_tfft_forward(Launch& L, int64_t ms, int n, const double* v, c
   if (!pow2) {
     const int TS = pick_ts_dft<Tc>(n);
     const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
-    cudaError_t e = cudaFuncSetAttribute(tdft_forward_kernel<Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(tdft_forward_kernel<Tc, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nf = n / 2 + 1;
     L.begin(KC_TFFT_FWD);
-    tdft_forward_kernel<Tc><<<(unsigned)((ms + TS - 1) / TS), 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, n, TS);
-    return L.end(KC_TFFT_FWD, 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t),
+    tdft_forward_kernel<Tc, Tin><<<(unsigned)((ms + TS - 1) / TS), 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, n, TS);
+    return L.end(KC_TFFT_FWD, 2.0 * n * ms * sizeof(Tin) + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t),
                  16.0 * (double)nf * n * ms);
   }
   if (n <= four_step_max<Tc>()) {
     const int nf = n / 2 + 1;
-    const double bytes = 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
+    const double bytes = 2.0 * n * ms * sizeof(Tin) + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
     const double flops = (double)ms * (5.0 * n * ilog2(n) + 2.0 * n);
     L.begin(KC_TFFT_FWD);
-    fwd4_dispatch<double, Tc>(L, ms, n, v, dpow, dinv, tw, spec, vstride, jdev);
+    fwd4_dispatch<Tin, Tc>(L, ms, n, v, dpow, dinv, tw, spec, vstride, jdev);
     return L.end(KC_TFFT_FWD, bytes, flops);
   }
   const int TS = pick_ts<Tc>(n);
   const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
-  cudaError_t e = cudaFuncSetAttribute(tfft_forward_kernel<Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(tfft_forward_kernel<Tc, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ms + TS - 1) / TS);
   const int nf = n / 2 + 1;
-  const double bytes = 2.0 * n * ms * 8.0 + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
+  const double bytes = 2.0 * n * ms * sizeof(Tin) + 2.0 * nf * ms * sizeof(typename Cx<Tc>::t);
   const double flops = (double)ms * (5.0 * n * ilog2(n) + 2.0 * n);
   L.begin(KC_TFFT_FWD);
-  tfft_forward_kernel<Tc><<<blocks, 256, smem, L.stream>>>(v, dpow, tw, spec, ms, n, ilog2(n), TS);
+  tfft_forward_kernel<Tc, Tin><<<blocks, 256, smem, L.stream>>>(v, dpow, tw, spec, ms, n, ilog2(n), TS);
   return L.end(KC_TFFT_FWD, bytes, flops);
 }
 
@@ -900,10 +900,12 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
   return L.end(KC_TFFT_INV, bytes, flops);
 }
 
-template cudaError_t launch_tfft_forward<double>(Launch&, int64_t, int, const double*, const double*, const double*,
-                                                 const double2*, double2*, size_t, const int*);
-template cudaError_t launch_tfft_forward<float>(Launch&, int64_t, int, const double*, const float*, const float*,
-                                                const float2*, float2*, size_t, const int*);
+template cudaError_t launch_tfft_forward<double, double>(Launch&, int64_t, int, const double*, const double*,
+                                                         const double*, const double2*, double2*, size_t, const int*);
+template cudaError_t launch_tfft_forward<float, double>(Launch&, int64_t, int, const double*, const float*,
+                                                        const float*, const float2*, float2*, size_t, const int*);
+template cudaError_t launch_tfft_forward<float, float>(Launch&, int64_t, int, const float*, const float*,
+                                                       const float*, const float2*, float2*, size_t, const int*);
 #define PCOPT_INV(Tc, TU, Tout)                                                                                  \
   template cudaError_t launch_tfft_inverse<Tc, TU, Tout>(Launch&, int64_t, int, const TU*, const Tc*, const Tc*, \
                                                          const Cx<Tc>::t*, Tout*, size_t, const int*,         \

@@ -23,14 +23,14 @@ import os
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiles_gb300.json")
 FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch", "fft_stream")
 
-# (dim, m1, n, precision): the bench and test workloads
-WORKLOADS = (
+# (dim, m1, n, precision): the bench and test workloads, each shape once
+WORKLOADS = tuple(dict.fromkeys(
     [(2, 255, 256, p) for p in ("mixed", "bf16s", "fp64")]
     + [(3, 63, 128, p) for p in ("mixed", "bf16s", "fp64")]
     + [(2, 127, 128, p) for p in ("fp64", "mixed")]
     + [(2, 31, 32, "fp64")]
     + [(2, m, n, "mixed") for m in (31, 63, 127, 255) for n in (16, 64, 256, 512)]
-)
+))
 
 _cache: dict | None = None
 
