@@ -236,10 +236,15 @@ int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
  *   fft_stream: time FFTs (power-of-two n): 0 = one CTA per tile of spatial
  *            columns (default), 1 = persistent CTAs that copy the next tile into
  *            shared memory (cp.async) while transforming the current one.
+ *   mg_march: fused 2D down leg with FP32 iterates: 0 = shared-memory tiles
+ *            (default), 1 = register-marching warps (a warp walks the rows of one
+ *            plane over a 64-column strip; neighbours by lane shuffles).
+ *   mg_seg:  register-marching down leg: coarse rows per warp, 1..1024 (default 16).
  * pc_set_tiles validates (PC_ERR_ARG), applies the shapes to every later call on
  * the handle and drops its cached solve graph.  pc_autotune times candidate
  * shapes on the handle's own workspace (the multigrid spatial step for each
- * (mg_cx, mg_ctas), then pro_pch; the forward + inverse time FFT for each
+ * (mg_cx, mg_ctas) and, with FP32 iterates, the register-marching kernel for each
+ * mg_seg, then pro_pch; the forward + inverse time FFT for each
  * fft_stream; the matvec for each mv_tj), `reps` timed calls
  * each (1..100) after one untimed call, keeps the fastest, applies it and copies
  * it to *chosen (may be NULL).  It synchronises `stream`, overwrites the
@@ -251,6 +256,8 @@ typedef struct pc_tiles {
   int mv_tj;
   int pro_pch;
   int fft_stream;
+  int mg_march;
+  int mg_seg;
 } pc_tiles;
 
 int pc_get_tiles(const pc_handle* h, pc_tiles* out);

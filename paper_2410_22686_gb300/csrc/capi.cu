@@ -142,6 +142,7 @@ struct LevelBuf {
   double* d64 = nullptr;   // [np]
   float* w32 = nullptr;
   float* d32 = nullptr;
+  float4* w4 = nullptr;    // 2D FP32 handles: the four face weights of each point packed (np)
   void* r = nullptr;       // complex spectral planes (Tc)
   void* u = nullptr;
   void* res = nullptr;
@@ -376,6 +377,14 @@ static int upload(pc_handle* h, T** dst, const std::vector<double>& src, cudaStr
   return PC_OK;
 }
 
+// face weights [4][np] (2D) packed per point for one-load access
+static std::vector<float4> pack_w4(const std::vector<double>& w, int64_t np) {
+  std::vector<float4> t((size_t)np);
+  for (int64_t i = 0; i < np; ++i)
+    t[i] = make_float4((float)w[i], (float)w[np + i], (float)w[2 * np + i], (float)w[3 * np + i]);
+  return t;
+}
+
 static int upload_c(pc_handle* h, void** dst, const std::vector<double>& re, const std::vector<double>& im, bool f32,
                     cudaStream_t st) {
   const size_t n = re.size();
@@ -469,6 +478,15 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       if ((rc = upload(h, &L.d64, ds[l], st))) goto fail_out;
       if ((rc = upload(h, &L.w32, ws[l], st))) goto fail_out;
       if ((rc = upload(h, &L.d32, ds[l], st))) goto fail_out;
+      if (dim == 2 && h->fp32) {
+        const std::vector<float4> w4 = pack_w4(ws[l], L.np);
+        if ((rc = dev_alloc_t(h, &L.w4, w4.size()))) goto fail_out;
+        if (cudaMemcpyAsync(L.w4, w4.data(), w4.size() * sizeof(float4), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          rc = fail(PC_ERR_CUDA, "upload of packed face weights failed");
+          goto fail_out;
+        }
+      }
       if ((rc = dev_alloc(h, &L.r, (size_t)h->planes * L.np * cb))) goto fail_out;
       if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * ub))) goto fail_out;
       // per-level residual planes: only the 3D path writes them (2D fuses the residual away)
@@ -651,6 +669,11 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
     if ((rc = refill(h->lv[l].d64, ds[l], st, s64))) return rc;
     if ((rc = refill(h->lv[l].w32, ws[l], st, s32))) return rc;
     if ((rc = refill(h->lv[l].d32, ds[l], st, s32))) return rc;
+    if (h->lv[l].w4) {
+      const std::vector<float4> w4 = pack_w4(ws[l], h->lv[l].np);
+      PC_CUDA(cudaMemcpyAsync(h->lv[l].w4, w4.data(), w4.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+      PC_CUDA(cudaStreamSynchronize(st));
+    }
   }
   {
     std::vector<float2> wsp(ws[0].size()), dsp(ds[0].size());
@@ -776,8 +799,8 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
     Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
     const Grid g = grid_of(h, l);
     if (g.dim == 2) {
-      if ((e = launch_mg_down<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u, (C*)h->lv[l + 1].r)) !=
-          cudaSuccess)
+      if ((e = launch_mg_down<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u, (C*)h->lv[l + 1].r, 0, 0,
+                                      Lb.w4)) != cudaSuccess)
         return e;
       continue;
     }
@@ -1406,6 +1429,8 @@ static int check_tiles(const pc_tiles* t) {
   if (t->mv_tj < 0 || t->mv_tj > 4096) return fail(PC_ERR_ARG, "mv_tj must be in [0, 4096]");
   if (t->pro_pch < 0 || t->pro_pch > 64) return fail(PC_ERR_ARG, "pro_pch must be in [0, 64]");
   if (t->fft_stream < 0 || t->fft_stream > 1) return fail(PC_ERR_ARG, "fft_stream must be 0 or 1");
+  if (t->mg_march < 0 || t->mg_march > 1) return fail(PC_ERR_ARG, "mg_march must be 0 or 1");
+  if (t->mg_seg < 0 || t->mg_seg > 1024) return fail(PC_ERR_ARG, "mg_seg must be in [0, 1024]");
   return PC_OK;
 }
 
@@ -1421,6 +1446,8 @@ extern "C" int pc_get_tiles(const pc_handle* h, pc_tiles* out) {
   out->mv_tj = h->tiles.mv_tj;
   out->pro_pch = h->tiles.pro_pch;
   out->fft_stream = h->tiles.fft_stream;
+  out->mg_march = h->tiles.mg_march;
+  out->mg_seg = h->tiles.mg_seg;
   return PC_OK;
 }
 
@@ -1432,6 +1459,8 @@ extern "C" int pc_set_tiles(pc_handle* h, const pc_tiles* t) {
   h->tiles.mv_tj = t->mv_tj;
   h->tiles.pro_pch = t->pro_pch;
   h->tiles.fft_stream = t->fft_stream;
+  h->tiles.mg_march = t->mg_march;
+  h->tiles.mg_seg = t->mg_seg;
   drop_graphs(h);  // a cached solve graph holds the old launch shapes
   return PC_OK;
 }
@@ -1493,6 +1522,7 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
         if (fused) {
           t.mg_cx = cxs[ci];
           t.mg_ctas = ctas[ki];
+          t.mg_march = 0;
         }
         Launch L{st, nullptr, &t};
         const double ms = time_reps(st, reps, [&] { return spatial_for(h, L); });
@@ -1500,8 +1530,24 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
           tbest = ms;
           best.mg_cx = t.mg_cx;
           best.mg_ctas = t.mg_ctas;
+          best.mg_march = 0;
         }
       }
+    // the register-marching down leg (FP32 iterates), by coarse rows per segment
+    const bool march = fused && h->fp32 && !h->bf16s && h->lv[0].w4;
+    const int segs[4] = {8, 16, 32, 64};
+    for (int si = 0; si < (march ? 4 : 0); ++si) {
+      Tiles t = best;
+      t.mg_march = 1;
+      t.mg_seg = segs[si];
+      Launch L{st, nullptr, &t};
+      const double ms = time_reps(st, reps, [&] { return spatial_for(h, L); });
+      if (ms < tbest) {
+        tbest = ms;
+        best.mg_march = 1;
+        best.mg_seg = segs[si];
+      }
+    }
     const int pchs[5] = {2, 4, 8, 16, 32};
     if (h->coarse_l0 >= 2 || (h->dim == 3 && h->coarse_l0 >= 1)) {
       tbest = HUGE_VAL;

@@ -167,6 +167,8 @@ struct Tiles {
   int mv_tj = 0;    // matvec kernels: time blocks per thread
   int pro_pch = 0;  // prolongation and per-level (3D) multigrid kernels: planes per CTA
   int fft_stream = 0;  // time FFTs: 0 one CTA per column tile, 1 persistent CTAs streaming tiles (cp.async)
+  int mg_march = 0;    // fused 2D down leg with FP32 iterates: 0 shared-memory tiles, 1 register-marching warps
+  int mg_seg = 0;      // register-marching down leg: coarse rows per warp segment (default 16)
   int sms = 0;      // SMs of the device (set at setup)
 };
 
@@ -258,7 +260,7 @@ cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const
 template <typename Tc, typename TU>
 cudaError_t launch_mg_down(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                            const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u,
-                           typename Cx<Tc>::t* rc, int cx = 0, int pch = 0);
+                           typename Cx<Tc>::t* rc, int cx = 0, int pch = 0, const float4* w4 = nullptr);
 int mg_down_default_cx(int tc_bytes);
 int mg_down_default_pch(int m, int planes, int cx, int ctas_per_sm, int sms);
 template <typename Tc, typename TU>

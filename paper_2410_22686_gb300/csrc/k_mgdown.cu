@@ -18,6 +18,8 @@
 // Values of u are rounded to the storage type TU before any later step reads
 // them, so the BF16-storage variant smooths, takes residuals and is corrected on
 // exactly what it stores.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace pcopt {
@@ -277,6 +279,176 @@ __global__ void __launch_bounds__(256) mg_down2_kernel(const typename Cx<Tc>::t*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-marching variant (FP32 iterates): no shared memory, no barriers.  A warp
+// owns one spectral plane, a strip of 64 fine columns (lane q: the column pair
+// cA = 2 I0 - 2 + 2q, cB = cA + 1, which always holds one red and one black cell)
+// and a segment of coarse rows [J0, J1); it walks the fine rows t = 2 J0 - 2 ...
+// 2 J1 + 2 and at each step forms
+//   red u of row t (from r and the shift alone),
+//   black u of row t - 1 (red neighbours: the lane's own rows t - 2, t - 1, t and
+//     the pair partner or the neighbouring lane's row t - 1 via a shuffle),
+//   the red residual of row t - 2 (black neighbours likewise, the sweep-from-zero
+//     identity: res_red = sum_k w_k u_black, res_black = 0),
+//   and, when row t - 2 = 2J + 2 is even, the full-weighting value of coarse row J
+//     from the residual rows 2J, 2J + 1, 2J + 2 (centre at cB, corners at cA and at
+//     the next lane's cA).
+// Lanes 1..29 own their pairs and coarse points; lanes 0, 30, 31 are the halo whose
+// values only feed their neighbours.  Rows and columns outside the grid hold zero.
+constexpr int kMarchPairs = 29;
+
+__device__ __forceinline__ float2 shfl_dn(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_upc(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ void prefetch_l1(const void* ptr) { asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr)); }
+
+// State of one lane between steps: red u of rows t-2, t-1 (R0, R1), black u of rows
+// t-3, t-2 (B0, B1), the black r of row t-1, the last even-row restriction partial
+// and the last odd-row residual; r of rows t and t+1 in flight.
+struct MarchState {
+  float2 R0, R1, B0, B1, rbp, Ep, ro, nA0, nB0, nA1, nB1;
+};
+
+// One step at row t; EV = (t even).  Red cells: cA on even rows, cB on odd rows.
+template <bool EV>
+__device__ __forceinline__ void march_step(MarchState& S, int t, const float2* __restrict__ rp,
+                                           float2* __restrict__ up, float2* __restrict__ rcp,
+                                           const float4* __restrict__ w4, const float* __restrict__ diag,
+                                           float2 sig, int m, int mc, int cA, bool inA, bool inB, bool own,
+                                           bool ownc, int Ic, int k0, int k1, int J0, int J1) {
+  const float2 z = make_float2(0.f, 0.f);
+  const int cB = cA + 1;
+  const float2 rA = S.nA0, rB = S.nB0;
+  S.nA0 = S.nA1;
+  S.nB0 = S.nB1;
+  {  // r two rows ahead, coefficients three rows ahead into L1
+    const int t2 = t + 2;
+    const bool ok = t2 >= 0 && t2 < m;
+    const int o = t2 * m;
+    S.nA1 = (ok && inA) ? rp[o + cA] : z;
+    S.nB1 = (ok && inB) ? rp[o + cB] : z;
+    const int t3 = t + 3;
+    if (inA && t3 >= 0 && t3 < m) {
+      prefetch_l1(w4 + t3 * m + cA);
+      prefetch_l1(diag + t3 * m + cA);
+    }
+  }
+  // red u of row t
+  float2 R2 = z;
+  {
+    const int c = EV ? cA : cB;
+    if ((EV ? inA : inB) && t >= 0 && t < m)
+      R2 = cmul(EV ? rA : rB, inv_shift(make_float2(sig.x + diag[t * m + c], sig.y)));
+  }
+  // black u of row t - 1 (black at cB on even rows, at cA on odd rows)
+  float2 B2 = z;
+  {
+    const int k = t - 1;  // parity opposite to t
+    const float2 nb = EV ? shfl_upc(S.R1) : shfl_dn(S.R1);
+    const float2 left = EV ? nb : S.R1, right = EV ? S.R1 : nb;
+    const int c = EV ? cA : cB;
+    if ((EV ? inA : inB) && k >= 0 && k < m) {
+      const int o = k * m + c;
+      const float4 wv = w4[o];
+      float2 acc = S.rbp;
+      cfma<float>(acc, wv.x, left);
+      cfma<float>(acc, wv.y, right);
+      cfma<float>(acc, wv.z, S.R0);
+      cfma<float>(acc, wv.w, R2);
+      B2 = cmul(acc, inv_shift(make_float2(sig.x + diag[o], sig.y)));
+    }
+    if (own && k >= k0 && k < k1) {
+      const int o = k * m;
+      if (inA) up[o + cA] = EV ? B2 : S.R1;
+      if (inB) up[o + cB] = EV ? S.R1 : B2;
+    }
+  }
+  // red residual of row t - 2 (same parity as t)
+  {
+    const int k2 = t - 2;
+    const float2 nb = EV ? shfl_upc(S.B1) : shfl_dn(S.B1);
+    const float2 left = EV ? nb : S.B1, right = EV ? S.B1 : nb;
+    const int c = EV ? cA : cB;
+    float2 res = z;
+    if ((EV ? inA : inB) && k2 >= 0 && k2 < m) {
+      const float4 wv = w4[k2 * m + c];
+      res.x = wv.x * left.x;
+      res.y = wv.x * left.y;
+      cfma<float>(res, wv.y, right);
+      cfma<float>(res, wv.z, S.B0);
+      cfma<float>(res, wv.w, B2);
+    }
+    if (EV) {
+      const float2 sdr = shfl_dn(res);
+      const float2 E = make_float2(res.x + sdr.x, res.y + sdr.y);
+      const int J = (k2 >> 1) - 1;  // coarse row whose last residual row is k2
+      if (ownc && J >= J0 && J < J1) {
+        float2 v;
+        v.x = fmaf(0.25f, S.ro.x, 0.0625f * (S.Ep.x + E.x));
+        v.y = fmaf(0.25f, S.ro.y, 0.0625f * (S.Ep.y + E.y));
+        rcp[J * mc + Ic] = v;
+      }
+      S.Ep = E;
+    } else {
+      S.ro = res;
+    }
+  }
+  S.R0 = S.R1;
+  S.R1 = R2;
+  S.B0 = S.B1;
+  S.B1 = B2;
+  S.rbp = EV ? rB : rA;  // black r of row t
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) mg_down2_march_kernel(const float2* __restrict__ r,
+                                                                    float2* __restrict__ u,
+                                                                    float2* __restrict__ rc,
+                                                                    const float4* __restrict__ w4,
+                                                                    const float* __restrict__ diag,
+                                                                    const float2* __restrict__ sigma, int m,
+                                                                    int planes, int segj, int nstrips) {
+  const int lane = threadIdx.x & 31;
+  const int p = blockIdx.y * WARPS + (threadIdx.x >> 5);
+  if (p >= planes) return;  // whole warp
+  const int mc = (m - 1) / 2;
+  const int st = blockIdx.x % nstrips, sg = blockIdx.x / nstrips;
+  const int I0 = st * kMarchPairs;
+  const int J0 = sg * segj, J1 = min(mc, J0 + segj);
+  const int k0 = 2 * J0, k1 = (J1 == mc) ? m : 2 * J1;
+  const int cA = 2 * I0 - 2 + 2 * lane;
+  const bool inA = cA >= 0 && cA < m, inB = cA + 1 >= 0 && cA + 1 < m;
+  const bool own = lane >= 1 && lane <= kMarchPairs;
+  const int Ic = I0 - 1 + lane;
+  const bool ownc = own && Ic < mc;
+  const int64_t np = (int64_t)m * m;
+  const float2* rp = r + (int64_t)p * np;
+  float2* up = u + (int64_t)p * np;
+  float2* rcp = rc + (int64_t)p * mc * mc;
+  const float2 sig = sigma[p];
+  const float2 z = make_float2(0.f, 0.f);
+  MarchState S{z, z, z, z, z, z, z, z, z, z, z};
+  // rows k0 - 2 (even) and k0 - 1 in flight before the first step
+  if (k0 - 2 >= 0) {
+    S.nA0 = inA ? rp[(k0 - 2) * m + cA] : z;
+    S.nB0 = inB ? rp[(k0 - 2) * m + cA + 1] : z;
+  }
+  if (k0 - 1 >= 0) {
+    S.nA1 = inA ? rp[(k0 - 1) * m + cA] : z;
+    S.nB1 = inB ? rp[(k0 - 1) * m + cA + 1] : z;
+  }
+  const int tEnd = 2 * J1 + 2;  // even, like the first row k0 - 2
+  int t = k0 - 2;
+  for (; t + 1 <= tEnd; t += 2) {
+    march_step<true>(S, t, rp, up, rcp, w4, diag, sig, m, mc, cA, inA, inB, own, ownc, Ic, k0, k1, J0, J1);
+    march_step<false>(S, t + 1, rp, up, rcp, w4, diag, sig, m, mc, cA, inA, inB, own, ownc, Ic, k0, k1, J0, J1);
+  }
+  march_step<true>(S, t, rp, up, rcp, w4, diag, sig, m, mc, cA, inA, inB, own, ownc, Ic, k0, k1, J0, J1);
+}
+
 template <typename Tc, typename TU, int CX>
 cudaError_t down2(Launch& L, int m, int planes, int pch, const Tc* w, const Tc* diag,
                   const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u, typename Cx<Tc>::t* rc) {
@@ -316,8 +488,29 @@ int mg_down_default_pch(int m, int planes, int cx, int ctas_per_sm, int sms) {
 template <typename Tc, typename TU>
 cudaError_t launch_mg_down(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                            const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u,
-                           typename Cx<Tc>::t* rc, int cx, int pch) {
+                           typename Cx<Tc>::t* rc, int cx, int pch, const float4* w4) {
   if (g.dim != 2 || g.m < 3 || (g.m & 1) == 0) return cudaErrorInvalidValue;
+  if constexpr (std::is_same<Tc, float>::value && std::is_same<TU, float2>::value) {
+    if (w4 && L.tiles && L.tiles->mg_march > 0) {
+      constexpr int WARPS = 4;
+      const int mc = (g.m - 1) / 2;
+      const int nstrips = (mc + kMarchPairs - 1) / kMarchPairs;
+      // the tuned segment length, shortened on small levels until the grid holds
+      // about 32 warps per SM
+      int segj = L.tiles->mg_seg > 0 ? L.tiles->mg_seg : 16;
+      const long target = 32L * (L.tiles->sms > 0 ? L.tiles->sms : 152);
+      const long need = (target + (long)nstrips * planes - 1) / ((long)nstrips * planes);
+      if (need > 1) segj = std::min(segj, std::max(2, (int)(mc / need)));
+      const int nsegs = (mc + segj - 1) / segj;
+      const double tot = (double)g.np * planes;
+      L.begin(KC_MG_DOWN);
+      mg_down2_march_kernel<WARPS><<<dim3((unsigned)(nstrips * nsegs), (unsigned)((planes + WARPS - 1) / WARPS)),
+                                     32 * WARPS, 0, L.stream>>>(r, u, rc, w4, st.diag, sigma, g.m, planes, segj,
+                                                                nstrips);
+      return L.end(KC_MG_DOWN, tot * (sizeof(float2) + sizeof(float2)) + (double)mc * mc * planes * sizeof(float2),
+                   tot * 60.0);
+    }
+  }
   if (cx <= 0 && L.tiles) cx = L.tiles->mg_cx;
   if (cx <= 0) cx = mg_down_default_cx((int)sizeof(Tc));
   if (pch <= 0)
@@ -341,7 +534,7 @@ cudaError_t launch_mg_down(Launch& L, const Grid& g, int planes, const Stencil<T
 
 #define PCOPT_INST_DOWN(Tc, TU)                                                                              \
   template cudaError_t launch_mg_down<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&, const Cx<Tc>::t*, \
-                                              const Cx<Tc>::t*, TU*, Cx<Tc>::t*, int, int);
+                                              const Cx<Tc>::t*, TU*, Cx<Tc>::t*, int, int, const float4*);
 PCOPT_INST_DOWN(float, float2)
 PCOPT_INST_DOWN(double, double2)
 PCOPT_INST_DOWN(float, __nv_bfloat162)

@@ -2,7 +2,8 @@
 
 ``pc_autotune`` times candidate tile shapes of the tunable kernels on one handle
 (fused multigrid down leg: tile width and CTAs per SM; prolongation planes per
-CTA; streaming or one-CTA-per-tile time FFTs; matvec time blocks per thread) and keeps the fastest.  This module keeps
+CTA; shared-memory or register-marching down leg; streaming or one-CTA-per-tile
+time FFTs; matvec time blocks per thread) and keeps the fastest.  This module keeps
 the chosen shapes in a JSON table next to the package, keyed by
 (dim, m1, n, precision), so that ``Solver(..., tiles="table")`` (the default)
 starts with the tuned shapes without re-timing.  Shapes missing from the table
@@ -21,7 +22,7 @@ import json
 import os
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tiles_gb300.json")
-FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch", "fft_stream")
+FIELDS = ("mg_cx", "mg_ctas", "mv_tj", "pro_pch", "fft_stream", "mg_march", "mg_seg")
 
 # (dim, m1, n, precision): the bench and test workloads, each shape once
 WORKLOADS = tuple(dict.fromkeys(
@@ -109,7 +110,9 @@ def main(argv=None):
                       "mg_ctas": "fused down-leg CTAs per SM",
                       "mv_tj": "matvec time blocks per thread",
                       "pro_pch": "prolongation / 3D per-level planes per CTA",
-                      "fft_stream": "time FFTs: 0 one CTA per tile, 1 persistent streaming CTAs"},
+                      "fft_stream": "time FFTs: 0 one CTA per tile, 1 persistent streaming CTAs",
+                      "mg_march": "fused down leg: 0 shared-memory tiles, 1 register-marching warps",
+                      "mg_seg": "register-marching down leg: coarse rows per warp"},
            "entries": entries}
     with open(args.out, "w") as fh:
         json.dump(doc, fh, indent=1, sort_keys=True)
