@@ -307,9 +307,11 @@ __device__ __forceinline__ void prefetch_l1(const void* ptr) { asm volatile("pre
 
 // State of one lane between steps: red u of rows t-2, t-1 (R0, R1), black u of rows
 // t-3, t-2 (B0, B1), the black r of row t-1, the last even-row restriction partial
-// and the last odd-row residual; r of rows t and t+1 in flight.
+// and the last odd-row residual; r of rows t .. t + kMarchAhead - 1 in flight.
+constexpr int kMarchAhead = 2;  // (4 was slower: fewer resident warps)
 struct MarchState {
-  float2 R0, R1, B0, B1, rbp, Ep, ro, nA0, nB0, nA1, nB1;
+  float2 R0, R1, B0, B1, rbp, Ep, ro;
+  float2 nA[kMarchAhead], nB[kMarchAhead];
 };
 
 // One step at row t; EV = (t even).  Red cells: cA on even rows, cB on odd rows.
@@ -321,19 +323,22 @@ __device__ __forceinline__ void march_step(MarchState& S, int t, const float2* _
                                            bool ownc, int Ic, int k0, int k1, int J0, int J1) {
   const float2 z = make_float2(0.f, 0.f);
   const int cB = cA + 1;
-  const float2 rA = S.nA0, rB = S.nB0;
-  S.nA0 = S.nA1;
-  S.nB0 = S.nB1;
-  {  // r two rows ahead, coefficients three rows ahead into L1
-    const int t2 = t + 2;
-    const bool ok = t2 >= 0 && t2 < m;
-    const int o = t2 * m;
-    S.nA1 = (ok && inA) ? rp[o + cA] : z;
-    S.nB1 = (ok && inB) ? rp[o + cB] : z;
-    const int t3 = t + 3;
-    if (inA && t3 >= 0 && t3 < m) {
-      prefetch_l1(w4 + t3 * m + cA);
-      prefetch_l1(diag + t3 * m + cA);
+  const float2 rA = S.nA[0], rB = S.nB[0];
+#pragma unroll
+  for (int i = 0; i + 1 < kMarchAhead; ++i) {
+    S.nA[i] = S.nA[i + 1];
+    S.nB[i] = S.nB[i + 1];
+  }
+  {  // r kMarchAhead rows ahead in flight, coefficients one row further into L1
+    const int ta = t + kMarchAhead;
+    const bool ok = ta >= 0 && ta < m;
+    const int o = ta * m;
+    S.nA[kMarchAhead - 1] = (ok && inA) ? rp[o + cA] : z;
+    S.nB[kMarchAhead - 1] = (ok && inB) ? rp[o + cB] : z;
+    const int tc = ta + 1;
+    if (inA && tc >= 0 && tc < m) {
+      prefetch_l1(w4 + tc * m + cA);
+      prefetch_l1(diag + tc * m + cA);
     }
   }
   // red u of row t
@@ -430,15 +435,15 @@ __global__ void __launch_bounds__(32 * WARPS) mg_down2_march_kernel(const float2
   float2* rcp = rc + (int64_t)p * mc * mc;
   const float2 sig = sigma[p];
   const float2 z = make_float2(0.f, 0.f);
-  MarchState S{z, z, z, z, z, z, z, z, z, z, z};
-  // rows k0 - 2 (even) and k0 - 1 in flight before the first step
-  if (k0 - 2 >= 0) {
-    S.nA0 = inA ? rp[(k0 - 2) * m + cA] : z;
-    S.nB0 = inB ? rp[(k0 - 2) * m + cA + 1] : z;
-  }
-  if (k0 - 1 >= 0) {
-    S.nA1 = inA ? rp[(k0 - 1) * m + cA] : z;
-    S.nB1 = inB ? rp[(k0 - 1) * m + cA + 1] : z;
+  MarchState S;
+  S.R0 = S.R1 = S.B0 = S.B1 = S.rbp = S.Ep = S.ro = z;
+  // rows k0 - 2 (even) ... k0 - 3 + kMarchAhead in flight before the first step
+#pragma unroll
+  for (int i = 0; i < kMarchAhead; ++i) {
+    const int ti = k0 - 2 + i;
+    const bool ok = ti >= 0 && ti < m;
+    S.nA[i] = (ok && inA) ? rp[ti * m + cA] : z;
+    S.nB[i] = (ok && inB) ? rp[ti * m + cA + 1] : z;
   }
   const int tEnd = 2 * J1 + 2;  // even, like the first row k0 - 2
   int t = k0 - 2;

@@ -447,77 +447,108 @@ __device__ __forceinline__ int64_t lin(int i1, int i2, int i3, int m) {
   return DIM == 2 ? (int64_t)i2 * m + i1 : ((int64_t)i3 * m + i2) * m + i1;
 }
 
+// 1 / (sigma + d); FP32 with the hardware-approximate divide (2 ulp)
+__device__ __forceinline__ float2 inv_shift_c(float2 sig, float d) {
+  const float a = sig.x + d;
+  const float q = __fdividef(1.0f, fmaf(a, a, sig.y * sig.y));
+  return make_float2(a * q, -sig.y * q);
+}
+__device__ __forceinline__ double2 inv_shift_c(double2 sig, double d) { return inv_diag<double>(sig, d); }
+
+// one plane per CTA; in FP32, 1024 threads give about one point per thread on the
+// largest coarse level (31^2), so each of the cycle's ~20 dependent phases is short
+// (FP64 is bound by its arithmetic and runs faster with 256)
+template <typename Tc>
+constexpr int coarse_threads() {
+  return sizeof(Tc) == 4 ? 1024 : 256;
+}
+
+// For odd m the parity of the linear index s = i1 + m i2 (+ m^2 i3) is that of
+// i1 + i2 (+ i3), so red points (i1 + i2 + i3 + DIM even) are s = DIM mod 2,
+// DIM mod 2 + 2, ... and each colour is swept without idle threads.  With `stage`
+// the coarse levels' face weights and diagonals are copied into shared memory once.
 template <typename Tc, typename TU, int DIM>
-__global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels<Tc> lv,
+__global__ void __launch_bounds__(1024) mg_coarse_cycle_kernel(const CoarseLevels<Tc> lv,
                                                               const typename Cx<Tc>::t* __restrict__ r0,
                                                               TU* __restrict__ u0,
-                                                              const typename Cx<Tc>::t* __restrict__ sigma) {
+                                                              const typename Cx<Tc>::t* __restrict__ sigma,
+                                                              int stage) {
   typedef typename Cx<Tc>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const C sig = sigma[p];
-  // carve: per level r, u (as TU), res
   C* rl[kMaxCoarseLevels];
   TU* ul[kMaxCoarseLevels];
   C* resl[kMaxCoarseLevels];
+  const Tc* wl[kMaxCoarseLevels];
+  const Tc* dl[kMaxCoarseLevels];
   {
     unsigned char* q = smem_raw;
     for (int l = 0; l < lv.count; ++l) {
-      const int64_t np = lv.np[l];
+      const int np = (int)lv.np[l];
       rl[l] = reinterpret_cast<C*>(q);
-      q += np * sizeof(C);
+      q += (size_t)np * sizeof(C);
       resl[l] = reinterpret_cast<C*>(q);
-      q += np * sizeof(C);
+      q += (size_t)np * sizeof(C);
       ul[l] = reinterpret_cast<TU*>(q);
-      q += ((np * sizeof(TU) + 15) / 16) * 16;
+      q += (((size_t)np * sizeof(TU) + 15) / 16) * 16;
+    }
+    for (int l = 0; l < lv.count; ++l) {
+      const int np = (int)lv.np[l];
+      if (stage) {
+        Tc* w = reinterpret_cast<Tc*>(q);
+        q += (((size_t)(2 * DIM + 1) * np * sizeof(Tc) + 15) / 16) * 16;
+        for (int e = tid; e < 2 * DIM * np; e += nt) w[e] = lv.w[l][e];
+        for (int e = tid; e < np; e += nt) w[2 * DIM * np + e] = lv.diag[l][e];
+        wl[l] = w;
+        dl[l] = w + 2 * DIM * np;
+      } else {
+        wl[l] = lv.w[l];
+        dl[l] = lv.diag[l];
+      }
     }
   }
   // level 0 of the coarse part comes from global memory
-  for (int64_t s = threadIdx.x; s < lv.np[0]; s += blockDim.x) rl[0][s] = r0[(int64_t)p * lv.np[0] + s];
+  const int np0 = (int)lv.np[0];
+  for (int s = tid; s < np0; s += nt) rl[0][s] = r0[(int64_t)p * np0 + s];
   __syncthreads();
-  const Tc wt[3] = {Tc(0.25), Tc(0.5), Tc(0.25)};
+  constexpr int red0 = DIM & 1;
   for (int l = 0; l + 1 < lv.count; ++l) {
     const int m = lv.m[l];
-    const int64_t np = lv.np[l];
-    const Tc* w = lv.w[l];
-    const Tc* dg = lv.diag[l];
+    const int np = (int)lv.np[l];
+    const Tc* w = wl[l];
+    const Tc* dg = dl[l];
     // red points: u = r / d ; black points wait for them
-    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
-      const int i1 = (int)(s % m);
-      const int64_t rr = s / m;
-      const int i2 = (int)(DIM == 2 ? rr : rr % m);
-      const int i3 = (int)(DIM == 3 ? rr / m : 0);
-      if (((i1 + i2 + i3 + DIM) & 1) == 0) stc(ul[l], s, cmul(rl[l][s], inv_diag<Tc>(sig, dg[s])));
-    }
+    for (int s = red0 + 2 * tid; s < np; s += 2 * nt) stc(ul[l], s, cmul(rl[l][s], inv_shift_c(sig, dg[s])));
     __syncthreads();
-    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
-      const int i1 = (int)(s % m);
-      const int64_t rr = s / m;
-      const int i2 = (int)(DIM == 2 ? rr : rr % m);
-      const int i3 = (int)(DIM == 3 ? rr / m : 0);
-      if (((i1 + i2 + i3 + DIM) & 1) == 0) continue;
-      const int64_t off[6] = {-1, 1, -(int64_t)m, (int64_t)m, -(int64_t)m * m, (int64_t)m * m};
+    for (int s = 1 - red0 + 2 * tid; s < np; s += 2 * nt) {
+      const int i1 = s % m;
+      const int rr = s / m;
+      const int i2 = DIM == 2 ? rr : rr % m;
+      const int i3 = DIM == 3 ? rr / m : 0;
+      const int off[6] = {-1, 1, -m, m, -m * m, m * m};
       const bool ex[6] = {i1 > 0, i1 < m - 1, i2 > 0, i2 < m - 1, i3 > 0, i3 < m - 1};
       C acc = rl[l][s];
 #pragma unroll
       for (int k = 0; k < 2 * DIM; ++k) {
         if (ex[k]) {
           const C ured = ldc(ul[l], s + off[k]);
-          const Tc wk = w[(int64_t)k * np + s];
+          const Tc wk = w[k * np + s];
           acc.x = fma(wk, ured.x, acc.x);
           acc.y = fma(wk, ured.y, acc.y);
         }
       }
-      stc(ul[l], s, cmul(acc, inv_diag<Tc>(sig, dg[s])));
+      stc(ul[l], s, cmul(acc, inv_shift_c(sig, dg[s])));
     }
     __syncthreads();
     // residual res = r - (sigma u + tau K u)
-    for (int64_t s = threadIdx.x; s < np; s += blockDim.x) {
-      const int i1 = (int)(s % m);
-      const int64_t rr = s / m;
-      const int i2 = (int)(DIM == 2 ? rr : rr % m);
-      const int i3 = (int)(DIM == 3 ? rr / m : 0);
-      const int64_t off[6] = {-1, 1, -(int64_t)m, (int64_t)m, -(int64_t)m * m, (int64_t)m * m};
+    for (int s = tid; s < np; s += nt) {
+      const int i1 = s % m;
+      const int rr = s / m;
+      const int i2 = DIM == 2 ? rr : rr % m;
+      const int i3 = DIM == 3 ? rr / m : 0;
+      const int off[6] = {-1, 1, -m, m, -m * m, m * m};
       const bool ex[6] = {i1 > 0, i1 < m - 1, i2 > 0, i2 < m - 1, i3 > 0, i3 < m - 1};
       const C uc = ldc(ul[l], s);
       C lu = cmul(cmk<Tc>(sig.x + dg[s], sig.y), uc);
@@ -525,7 +556,7 @@ __global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels
       for (int k = 0; k < 2 * DIM; ++k) {
         if (ex[k]) {
           const C un = ldc(ul[l], s + off[k]);
-          const Tc wk = w[(int64_t)k * np + s];
+          const Tc wk = w[k * np + s];
           lu.x = fma(-wk, un.x, lu.x);
           lu.y = fma(-wk, un.y, lu.y);
         }
@@ -535,19 +566,23 @@ __global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels
     __syncthreads();
     // full weighting onto level l + 1
     const int mc = lv.m[l + 1];
-    for (int64_t sc = threadIdx.x; sc < lv.np[l + 1]; sc += blockDim.x) {
-      const int c1 = (int)(sc % mc);
-      const int64_t rr = sc / mc;
-      const int c2 = (int)(DIM == 2 ? rr : rr % mc);
-      const int c3 = (int)(DIM == 3 ? rr / mc : 0);
+    const int npc = (int)lv.np[l + 1];
+    const Tc wt[3] = {Tc(0.25), Tc(0.5), Tc(0.25)};
+    for (int sc = tid; sc < npc; sc += nt) {
+      const int c1 = sc % mc;
+      const int rr = sc / mc;
+      const int c2 = DIM == 2 ? rr : rr % mc;
+      const int c3 = DIM == 3 ? rr / mc : 0;
       const int f1 = 2 * c1 + 1, f2 = 2 * c2 + 1, f3 = 2 * c3 + 1;
       C acc = czero<Tc>();
       for (int o3 = (DIM == 3 ? -1 : 0); o3 <= (DIM == 3 ? 1 : 0); ++o3)
+#pragma unroll
         for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
           for (int o1 = -1; o1 <= 1; ++o1) {
             Tc wgt = wt[o1 + 1] * wt[o2 + 1];
             if (DIM == 3) wgt *= wt[o3 + 1];
-            const C v = resl[l][lin<DIM>(f1 + o1, f2 + o2, f3 + o3, m)];
+            const C v = resl[l][(int)lin<DIM>(f1 + o1, f2 + o2, f3 + o3, m)];
             acc.x = fma(wgt, v.x, acc.x);
             acc.y = fma(wgt, v.y, acc.y);
           }
@@ -558,14 +593,15 @@ __global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels
   // one-point level
   {
     const int l = lv.count - 1;
-    if (threadIdx.x == 0) stc(ul[l], 0, cmul(rl[l][0], inv_diag<Tc>(sig, lv.diag[l][0])));
+    if (tid == 0) stc(ul[l], 0, cmul(rl[l][0], inv_shift_c(sig, dl[l][0])));
     __syncthreads();
   }
   // prolongation and correction back up
   for (int l = lv.count - 2; l >= 0; --l) {
     const int mf = lv.m[l], mc = lv.m[l + 1];
-    for (int64_t s = threadIdx.x; s < lv.np[l]; s += blockDim.x) {
-      const int fi[3] = {(int)(s % mf), (int)(DIM == 2 ? s / mf : (s / mf) % mf), (int)(DIM == 3 ? s / mf / mf : 0)};
+    const int npf = (int)lv.np[l];
+    for (int s = tid; s < npf; s += nt) {
+      const int fi[3] = {s % mf, DIM == 2 ? s / mf : (s / mf) % mf, DIM == 3 ? s / mf / mf : 0};
       int ci[3][2];
       Tc cw[3][2];
       int cnt[3] = {1, 1, 1};
@@ -597,7 +633,7 @@ __global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels
         for (int a2 = 0; a2 < cnt[1]; ++a2)
           for (int a1 = 0; a1 < cnt[0]; ++a1) {
             const Tc wgt = cw[0][a1] * cw[1][a2] * cw[2][a3];
-            const C v = ldc(ul[l + 1], lin<DIM>(ci[0][a1], ci[1][a2], ci[2][a3], mc));
+            const C v = ldc(ul[l + 1], (int)lin<DIM>(ci[0][a1], ci[1][a2], ci[2][a3], mc));
             acc.x = fma(wgt, v.x, acc.x);
             acc.y = fma(wgt, v.y, acc.y);
           }
@@ -605,7 +641,7 @@ __global__ void __launch_bounds__(256) mg_coarse_cycle_kernel(const CoarseLevels
     }
     __syncthreads();
   }
-  for (int64_t s = threadIdx.x; s < lv.np[0]; s += blockDim.x) stc(u0, (int64_t)p * lv.np[0] + s, ldc(ul[0], s));
+  for (int s = tid; s < np0; s += nt) stc(u0, (int64_t)p * np0 + s, ldc(ul[0], s));
 }
 
 }  // namespace
@@ -618,10 +654,22 @@ size_t mg_coarse_cycle_smem(const CoarseLevels<Tc>& lv) {
   return b;
 }
 
+// shared memory of the staged face weights and diagonals of all coarse levels
+template <typename Tc>
+static size_t coarse_coef_smem(const CoarseLevels<Tc>& lv, int dim) {
+  size_t b = 0;
+  for (int l = 0; l < lv.count; ++l) b += (((size_t)(2 * dim + 1) * lv.np[l] * sizeof(Tc) + 15) / 16) * 16;
+  return b;
+}
+
 template <typename Tc, typename TU>
 cudaError_t launch_mg_coarse_cycle(Launch& L, int dim, int planes, const CoarseLevels<Tc>& lv,
                                    const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r0, TU* u0) {
-  const size_t smem = mg_coarse_cycle_smem<Tc, TU>(lv);
+  // stage the coefficients too when everything fits beside the levels
+  const size_t base = mg_coarse_cycle_smem<Tc, TU>(lv);
+  const size_t coef = coarse_coef_smem<Tc>(lv, dim);
+  const int stage = base + coef <= 200 * 1024 ? 1 : 0;
+  const size_t smem = base + (stage ? coef : 0);
   cudaError_t e;
   if (dim == 2)
     e = cudaFuncSetAttribute(mg_coarse_cycle_kernel<Tc, TU, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -633,9 +681,9 @@ cudaError_t launch_mg_coarse_cycle(Launch& L, int dim, int planes, const CoarseL
   const double cs = sizeof(typename Cx<Tc>::t);
   L.begin(KC_MG_COARSE);
   if (dim == 2)
-    mg_coarse_cycle_kernel<Tc, TU, 2><<<planes, 256, smem, L.stream>>>(lv, r0, u0, sigma);
+    mg_coarse_cycle_kernel<Tc, TU, 2><<<planes, coarse_threads<Tc>(), smem, L.stream>>>(lv, r0, u0, sigma, stage);
   else
-    mg_coarse_cycle_kernel<Tc, TU, 3><<<planes, 256, smem, L.stream>>>(lv, r0, u0, sigma);
+    mg_coarse_cycle_kernel<Tc, TU, 3><<<planes, coarse_threads<Tc>(), smem, L.stream>>>(lv, r0, u0, sigma, stage);
   return L.end(KC_MG_COARSE, (double)planes * lv.np[0] * (cs + sizeof(TU)), (double)planes * pts * 60.0);
 }
 

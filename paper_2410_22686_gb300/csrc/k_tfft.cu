@@ -308,11 +308,16 @@ __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, 
   if (valid) {
     // Hermitian split of the two-for-one spectrum, k = 0..n/2
     const Tc hf = Tc(0.5);
-    for (int k = r; k <= n / 2; k += N1) {
-      const C Z = sm[k * COLS + c];
-      const C W = sm[((n - k) & (n - 1)) * COLS + c];
-      spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
-      spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+    constexpr int NI = (n / 2) / N1 + 1;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int k = r + N1 * i;
+      if (k <= n / 2) {
+        const C Z = sm[k * COLS + c];
+        const C W = sm[((n - k) & (n - 1)) * COLS + c];
+        spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
+        spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+      }
     }
   }
 }
@@ -328,12 +333,18 @@ __device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, 
   typedef typename Cx<Tc>::t C;
   constexpr int n = N1 * N2;
   constexpr int COLS = 256 / N1;
-  // Y[k] = hat w1[k] + i hat w2[k] for all k from the half spectrum
-  for (int k = r; k <= n / 2; k += N1) {
-    C sa, sb;
-    ld(k, sa, sb);
-    sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
-    if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+  // Y[k] = hat w1[k] + i hat w2[k] for all k from the half spectrum (a fixed trip
+  // count, so all of a thread's loads are in flight together)
+  constexpr int NI = (n / 2) / N1 + 1;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = r + N1 * i;
+    if (k <= n / 2) {
+      C sa, sb;
+      ld(k, sa, sb);
+      sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
+      if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+    }
   }
   __syncthreads();
   // (A) row k1 = r: N2-point inverse DFT over k2 of Y[k1 + N1 k2], twiddle w^{-k1 j2}
