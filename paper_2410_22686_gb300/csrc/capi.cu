@@ -815,8 +815,9 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
         cudaSuccess)
       return e;
   }
-  // the finest level's correction is added by the inverse time transform (fine_correction)
-  for (int l = l0 - 1; l >= 1; --l) {
+  // in 2D the finest level's correction is added by the inverse time transform
+  // (fine_correction); in 3D (eight coarse parents per point) by the prolongation kernel
+  for (int l = l0 - 1; l >= (h->dim == 2 ? 1 : 0); --l) {
     if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
         cudaSuccess)
       return e;
@@ -828,7 +829,7 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
 template <typename TU>
 static FineCorrection<TU> fine_correction(const pc_handle* h) {
   FineCorrection<TU> fc;
-  if (h->spatial == PC_SPATIAL_FST || h->coarse_l0 < 1) return fc;
+  if (h->spatial == PC_SPATIAL_FST || h->coarse_l0 < 1 || h->dim != 2) return fc;
   const Grid g0 = grid_of(h, 0), g1 = grid_of(h, 1);
   fc.ec = (const TU*)h->lv[1].u;
   fc.dim = h->dim;

@@ -24,6 +24,15 @@ __device__ __forceinline__ typename Cx<Tc>::t inv_diag(typename Cx<Tc>::t sig, T
   return cinv(cmk<Tc>(sig.x + dg, sig.y));
 }
 
+// 1 / (sigma + d); FP32 with the hardware-approximate divide (2 ulp, far inside what
+// a smoother needs), FP64 exact
+__device__ __forceinline__ float2 inv_shift_c(float2 sig, float d) {
+  const float a = sig.x + d;
+  const float q = __fdividef(1.0f, fmaf(a, a, sig.y * sig.y));
+  return make_float2(a * q, -sig.y * q);
+}
+__device__ __forceinline__ double2 inv_shift_c(double2 sig, double d) { return inv_diag<double>(sig, d); }
+
 struct Coord {
   int i1, i2, i3;
 };
@@ -76,10 +85,12 @@ __global__ void fst_divide_kernel(typename Cx<Tc>::t* __restrict__ buf, const Tc
 }
 
 // ------------------------------------------------------------------- multigrid
-// One red-black Gauss-Seidel sweep from u = 0, fused: a red point takes
-// r/d; a black point takes (r + sum_k w_k u_red(nb_k))/d, where the red
-// neighbour values are recomputed from r on the fly.
-template <typename Tc, typename TU, int DIM>
+// One red-black Gauss-Seidel sweep from u = 0: a red point takes r/d; a black point
+// takes (r + sum_k w_k u_red(nb_k))/d.  MODE 0 does both colours in one pass and
+// recomputes the red neighbour values from r (one reciprocal per neighbour, cheap in
+// FP32); MODE 1 writes the red points only and MODE 2 the black ones from the stored
+// red values (two passes, one reciprocal per point: FP64, whose reciprocal is costly).
+template <typename Tc, typename TU, int DIM, int MODE>
 __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t* __restrict__ r,
                                                         TU* __restrict__ u,
                                                         const Tc* __restrict__ w, const Tc* __restrict__ diag,
@@ -94,12 +105,14 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
   const bool red = ((c.i1 + c.i2 + c.i3 + DIM) & 1) == 0;
   const Tc dg = diag[s];
   if (red) {
+    if (MODE == 2) return;
     for (int p = p0; p < p1; ++p) {
       const int64_t o = (int64_t)p * np + s;
-      stc(u, o, cmul(r[o], inv_diag<Tc>(sigma[p], dg)));
+      stc(u, o, cmul(r[o], inv_shift_c(sigma[p], dg)));
     }
     return;
   }
+  if (MODE == 1) return;
   int64_t off[2 * DIM];
   bool ex[2 * DIM];
   Tc wv[2 * DIM], dn[2 * DIM];
@@ -130,12 +143,12 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
 #pragma unroll
     for (int k = 0; k < 2 * DIM; ++k) {
       if (ex[k]) {
-        const C ured = cmul(r[o + off[k]], inv_diag<Tc>(sig, dn[k]));
+        const C ured = MODE == 2 ? ldc(u, o + off[k]) : cmul(r[o + off[k]], inv_shift_c(sig, dn[k]));
         acc.x = fma(wv[k], ured.x, acc.x);
         acc.y = fma(wv[k], ured.y, acc.y);
       }
     }
-    stc(u, o, cmul(acc, inv_diag<Tc>(sig, dg)));
+    stc(u, o, cmul(acc, inv_shift_c(sig, dg)));
   }
 }
 
@@ -345,13 +358,21 @@ cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil
   const int pch = plane_chunk(L);
   const double cs = 0.5 * (sizeof(typename Cx<Tc>::t) + sizeof(TU));
   const double tot = (double)g.np * planes;
+  const dim3 grid = plane_grid(g.np, planes, pch);
   L.begin(KC_MG_SMOOTH);
-  if (g.dim == 2)
-    mg_smooth_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
-                                                                            planes, pch);
-  else
-    mg_smooth_kernel<Tc, TU, 3><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np,
-                                                                            planes, pch);
+  if (sizeof(Tc) == 8) {  // two passes: one reciprocal per point
+    if (g.dim == 2) {
+      mg_smooth_kernel<Tc, TU, 2, 1><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+      mg_smooth_kernel<Tc, TU, 2, 2><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+    } else {
+      mg_smooth_kernel<Tc, TU, 3, 1><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+      mg_smooth_kernel<Tc, TU, 3, 2><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+    }
+  } else if (g.dim == 2) {
+    mg_smooth_kernel<Tc, TU, 2, 0><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+  } else {
+    mg_smooth_kernel<Tc, TU, 3, 0><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+  }
   return L.end(KC_MG_SMOOTH, 2.0 * tot * cs, tot * (12.0 + 10.0 * g.dim));
 }
 
@@ -446,14 +467,6 @@ template <int DIM>
 __device__ __forceinline__ int64_t lin(int i1, int i2, int i3, int m) {
   return DIM == 2 ? (int64_t)i2 * m + i1 : ((int64_t)i3 * m + i2) * m + i1;
 }
-
-// 1 / (sigma + d); FP32 with the hardware-approximate divide (2 ulp)
-__device__ __forceinline__ float2 inv_shift_c(float2 sig, float d) {
-  const float a = sig.x + d;
-  const float q = __fdividef(1.0f, fmaf(a, a, sig.y * sig.y));
-  return make_float2(a * q, -sig.y * q);
-}
-__device__ __forceinline__ double2 inv_shift_c(double2 sig, double d) { return inv_diag<double>(sig, d); }
 
 // one plane per CTA; in FP32, 1024 threads give about one point per thread on the
 // largest coarse level (31^2), so each of the cycle's ~20 dependent phases is short
