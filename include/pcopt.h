@@ -220,6 +220,22 @@ int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad
 int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const double* a_int, const double* x,
                           const double* lam, double* grad, void* stream);
 
+/* End-point values of the time discretisation (Section 1), which the
+ * all-at-once unknowns leave out: from a solution x of A x = b (device,
+ * 2*n*ms; y = x1 / sqrt(gamma), p = x2),
+ *   (I + tau K) y^(N) = y^(n) + tau f_T + (tau / gamma) p_N,
+ *   (I + tau K) p^(0) = p^(1) + tau g_0 - tau y0,
+ * each solved to relative residual rtol by flexible conjugate gradients
+ * preconditioned with the handle's spatial solver at shift 1 (exact for the
+ * sine-transform handle, one V(1,0) cycle otherwise).  f_T, g_0, y0, p_N:
+ * device, ms doubles each, or NULL for zero.  yN, p0: device outputs, ms
+ * doubles.  *iters (may be NULL) = the larger of the two CG iteration counts.
+ * Synchronises `stream`; uses the handle's Krylov workspace.  Errors:
+ * PC_ERR_ARG, PC_ERR_NOT_CONVERGED (after maxit, 1..10000), PC_ERR_BREAKDOWN. */
+int pc_end_point_solves(pc_handle* h, const double* x, const double* f_T, const double* g_0, const double* y0,
+                        const double* p_N, double* yN, double* p0, double rtol, int maxit, int* iters,
+                        void* stream);
+
 /* Problem sizes of a handle: ms = m1^dim and the all-at-once length 2*n*ms. */
 int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
 

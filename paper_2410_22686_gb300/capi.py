@@ -72,6 +72,7 @@ _SIGNATURES = {
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
     "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "pc_end_point_solves": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _i, _ip, _vp]),
     "pc_get_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
     "pc_set_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
     "pc_autotune": (_i, [_vp, _i, ctypes.POINTER(pc_tiles), _vp]),

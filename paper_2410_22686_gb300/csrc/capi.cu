@@ -176,6 +176,8 @@ struct pc_handle {
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   double2* sig64 = nullptr;
+  double2* sig1_64 = nullptr;  // the shift 1 (end-point solves)
+  float2* sig1_32 = nullptr;
   float2* sig32 = nullptr;
   // FST tables
   double* S64 = nullptr;
@@ -566,6 +568,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = upload_c(h, (void**)&h->tw32, twr, twi, true, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->sig64, sr, si, false, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->sig32, sr, si, true, st))) goto fail_out;
+    const std::vector<double> one{1.0}, zero{0.0};
+    if ((rc = upload_c(h, (void**)&h->sig1_64, one, zero, false, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->sig1_32, one, zero, true, st))) goto fail_out;
   }
   // ---- FST tables (constant a)
   if (spatial == PC_SPATIAL_FST) {
@@ -746,6 +751,7 @@ struct Tables<double> {
   static const double* dinv(const pc_handle* h) { return h->dinv64; }
   static const double2* tw(const pc_handle* h) { return h->tw64; }
   static const double2* sig(const pc_handle* h) { return h->sig64; }
+  static const double2* sig1(const pc_handle* h) { return h->sig1_64; }
   static const double* S(const pc_handle* h) { return h->S64; }
   static const double* lamK(const pc_handle* h) { return h->lamK64; }
 };
@@ -755,6 +761,7 @@ struct Tables<float> {
   static const float* dinv(const pc_handle* h) { return h->dinv32; }
   static const float2* tw(const pc_handle* h) { return h->tw32; }
   static const float2* sig(const pc_handle* h) { return h->sig32; }
+  static const float2* sig1(const pc_handle* h) { return h->sig1_32; }
   static const float* S(const pc_handle* h) { return h->S32; }
   static const float* lamK(const pc_handle* h) { return h->lamK32; }
 };
@@ -768,10 +775,13 @@ const CoarseLevels<double>& coarse_of<double>(const pc_handle* h) { return h->co
 
 // step 2: every plane of lv[0].r solved into lv[0].u (iterates stored as TU)
 template <typename Tc, typename TU>
-static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
+static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
+                                 const typename Cx<Tc>::t* sig_override = nullptr, bool complete = false) {
+  // nplanes / sig_override: solve only the first planes with other shifts; complete:
+  // also apply the finest correction that the inverse time FFT otherwise adds
   typedef typename Cx<Tc>::t C;
-  const int P = h->planes;
-  const C* sig = Tables<Tc>::sig(h);
+  const int P = nplanes > 0 ? nplanes : h->planes;
+  const C* sig = sig_override ? sig_override : Tables<Tc>::sig(h);
   cudaError_t e;
   if constexpr (std::is_same<TU, C>::value) {
     if (h->spatial == PC_SPATIAL_FST) {
@@ -817,7 +827,7 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L) {
   }
   // in 2D the finest level's correction is added by the inverse time transform
   // (fine_correction); in 3D (eight coarse parents per point) by the prolongation kernel
-  for (int l = l0 - 1; l >= (h->dim == 2 ? 1 : 0); --l) {
+  for (int l = l0 - 1; l >= (h->dim == 2 && !complete ? 1 : 0); --l) {
     if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
         cudaSuccess)
       return e;
@@ -1621,5 +1631,100 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
   h->tiles = best;
   drop_graphs(h);
   if (chosen) pc_get_tiles(h, chosen);
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// end-point solves (Section 1): y^(N) and p^(0) from a solution of A x = b
+// ---------------------------------------------------------------------------
+// z = (I + tau K)^{-1} r approximately: the handle's spatial solver at shift 1 on one plane
+template <typename Tc, typename TU>
+static cudaError_t shift1_solve(pc_handle* h, Launch& L, const double* r, double* z) {
+  typedef typename Cx<Tc>::t C;
+  cudaError_t e = launch_real_to_plane<Tc>(L, r, (C*)h->lv[0].r, h->ms);
+  if (e != cudaSuccess) return e;
+  if ((e = spatial_solve<Tc, TU>(h, L, 1, Tables<Tc>::sig1(h), true)) != cudaSuccess) return e;
+  return launch_plane_to_real<TU>(L, (const TU*)h->lv[0].u, z, h->ms);
+}
+
+static cudaError_t shift1_any(pc_handle* h, Launch& L, const double* r, double* z) {
+  if (!h->fp32) return shift1_solve<double, double2>(h, L, r, z);
+  return h->bf16s ? shift1_solve<float, __nv_bfloat162>(h, L, r, z) : shift1_solve<float, float2>(h, L, r, z);
+}
+
+// flexible preconditioned conjugate gradients on (I + tau K) u = b (u, b: ms doubles)
+static int pcg_E(pc_handle* h, Launch& L, const double* b, double* u, double rtol, int maxit, int* iters) {
+  const int64_t ms = h->ms;
+  const Grid g = grid_of(h, 0);
+  const Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
+  cudaStream_t s = L.stream;
+  double* r = h->V;
+  double* z = h->V + ms;
+  double* p = h->V + 2 * ms;
+  double* q = h->V + 3 * ms;
+  double* rold = h->tbuf;
+  double* sc = h->scal + 10;  // [0] b.b, [1] r.z, [2] p.q, [3] r.r, [4] rold.z
+  auto dot = [&](const double* a, const double* c, double* out) {
+    return launch_multidot(L, a, (size_t)ms, 1, c, (size_t)ms, h->partial, out, nullptr, nullptr);
+  };
+  auto fetch = [&](int cnt) -> int {
+    PC_CUDA(cudaMemcpyAsync(h->host, sc, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PC_CUDA(cudaStreamSynchronize(s));
+    return PC_OK;
+  };
+  PC_CUDA(cudaMemsetAsync(u, 0, ms * sizeof(double), s));
+  PC_CUDA(cudaMemcpyAsync(r, b, ms * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PC_CUDA(launch_norm2(L, b, ms, h->partial, sc));
+  PC_CUDA(shift1_any(h, L, r, z));
+  PC_CUDA(dot(r, z, sc + 1));
+  PC_CUDA(launch_axpby<double>(L, 1.0, z, 0.0, p, ms));
+  if (int rc = fetch(2)) return rc;
+  const double bnorm = std::sqrt(h->host[0]);
+  double rz = h->host[1];
+  if (iters) *iters = 0;
+  if (bnorm == 0.0) return PC_OK;
+  if (!std::isfinite(bnorm) || !std::isfinite(rz)) return fail(PC_ERR_BREAKDOWN, "end-point solve: non-finite input");
+  for (int it = 1; it <= maxit; ++it) {
+    PC_CUDA(launch_apply_E(L, g, st, p, q));
+    PC_CUDA(dot(p, q, sc + 2));
+    if (int rc = fetch(3)) return rc;
+    const double pq = h->host[2];
+    if (!(pq > 0) || !std::isfinite(pq)) return fail(PC_ERR_BREAKDOWN, "end-point solve: p.Ap not positive");
+    const double alpha = rz / pq;
+    PC_CUDA(launch_axpby<double>(L, alpha, p, 1.0, u, ms));
+    PC_CUDA(launch_axpby<double>(L, 1.0, r, 0.0, rold, ms));
+    PC_CUDA(launch_axpby<double>(L, -alpha, q, 1.0, r, ms));
+    PC_CUDA(launch_norm2(L, r, ms, h->partial, sc + 3));
+    if (int rc = fetch(4)) return rc;
+    if (iters) *iters = it;
+    const double rel = std::sqrt(h->host[3]) / bnorm;
+    if (!std::isfinite(rel)) return fail(PC_ERR_BREAKDOWN, "end-point solve: non-finite residual");
+    if (rel <= rtol) return PC_OK;
+    PC_CUDA(shift1_any(h, L, r, z));
+    PC_CUDA(dot(r, z, sc + 1));
+    PC_CUDA(dot(rold, z, sc + 4));
+    if (int rc = fetch(5)) return rc;
+    const double rz_new = h->host[1];
+    const double beta = (rz_new - h->host[4]) / rz;  // Polak-Ribiere: tolerates a varying preconditioner
+    PC_CUDA(launch_axpby<double>(L, 1.0, z, beta, p, ms));
+    rz = rz_new;
+  }
+  return fail(PC_ERR_NOT_CONVERGED, "end-point solve: not converged");
+}
+
+extern "C" int pc_end_point_solves(pc_handle* h, const double* x, const double* f_T, const double* g_0,
+                                   const double* y0, const double* p_N, double* yN, double* p0, double rtol,
+                                   int maxit, int* iters, void* stream) {
+  if (!h || !x || !yN || !p0) return fail(PC_ERR_ARG, "pc_end_point_solves: null argument");
+  if (!(rtol > 0)) return fail(PC_ERR_ARG, "pc_end_point_solves: rtol must be > 0");
+  if (maxit < 1 || maxit > 10000) return fail(PC_ERR_ARG, "pc_end_point_solves: maxit must be in [1, 10000]");
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  double* rhs_y = h->wbuf;
+  double* rhs_p = h->wbuf + h->ms;
+  GR_CUDA(launch_endpoint_rhs(L, x, h->ms, h->n, h->tau, h->prm.gamma, f_T, g_0, y0, p_N, rhs_y, rhs_p));
+  int it_y = 0, it_p = 0;
+  if (int rc = pcg_E(h, L, rhs_y, yN, rtol, maxit, &it_y)) return rc;
+  if (int rc = pcg_E(h, L, rhs_p, p0, rtol, maxit, &it_p)) return rc;
+  if (iters) *iters = it_y > it_p ? it_y : it_p;
   return PC_OK;
 }

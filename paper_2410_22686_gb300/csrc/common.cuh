@@ -350,6 +350,16 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
 // RHS assembly and gradient
 cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
                              const double* g, const double* y0, double* b);
+
+// end-point solves of the time discretisation (k_misc.cu)
+cudaError_t launch_endpoint_rhs(Launch& L, const double* x, int64_t ms, int n, double tau, double gamma,
+                                const double* fT, const double* g0, const double* y0, const double* pN, double* rhs_y,
+                                double* rhs_p);
+cudaError_t launch_apply_E(Launch& L, const Grid& g, const Stencil<double>& st, const double* u, double* out);
+template <typename Tc>
+cudaError_t launch_real_to_plane(Launch& L, const double* v, typename Cx<Tc>::t* plane, int64_t ms);
+template <typename TU>
+cudaError_t launch_plane_to_real(Launch& L, const TU* plane, double* v, int64_t ms);
 // grad_P = scale * a_P * sum_j sum_faces [(l1_P-l1_Q)(x2_P-x2_Q) - (l2_P-l2_Q)(x1_P-x1_Q)]
 cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, const double* a_int, const double* x,
                                 const double* lam, double* partial, int tj, double* grad);

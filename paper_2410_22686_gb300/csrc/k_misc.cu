@@ -80,6 +80,74 @@ __global__ void grad_finish_kernel(const double* __restrict__ partial, int nchun
   grad[s] = scale * a_int[s] * t;
 }
 
+// End-point right-hand sides (Section 1): with y = x1 / sqrt(gamma), p = x2,
+//   rhs_y = y^(n) + tau f_T + (tau / gamma) p_N,   rhs_p = p^(1) + tau g_0 - tau y0
+// (time blocks 1..n of the all-at-once vector; f_T, g_0, y0, p_N may be null = 0).
+__global__ void endpoint_rhs_kernel(const double* __restrict__ x, int64_t ms, int n, double tau, double gamma,
+                                    const double* __restrict__ fT, const double* __restrict__ g0,
+                                    const double* __restrict__ y0, const double* __restrict__ pN,
+                                    double* __restrict__ rhs_y, double* __restrict__ rhs_p) {
+  const double isg = 1.0 / sqrt(gamma);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride) {
+    double ry = x[(int64_t)(n - 1) * ms + s] * isg;
+    if (fT) ry = fma(tau, fT[s], ry);
+    if (pN) ry = fma(tau / gamma, pN[s], ry);
+    double rp = x[(int64_t)n * ms + s];
+    if (g0) rp = fma(tau, g0[s], rp);
+    if (y0) rp = fma(-tau, y0[s], rp);
+    rhs_y[s] = ry;
+    rhs_p[s] = rp;
+  }
+}
+
+// out = (I + tau K) u on the spatial grid: u + d u - sum_k w_k u_nb (w = tau a_f / h^2)
+template <int DIM>
+__global__ void apply_E_kernel(const double* __restrict__ u, double* __restrict__ out, const double* __restrict__ w,
+                               const double* __restrict__ d, int m, int64_t ms) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride) {
+    const int i1 = (int)(s % m);
+    const int64_t r = s / m;
+    const int i2 = (int)(DIM == 2 ? r : r % m);
+    const int i3 = (int)(DIM == 3 ? r / m : 0);
+    const double uc = u[s];
+    double acc = fma(d[s], uc, uc);
+    if (i1 > 0) acc = fma(-w[s], u[s - 1], acc);
+    if (i1 < m - 1) acc = fma(-w[ms + s], u[s + 1], acc);
+    if (i2 > 0) acc = fma(-w[2 * ms + s], u[s - m], acc);
+    if (i2 < m - 1) acc = fma(-w[3 * ms + s], u[s + m], acc);
+    if (DIM == 3) {
+      if (i3 > 0) acc = fma(-w[4 * ms + s], u[s - mm], acc);
+      if (i3 < m - 1) acc = fma(-w[5 * ms + s], u[s + mm], acc);
+    }
+    out[s] = acc;
+  }
+}
+
+// real vector <-> spectral plane (imaginary part zero / dropped)
+template <typename Tc>
+__global__ void real_to_plane_kernel(const double* __restrict__ v, typename Cx<Tc>::t* __restrict__ plane,
+                                     int64_t ms) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride)
+    plane[s] = cmk<Tc>(cvt<Tc>(v[s]), Tc(0));
+}
+template <typename TU>
+__global__ void plane_to_real_kernel(const TU* __restrict__ plane, double* __restrict__ v, int64_t ms) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride) {
+    const auto z = ldc(plane, s);
+    v[s] = cvt<double>(z.x);
+  }
+}
+
+static unsigned grid_for(int64_t len) {
+  int64_t b = (len + 255) / 256;
+  return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
 }  // namespace
 
 cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
@@ -109,5 +177,42 @@ cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, c
   grad_finish_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, L.stream>>>(partial, nchunks, g.np, scale, a_int, grad);
   return L.end(KC_GRAD, 8.0 * (nchunks + 2) * g.np, 1.0 * nchunks * g.np);
 }
+
+cudaError_t launch_endpoint_rhs(Launch& L, const double* x, int64_t ms, int n, double tau, double gamma,
+                                const double* fT, const double* g0, const double* y0, const double* pN, double* rhs_y,
+                                double* rhs_p) {
+  L.begin(KC_RHS);
+  endpoint_rhs_kernel<<<grid_for(ms), 256, 0, L.stream>>>(x, ms, n, tau, gamma, fT, g0, y0, pN, rhs_y, rhs_p);
+  return L.end(KC_RHS, 8.0 * ms * 6, 8.0 * ms);
+}
+
+cudaError_t launch_apply_E(Launch& L, const Grid& g, const Stencil<double>& st, const double* u, double* out) {
+  L.begin(KC_MATVEC);
+  if (g.dim == 2)
+    apply_E_kernel<2><<<grid_for(g.np), 256, 0, L.stream>>>(u, out, st.w, st.diag, g.m, g.np);
+  else
+    apply_E_kernel<3><<<grid_for(g.np), 256, 0, L.stream>>>(u, out, st.w, st.diag, g.m, g.np);
+  return L.end(KC_MATVEC, 8.0 * g.np * (2 * g.dim + 3), (4.0 * g.dim + 2) * g.np);
+}
+
+template <typename Tc>
+cudaError_t launch_real_to_plane(Launch& L, const double* v, typename Cx<Tc>::t* plane, int64_t ms) {
+  L.begin(KC_AXPBY);
+  real_to_plane_kernel<Tc><<<grid_for(ms), 256, 0, L.stream>>>(v, plane, ms);
+  return L.end(KC_AXPBY, 8.0 * ms + sizeof(typename Cx<Tc>::t) * ms, 0.0);
+}
+
+template <typename TU>
+cudaError_t launch_plane_to_real(Launch& L, const TU* plane, double* v, int64_t ms) {
+  L.begin(KC_AXPBY);
+  plane_to_real_kernel<TU><<<grid_for(ms), 256, 0, L.stream>>>(plane, v, ms);
+  return L.end(KC_AXPBY, 8.0 * ms + sizeof(TU) * ms, 0.0);
+}
+
+template cudaError_t launch_real_to_plane<float>(Launch&, const double*, float2*, int64_t);
+template cudaError_t launch_real_to_plane<double>(Launch&, const double*, double2*, int64_t);
+template cudaError_t launch_plane_to_real<float2>(Launch&, const float2*, double*, int64_t);
+template cudaError_t launch_plane_to_real<double2>(Launch&, const double2*, double*, int64_t);
+template cudaError_t launch_plane_to_real<__nv_bfloat162>(Launch&, const __nv_bfloat162*, double*, int64_t);
 
 }  // namespace pcopt

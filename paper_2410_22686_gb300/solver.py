@@ -191,6 +191,19 @@ class Solver:
         capi.check(self.lib.pc_grad_log_a(self.h, _ptr(x), _ptr(lam), _ptr(g), _stream()))
         return g
 
+    def end_point_solves(self, x, f_T=None, g_0=None, y0=None, p_N=None, rtol=1e-12, maxit=500):
+        """y^(N) and p^(0) of the time discretisation from a solution x (pc_end_point_solves)."""
+        self._vec(x)
+        for v in (f_T, g_0, y0, p_N):
+            if v is not None and v.numel() != self.ms:
+                raise ValueError("f_T, g_0, y0 and p_N hold m1^dim values")
+        yN = torch.empty((self.m1,) * self.dim, dtype=torch.float64, device="cuda")
+        p0 = torch.empty_like(yN)
+        it = ctypes.c_int(0)
+        capi.check(self.lib.pc_end_point_solves(self.h, _ptr(x), _ptr(f_T), _ptr(g_0), _ptr(y0), _ptr(p_N),
+                                                _ptr(yN), _ptr(p0), rtol, maxit, ctypes.byref(it), _stream()))
+        return yN, p0, it.value
+
     # ---------------------------------------------------------------- tile shapes
     def get_tiles(self) -> dict:
         t = capi.pc_tiles()

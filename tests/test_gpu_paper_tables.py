@@ -1,7 +1,8 @@
 """The GPU solver at the paper's own sizes (n = 2^k - 1 time blocks, eps =
 min{1/2, tau/2}, left-preconditioned GMRES from zero, tol 1e-8, Section 3)
 reproduces the iteration counts and discretisation errors printed in Table 3
-(Example 1, sine-transform solves) and Table 7 (Example 2, one V-cycle)."""
+(Example 1, sine-transform solves) and Table 7 (Example 2, one V-cycle); the
+end-point values y^(N), p^(0) come from the GPU too (pc_end_point_solves)."""
 import math
 
 import numpy as np
@@ -35,11 +36,14 @@ def _gpu_example(ex, m1, n, gamma):
     b = sol.build_rhs(torch.from_numpy(P.f).cuda(), torch.from_numpy(P.g).cuda(), torch.from_numpy(P.y0).cuda())
     _, it_paper_mode, _ = sol.solve(b, rtol=1e-8, mode="left")
     x, _, rel = sol.solve(b, rtol=1e-12, mode="right")
+    # end-point values y^(N), p^(0) on the GPU as well
+    yNd, p0d, _ = sol.end_point_solves(x, f_T=torch.from_numpy(P.extra["f_T"]).cuda(),
+                                       g_0=torch.from_numpy(P.extra["g_0"]).cuda(),
+                                       y0=torch.from_numpy(P.y0).cuda(), rtol=1e-13)
     sol.close()
     xg = x.cpu().numpy()
-    a = P.a_nodes if P.a_nodes is not None else osy.unit_coefficient(m1, 2)
     y, p = osy.unscale(xg, gamma)
-    yN, p0 = osy.end_point_solves(y, p, a, P.tau, gamma, P.extra["f_T"], P.extra["g_0"], P.y0)
+    yN, p0 = yNd.cpu().numpy(), p0d.cpu().numpy()
     N = n + 1
     x1, x2 = S.interior_grid(m1, 2)
     tl = P.tau * np.arange(N + 1)
