@@ -205,7 +205,8 @@ struct pc_handle {
   double* scal = nullptr;  // [0] nrm2, [1] est, [2] ref, [3] tmp, [4..9] Arnoldi step scalars
   double* partial = nullptr;
   int nblocks = 0;         // rows of `partial`: SMs x blocks per SM
-  double* host = nullptr;  // pinned: [0] est, [1] ref, [2] nrm2, ... (16 doubles)
+  double* host = nullptr;  // pinned, mapped: [0] est, [1] ref, [2] nrm2, ... (16 doubles) + 4 ints
+  double* host_dev = nullptr;  // device view of `host`
   std::vector<void*> allocs;
   Prof prof;
   // graph-captured solve
@@ -612,9 +613,13 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = dev_alloc_t(h, &h->scal, 16))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 2)))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->idx, 4))) goto fail_out;
-    cudaError_t e = cudaMallocHost((void**)&h->host, 16 * sizeof(double));
+    // scalars come back through mapped pinned memory written by a kernel, so the
+    // solver's per-iteration reads never queue behind bulk copies on a copy engine
+    cudaError_t e = cudaHostAlloc((void**)&h->host, 18 * sizeof(double), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h->host_dev, h->host, 0);
     if (e != cudaSuccess) {
-      rc = fail(PC_ERR_OOM, "cudaMallocHost failed");
+      cudaGetLastError();
+      rc = fail(PC_ERR_OOM, "mapped pinned host allocation failed");
       goto fail_out;
     }
   }
@@ -939,10 +944,30 @@ extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, d
 // ---------------------------------------------------------------------------
 // GMRES (Section 3: zero initial guess, relative tolerance; Lemma 2.1)
 // ---------------------------------------------------------------------------
+// copy n doubles (and optionally one int, stored as a double after them) from device
+// memory into the mapped host buffer
+__global__ void to_mapped_kernel(const double* __restrict__ src, int n, const int* __restrict__ isrc,
+                                 double* __restrict__ dst) {
+  const int t = threadIdx.x;
+  if (t < n) dst[t] = src[t];
+  if (t == 0 && isrc) dst[n] = (double)isrc[0];
+}
+
+// host[off .. off+n) = src[0 .. n) (+ host[off+n] = *isrc), visible to the host after `st`
+// is synchronised
+static int fetch_scalars(pc_handle* h, cudaStream_t st, const double* src, int n, int off,
+                         const int* isrc = nullptr) {
+  Launch L{st, &h->prof, &h->tiles};
+  L.begin(KC_REDUCE);
+  to_mapped_kernel<<<1, 32, 0, st>>>(src, n, isrc, h->host_dev + off);
+  PC_CUDA(L.end(KC_REDUCE, 8.0 * (n + (isrc ? 1 : 0)), 0.0));
+  PC_CUDA(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
 // host[0] = est, host[1] = ref, host[8] = re-orthogonalisation flag of the last step
 static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref, bool* reorth = nullptr) {
-  PC_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  PC_CUDA(cudaStreamSynchronize(st));
+  if (int rc = fetch_scalars(h, st, h->scal + 1, 9, 0)) return rc;
   if (est) *est = h->host[0];
   if (ref) *ref = h->host[1];
   if (reorth) *reorth = h->host[8] != 0.0;
@@ -972,7 +997,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
 
   // is x0 zero?  (one norm + readback)
   GM_CUDA(launch_norm2(L, x, U, h->partial, h->scal + 3));
-  PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (int rc = fetch_scalars(h, st, h->scal + 3, 1, 2)) return rc;
   PC_CUDA(cudaStreamSynchronize(st));
   const bool x0_zero = h->host[2] == 0.0;
 
@@ -1076,7 +1101,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
     GM_CUDA(launch_axpby<double>(L, 1.0, b, -1.0, h->wbuf, U));
     GM_CUDA(launch_norm2(L, h->wbuf, U, h->partial, h->scal + 3));
-    PC_CUDA(cudaMemcpyAsync(h->host + 2, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (int rc = fetch_scalars(h, st, h->scal + 3, 1, 2)) return rc;
     PC_CUDA(cudaStreamSynchronize(st));
     est_h = std::sqrt(h->host[2]) / ref_h;
   } else {
@@ -1238,10 +1263,8 @@ static int capture_solve(pc_handle* h, const double* b, double* x, double rtol, 
 
 // read iterations and the true relative residual of a finished graph solve
 static int graph_results(pc_handle* h, cudaStream_t st, double rtol, int* iters, double* relres) {
-  int kdone = 0;
-  GR_CUDA(cudaMemcpyAsync(&kdone, h->idx + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GR_CUDA(cudaMemcpyAsync(h->host, h->scal + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  GR_CUDA(cudaStreamSynchronize(st));
+  if (int rc = fetch_scalars(h, st, h->scal + 1, 3, 0, h->idx + 1)) return rc;
+  const int kdone = (int)h->host[3];
   const double ref = h->host[1], r2 = h->host[2];
   const double rr = ref > 0 ? std::sqrt(r2) / ref : 0.0;
   if (iters) *iters = kdone;
@@ -1668,9 +1691,7 @@ static int pcg_E(pc_handle* h, Launch& L, const double* b, double* u, double rto
     return launch_multidot(L, a, (size_t)ms, 1, c, (size_t)ms, h->partial, out, nullptr, nullptr);
   };
   auto fetch = [&](int cnt) -> int {
-    PC_CUDA(cudaMemcpyAsync(h->host, sc, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
-    PC_CUDA(cudaStreamSynchronize(s));
-    return PC_OK;
+    return fetch_scalars(h, s, sc, cnt, 0);
   };
   PC_CUDA(cudaMemsetAsync(u, 0, ms * sizeof(double), s));
   PC_CUDA(cudaMemcpyAsync(r, b, ms * sizeof(double), cudaMemcpyDeviceToDevice, s));

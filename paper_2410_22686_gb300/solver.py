@@ -246,6 +246,51 @@ class Solver:
         return int(self.lib.pc_launch_count(self.h))
 
 
+def solve_host_pipelined(jobs, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
+    """Solve several problems from pinned HOST buffers with the host<->device copies
+    overlapped with the solves.
+
+    jobs: sequence of (solver, b_host, x_host), pinned float64 CPU tensors of each
+    solver's vector length.  While problem i is solved on the current stream, the
+    right-hand side of problem i+1 is copied in and the solution of problem i-1 copied
+    out on a second stream (events order each copy after what it depends on).  Every
+    byte still crosses between host and device inside the call; returns
+    [(iterations, relative residual), ...] once all solutions are in their x_host."""
+    jobs = list(jobs)
+    for s, bh, xh in jobs:
+        if bh.is_cuda or xh.is_cuda or bh.dtype != torch.float64 or xh.dtype != torch.float64:
+            raise ValueError("b_host and x_host must be float64 CPU tensors")
+        if bh.numel() != s.vec_len or xh.numel() != s.vec_len:
+            raise ValueError("host buffers must hold the solver's vector length")
+    cur = torch.cuda.current_stream()
+    cp = torch.cuda.Stream()
+    dev_b = [torch.empty(bh.shape, dtype=torch.float64, device="cuda") for _, bh, _ in jobs]
+    cp.wait_stream(cur)  # the buffers exist before the copy stream writes them
+
+    def copy_in(i):
+        with torch.cuda.stream(cp):
+            dev_b[i].copy_(jobs[i][1], non_blocking=True)
+            return cp.record_event()
+
+    out = []
+    ev_in = copy_in(0) if jobs else None
+    for i, (s, _, xh) in enumerate(jobs):
+        ev_next = copy_in(i + 1) if i + 1 < len(jobs) else None
+        cur.wait_event(ev_in)
+        x, it, rr = s.solve(dev_b[i], rtol=rtol, maxit=maxit, mode=mode, raise_on_nonconv=raise_on_nonconv)
+        ev_done = cur.record_event()
+        with torch.cuda.stream(cp):
+            cp.wait_event(ev_done)
+            xh.copy_(x, non_blocking=True)
+            x.record_stream(cp)
+        out.append((it, rr))
+        ev_in = ev_next
+    cp.synchronize()
+    for b in dev_b:
+        b.record_stream(cp)
+    return out
+
+
 class Batch:
     """Independent problems solved by one graph launch (pc_batch_*).  ``solvers``
     are distinct Solver objects; ``bs`` their right-hand sides; ``xs`` receive the

@@ -81,3 +81,27 @@ def test_graph_solve_zero_rhs_and_maxit():
         sol.solve_graph(b, rtol=1e-14, maxit=3)
     assert ei.value.status == capi.PC_ERR_NOT_CONVERGED
     sol.close()
+
+
+def test_pipelined_host_solves_equal_device_solves():
+    # copies overlapped with the solves on a second stream change nothing in the results
+    from paper_2410_22686_gb300 import Solver, solve_host_pipelined
+    sols, hb, hx, ref = [], [], [], []
+    for gamma in (1e-2, 1e-4, 1e-6):
+        prob = S.variable_2d_problem(gamma=gamma, m1=31, n=16)
+        sol = Solver(2, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg",
+                     precision="mixed", max_iter=60)
+        b = sol.build_rhs(torch.from_numpy(prob.f).cuda(), torch.from_numpy(prob.g).cuda(),
+                          torch.from_numpy(prob.y0).cuda())
+        x, it, rr = sol.solve(b, rtol=1e-8)
+        sols.append(sol)
+        hb.append(b.cpu().pin_memory())
+        hx.append(torch.empty(b.shape, dtype=torch.float64).pin_memory())
+        ref.append((x.cpu(), it, rr))
+    for _ in range(2):
+        res = solve_host_pipelined(list(zip(sols, hb, hx)), rtol=1e-8)
+        for (xr, itr, rrr), (it, rr), xh in zip(ref, res, hx):
+            assert it == itr and rr == rrr
+            assert torch.equal(xh, xr)
+    for s in sols:
+        s.close()
