@@ -450,6 +450,11 @@ def run_ours(args):
     extras = _extra_workloads(args, torch, dev)
 
     # ---------------- roofline of the dominant kernel class
+    # DRAM bytes (read + write) over algorithmic bytes of one launch, from the ncu
+    # capture summarised in profiles/kernels_gmres_mixed_255x255_n128.md (255^2 x 128,
+    # four basis vectors); a full-size launch moves the same bytes per unknown, so the
+    # traffic of the average timed launch is this ratio times its algorithmic bytes
+    ncu_traffic_ratio = {"arnoldi_dot": (665.9 + 4.0) / 665.8, "arnoldi_update_norm": (665.9 + 176.8) / 865.6}
     tot_ms = sum(v["ms"] for v in stats.values())
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
     peaks, peak_src = {}, "fallback 6.8 TB/s (of fallback)"
@@ -474,6 +479,11 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "kernel": dom_name, "peak_source": peak_src}
+    if dom_name in ncu_traffic_ratio:
+        roof["traffic"] = ncu_traffic_ratio[dom_name] * dom_bytes
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel at "
+                                  "255^2 x 128 (profiles/kernels_gmres_mixed_255x255_n128.md), scaled to "
+                                  "this launch by its algorithmic bytes")
     roof["share_of_kernel_time"] = dom["ms"] / tot_ms if tot_ms else None
     breakdown = {k: {"share": v["ms"] / tot_ms if tot_ms else None, "launches": v["launches"],
                      "avg_us": 1000 * v["ms"] / v["launches"] if v["launches"] else None,
