@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--skip-3d", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-fst", action="store_true")
     ap.add_argument("--batch-gb", type=float, default=110.0, help="device memory per batched wave (GB)")
     a = ap.parse_args()
     a.gammas = tuple(float(x) for x in a.gammas.split(","))
@@ -251,6 +252,26 @@ def _extra_workloads(args, torch, dev):
             del b
             torch.cuda.empty_cache()
         out["grf_3d_63cubed_n128"] = {"unknowns": p.unknowns, "gamma": p.gamma, **res}
+
+    if not args.skip_fst:
+        # constant a: sine-transform solves, finite differences and bilinear finite elements
+        p = S.example1_problem(M1, NT, 1e-4)
+        eps = math.sqrt(p.tau)
+        res = {}
+        for space in ("fd", "fe"):
+            for prec in ("fp32", "fp64"):
+                sol = Solver(2, p.m1, p.n, p.T, p.gamma, eps, None, spatial="fst", precision=prec, max_iter=60,
+                             space=space)
+                b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
+                                  torch.from_numpy(p.y0).to(dev))
+                t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
+                res[f"{space}_{prec}"] = {"solve_s": t, "iters": r[1], "relres": r[2]}
+                sol.close()
+                del b
+                torch.cuda.empty_cache()
+        out["const_a_fst_255sq_n256"] = {"data": "Example 1 fields, a = 1, gamma 1e-4, eps = sqrt(tau)",
+                                         "fd": "finite differences (M = I)",
+                                         "fe": "bilinear finite elements (mass matrix M)", **res}
 
     if not args.skip_grad:
         p = S.gradient_problem()

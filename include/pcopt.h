@@ -71,6 +71,13 @@ typedef enum pc_gmres_mode {
   PC_GMRES_LEFT = 1    /* GMRES on P^{-1}A x = P^{-1}b, stops on ||P^{-1}(b-Ax)||/||P^{-1}b|| */
 } pc_gmres_mode;
 
+typedef enum pc_space {
+  PC_SPACE_FD = 0,  /* finite differences: M = I, conservative stencil of K (Eq. matrix_A as printed) */
+  PC_SPACE_FE = 1   /* conforming bilinear (2D) / trilinear (3D) finite elements, mass matrix M
+                       (Section 1: A = [[alpha I(x)M, T^T], [-T, alpha I(x)M]], T = B_n(x)M + tau I(x)K);
+                       constant coefficient a only, sine-transform spatial solves */
+} pc_space;
+
 typedef struct pc_params {
   int dim;          /* 2 or 3 */
   int m1;           /* interior grid points per dimension, h = 1/(m1+1); multigrid needs m1 = 2^k-1 */
@@ -82,6 +89,7 @@ typedef struct pc_params {
   int spatial;      /* pc_spatial */
   int precision;    /* pc_precision */
   int max_iter;     /* Krylov capacity: basis storage for this many iterations (1..1000) */
+  int space;        /* pc_space: spatial discretisation (0 = finite differences) */
 } pc_params;
 
 typedef struct pc_handle pc_handle;
@@ -94,9 +102,14 @@ typedef struct pc_handle pc_handle;
  *            and >= 0 at boundary nodes.
  *   stream:  stream used for the coefficient upload.
  *   out:     receives the handle (caller releases it with pc_destroy).
+ * With space = PC_SPACE_FE the matrices are the bilinear / trilinear element
+ * matrices of the uniform grid (M = (h/6)^dim [1 4 1]^(x)dim,
+ * K = a (h/6)^(dim-1)/h sum_axes [-1 2 -1] (x) [1 4 1]..), every spatial solve
+ * (sigma M + tau K) z = r is exact by sine transforms, and a must be constant.
  * Errors: PC_ERR_ARG (dim not 2/3, m1 < 1, n outside 1..4096,
  * T <= 0, gamma <= 0, eps outside (0,1], a not as above, FST with non-constant a,
- * MG with m1 != 2^k-1), PC_ERR_OOM, PC_ERR_CUDA. */
+ * MG with m1 != 2^k-1, unknown space), PC_ERR_UNSUPPORTED (finite elements with a
+ * non-constant a or multigrid), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
 
 /* Replace the coefficient a(x) of an existing handle without reallocating:
@@ -109,7 +122,8 @@ int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
 int pc_destroy(pc_handle* h);
 
-/* y = A x  (Eq. matrix_A, Section 2.1: two block-bidiagonal Toeplitz products, O(mn)).
+/* y = A x  (Eq. matrix_A, Section 2.1: two block-bidiagonal Toeplitz products, O(mn);
+ * with finite elements the blocks carry M, see pc_space).
  * x, y: device, 2*n*ms FP64, must not overlap. */
 int pc_matvec(pc_handle* h, const double* x, double* y, void* stream);
 
@@ -117,6 +131,7 @@ int pc_matvec(pc_handle* h, const double* x, double* y, void* stream);
  * with its FP32 basis Z.  Evaluated in double-float arithmetic on the FP32 units
  * (each FP64 coefficient split into two floats, FMA error terms, TwoSum
  * accumulation); relative error of order 2^-46 of the largest term; FP64 output.
+ * Finite-element handles evaluate it in FP64 arithmetic.
  * x: device, 2*n*ms FP32; y: device, 2*n*ms FP64. */
 int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream);
 
@@ -133,7 +148,8 @@ int pc_apply_precond(pc_handle* h, const double* v, double* w, void* stream);
 
 /* b = [g_vec; -sqrt(gamma) f_vec] of Eq. main_system_before / Eq. main_system:
  * g_vec_j = tau g^(j) (j = 1..n; the final condition p^(N) = 0 adds nothing),
- * f_vec_1 = tau f^(1) + y0, f_vec_j = tau f^(j).
+ * f_vec_1 = tau f^(1) + y0, f_vec_j = tau f^(j).  Finite elements: every term is
+ * multiplied by M (g_vec_j = tau M g^(j), f_vec_1 = tau M f^(1) + M y0, ...).
  * f, g: device, n*ms FP64 (time levels t_j = j tau, j = 1..n); y0: device, ms
  * FP64 (NULL means 0); f may be NULL (means 0).  b: device, 2*n*ms FP64. */
 int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y0,
@@ -190,6 +206,7 @@ int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, in
  *   grad_P = -tau * sum_j [ lam1_j^T (dK/dlog a_P) x2_j - lam2_j^T (dK/dlog a_P) x1_j ],
  *   u^T (dK/dlog a_P) v = a_P/(2h^2) sum_{faces (P,Q)} (u_P-u_Q)(v_P-v_Q),
  * i.e. -lam^T (dA/dlog a_P) x for interior nodes P (boundary nodes fixed).
+ * Finite-difference handles only (PC_ERR_UNSUPPORTED for finite elements).
  *   x, lam: device all-at-once vectors; grad: device, ms FP64 (interior nodes,
  *   same spatial ordering), overwritten. */
 int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream);
@@ -224,7 +241,8 @@ int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const double* a_int,
  * all-at-once unknowns leave out: from a solution x of A x = b (device,
  * 2*n*ms; y = x1 / sqrt(gamma), p = x2),
  *   (I + tau K) y^(N) = y^(n) + tau f_T + (tau / gamma) p_N,
- *   (I + tau K) p^(0) = p^(1) + tau g_0 - tau y0,
+ *   (I + tau K) p^(0) = p^(1) + tau g_0 - tau y0
+ * (finite elements: M + tau K on the left, each right-hand side multiplied by M),
  * each solved to relative residual rtol by flexible conjugate gradients
  * preconditioned with the handle's spatial solver at shift 1 (exact for the
  * sine-transform handle, one V(1,0) cycle otherwise).  f_T, g_0, y0, p_N:

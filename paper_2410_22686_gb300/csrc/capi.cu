@@ -51,7 +51,8 @@ const char* kernel_class_name(int kc) {
                                         "arnoldi_dot",   "arnoldi_update_norm", "reduce_partials",
                                         "normalize",     "givens",       "x_update",
                                         "axpby",         "build_rhs",    "grad_stencil",
-                                        "arnoldi_reorth", "mg_coarse_cycle", "mg_down"};
+                                        "arnoldi_reorth", "mg_coarse_cycle", "mg_down",
+                                        "fe_apply"};
   return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
 }
 
@@ -159,6 +160,8 @@ struct pc_handle {
   bool bf16s = false;  // multigrid iterates stored as BF16 pairs (FP32 arithmetic)
   int cap = 0;
   double a_const = 1.0;
+  bool fe = false;  // finite elements in space (mass matrix M): constant a, FST
+  FeScale fes;
 
   std::vector<LevelBuf> lv;
   int coarse_l0 = 0;                 // first level run by the fused coarse-cycle kernel
@@ -184,6 +187,10 @@ struct pc_handle {
   float* S32 = nullptr;
   double* lamK64 = nullptr;
   float* lamK32 = nullptr;
+  double* rmass64 = nullptr;  // finite elements: 1 / (eigenvalue of M) per sine mode
+  float* rmass32 = nullptr;
+  double2* fst_tw64 = nullptr;  // fast sine transforms: exp(-2 pi i q / (2(m+1))), q < 2(m+1)
+  float2* fst_tw32 = nullptr;
   void* fst_tmp = nullptr;
   // gradient
   double* a_int = nullptr;
@@ -350,22 +357,40 @@ static std::vector<double> interior_of(const std::vector<double>& a, int m1, int
   return ai;
 }
 
-// FST eigenvalues tau * c * sum_axes 4 sin^2(pi i/(2(m+1)))/h^2 of tau K for a == c
-static std::vector<double> fst_eigenvalues(int m, int dim, double tau, double c) {
+// FST eigenvalues on the sine modes (i1, i2[, i3]) for a == c.  Finite differences:
+// lam = tau c sum_axes 4 sin^2(pi i/(2(m+1)))/h^2 of tau K.  Finite elements: the 1D
+// element matrices have the eigenvalues mu_M(i) = h/6 (4 + 2 cos(pi i/(m+1))) and
+// mu_K(i) = 4 sin^2(pi i/(2(m+1)))/h, so M has prod_axes mu_M and K has
+// c sum_axes mu_K prod_others mu_M; (sigma M + tau K)^{-1} is applied as
+// rmass / (sigma + lam) with rmass = 1/eig(M) and lam = tau eig(K)/eig(M).
+static std::vector<double> fst_eigenvalues(int m, int dim, double tau, double c, bool fe,
+                                           std::vector<double>* rmass = nullptr) {
   const double h = 1.0 / (m + 1);
-  std::vector<double> mu(m);
+  std::vector<double> mu(m), muM(m, 1.0);
   for (int i = 0; i < m; ++i) {
     const double sv = std::sin(M_PI * (double)(i + 1) / (2.0 * (m + 1)));
-    mu[i] = 4.0 * sv * sv / (h * h);
+    if (fe) {
+      mu[i] = 4.0 * sv * sv / h;
+      muM[i] = h / 6.0 * (4.0 + 2.0 * std::cos(M_PI * (double)(i + 1) / (m + 1)));
+    } else {
+      mu[i] = 4.0 * sv * sv / (h * h);
+    }
   }
   const int64_t ms = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
   std::vector<double> lam((size_t)ms);
+  if (rmass) rmass->assign((size_t)ms, 1.0);
   for (int64_t s = 0; s < ms; ++s) {
-    const int i1 = (int)(s % m);
-    const int64_t r = s / m;
-    const int i2 = (int)(dim == 2 ? r : r % m);
-    const int i3 = dim == 3 ? (int)(r / m) : -1;
-    lam[(size_t)s] = tau * c * (mu[i1] + mu[i2] + (i3 >= 0 ? mu[i3] : 0.0));
+    const int ix[3] = {(int)(s % m), (int)(dim == 2 ? s / m : (s / m) % m), dim == 3 ? (int)(s / m / m) : -1};
+    double eM = 1.0, eK = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double t = mu[ix[a]];
+      for (int b = 0; b < dim; ++b)
+        if (b != a) t *= muM[ix[b]];
+      eK += t;
+      eM *= muM[ix[a]];
+    }
+    lam[(size_t)s] = tau * c * eK / eM;
+    if (rmass) (*rmass)[(size_t)s] = 1.0 / eM;
   }
   return lam;
 }
@@ -423,6 +448,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     return fail(PC_ERR_ARG, "unknown precision");
   if (p->spatial < 0 || p->spatial > 2) return fail(PC_ERR_ARG, "unknown spatial solver");
   if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
+  if (p->space != PC_SPACE_FD && p->space != PC_SPACE_FE) return fail(PC_ERR_ARG, "unknown space discretisation");
 
   const int dim = p->dim, m1 = p->m1;
   const int M = m1 + 2;
@@ -437,6 +463,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     }
   }
   int spatial = p->spatial;
+  const bool fe = p->space == PC_SPACE_FE;
+  if (fe && (!constant || spatial == PC_SPATIAL_MG))
+    return fail(PC_ERR_UNSUPPORTED, "finite elements: implemented for a constant coefficient with sine-transform solves");
   if (spatial == PC_SPATIAL_AUTO) spatial = constant ? PC_SPATIAL_FST : PC_SPATIAL_MG;
   if (spatial == PC_SPATIAL_FST && !constant) return fail(PC_ERR_ARG, "FST needs a constant coefficient a");
   if (spatial == PC_SPATIAL_MG && ((m1 + 1) & m1) != 0) return fail(PC_ERR_ARG, "multigrid needs m1 = 2^k - 1");
@@ -462,6 +491,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->bf16s = p->precision == PC_PREC_MIXED_BF16S && spatial == PC_SPATIAL_MG;
   h->cap = p->max_iter;
   h->a_const = a[0];
+  h->fe = fe;
+  h->fes = fe_scale(dim, m1, h->a_const);
   h->prof.on = false;
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -580,11 +611,24 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     const double sc = std::sqrt(2.0 / (m + 1));
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = sc * std::sin(M_PI * (double)(i + 1) * (j + 1) / (m + 1));
-    const std::vector<double> lam = fst_eigenvalues(m, dim, h->tau, h->a_const);
+    std::vector<double> rmass;
+    const std::vector<double> lam = fst_eigenvalues(m, dim, h->tau, h->a_const, fe, &rmass);
     if ((rc = upload(h, &h->S64, S, st))) goto fail_out;
     if ((rc = upload(h, &h->S32, S, st))) goto fail_out;
     if ((rc = upload(h, &h->lamK64, lam, st))) goto fail_out;
     if ((rc = upload(h, &h->lamK32, lam, st))) goto fail_out;
+    if (fe && (rc = upload(h, &h->rmass64, rmass, st))) goto fail_out;
+    if (fe && (rc = upload(h, &h->rmass32, rmass, st))) goto fail_out;
+    if (fst_fast_supported<float>(m)) {
+      const int Lf = 2 * (m + 1);
+      std::vector<double> twr(Lf), twi(Lf);
+      for (int q = 0; q < Lf; ++q) {
+        twr[q] = std::cos(2.0 * M_PI * q / Lf);
+        twi[q] = -std::sin(2.0 * M_PI * q / Lf);
+      }
+      if ((rc = upload_c(h, (void**)&h->fst_tw64, twr, twi, false, st))) goto fail_out;
+      if ((rc = upload_c(h, (void**)&h->fst_tw32, twr, twi, true, st))) goto fail_out;
+    }
     if ((rc = dev_alloc(h, &h->fst_tmp, (size_t)h->planes * h->ms * cb))) goto fail_out;
   }
   // ---- interior coefficient (gradient) and its scratch
@@ -701,8 +745,9 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
   }
   if ((rc = refill(h->a_int, interior_of(a, m1, dim), st, s64))) return rc;
   h->a_const = a[0];
+  h->fes = fe_scale(dim, m1, h->a_const);
   if (h->spatial == PC_SPATIAL_FST) {
-    const std::vector<double> lam = fst_eigenvalues(m1, dim, h->tau, h->a_const);
+    const std::vector<double> lam = fst_eigenvalues(m1, dim, h->tau, h->a_const, h->fe);
     if ((rc = refill(h->lamK64, lam, st, s64))) return rc;
     if ((rc = refill(h->lamK32, lam, st, s32))) return rc;
   }
@@ -759,6 +804,8 @@ struct Tables<double> {
   static const double2* sig1(const pc_handle* h) { return h->sig1_64; }
   static const double* S(const pc_handle* h) { return h->S64; }
   static const double* lamK(const pc_handle* h) { return h->lamK64; }
+  static const double* rmass(const pc_handle* h) { return h->rmass64; }
+  static const double2* fst_tw(const pc_handle* h) { return h->fst_tw64; }
 };
 template <>
 struct Tables<float> {
@@ -769,6 +816,8 @@ struct Tables<float> {
   static const float2* sig1(const pc_handle* h) { return h->sig1_32; }
   static const float* S(const pc_handle* h) { return h->S32; }
   static const float* lamK(const pc_handle* h) { return h->lamK32; }
+  static const float* rmass(const pc_handle* h) { return h->rmass32; }
+  static const float2* fst_tw(const pc_handle* h) { return h->fst_tw32; }
 };
 
 template <typename Tc>
@@ -789,6 +838,26 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
   const C* sig = sig_override ? sig_override : Tables<Tc>::sig(h);
   cudaError_t e;
   if constexpr (std::is_same<TU, C>::value) {
+    if (h->spatial == PC_SPATIAL_FST && Tables<Tc>::fst_tw(h) && fst_fast_supported<Tc>(h->m1)) {
+      // fast transforms: forward along x1 (.. x_{d-1}), the last axis fused with the
+      // divide, inverse back down to x1
+      const Grid g = grid_of(h, 0);
+      const C* tw = Tables<Tc>::fst_tw(h);
+      C* tmp = (C*)h->fst_tmp;
+      const int last = h->dim - 1;
+      for (int ax = 0; ax < last; ++ax)
+        if ((e = launch_fst_fast<Tc>(L, g, P, ax, false, tw, nullptr, nullptr, nullptr, ax == 0 ? (const C*)h->lv[0].r : tmp,
+                                     tmp)) != cudaSuccess)
+          return e;
+      if ((e = launch_fst_fast<Tc>(L, g, P, last, true, tw, Tables<Tc>::lamK(h), Tables<Tc>::rmass(h), sig, tmp,
+                                   last == 0 ? (C*)h->lv[0].u : tmp)) != cudaSuccess)
+        return e;
+      for (int ax = last - 1; ax >= 0; --ax)
+        if ((e = launch_fst_fast<Tc>(L, g, P, ax, false, tw, nullptr, nullptr, nullptr, tmp,
+                                     ax == 0 ? (C*)h->lv[0].u : tmp)) != cudaSuccess)
+          return e;
+      return cudaSuccess;
+    }
     if (h->spatial == PC_SPATIAL_FST) {
       const Grid g = grid_of(h, 0);
       C* bufs[2] = {(C*)h->lv[0].r, (C*)h->fst_tmp};
@@ -797,7 +866,7 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
         if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], bufs[1 - cur])) != cudaSuccess) return e;
         cur = 1 - cur;
       }
-      if ((e = launch_fst_divide<Tc>(L, g, P, Tables<Tc>::lamK(h), sig, bufs[cur])) != cudaSuccess) return e;
+      if ((e = launch_fst_divide<Tc>(L, g, P, Tables<Tc>::lamK(h), Tables<Tc>::rmass(h), sig, bufs[cur])) != cudaSuccess) return e;
       for (int ax = h->dim - 1; ax >= 0; --ax) {
         C* dst = ax == 0 ? (C*)h->lv[0].u : bufs[1 - cur];
         if ((e = launch_fst_axis<Tc>(L, g, P, ax, Tables<Tc>::S(h), bufs[cur], dst)) != cudaSuccess) return e;
@@ -886,8 +955,28 @@ static cudaError_t precond64(pc_handle* h, Launch& L, const double* v, double* w
 static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32, double* y, bool transpose) {
   Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
   const Grid g = grid_of(h, 0);
+  if (h->fe) {
+    if (x_f32) return launch_matvec_fe<float>(L, g, h->n, h->alpha, h->fes, h->tau, (const float*)x, y, transpose);
+    return launch_matvec_fe<double>(L, g, h->n, h->alpha, h->fes, h->tau, (const double*)x, y, transpose);
+  }
   if (x_f32) return launch_matvec<float>(L, g, h->n, st, h->alpha, (const float*)x, y, transpose);
   return launch_matvec<double>(L, g, h->n, st, h->alpha, (const double*)x, y, transpose);
+}
+
+// y = A z for the preconditioned basis vector z of flexible GMRES (FP32 in the
+// mixed modes: double-float arithmetic for finite differences, FP64 for elements);
+// with jdev: z += (*jdev) zs, y += (*jdev + 1) ys
+static cudaError_t matvec_basis(pc_handle* h, Launch& L, const void* z, double* y, size_t zs = 0, size_t ys = 0,
+                                const int* jdev = nullptr) {
+  const Grid g = grid_of(h, 0);
+  if (h->fe)
+    return h->fp32 ? launch_matvec_fe<float>(L, g, h->n, h->alpha, h->fes, h->tau, (const float*)z, y, false, zs, ys,
+                                             jdev)
+                   : launch_matvec_fe<double>(L, g, h->n, h->alpha, h->fes, h->tau, (const double*)z, y, false, zs,
+                                              ys, jdev);
+  if (h->fp32) return launch_matvec_df(L, g, h->n, h->wdf, h->ddf, h->alpha_df, (const float*)z, y, zs, ys, jdev);
+  return launch_matvec<double>(L, g, h->n, Stencil<double>{h->lv[0].w64, h->lv[0].d64}, h->alpha,
+                               (const double*)z, y, false, zs, ys, jdev);
 }
 
 // ---------------------------------------------------------------------------
@@ -904,7 +993,8 @@ extern "C" int pc_matvec(pc_handle* h, const double* x, double* y, void* stream)
 extern "C" int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream) {
   if (!h || !x || !y) return fail(PC_ERR_ARG, "pc_matvec_f32: null argument");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
-  cudaError_t e = launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, x, y);
+  cudaError_t e = h->fe ? matvec_any(h, L, x, true, y, false)
+                        : launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, x, y);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_matvec_f32");
 }
 
@@ -927,12 +1017,25 @@ extern "C" int pc_build_rhs(pc_handle* h, const double* f, const double* g, cons
                             void* stream) {
   if (!h || !g || !b) return fail(PC_ERR_ARG, "pc_build_rhs: null g or b");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
-  cudaError_t e = launch_build_rhs(L, h->ms, h->n, h->tau, h->sqrtg, f, g, y0, b);
+  cudaError_t e;
+  if (!h->fe) {
+    e = launch_build_rhs(L, h->ms, h->n, h->tau, h->sqrtg, f, g, y0, b);
+  } else {
+    // b = [tau (I(x)M) g; -sqrt(gamma) (tau (I(x)M) f + M y0 e_1)]
+    const Grid gr = grid_of(h, 0);
+    const size_t half = (size_t)h->n * h->ms;
+    e = launch_fe_apply(L, gr, h->n, h->tau * h->fes.wM, 0.0, g, 0.0, b);
+    if (e == cudaSuccess)
+      e = f ? launch_fe_apply(L, gr, h->n, -h->sqrtg * h->tau * h->fes.wM, 0.0, f, 0.0, b + half)
+            : cudaMemsetAsync(b + half, 0, half * sizeof(double), L.stream);
+    if (e == cudaSuccess && y0) e = launch_fe_apply(L, gr, 1, -h->sqrtg * h->fes.wM, 0.0, y0, 1.0, b + half);
+  }
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_build_rhs");
 }
 
 extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream) {
   if (!h || !x || !lam || !grad) return fail(PC_ERR_ARG, "pc_grad_log_a: null argument");
+  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_grad_log_a: finite-difference handles only");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   // -tau * a_P / (2 h^2) * sum_j sum_faces [...]
   const double scale = -h->tau * 0.5 / (h->h * h->h);
@@ -1057,7 +1160,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
         GM_CUDA(precond32<float, float>(h, L, vf, zj));
-        GM_CUDA(launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, zj, vn));
+        GM_CUDA(matvec_basis(h, L, zj, vn));
       } else {
         double* zj = (double*)h->Z + (size_t)j * U;
         GM_CUDA(precond_t<double, double2, double>(h, L, vj, zj));
@@ -1183,16 +1286,14 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   const int ldh = h->cap + 1;
   const int* j = h->idx;
   const ArnoldiScalars AS{h->scal + 4, h->scal + 5, h->scal + 6, h->scal + 7, h->scal + 8, h->scal + 9};
-  Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
-  const Grid g = grid_of(h, 0);
   if (h->fp32) {
     float* Z = (float*)h->Z;
     GR_CUDA((precond32<float, float>(h, L, h->vf32, Z, U, j, false)));
-    GR_CUDA(launch_matvec_df(L, g, h->n, h->wdf, h->ddf, h->alpha_df, Z, h->V, U, U, j));
+    GR_CUDA(matvec_basis(h, L, Z, h->V, U, U, j));
   } else {
     double* Z = (double*)h->Z;
     GR_CUDA((precond_t<double, double2, double>(h, L, h->V, Z, U, j)));
-    GR_CUDA(launch_matvec<double>(L, g, h->n, st, h->alpha, Z, h->V, false, U, U, j));
+    GR_CUDA(matvec_basis(h, L, Z, h->V, U, U, j));
   }
   GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol, AS.ww, nullptr));
   GR_CUDA(launch_arnoldi_prep_dev(L, j, h->hcol, AS));
@@ -1639,10 +1740,7 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
       t.mv_tj = tjs[ti];
       Launch L{st, nullptr, &t};
       const double ms = time_reps(st, reps, [&] {
-        return h->fp32 ? launch_matvec_df(L, grid_of(h, 0), h->n, h->wdf, h->ddf, h->alpha_df, (const float*)h->Z,
-                                          h->V + h->U)
-                       : launch_matvec<double>(L, grid_of(h, 0), h->n, Stencil<double>{h->lv[0].w64, h->lv[0].d64},
-                                               h->alpha, (const double*)h->Z, h->V + h->U, false);
+        return matvec_basis(h, L, h->Z, h->V + h->U);
       });
       if (ms < tbest) {
         tbest = ms;
@@ -1706,7 +1804,10 @@ static int pcg_E(pc_handle* h, Launch& L, const double* b, double* u, double rto
   if (bnorm == 0.0) return PC_OK;
   if (!std::isfinite(bnorm) || !std::isfinite(rz)) return fail(PC_ERR_BREAKDOWN, "end-point solve: non-finite input");
   for (int it = 1; it <= maxit; ++it) {
-    PC_CUDA(launch_apply_E(L, g, st, p, q));
+    if (h->fe)
+      PC_CUDA(launch_fe_apply(L, g, 1, h->fes.wM, h->tau * h->fes.wK, p, 0.0, q));  // (M + tau K) p
+    else
+      PC_CUDA(launch_apply_E(L, g, st, p, q));
     PC_CUDA(dot(p, q, sc + 2));
     if (int rc = fetch(3)) return rc;
     const double pq = h->host[2];
@@ -1742,7 +1843,13 @@ extern "C" int pc_end_point_solves(pc_handle* h, const double* x, const double* 
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   double* rhs_y = h->wbuf;
   double* rhs_p = h->wbuf + h->ms;
-  GR_CUDA(launch_endpoint_rhs(L, x, h->ms, h->n, h->tau, h->prm.gamma, f_T, g_0, y0, p_N, rhs_y, rhs_p));
+  if (!h->fe) {
+    GR_CUDA(launch_endpoint_rhs(L, x, h->ms, h->n, h->tau, h->prm.gamma, f_T, g_0, y0, p_N, rhs_y, rhs_p));
+  } else {  // the same combinations, multiplied by M
+    GR_CUDA(launch_endpoint_rhs(L, x, h->ms, h->n, h->tau, h->prm.gamma, f_T, g_0, y0, p_N, h->tbuf,
+                                h->tbuf + h->ms));
+    GR_CUDA(launch_fe_apply(L, grid_of(h, 0), 2, h->fes.wM, 0.0, h->tbuf, 0.0, rhs_y));
+  }
   int it_y = 0, it_p = 0;
   if (int rc = pcg_E(h, L, rhs_y, yN, rtol, maxit, &it_y)) return rc;
   if (int rc = pcg_E(h, L, rhs_p, p0, rtol, maxit, &it_p)) return rc;

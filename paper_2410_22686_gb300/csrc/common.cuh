@@ -51,6 +51,11 @@ __host__ __device__ __forceinline__ double2 cinv(double2 z) {
 }
 template <typename T>
 __host__ __device__ __forceinline__ typename Cx<T>::t czero() { return cmk<T>(T(0), T(0)); }
+// 1 / (sigma + d) for a complex shift sigma and a real diagonal d
+template <typename Tc>
+__device__ __forceinline__ typename Cx<Tc>::t inv_diag(typename Cx<Tc>::t sig, Tc dg) {
+  return cinv(cmk<Tc>(sig.x + dg, sig.y));
+}
 
 // FP64 <-> FP32 conversions on the integer pipes.  GB300 executes F2F
 // conversions on its FP64 unit, whose rate is 1/64 of FP32, which made plain
@@ -134,6 +139,7 @@ enum KernelClass {
   KC_REORTH,  // gated re-orthogonalisation passes (bytes booked only when they ran)
   KC_MG_COARSE,
   KC_MG_DOWN,  // fused smooth + residual + restriction of one level
+  KC_FE_APPLY, // finite-element mass / stiffness product of single fields
   KC_COUNT
 };
 const char* kernel_class_name(int kc);
@@ -215,6 +221,23 @@ cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, c
                              const float* x, double* y, size_t xstride = 0, size_t ystride = 0,
                              const int* jdev = nullptr);
 
+// Finite elements in space (bilinear / trilinear, constant coefficient c): the
+// mass and stiffness matrices are wM and wK times fixed integer stencils.
+struct FeScale {
+  double wM = 0.0;  // (h/6)^dim
+  double wK = 0.0;  // c (h/6)^(dim-1) / h
+};
+FeScale fe_scale(int dim, int m1, double c);
+// y = A x or A^T x with A = [[alpha I(x)M, T^T], [-T, alpha I(x)M]], T = B_n(x)M + tau I(x)K;
+// x in Tin, FP64 arithmetic and output; strides / jdev as launch_matvec
+template <typename Tin>
+cudaError_t launch_matvec_fe(Launch& L, const Grid& g, int n, double alpha, FeScale fs, double tau, const Tin* x,
+                             double* y, bool transpose, size_t xstride = 0, size_t ystride = 0,
+                             const int* jdev = nullptr);
+// out_p = cM (M/wM) in_p + cK (K/wK) in_p + beta out_p for `planes` fields of g.np values
+cudaError_t launch_fe_apply(Launch& L, const Grid& g, int planes, double cM, double cK, const double* in, double beta,
+                            double* out);
+
 // forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
 // dpow[j] = eps^{j/n}, dinv[j] = eps^{-j/n}, tw[k] = exp(-2 pi i k/n) for k = 0..n-1
 // With jdev != nullptr the input is v + (*jdev) * vstride (device-resident Arnoldi index).
@@ -242,12 +265,24 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
                                 const int* jdev = nullptr, FineCorrection<TU> fc = FineCorrection<TU>());
 
 // FST: one DST-I along `axis` of every plane (out = S in), and the spectral divide
+// buf *= rmass / (sigma + lamK) (rmass == nullptr: 1)
 template <typename Tc>
 cudaError_t launch_fst_axis(Launch& L, const Grid& g, int planes, int axis, const Tc* S,
                             const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out);
 template <typename Tc>
-cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK,
+cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK, const Tc* rmass,
                               const typename Cx<Tc>::t* sigma, typename Cx<Tc>::t* buf);
+// Fast sine transforms (k_fst.cu) for m + 1 a power of two, 2(m+1) <= 1024 (FP32) /
+// 512 (FP64): out = S in along `axis` (S the orthonormal DST-I), or with `divide`
+// out = S diag(rmass / (sigma_p + lamK)) S in along the last axis.  tw: the
+// 2(m+1)-point twiddle circle exp(-2 pi i q / (2(m+1))).  in may equal out.
+template <typename Tc>
+bool fst_fast_supported(int m);
+template <typename Tc>
+cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool divide,
+                            const typename Cx<Tc>::t* tw, const Tc* lamK, const Tc* rmass,
+                            const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
+                            typename Cx<Tc>::t* out);
 
 // multigrid pieces (planes = 2*nfreq, sigma per plane); iterates u stored as TU
 template <typename Tc, typename TU>

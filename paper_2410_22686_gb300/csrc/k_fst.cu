@@ -1,0 +1,221 @@
+// Fast sine transform (DST-I) along one axis of the spectral planes: the exact
+// spatial solves of the constant-coefficient case (step 2 of the four-step
+// apply, Section 2.1), O(m log m) per grid line instead of the dense O(m^2)
+// product with the DST matrix.
+//
+// With N = m + 1 a power of two, the orthonormal DST-I of a line x_1..x_m,
+//   X_k = sqrt(2/N) sum_j x_j sin(pi j k / N),
+// is read off the length-L = 2N FFT of the odd extension y (y_0 = y_N = 0,
+// y_j = x_j, y_{L-j} = -x_j): Y_k = -2i sum_j x_j sin(pi j k / N), so
+// X_k = sqrt(2/N) (i/2) Y_k.  The transform is its own inverse.
+//
+// One CTA of 256 threads owns COLS = 256/N1 grid lines along the axis:
+//  * the tile (m values of each line) is copied into shared memory with the
+//    line index fastest, so a warp reads whole 32-byte sectors for every axis
+//    (along x1 four consecutive values of each of eight lines, along x2/x3
+//    consecutive lines) and the shared-memory accesses are conflict-free;
+//  * the L-point FFT is the four-step split L = N1 N2 of the time FFT: an
+//    N2-point register FFT per thread row, a twiddle, one shared-memory
+//    exchange, an N1-point register FFT;
+//  * the results go back through shared memory and out with the same pattern.
+// The last axis of a solve runs fused: forward transform, the spectral divide
+// by (sigma_p M + tau K) eigenvalues, inverse transform, one read and one write.
+#include <cmath>
+
+#include "common.cuh"
+#include "regfft.cuh"
+
+namespace pcopt {
+
+namespace {
+
+// One DST-I of every line of the tile in `sm` ([j][c], j < m, line index c fastest),
+// in place.  Ends with a barrier.
+template <typename Tc, int N1, int N2>
+__device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* __restrict__ tw, int m,
+                                         Tc half_scale, int r, int c) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int L = N1 * N2;
+  constexpr int N = L / 2;
+  constexpr int COLS = 256 / N1;
+  // (A) rows j = r + N1 j2 of the odd extension, N2-point DFT over j2
+  C x[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    const int j = r + N1 * j2;
+    C v = czero<Tc>();
+    if (j > 0 && j < N) {
+      v = sm[(j - 1) * COLS + c];
+    } else if (j > N) {
+      const C t = sm[(L - j - 1) * COLS + c];
+      v = cmk<Tc>(-t.x, -t.y);
+    }
+    x[j2] = v;
+  }
+  __syncthreads();  // every read of the tile is done before the exchange overwrites it
+  reg_fft<N2, false>(x, tw, N1);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const C y = (k2 == 0 || r == 0) ? x[k2] : cmul(tw[r * k2], x[k2]);
+    sm[(k2 * N1 + r) * COLS + c] = y;
+  }
+  __syncthreads();
+  // (C) row k2 = r (< N2): N1-point DFT over j1, Y[k2 + N2 k1]
+  C y[N1];
+  if (r < N2) {
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) y[j1] = sm[(r * N1 + j1) * COLS + c];
+  }
+  __syncthreads();
+  if (r < N2) {
+    reg_fft<N1, false>(y, tw, N2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int k = r + N2 * k1;  // X_k = sqrt(2/N) (i/2) Y_k for k = 1..m
+      if (k >= 1 && k <= m) sm[(k - 1) * COLS + c] = cmk<Tc>(-y[k1].y * half_scale, y[k1].x * half_scale);
+    }
+  }
+  __syncthreads();
+}
+
+// DIVIDE: forward DST, sm *= rmass / (sigma_p + lamK), inverse DST (the last axis).
+// in may equal out: a CTA reads its whole tile before it writes it back.
+// Lines: plane p = line / (np / m); inside the plane, a line along `axis` starts at
+// outer * m * lstride + inner with lstride = m^axis, inner < lstride.
+template <typename Tc, int N1, int N2, bool DIVIDE>
+__global__ void __launch_bounds__(256) fst4_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
+                                                   const typename Cx<Tc>::t* __restrict__ tw, int m, int64_t np,
+                                                   int64_t lstride, int64_t nlines, Tc half_scale,
+                                                   const Tc* __restrict__ lamK, const Tc* __restrict__ rmass,
+                                                   const typename Cx<Tc>::t* __restrict__ sigma) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char fst_smem[];
+  C* sm = reinterpret_cast<C*>(fst_smem);
+  __shared__ int64_t lbase[COLS];  // offset of each line's first value (plane included)
+  __shared__ int lplane[COLS];
+  const int tid = threadIdx.x;
+  const int64_t line0 = (int64_t)blockIdx.x * COLS;
+  if (tid < COLS) {
+    const int64_t l = line0 + tid;
+    const int64_t lpp = np / m;  // lines per plane
+    int64_t b = 0;
+    int p = 0;
+    if (l < nlines) {
+      p = (int)(l / lpp);
+      b = l - (int64_t)p * lpp;
+    }
+    const int64_t outer = b / lstride, inner = b - outer * lstride;
+    lbase[tid] = (int64_t)p * np + outer * lstride * m + inner;
+    lplane[tid] = l < nlines ? p : -1;
+  }
+  __syncthreads();
+  const int tot = COLS * m;
+  for (int e = tid; e < tot; e += 256) {
+    const int j = e / COLS, c = e - j * COLS;
+    sm[e] = lplane[c] >= 0 ? in[lbase[c] + (int64_t)j * lstride] : czero<Tc>();
+  }
+  __syncthreads();
+  const int r = tid / COLS, c = tid - (tid / COLS) * COLS;
+  dst_tile<Tc, N1, N2>(sm, tw, m, half_scale, r, c);
+  if (DIVIDE) {
+    for (int e = tid; e < tot; e += 256) {
+      const int j = e / COLS, cc = e - j * COLS;
+      const int p = lplane[cc];
+      if (p < 0) continue;
+      const int64_t s = lbase[cc] - (int64_t)p * np + (int64_t)j * lstride;  // spectral index in the plane
+      C v = sm[e];
+      if (rmass) v = cscale(v, rmass[s]);
+      sm[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
+    }
+    __syncthreads();
+    dst_tile<Tc, N1, N2>(sm, tw, m, half_scale, r, c);
+  }
+  for (int e = tid; e < tot; e += 256) {
+    const int j = e / COLS, cc = e - j * COLS;
+    if (lplane[cc] >= 0) out[lbase[cc] + (int64_t)j * lstride] = sm[e];
+  }
+}
+
+template <typename Tc, int N1, int N2>
+cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, const typename Cx<Tc>::t* tw,
+                 const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
+                 typename Cx<Tc>::t* out) {
+  constexpr int COLS = 256 / N1;
+  const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
+  int64_t lstride = 1;
+  for (int a = 0; a < axis; ++a) lstride *= g.m;
+  const int64_t nlines = (int64_t)planes * (g.np / g.m);
+  const unsigned blocks = (unsigned)((nlines + COLS - 1) / COLS);
+  const Tc hs = (Tc)(0.5 * std::sqrt(2.0 / (g.m + 1)));
+  cudaError_t e;
+  if (divide) {
+    e = cudaFuncSetAttribute(fst4_kernel<Tc, N1, N2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fst4_kernel<Tc, N1, N2, true><<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs, lamK,
+                                                                   rmass, sigma);
+  } else {
+    e = cudaFuncSetAttribute(fst4_kernel<Tc, N1, N2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fst4_kernel<Tc, N1, N2, false><<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs,
+                                                                    nullptr, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename Tc>
+bool fst_fast_supported(int m) {
+  const int L = 2 * (m + 1);
+  return (L & (L - 1)) == 0 && L >= 4 && L <= (sizeof(Tc) == 4 ? 1024 : 512);
+}
+
+template <typename Tc>
+cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool divide,
+                            const typename Cx<Tc>::t* tw, const Tc* lamK, const Tc* rmass,
+                            const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
+                            typename Cx<Tc>::t* out) {
+  const int Lfft = 2 * (g.m + 1);
+  const double tot = (double)planes * (double)g.np;
+  const double cs = sizeof(typename Cx<Tc>::t);
+  const int kc = divide ? KC_FST_DIVIDE : KC_FST_AXIS;
+  const double lg = std::log2((double)Lfft);
+  // per line: (divide ? 2 : 1) complex FFTs of length 2(m+1)
+  const double flops = (divide ? 2.0 : 1.0) * (tot / g.m) * 5.0 * Lfft * lg;
+  L.begin(kc);
+  cudaError_t e;
+  switch (Lfft) {
+#define PCOPT_FST_CASE(LL, A, B) \
+  case LL: e = fst4<Tc, A, B>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out); break;
+    PCOPT_FST_CASE(4, 2, 2)
+    PCOPT_FST_CASE(8, 4, 2)
+    PCOPT_FST_CASE(16, 4, 4)
+    PCOPT_FST_CASE(32, 8, 4)
+    PCOPT_FST_CASE(64, 8, 8)
+    PCOPT_FST_CASE(128, 16, 8)
+    PCOPT_FST_CASE(256, 16, 16)
+    PCOPT_FST_CASE(512, 32, 16)
+#undef PCOPT_FST_CASE
+    case 1024:
+      if constexpr (sizeof(Tc) == 4) {
+        e = fst4<Tc, 32, 32>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out);
+        break;
+      } else {
+        return cudaErrorNotSupported;
+      }
+    default:
+      return cudaErrorNotSupported;
+  }
+  if (e != cudaSuccess) return e;
+  return L.end(kc, 2.0 * tot * cs, flops);
+}
+
+template bool fst_fast_supported<float>(int);
+template bool fst_fast_supported<double>(int);
+template cudaError_t launch_fst_fast<float>(Launch&, const Grid&, int, int, bool, const float2*, const float*,
+                                            const float*, const float2*, const float2*, float2*);
+template cudaError_t launch_fst_fast<double>(Launch&, const Grid&, int, int, bool, const double2*, const double*,
+                                             const double*, const double2*, const double2*, double2*);
+
+}  // namespace pcopt

@@ -19,11 +19,6 @@ namespace {
 
 constexpr int kPlaneChunk = 8;  // default planes per CTA
 
-template <typename Tc>
-__device__ __forceinline__ typename Cx<Tc>::t inv_diag(typename Cx<Tc>::t sig, Tc dg) {
-  return cinv(cmk<Tc>(sig.x + dg, sig.y));
-}
-
 // 1 / (sigma + d); FP32 with the hardware-approximate divide (2 ulp, far inside what
 // a smoother needs), FP64 exact
 __device__ __forceinline__ float2 inv_shift_c(float2 sig, float d) {
@@ -76,12 +71,15 @@ __global__ void fst_axis_kernel(const typename Cx<Tc>::t* __restrict__ in, typen
 
 template <typename Tc>
 __global__ void fst_divide_kernel(typename Cx<Tc>::t* __restrict__ buf, const Tc* __restrict__ lamK,
-                                  const typename Cx<Tc>::t* __restrict__ sigma, int64_t np, int planes) {
+                                  const Tc* __restrict__ rmass, const typename Cx<Tc>::t* __restrict__ sigma,
+                                  int64_t np, int planes) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= np * planes) return;
   const int64_t p = e / np;
   const int64_t s = e - p * np;
-  buf[e] = cmul(buf[e], inv_diag<Tc>(sigma[p], lamK[s]));
+  typename Cx<Tc>::t v = buf[e];
+  if (rmass) v = cscale(v, rmass[s]);  // finite elements: 1 / eigenvalue of M
+  buf[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
 }
 
 // ------------------------------------------------------------------- multigrid
@@ -343,12 +341,13 @@ cudaError_t launch_fst_axis(Launch& L, const Grid& g, int planes, int axis, cons
 }
 
 template <typename Tc>
-cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK, const typename Cx<Tc>::t* sigma,
+cudaError_t launch_fst_divide(Launch& L, const Grid& g, int planes, const Tc* lamK, const Tc* rmass,
+                              const typename Cx<Tc>::t* sigma,
                               typename Cx<Tc>::t* buf) {
   const int64_t tot = g.np * planes;
   const double cs = sizeof(typename Cx<Tc>::t);
   L.begin(KC_FST_DIVIDE);
-  fst_divide_kernel<Tc><<<(unsigned)((tot + 255) / 256), 256, 0, L.stream>>>(buf, lamK, sigma, g.np, planes);
+  fst_divide_kernel<Tc><<<(unsigned)((tot + 255) / 256), 256, 0, L.stream>>>(buf, lamK, rmass, sigma, g.np, planes);
   return L.end(KC_FST_DIVIDE, 2.0 * tot * cs, 12.0 * tot);
 }
 
@@ -432,7 +431,7 @@ cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const type
 #define PCOPT_INST_FST(Tc)                                                                                   \
   template cudaError_t launch_fst_axis<Tc>(Launch&, const Grid&, int, int, const Tc*, const Cx<Tc>::t*,          \
                                            Cx<Tc>::t*);                                                             \
-  template cudaError_t launch_fst_divide<Tc>(Launch&, const Grid&, int, const Tc*, const Cx<Tc>::t*, Cx<Tc>::t*);
+  template cudaError_t launch_fst_divide<Tc>(Launch&, const Grid&, int, const Tc*, const Tc*, const Cx<Tc>::t*, Cx<Tc>::t*);
 #define PCOPT_INST_MG(Tc, TU)                                                                                    \
   template cudaError_t launch_mg_smooth<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&, const Cx<Tc>::t*, \
                                                 const Cx<Tc>::t*, TU*);                                             \

@@ -17,6 +17,7 @@ _SPATIAL = {"auto": capi.PC_SPATIAL_AUTO, "fst": capi.PC_SPATIAL_FST, "mg": capi
 _PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": capi.PC_PREC_MIXED_FP32,
          "bf16s": capi.PC_PREC_MIXED_BF16S}
 _MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
+_SPACE = {"fd": capi.PC_SPACE_FD, "fe": capi.PC_SPACE_FE}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -36,8 +37,10 @@ class Solver:
 
     def __init__(self, dim: int, m1: int, n: int, T: float, gamma: float, eps: float,
                  a_nodes: np.ndarray | None = None, spatial: str = "auto", precision: str = "fp64",
-                 max_iter: int = 60, tiles: str | dict | None = "table"):
-        """tiles: "table" applies the stored autotune table's entry for this shape
+                 max_iter: int = 60, tiles: str | dict | None = "table", space: str = "fd"):
+        """space: "fd" finite differences (M = I) or "fe" bilinear / trilinear finite
+        elements (mass matrix M; constant a, sine-transform solves).
+        tiles: "table" applies the stored autotune table's entry for this shape
         (if any), "auto" runs the autotuner now, a dict sets the shapes, None keeps
         the built-in defaults."""
         self.lib = capi.load()
@@ -46,7 +49,8 @@ class Solver:
         self.dim, self.m1, self.n = dim, m1, n
         self.T, self.gamma, self.eps = T, gamma, eps
         self.max_iter = max_iter
-        prm = capi.pc_params(dim, m1, n, T, gamma, eps, _SPATIAL[spatial], _PREC[precision], max_iter)
+        prm = capi.pc_params(dim, m1, n, T, gamma, eps, _SPATIAL[spatial], _PREC[precision], max_iter,
+                             _SPACE[space])
         a_ptr = None
         if a_nodes is not None:
             self._a = np.ascontiguousarray(a_nodes, dtype=np.float64)
@@ -61,8 +65,9 @@ class Solver:
         self.tau = T / (n + 1)
         self.precision = precision
         self.spatial = spatial
+        self.space = space
         if tiles == "table":
-            entry = tuning.lookup(dim, m1, n, precision, spatial)
+            entry = tuning.lookup(dim, m1, n, precision, spatial) if space == "fd" else None
             if entry:
                 self.set_tiles(**entry)
         elif tiles == "auto":

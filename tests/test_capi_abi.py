@@ -52,6 +52,7 @@ def test_status_strings_and_argument_errors_without_gpu():
         capi.pc_params(2, 6, 8, 1.0, 1e-2, 0.5, 2, 0, 10),     # MG needs 2^k - 1
         capi.pc_params(2, 7, 8, -1.0, 1e-2, 0.5, 0, 0, 10),    # T
         capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 0),      # max_iter
+        capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10, 2),  # space
     ]
     for p in bad:
         assert l.pc_setup(ctypes.byref(p), None, None, ctypes.byref(h)) == capi.PC_ERR_ARG
@@ -65,4 +66,11 @@ def test_status_strings_and_argument_errors_without_gpu():
         assert l.pc_setup(ctypes.byref(p), a.ctypes.data_as(ctypes.c_void_p), None,
                           ctypes.byref(h)) == capi.PC_ERR_ARG, (i, j, v)
         assert b"boundary" in l.pc_last_error()
+    # finite elements: constant coefficient with sine-transform solves only
+    a = np.ones((9, 9))
+    a[4, 4] = 2.0
+    for p, a_ptr in [(capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 2, 0, 10, 1), None),
+                     (capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10, 1), a.ctypes.data_as(ctypes.c_void_p))]:
+        assert l.pc_setup(ctypes.byref(p), a_ptr, None, ctypes.byref(h)) == capi.PC_ERR_UNSUPPORTED
+        assert b"finite elements" in l.pc_last_error()
     assert l.pc_destroy(None) == capi.PC_OK

@@ -87,7 +87,10 @@ def test_build_rhs_matches_oracle():
 PRECOND_CASES = [(2, 31, 32, "const", "fst"), (2, 20, 16, "const", "fst"), (2, 15, 16, "var", "mg"),
                  (2, 63, 8, "var", "mg"), (3, 7, 8, "var", "mg"), (3, 5, 4, "const", "fst"),
                  (2, 1, 2, "var", "mg"), (2, 3, 1, "var", "mg"), (2, 7, 128, "var", "mg"),
-                 (2, 31, 256, "var", "mg")]
+                 (2, 31, 256, "var", "mg"),
+                 # sine transforms by FFT for every power-of-two length 2(m1+1) from 4 to 512
+                 (2, 1, 4, "const", "fst"), (2, 3, 2, "const", "fst"), (2, 63, 16, "const", "fst"),
+                 (2, 127, 8, "const", "fst"), (3, 15, 4, "const", "fst"), (2, 255, 4, "const", "fst")]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
