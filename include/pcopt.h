@@ -131,7 +131,7 @@ int pc_matvec(pc_handle* h, const double* x, double* y, void* stream);
  * with its FP32 basis Z.  Evaluated in double-float arithmetic on the FP32 units
  * (each FP64 coefficient split into two floats, FMA error terms, TwoSum
  * accumulation); relative error of order 2^-46 of the largest term; FP64 output.
- * Finite-element handles evaluate it in FP64 arithmetic.
+ * Finite-element handles use the same double-float scheme on the element stencils.
  * x: device, 2*n*ms FP32; y: device, 2*n*ms FP64. */
 int pc_matvec_f32(pc_handle* h, const float* x, double* y, void* stream);
 

@@ -14,6 +14,8 @@
 // In the all-at-once product these columns come from the warp's neighbouring
 // lanes (shuffles); a warp spans 32 consecutive x1 columns and writes the 30
 // inner ones.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pcopt {
@@ -115,6 +117,141 @@ __global__ void __launch_bounds__(256) matvec_fe_kernel(const Tin* __restrict__ 
   if (out) y1[(int64_t)(j1 - 1) * ms + s] = fma(wM, fma(-sg, m2n, pm), sg * tKw * pk);
 }
 
+// ---------------------------------------------------------------------------
+// The same product for an FP32 input z (the flexible-GMRES basis) in double-float
+// arithmetic on the FP32 units: every quantity is an unevaluated sum hi + lo of two
+// floats (about 48 significant bits).  The stencil weights are small integers, so
+// the column sums and x1 combinations are exact TwoSum chains of scaled inputs; the
+// FP64 scale factors (alpha, wM, tau wK) are split into float pairs and multiplied
+// with an FMA error term.  Only the final hi + lo becomes an FP64 value.  GB300's
+// FP64 unit bounds the FP64 kernel above; this one runs on the FP32 pipes.
+struct DF {
+  float hi, lo;
+};
+
+// a + b = s + err exactly (Knuth); the _rn intrinsics keep each operation separately
+// rounded (no FMA contraction, which would break the exactness)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// hi + lo renormalised so that |lo| <= ulp(hi)/2 (needs |hi| >= |lo|)
+__device__ __forceinline__ DF renorm(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return DF{s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_scale2(DF a, float p2) { return DF{a.hi * p2, a.lo * p2}; }  // exact: p2 = 2^k
+// c * v for a split FP64 constant c
+__device__ __forceinline__ DF df_mul(DF c, DF v) {
+  const float p = __fmul_rn(c.hi, v.hi);
+  const float e = __fadd_rn(fmaf(c.hi, v.hi, -p), __fadd_rn(__fmul_rn(c.hi, v.lo), __fmul_rn(c.lo, v.hi)));
+  return renorm(p, e);
+}
+__device__ __forceinline__ double df_to_f64(DF a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+__device__ __forceinline__ DF df_shfl_up(DF a) {
+  return DF{__shfl_up_sync(kFull, a.hi, 1), __shfl_up_sync(kFull, a.lo, 1)};
+}
+__device__ __forceinline__ DF df_shfl_down(DF a) {
+  return DF{__shfl_down_sync(kFull, a.hi, 1), __shfl_down_sync(kFull, a.lo, 1)};
+}
+
+// column sums q = S(x)S[..] v and r = (D(x)S + S(x)D)[..] v at p from exact float inputs
+template <int DIM>
+__device__ __forceinline__ void fe_column_df(const float* __restrict__ p, int64_t m, int64_t mm, bool e2m, bool e2p,
+                                             bool e3m, bool e3p, DF& q, DF& r) {
+  const float x0 = p[0];
+  const float xs = e2m ? p[-m] : 0.0f, xn = e2p ? p[m] : 0.0f;
+  if (DIM == 2) {
+    const DF s = two_sum(xs, xn);                          // xs + xn
+    const DF q0 = two_sum(s.hi, 4.0f * x0);                // + 4 x0
+    q = renorm(q0.hi, __fadd_rn(q0.lo, s.lo));
+    const DF r0 = two_sum(2.0f * x0, -s.hi);               // 2 x0 - xs - xn
+    r = renorm(r0.hi, __fsub_rn(r0.lo, s.lo));
+  } else {
+    const float xb = e3m ? p[-mm] : 0.0f, xt = e3p ? p[mm] : 0.0f;
+    const float c1 = e2m && e3m ? p[-m - mm] : 0.0f, c2 = e2p && e3m ? p[m - mm] : 0.0f;
+    const float c3 = e2m && e3p ? p[-m + mm] : 0.0f, c4 = e2p && e3p ? p[m + mm] : 0.0f;
+    // edges e and corners c as exact double-float sums
+    const DF e = df_add(two_sum(xs, xn), two_sum(xb, xt));
+    const DF c = df_add(two_sum(c1, c2), two_sum(c3, c4));
+    // q = 16 x0 + 4 e + c,  r = 16 x0 - 2 (c + e)
+    const DF x16{16.0f * x0, 0.0f};
+    q = df_add(df_add(x16, df_scale2(e, 4.0f)), c);
+    r = df_add(x16, df_scale2(df_add(c, e), -2.0f));
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) matvec_fe_df_kernel(const float* __restrict__ x, double* __restrict__ y, int m,
+                                                           int64_t ms, int64_t rows, int segs, int n, int tj,
+                                                           DF alpha, DF wM, DF tKw, size_t xstride, size_t ystride,
+                                                           const int* __restrict__ jdev) {
+  if (jdev) {
+    x += (size_t)(*jdev) * xstride;
+    y += (size_t)(*jdev + 1) * ystride;
+  }
+  const int lane = threadIdx.x & 31;
+  const int seg = (int)(blockIdx.x % (unsigned)segs);
+  const int64_t row = (int64_t)(blockIdx.x / (unsigned)segs) * kFeRowsPerCta + (threadIdx.x >> 5);
+  if (row >= rows) return;  // whole warps leave together
+  const int j0 = blockIdx.y * tj;
+  const int j1 = min(n, j0 + tj);
+  const int i1 = seg * kFeOut - 1 + lane;
+  const bool has = i1 >= 0 && i1 < m;
+  const bool out = has && lane >= 1 && lane <= kFeOut;
+  const int i2 = (int)(DIM == 2 ? row : row % m);
+  const int i3 = (int)(DIM == 3 ? row / m : 0);
+  const bool e2m = i2 > 0, e2p = i2 < m - 1;
+  const bool e3m = DIM == 3 && i3 > 0, e3p = DIM == 3 && i3 < m - 1;
+  const int64_t mm = (int64_t)m * m;
+  const int64_t s = row * m + (has ? i1 : 0);
+  const float* x1 = x;
+  const float* x2 = x + (int64_t)n * ms;
+  double* y1 = y;
+  double* y2 = y + (int64_t)n * ms;
+  const DF zero{0.0f, 0.0f};
+
+  auto stencils = [&](const float* v, int j, DF& mt, DF& kt) {
+    DF q = zero, r = zero;
+    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, r);
+    const DF ql = df_shfl_up(q), qr = df_shfl_down(q), rl = df_shfl_up(r), rr = df_shfl_down(r);
+    const DF sq = df_add(ql, qr);
+    mt = df_add(df_scale2(q, 4.0f), sq);
+    kt = df_add(df_add(df_scale2(r, 4.0f), df_add(rl, rr)), df_add(df_scale2(q, 2.0f), df_neg(sq)));
+  };
+  auto mass = [&](const float* v, int j) -> DF {
+    DF q = zero, r = zero;
+    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, r);
+    return df_add(df_scale2(q, 4.0f), df_add(df_shfl_up(q), df_shfl_down(q)));
+  };
+
+  // y1_j = wM (alpha m1_j + m2_j - m2_{j+1}) + tKw k2_j,  y2_j = wM (alpha m2_j - m1_j + m1_{j-1}) - tKw k1_j
+  DF m1p = j0 > 0 ? mass(x1, j0 - 1) : zero;
+  DF pm = zero, pk = zero;  // alpha m1 + m2 and tKw k2 of the previous time block
+  for (int j = j0; j < j1; ++j) {
+    DF m1, k1, m2, k2;
+    stencils(x1, j, m1, k1);
+    stencils(x2, j, m2, k2);
+    const int64_t idx = (int64_t)j * ms + s;
+    if (out) {
+      if (j > j0) y1[idx - ms] = df_to_f64(df_add(df_mul(wM, df_add(pm, df_neg(m2))), pk));
+      const DF t = df_add(df_mul(alpha, m2), df_add(m1p, df_neg(m1)));
+      y2[idx] = df_to_f64(df_add(df_mul(wM, t), df_neg(df_mul(tKw, k1))));
+    }
+    pm = df_add(df_mul(alpha, m1), m2);
+    pk = df_mul(tKw, k2);
+    m1p = m1;
+  }
+  const DF m2n = j1 < n ? mass(x2, j1) : zero;
+  if (out) y1[(int64_t)(j1 - 1) * ms + s] = df_to_f64(df_add(df_mul(wM, df_add(pm, df_neg(m2n))), pk));
+}
+
 // out_p = cM (S(x)S..) in_p + cK (K stencil) in_p + beta out_p for every plane p
 // (mass / stiffness products of single fields: right-hand side, end-point solves)
 template <int DIM>
@@ -170,6 +307,21 @@ cudaError_t launch_matvec_fe(Launch& L, const Grid& g, int n, double alpha, FeSc
   const double flops = pts * (g.dim == 2 ? 48.0 : 64.0);
   const double tKw = tau * fs.wK;
   L.begin(KC_MATVEC);
+  if constexpr (std::is_same<Tin, float>::value) {
+    if (!transpose) {  // the flexible-GMRES product: double-float on the FP32 units
+      auto split = [](double v) {
+        const float hi = (float)v;
+        return DF{hi, (float)(v - (double)hi)};
+      };
+      if (g.dim == 2)
+        matvec_fe_df_kernel<2><<<grid, 256, 0, L.stream>>>(x, y, g.m, g.np, rows, segs, n, tj, split(alpha),
+                                                           split(fs.wM), split(tKw), xstride, ystride, jdev);
+      else
+        matvec_fe_df_kernel<3><<<grid, 256, 0, L.stream>>>(x, y, g.m, g.np, rows, segs, n, tj, split(alpha),
+                                                           split(fs.wM), split(tKw), xstride, ystride, jdev);
+      return L.end(KC_MATVEC, jdev ? 0.0 : bytes, jdev ? 0.0 : flops);
+    }
+  }
 #define PCOPT_FE_MV(D, TR)                                                                                    \
   matvec_fe_kernel<Tin, D, TR><<<grid, 256, 0, L.stream>>>(x, y, g.m, g.np, rows, segs, n, tj, alpha, fs.wM, \
                                                            tKw, xstride, ystride, jdev)

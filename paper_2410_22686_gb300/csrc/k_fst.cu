@@ -29,8 +29,15 @@ namespace pcopt {
 
 namespace {
 
+// Exchange layout of the four-step FFT: row k2 (N1 entries of COLS lines) padded by
+// COLS entries, so that the rows a warp reads in step (C) fall on different banks.
+template <int N1, int COLS>
+__device__ __forceinline__ int xidx(int k2, int j1, int c) {
+  return (k2 * (N1 + 1) + j1) * COLS + c;
+}
+
 // One DST-I of every line of the tile in `sm` ([j][c], j < m, line index c fastest),
-// in place.  Ends with a barrier.
+// in place.  Ends with a barrier.  `sm` holds at least N2 (N1 + 1) COLS entries.
 template <typename Tc, int N1, int N2>
 __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* __restrict__ tw, int m,
                                          Tc half_scale, int r, int c) {
@@ -57,22 +64,54 @@ __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename 
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
     const C y = (k2 == 0 || r == 0) ? x[k2] : cmul(tw[r * k2], x[k2]);
-    sm[(k2 * N1 + r) * COLS + c] = y;
+    sm[xidx<N1, COLS>(k2, r, c)] = y;
   }
   __syncthreads();
-  // (C) row k2 = r (< N2): N1-point DFT over j1, Y[k2 + N2 k1]
-  C y[N1];
-  if (r < N2) {
+  // (C) N1-point DFT over j1 for each k2, Y[k2 + N2 k1]; written as X_k = sqrt(2/N) (i/2) Y_k
+  auto put = [&](int k, C y) {
+    if (k >= 1 && k <= m) sm[(k - 1) * COLS + c] = cmk<Tc>(-y.y * half_scale, y.x * half_scale);
+  };
+  if constexpr (N1 == 2 * N2 && sizeof(Tc) == 4) {
+    // every thread row works: row r < N2 transforms the even j1 of k2 = r, row r + N2 the
+    // odd ones (N2-point DFTs), and the two halves meet in one radix-2 step.  (FP32 only:
+    // it halves the registers for four CTAs per SM; the FP64 kernel is bound by its
+    // arithmetic, where the extra exchange costs more than the occupancy gains.)
+    constexpr int H = N1 / 2;
+    const int k2 = r < N2 ? r : r - N2;
+    const int b = r < N2 ? 0 : 1;
+    C y[H];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) y[j1] = sm[(r * N1 + j1) * COLS + c];
-  }
-  __syncthreads();
-  if (r < N2) {
-    reg_fft<N1, false>(y, tw, N2);
+    for (int a = 0; a < H; ++a) y[a] = sm[xidx<N1, COLS>(k2, 2 * a + b, c)];
+    __syncthreads();
+    reg_fft<H, false>(y, tw, 2 * N2);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      const int k = r + N2 * k1;  // X_k = sqrt(2/N) (i/2) Y_k for k = 1..m
-      if (k >= 1 && k <= m) sm[(k - 1) * COLS + c] = cmk<Tc>(-y[k1].y * half_scale, y[k1].x * half_scale);
+    for (int q = 0; q < H; ++q) {
+      C v = y[q];
+      if (b == 1 && q != 0) v = cmul(tw[q * N2], v);  // w_{N1}^{q} = exp(-2 pi i q / N1)
+      sm[xidx<N1, COLS>(k2, b * H + q, c)] = v;
+    }
+    __syncthreads();
+    C e[H], o[H];
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      e[q] = sm[xidx<N1, COLS>(k2, q, c)];
+      o[q] = sm[xidx<N1, COLS>(k2, H + q, c)];
+    }
+    __syncthreads();
+    // row b = 0 writes k1 = q (even + odd), row b = 1 writes k1 = q + H (even - odd)
+#pragma unroll
+    for (int q = 0; q < H; ++q) put(k2 + N2 * (q + b * H), b == 0 ? e[q] + o[q] : e[q] - o[q]);
+  } else {
+    C y[N1];
+    if (r < N2) {
+#pragma unroll
+      for (int j1 = 0; j1 < N1; ++j1) y[j1] = sm[xidx<N1, COLS>(r, j1, c)];
+    }
+    __syncthreads();
+    if (r < N2) {
+      reg_fft<N1, false>(y, tw, N2);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) put(r + N2 * k1, y[k1]);
     }
   }
   __syncthreads();
@@ -83,7 +122,7 @@ __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename 
 // Lines: plane p = line / (np / m); inside the plane, a line along `axis` starts at
 // outer * m * lstride + inner with lstride = m^axis, inner < lstride.
 template <typename Tc, int N1, int N2, bool DIVIDE>
-__global__ void __launch_bounds__(256) fst4_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2) : 1) fst4_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
                                                    const typename Cx<Tc>::t* __restrict__ tw, int m, int64_t np,
                                                    int64_t lstride, int64_t nlines, Tc half_scale,
                                                    const Tc* __restrict__ lamK, const Tc* __restrict__ rmass,
@@ -142,7 +181,7 @@ cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, co
                  const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
                  typename Cx<Tc>::t* out) {
   constexpr int COLS = 256 / N1;
-  const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
+  const size_t smem = (size_t)(N1 + 1) * N2 * COLS * sizeof(typename Cx<Tc>::t);
   int64_t lstride = 1;
   for (int a = 0; a < axis; ++a) lstride *= g.m;
   const int64_t nlines = (int64_t)planes * (g.np / g.m);

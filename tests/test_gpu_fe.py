@@ -55,7 +55,7 @@ def test_fe_matvec_and_transpose_match_oracle(d, m1, n, tj):
     x = S.random_vector((2, n) + (m1,) * d, 7)
     assert _rel(sol.matvec(_dev(x)).cpu().numpy(), fe.apply_A(x, M, K, tau, alpha)) <= 1e-12
     assert _rel(sol.matvec(_dev(x), transpose=True).cpu().numpy(), fe.apply_AT(x, M, K, tau, alpha)) <= 1e-12
-    # FP32 input (the flexible-GMRES basis): FP64 arithmetic on the exact float values
+    # FP32 input (the flexible-GMRES basis; double-float arithmetic, transpose in FP64)
     x32 = x.astype(np.float32)
     y32 = sol.matvec_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
     assert _rel(y32, fe.apply_A(x32.astype(np.float64), M, K, tau, alpha)) <= 1e-12
