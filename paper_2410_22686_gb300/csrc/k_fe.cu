@@ -120,11 +120,16 @@ __global__ void __launch_bounds__(256) matvec_fe_kernel(const Tin* __restrict__ 
 // ---------------------------------------------------------------------------
 // The same product for an FP32 input z (the flexible-GMRES basis) in double-float
 // arithmetic on the FP32 units: every quantity is an unevaluated sum hi + lo of two
-// floats (about 48 significant bits).  The stencil weights are small integers, so
-// the column sums and x1 combinations are exact TwoSum chains of scaled inputs; the
-// FP64 scale factors (alpha, wM, tau wK) are split into float pairs and multiplied
-// with an FMA error term.  Only the final hi + lo becomes an FP64 value.  GB300's
-// FP64 unit bounds the FP64 kernel above; this one runs on the FP32 pipes.
+// floats.  The stencil weights are small integers, so the column and row sums are
+// exact TwoSum chains of scaled inputs; the FP64 scale factors (alpha, wM, tau wK)
+// are split into float pairs and multiplied with an FMA error term.  Sums are not
+// renormalised: every rounding error lands in `lo`, whose own rounding is then of
+// order 2^-48 of the terms, and only the final hi + lo becomes an FP64 value.
+// GB300's FP64 unit bounds the FP64 kernel above; this one runs on the FP32 pipes.
+//
+// The x1 direction uses D = 6 I - S:  with q the column sums as above and u the
+// cross sums u = (I(x)S + S(x)I) v in the x2-x3 plane (2D: u = v),
+//   M v / wM = S1 q,   K v / wK = 6 (q + S1 u) - dim S1 q.
 struct DF {
   float hi, lo;
 };
@@ -136,22 +141,16 @@ __device__ __forceinline__ DF two_sum(float a, float b) {
   const float bb = __fsub_rn(s, a);
   return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
-// hi + lo renormalised so that |lo| <= ulp(hi)/2 (needs |hi| >= |lo|)
-__device__ __forceinline__ DF renorm(float hi, float lo) {
-  const float s = __fadd_rn(hi, lo);
-  return DF{s, __fsub_rn(lo, __fsub_rn(s, hi))};
-}
 __device__ __forceinline__ DF df_add(DF a, DF b) {
   const DF s = two_sum(a.hi, b.hi);
-  return renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
 __device__ __forceinline__ DF df_scale2(DF a, float p2) { return DF{a.hi * p2, a.lo * p2}; }  // exact: p2 = 2^k
 // c * v for a split FP64 constant c
 __device__ __forceinline__ DF df_mul(DF c, DF v) {
   const float p = __fmul_rn(c.hi, v.hi);
-  const float e = __fadd_rn(fmaf(c.hi, v.hi, -p), __fadd_rn(__fmul_rn(c.hi, v.lo), __fmul_rn(c.lo, v.hi)));
-  return renorm(p, e);
+  return DF{p, __fadd_rn(fmaf(c.hi, v.hi, -p), __fadd_rn(__fmul_rn(c.hi, v.lo), __fmul_rn(c.lo, v.hi)))};
 }
 __device__ __forceinline__ double df_to_f64(DF a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
 __device__ __forceinline__ DF df_shfl_up(DF a) {
@@ -160,30 +159,30 @@ __device__ __forceinline__ DF df_shfl_up(DF a) {
 __device__ __forceinline__ DF df_shfl_down(DF a) {
   return DF{__shfl_down_sync(kFull, a.hi, 1), __shfl_down_sync(kFull, a.lo, 1)};
 }
+// a + b + 4 c from exact floats (S applied to a neighbour pair and a centre)
+__device__ __forceinline__ DF s_sum(float a, float b, float c) {
+  const DF t = two_sum(a, b);
+  const DF q = two_sum(t.hi, 4.0f * c);
+  return DF{q.hi, __fadd_rn(q.lo, t.lo)};
+}
 
-// column sums q = S(x)S[..] v and r = (D(x)S + S(x)D)[..] v at p from exact float inputs
+// column sums at p: q = S(x)S[..] v, and (3D) u = (I(x)S + S(x)I) v; 2D returns u = v
 template <int DIM>
 __device__ __forceinline__ void fe_column_df(const float* __restrict__ p, int64_t m, int64_t mm, bool e2m, bool e2p,
-                                             bool e3m, bool e3p, DF& q, DF& r) {
+                                             bool e3m, bool e3p, DF& q, DF& u) {
   const float x0 = p[0];
   const float xs = e2m ? p[-m] : 0.0f, xn = e2p ? p[m] : 0.0f;
   if (DIM == 2) {
-    const DF s = two_sum(xs, xn);                          // xs + xn
-    const DF q0 = two_sum(s.hi, 4.0f * x0);                // + 4 x0
-    q = renorm(q0.hi, __fadd_rn(q0.lo, s.lo));
-    const DF r0 = two_sum(2.0f * x0, -s.hi);               // 2 x0 - xs - xn
-    r = renorm(r0.hi, __fsub_rn(r0.lo, s.lo));
+    q = s_sum(xs, xn, x0);
+    u = DF{x0, 0.0f};
   } else {
     const float xb = e3m ? p[-mm] : 0.0f, xt = e3p ? p[mm] : 0.0f;
     const float c1 = e2m && e3m ? p[-m - mm] : 0.0f, c2 = e2p && e3m ? p[m - mm] : 0.0f;
     const float c3 = e2m && e3p ? p[-m + mm] : 0.0f, c4 = e2p && e3p ? p[m + mm] : 0.0f;
-    // edges e and corners c as exact double-float sums
-    const DF e = df_add(two_sum(xs, xn), two_sum(xb, xt));
-    const DF c = df_add(two_sum(c1, c2), two_sum(c3, c4));
-    // q = 16 x0 + 4 e + c,  r = 16 x0 - 2 (c + e)
-    const DF x16{16.0f * x0, 0.0f};
-    q = df_add(df_add(x16, df_scale2(e, 4.0f)), c);
-    r = df_add(x16, df_scale2(df_add(c, e), -2.0f));
+    const DF e = df_add(two_sum(xs, xn), two_sum(xb, xt));   // edges
+    const DF c = df_add(two_sum(c1, c2), two_sum(c3, c4));   // corners
+    q = df_add(df_add(DF{16.0f * x0, 0.0f}, df_scale2(e, 4.0f)), c);  // 16 x0 + 4 e + c
+    u = df_add(e, DF{8.0f * x0, 0.0f});                            // 8 x0 + e
   }
 }
 
@@ -217,18 +216,27 @@ __global__ void __launch_bounds__(256) matvec_fe_df_kernel(const float* __restri
   double* y2 = y + (int64_t)n * ms;
   const DF zero{0.0f, 0.0f};
 
+  // unscaled M v (mt) and K v (kt) of time block j
   auto stencils = [&](const float* v, int j, DF& mt, DF& kt) {
-    DF q = zero, r = zero;
-    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, r);
-    const DF ql = df_shfl_up(q), qr = df_shfl_down(q), rl = df_shfl_up(r), rr = df_shfl_down(r);
-    const DF sq = df_add(ql, qr);
-    mt = df_add(df_scale2(q, 4.0f), sq);
-    kt = df_add(df_add(df_scale2(r, 4.0f), df_add(rl, rr)), df_add(df_scale2(q, 2.0f), df_neg(sq)));
+    DF q = zero, u = zero;
+    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, u);
+    mt = df_add(df_add(df_shfl_up(q), df_shfl_down(q)), df_scale2(q, 4.0f));  // S1 q
+    DF su;                                                                   // S1 u
+    if (DIM == 2) {
+      su = s_sum(__shfl_up_sync(kFull, u.hi, 1), __shfl_down_sync(kFull, u.hi, 1), u.hi);
+    } else {
+      su = df_add(df_add(df_shfl_up(u), df_shfl_down(u)), df_scale2(u, 4.0f));
+    }
+    const DF w = df_add(q, su);
+    // 6 w - DIM mt = 4 w + 2 w - 2 mt (- mt in 3D)
+    DF k = df_sub(df_add(df_scale2(w, 4.0f), df_scale2(w, 2.0f)), df_scale2(mt, 2.0f));
+    if (DIM == 3) k = df_sub(k, mt);
+    kt = k;
   };
   auto mass = [&](const float* v, int j) -> DF {
-    DF q = zero, r = zero;
-    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, r);
-    return df_add(df_scale2(q, 4.0f), df_add(df_shfl_up(q), df_shfl_down(q)));
+    DF q = zero, u = zero;
+    if (has) fe_column_df<DIM>(v + (int64_t)j * ms + s, m, mm, e2m, e2p, e3m, e3p, q, u);
+    return df_add(df_add(df_shfl_up(q), df_shfl_down(q)), df_scale2(q, 4.0f));
   };
 
   // y1_j = wM (alpha m1_j + m2_j - m2_{j+1}) + tKw k2_j,  y2_j = wM (alpha m2_j - m1_j + m1_{j-1}) - tKw k1_j
@@ -240,16 +248,16 @@ __global__ void __launch_bounds__(256) matvec_fe_df_kernel(const float* __restri
     stencils(x2, j, m2, k2);
     const int64_t idx = (int64_t)j * ms + s;
     if (out) {
-      if (j > j0) y1[idx - ms] = df_to_f64(df_add(df_mul(wM, df_add(pm, df_neg(m2))), pk));
-      const DF t = df_add(df_mul(alpha, m2), df_add(m1p, df_neg(m1)));
-      y2[idx] = df_to_f64(df_add(df_mul(wM, t), df_neg(df_mul(tKw, k1))));
+      if (j > j0) y1[idx - ms] = df_to_f64(df_add(df_mul(wM, df_sub(pm, m2)), pk));
+      const DF t = df_add(df_mul(alpha, m2), df_sub(m1p, m1));
+      y2[idx] = df_to_f64(df_sub(df_mul(wM, t), df_mul(tKw, k1)));
     }
     pm = df_add(df_mul(alpha, m1), m2);
     pk = df_mul(tKw, k2);
     m1p = m1;
   }
   const DF m2n = j1 < n ? mass(x2, j1) : zero;
-  if (out) y1[(int64_t)(j1 - 1) * ms + s] = df_to_f64(df_add(df_mul(wM, df_add(pm, df_neg(m2n))), pk));
+  if (out) y1[(int64_t)(j1 - 1) * ms + s] = df_to_f64(df_add(df_mul(wM, df_sub(pm, m2n)), pk));
 }
 
 // out_p = cM (S(x)S..) in_p + cK (K stencil) in_p + beta out_p for every plane p

@@ -163,13 +163,16 @@ def test_fe_unsupported_requests_fail_loudly():
 
 def test_fe_full_size_operators_match_oracle():
     """255^2 grid, n = 256 (the size the finite-element solve is timed on): the whole
-    matvec output and the FP32 preconditioner against the oracle."""
+    product (FP64 and FP32 input) and the FP32 preconditioner against the oracle."""
     d, m1, n, gamma, eps = 2, 255, 256, 1e-2, 0.5
     sol = _solver(d, m1, n, precision="mixed", gamma=gamma, eps=eps)
     M, K = fe.fe_matrices(m1, d)
     tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
     x = S.random_vector((2, n) + (m1,) * d, 21)
     assert _rel(sol.matvec(_dev(x)).cpu().numpy(), fe.apply_A(x, M, K, tau, alpha)) <= 1e-12
+    x32 = x.astype(np.float32)
+    y32 = sol.matvec_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert _rel(y32, fe.apply_A(x32.astype(np.float64), M, K, tau, alpha)) <= 1e-12
     w = sol.apply_precond(_dev(x)).cpu().numpy()
     ref = opc.apply_Peps_inv(x, n, alpha, eps, fe.FSTSpatialSolverFE(m1, d, tau))
     assert _rel(w, ref) <= 1e-5
