@@ -177,3 +177,51 @@ def test_fe_full_size_operators_match_oracle():
     ref = opc.apply_Peps_inv(x, n, alpha, eps, fe.FSTSpatialSolverFE(m1, d, tau))
     assert _rel(w, ref) <= 1e-5
     sol.close()
+
+
+@pytest.mark.parametrize("precision,rtol,tol", [("fp64", 1e-12, 1e-10), ("mixed", 1e-11, 1e-7)])
+def test_fe_3d_solve_and_end_points_match_oracle(precision, rtol, tol):
+    d, m1, n, gamma, eps = 3, 7, 8, 1e-3, 0.25
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    M, K = fe.fe_matrices(m1, d)
+    f = S.random_vector((n,) + (m1,) * d, 31)
+    g = S.random_vector((n,) + (m1,) * d, 32)
+    y0 = S.random_vector((m1,) * d, 33)
+    b_ref = fe.build_rhs(f, g, y0, tau, gamma, M)
+    ref = okr.gmres(lambda v: fe.apply_A(v, M, K, tau, alpha),
+                    lambda v: opc.apply_Peps_inv(v, n, alpha, eps, fe.FSTSpatialSolverFE(m1, d, tau)),
+                    b_ref, rtol=1e-13, maxit=200, mode="right")
+    assert ref.converged
+    sol = _solver(d, m1, n, precision=precision, gamma=gamma, eps=eps)
+    b = sol.build_rhs(_dev(f), _dev(g), _dev(y0))
+    assert _rel(b.cpu().numpy(), b_ref) <= 1e-13
+    x, it, rr = sol.solve(b, rtol=rtol)
+    assert rr <= rtol
+    xg = x.cpu().numpy().reshape(b_ref.shape)
+    xr = ref.x.reshape(b_ref.shape)
+    assert np.linalg.norm(xg - xr) <= tol * np.linalg.norm(xr)
+    fT, g0 = S.random_vector((m1,) * d, 34), S.random_vector((m1,) * d, 35)
+    yN, p0, _ = sol.end_point_solves(x, f_T=_dev(fT), g_0=_dev(g0), y0=_dev(y0), rtol=1e-13)
+    y, p = osy.unscale(xg, gamma)
+    yN_ref, p0_ref = fe.end_point_solves(y, p, M, K, tau, gamma, fT, g0, y0)
+    assert _rel(yN.cpu().numpy(), yN_ref) <= 1e-11
+    assert _rel(p0.cpu().numpy(), p0_ref) <= 1e-11
+    sol.close()
+
+
+def test_fe_and_fd_handles_in_one_batch_match_individual_solves():
+    from paper_2410_22686_gb300 import Batch, Solver
+    P = S.example1_problem(31, 32, 1e-2)
+    sols = [Solver(2, 31, 32, P.T, P.gamma, P.eps, None, spatial="fst", precision=prec, max_iter=60, space=sp)
+            for sp, prec in (("fe", "fp64"), ("fd", "fp64"), ("fe", "fp32"))]
+    bs = [s.build_rhs(_dev(P.f), _dev(P.g), _dev(P.y0)) for s in sols]
+    singles = [s.solve(b, rtol=1e-10) for s, b in zip(sols, bs)]
+    batch = Batch(sols, bs, rtol=1e-10, maxit=60)
+    iters, rel = batch.solve()
+    for k, (x_ref, it_ref, _) in enumerate(singles):
+        assert iters[k] == it_ref
+        assert rel[k] <= 1e-10
+        assert (batch.xs[k] - x_ref).norm().item() <= 1e-12 * x_ref.norm().item()
+    batch.close()
+    for s in sols:
+        s.close()
