@@ -225,3 +225,27 @@ def test_fe_and_fd_handles_in_one_batch_match_individual_solves():
     batch.close()
     for s in sols:
         s.close()
+
+
+def test_fe_set_coefficient_and_autotune():
+    """A constant coefficient c scales K (the sine-transform eigenvalues follow); the
+    tuner's shapes leave the results unchanged."""
+    d, m1, n, gamma, eps = 2, 31, 16, 1e-3, 0.3
+    sol = _solver(d, m1, n, gamma=gamma, eps=eps, precision="fp32")
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    sol.set_coefficient(np.full((m1 + 2,) * d, 2.5))
+    M, K = fe.fe_matrices(m1, d, coeff=2.5)
+    x = S.random_vector((2, n) + (m1,) * d, 41)
+    assert _rel(sol.matvec(_dev(x)).cpu().numpy(), fe.apply_A(x, M, K, tau, alpha)) <= 1e-12
+    ref = opc.apply_Peps_inv(x, n, alpha, eps, fe.FSTSpatialSolverFE(m1, d, tau, coeff=2.5))
+    w0 = sol.apply_precond(_dev(x)).cpu().numpy()
+    assert _rel(w0, ref) <= 1e-5
+    chosen = sol.autotune(2)
+    assert chosen["mv_tj"] > 0
+    assert _rel(sol.matvec(_dev(x)).cpu().numpy(), fe.apply_A(x, M, K, tau, alpha)) <= 1e-12
+    assert _rel(sol.apply_precond(_dev(x)).cpu().numpy(), ref) <= 1e-5
+    with pytest.raises(Exception):
+        a = np.full((m1 + 2,) * d, 1.0)
+        a[5, 5] = 2.0
+        sol.set_coefficient(a)  # element handles keep a constant coefficient
+    sol.close()
