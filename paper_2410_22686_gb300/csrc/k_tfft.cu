@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) tfft4s_forward_kernel(const Tin* __restri
 }
 
 template <typename Tc, typename TU, typename Tout, int N1, int N2>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 1) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+__global__ void __launch_bounds__(256, (sizeof(Tc) == 4 && N1 * N2 <= 256) ? 4 : 1) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
                                                             const Tc* __restrict__ dinv,
                                                             const typename Cx<Tc>::t* __restrict__ tw,
                                                             Tout* __restrict__ w, int64_t ms, size_t wstride,
