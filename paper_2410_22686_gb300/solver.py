@@ -141,10 +141,19 @@ class Solver:
         capi.check(self.lib.pc_build_rhs(self.h, _ptr(f), _ptr(g), _ptr(y0), _ptr(b), _stream()))
         return b
 
-    def solve(self, b, x0=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
-        """GMRES on A x = b; returns (x, iterations, relative residual)."""
+    def solve(self, b, x0=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True, out=None):
+        """GMRES on A x = b; returns (x, iterations, relative residual).  out: a device
+        vector to solve into (zeroed first unless x0 is given; no allocation then)."""
         self._vec(b)
-        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        if out is not None:
+            self._vec(out)
+            x = out
+            if x0 is None:
+                x.zero_()
+            elif x0.data_ptr() != x.data_ptr():
+                x.copy_(x0)
+        else:
+            x = torch.zeros_like(b) if x0 is None else x0.clone()
         it = ctypes.c_int(0)
         rr = ctypes.c_double(0.0)
         st = self.lib.pc_gmres_solve(self.h, _ptr(b), _ptr(x), rtol, maxit or self.max_iter, _MODE[mode],
@@ -269,8 +278,24 @@ def solve_host_pipelined(jobs, rtol=1e-8, maxit=None, mode="right", raise_on_non
             raise ValueError("host buffers must hold the solver's vector length")
     cur = torch.cuda.current_stream()
     cp = torch.cuda.Stream()
-    dev_b = [torch.empty(bh.shape, dtype=torch.float64, device="cuda") for _, bh, _ in jobs]
-    cp.wait_stream(cur)  # the buffers exist before the copy stream writes them
+    # device buffers live on the solvers and are reused by later calls: allocating
+    # inside the loop could make the caching allocator wait for the copy stream
+    dev_b, dev_x, seen = [], [], set()
+    for s, bh, _ in jobs:
+        bufs = getattr(s, "_pipe_bufs", None)
+        if id(s) in seen:  # a solver listed twice needs a second pair for this call
+            bufs = None
+        elif bufs is None or bufs[0].shape != bh.shape:
+            bufs = None
+        if bufs is None:
+            bufs = (torch.empty(bh.shape, dtype=torch.float64, device="cuda"),
+                    torch.empty(bh.shape, dtype=torch.float64, device="cuda"))
+            if id(s) not in seen:
+                s._pipe_bufs = bufs
+        seen.add(id(s))
+        dev_b.append(bufs[0])
+        dev_x.append(bufs[1])
+    cp.wait_stream(cur)  # the buffers are free before the copy stream writes them
 
     def copy_in(i):
         with torch.cuda.stream(cp):
@@ -282,17 +307,15 @@ def solve_host_pipelined(jobs, rtol=1e-8, maxit=None, mode="right", raise_on_non
     for i, (s, _, xh) in enumerate(jobs):
         ev_next = copy_in(i + 1) if i + 1 < len(jobs) else None
         cur.wait_event(ev_in)
-        x, it, rr = s.solve(dev_b[i], rtol=rtol, maxit=maxit, mode=mode, raise_on_nonconv=raise_on_nonconv)
+        x, it, rr = s.solve(dev_b[i], rtol=rtol, maxit=maxit, mode=mode, raise_on_nonconv=raise_on_nonconv,
+                            out=dev_x[i])
         ev_done = cur.record_event()
         with torch.cuda.stream(cp):
             cp.wait_event(ev_done)
             xh.copy_(x, non_blocking=True)
-            x.record_stream(cp)
         out.append((it, rr))
         ev_in = ev_next
     cp.synchronize()
-    for b in dev_b:
-        b.record_stream(cp)
     return out
 
 

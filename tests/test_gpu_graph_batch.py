@@ -103,5 +103,15 @@ def test_pipelined_host_solves_equal_device_solves():
         for (xr, itr, rrr), (it, rr), xh in zip(ref, res, hx):
             assert it == itr and rr == rrr
             assert torch.equal(xh, xr)
+    # the same solver listed twice gets a second pair of device buffers for that call
+    hx2 = [torch.empty(hx[0].shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    res = solve_host_pipelined([(sols[0], hb[0], hx2[0]), (sols[0], hb[0], hx2[1])], rtol=1e-8)
+    for (it, rr), xh in zip(res, hx2):
+        assert it == ref[0][1] and rr == ref[0][2]
+        assert torch.equal(xh, ref[0][0])
+    # solving into a given vector equals the allocating call
+    out = torch.full((sols[1].vec_len,), 7.0, dtype=torch.float64, device="cuda")
+    x, it, rr = sols[1].solve(hb[1].cuda(), rtol=1e-8, out=out)
+    assert x.data_ptr() == out.data_ptr() and it == ref[1][1] and torch.equal(x.cpu().reshape(ref[1][0].shape), ref[1][0])
     for s in sols:
         s.close()
