@@ -11,6 +11,15 @@
 // This is classical Gram-Schmidt with selective re-orthogonalisation: two passes
 // over the basis per iteration in the common case instead of four.
 //
+// The re-orthogonalisation pass removes what the first pass left along the basis,
+// components of ~1e-6 relative size at most (the check triggers there), so its
+// coefficients e = V^T v need only a few significant digits: they are formed on the
+// FP32 units from 20-bit truncations of V and v (error ~1e-10 absolute for 33 M
+// unknowns), and v - V e is accumulated in FP32 and subtracted from the FP64 v.  The
+// Arnoldi relation stays exact to FP64 rounding (column j of H takes the same e), the
+// new vector is orthogonal to ~1e-10, and the pass runs at memory speed instead of at
+// the FP64 unit's rate.
+//
 // Reductions are deterministic: an occupancy-sized grid writes per-block partial
 // sums (warp shuffles, then shared memory) and a second kernel adds them in a
 // fixed order.  The multi-dot is instantiated per vector count (1..16) so that
@@ -33,23 +42,46 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ bool gated_off(const double* gate) { return gate && gate[0] == 0.0; }
 
+// The top 20 mantissa bits of a double as a float (sign, exponent rebiased,
+// truncated), in integer operations; magnitudes below the float range become 0.
+__device__ __forceinline__ float hi20(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned mag = hi & 0x7FFFFFFFu;
+  const unsigned f = mag >= (897u << 20) ? (mag - (896u << 20)) << 3 : 0u;
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
+
 // partial[b*ld + i0 + c] = sum over block b of V_{i0+c} . w   (c < CNT)
 // partial[b*ld + nv]     = sum over block b of w . w          (WITH_NORM)
-template <int CNT, bool WITH_NORM>
+// LP: FP32 products of 20-bit truncations (the re-orthogonalisation pass), no norm.
+template <int CNT, bool WITH_NORM, bool LP = false>
 __device__ __forceinline__ void multidot_body(const double* __restrict__ V, size_t ldv, int i0,
                                               const double* __restrict__ w, size_t len,
                                               double* __restrict__ partial, int ncol_norm, int ld) {
   double acc[CNT];
+  float accf[LP ? CNT : 1];
   double ww = 0.0;
 #pragma unroll
   for (int c = 0; c < CNT; ++c) acc[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < (LP ? CNT : 1); ++c) accf[c] = 0.0f;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const double* Vb = V + (size_t)i0 * ldv;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
     const double we = w[e];
+    if (LP) {
+      const float wf = hi20(we);
+#pragma unroll
+      for (int c = 0; c < CNT; ++c) accf[LP ? c : 0] = fmaf(hi20(__ldg(Vb + (size_t)c * ldv + e)), wf, accf[LP ? c : 0]);
+      continue;
+    }
     if (WITH_NORM) ww = fma(we, we, ww);
 #pragma unroll
     for (int c = 0; c < CNT; ++c) acc[c] = fma(__ldg(Vb + (size_t)c * ldv + e), we, acc[c]);
+  }
+  if (LP) {
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) acc[c] = (double)accf[LP ? c : 0];
   }
   __shared__ double red[kThreads / 32][CNT + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -71,19 +103,19 @@ __device__ __forceinline__ void multidot_body(const double* __restrict__ V, size
   }
 }
 
-template <int CNT, bool WITH_NORM>
+template <int CNT, bool WITH_NORM, bool LP = false>
 __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ldv, int i0,
                                                             const double* __restrict__ w, size_t len,
                                                             double* __restrict__ partial, int nv, int ld,
                                                             const double* __restrict__ gate) {
   if (gated_off(gate)) return;
-  multidot_body<CNT, WITH_NORM>(V, ldv, i0, w, len, partial, nv, ld);
+  multidot_body<CNT, WITH_NORM, LP>(V, ldv, i0, w, len, partial, nv, ld);
 }
 
 // Device-resident Arnoldi index: nv = *jdev + 1 vectors, w = wbase + (*jdev + 1) wstride;
 // the chunk [i0, i0 + 16) exits when it lies beyond nv, otherwise dispatches on its count.
 // The norm column is ld - 1.
-template <bool WITH_NORM>
+template <bool WITH_NORM, bool LP = false>
 __global__ void __launch_bounds__(kThreads) multidot_dyn_kernel(const double* __restrict__ V, size_t ldv, int i0,
                                                                 const double* __restrict__ wbase, size_t wstride,
                                                                 const int* __restrict__ jdev, size_t len,
@@ -96,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) multidot_dyn_kernel(const double* __
   const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
   switch (cnt) {
 #define PCOPT_DYN(k) \
-  case k: multidot_body<k, WITH_NORM>(V, ldv, i0, w, len, partial, ld - 1, ld); break;
+  case k: multidot_body<k, WITH_NORM, LP>(V, ldv, i0, w, len, partial, ld - 1, ld); break;
     PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
     PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
 #undef PCOPT_DYN
@@ -148,6 +180,9 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double*
 // v = (v - sum_i coef_i V_i) * scale ;  partial[b] = sum over block b of (v - sum)^2 (before scaling)
 // with jdev != nullptr: nv = *jdev + 1 and v = vbase + nv * vstride.  vf != nullptr also
 // receives the FP32 rounding of the new v (the FP32 preconditioner's input).
+// LP: sum_i coef_i V_i in FP32 from 20-bit truncations of V (the re-orthogonalisation
+// pass, whose coefficients are tiny), subtracted from the FP64 v.
+template <bool LP>
 __global__ void __launch_bounds__(kThreads) update_kernel(const double* __restrict__ V, size_t ldv, int nv,
                                                           const double* __restrict__ coef, double* __restrict__ v,
                                                           size_t len, const double* __restrict__ scale,
@@ -161,14 +196,26 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const double* __restri
     v += (size_t)nv * vstride;
   }
   extern __shared__ double hs[];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = coef[i];
+  float* hf = reinterpret_cast<float*>(hs);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    if (LP)
+      hf[i] = (float)coef[i];
+    else
+      hs[i] = coef[i];
+  }
   __syncthreads();
   const double sc = scale ? scale[0] : 1.0;
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
     double we = v[e];
-    for (int i = 0; i < nv; ++i) we = fma(-hs[i], __ldg(V + (size_t)i * ldv + e), we);
+    if (LP) {
+      float sf = 0.0f;
+      for (int i = 0; i < nv; ++i) sf = fmaf(hf[i], hi20(__ldg(V + (size_t)i * ldv + e)), sf);
+      we -= f32_to_f64(sf);
+    } else {
+      for (int i = 0; i < nv; ++i) we = fma(-hs[i], __ldg(V + (size_t)i * ldv + e), we);
+    }
     acc = fma(we, we, acc);
     const double vn = we * sc;
     v[e] = vn;
@@ -375,11 +422,13 @@ ChunkGrids one_grid(unsigned nb) {
 template <int CNT, bool N>
 cudaError_t multidot_chunk(Launch& L, const double* V, size_t ldv, int i0, const double* w, size_t len,
                            double* partial, int nv, int ld, const double* gate, unsigned* blocks_out) {
-  const unsigned nb = wave_blocks(multidot_kernel<CNT, N>, 0, len);
+  // gated launches are the re-orthogonalisation pass: FP32 products (see the file header)
+  auto kern = gate ? multidot_kernel<CNT, N, true> : multidot_kernel<CNT, N, false>;
+  const unsigned nb = wave_blocks(kern, 0, len);
   *blocks_out = nb;
   const int kc = gate ? KC_REORTH : KC_DOT;
   L.begin(kc);
-  multidot_kernel<CNT, N><<<nb, kThreads, 0, L.stream>>>(V, ldv, i0, w, len, partial, nv, ld, gate);
+  kern<<<nb, kThreads, 0, L.stream>>>(V, ldv, i0, w, len, partial, nv, ld, gate);
   return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * len * (CNT + 1), 2.0 * len * (CNT + (N ? 1 : 0)));
 }
 
@@ -424,10 +473,11 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
 cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
                           const double* scale, double* partial, double* q, const double* gate, float* vf) {
   const size_t smem = sizeof(double) * (nv > 0 ? nv : 1);
-  const unsigned nb = wave_blocks(update_kernel, smem, len);
+  auto kern = gate ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
+  const unsigned nb = wave_blocks(kern, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
-  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate, nullptr, 0, vf);
+  kern<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv, coef, v, len, scale, partial, gate, nullptr, 0, vf);
   cudaError_t e = gate ? L.end(kc, 0.0, 0.0)
                        : L.end(kc, 8.0 * len * (nv + 2) + (vf ? 4.0 * len : 0.0), 2.0 * len * (nv + 1));
   if (e != cudaSuccess) return e;
@@ -517,8 +567,10 @@ cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_m
                                 double* ww, const double* gate) {
   if (nv_max < 1 || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
   const int ld = nv_max + 1;
+  // gated launches are the re-orthogonalisation pass: FP32 products (see the file header)
+  auto plain = gate ? multidot_dyn_kernel<false, true> : multidot_dyn_kernel<false, false>;
   const unsigned nb_norm = wave_blocks(multidot_dyn_kernel<true>, 0, len);
-  const unsigned nb_plain = wave_blocks(multidot_dyn_kernel<false>, 0, len);
+  const unsigned nb_plain = wave_blocks(plain, 0, len);
   ChunkGrids cg = one_grid(nb_plain);
   const int kc = gate ? KC_REORTH : KC_DOT;
   for (int i0 = 0, c = 0; i0 < nv_max; i0 += kChunk, ++c) {
@@ -528,8 +580,7 @@ cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_m
       multidot_dyn_kernel<true><<<nb_norm, kThreads, 0, L.stream>>>(V, ldv, i0, wbase, wstride, jdev, len, partial,
                                                                    ld, gate);
     } else {
-      multidot_dyn_kernel<false><<<nb_plain, kThreads, 0, L.stream>>>(V, ldv, i0, wbase, wstride, jdev, len,
-                                                                     partial, ld, gate);
+      plain<<<nb_plain, kThreads, 0, L.stream>>>(V, ldv, i0, wbase, wstride, jdev, len, partial, ld, gate);
     }
     cudaError_t e = L.end(kc, 0.0, 0.0);
     if (e != cudaSuccess) return e;
@@ -544,10 +595,11 @@ cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max
                               double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
                               double* q, const double* gate, float* vf) {
   const size_t smem = sizeof(double) * nv_max;
-  const unsigned nb = wave_blocks(update_kernel, smem, len);
+  auto kern = gate ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
+  const unsigned nb = wave_blocks(kern, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
-  update_kernel<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv_max, coef, vbase, len, scale, partial, gate, jdev,
+  kern<<<nb, kThreads, smem, L.stream>>>(V, ldv, nv_max, coef, vbase, len, scale, partial, gate, jdev,
                                                   vstride, vf);
   cudaError_t e = L.end(kc, 0.0, 0.0);
   if (e != cudaSuccess) return e;
