@@ -24,6 +24,8 @@
 // sums (warp shuffles, then shared memory) and a second kernel adds them in a
 // fixed order.  The multi-dot is instantiated per vector count (1..16) so that
 // every FMA it issues is useful; more vectors take several chunked launches.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pcopt {
@@ -352,13 +354,40 @@ __global__ void __launch_bounds__(kThreads) xupdate_kernel(const Tz* __restrict_
                                                            size_t len, const int* __restrict__ kdev) {
   if (kdev) k = *kdev;
   extern __shared__ double ys[];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
-  __syncthreads();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    double xe = x[e];
-    for (int i = 0; i < k; ++i) xe = fma(ys[i], cvt<double>(Z[(size_t)i * ldz + e]), xe);
-    x[e] = xe;
+  if constexpr (std::is_same<Tz, float>::value) {
+    // FP32 basis Z: sum_i y_i z_i in double-float on the FP32 units (y_i split into
+    // float pairs, each product exact up to its FMA error term, the leading parts added
+    // by TwoSum, every error gathered in one float; ~2^-46 of the terms), then one FP64
+    // addition into x.  The FP64 unit would otherwise bound this kernel.
+    float2* yf = reinterpret_cast<float2*>(ys);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const float hi = (float)y[i];
+      yf[i] = make_float2(hi, (float)(y[i] - (double)hi));
+    }
+    __syncthreads();
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+      float sh = 0.0f, err = 0.0f;
+      for (int i = 0; i < k; ++i) {
+        const float2 c = yf[i];
+        const float z = Z[(size_t)i * ldz + e];
+        const float p = __fmul_rn(c.x, z);
+        err = __fadd_rn(err, __fadd_rn(fmaf(c.x, z, -p), __fmul_rn(c.y, z)));
+        const float s = __fadd_rn(sh, p);
+        const float bb = __fsub_rn(s, sh);
+        err = __fadd_rn(err, __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb)));
+        sh = s;
+      }
+      x[e] += f32_to_f64(sh) + f32_to_f64(err);
+    }
+  } else {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+      double xe = x[e];
+      for (int i = 0; i < k; ++i) xe = fma(ys[i], cvt<double>(Z[(size_t)i * ldz + e]), xe);
+      x[e] = xe;
+    }
   }
 }
 
