@@ -310,32 +310,46 @@ __global__ void arnoldi_check_kernel(ArnoldiScalars s) {
 //   re-orthogonalisation:     w = V (d + c e) + c rho v_{j+1},  rho^2 = s.rho2
 __global__ void givens_kernel(int j, int ldh, double* H, double* cs, double* sn, double* g, const double* d,
                               const double* e, ArnoldiScalars s, double* est, const double* ref, const int* jdev) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
   if (jdev) j = *jdev;
+  // the warp stages the column and the rotations in shared memory; one thread then
+  // applies the j sequential rotations without waiting on global memory
+  __shared__ double cl[1026], sc[1024], ss[1024];
   double* col = H + (size_t)j * ldh;
   const bool re = s.flag[0] != 0.0;
   const double c = s.c[0];
-  for (int i = 0; i <= j; ++i) col[i] = re ? fma(c, e[i], d[i]) : d[i];
-  col[j + 1] = re ? c * sqrt(s.rho2[0]) : c;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    cl[i] = re ? fma(c, e[i], d[i]) : d[i];
+    if (i < j) {
+      sc[i] = cs[i];
+      ss[i] = sn[i];
+    }
   }
-  const double a = col[j], b = col[j + 1];
-  double cr = 1.0, sr = 0.0, r = a;
-  if (b != 0.0) {
-    r = hypot(a, b);
-    cr = a / r;
-    sr = b / r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cl[j + 1] = re ? c * sqrt(s.rho2[0]) : c;
+    for (int i = 0; i < j; ++i) {
+      const double t = sc[i] * cl[i] + ss[i] * cl[i + 1];
+      cl[i + 1] = -ss[i] * cl[i] + sc[i] * cl[i + 1];
+      cl[i] = t;
+    }
+    const double a = cl[j], b = cl[j + 1];
+    double cr = 1.0, sr = 0.0, r = a;
+    if (b != 0.0) {
+      r = hypot(a, b);
+      cr = a / r;
+      sr = b / r;
+    }
+    cs[j] = cr;
+    sn[j] = sr;
+    cl[j] = r;
+    cl[j + 1] = 0.0;
+    g[j + 1] = -sr * g[j];
+    g[j] = cr * g[j];
+    est[0] = fabs(g[j + 1]) / ref[0];
   }
-  cs[j] = cr;
-  sn[j] = sr;
-  col[j] = r;
-  col[j + 1] = 0.0;
-  g[j + 1] = -sr * g[j];
-  g[j] = cr * g[j];
-  est[0] = fabs(g[j + 1]) / ref[0];
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = cl[i];
 }
 
 __global__ void backsolve_kernel(int k, int ldh, const double* H, const double* g, double* y, const int* kdev) {
