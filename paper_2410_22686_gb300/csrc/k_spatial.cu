@@ -88,6 +88,93 @@ __global__ void fst_divide_kernel(typename Cx<Tc>::t* __restrict__ buf, const Tc
 // recomputes the red neighbour values from r (one reciprocal per neighbour, cheap in
 // FP32); MODE 1 writes the red points only and MODE 2 the black ones from the stored
 // red values (two passes, one reciprocal per point: FP64, whose reciprocal is costly).
+// MODE 0 with one thread per pair of x1-neighbours (i1 = 2q, 2q+1): one point of the
+// pair is red and one black, so every lane does one red and one black update (a thread
+// per point splits each warp between the cheap red and the expensive black update) and
+// the black point takes its partner's red value without recomputing it.
+template <typename Tc, typename TU, int DIM>
+__global__ void __launch_bounds__(256) mg_smooth_pair_kernel(const typename Cx<Tc>::t* __restrict__ r,
+                                                             TU* __restrict__ u, const Tc* __restrict__ w,
+                                                             const Tc* __restrict__ diag,
+                                                             const typename Cx<Tc>::t* __restrict__ sigma, int m,
+                                                             int64_t np, int planes, int pch) {
+  typedef typename Cx<Tc>::t C;
+  const int half = (m + 1) / 2;  // pairs per grid row (the last one may hold a single point)
+  const int64_t rows = np / m;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * half) return;
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
+  const int64_t row = t / half;
+  const int q = (int)(t - row * half);
+  const int i2 = (int)(DIM == 2 ? row : row % m);
+  const int i3 = (int)(DIM == 3 ? row / m : 0);
+  const int ia = 2 * q;
+  const bool hasb = ia + 1 < m;
+  const bool a_red = ((ia + i2 + i3 + DIM) & 1) == 0;
+  const int64_t sa = row * m + ia;
+  // the black point of the pair (absent when the pair holds only a red point)
+  const bool has_black = !a_red || hasb;
+  const bool has_red = a_red || hasb;
+  const int64_t sr = a_red ? sa : sa + 1;
+  const int64_t sk = a_red ? sa + 1 : sa;
+  const int ik = a_red ? ia + 1 : ia;  // x1 index of the black point
+  const Tc dr = has_red ? diag[sr] : Tc(1);
+  // neighbours of the black point: x1 -/+ (one of them is the red partner), x2 -/+, x3 -/+
+  int64_t off[2 * DIM];
+  bool ex[2 * DIM];
+  bool partner[2 * DIM];
+  Tc wv[2 * DIM], dn[2 * DIM];
+  const int64_t mm = (int64_t)m * m;
+  off[0] = -1;
+  ex[0] = ik > 0;
+  off[1] = 1;
+  ex[1] = ik < m - 1;
+  off[2] = -(int64_t)m;
+  ex[2] = i2 > 0;
+  off[3] = m;
+  ex[3] = i2 < m - 1;
+  if (DIM == 3) {
+    off[4] = -mm;
+    ex[4] = i3 > 0;
+    off[5] = mm;
+    ex[5] = i3 < m - 1;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * DIM; ++k) partner[k] = has_red && (k == (a_red ? 0 : 1));
+  Tc dk = Tc(1);
+  if (has_black) {
+    dk = diag[sk];
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k) {
+      wv[k] = w[(int64_t)k * np + sk];
+      dn[k] = (ex[k] && !partner[k]) ? diag[sk + off[k]] : Tc(0);
+    }
+  }
+  for (int p = p0; p < p1; ++p) {
+    const int64_t base = (int64_t)p * np;
+    const C sig = sigma[p];
+    C ur = czero<Tc>();
+    if (has_red) {
+      ur = cmul(r[base + sr], inv_shift_c(sig, dr));
+      stc(u, base + sr, ur);
+    }
+    if (has_black) {
+      const int64_t o = base + sk;
+      C acc = r[o];
+#pragma unroll
+      for (int k = 0; k < 2 * DIM; ++k) {
+        if (ex[k]) {
+          const C v = partner[k] ? ur : cmul(r[o + off[k]], inv_shift_c(sig, dn[k]));
+          acc.x = fma(wv[k], v.x, acc.x);
+          acc.y = fma(wv[k], v.y, acc.y);
+        }
+      }
+      stc(u, o, cmul(acc, inv_shift_c(sig, dk)));
+    }
+  }
+}
+
 template <typename Tc, typename TU, int DIM, int MODE>
 __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t* __restrict__ r,
                                                         TU* __restrict__ u,
@@ -367,10 +454,13 @@ cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil
       mg_smooth_kernel<Tc, TU, 3, 1><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
       mg_smooth_kernel<Tc, TU, 3, 2><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
     }
-  } else if (g.dim == 2) {
-    mg_smooth_kernel<Tc, TU, 2, 0><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
   } else {
-    mg_smooth_kernel<Tc, TU, 3, 0><<<grid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+    const int64_t pairs = (g.np / g.m) * ((g.m + 1) / 2);
+    const dim3 pgrid((unsigned)((pairs + 255) / 256), (unsigned)((planes + pch - 1) / pch));
+    if (g.dim == 2)
+      mg_smooth_pair_kernel<Tc, TU, 2><<<pgrid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
+    else
+      mg_smooth_pair_kernel<Tc, TU, 3><<<pgrid, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np, planes, pch);
   }
   return L.end(KC_MG_SMOOTH, 2.0 * tot * cs, tot * (12.0 + 10.0 * g.dim));
 }
