@@ -11,6 +11,8 @@
 //
 // Threads own one spatial point and loop over a chunk of planes, so the
 // point's face weights and diagonal are read once and reused for every shift.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pcopt {
@@ -238,6 +240,76 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
 }
 
 // res = r - (sigma u + tau K u)
+// Residual after the red-black sweep from zero, from the sweep's identity: zero at
+// black points (their update solved their own equation) and sum_k w_k u_black at red
+// ones (the red update used zero neighbours).  One thread per red/black pair along x1.
+// Iterates stored in the compute type only (BF16 storage breaks the identity).
+template <typename Tc, int DIM>
+__global__ void __launch_bounds__(256) mg_residual_pair_kernel(const typename Cx<Tc>::t* __restrict__ u,
+                                                               typename Cx<Tc>::t* __restrict__ res,
+                                                               const Tc* __restrict__ w, int m, int64_t np,
+                                                               int planes, int pch) {
+  typedef typename Cx<Tc>::t C;
+  const int half = (m + 1) / 2;
+  const int64_t rows = np / m;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * half) return;
+  const int p0 = blockIdx.y * pch;
+  const int p1 = min(planes, p0 + pch);
+  const int64_t row = t / half;
+  const int q = (int)(t - row * half);
+  const int i2 = (int)(DIM == 2 ? row : row % m);
+  const int i3 = (int)(DIM == 3 ? row / m : 0);
+  const int ia = 2 * q;
+  const bool hasb = ia + 1 < m;
+  const bool a_red = ((ia + i2 + i3 + DIM) & 1) == 0;
+  const int64_t sa = row * m + ia;
+  const bool has_red = a_red || hasb;
+  const bool has_black = !a_red || hasb;
+  const int64_t sr = a_red ? sa : sa + 1;
+  const int64_t sk = a_red ? sa + 1 : sa;
+  const int ir = a_red ? ia : ia + 1;
+  int64_t off[2 * DIM];
+  bool ex[2 * DIM];
+  Tc wv[2 * DIM];
+  const int64_t mm = (int64_t)m * m;
+  off[0] = -1;
+  ex[0] = ir > 0;
+  off[1] = 1;
+  ex[1] = ir < m - 1;
+  off[2] = -(int64_t)m;
+  ex[2] = i2 > 0;
+  off[3] = m;
+  ex[3] = i2 < m - 1;
+  if (DIM == 3) {
+    off[4] = -mm;
+    ex[4] = i3 > 0;
+    off[5] = mm;
+    ex[5] = i3 < m - 1;
+  }
+  if (has_red) {
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k) wv[k] = w[(int64_t)k * np + sr];
+  }
+  for (int p = p0; p < p1; ++p) {
+    const int64_t base = (int64_t)p * np;
+    if (has_black) res[base + sk] = czero<Tc>();
+    if (has_red) {
+      const int64_t o = base + sr;
+      C acc = czero<Tc>();
+#pragma unroll
+      for (int k = 0; k < 2 * DIM; ++k) {
+        if (ex[k]) {
+          const C un = u[o + off[k]];
+          acc.x = fma(wv[k], un.x, acc.x);
+          acc.y = fma(wv[k], un.y, acc.y);
+        }
+      }
+      res[o] = acc;
+    }
+  }
+}
+
 template <typename Tc, typename TU, int DIM>
 __global__ void __launch_bounds__(256) mg_residual_kernel(const typename Cx<Tc>::t* __restrict__ r,
                                                           const TU* __restrict__ u,
@@ -475,13 +547,25 @@ cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const
   const int64_t npc = g.dim == 2 ? (int64_t)mc * mc : (int64_t)mc * mc * mc;
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_RESID_RESTRICT);
-  if (g.dim == 2)
-    mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
-                                                                              g.np, planes, pch);
-  else
-    mg_residual_kernel<Tc, TU, 3><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag, sigma, g.m,
-                                                                              g.np, planes, pch);
-  cudaError_t e = L.end(KC_MG_RESID_RESTRICT, 3.0 * tot * cs, tot * (8.0 + 4.0 * g.dim));
+  double rbytes = 3.0 * tot * cs;
+  if constexpr (std::is_same<TU, typename Cx<Tc>::t>::value) {
+    // u is the sweep from zero just made: its residual follows from the sweep's identity
+    const int64_t pairs = (g.np / g.m) * ((g.m + 1) / 2);
+    const dim3 pgrid((unsigned)((pairs + 255) / 256), (unsigned)((planes + pch - 1) / pch));
+    if (g.dim == 2)
+      mg_residual_pair_kernel<Tc, 2><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
+    else
+      mg_residual_pair_kernel<Tc, 3><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
+    rbytes = 2.0 * tot * cs;
+  } else {
+    if (g.dim == 2)
+      mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag,
+                                                                                        sigma, g.m, g.np, planes, pch);
+    else
+      mg_residual_kernel<Tc, TU, 3><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag,
+                                                                                        sigma, g.m, g.np, planes, pch);
+  }
+  cudaError_t e = L.end(KC_MG_RESID_RESTRICT, rbytes, tot * (8.0 + 4.0 * g.dim));
   if (e != cudaSuccess) return e;
   L.begin(KC_MG_RESID_RESTRICT);
   if (g.dim == 2)
