@@ -249,3 +249,23 @@ def test_fe_set_coefficient_and_autotune():
         a[5, 5] = 2.0
         sol.set_coefficient(a)  # element handles keep a constant coefficient
     sol.close()
+
+
+def test_fe_left_preconditioned_gmres_matches_oracle():
+    """The paper's own GMRES mode (left preconditioning, stop on the preconditioned
+    residual) with elements and a length n = 2^k - 1 (direct DFT in time)."""
+    P = S.example1_problem(15, 15, 1e-2)
+    M, K = fe.fe_matrices(15, 2)
+    alpha = osy.alpha_weight(P.T, P.n, P.gamma)
+    b_ref = fe.build_rhs(P.f, P.g, P.y0, P.tau, P.gamma, M)
+    A = lambda v: fe.apply_A(v, M, K, P.tau, alpha)
+    Pi = lambda v: opc.apply_Peps_inv(v, P.n, alpha, P.eps, fe.FSTSpatialSolverFE(15, 2, P.tau))
+    ref = okr.gmres(A, Pi, b_ref, rtol=1e-10, maxit=100, mode="left")
+    assert ref.converged
+    sol = _solver(2, 15, 15, gamma=P.gamma, eps=P.eps, T=P.T, max_iter=60)
+    b = sol.build_rhs(_dev(P.f), _dev(P.g), _dev(P.y0))
+    x, it, rr = sol.solve(b, rtol=1e-10, mode="left")
+    assert it == ref.iters
+    xr = ref.x.reshape(b_ref.shape)
+    assert np.linalg.norm(x.cpu().numpy().reshape(b_ref.shape) - xr) <= 1e-9 * np.linalg.norm(xr)
+    sol.close()
