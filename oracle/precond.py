@@ -205,12 +205,19 @@ def prolong_linear(e: np.ndarray, d: int) -> np.ndarray:
 
 class MGSpatialSolver:
     """One V(1,0) cycle per shifted system (Example 2, Section 2.1): the
-    preconditioner is *defined* by this cycle, not by an exact solve."""
+    preconditioner is *defined* by this cycle, not by an exact solve.
 
-    def __init__(self, a_nodes: np.ndarray, tau: float):
+    smoother: "red-black" (one red-black Gauss-Seidel sweep from zero, red first) or
+    "lexicographic" (one sweep in the natural order, x1 fastest: every point takes its
+    lower neighbours' new values and zero for the others)."""
+
+    def __init__(self, a_nodes: np.ndarray, tau: float, smoother: str = "red-black"):
         m = a_nodes.shape[0] - 2
         if m < 1 or (m + 1) & m:
             raise ValueError("multigrid needs m1 = 2^k - 1")
+        if smoother not in ("red-black", "lexicographic"):
+            raise ValueError("smoother must be 'red-black' or 'lexicographic'")
+        self.smoother = smoother
         self.tau = tau
         self.d = a_nodes.ndim
         self.levels = []
@@ -231,16 +238,49 @@ class MGSpatialSolver:
         dg = s + self.tau * lev.diagK[None]
         if lev.m == 1:
             return r / dg
-        u = np.zeros_like(r)
-        # red-black Gauss-Seidel sweep from zero: red first (its neighbours are 0) ...
-        u[:, lev.red] = r[:, lev.red] / dg[:, lev.red]
-        # ... then black, using the updated red values
-        off = self._op(lev, sigma, u) - dg * u
-        u[:, lev.black] = (r[:, lev.black] - off[:, lev.black]) / dg[:, lev.black]
+        if self.smoother == "lexicographic":
+            u = self._lex_sweep(lev, dg, r)
+        else:
+            u = np.zeros_like(r)
+            # red-black Gauss-Seidel sweep from zero: red first (its neighbours are 0) ...
+            u[:, lev.red] = r[:, lev.red] / dg[:, lev.red]
+            # ... then black, using the updated red values
+            off = self._op(lev, sigma, u) - dg * u
+            u[:, lev.black] = (r[:, lev.black] - off[:, lev.black]) / dg[:, lev.black]
         res = r - self._op(lev, sigma, u)
         rc = restrict_full_weighting(res, self.d)
         ec = self.vcycle(l + 1, sigma, rc)
         return u + prolong_linear(ec, self.d)
+
+    def _lex_sweep(self, lev: MGLevel, dg: np.ndarray, r: np.ndarray) -> np.ndarray:
+        """Gauss-Seidel sweep from zero in the natural order: u_P = (r_P + sum over the
+        lower neighbours Q of w_PQ u_Q) / (sigma + d_P), w_PQ = tau (a_P + a_Q) / (2 h^2).
+        Points with equal index sum do not depend on each other, so the sweep runs one
+        such diagonal at a time (the result is that of the point-by-point loop)."""
+        d, m, a = self.d, lev.m, lev.a
+        h = system.mesh_width(m)
+        inner = (slice(1, -1),) * d
+        aP = a[inner]
+        wlow = []  # weight towards the lower neighbour along each array axis
+        for ax in range(d):
+            sl = [slice(1, -1)] * d
+            sl[ax] = slice(0, -2)
+            wlow.append(self.tau * 0.5 * (aP + a[tuple(sl)]) / (h * h))
+        u = np.zeros_like(r)
+        tsum = np.indices((m,) * d).sum(axis=0)
+        for t in range(d * (m - 1) + 1):
+            pts = np.nonzero(tsum == t)
+            acc = r[(slice(None),) + pts].copy()
+            for ax in range(d):
+                has = pts[ax] > 0
+                if not has.any():
+                    continue
+                sel = tuple(p[has] for p in pts)
+                nb = list(sel)
+                nb[ax] = nb[ax] - 1
+                acc[:, has] += wlow[ax][sel] * u[(slice(None),) + tuple(nb)]
+            u[(slice(None),) + pts] = acc / dg[(slice(None),) + pts]
+        return u
 
     def __call__(self, sigma: np.ndarray, R: np.ndarray) -> np.ndarray:
         return self.vcycle(0, sigma, R.astype(complex))
@@ -272,8 +312,8 @@ def apply_Peps_inv(v: np.ndarray, n: int, alpha: float, eps: float, spatial) -> 
     return np.stack([wt1 - wt2, wt1 + wt2])
 
 
-def make_spatial_solver(kind: str, a_nodes, m1: int, d: int, tau: float):
-    """'dense' | 'fst' (a constant; a_nodes None means a = 1) | 'mg'."""
+def make_spatial_solver(kind: str, a_nodes, m1: int, d: int, tau: float, smoother: str = "red-black"):
+    """'dense' | 'fst' (a constant; a_nodes None means a = 1) | 'mg' (with the given smoother)."""
     if a_nodes is None:
         a_nodes = system.unit_coefficient(m1, d)
     if kind == "dense":
@@ -284,5 +324,5 @@ def make_spatial_solver(kind: str, a_nodes, m1: int, d: int, tau: float):
             raise ValueError("FST needs a constant coefficient")
         return FSTSpatialSolver(m1, d, tau, c)
     if kind == "mg":
-        return MGSpatialSolver(a_nodes, tau)
+        return MGSpatialSolver(a_nodes, tau, smoother)
     raise ValueError(kind)

@@ -178,11 +178,12 @@ def test_multigrid_coarsest_level_is_exact():
     assert np.allclose(sol(sig, r), ref)
 
 
+@pytest.mark.parametrize("smoother", ["red-black", "lexicographic"])
 @pytest.mark.parametrize("d,m1", [(2, 15), (3, 7)])
-def test_multigrid_vcycle_is_a_convergent_linear_approximate_inverse(d, m1):
+def test_multigrid_vcycle_is_a_convergent_linear_approximate_inverse(d, m1, smoother):
     a = np.exp(0.5 * S.random_vector((m1 + 2,) * d, 7))
     tau = 1.0 / 17
-    sol = pc.MGSpatialSolver(a, tau)
+    sol = pc.MGSpatialSolver(a, tau, smoother)
     dense = pc.DenseSpatialSolver(a, tau)
     sig = np.array([1 + 0.05 + 0j, 0.3 + 0.8j, 0.01 - 0.9j])   # lambda_k + alpha-like shifts
     r = S.random_vector((3,) + (m1,) * d, 8) + 1j * S.random_vector((3,) + (m1,) * d, 9)
@@ -199,6 +200,29 @@ def test_multigrid_vcycle_is_a_convergent_linear_approximate_inverse(d, m1):
         norms.append(np.abs(u - exact).max() / np.abs(exact).max())
     assert norms[-1] < 1e-8, norms
     assert max(norms[i + 1] / norms[i] for i in range(4)) < 0.6
+
+
+@pytest.mark.parametrize("d,m1", [(2, 7), (3, 3)])
+def test_lexicographic_sweep_is_pointwise_gauss_seidel_in_the_natural_order(d, m1):
+    # brute force: visit the points one by one in the natural order (x1 fastest) and
+    # solve each row of the dense shifted matrix with the values computed so far
+    a = np.exp(0.5 * S.random_vector((m1 + 2,) * d, 21))
+    tau = 0.07
+    sol = pc.MGSpatialSolver(a, tau, "lexicographic")
+    lev = sol.levels[0]
+    sig = np.array([0.6 + 0.4j, 1.1 - 0.2j])
+    r = S.random_vector((2,) + (m1,) * d, 22) + 1j * S.random_vector((2,) + (m1,) * d, 23)
+    dg = sig.reshape((-1,) + (1,) * d) + tau * lev.diagK[None]
+    got = sol._lex_sweep(lev, dg, r)
+    K = sy.K_sparse(a).toarray()
+    ms = K.shape[0]
+    for k in range(2):
+        Ak = sig[k] * np.eye(ms) + tau * K
+        rk = r[k].reshape(ms)
+        u = np.zeros(ms, dtype=complex)
+        for i in range(ms):  # flattened order = natural order, x1 fastest
+            u[i] = (rk[i] - Ak[i, :i] @ u[:i]) / Ak[i, i]
+        assert np.allclose(got[k].reshape(ms), u, rtol=0, atol=1e-13 * np.abs(u).max())
 
 
 def test_red_black_sweep_leaves_zero_residual_on_black_points():
