@@ -78,6 +78,12 @@ typedef enum pc_space {
                        constant coefficient a only, sine-transform spatial solves */
 } pc_space;
 
+typedef enum pc_smoother {
+  PC_SMOOTHER_RED_BLACK = 0,     /* one red-black Gauss-Seidel sweep from zero, red first (parallel) */
+  PC_SMOOTHER_LEXICOGRAPHIC = 1  /* one sweep in the natural order, x1 fastest (Example 2's counts of
+                                    Table 7 exactly; sequential along the grid diagonals, much slower) */
+} pc_smoother;
+
 typedef struct pc_params {
   int dim;          /* 2 or 3 */
   int m1;           /* interior grid points per dimension, h = 1/(m1+1); multigrid needs m1 = 2^k-1 */
@@ -90,6 +96,7 @@ typedef struct pc_params {
   int precision;    /* pc_precision */
   int max_iter;     /* Krylov capacity: basis storage for this many iterations (1..1000) */
   int space;        /* pc_space: spatial discretisation (0 = finite differences) */
+  int smoother;     /* pc_smoother: Gauss-Seidel ordering of the multigrid pre-smoother (0 = red-black) */
 } pc_params;
 
 typedef struct pc_handle pc_handle;

@@ -21,13 +21,14 @@ PC_SPATIAL_AUTO, PC_SPATIAL_FST, PC_SPATIAL_MG = 0, 1, 2
 PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S = 0, 1, 2
 PC_GMRES_RIGHT, PC_GMRES_LEFT = 0, 1
 PC_SPACE_FD, PC_SPACE_FE = 0, 1
+PC_SMOOTHER_RED_BLACK, PC_SMOOTHER_LEXICOGRAPHIC = 0, 1
 
 
 class pc_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("m1", ctypes.c_int), ("n", ctypes.c_int),
                 ("T", ctypes.c_double), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
                 ("spatial", ctypes.c_int), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("space", ctypes.c_int)]
+                ("space", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class pc_tiles(ctypes.Structure):

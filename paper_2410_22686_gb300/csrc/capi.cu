@@ -161,6 +161,7 @@ struct pc_handle {
   int cap = 0;
   double a_const = 1.0;
   bool fe = false;  // finite elements in space (mass matrix M): constant a, FST
+  bool lex = false;  // multigrid smoother in the natural order (per-level kernels on every level)
   FeScale fes;
 
   std::vector<LevelBuf> lv;
@@ -449,6 +450,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   if (p->spatial < 0 || p->spatial > 2) return fail(PC_ERR_ARG, "unknown spatial solver");
   if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
   if (p->space != PC_SPACE_FD && p->space != PC_SPACE_FE) return fail(PC_ERR_ARG, "unknown space discretisation");
+  if (p->smoother != PC_SMOOTHER_RED_BLACK && p->smoother != PC_SMOOTHER_LEXICOGRAPHIC)
+    return fail(PC_ERR_ARG, "unknown smoother");
 
   const int dim = p->dim, m1 = p->m1;
   const int M = m1 + 2;
@@ -493,6 +496,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->a_const = a[0];
   h->fe = fe;
   h->fes = fe_scale(dim, m1, h->a_const);
+  h->lex = spatial == PC_SPATIAL_MG && p->smoother == PC_SMOOTHER_LEXICOGRAPHIC;
   h->prof.on = false;
   cudaStream_t st = (cudaStream_t)stream;
 
@@ -523,8 +527,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       }
       if ((rc = dev_alloc(h, &L.r, (size_t)h->planes * L.np * cb))) goto fail_out;
       if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * ub))) goto fail_out;
-      // per-level residual planes: only the 3D path writes them (2D fuses the residual away)
-      if (dim == 3 && l + 1 < mlev.size() && (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb)))
+      // per-level residual planes: the 3D path and the natural-order smoother write them
+      // (the 2D red-black down leg fuses the residual away)
+      if ((dim == 3 || h->lex) && l + 1 < mlev.size() &&
+          (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb)))
         goto fail_out;
       h->lv.push_back(L);
     }
@@ -878,6 +884,27 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
   // multigrid V(1,0): per-level kernels on the fine levels, one fused kernel for the rest
   const int nl = (int)h->lv.size();
   const int l0 = h->coarse_l0;
+  if (h->lex) {
+    // smoother in the natural order: per-level kernels on every level, explicit residuals,
+    // the one-point level solved exactly, every prolongation here
+    for (int l = 0; l + 1 < nl; ++l) {
+      const LevelBuf& Lb = h->lv[l];
+      Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
+      const Grid g = grid_of(h, l);
+      if ((e = launch_mg_smooth_lex<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (TU*)Lb.u)) != cudaSuccess) return e;
+      if ((e = launch_mg_resid_restrict<Tc, TU>(L, g, P, st, sig, (const C*)Lb.r, (const TU*)Lb.u, (C*)Lb.res,
+                                                (C*)h->lv[l + 1].r, false)) != cudaSuccess)
+        return e;
+    }
+    if ((e = launch_mg_coarsest<Tc, TU>(L, P, lvd<Tc>(h->lv[nl - 1]), sig, (const C*)h->lv[nl - 1].r,
+                                        (TU*)h->lv[nl - 1].u)) != cudaSuccess)
+      return e;
+    for (int l = nl - 2; l >= 0; --l)
+      if ((e = launch_mg_prolong<Tc, TU>(L, grid_of(h, l), P, (const TU*)h->lv[l + 1].u, (TU*)h->lv[l].u)) !=
+          cudaSuccess)
+        return e;
+    return cudaSuccess;
+  }
   for (int l = 0; l < l0; ++l) {
     const LevelBuf& Lb = h->lv[l];
     Stencil<Tc> st{lvw<Tc>(Lb), lvd<Tc>(Lb)};
@@ -913,7 +940,7 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
 template <typename TU>
 static FineCorrection<TU> fine_correction(const pc_handle* h) {
   FineCorrection<TU> fc;
-  if (h->spatial == PC_SPATIAL_FST || h->coarse_l0 < 1 || h->dim != 2) return fc;
+  if (h->spatial == PC_SPATIAL_FST || h->lex || h->coarse_l0 < 1 || h->dim != 2) return fc;
   const Grid g0 = grid_of(h, 0), g1 = grid_of(h, 1);
   fc.ec = (const TU*)h->lv[1].u;
   fc.dim = h->dim;

@@ -288,10 +288,16 @@ cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool
 template <typename Tc, typename TU>
 cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                              const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u);
+// residual of the sweep's result and its full weighting onto the next level; rb_sweep:
+// u is a red-black sweep from zero, whose residual follows from the sweep's identity
 template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                                      const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
-                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc);
+                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc, bool rb_sweep = true);
+// Gauss-Seidel sweep from zero in the natural order (one CTA per plane, diagonal by diagonal)
+template <typename Tc, typename TU>
+cudaError_t launch_mg_smooth_lex(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
+                                 const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u);
 template <typename Tc, typename TU>
 cudaError_t launch_mg_down(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                            const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u,

@@ -240,6 +240,81 @@ __global__ void __launch_bounds__(256) mg_smooth_kernel(const typename Cx<Tc>::t
 }
 
 // res = r - (sigma u + tau K u)
+// Gauss-Seidel sweep from zero in the natural order (x1 fastest): u_P = (r_P + sum over
+// the lower neighbours Q of w_PQ u_Q) / (sigma + d_P); the other neighbours are still
+// zero.  Points with equal index sum i1 + i2 (+ i3) do not depend on each other, so one
+// CTA per spectral plane walks these diagonals in order, a barrier between two (the
+// values of the previous diagonal come back through the CTA's own global writes).
+// This is the paper-reproduction option of the smoother; the red-black sweep is the
+// parallel default.
+template <typename Tc, typename TU, int DIM>
+__global__ void __launch_bounds__(256) mg_smooth_lex_kernel(const typename Cx<Tc>::t* __restrict__ r, TU* u,
+                                                            const Tc* __restrict__ w, const Tc* __restrict__ diag,
+                                                            const typename Cx<Tc>::t* __restrict__ sigma, int m,
+                                                            int64_t np) {
+  typedef typename Cx<Tc>::t C;
+  const int p = blockIdx.x;
+  const C sig = sigma[p];
+  const C* rp = r + (int64_t)p * np;
+  TU* up = u + (int64_t)p * np;
+  const int64_t mm = (int64_t)m * m;
+  const int tmax = DIM * (m - 1);
+  for (int t = 0; t <= tmax; ++t) {
+    if (DIM == 2) {
+      const int lo = max(0, t - (m - 1)), hi = min(m - 1, t);
+      for (int i2 = lo + (int)threadIdx.x; i2 <= hi; i2 += blockDim.x) {
+        const int i1 = t - i2;
+        const int64_t s = (int64_t)i2 * m + i1;
+        C acc = rp[s];
+        if (i1 > 0) {
+          const C v = ldc(up, s - 1);
+          const Tc wk = w[s];  // towards -x1
+          acc.x = fma(wk, v.x, acc.x);
+          acc.y = fma(wk, v.y, acc.y);
+        }
+        if (i2 > 0) {
+          const C v = ldc(up, s - m);
+          const Tc wk = w[2 * np + s];  // towards -x2
+          acc.x = fma(wk, v.x, acc.x);
+          acc.y = fma(wk, v.y, acc.y);
+        }
+        stc(up, s, cmul(acc, inv_diag<Tc>(sig, diag[s])));
+      }
+    } else {
+      // (i2, i3) pairs of the diagonal: i1 = t - i2 - i3 in [0, m)
+      const int lo3 = max(0, t - 2 * (m - 1)), hi3 = min(m - 1, t);
+      const int n3 = hi3 - lo3 + 1;
+      for (int q = (int)threadIdx.x; q < n3 * m; q += blockDim.x) {
+        const int i3 = lo3 + q / m, i2 = q - (q / m) * m;
+        const int i1 = t - i2 - i3;
+        if (i1 < 0 || i1 >= m) continue;
+        const int64_t s = (int64_t)i3 * mm + (int64_t)i2 * m + i1;
+        C acc = rp[s];
+        if (i1 > 0) {
+          const C v = ldc(up, s - 1);
+          const Tc wk = w[s];
+          acc.x = fma(wk, v.x, acc.x);
+          acc.y = fma(wk, v.y, acc.y);
+        }
+        if (i2 > 0) {
+          const C v = ldc(up, s - m);
+          const Tc wk = w[2 * np + s];
+          acc.x = fma(wk, v.x, acc.x);
+          acc.y = fma(wk, v.y, acc.y);
+        }
+        if (i3 > 0) {
+          const C v = ldc(up, s - mm);
+          const Tc wk = w[4 * np + s];  // towards -x3
+          acc.x = fma(wk, v.x, acc.x);
+          acc.y = fma(wk, v.y, acc.y);
+        }
+        stc(up, s, cmul(acc, inv_diag<Tc>(sig, diag[s])));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Residual after the red-black sweep from zero, from the sweep's identity: zero at
 // black points (their update solved their own equation) and sum_k w_k u_black at red
 // ones (the red update used zero neighbours).  One thread per red/black pair along x1.
@@ -538,9 +613,22 @@ cudaError_t launch_mg_smooth(Launch& L, const Grid& g, int planes, const Stencil
 }
 
 template <typename Tc, typename TU>
+cudaError_t launch_mg_smooth_lex(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
+                                 const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, TU* u) {
+  const double cs = 0.5 * (sizeof(typename Cx<Tc>::t) + sizeof(TU));
+  const double tot = (double)g.np * planes;
+  L.begin(KC_MG_SMOOTH);
+  if (g.dim == 2)
+    mg_smooth_lex_kernel<Tc, TU, 2><<<planes, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np);
+  else
+    mg_smooth_lex_kernel<Tc, TU, 3><<<planes, 256, 0, L.stream>>>(r, u, st.w, st.diag, sigma, g.m, g.np);
+  return L.end(KC_MG_SMOOTH, 2.0 * tot * cs, tot * (6.0 + 4.0 * g.dim));
+}
+
+template <typename Tc, typename TU>
 cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const Stencil<Tc>& st,
                                      const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, const TU* u,
-                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc) {
+                                     typename Cx<Tc>::t* res, typename Cx<Tc>::t* rc, bool rb_sweep) {
   const int pch = plane_chunk(L);
   const double cs = sizeof(typename Cx<Tc>::t);
   const int mc = (g.m - 1) / 2;
@@ -548,16 +636,21 @@ cudaError_t launch_mg_resid_restrict(Launch& L, const Grid& g, int planes, const
   const double tot = (double)g.np * planes;
   L.begin(KC_MG_RESID_RESTRICT);
   double rbytes = 3.0 * tot * cs;
+  bool done = false;
   if constexpr (std::is_same<TU, typename Cx<Tc>::t>::value) {
-    // u is the sweep from zero just made: its residual follows from the sweep's identity
-    const int64_t pairs = (g.np / g.m) * ((g.m + 1) / 2);
-    const dim3 pgrid((unsigned)((pairs + 255) / 256), (unsigned)((planes + pch - 1) / pch));
-    if (g.dim == 2)
-      mg_residual_pair_kernel<Tc, 2><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
-    else
-      mg_residual_pair_kernel<Tc, 3><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
-    rbytes = 2.0 * tot * cs;
-  } else {
+    if (rb_sweep) {
+      // u is the red-black sweep from zero just made: its residual follows from the sweep's identity
+      const int64_t pairs = (g.np / g.m) * ((g.m + 1) / 2);
+      const dim3 pgrid((unsigned)((pairs + 255) / 256), (unsigned)((planes + pch - 1) / pch));
+      if (g.dim == 2)
+        mg_residual_pair_kernel<Tc, 2><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
+      else
+        mg_residual_pair_kernel<Tc, 3><<<pgrid, 256, 0, L.stream>>>(u, res, st.w, g.m, g.np, planes, pch);
+      rbytes = 2.0 * tot * cs;
+      done = true;
+    }
+  }
+  if (!done) {
     if (g.dim == 2)
       mg_residual_kernel<Tc, TU, 2><<<plane_grid(g.np, planes, pch), 256, 0, L.stream>>>(r, u, res, st.w, st.diag,
                                                                                         sigma, g.m, g.np, planes, pch);
@@ -609,9 +702,11 @@ cudaError_t launch_mg_coarsest(Launch& L, int planes, const Tc* diag, const type
 #define PCOPT_INST_MG(Tc, TU)                                                                                    \
   template cudaError_t launch_mg_smooth<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&, const Cx<Tc>::t*, \
                                                 const Cx<Tc>::t*, TU*);                                             \
+  template cudaError_t launch_mg_smooth_lex<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&,              \
+                                                    const Cx<Tc>::t*, const Cx<Tc>::t*, TU*);                       \
   template cudaError_t launch_mg_resid_restrict<Tc, TU>(Launch&, const Grid&, int, const Stencil<Tc>&,           \
                                                         const Cx<Tc>::t*, const Cx<Tc>::t*, const TU*, Cx<Tc>::t*, \
-                                                        Cx<Tc>::t*);                                                \
+                                                        Cx<Tc>::t*, bool);                                          \
   template cudaError_t launch_mg_prolong<Tc, TU>(Launch&, const Grid&, int, const TU*, TU*);                     \
   template cudaError_t launch_mg_coarsest<Tc, TU>(Launch&, int, const Tc*, const Cx<Tc>::t*, const Cx<Tc>::t*,   \
                                                   TU*);

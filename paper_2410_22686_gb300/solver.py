@@ -18,6 +18,7 @@ _PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": ca
          "bf16s": capi.PC_PREC_MIXED_BF16S}
 _MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
 _SPACE = {"fd": capi.PC_SPACE_FD, "fe": capi.PC_SPACE_FE}
+_SMOOTHER = {"red-black": capi.PC_SMOOTHER_RED_BLACK, "lexicographic": capi.PC_SMOOTHER_LEXICOGRAPHIC}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -37,9 +38,12 @@ class Solver:
 
     def __init__(self, dim: int, m1: int, n: int, T: float, gamma: float, eps: float,
                  a_nodes: np.ndarray | None = None, spatial: str = "auto", precision: str = "fp64",
-                 max_iter: int = 60, tiles: str | dict | None = "table", space: str = "fd"):
+                 max_iter: int = 60, tiles: str | dict | None = "table", space: str = "fd",
+                 smoother: str = "red-black"):
         """space: "fd" finite differences (M = I) or "fe" bilinear / trilinear finite
         elements (mass matrix M; constant a, sine-transform solves).
+        smoother: Gauss-Seidel ordering of the multigrid pre-smoother, "red-black"
+        (parallel) or "lexicographic" (the natural order: the paper's Table 7 counts).
         tiles: "table" applies the stored autotune table's entry for this shape
         (if any), "auto" runs the autotuner now, a dict sets the shapes, None keeps
         the built-in defaults."""
@@ -50,7 +54,7 @@ class Solver:
         self.T, self.gamma, self.eps = T, gamma, eps
         self.max_iter = max_iter
         prm = capi.pc_params(dim, m1, n, T, gamma, eps, _SPATIAL[spatial], _PREC[precision], max_iter,
-                             _SPACE[space])
+                             _SPACE[space], _SMOOTHER[smoother])
         a_ptr = None
         if a_nodes is not None:
             self._a = np.ascontiguousarray(a_nodes, dtype=np.float64)

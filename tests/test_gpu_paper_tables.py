@@ -28,11 +28,11 @@ def _printed(value, printed):
     return abs(value - printed) <= 0.6 * unit
 
 
-def _gpu_example(ex, m1, n, gamma):
+def _gpu_example(ex, m1, n, gamma, smoother="red-black"):
     from paper_2410_22686_gb300 import Solver
     P = (S.example1_problem if ex == 1 else S.example2_problem)(m1, n, gamma)
     sol = Solver(2, m1, n, P.T, gamma, P.eps, P.a_nodes, spatial="fst" if ex == 1 else "mg",
-                 precision="fp64", max_iter=150)
+                 precision="fp64", max_iter=150, smoother=smoother)
     b = sol.build_rhs(torch.from_numpy(P.f).cuda(), torch.from_numpy(P.g).cuda(), torch.from_numpy(P.y0).cuda())
     _, it_paper_mode, _ = sol.solve(b, rtol=1e-8, mode="left")
     x, _, rel = sol.solve(b, rtol=1e-12, mode="right")
@@ -68,3 +68,12 @@ def test_gpu_reproduces_table7(row):
     iters, got = _gpu_example(2, 2 ** lh - 1, 2 ** lt - 1, gamma)
     assert _printed(got, eh), (got, eh)
     assert abs(iters - it) <= 3, (iters, it)
+
+
+@pytest.mark.parametrize("row", read_golden("table7_example2.txt"))
+def test_gpu_lexicographic_smoother_gives_table7_exactly(row):
+    # Gauss-Seidel in the natural order: every iteration count of Table 7, e_h to the printed digit
+    gamma, lh, lt, it, eh = float(row[0]), int(row[1]), int(row[2]), int(row[4]), float(row[5])
+    iters, got = _gpu_example(2, 2 ** lh - 1, 2 ** lt - 1, gamma, "lexicographic")
+    assert _printed(got, eh), (got, eh)
+    assert iters == it, (iters, it)

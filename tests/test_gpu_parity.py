@@ -356,3 +356,26 @@ def test_second_gram_schmidt_pass_runs_and_keeps_the_solution(precision, rtol, t
     xr = ref.x.reshape(b.shape)
     assert np.linalg.norm(x.cpu().numpy().reshape(b.shape) - xr) <= tol * np.linalg.norm(xr)
     sol.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n", [(2, 15, 16), (2, 31, 8), (2, 63, 4), (3, 7, 8), (2, 1, 2)])
+def test_lexicographic_smoother_precond_matches_oracle(d, m1, n, precision, tol):
+    """V(1,0) cycle with the Gauss-Seidel sweep in the natural order (one CTA per plane,
+    diagonal by diagonal) against the oracle's cycle with the same ordering."""
+    from paper_2410_22686_gb300 import Solver
+    a = _coef(d, m1, "var", seed=5 * m1 + n)
+    gamma, eps = 1e-4, 0.25
+    sol = Solver(d, m1, n, 1.0, gamma, eps, a, spatial="mg", precision=precision, max_iter=10,
+                 smoother="lexicographic")
+    v = S.random_vector((2, n) + (m1,) * d, 13)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    spat = opc.make_spatial_solver("mg", a, m1, d, tau, "lexicographic")
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, spat)
+    assert _rel(w, ref) <= tol
+    # and it differs from the red-black cycle (the option is really taken)
+    rb = opc.apply_Peps_inv(v, n, alpha, eps, opc.make_spatial_solver("mg", a, m1, d, tau))
+    if m1 > 1:
+        assert _rel(rb, ref) > 1e-6
+    sol.close()
