@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-fst", action="store_true")
+    ap.add_argument("--skip-graph", action="store_true")
     ap.add_argument("--batch-gb", type=float, default=110.0, help="device memory per batched wave (GB)")
     a = ap.parse_args()
     a.gammas = tuple(float(x) for x in a.gammas.split(","))
@@ -442,6 +443,24 @@ def run_ours(args):
     p_ms = ea.elapsed_time(eb) / reps
     precond_gbs = p_bytes / (p_ms * 1e-3) / 1e9
 
+    # ---------------- the same four solves, each one CUDA-graph launch (device-side stop)
+    graph_s = None
+    if not args.skip_graph:
+        xg = [torch.empty_like(b) for b in rhs]
+        for s, b, x in zip(sols, rhs, xg):  # capture and one replay each
+            s.solve_graph(b, x, rtol=RTOL, raise_on_nonconv=False)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record()
+        for s, b, x in zip(sols, rhs, xg):
+            s.solve_graph(b, x, rtol=RTOL, raise_on_nonconv=False)
+        gb.record()
+        torch.cuda.synchronize()
+        graph_s = whole_job_seconds_per_solve(dist_max(dist, ga.elapsed_time(gb), dev), 1, len(GAM), ws)
+        del xg
+
     # ---------------- end to end through host buffers (same metric)
     e2e_s = None
     if not args.skip_e2e:
@@ -526,7 +545,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": workload_config(args.m1, args.nt, GAM),
-        "fp64_solve_s": fp64_s, "mixed_solve_s": value,
+        "fp64_solve_s": fp64_s, "mixed_solve_s": value, "mixed_graph_solve_s": graph_s,
         "mixed_speedup_vs_fp64": (fp64_s / value) if fp64_s else None,
         "bf16_storage_solve_s": bf16_s, "iters_bf16_storage": iters_bf16,
         "iters_mixed": iters_mixed, "iters_fp64": iters64, "relres_mixed": relres_mixed,

@@ -281,12 +281,18 @@ int pc_sizes(const pc_handle* h, int64_t* ms, int64_t* vec_len);
  *            (default), 1 = register-marching warps (a warp walks the rows of one
  *            plane over a 64-column strip; neighbours by lane shuffles).
  *   mg_seg:  register-marching down leg: coarse rows per warp, 1..1024 (default 16).
+ *   fst_stream: sine-transform spatial solves, 0..3: persistent CTAs that copy
+ *            the next tile of grid lines into shared memory (cp.async) while
+ *            transforming the current one, for the single-axis passes (bit 0)
+ *            and for the fused last-axis pass with the spectral divide (bit 1);
+ *            one CTA per tile otherwise (default 0).
  * pc_set_tiles validates (PC_ERR_ARG), applies the shapes to every later call on
  * the handle and drops its cached solve graph.  pc_autotune times candidate
  * shapes on the handle's own workspace (the multigrid spatial step for each
  * (mg_cx, mg_ctas) and, with FP32 iterates, the register-marching kernel for each
- * mg_seg, then pro_pch; the forward + inverse time FFT for each
- * fft_stream; the matvec for each mv_tj), `reps` timed calls
+ * mg_seg, then pro_pch; with sine-transform solves the spatial step for each
+ * fst_stream; the forward + inverse time FFT for each fft_stream; the matvec
+ * for each mv_tj), `reps` timed calls
  * each (1..100) after one untimed call, keeps the fastest, applies it and copies
  * it to *chosen (may be NULL).  It synchronises `stream`, overwrites the
  * handle's Krylov and spectral workspace (not the caller's vectors) and must not
@@ -299,6 +305,7 @@ typedef struct pc_tiles {
   int fft_stream;
   int mg_march;
   int mg_seg;
+  int fst_stream;
 } pc_tiles;
 
 int pc_get_tiles(const pc_handle* h, pc_tiles* out);

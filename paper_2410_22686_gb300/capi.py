@@ -34,7 +34,7 @@ class pc_params(ctypes.Structure):
 class pc_tiles(ctypes.Structure):
     _fields_ = [("mg_cx", ctypes.c_int), ("mg_ctas", ctypes.c_int), ("mv_tj", ctypes.c_int),
                 ("pro_pch", ctypes.c_int), ("fft_stream", ctypes.c_int), ("mg_march", ctypes.c_int),
-                ("mg_seg", ctypes.c_int)]
+                ("mg_seg", ctypes.c_int), ("fst_stream", ctypes.c_int)]
 
 
 class pc_kernel_stat(ctypes.Structure):

@@ -1593,6 +1593,7 @@ static int check_tiles(const pc_tiles* t) {
   if (t->fft_stream < 0 || t->fft_stream > 1) return fail(PC_ERR_ARG, "fft_stream must be 0 or 1");
   if (t->mg_march < 0 || t->mg_march > 1) return fail(PC_ERR_ARG, "mg_march must be 0 or 1");
   if (t->mg_seg < 0 || t->mg_seg > 1024) return fail(PC_ERR_ARG, "mg_seg must be in [0, 1024]");
+  if (t->fst_stream < 0 || t->fst_stream > 3) return fail(PC_ERR_ARG, "fst_stream must be in [0, 3]");
   return PC_OK;
 }
 
@@ -1610,6 +1611,7 @@ extern "C" int pc_get_tiles(const pc_handle* h, pc_tiles* out) {
   out->fft_stream = h->tiles.fft_stream;
   out->mg_march = h->tiles.mg_march;
   out->mg_seg = h->tiles.mg_seg;
+  out->fst_stream = h->tiles.fst_stream;
   return PC_OK;
 }
 
@@ -1623,6 +1625,7 @@ extern "C" int pc_set_tiles(pc_handle* h, const pc_tiles* t) {
   h->tiles.fft_stream = t->fft_stream;
   h->tiles.mg_march = t->mg_march;
   h->tiles.mg_seg = t->mg_seg;
+  h->tiles.fst_stream = t->fst_stream;
   drop_graphs(h);  // a cached solve graph holds the old launch shapes
   return PC_OK;
 }
@@ -1722,6 +1725,20 @@ extern "C" int pc_autotune(pc_handle* h, int reps, pc_tiles* chosen, void* strea
           tbest = ms;
           best.pro_pch = t.pro_pch;
         }
+      }
+    }
+  }
+  // sine-transform solves: one CTA per line tile or persistent streaming CTAs
+  if (h->spatial == PC_SPATIAL_FST) {
+    double tbest = HUGE_VAL;
+    for (int mode = 0; mode < 4; ++mode) {
+      Tiles t = best;
+      t.fst_stream = mode;
+      Launch L{st, nullptr, &t};
+      const double ms = time_reps(st, reps, [&] { return spatial_for(h, L); });
+      if (ms < tbest) {
+        tbest = ms;
+        best.fst_stream = mode;
       }
     }
   }

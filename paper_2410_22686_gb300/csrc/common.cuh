@@ -175,6 +175,8 @@ struct Tiles {
   int fft_stream = 0;  // time FFTs: 0 one CTA per column tile, 1 persistent CTAs streaming tiles (cp.async)
   int mg_march = 0;    // fused 2D down leg with FP32 iterates: 0 shared-memory tiles, 1 register-marching warps
   int mg_seg = 0;      // register-marching down leg: coarse rows per warp segment (default 16)
+  int fst_stream = 0;  // sine transforms, persistent CTAs streaming tiles (cp.async) in: bit 0 the axis
+                       // passes, bit 1 the fused last-axis pass; one CTA per line tile otherwise
   int sms = 0;      // SMs of the device (set at setup)
 };
 

@@ -36,11 +36,16 @@ __device__ __forceinline__ int xidx(int k2, int j1, int c) {
   return (k2 * (N1 + 1) + j1) * COLS + c;
 }
 
-// One DST-I of every line of the tile in `sm` ([j][c], j < m, line index c fastest),
-// in place.  Ends with a barrier.  `sm` holds at least N2 (N1 + 1) COLS entries.
-template <typename Tc, int N1, int N2>
-__device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* __restrict__ tw, int m,
-                                         Tc half_scale, int r, int c) {
+// One DST-I of every line of the tile in `src` ([j][c], j < m, line index c
+// fastest); the result lands in `sm` with the same layout (src may be sm).  Ends
+// with a barrier.  `sm` holds at least N2 (N1 + 1) COLS entries.  after_read() runs
+// once every thread has read `src` (behind two barriers), between the first
+// exchange and the second register FFT: the persistent kernel refills `src` with
+// the next tile there.
+template <typename Tc, int N1, int N2, typename AfterRead>
+__device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* src,
+                                         const typename Cx<Tc>::t* __restrict__ tw, int m, Tc half_scale, int r,
+                                         int c, AfterRead&& after_read) {
   typedef typename Cx<Tc>::t C;
   constexpr int L = N1 * N2;
   constexpr int N = L / 2;
@@ -52,9 +57,9 @@ __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename 
     const int j = r + N1 * j2;
     C v = czero<Tc>();
     if (j > 0 && j < N) {
-      v = sm[(j - 1) * COLS + c];
+      v = src[(j - 1) * COLS + c];
     } else if (j > N) {
-      const C t = sm[(L - j - 1) * COLS + c];
+      const C t = src[(L - j - 1) * COLS + c];
       v = cmk<Tc>(-t.x, -t.y);
     }
     x[j2] = v;
@@ -67,6 +72,7 @@ __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename 
     sm[xidx<N1, COLS>(k2, r, c)] = y;
   }
   __syncthreads();
+  after_read();  // here no transform values are held in registers
   // (C) N1-point DFT over j1 for each k2, Y[k2 + N2 k1]; written as X_k = sqrt(2/N) (i/2) Y_k
   auto put = [&](int k, C y) {
     if (k >= 1 && k <= m) sm[(k - 1) * COLS + c] = cmk<Tc>(-y.y * half_scale, y.x * half_scale);
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
   }
   __syncthreads();
   const int r = tid / COLS, c = tid - (tid / COLS) * COLS;
-  dst_tile<Tc, N1, N2>(sm, tw, m, half_scale, r, c);
+  dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
   if (DIVIDE) {
     for (int e = tid; e < tot; e += 256) {
       const int j = e / COLS, cc = e - j * COLS;
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
       sm[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
     }
     __syncthreads();
-    dst_tile<Tc, N1, N2>(sm, tw, m, half_scale, r, c);
+    dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
   }
   for (int e = tid; e < tot; e += 256) {
     const int j = e / COLS, cc = e - j * COLS;
@@ -176,10 +182,107 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
   }
 }
 
+// Persistent streaming variant of fst4_kernel: each CTA walks tiles blockIdx.x,
+// + gridDim.x, ...; the next tile is copied into the stage with cp.async as soon as
+// the current one has been read into registers, so its load overlaps the transform,
+// the spectral divide and the stores of the current tile.  Shared memory: the
+// exchange area (N2 (N1 + 1) COLS entries) followed by the stage (m COLS entries).
+// in may equal out: tiles are disjoint sets of lines, and a tile is read whole
+// before any of it is written.
+template <typename Tc, int N1, int N2, bool DIVIDE>
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 256 ? 4 : N1 * N2 <= 512 ? 3 : 2) : 1) fst4s_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
+                                                   const typename Cx<Tc>::t* __restrict__ tw, int m, int64_t np,
+                                                   int64_t lstride, int64_t nlines, int ntiles, Tc half_scale,
+                                                   const Tc* __restrict__ lamK, const Tc* __restrict__ rmass,
+                                                   const typename Cx<Tc>::t* __restrict__ sigma) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char fst_smem[];
+  C* sm = reinterpret_cast<C*>(fst_smem);
+  C* stage = sm + N2 * (N1 + 1) * COLS;
+  __shared__ int64_t lbase[2][COLS];
+  __shared__ int lplane[2][COLS];
+  const int tid = threadIdx.x;
+  const int tot = COLS * m;
+  const int r = tid / COLS, c = tid - (tid / COLS) * COLS;
+  auto bases = [&](int tile, int slot) {  // threads < COLS: where the tile's lines start
+    if (tid < COLS) {
+      const int64_t l = (int64_t)tile * COLS + tid;
+      const int64_t lpp = np / m;
+      int64_t b = 0;
+      int p = 0;
+      if (l < nlines) {
+        p = (int)(l / lpp);
+        b = l - (int64_t)p * lpp;
+      }
+      const int64_t outer = b / lstride, inner = b - outer * lstride;
+      lbase[slot][tid] = (int64_t)p * np + outer * lstride * m + inner;
+      lplane[slot][tid] = l < nlines ? p : -1;
+    }
+  };
+  auto issue = [&](int slot) {  // the tile whose bases are in `slot` -> stage
+    for (int e = tid; e < tot; e += 256) {
+      const int j = e / COLS, cc = e - j * COLS;
+      const bool ok = lplane[slot][cc] >= 0;
+      cp_async<sizeof(C)>(stage + e, in + (ok ? lbase[slot][cc] + (int64_t)j * lstride : 0), ok);
+    }
+    cp_async_commit();
+  };
+  int tile = blockIdx.x, slot = 0;
+  if (tile < ntiles) bases(tile, 0);
+  __syncthreads();
+  if (tile < ntiles) issue(0);
+  for (; tile < ntiles; tile += gridDim.x, slot ^= 1) {
+    const int next = tile + (int)gridDim.x;
+    cp_async_wait<0>();
+    __syncthreads();  // the stage holds this tile; the previous tile's stores are done
+    if (next < ntiles) bases(next, slot ^ 1);
+    dst_tile<Tc, N1, N2>(sm, stage, tw, m, half_scale, r, c, [&] {
+      if (next < ntiles) issue(slot ^ 1);
+    });
+    if (DIVIDE) {
+      for (int e = tid; e < tot; e += 256) {
+        const int j = e / COLS, cc = e - j * COLS;
+        const int p = lplane[slot][cc];
+        if (p < 0) continue;
+        const int64_t s = lbase[slot][cc] - (int64_t)p * np + (int64_t)j * lstride;
+        C v = sm[e];
+        if (rmass) v = cscale(v, rmass[s]);
+        sm[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
+      }
+      __syncthreads();
+      dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
+    }
+    for (int e = tid; e < tot; e += 256) {
+      const int j = e / COLS, cc = e - j * COLS;
+      if (lplane[slot][cc] >= 0) out[lbase[slot][cc] + (int64_t)j * lstride] = sm[e];
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <typename Tc, int N1, int N2, bool DIVIDE>
+cudaError_t fst4s(Launch& L, const Grid& g, int64_t lstride, int64_t nlines, Tc hs, const typename Cx<Tc>::t* tw,
+                  const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
+                  typename Cx<Tc>::t* out) {
+  constexpr int COLS = 256 / N1;
+  const size_t smem = ((size_t)(N1 + 1) * N2 * COLS + (size_t)g.m * COLS) * sizeof(typename Cx<Tc>::t);
+  auto kern = fst4s_kernel<Tc, N1, N2, DIVIDE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess) return e;
+  const int ntiles = (int)((nlines + COLS - 1) / COLS);
+  const int sms = L.tiles && L.tiles->sms > 0 ? L.tiles->sms : 152;
+  const int grid = std::min(ntiles, std::max(1, per_sm) * sms);
+  kern<<<grid, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, ntiles, hs, lamK, rmass, sigma);
+  return cudaGetLastError();
+}
+
 template <typename Tc, int N1, int N2>
 cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, const typename Cx<Tc>::t* tw,
                  const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
-                 typename Cx<Tc>::t* out) {
+                 typename Cx<Tc>::t* out, bool stream) {
   constexpr int COLS = 256 / N1;
   const size_t smem = (size_t)(N1 + 1) * N2 * COLS * sizeof(typename Cx<Tc>::t);
   int64_t lstride = 1;
@@ -187,6 +290,11 @@ cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, co
   const int64_t nlines = (int64_t)planes * (g.np / g.m);
   const unsigned blocks = (unsigned)((nlines + COLS - 1) / COLS);
   const Tc hs = (Tc)(0.5 * std::sqrt(2.0 / (g.m + 1)));
+  if constexpr (sizeof(Tc) == 4 || N1 * N2 <= 256) {  // FP64 at L = 512 has no registers to spare
+    if (stream)
+      return divide ? fst4s<Tc, N1, N2, true>(L, g, lstride, nlines, hs, tw, lamK, rmass, sigma, in, out)
+                    : fst4s<Tc, N1, N2, false>(L, g, lstride, nlines, hs, tw, nullptr, nullptr, nullptr, in, out);
+  }
   cudaError_t e;
   if (divide) {
     e = cudaFuncSetAttribute(fst4_kernel<Tc, N1, N2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -219,6 +327,8 @@ cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool
   const double tot = (double)planes * (double)g.np;
   const double cs = sizeof(typename Cx<Tc>::t);
   const int kc = divide ? KC_FST_DIVIDE : KC_FST_AXIS;
+  // fst_stream bit 0: the axis passes stream tiles, bit 1: the fused last-axis pass does
+  const bool stream = L.tiles && (L.tiles->fst_stream & (divide ? 2 : 1));
   const double lg = std::log2((double)Lfft);
   // per line: (divide ? 2 : 1) complex FFTs of length 2(m+1)
   const double flops = (divide ? 2.0 : 1.0) * (tot / g.m) * 5.0 * Lfft * lg;
@@ -226,7 +336,7 @@ cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool
   cudaError_t e;
   switch (Lfft) {
 #define PCOPT_FST_CASE(LL, A, B) \
-  case LL: e = fst4<Tc, A, B>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out); break;
+  case LL: e = fst4<Tc, A, B>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream); break;
     PCOPT_FST_CASE(4, 2, 2)
     PCOPT_FST_CASE(8, 4, 2)
     PCOPT_FST_CASE(16, 4, 4)
@@ -238,7 +348,7 @@ cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool
 #undef PCOPT_FST_CASE
     case 1024:
       if constexpr (sizeof(Tc) == 4) {
-        e = fst4<Tc, 32, 32>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out);
+        e = fst4<Tc, 32, 32>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream);
         break;
       } else {
         return cudaErrorNotSupported;

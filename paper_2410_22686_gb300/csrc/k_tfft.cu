@@ -210,20 +210,6 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
 // the N1 thread rows of a CTA owns one j1 (then one k2) of COLS = 256/N1
 // spatial columns: two register FFTs and one shared-memory exchange instead of
 // log2(n) shared-memory radix-2 stages.
-// cp.async (sm_80+ asynchronous global -> shared copy, bypassing registers);
-// `ok == false` zero-fills the destination without reading global memory
-template <int B>
-__device__ __forceinline__ void cp_async(void* dst, const void* src, bool ok) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int sz = ok ? B : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(B), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Forward transform of one tile of COLS = 256 / N1 columns.  ld(j, a, b) gives
 // v1[j] and v2[j] of the thread's column (zero outside the grid).  Returns after
 // the spectrum stores; the caller's barrier orders the reuse of `sm`.

@@ -1,5 +1,6 @@
 // Radix-2 FFT of a small power-of-two length held in registers (one thread
-// owns the whole sequence), shared by the time FFTs and the sine transforms.
+// owns the whole sequence) and the cp.async helpers, shared by the time FFTs and
+// the sine transforms.
 #pragma once
 
 #include "common.cuh"
@@ -45,6 +46,21 @@ __device__ __forceinline__ void reg_fft(C (&x)[R], const C* __restrict__ tw, int
       }
     }
   }
+}
+
+// cp.async (sm_80+ asynchronous global -> shared copy of B = 4, 8 or 16 bytes,
+// bypassing registers); `ok == false` zero-fills the destination without reading
+// global memory
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = ok ? B : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(B), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 }  // namespace pcopt

@@ -88,6 +88,21 @@ def test_fe_precond_apply_matches_oracle(d, m1, n, precision, tol):
     sol.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n", [(2, 255, 64), (3, 31, 16), (2, 15, 24)])
+def test_fe_streaming_sine_transform_precond_matches_oracle(d, m1, n, precision, tol):
+    """Persistent streaming sine transforms (several tiles per CTA at 255^2 x 66 planes)
+    with the mass-matrix eigenvalues in the spectral divide."""
+    gamma, eps = 1e-4, 0.25
+    sol = _solver(d, m1, n, precision=precision, gamma=gamma, eps=eps, tiles={"fst_stream": 3})
+    v = S.random_vector((2, n) + (m1,) * d, 17)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, fe.FSTSpatialSolverFE(m1, d, tau))
+    assert _rel(w, ref) <= tol
+    sol.close()
+
+
 def _oracle_fe_solution(P, rtol=1e-13):
     M, K = fe.fe_matrices(P.m1, P.d)
     alpha = osy.alpha_weight(P.T, P.n, P.gamma)

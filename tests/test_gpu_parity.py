@@ -108,6 +108,30 @@ def test_precond_apply_matches_oracle(d, m1, n, kind, spatial, precision, tol):
     sol.close()
 
 
+# Persistent streaming sine transforms (tile shape fst_stream: bit 0 the axis passes,
+# bit 1 the fused last-axis pass with the spectral divide): a CTA per SM walks
+# several line tiles (255^2 x 66 planes, 63^2 x 258 planes, 31^3 x 66 planes), at most
+# one tile per CTA (127^2, 15^3) and every power-of-two length 2(m1+1) from 4 to 512
+STREAM_FST_CASES = [(2, 255, 64), (2, 63, 256), (3, 31, 64), (2, 127, 8), (3, 15, 4), (2, 1, 4), (2, 3, 2),
+                    (2, 7, 16), (2, 31, 32)]
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n", STREAM_FST_CASES)
+def test_streaming_sine_transform_precond_matches_oracle(d, m1, n, precision, tol, mode):
+    gamma, eps = 1e-4, 0.25
+    sol = _solver(d, m1, n, None, "fst", precision=precision, gamma=gamma, eps=eps)
+    sol.set_tiles(fst_stream=mode)
+    assert sol.get_tiles()["fst_stream"] == mode
+    v = S.random_vector((2, n) + (m1,) * d, 13)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, opc.make_spatial_solver("fst", None, m1, d, tau))
+    assert _rel(w, ref) <= tol
+    sol.close()
+
+
 def _oracle_solution(prob, spatial, rtol=1e-13):
     a = _a_or_one(prob.a_nodes, prob.d, prob.m1)
     tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, prob.gamma)

@@ -11,6 +11,8 @@ def test_fields_match_the_c_struct():
 def test_key_normalises_precision_aliases():
     assert tuning.key(2, 255, 256, "fp32") == tuning.key(2, 255, 256, "mixed") == "2d_m255_n256_mixed"
     assert tuning.key(3, 63, 128, "bf16s") == "3d_m63_n128_bf16s"
+    assert tuning.key(2, 255, 256, "fp32", "fst") == "2d_m255_n256_mixed_fst"
+    assert tuning.key(2, 255, 256, "fp64", "mg") == "2d_m255_n256_fp64"
 
 
 def test_lookup_reads_entries(tmp_path, monkeypatch):
@@ -22,6 +24,7 @@ def test_lookup_reads_entries(tmp_path, monkeypatch):
     assert tuning.lookup(2, 15, 16, "fp64") == {"mg_cx": 8, "mg_ctas": 4, "mv_tj": 16, "pro_pch": 2,
                                                 "fft_stream": 1, "mg_march": 1, "mg_seg": 8}
     assert tuning.lookup(2, 15, 32, "fp64") is None
+    assert tuning.lookup(2, 15, 16, "fp64", "fst") is None  # sine-transform shapes are keyed apart
 
 
 def test_missing_table_is_empty(tmp_path):
@@ -31,7 +34,7 @@ def test_missing_table_is_empty(tmp_path):
 def test_workloads_cover_the_bench_shapes():
     keys = {tuning.key(*w) for w in tuning.WORKLOADS}
     for k in ("2d_m255_n256_mixed", "2d_m255_n256_fp64", "2d_m255_n256_bf16s", "3d_m63_n128_mixed",
-              "2d_m127_n128_fp64"):
+              "2d_m127_n128_fp64", "2d_m31_n32_fp64_fst", "2d_m255_n256_mixed_fst", "2d_m255_n256_fp64_fst"):
         assert k in keys
 
 
@@ -42,3 +45,4 @@ def test_stored_table_is_well_formed():
         assert e["mg_cx"] in (0, 8, 16)
         assert 0 <= e["mg_ctas"] <= 64 and 0 <= e["mv_tj"] <= 4096 and 0 <= e["pro_pch"] <= 64
         assert e["fft_stream"] in (0, 1)
+        assert e.get("fst_stream", 0) in (0, 1, 2, 3)
