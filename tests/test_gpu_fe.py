@@ -176,11 +176,13 @@ def test_fe_unsupported_requests_fail_loudly():
     sol.close()
 
 
-def test_fe_full_size_operators_match_oracle():
+@pytest.mark.parametrize("fst_stream", [0, 1], ids=["tiles", "stream"])
+def test_fe_full_size_operators_match_oracle(fst_stream):
     """255^2 grid, n = 256 (the size the finite-element solve is timed on): the whole
-    product (FP64 and FP32 input) and the FP32 preconditioner against the oracle."""
+    product (FP64 and FP32 input) and the FP32 preconditioner against the oracle, with
+    the sine-transform axis passes as one CTA per tile or as persistent streaming CTAs."""
     d, m1, n, gamma, eps = 2, 255, 256, 1e-2, 0.5
-    sol = _solver(d, m1, n, precision="mixed", gamma=gamma, eps=eps)
+    sol = _solver(d, m1, n, precision="mixed", gamma=gamma, eps=eps, max_iter=4, tiles={"fst_stream": fst_stream})
     M, K = fe.fe_matrices(m1, d)
     tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
     x = S.random_vector((2, n) + (m1,) * d, 21)
