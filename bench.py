@@ -423,8 +423,11 @@ def run_ours(args):
     # whole job: every rank runs its own replica of the four solves (weak scaling)
     value = whole_job_seconds_per_solve(ms_mixed, args.steps, len(GAM), ws)
 
-    # precond-apply GB/s (mixed): the apply alone, on the same handle and launch configuration
+    # the Givens residual estimates of the last timed solve at the second gamma
     s0 = sols[min(1, len(sols) - 1)]
+    history = [float(f"{r:.3e}") for r in s0.residual_history()]
+
+    # precond-apply GB/s (mixed): the apply alone, on the same handle and launch configuration
     v = torch.randn(U, dtype=torch.float64, device=dev)
     w = torch.empty_like(v)
     for _ in range(3):
@@ -549,6 +552,7 @@ def run_ours(args):
         "mixed_speedup_vs_fp64": (fp64_s / value) if fp64_s else None,
         "bf16_storage_solve_s": bf16_s, "iters_bf16_storage": iters_bf16,
         "iters_mixed": iters_mixed, "iters_fp64": iters64, "relres_mixed": relres_mixed,
+        "residual_history_mixed": {"gamma": GAM[min(1, len(GAM) - 1)], "estimates": history},
         "unknowns_iters_per_s": ws * sum(U * it for it in iters_mixed) / (ms_mixed / 1000.0 / args.steps),
         "precond_apply": {"gbs": precond_gbs, "ms": p_ms, "frac_of_hbm": precond_gbs / hbm_peak,
                           "bytes": p_bytes, "precision": "fp32"},

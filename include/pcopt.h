@@ -175,6 +175,18 @@ int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y
 int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit,
                    int mode, int* iters, double* relres, void* stream);
 
+/* Residual history of the handle's last solve (pc_gmres_solve, pc_adjoint_solve,
+ * pc_gmres_solve_graph or its batch): out[0] = initial relative residual, out[i]
+ * = the GMRES least-squares estimate ||r_i|| / ||b|| after iteration i (RIGHT:
+ * of the true residual in exact arithmetic; LEFT: of the preconditioned one),
+ * i.e. out[0] times the product of the first i Givens sines, non-increasing.
+ *   out: HOST array of cap entries; *count (HOST) = entries written, min(cap,
+ *   iterations + 1); 0 before any solve, or after one that failed before its
+ *   first residual.  Copies the sines from the device on `stream` and
+ *   synchronises it.
+ * Errors: PC_ERR_ARG (null h or count, cap < 0, out NULL with cap > 0). */
+int pc_residual_history(pc_handle* h, double* out, int cap, int* count, void* stream);
+
 /* The same right-preconditioned (flexible) GMRES solve from a zero initial
  * guess, run as ONE CUDA-graph launch: the iteration is the body of a graph
  * WHILE node whose condition a kernel sets on the device from the residual

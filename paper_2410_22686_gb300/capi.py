@@ -67,6 +67,7 @@ _SIGNATURES = {
     "pc_build_rhs": (_i, [_vp, _dp, _dp, _dp, _dp, _vp]),
     "pc_gmres_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
     "pc_gmres_solve_graph": (_i, [_vp, _dp, _dp, _d, _i, _ip, _dpp, _vp]),
+    "pc_residual_history": (_i, [_vp, _dpp, _i, _ip, _vp]),
     "pc_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
                              ctypes.POINTER(_vp)]),
     "pc_batch_solve": (_i, [_vp, _ip, _dpp, _vp]),

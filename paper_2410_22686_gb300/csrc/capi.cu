@@ -214,6 +214,8 @@ struct pc_handle {
   double* partial = nullptr;
   int nblocks = 0;         // rows of `partial`: SMs x blocks per SM
   double* host = nullptr;  // pinned, mapped: [0] est, [1] ref, [2] nrm2, ... (16 doubles) + 4 ints
+  int last_k = -1;          // iterations of the last solve (-1: none yet)
+  double last_res0 = 0.0;   // its initial relative residual (history entry 0)
   double* host_dev = nullptr;  // device view of `host`
   std::vector<void*> allocs;
   Prof prof;
@@ -1112,6 +1114,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   if (mode != PC_GMRES_RIGHT && mode != PC_GMRES_LEFT) return fail(PC_ERR_ARG, "gmres: unknown mode");
   if (mode == PC_GMRES_LEFT && h->fp32) return fail(PC_ERR_ARG, "gmres: LEFT mode needs the FP64 preconditioner");
   Launch L{st, &h->prof, &h->tiles};
+  h->last_k = -1;
   const size_t U = h->U;
   const int ldh = h->cap + 1;
   double* nrm2 = h->scal + 0;
@@ -1159,6 +1162,8 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   }
   double est_h = 0, ref_h = 0;
   if (int rc = read_scalars(h, st, &est_h, &ref_h)) return rc;
+  h->last_res0 = ref_h == 0.0 ? 0.0 : est_h;
+  h->last_k = 0;
   if (ref_h == 0.0) {
     // b == 0 (or P^{-1}b == 0): the solution is x = 0
     PC_CUDA(cudaMemsetAsync(x, 0, U * sizeof(double), st));
@@ -1215,6 +1220,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       h->prof.launches[KC_REORTH]++;
     }
     k = j + 1;
+    h->last_k = k;
     if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite residual estimate");
     if (est_h <= rtol) {
       converged = true;
@@ -1243,6 +1249,27 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   if (relres) *relres = est_h;
   if (!std::isfinite(est_h)) return fail(PC_ERR_BREAKDOWN, "gmres: non-finite final residual");
   if (!converged) return fail(PC_ERR_NOT_CONVERGED, "gmres: maxit reached before rtol");
+  return PC_OK;
+}
+
+// residual estimates of the last solve: |g_{i}| / ref = res_0 * prod_{q < i} |s_q|, with
+// the sines s_q of the Givens rotations (the rotated right-hand side itself is
+// overwritten by later rotations)
+extern "C" int pc_residual_history(pc_handle* h, double* out, int cap, int* count, void* stream) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return fail(PC_ERR_ARG, "pc_residual_history: bad argument");
+  *count = 0;
+  if (h->last_k < 0) return PC_OK;
+  const int k = h->last_k;
+  const int nout = std::min(cap, k + 1);
+  *count = nout;
+  if (nout == 0) return PC_OK;
+  out[0] = h->last_res0;
+  if (nout == 1) return PC_OK;
+  std::vector<double> sn((size_t)nout - 1);
+  cudaStream_t st = (cudaStream_t)stream;
+  PC_CUDA(cudaMemcpyAsync(sn.data(), h->sn, sn.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaStreamSynchronize(st));
+  for (int i = 1; i < nout; ++i) out[i] = out[i - 1] * std::fabs(sn[(size_t)i - 1]);
   return PC_OK;
 }
 
@@ -1395,6 +1422,8 @@ static int graph_results(pc_handle* h, cudaStream_t st, double rtol, int* iters,
   const int kdone = (int)h->host[3];
   const double ref = h->host[1], r2 = h->host[2];
   const double rr = ref > 0 ? std::sqrt(r2) / ref : 0.0;
+  h->last_k = kdone;
+  h->last_res0 = ref > 0 ? 1.0 : 0.0;  // zero initial guess
   if (iters) *iters = kdone;
   if (relres) *relres = rr;
   if (ref == 0.0) return PC_OK;  // b = 0: x = 0 is exact
@@ -1409,6 +1438,7 @@ extern "C" int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, do
   if (!(rtol > 0)) return fail(PC_ERR_ARG, "pc_gmres_solve_graph: rtol must be > 0");
   if (int rc = graph_supported(h, maxit)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_k = -1;
   if (!h->gexec || h->g_b != b || h->g_x != x || h->g_rtol != rtol || h->g_maxit != maxit) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -1512,6 +1542,7 @@ extern "C" int pc_batch_create(pc_handle* const* hs, int count, const double* co
 extern "C" int pc_batch_solve(pc_batch* bt, int* iters, double* relres, void* stream) {
   if (!bt) return fail(PC_ERR_ARG, "pc_batch_solve: null batch");
   cudaStream_t st = (cudaStream_t)stream;
+  for (pc_handle* h : bt->hs) h->last_k = -1;
   GR_CUDA(cudaGraphLaunch(bt->exec, st));
   int worst = PC_OK;
   for (size_t i = 0; i < bt->hs.size(); ++i) {

@@ -179,6 +179,15 @@ class Solver:
             capi.check(st)
         return x, it.value, rr.value
 
+    def residual_history(self, cap: int | None = None) -> list:
+        """Relative residual estimates of the last solve on this handle: entry 0 the
+        initial one, entry i the GMRES estimate after iteration i (non-increasing)."""
+        cap = (self.max_iter + 1) if cap is None else cap
+        out = (ctypes.c_double * max(cap, 1))()
+        cnt = ctypes.c_int(0)
+        capi.check(self.lib.pc_residual_history(self.h, out, cap, ctypes.byref(cnt), _stream()))
+        return [out[i] for i in range(cnt.value)]
+
     def solve_host(self, b_host, x_host=None, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):
         """Solve from a HOST right-hand side: copy b to the device, run GMRES,
         copy x back into ``x_host`` (pinned CPU tensors give asynchronous copies).

@@ -38,6 +38,49 @@ def test_graph_solve_equals_host_driven_solve(precision):
     sol.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16s"])
+def test_solves_are_bitwise_reproducible(precision):
+    """Fixed grids and fixed reduction orders: the same solve twice gives the same bits
+    (host-driven and graph-launched), and so do two preconditioner applies."""
+    prob = S.variable_2d_problem(gamma=1e-4, m1=63, n=64)
+    sol, b = _make(prob, precision)
+    x1, it1, r1 = sol.solve(b, rtol=1e-8)
+    x2, it2, r2 = sol.solve(b, rtol=1e-8)
+    assert (it1, r1) == (it2, r2) and torch.equal(x1, x2)
+    g1 = sol.solve_graph(b, rtol=1e-8)[0].clone()
+    g2 = sol.solve_graph(b, rtol=1e-8)[0]
+    assert torch.equal(g1, g2)
+    w1, w2 = sol.apply_precond(b), sol.apply_precond(b)
+    assert torch.equal(w1, w2)
+    sol.close()
+
+
+def test_residual_history_of_host_graph_and_batch_solves():
+    """The history is the Givens estimate after every iteration: starts at 1 (zero
+    initial guess), never increases, ends at or below rtol, one entry per iteration
+    plus the start; host-driven, graph and batched solves give the same history (to
+    1e-4: the two paths round the mixed-precision iteration differently, ~1e-6 relative
+    in the last estimates)."""
+    from paper_2410_22686_gb300 import Batch
+    prob = S.variable_2d_problem(gamma=1e-6, m1=63, n=64)
+    sol, b = _make(prob, "fp32")
+    assert sol.residual_history() == []  # no solve yet
+    x, it, rr = sol.solve(b, rtol=1e-8)
+    h1 = np.array(sol.residual_history())
+    assert len(h1) == it + 1 and h1[0] == 1.0
+    assert np.all(np.diff(h1) <= 0) and h1[-1] <= 1e-8 < h1[-2]
+    assert len(sol.residual_history(cap=3)) == 3
+    xg, itg, _ = sol.solve_graph(b, rtol=1e-8)
+    h2 = np.array(sol.residual_history())
+    assert itg == it and np.allclose(h2, h1, rtol=1e-4, atol=0)
+    bt = Batch([sol], [b], rtol=1e-8, maxit=60)
+    itb, _ = bt.solve()
+    h3 = np.array(sol.residual_history())
+    assert itb[0] == it and np.allclose(h3, h1, rtol=1e-4, atol=0)
+    bt.close()
+    sol.close()
+
+
 def test_batch_of_uneven_problems_matches_individual_solves_and_oracle():
     from paper_2410_22686_gb300 import Batch
     probs = [S.variable_2d_problem(gamma=1e-2, m1=15, n=16), S.variable_2d_problem(gamma=1e-6, m1=31, n=64),

@@ -179,6 +179,21 @@ def test_iteration_counts_match_oracle_left_and_right(gamma):
     sol.close()
 
 
+@pytest.mark.parametrize("mode", ["right", "left"])
+def test_residual_history_matches_oracle(mode):
+    # the Givens estimates after every iteration, FP64 path against the oracle's GMRES
+    prob = S.variable_2d_problem(gamma=1e-4, m1=31, n=32)
+    b, A, Pi, _ = _oracle_solution(prob, "mg")
+    ref = okr.gmres(A, Pi, b, rtol=1e-8, maxit=100, mode=mode)
+    sol = _solver(2, 31, 32, prob.a_nodes, "mg", gamma=prob.gamma, eps=prob.eps, max_iter=60)
+    x, iters, rel = sol.solve(_dev(b), rtol=1e-8, mode=mode)
+    h, r = np.array(sol.residual_history()), np.array(ref.resid_history)
+    assert len(h) == iters + 1 == len(r)
+    assert np.all(np.abs(h - r) <= 1e-6 * r)
+    assert np.all(np.diff(h) <= 0) and h[-1] <= 1e-8 < h[-2]
+    sol.close()
+
+
 def test_gmres_kth_iterate_matches_oracle():
     # equal fixed iteration count: the iterates agree to 1e-10 (both FP64)
     prob = S.variable_2d_problem(gamma=1e-4, m1=15, n=16)
