@@ -5,16 +5,26 @@
 //
 // With N = m + 1 a power of two, the orthonormal DST-I of a line x_1..x_m,
 //   X_k = sqrt(2/N) sum_j x_j sin(pi j k / N),
-// is read off the length-L = 2N FFT of the odd extension y (y_0 = y_N = 0,
-// y_j = x_j, y_{L-j} = -x_j): Y_k = -2i sum_j x_j sin(pi j k / N), so
-// X_k = sqrt(2/N) (i/2) Y_k.  The transform is its own inverse.
+// is its own inverse.  Two ways to get it from an FFT:
+//  * half length (N >= 8, used in practice): with x_0 = x_N = 0 form
+//      y_j = sin(pi j / N) (x_j + x_{N-j}) + (x_j - x_{N-j}) / 2,  j = 0..N-1,
+//    and its N-point FFT Y.  Splitting y into the part symmetric under j -> N-j
+//    and the antisymmetric part gives, for real x, X_{2q} = -Im Y_q and
+//    X_{2q+1} - X_{2q-1} = Re Y_q; written with Y_{N-q} instead of conjugates,
+//      X_{2q} = (i/2) (Y_q - Y_{N-q}),   X_{2q+1} = Y_0 / 2 + sum_{p=1..q} (Y_p + Y_{N-p}) / 2,
+//    which is linear in x and so holds for complex lines too.  The odd outputs
+//    are a prefix sum, taken in chunks per thread plus one pass over the chunk
+//    totals (error growth ~ (chunk + threads per line) u, not N u);
+//  * odd extension (N < 8): the length-L = 2N FFT of y (y_0 = y_N = 0, y_j = x_j,
+//    y_{L-j} = -x_j) is Y_k = -2i sum_j x_j sin(pi j k / N), so
+//    X_k = sqrt(2/N) (i/2) Y_k: twice the FFT length of the first way.
 //
 // One CTA of 256 threads owns COLS = 256/N1 grid lines along the axis:
 //  * the tile (m values of each line) is copied into shared memory with the
 //    line index fastest, so a warp reads whole 32-byte sectors for every axis
 //    (along x1 four consecutive values of each of eight lines, along x2/x3
 //    consecutive lines) and the shared-memory accesses are conflict-free;
-//  * the L-point FFT is the four-step split L = N1 N2 of the time FFT: an
+//  * the FFT (N or L points) is the four-step split N1 N2 of the time FFT: an
 //    N2-point register FFT per thread row, a twiddle, one shared-memory
 //    exchange, an N1-point register FFT;
 //  * the results go back through shared memory and out with the same pattern.
@@ -123,12 +133,107 @@ __device__ __forceinline__ void dst_tile(typename Cx<Tc>::t* sm, const typename 
   __syncthreads();
 }
 
+// The half-length DST-I (file header) of every line of the tile in `src` into `sm`,
+// N = N1 N2 = m + 1 >= 8, with the twiddle table of length 2N: the N-point FFT uses
+// tw[2q] and sin(pi j / N) = -Im tw[j].  `scale` = sqrt(2/N).  Same contract as
+// dst_tile: ends with a barrier; after_read() runs behind two barriers after every
+// read of `src`, when no transform values are held in registers.
+template <typename Tc, int N1, int N2, typename AfterRead>
+__device__ __forceinline__ void dsth_tile(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* src,
+                                          const typename Cx<Tc>::t* __restrict__ tw, int m, Tc scale, int r, int c,
+                                          AfterRead&& after_read) {
+  typedef typename Cx<Tc>::t C;
+  constexpr int N = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  constexpr int Q = N / 2 / N1;  // odd outputs per thread row
+  static_assert(Q >= 1, "N must be at least 2 N1");
+  __shared__ C tot[N1 * COLS];  // chunk totals of the prefix sum
+  // (A) rows j = r + N1 j2 of y, N2-point DFT over j2
+  C x[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    const int j = r + N1 * j2;
+    const C a = (j >= 1) ? src[(j - 1) * COLS + c] : czero<Tc>();       // x_j (j <= N - 1 = m)
+    const C b = (j >= 1) ? src[(N - j - 1) * COLS + c] : czero<Tc>();   // x_{N-j}; x_N = 0 when j = 0
+    const Tc sj = -tw[j].y;
+    const Tc h = Tc(0.5);
+    x[j2] = cmk<Tc>(sj * (a.x + b.x) + h * (a.x - b.x), sj * (a.y + b.y) + h * (a.y - b.y));
+  }
+  __syncthreads();  // every read of the tile is done before the exchange overwrites it
+  reg_fft<N2, false>(x, tw, 2 * N1);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const C y = (k2 == 0 || r == 0) ? x[k2] : cmul(tw[2 * r * k2], x[k2]);
+    sm[xidx<N1, COLS>(k2, r, c)] = y;
+  }
+  __syncthreads();
+  after_read();  // here no transform values are held in registers
+  // (C) row k2 = r (< N2): N1-point DFT over j1 -> Y[k2 + N2 k1], stored as [k][c]
+  {
+    C y[N1];
+    if (r < N2) {
+#pragma unroll
+      for (int j1 = 0; j1 < N1; ++j1) y[j1] = sm[xidx<N1, COLS>(r, j1, c)];
+    }
+    __syncthreads();
+    if (r < N2) {
+      reg_fft<N1, false>(y, tw, 2 * N2);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) sm[(r + N2 * k1) * COLS + c] = y[k1];
+    }
+  }
+  __syncthreads();
+  // outputs: thread row r owns q = r Q .. r Q + Q - 1 (odd outputs 2q + 1, even 2q)
+  C ev[Q], od[Q];
+  C run = czero<Tc>();
+  const Tc hs = Tc(0.5) * scale;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int q = r * Q + i;
+    const C yq = sm[q * COLS + c];
+    const C ym = sm[((N - q) & (N - 1)) * COLS + c];
+    ev[i] = cmk<Tc>(-(yq.y - ym.y) * hs, (yq.x - ym.x) * hs);  // (i/2)(Y_q - Y_{N-q}) scale
+    const Tc w = q == 0 ? Tc(0.25) * scale : hs;
+    run = cmk<Tc>(run.x + (yq.x + ym.x) * w, run.y + (yq.y + ym.y) * w);
+    od[i] = run;
+  }
+  tot[r * COLS + c] = run;
+  __syncthreads();  // every Y read and every chunk total are in
+  C off = czero<Tc>();
+  for (int rr = 0; rr < r; ++rr) off = off + tot[rr * COLS + c];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int q = r * Q + i;
+    sm[(2 * q) * COLS + c] = off + od[i];                // X_{2q+1} at index 2q
+    if (q >= 1) sm[(2 * q - 1) * COLS + c] = ev[i];      // X_{2q} at index 2q - 1
+  }
+  __syncthreads();
+}
+
 // DIVIDE: forward DST, sm *= rmass / (sigma_p + lamK), inverse DST (the last axis).
 // in may equal out: a CTA reads its whole tile before it writes it back.
 // Lines: plane p = line / (np / m); inside the plane, a line along `axis` starts at
 // outer * m * lstride + inner with lstride = m^axis, inner < lstride.
-template <typename Tc, int N1, int N2, bool DIVIDE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2) : 1) fst4_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
+// one line-tile DST of the kind HALF selects (dsth_tile or dst_tile)
+template <typename Tc, int N1, int N2, bool HALF, typename AfterRead>
+__device__ __forceinline__ void dst_any(typename Cx<Tc>::t* sm, const typename Cx<Tc>::t* src,
+                                        const typename Cx<Tc>::t* __restrict__ tw, int m, Tc scale, int r, int c,
+                                        AfterRead&& after_read) {
+  if constexpr (HALF)
+    dsth_tile<Tc, N1, N2>(sm, src, tw, m, scale, r, c, after_read);
+  else
+    dst_tile<Tc, N1, N2>(sm, src, tw, m, scale, r, c, after_read);
+}
+
+// CTAs per SM the kernels are compiled for (registers per thread = 65536 / (256 x it))
+template <typename Tc, int NP, bool STREAM>
+constexpr int fst_min_blocks() {
+  if constexpr (sizeof(Tc) == 4) return NP <= 256 ? (STREAM ? 3 : 4) : 2;
+  return (NP <= 256 && !STREAM) ? 2 : 1;
+}
+
+template <typename Tc, int N1, int N2, bool DIVIDE, bool HALF>
+__global__ void __launch_bounds__(256, fst_min_blocks<Tc, N1 * N2, false>()) fst4_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
                                                    const typename Cx<Tc>::t* __restrict__ tw, int m, int64_t np,
                                                    int64_t lstride, int64_t nlines, Tc half_scale,
                                                    const Tc* __restrict__ lamK, const Tc* __restrict__ rmass,
@@ -162,7 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
   }
   __syncthreads();
   const int r = tid / COLS, c = tid - (tid / COLS) * COLS;
-  dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
+  dst_any<Tc, N1, N2, HALF>(sm, sm, tw, m, half_scale, r, c, [] {});
   if (DIVIDE) {
     for (int e = tid; e < tot; e += 256) {
       const int j = e / COLS, cc = e - j * COLS;
@@ -174,7 +279,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
       sm[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
     }
     __syncthreads();
-    dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
+    dst_any<Tc, N1, N2, HALF>(sm, sm, tw, m, half_scale, r, c, [] {});
   }
   for (int e = tid; e < tot; e += 256) {
     const int j = e / COLS, cc = e - j * COLS;
@@ -189,8 +294,8 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 512 ? 4 : 2
 // exchange area (N2 (N1 + 1) COLS entries) followed by the stage (m COLS entries).
 // in may equal out: tiles are disjoint sets of lines, and a tile is read whole
 // before any of it is written.
-template <typename Tc, int N1, int N2, bool DIVIDE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 256 ? 4 : N1 * N2 <= 512 ? 3 : 2) : 1) fst4s_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
+template <typename Tc, int N1, int N2, bool DIVIDE, bool HALF>
+__global__ void __launch_bounds__(256, fst_min_blocks<Tc, N1 * N2, true>()) fst4s_kernel(const typename Cx<Tc>::t* in, typename Cx<Tc>::t* out,
                                                    const typename Cx<Tc>::t* __restrict__ tw, int m, int64_t np,
                                                    int64_t lstride, int64_t nlines, int ntiles, Tc half_scale,
                                                    const Tc* __restrict__ lamK, const Tc* __restrict__ rmass,
@@ -237,7 +342,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 256 ? 4 : N
     cp_async_wait<0>();
     __syncthreads();  // the stage holds this tile; the previous tile's stores are done
     if (next < ntiles) bases(next, slot ^ 1);
-    dst_tile<Tc, N1, N2>(sm, stage, tw, m, half_scale, r, c, [&] {
+    dst_any<Tc, N1, N2, HALF>(sm, stage, tw, m, half_scale, r, c, [&] {
       if (next < ntiles) issue(slot ^ 1);
     });
     if (DIVIDE) {
@@ -251,7 +356,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 256 ? 4 : N
         sm[e] = cmul(v, inv_diag<Tc>(sigma[p], lamK[s]));
       }
       __syncthreads();
-      dst_tile<Tc, N1, N2>(sm, sm, tw, m, half_scale, r, c, [] {});
+      dst_any<Tc, N1, N2, HALF>(sm, sm, tw, m, half_scale, r, c, [] {});
     }
     for (int e = tid; e < tot; e += 256) {
       const int j = e / COLS, cc = e - j * COLS;
@@ -261,13 +366,13 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? (N1 * N2 <= 256 ? 4 : N
   cp_async_wait<0>();
 }
 
-template <typename Tc, int N1, int N2, bool DIVIDE>
+template <typename Tc, int N1, int N2, bool DIVIDE, bool HALF>
 cudaError_t fst4s(Launch& L, const Grid& g, int64_t lstride, int64_t nlines, Tc hs, const typename Cx<Tc>::t* tw,
                   const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
                   typename Cx<Tc>::t* out) {
   constexpr int COLS = 256 / N1;
   const size_t smem = ((size_t)(N1 + 1) * N2 * COLS + (size_t)g.m * COLS) * sizeof(typename Cx<Tc>::t);
-  auto kern = fst4s_kernel<Tc, N1, N2, DIVIDE>;
+  auto kern = fst4s_kernel<Tc, N1, N2, DIVIDE, HALF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -279,7 +384,8 @@ cudaError_t fst4s(Launch& L, const Grid& g, int64_t lstride, int64_t nlines, Tc 
   return cudaGetLastError();
 }
 
-template <typename Tc, int N1, int N2>
+// HALF: N1 N2 = m + 1 (half-length DST); otherwise N1 N2 = 2(m + 1) (odd extension)
+template <typename Tc, int N1, int N2, bool HALF>
 cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, const typename Cx<Tc>::t* tw,
                  const Tc* lamK, const Tc* rmass, const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* in,
                  typename Cx<Tc>::t* out, bool stream) {
@@ -289,23 +395,25 @@ cudaError_t fst4(Launch& L, const Grid& g, int planes, int axis, bool divide, co
   for (int a = 0; a < axis; ++a) lstride *= g.m;
   const int64_t nlines = (int64_t)planes * (g.np / g.m);
   const unsigned blocks = (unsigned)((nlines + COLS - 1) / COLS);
-  const Tc hs = (Tc)(0.5 * std::sqrt(2.0 / (g.m + 1)));
-  if constexpr (sizeof(Tc) == 4 || N1 * N2 <= 256) {  // FP64 at L = 512 has no registers to spare
+  const double s2n = std::sqrt(2.0 / (g.m + 1));
+  const Tc hs = (Tc)(HALF ? s2n : 0.5 * s2n);
+  if constexpr (sizeof(Tc) == 4 || N1 * N2 <= 256) {  // FP64 at 512 points has no registers to spare
     if (stream)
-      return divide ? fst4s<Tc, N1, N2, true>(L, g, lstride, nlines, hs, tw, lamK, rmass, sigma, in, out)
-                    : fst4s<Tc, N1, N2, false>(L, g, lstride, nlines, hs, tw, nullptr, nullptr, nullptr, in, out);
+      return divide ? fst4s<Tc, N1, N2, true, HALF>(L, g, lstride, nlines, hs, tw, lamK, rmass, sigma, in, out)
+                    : fst4s<Tc, N1, N2, false, HALF>(L, g, lstride, nlines, hs, tw, nullptr, nullptr, nullptr, in,
+                                                     out);
   }
   cudaError_t e;
   if (divide) {
-    e = cudaFuncSetAttribute(fst4_kernel<Tc, N1, N2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = fst4_kernel<Tc, N1, N2, true, HALF>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fst4_kernel<Tc, N1, N2, true><<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs, lamK,
-                                                                   rmass, sigma);
+    kern<<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs, lamK, rmass, sigma);
   } else {
-    e = cudaFuncSetAttribute(fst4_kernel<Tc, N1, N2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = fst4_kernel<Tc, N1, N2, false, HALF>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fst4_kernel<Tc, N1, N2, false><<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs,
-                                                                    nullptr, nullptr, nullptr);
+    kern<<<blocks, 256, smem, L.stream>>>(in, out, tw, g.m, g.np, lstride, nlines, hs, nullptr, nullptr, nullptr);
   }
   return cudaGetLastError();
 }
@@ -329,26 +437,29 @@ cudaError_t launch_fst_fast(Launch& L, const Grid& g, int planes, int axis, bool
   const int kc = divide ? KC_FST_DIVIDE : KC_FST_AXIS;
   // fst_stream bit 0: the axis passes stream tiles, bit 1: the fused last-axis pass does
   const bool stream = L.tiles && (L.tiles->fst_stream & (divide ? 2 : 1));
-  const double lg = std::log2((double)Lfft);
-  // per line: (divide ? 2 : 1) complex FFTs of length 2(m+1)
-  const double flops = (divide ? 2.0 : 1.0) * (tot / g.m) * 5.0 * Lfft * lg;
+  const int N = g.m + 1;
+  // half-length transforms (N points) from N = 8 on, the odd extension (2N points) below
+  const int Lfft_used = N >= 8 ? N : Lfft;
+  const double lg = std::log2((double)Lfft_used);
+  // per line: (divide ? 2 : 1) complex FFTs of the length used
+  const double flops = (divide ? 2.0 : 1.0) * (tot / g.m) * 5.0 * Lfft_used * lg;
   L.begin(kc);
   cudaError_t e;
-  switch (Lfft) {
-#define PCOPT_FST_CASE(LL, A, B) \
-  case LL: e = fst4<Tc, A, B>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream); break;
-    PCOPT_FST_CASE(4, 2, 2)
-    PCOPT_FST_CASE(8, 4, 2)
-    PCOPT_FST_CASE(16, 4, 4)
-    PCOPT_FST_CASE(32, 8, 4)
-    PCOPT_FST_CASE(64, 8, 8)
-    PCOPT_FST_CASE(128, 16, 8)
-    PCOPT_FST_CASE(256, 16, 16)
-    PCOPT_FST_CASE(512, 32, 16)
+  switch (N) {
+#define PCOPT_FST_CASE(NN, A, B, HALF) \
+  case NN: e = fst4<Tc, A, B, HALF>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream); break;
+    PCOPT_FST_CASE(2, 2, 2, false)    // odd extension, 4 points
+    PCOPT_FST_CASE(4, 4, 2, false)    // odd extension, 8 points
+    PCOPT_FST_CASE(8, 4, 2, true)
+    PCOPT_FST_CASE(16, 4, 4, true)
+    PCOPT_FST_CASE(32, 8, 4, true)
+    PCOPT_FST_CASE(64, 8, 8, true)
+    PCOPT_FST_CASE(128, 16, 8, true)
+    PCOPT_FST_CASE(256, 16, 16, true)
 #undef PCOPT_FST_CASE
-    case 1024:
+    case 512:
       if constexpr (sizeof(Tc) == 4) {
-        e = fst4<Tc, 32, 32>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream);
+        e = fst4<Tc, 32, 16, true>(L, g, planes, axis, divide, tw, lamK, rmass, sigma, in, out, stream);
         break;
       } else {
         return cudaErrorNotSupported;
