@@ -327,8 +327,15 @@ __device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, 
 }
 
 // one CTA per tile, inputs loaded straight into registers
+// FP64 transforms of up to 256 points are compiled for two CTAs per SM (128 registers):
+// their arithmetic bounds them, and a second CTA hides the FP64 and shared-memory latency
+template <typename Tc, int NP>
+constexpr int tfft_fp64_blocks() {
+  return (sizeof(Tc) == 8 && NP <= 256) ? 2 : 1;
+}
+
 template <typename Tin, typename Tc, int N1, int N2>
-__global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
+__global__ void __launch_bounds__(256, tfft_fp64_blocks<Tc, N1 * N2>()) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
                                                             const Tc* __restrict__ dinv,
                                                             const typename Cx<Tc>::t* __restrict__ tw,
                                                             typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(256) tfft4s_forward_kernel(const Tin* __restri
 }
 
 template <typename Tc, typename TU, typename Tout, int N1, int N2>
-__global__ void __launch_bounds__(256, (sizeof(Tc) == 4 && N1 * N2 <= 256) ? 4 : 1) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
+__global__ void __launch_bounds__(256, (sizeof(Tc) == 4 && N1 * N2 <= 256) ? 4 : tfft_fp64_blocks<Tc, N1 * N2>()) tfft4_inverse_kernel(const TU* __restrict__ spec, const Tc* __restrict__ dpow,
                                                             const Tc* __restrict__ dinv,
                                                             const typename Cx<Tc>::t* __restrict__ tw,
                                                             Tout* __restrict__ w, int64_t ms, size_t wstride,

@@ -20,10 +20,10 @@ def _rel(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
-SHAPES = [dict(mg_cx=8, mg_ctas=2, mv_tj=8, pro_pch=2, fft_stream=1, mg_march=0, mg_seg=0),
-          dict(mg_cx=16, mg_ctas=32, mv_tj=128, pro_pch=32, fft_stream=0, mg_march=1, mg_seg=16),
-          dict(mg_cx=16, mg_ctas=1, mv_tj=1, pro_pch=1, fft_stream=1, mg_march=1, mg_seg=1),
-          dict(mg_cx=0, mg_ctas=0, mv_tj=0, pro_pch=0, fft_stream=0, mg_march=1, mg_seg=1024)]
+SHAPES = [dict(mg_cx=8, mg_ctas=2, mv_tj=8, pro_pch=2, fft_stream=1, mg_march=0, mg_seg=0, fst_stream=1),
+          dict(mg_cx=16, mg_ctas=32, mv_tj=128, pro_pch=32, fft_stream=0, mg_march=1, mg_seg=16, fst_stream=2),
+          dict(mg_cx=16, mg_ctas=1, mv_tj=1, pro_pch=1, fft_stream=1, mg_march=1, mg_seg=1, fst_stream=3),
+          dict(mg_cx=0, mg_ctas=0, mv_tj=0, pro_pch=0, fft_stream=0, mg_march=1, mg_seg=1024, fst_stream=0)]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5), ("bf16s", 3e-2)])
@@ -55,7 +55,7 @@ def test_invalid_tile_shapes_are_rejected():
     from paper_2410_22686_gb300 import Solver, capi
     sol = Solver(2, 15, 8, 1.0, 1e-3, 0.3, None, spatial="fst", tiles=None)
     for bad in (dict(mg_cx=12), dict(mg_ctas=-1), dict(mv_tj=5000), dict(pro_pch=65), dict(fft_stream=2),
-                dict(mg_march=2), dict(mg_seg=-1)):
+                dict(mg_march=2), dict(mg_seg=-1), dict(fst_stream=4), dict(fst_stream=-1)):
         with pytest.raises(capi.PCError):
             sol.set_tiles(**bad)
     with pytest.raises(ValueError):
