@@ -326,7 +326,6 @@ __device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, 
   }
 }
 
-// one CTA per tile, inputs loaded straight into registers
 // FP64 transforms of up to 256 points are compiled for two CTAs per SM (128 registers):
 // their arithmetic bounds them, and a second CTA hides the FP64 and shared-memory latency
 template <typename Tc, int NP>
@@ -334,8 +333,9 @@ constexpr int tfft_fp64_blocks() {
   return (sizeof(Tc) == 8 && NP <= 256) ? 2 : 1;
 }
 
+// one CTA per tile, inputs loaded straight into registers
 template <typename Tin, typename Tc, int N1, int N2>
-__global__ void __launch_bounds__(256, tfft_fp64_blocks<Tc, N1 * N2>()) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
+__global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restrict__ v, const Tc* __restrict__ dpow,
                                                             const Tc* __restrict__ dinv,
                                                             const typename Cx<Tc>::t* __restrict__ tw,
                                                             typename Cx<Tc>::t* __restrict__ spec, int64_t ms,
@@ -356,6 +356,34 @@ __global__ void __launch_bounds__(256, tfft_fp64_blocks<Tc, N1 * N2>()) tfft4_fo
       [&](int j, Tc& a, Tc& b) {
         a = valid ? cvt<Tc>(v1[(int64_t)j * ms + s]) : Tc(0);
         b = valid ? cvt<Tc>(v2[(int64_t)j * ms + s]) : Tc(0);
+      },
+      dpow, dinv, tw, spec, sm, ms, s, valid, r, c);
+}
+
+// the same for FP64 transforms of up to 256 points, compiled for two CTAs per SM
+// (128 registers): their FP64 arithmetic bounds them, and a second CTA hides latency
+template <typename Tin, int N1, int N2>
+__global__ void __launch_bounds__(256, 2) tfft4_forward_f64_kernel(const Tin* __restrict__ v,
+                                                                   const double* __restrict__ dpow,
+                                                                   const double* __restrict__ dinv,
+                                                                   const double2* __restrict__ tw,
+                                                                   double2* __restrict__ spec, int64_t ms,
+                                                                   size_t vstride, const int* __restrict__ jdev) {
+  constexpr int n = N1 * N2;
+  constexpr int COLS = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sm = reinterpret_cast<double2*>(smem_raw);  // [n][COLS]
+  const int c = threadIdx.x % COLS;
+  const int r = threadIdx.x / COLS;
+  const int64_t s = (int64_t)blockIdx.x * COLS + c;
+  const bool valid = s < ms;
+  if (jdev) v += (size_t)(*jdev) * vstride;
+  const Tin* v1 = v;
+  const Tin* v2 = v + (int64_t)n * ms;
+  fwd4_body<double, N1, N2>(
+      [&](int j, double& a, double& b) {
+        a = valid ? cvt<double>(v1[(int64_t)j * ms + s]) : 0.0;
+        b = valid ? cvt<double>(v2[(int64_t)j * ms + s]) : 0.0;
       },
       dpow, dinv, tw, spec, sm, ms, s, valid, r, c);
 }
@@ -643,12 +671,18 @@ cudaError_t fwd4(Launch& L, int64_t ms, const Tin* v, const Tc* dpow, const Tc* 
                  typename Cx<Tc>::t* spec, size_t vstride, const int* jdev) {
   constexpr int COLS = 256 / N1;
   const size_t smem = (size_t)N1 * N2 * COLS * sizeof(typename Cx<Tc>::t);
-  cudaError_t e = cudaFuncSetAttribute(tfft4_forward_kernel<Tin, Tc, N1, N2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  tfft4_forward_kernel<Tin, Tc, N1, N2><<<(unsigned)((ms + COLS - 1) / COLS), 256, smem, L.stream>>>(v, dpow, dinv,
-                                                                                                    tw, spec, ms,
-                                                                                                    vstride, jdev);
+  const unsigned blocks = (unsigned)((ms + COLS - 1) / COLS);
+  if constexpr (tfft_fp64_blocks<Tc, N1 * N2>() == 2) {
+    auto kern = tfft4_forward_f64_kernel<Tin, N1, N2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, vstride, jdev);
+  } else {
+    auto kern = tfft4_forward_kernel<Tin, Tc, N1, N2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, 256, smem, L.stream>>>(v, dpow, dinv, tw, spec, ms, vstride, jdev);
+  }
   return cudaGetLastError();
 }
 
