@@ -88,9 +88,11 @@ PRECOND_CASES = [(2, 31, 32, "const", "fst"), (2, 20, 16, "const", "fst"), (2, 1
                  (2, 63, 8, "var", "mg"), (3, 7, 8, "var", "mg"), (3, 5, 4, "const", "fst"),
                  (2, 1, 2, "var", "mg"), (2, 3, 1, "var", "mg"), (2, 7, 128, "var", "mg"),
                  (2, 31, 256, "var", "mg"),
-                 # sine transforms by FFT for every power-of-two length 2(m1+1) from 4 to 512
+                 # sine transforms by FFT for every power-of-two N = m1 + 1 from 2 to 512
                  (2, 1, 4, "const", "fst"), (2, 3, 2, "const", "fst"), (2, 63, 16, "const", "fst"),
-                 (2, 127, 8, "const", "fst"), (3, 15, 4, "const", "fst"), (2, 255, 4, "const", "fst")]
+                 (2, 127, 8, "const", "fst"), (3, 15, 4, "const", "fst"), (2, 255, 4, "const", "fst"),
+                 # N = m1 + 1 = 512: the longest FP32 sine transform; FP64 takes the dense product
+                 (2, 511, 2, "const", "fst")]
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
@@ -111,9 +113,9 @@ def test_precond_apply_matches_oracle(d, m1, n, kind, spatial, precision, tol):
 # Persistent streaming sine transforms (tile shape fst_stream: bit 0 the axis passes,
 # bit 1 the fused last-axis pass with the spectral divide): a CTA per SM walks
 # several line tiles (255^2 x 66 planes, 63^2 x 258 planes, 31^3 x 66 planes), at most
-# one tile per CTA (127^2, 15^3) and every power-of-two length 2(m1+1) from 4 to 512
+# one tile per CTA (127^2, 15^3) and every power-of-two N = m1 + 1 from 2 to 512
 STREAM_FST_CASES = [(2, 255, 64), (2, 63, 256), (3, 31, 64), (2, 127, 8), (3, 15, 4), (2, 1, 4), (2, 3, 2),
-                    (2, 7, 16), (2, 31, 32)]
+                    (2, 7, 16), (2, 31, 32), (2, 511, 2)]
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3])
