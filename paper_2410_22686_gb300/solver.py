@@ -47,6 +47,12 @@ class Solver:
         tiles: "table" applies the stored autotune table's entry for this shape
         (if any), "auto" runs the autotuner now, a dict sets the shapes, None keeps
         the built-in defaults."""
+        for name, val, table in (("spatial", spatial, _SPATIAL), ("precision", precision, _PREC),
+                                 ("space", space, _SPACE), ("smoother", smoother, _SMOOTHER)):
+            if val not in table:
+                raise ValueError(f"{name} must be one of {sorted(table)}, got {val!r}")
+        if not (tiles in ("table", "auto", None) or isinstance(tiles, dict)):
+            raise ValueError("tiles must be 'table', 'auto', a dict or None")
         self.lib = capi.load()
         if not torch.cuda.is_available():
             raise RuntimeError("pcopt needs a CUDA device")
