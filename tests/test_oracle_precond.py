@@ -269,6 +269,28 @@ def test_gmres_iterate_is_the_krylov_minimiser(mode):
         assert np.allclose(res.x.ravel(), xb, rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("mode", ["left", "right"])
+def test_gmres_history_is_the_residual_of_each_iterate(mode):
+    # the least-squares estimate after k steps equals the (preconditioned, for left)
+    # relative residual of the k-th iterate, computed from the iterate itself
+    d, m1, n, eps = 2, 3, 4, 0.3
+    a, K, tau, alpha = _setup(d, m1, n)
+    b = S.random_vector((2, n, m1, m1), 33)
+    Aop = lambda v: sy.apply_A(v, a, tau, alpha)
+    Pi = lambda v: pc.apply_Peps_inv(v, n, alpha, eps, pc.DenseSpatialSolver(a, tau))
+    hist = kr.gmres(Aop, Pi, b, rtol=0.0, maxit=6, mode=mode).resid_history
+    assert len(hist) == 7 and hist[0] == pytest.approx(1.0)
+    for k in range(1, 7):
+        xk = kr.gmres(Aop, Pi, b, rtol=0.0, maxit=k, mode=mode).x
+        r = b - Aop(xk)
+        if mode == "left":
+            true = np.linalg.norm(Pi(r)) / np.linalg.norm(Pi(b))
+        else:
+            true = np.linalg.norm(r) / np.linalg.norm(b)
+        assert hist[k] == pytest.approx(true, rel=1e-8, abs=1e-14)
+        assert hist[k] <= hist[k - 1] * (1 + 1e-12)
+
+
 def test_gmres_reaches_dense_solution():
     d, m1, n = 2, 3, 4
     a, K, tau, alpha = _setup(d, m1, n)
