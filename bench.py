@@ -112,6 +112,28 @@ def dist_max(dist, value, device):
     return float(t.item())
 
 
+def dist_sum(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_by_work(costs, rank, world_size):
+    """Indices of the independent problems rank `rank` solves: largest cost first, each
+    to the least-loaded rank (ties to the lower rank).  Every rank computes the same
+    assignment, so no collective is needed."""
+    load = [0.0] * world_size
+    owner = [0] * len(costs)
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world_size), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += costs[i]
+    return [i for i in range(len(costs)) if owner[i] == rank]
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
@@ -227,8 +249,10 @@ def _e2e(args, sols, rhs, gammas, torch):
     return (time.perf_counter() - t0) / (args.steps * len(gammas))
 
 
-def _extra_workloads(args, torch, dev):
-    """Timed extras on the other workloads of the path (not part of `value`)."""
+def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
+    """Timed extras on the other workloads of the path (not part of `value`).  With
+    several ranks the batched workload's problems are split between them (they are
+    independent); the other extras run as one replica per rank."""
     import synthetic as S
     from paper_2410_22686_gb300 import Batch, Solver
     from paper_2410_22686_gb300 import autograd as pag
@@ -313,7 +337,8 @@ def _extra_workloads(args, torch, dev):
         torch.cuda.empty_cache()
 
     if not args.skip_batched:
-        probs = S.batched_problems(64)
+        all_probs = S.batched_problems(64)
+        probs = [all_probs[i] for i in shard_by_work([q.unknowns for q in all_probs], rank, ws)]
         cap = 48
         waves, cur, cur_b = [], [], 0.0
         for q in probs:
@@ -352,13 +377,21 @@ def _extra_workloads(args, torch, dev):
                 so.close()
             del bs, sols
             torch.cuda.empty_cache()
-        out["batched_64"] = {"problems": len(probs), "waves": len(waves), "batch_seconds": t_batch,
+        # the job ends when the slowest rank's share is done
+        t_batch = dist_max(dist, t_batch, dev)
+        t_seq = dist_max(dist, t_seq, dev)
+        unk_it = dist_sum(dist, unk_it, dev)
+        conv = int(dist_sum(dist, float(sum(1 for r in rels if r <= RTOL)), dev))
+        max_it = int(dist_max(dist, float(max(iters) if iters else 0), dev))
+        out["batched_64"] = {"problems": len(all_probs), "ranks": ws, "waves": len(waves), "batch_seconds": t_batch,
                              "sequential_seconds": t_seq, "speedup": t_seq / t_batch if t_batch else None,
                              "unknowns_iters_per_s": unk_it / t_batch if t_batch else None,
-                             "total_unknowns": sum(q.unknowns for q in probs), "max_iters": max(iters),
-                             "converged": int(sum(1 for r in rels if r <= RTOL)),
+                             "total_unknowns": sum(q.unknowns for q in all_probs), "max_iters": max_it,
+                             "converged": conv,
                              "how": "each wave is one graph launch (pc_batch_solve), FP32 preconditioner; "
-                                    "sequential = the same problems one host-driven solve after another"}
+                                    "sequential = the same problems one host-driven solve after another; "
+                                    "with several ranks each takes a share balanced by size, times are the "
+                                    "slowest rank's"}
     return out
 
 
@@ -512,7 +545,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     # ---------------- the other workloads of the path
-    extras = _extra_workloads(args, torch, dev)
+    extras = _extra_workloads(args, torch, dev, dist, ws, rank)
 
     # ---------------- roofline of the dominant kernel class
     # DRAM bytes (read + write) over algorithmic bytes of one launch, from the ncu

@@ -93,3 +93,105 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["m1"] == 15 and d["config"]["n"] == 16
+
+
+@pytest.mark.parametrize("ws", [1, 2, 3, 4])
+def test_batched_problems_are_split_without_overlap_and_balanced(ws):
+    costs = [(i * 37) % 11 + 1.0 for i in range(64)]  # uneven sizes
+    shards = [bench.shard_by_work(costs, r, ws) for r in range(ws)]
+    flat = sorted(i for sh in shards for i in sh)
+    assert flat == list(range(64))  # every problem exactly once
+    loads = [sum(costs[i] for i in sh) for sh in shards]
+    assert max(loads) - min(loads) <= max(costs)  # greedy largest-first balance
+    assert bench.shard_by_work(costs, 0, 1) == list(range(64))  # one rank keeps the order
+
+
+_SHARD_WORKER = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import torch.distributed as td
+import bench
+dist = bench.dist_init("gloo")
+ws, rank, _ = bench.dist_env()
+costs = [float((7 * i) % 13 + 1) for i in range(64)]
+mine = bench.shard_by_work(costs, rank, ws)
+got = [None] * ws
+td.all_gather_object(got, mine)
+flat = sorted(i for sh in got for i in sh)
+assert flat == list(range(64)), flat
+assert bench.dist_sum(dist, float(len(mine)), "cpu") == 64.0
+dist.barrier()
+dist.destroy_process_group()
+print("rank", rank, "ok", flush=True)
+"""
+
+
+def test_two_gloo_ranks_take_complementary_shares():
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", _SHARD_WORKER.format(root=ROOT)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True))
+    for rank, p in enumerate(procs):
+        out, _ = p.communicate(timeout=120)
+        assert p.returncode == 0, out
+        assert f"rank {rank} ok" in out
+
+
+def test_batched_extra_logic_with_fake_solvers(monkeypatch):
+    """The batched section of the benchmark on the host: fake solvers and events stand in
+    for the GPU, so the wave split, the per-rank share and the reported fields are
+    checked without a device (one rank)."""
+    import time
+    import types
+
+    import torch
+
+    import paper_2410_22686_gb300 as pkg
+    import synthetic
+
+    class FakeSolver:
+        def __init__(self, dim, m1, n, *a, **k):
+            self.len = 2 * n * m1 ** dim
+
+        def build_rhs(self, f, g, y0):
+            return torch.ones(self.len, dtype=torch.float64)
+
+        def solve(self, b, rtol=1e-8, raise_on_nonconv=True):
+            return b, 7, 1e-9
+
+        def close(self):
+            pass
+
+    class FakeBatch:
+        def __init__(self, sols, bs, rtol=1e-8, maxit=None):
+            self.k = len(sols)
+
+        def solve(self, raise_on_nonconv=True):
+            return [7] * self.k, [1e-9] * self.k
+
+        def close(self):
+            pass
+
+    class FakeEvent:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self):
+            self.t = time.perf_counter()
+
+        def elapsed_time(self, other):
+            return 1000.0 * (other.t - self.t)
+
+    monkeypatch.setattr(pkg, "Solver", FakeSolver)
+    monkeypatch.setattr(pkg, "Batch", FakeBatch)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    args = types.SimpleNamespace(skip_3d=True, skip_fst=True, skip_grad=True, skip_batched=False, batch_gb=110.0)
+    out = bench._extra_workloads(args, torch, "cpu")["batched_64"]
+    assert out["problems"] == 64 and out["ranks"] == 1 and out["converged"] == 64 and out["max_iters"] == 7
+    assert out["waves"] >= 1 and out["batch_seconds"] >= 0.0
+    assert out["total_unknowns"] == sum(q.unknowns for q in synthetic.batched_problems(64))
