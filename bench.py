@@ -12,6 +12,16 @@ sides resident in HBM.  Prints one JSON line (rank 0).
 
 ``--impl reference`` times the CPU oracle (plain numpy FP64) on the machine's host
 cores on a bounded sample of the same workload.
+
+Beyond the contract keys (metric, value, unit, n_gpus, steps, warmup, ms_per_step,
+higher_is_better, scaling, vs_baseline, dtype, data, config, roofline, cpu_baseline,
+clocks, e2e, gpu_launches) the line carries: fp64_solve_s, mixed_graph_solve_s (the
+same solves as one CUDA-graph launch each), bf16_storage_solve_s, iteration counts and
+final residuals, residual_history_mixed, unknowns_iters_per_s, precond_apply (GB/s of
+the preconditioner alone), kernel_breakdown (CUDA-event time per kernel class in the
+timed region) and other_workloads (3D random field with its kernel breakdown,
+constant-coefficient sine-transform solves with finite differences and elements, one
+gradient, the 64-problem batch).
 """
 from __future__ import annotations
 
