@@ -17,5 +17,8 @@ Modules (each function cites the passage of the paper it follows):
 * ``krylov``   -- GMRES (left preconditioned) and flexible GMRES (right)
                                                              (Lemma 2.1, Section 3)
 * ``gradient`` -- discrete objective, envelope and adjoint gradients
+* ``fe``       -- bilinear / trilinear finite elements (mass matrix M, constant a):
+                  M, K, the operator, right-hand side, end points and
+                  mass-scaled sine-transform solves            (Section 1, the M != I case)
 """
-from . import system, precond, krylov, gradient  # noqa: F401
+from . import system, precond, krylov, gradient, fe  # noqa: F401
