@@ -46,3 +46,27 @@ def test_stored_table_is_well_formed():
         assert 0 <= e["mg_ctas"] <= 64 and 0 <= e["mv_tj"] <= 4096 and 0 <= e["pro_pch"] <= 64
         assert e["fft_stream"] in (0, 1)
         assert e.get("fst_stream", 0) in (0, 1, 2, 3)
+
+
+def test_write_missing_tunes_only_the_absent_shapes(tmp_path, monkeypatch):
+    """``--write --missing`` keeps the stored entries and tunes only the shapes the table
+    lacks (the tuner itself is replaced by a stub: no GPU)."""
+    import torch
+    path = tmp_path / "t.json"
+    keep = {"mg_cx": 8, "mg_ctas": 4, "mv_tj": 16, "pro_pch": 2, "fft_stream": 1, "mg_march": 0, "mg_seg": 0,
+            "fst_stream": 0}
+    first = tuning.WORKLOADS[0]
+    path.write_text(json.dumps({"entries": {tuning.key(*first): keep}}))
+    tuned = []
+
+    def stub(dim, m1, n, precision, spatial, reps):
+        tuned.append((dim, m1, n, precision, spatial))
+        return {f: 0 for f in tuning.FIELDS}
+
+    monkeypatch.setattr(tuning, "_tune_one", stub)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "stub")
+    assert tuning.main(["--write", "--missing", "--out", str(path)]) == 0
+    entries = tuning.load(str(path))
+    assert entries[tuning.key(*first)] == keep
+    assert first not in tuned and len(tuned) == len(tuning.WORKLOADS) - 1
+    assert set(entries) == {tuning.key(*w) for w in tuning.WORKLOADS}
