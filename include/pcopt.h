@@ -126,6 +126,20 @@ int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_ha
  * Errors: PC_ERR_ARG (a not as in pc_setup; non-constant a on an FST handle). */
 int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
 
+/* Replace a(x) at the interior nodes by exp(log_a), on the device (the
+ * differentiable parameters of pc_grad_log_a: the nodal log-coefficient).  The
+ * boundary nodes keep the values given at setup or by the last
+ * pc_set_coefficient.  Rebuilds every multigrid level's face weights from the
+ * nodal values by injection (as pc_setup does), so the handle then acts exactly
+ * as one set up with those nodal values.  Asynchronous on `stream` (no host
+ * work, no synchronisation).
+ *   log_a: device, ms = m1^dim FP64, interior nodes in vector ordering.  The
+ *          values must be finite (exp of them is the coefficient; no device-side
+ *          check: NaN or Inf surfaces later as PC_ERR_BREAKDOWN of a solve).
+ * Errors: PC_ERR_ARG (null), PC_ERR_UNSUPPORTED (sine-transform or finite-element
+ * handles, whose coefficient must stay constant). */
+int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream);
+
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
 int pc_destroy(pc_handle* h);
 
@@ -230,6 +244,29 @@ int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, in
  *   same spatial ordering), overwritten. */
 int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream);
 
+/* Gradient with respect to the target g of a scalar L(x) through the solve
+ * (b1_j = tau g_j in Eq. main_system): given the adjoint lam = A^{-T} dL/dx,
+ *   grad_g[j][s] = tau * lam1[j][s],  j = 1..n (the first half of lam).
+ *   lam: device all-at-once vector; grad_g: device, n*ms FP64, overwritten.
+ * Finite-difference handles only (PC_ERR_UNSUPPORTED for finite elements). */
+int pc_grad_g(pc_handle* h, const double* lam, double* grad_g, void* stream);
+
+/* The discrete tracking objective (Eq. Cost_functional_heat on the grid, with
+ * u = p/gamma):
+ *   J_h = h^d tau [ 1/2 sum_{j=1..n} ||y_j - g_j||^2 + 1/(2 gamma) sum_{j=1..n} ||p_j||^2 ],
+ * y = x1/sqrt(gamma), p = x2; the optimality system of Eq. main_system is its
+ * KKT system.  x: device all-at-once vector; g: device, n*ms; J: device, one
+ * FP64, written asynchronously (deterministic reduction order).  Uses the
+ * handle's reduction scratch: do not overlap with a solve on the same handle. */
+int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void* stream);
+
+/* Gradient of J_h (pc_objective) times the scalar *gJ (device; NULL means 1):
+ *   gx1 = gJ h^d tau (y - g)/sqrt(gamma),  gx2 = gJ h^d tau p/gamma   (dJ/dx)
+ *   gg  = -gJ h^d tau (y - g)                                          (explicit dJ/dg)
+ * gx: device all-at-once vector or NULL; gg: device n*ms or NULL (not both). */
+int pc_objective_grad(pc_handle* h, const double* x, const double* g, const double* gJ, double* gx, double* gg,
+                      void* stream);
+
 /* Allocation-free variant of pc_grad_log_a (the paper has no counterpart: it
  * is a deployment feature of this library).  For callers that may not
  * allocate device memory at all -- e.g. code running under another
@@ -245,14 +282,17 @@ int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad
  * Scratch: the per-time-chunk partial sums live in one file-scope device array
  * of PC_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB) that every GPU loading the
  * library holds until exit.  m1^dim above that size is rejected with
- * PC_ERR_ARG; larger n only coarsens the time chunks.  All calls on a device
- * share the array and it keeps the last call's contents (every entry a call
- * reads it first writes, so nothing needs clearing); calls whose execution
- * overlaps on the GPU (different streams without ordering) race on it.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. */
+ * PC_ERR_ARG, and so is n above PC_NOALLOC_MAX_N (a handle's limit); larger
+ * n only coarsens the time chunks.  All calls on a device share the array and
+ * it keeps the last call's contents (every entry a call reads it first writes,
+ * so nothing needs clearing); calls whose execution overlaps on the GPU
+ * (different streams without ordering) race on it.
+ * Every call looks up the array's device address (cudaGetSymbolAddress) in the
+ * context current at the call, so the device and context the caller has made
+ * current are the ones used; the first call on a device loads the module there,
+ * so make it before any stream capture. */
 #define PC_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+#define PC_NOALLOC_MAX_N 4096
 int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const double* a_int, const double* x,
                           const double* lam, double* grad, void* stream);
 
@@ -344,6 +384,15 @@ int pc_profile(pc_handle* h, int on);
 int pc_stats(pc_handle* h, pc_kernel_stat* out, int cap, int* count);
 int pc_stats_reset(pc_handle* h);
 int64_t pc_launch_count(const pc_handle* h);
+
+/* Arithmetic-rate probes (instrumentation; the paper has no counterpart): the
+ * best of five CUDA-event-timed launches of register-only FMA chains (eight
+ * independent chains per thread, grid of a few CTAs per SM), in TFLOP/s
+ * (2 flops per FMA).  *fp64_tflops bounds the FP64 Arnoldi and matvec
+ * kernels, whose FP64 operations per byte exceed the ridge point of a GPU
+ * with a small FP64 unit.  Either output may be NULL (not both).  Synchronises
+ * `stream`; takes tens of milliseconds. */
+int pc_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
 
 /* Message of the calling thread's last error (never NULL). */
 const char* pc_last_error(void);

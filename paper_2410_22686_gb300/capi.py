@@ -75,6 +75,10 @@ _SIGNATURES = {
     "pc_adjoint_solve": (_i, [_vp, _dp, _dp, _d, _i, _i, _ip, _dpp, _vp]),
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
+    "pc_set_log_coefficient": (_i, [_vp, _dp, _vp]),
+    "pc_grad_g": (_i, [_vp, _dp, _dp, _vp]),
+    "pc_objective": (_i, [_vp, _dp, _dp, _dp, _vp]),
+    "pc_objective_grad": (_i, [_vp, _dp, _dp, _dp, _dp, _dp, _vp]),
     "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "pc_end_point_solves": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _i, _ip, _vp]),
     "pc_get_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
@@ -84,6 +88,7 @@ _SIGNATURES = {
     "pc_stats": (_i, [_vp, ctypes.POINTER(pc_kernel_stat), _i, _ip]),
     "pc_stats_reset": (_i, [_vp]),
     "pc_launch_count": (ctypes.c_int64, [_vp]),
+    "pc_measure_peaks": (_i, [_dpp, _dpp, _vp]),
     "pc_last_error": (ctypes.c_char_p, []),
     "pc_status_string": (ctypes.c_char_p, [_i]),
 }

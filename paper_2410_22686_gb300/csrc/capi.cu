@@ -195,6 +195,7 @@ struct pc_handle {
   void* fst_tmp = nullptr;
   // gradient
   double* a_int = nullptr;
+  double* a_nodes_dev = nullptr;  // nodal coefficient incl. the boundary, (m1+2)^dim (device)
   double* grad_partial = nullptr;
   int grad_tj = 16;
   // Krylov workspace
@@ -642,6 +643,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   // ---- interior coefficient (gradient) and its scratch
   {
     if ((rc = upload(h, &h->a_int, interior_of(a, m1, dim), st))) goto fail_out;
+    if ((rc = upload(h, &h->a_nodes_dev, a, st))) goto fail_out;
     const int nch = (h->n + h->grad_tj - 1) / h->grad_tj;
     if ((rc = dev_alloc_t(h, &h->grad_partial, (size_t)nch * h->ms))) goto fail_out;
   }
@@ -752,6 +754,7 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
     PC_CUDA(cudaStreamSynchronize(st));
   }
   if ((rc = refill(h->a_int, interior_of(a, m1, dim), st, s64))) return rc;
+  if ((rc = refill(h->a_nodes_dev, a, st, s64))) return rc;
   h->a_const = a[0];
   h->fes = fe_scale(dim, m1, h->a_const);
   if (h->spatial == PC_SPATIAL_FST) {
@@ -760,6 +763,22 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
     if ((rc = refill(h->lamK32, lam, st, s32))) return rc;
   }
   return PC_OK;
+}
+
+extern "C" int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream) {
+  if (!h || !log_a) return fail(PC_ERR_ARG, "pc_set_log_coefficient: null argument");
+  if (h->spatial != PC_SPATIAL_MG || h->fe)
+    return fail(PC_ERR_UNSUPPORTED, "pc_set_log_coefficient: variable-coefficient (multigrid, finite-difference) "
+                                    "handles only");
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  cudaError_t e = launch_set_log_coefficient(L, h->dim, h->m1, log_a, h->a_nodes_dev, h->a_int);
+  int stride = 1;
+  for (size_t l = 0; l < h->lv.size() && e == cudaSuccess; ++l, stride *= 2) {
+    LevelBuf& B = h->lv[l];
+    e = launch_level_stencil(L, h->dim, h->m1 + 2, stride, B.m, h->tau, B.w64, B.d64, B.w32, B.d32, B.w4,
+                             l == 0 ? h->wdf : nullptr, l == 0 ? h->ddf : nullptr, h->a_nodes_dev);
+  }
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_set_log_coefficient");
 }
 
 extern "C" int pc_destroy(pc_handle* h) {
@@ -1071,6 +1090,35 @@ extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, d
   cudaError_t e =
       launch_grad_chunked(L, grid_of(h, 0), h->n, scale, h->a_int, x, lam, h->grad_partial, h->grad_tj, grad);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_log_a");
+}
+
+extern "C" int pc_grad_g(pc_handle* h, const double* lam, double* grad_g, void* stream) {
+  if (!h || !lam || !grad_g) return fail(PC_ERR_ARG, "pc_grad_g: null argument");
+  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_grad_g: finite-difference handles only");
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  cudaError_t e = launch_grad_g(L, lam, (int64_t)h->n * h->ms, h->tau, grad_g);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_g");
+}
+
+// c = h^d tau, the quadrature weight of the discrete objective
+static double objective_weight(const pc_handle* h) { return std::pow(h->h, h->dim) * h->tau; }
+
+extern "C" int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void* stream) {
+  if (!h || !x || !g || !J) return fail(PC_ERR_ARG, "pc_objective: null argument");
+  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_objective: finite-difference handles only");
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  cudaError_t e = launch_objective(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), h->partial,
+                                   h->nblocks * (h->cap + 2), J);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective");
+}
+
+extern "C" int pc_objective_grad(pc_handle* h, const double* x, const double* g, const double* gJ, double* gx,
+                                 double* gg, void* stream) {
+  if (!h || !x || !g || (!gx && !gg)) return fail(PC_ERR_ARG, "pc_objective_grad: null argument");
+  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_objective_grad: finite-difference handles only");
+  Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  cudaError_t e = launch_objective_grad(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), gJ, gx, gg);
+  return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective_grad");
 }
 
 // ---------------------------------------------------------------------------

@@ -404,6 +404,18 @@ cudaError_t launch_real_to_plane(Launch& L, const double* v, typename Cx<Tc>::t*
 template <typename TU>
 cudaError_t launch_plane_to_real(Launch& L, const TU* plane, double* v, int64_t ms);
 // grad_P = scale * a_P * sum_j sum_faces [(l1_P-l1_Q)(x2_P-x2_Q) - (l2_P-l2_Q)(x1_P-x1_Q)]
+// a(x) at the interior nodes = exp(log_a) into the nodal array and the interior copy
+cudaError_t launch_set_log_coefficient(Launch& L, int dim, int m1, const double* log_a, double* a_nodes,
+                                       double* a_int);
+// face weights of one level from the fine nodal coefficient (level node I = fine node stride*I)
+cudaError_t launch_level_stencil(Launch& L, int dim, int M0, int stride, int m, double tau, double* w64,
+                                 double* d64, float* w32, float* d32, float4* w4, float2* wdf, float2* ddf,
+                                 const double* a_nodes);
+cudaError_t launch_grad_g(Launch& L, const double* lam, int64_t len, double tau, double* out);
+cudaError_t launch_objective(Launch& L, const double* x, const double* g, int64_t half, double gamma, double c,
+                             double* partial, int max_partial, double* J);
+cudaError_t launch_objective_grad(Launch& L, const double* x, const double* g, int64_t half, double gamma, double c,
+                                  const double* gJ, double* gx, double* gg);
 cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, const double* a_int, const double* x,
                                 const double* lam, double* partial, int tj, double* grad);
 

@@ -143,6 +143,130 @@ __global__ void plane_to_real_kernel(const TU* __restrict__ plane, double* __res
   }
 }
 
+// a at the interior nodes from its logarithm (the differentiable parameters):
+// a_nodes[interior node of s] = a_int[s] = exp(log_a[s]); boundary nodes untouched
+template <int DIM>
+__global__ void exp_log_coefficient_kernel(const double* __restrict__ log_a, int m, int64_t ms,
+                                           double* __restrict__ a_nodes, double* __restrict__ a_int) {
+  const int M = m + 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride) {
+    const int i1 = (int)(s % m) + 1;
+    const int64_t r = s / m;
+    const int i2 = (int)(DIM == 2 ? r : r % m) + 1;
+    const int i3 = DIM == 3 ? (int)(r / m) + 1 : 0;
+    const double v = exp(log_a[s]);
+    a_int[s] = v;
+    a_nodes[DIM == 2 ? (int64_t)i2 * M + i1 : ((int64_t)i3 * M + i2) * M + i1] = v;
+  }
+}
+
+// Face weights tau*a_f/h_l^2 (a_f = (a_P + a_Q)/2) and their sum for the level
+// with m interior points per axis, whose node I is the fine node `stride`*I
+// (injection a_c[I] = a[2I] applied level by level).  Same operation order as
+// the host construction at setup (no contraction), so both give the same bits
+// from the same nodal values.  Optional outputs may be null.
+template <int DIM>
+__global__ void level_stencil_kernel(const double* __restrict__ a_nodes, int M0, int stride, int m, int64_t np,
+                                     double sc, double* __restrict__ w64, double* __restrict__ d64,
+                                     float* __restrict__ w32, float* __restrict__ d32, float4* __restrict__ w4,
+                                     float2* __restrict__ wdf, float2* __restrict__ ddf) {
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  const double half_sc = __dmul_rn(sc, 0.5);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < np; s += gs) {
+    const int i1 = (int)(s % m) + 1;
+    const int64_t r = s / m;
+    const int i2 = (int)(DIM == 2 ? r : r % m) + 1;
+    const int i3 = DIM == 3 ? (int)(r / m) + 1 : 0;
+    auto node = [&](int j1, int j2, int j3) -> double {
+      const int64_t f1 = (int64_t)j1 * stride, f2 = (int64_t)j2 * stride, f3 = (int64_t)j3 * stride;
+      return DIM == 2 ? a_nodes[f2 * M0 + f1] : a_nodes[(f3 * M0 + f2) * M0 + f1];
+    };
+    const double aP = node(i1, i2, i3);
+    double nb[2 * DIM];
+    nb[0] = node(i1 - 1, i2, i3);
+    nb[1] = node(i1 + 1, i2, i3);
+    nb[2] = node(i1, i2 - 1, i3);
+    nb[3] = node(i1, i2 + 1, i3);
+    if (DIM == 3) {
+      nb[4] = node(i1, i2, i3 - 1);
+      nb[5] = node(i1, i2, i3 + 1);
+    }
+    double sum = 0.0;
+    float wf32[2 * DIM];
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k) {
+      const double wf = __dmul_rn(half_sc, __dadd_rn(aP, nb[k]));
+      w64[(int64_t)k * np + s] = wf;
+      wf32[k] = __double2float_rn(wf);
+      w32[(int64_t)k * np + s] = wf32[k];
+      if (wdf) wdf[(int64_t)k * np + s] = make_float2(wf32[k], __double2float_rn(__dsub_rn(wf, (double)wf32[k])));
+      sum = __dadd_rn(sum, wf);
+    }
+    d64[s] = sum;
+    const float s32 = __double2float_rn(sum);
+    d32[s] = s32;
+    if (ddf) ddf[s] = make_float2(s32, __double2float_rn(__dsub_rn(sum, (double)s32)));
+    if (DIM == 2 && w4) w4[s] = make_float4(wf32[0], wf32[1], wf32[2], wf32[3]);
+  }
+}
+
+// dJ/dg of the right-hand side b1_j = tau g_j: out[j][s] = tau * lam1[j][s]
+__global__ void grad_g_kernel(const double* __restrict__ lam, int64_t len, double tau, double* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) out[e] = tau * lam[e];
+}
+
+// Discrete objective J_h = c [1/2 sum (x1/sqrt(gamma) - g)^2 + 1/(2 gamma) sum x2^2],
+// c = h^d tau: per-block partial sums (fixed grid, fixed order: deterministic)
+__global__ void __launch_bounds__(256) objective_partial_kernel(const double* __restrict__ x,
+                                                                const double* __restrict__ g, int64_t half,
+                                                                double isg, double igam,
+                                                                double* __restrict__ partial) {
+  __shared__ double red[256 / 32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < half; e += stride) {
+    const double d = fma(x[e], isg, -g[e]);
+    const double p = x[half + e];
+    acc = fma(d, d, acc);
+    acc = fma(igam * p, p, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  }
+}
+
+__global__ void objective_finish_kernel(const double* __restrict__ partial, int nb, double c, double* __restrict__ J) {
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) acc += partial[b];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) *J = 0.5 * c * acc;
+}
+
+// Gradient of J_h times the upstream scalar gJ (1 when null):
+//   dJ/dx1 = c (x1/sqrt(gamma) - g)/sqrt(gamma),  dJ/dx2 = c x2/gamma,
+//   dJ/dg (explicit) = -c (x1/sqrt(gamma) - g)
+__global__ void objective_grad_kernel(const double* __restrict__ x, const double* __restrict__ g, int64_t half,
+                                      double isg, double igam, double c, const double* __restrict__ gJ,
+                                      double* __restrict__ gx, double* __restrict__ gg) {
+  const double cs = gJ ? c * gJ[0] : c;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < half; e += stride) {
+    const double d = fma(x[e], isg, -g[e]);
+    if (gx) {
+      gx[e] = cs * d * isg;
+      gx[half + e] = cs * igam * x[half + e];
+    }
+    if (gg) gg[e] = -cs * d;
+  }
+}
+
 static unsigned grid_for(int64_t len) {
   int64_t b = (len + 255) / 256;
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -176,6 +300,58 @@ cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, c
   L.begin(KC_GRAD);
   grad_finish_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, L.stream>>>(partial, nchunks, g.np, scale, a_int, grad);
   return L.end(KC_GRAD, 8.0 * (nchunks + 2) * g.np, 1.0 * nchunks * g.np);
+}
+
+cudaError_t launch_set_log_coefficient(Launch& L, int dim, int m1, const double* log_a, double* a_nodes,
+                                       double* a_int) {
+  const int64_t ms = dim == 2 ? (int64_t)m1 * m1 : (int64_t)m1 * m1 * m1;
+  L.begin(KC_RHS);
+  if (dim == 2)
+    exp_log_coefficient_kernel<2><<<grid_for(ms), 256, 0, L.stream>>>(log_a, m1, ms, a_nodes, a_int);
+  else
+    exp_log_coefficient_kernel<3><<<grid_for(ms), 256, 0, L.stream>>>(log_a, m1, ms, a_nodes, a_int);
+  return L.end(KC_RHS, 24.0 * ms, 20.0 * ms);
+}
+
+cudaError_t launch_level_stencil(Launch& L, int dim, int M0, int stride, int m, double tau, double* w64,
+                                 double* d64, float* w32, float* d32, float4* w4, float2* wdf, float2* ddf,
+                                 const double* a_nodes) {
+  const int64_t np = dim == 2 ? (int64_t)m * m : (int64_t)m * m * m;
+  const double hl = 1.0 / (m + 1);
+  const double sc = tau / (hl * hl);
+  L.begin(KC_RHS);
+  if (dim == 2)
+    level_stencil_kernel<2><<<grid_for(np), 256, 0, L.stream>>>(a_nodes, M0, stride, m, np, sc, w64, d64, w32, d32,
+                                                                 w4, wdf, ddf);
+  else
+    level_stencil_kernel<3><<<grid_for(np), 256, 0, L.stream>>>(a_nodes, M0, stride, m, np, sc, w64, d64, w32, d32,
+                                                                 nullptr, wdf, ddf);
+  return L.end(KC_RHS, (8.0 * (2 * dim + 1) + 12.0 * (2 * dim + 1)) * np, 3.0 * 2 * dim * np);
+}
+
+cudaError_t launch_grad_g(Launch& L, const double* lam, int64_t len, double tau, double* out) {
+  L.begin(KC_GRAD);
+  grad_g_kernel<<<grid_for(len), 256, 0, L.stream>>>(lam, len, tau, out);
+  return L.end(KC_GRAD, 16.0 * len, 1.0 * len);
+}
+
+cudaError_t launch_objective(Launch& L, const double* x, const double* g, int64_t half, double gamma, double c,
+                             double* partial, int max_partial, double* J) {
+  int nb = (int)grid_for(half);
+  if (nb > max_partial) nb = max_partial;
+  if (nb < 1) return cudaErrorInvalidValue;
+  L.begin(KC_REDUCE);
+  objective_partial_kernel<<<nb, 256, 0, L.stream>>>(x, g, half, 1.0 / sqrt(gamma), 1.0 / gamma, partial);
+  objective_finish_kernel<<<1, 32, 0, L.stream>>>(partial, nb, c, J);
+  return L.end(KC_REDUCE, 24.0 * half, 6.0 * half);
+}
+
+cudaError_t launch_objective_grad(Launch& L, const double* x, const double* g, int64_t half, double gamma, double c,
+                                  const double* gJ, double* gx, double* gg) {
+  L.begin(KC_GRAD);
+  objective_grad_kernel<<<grid_for(half), 256, 0, L.stream>>>(x, g, half, 1.0 / sqrt(gamma), 1.0 / gamma, c, gJ, gx,
+                                                             gg);
+  return L.end(KC_GRAD, (24.0 + (gx ? 16.0 : 0.0) + (gg ? 8.0 : 0.0)) * half, 6.0 * half);
 }
 
 cudaError_t launch_endpoint_rhs(Launch& L, const double* x, int64_t ms, int n, double tau, double gamma,

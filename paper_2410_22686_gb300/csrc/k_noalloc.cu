@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/pcopt.h"
@@ -24,25 +23,16 @@ static __device__ __align__(256) double g_noalloc_scratch[PC_NOALLOC_SCRATCH_DOU
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array for the current device.  Host code must
-// not use the symbol itself (it is a host-side stand-in, not a device address).
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Device address of the scratch array in the context that is current now.
+// Host code must not use the symbol itself (it is a host-side stand-in, not a
+// device address).  The lookup is a cheap host call and is repeated on every
+// call: an address cached per device ordinal would go stale when the caller
+// switches to another context on that device or after cudaDeviceReset.
+cudaError_t scratch_for_current_context(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -53,18 +43,23 @@ extern "C" int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const dou
   if (dim != 2 && dim != 3) return set_error(PC_ERR_ARG, "pc_grad_log_a_noalloc: dim must be 2 or 3");
   if (m1 < 1 || n < 1 || !(T > 0) || !std::isfinite(T))
     return set_error(PC_ERR_ARG, "pc_grad_log_a_noalloc: need m1 >= 1, n >= 1, finite T > 0");
+  if (n > PC_NOALLOC_MAX_N)  // the same limit as a handle's n
+    return set_error(PC_ERR_ARG, "pc_grad_log_a_noalloc: n = " + std::to_string(n) + " exceeds " +
+                                     std::to_string(PC_NOALLOC_MAX_N));
   if (!a_int || !x || !lam || !grad) return set_error(PC_ERR_ARG, "pc_grad_log_a_noalloc: null pointer");
   const int64_t ms = dim == 2 ? (int64_t)m1 * m1 : (int64_t)m1 * m1 * m1;
   if (ms > (int64_t)PC_NOALLOC_SCRATCH_DOUBLES)  // one time chunk of partial sums must fit
     return set_error(PC_ERR_ARG, "pc_grad_log_a_noalloc: m1^dim = " + std::to_string(ms) +
                                      " exceeds the static scratch of " +
                                      std::to_string((long long)PC_NOALLOC_SCRATCH_DOUBLES) + " doubles");
-  // time chunk of 16 blocks, as pc_grad_log_a, enlarged until the partial sums fit
-  int tj = 16;
-  const int64_t max_chunks = (int64_t)PC_NOALLOC_SCRATCH_DOUBLES / ms;
-  if ((n + tj - 1) / tj > max_chunks) tj = (int)((n + max_chunks - 1) / max_chunks);
+  // time chunk of 16 blocks, as pc_grad_log_a, enlarged until the partial sums
+  // fit the scratch and the chunk count fits the grid's y extent (65535)
+  int64_t max_chunks = (int64_t)PC_NOALLOC_SCRATCH_DOUBLES / ms;
+  if (max_chunks > 65535) max_chunks = 65535;
+  int64_t tj = 16;
+  if (((int64_t)n + tj - 1) / tj > max_chunks) tj = ((int64_t)n + max_chunks - 1) / max_chunks;
   double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
+  cudaError_t e = scratch_for_current_context(&scratch);
   if (e != cudaSuccess)
     return set_error(PC_ERR_CUDA, std::string("pc_grad_log_a_noalloc: scratch address: ") + cudaGetErrorString(e));
   Launch L{(cudaStream_t)stream, nullptr};
@@ -74,7 +69,7 @@ extern "C" int pc_grad_log_a_noalloc(int dim, int m1, int n, double T, const dou
   g.np = ms;
   const double tau = T / (n + 1);
   const double h = 1.0 / (m1 + 1);
-  e = launch_grad_chunked(L, g, n, -tau * 0.5 / (h * h), a_int, x, lam, scratch, tj, grad);
+  e = launch_grad_chunked(L, g, n, -tau * 0.5 / (h * h), a_int, x, lam, scratch, (int)tj, grad);
   if (e != cudaSuccess)
     return set_error(PC_ERR_CUDA, std::string("pc_grad_log_a_noalloc: ") + cudaGetErrorString(e));
   return PC_OK;

@@ -115,6 +115,13 @@ class Solver:
             ptr = self._a.ctypes.data_as(ctypes.c_void_p)
         capi.check(self.lib.pc_set_coefficient(self.h, ptr, _stream()))
 
+    def set_log_coefficient(self, log_a: torch.Tensor):
+        """a = exp(log_a) at the interior nodes, on the device (pc_set_log_coefficient);
+        log_a: float64 CUDA tensor of m1^dim values.  The boundary keeps its values."""
+        if log_a.numel() != self.ms:
+            raise ValueError(f"log_a must hold {self.ms} values")
+        capi.check(self.lib.pc_set_log_coefficient(self.h, _ptr(log_a), _stream()))
+
     # ---------------------------------------------------------------- helpers
     def empty_vector(self):
         return torch.empty((2, self.n) + (self.m1,) * self.dim, dtype=torch.float64, device="cuda")
@@ -224,6 +231,34 @@ class Solver:
         capi.check(self.lib.pc_grad_log_a(self.h, _ptr(x), _ptr(lam), _ptr(g), _stream()))
         return g
 
+    def grad_g(self, lam, out=None):
+        """tau * lam1: the gradient with respect to the target g (pc_grad_g)."""
+        self._vec(lam)
+        gg = torch.empty((self.n,) + (self.m1,) * self.dim, dtype=torch.float64, device="cuda") if out is None else out
+        if gg.numel() != self.n * self.ms:
+            raise ValueError("out must hold n * m1^dim values")
+        capi.check(self.lib.pc_grad_g(self.h, _ptr(lam), _ptr(gg), _stream()))
+        return gg
+
+    def objective(self, x, g, out=None):
+        """J_h(x; g) as a 0-d device tensor (pc_objective)."""
+        self._vec(x)
+        if g.numel() != self.n * self.ms:
+            raise ValueError("g must hold n * m1^dim values")
+        J = torch.empty((), dtype=torch.float64, device="cuda") if out is None else out
+        capi.check(self.lib.pc_objective(self.h, _ptr(x), _ptr(g), _ptr(J), _stream()))
+        return J
+
+    def objective_grad(self, x, g, gJ=None, gx=None, gg=None):
+        """(dJ/dx, explicit dJ/dg) times the device scalar gJ (pc_objective_grad)."""
+        self._vec(x)
+        if g.numel() != self.n * self.ms:
+            raise ValueError("g must hold n * m1^dim values")
+        gx = torch.empty_like(x) if gx is None else gx
+        gg = torch.empty_like(g) if gg is None else gg
+        capi.check(self.lib.pc_objective_grad(self.h, _ptr(x), _ptr(g), _ptr(gJ), _ptr(gx), _ptr(gg), _stream()))
+        return gx, gg
+
     def end_point_solves(self, x, f_T=None, g_0=None, y0=None, p_N=None, rtol=1e-12, maxit=500):
         """y^(N) and p^(0) of the time discretisation from a solution x (pc_end_point_solves)."""
         self._vec(x)
@@ -277,6 +312,14 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.pc_launch_count(self.h))
+
+
+def measure_peaks():
+    """Measured FP64 and FP32 FMA rates of the current GPU in TFLOP/s (pc_measure_peaks)."""
+    lib = capi.load()
+    f64, f32 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    capi.check(lib.pc_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), _stream()))
+    return f64.value, f32.value
 
 
 def solve_host_pipelined(jobs, rtol=1e-8, maxit=None, mode="right", raise_on_nonconv=True):

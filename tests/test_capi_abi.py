@@ -74,3 +74,17 @@ def test_status_strings_and_argument_errors_without_gpu():
         assert l.pc_setup(ctypes.byref(p), a_ptr, None, ctypes.byref(h)) == capi.PC_ERR_UNSUPPORTED
         assert b"finite elements" in l.pc_last_error()
     assert l.pc_destroy(None) == capi.PC_OK
+
+
+def test_noalloc_gradient_rejects_bad_sizes_without_gpu():
+    """The allocation-free gradient checks its sizes on the host, before it looks
+    up its scratch or launches anything."""
+    l = capi.load()
+    nul = ctypes.c_void_p(0)
+    one = ctypes.c_void_p(8)  # never dereferenced: every case fails its size check first
+    cases = [(4, 7, 8), (2, 0, 8), (2, 7, 0), (2, 7, 4097), (2, 7, 1 << 30), (3, 129, 8), (2, 1449, 8)]
+    for d, m1, n in cases:
+        assert l.pc_grad_log_a_noalloc(d, m1, n, 1.0, one, one, one, one, nul) == capi.PC_ERR_ARG, (d, m1, n)
+        assert len(l.pc_last_error()) > 0
+    assert l.pc_grad_log_a_noalloc(2, 7, 8, 1.0, nul, one, one, one, nul) == capi.PC_ERR_ARG
+    assert b"null" in l.pc_last_error()

@@ -34,9 +34,11 @@ def lib():
 
 def test_noalloc_gradient_equals_handle_gradient_on_consecutive_calls(lib):
     from paper_2410_22686_gb300 import Solver, capi
-    # two calls in a row on different problems: 3D (default time chunks), then a
-    # 2D grid large enough that the time chunks are coarsened to fit the scratch
-    cases = [(3, 15, 64, 1), (2, 511, 256, 2)]
+    # calls in a row on different problems: 3D (default time chunks); a 2D grid
+    # large enough that the time chunks are coarsened to fit the scratch (8
+    # blocks per chunk, all full); 1023^2 with n = 257, where only two chunks
+    # fit (129 + 128 blocks, a partial last chunk)
+    cases = [(3, 15, 64, 1), (2, 511, 256, 2), (2, 1023, 257, 3)]
     for d, m1, n, seed in cases:
         a_nodes = np.exp(0.3 * S.random_vector((m1 + 2,) * d, seed))
         sol = Solver(d, m1, n, 1.0, 1e-3, 0.5, a_nodes, spatial="mg", precision="fp64", max_iter=1)
@@ -61,3 +63,5 @@ def test_noalloc_rejects_grids_beyond_the_static_scratch(lib):
     assert _noalloc(lib, 3, 129, 8, 1.0, t, t, t, t) == capi.PC_ERR_ARG
     assert b"static scratch" in lib.pc_last_error()
     assert _noalloc(lib, 4, 7, 8, 1.0, t, t, t, t) == capi.PC_ERR_ARG
+    # n beyond a handle's limit
+    assert _noalloc(lib, 2, 7, 4097, 1.0, t, t, t, t) == capi.PC_ERR_ARG
