@@ -10,6 +10,9 @@ sides resident in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+With --gpus N > 1 and no torchrun environment (WORLD_SIZE unset) it starts N
+local ranks itself, one per GPU, each running a replica of the workload.
+
 ``--impl reference`` times the CPU oracle (plain numpy FP64) on the machine's host
 cores on a bounded sample of the same workload.
 
@@ -48,10 +51,6 @@ METRIC = "GMRES solve time to 1e-8 rel. residual, mixed vs FP64; precond-apply H
 GAMMAS = (1e-2, 1e-4, 1e-6, 1e-8)
 M1, NT = 255, 256
 RTOL = 1e-8
-# Iterations reported by the paper for its variable-coefficient example at the same
-# number of unknowns (h = tau = 2^-8, gamma = 1e-4; Table 6): used only to scale the
-# oracle's per-iteration time to a solve in the reference arm.
-PAPER_ITERS_H8 = 15
 
 
 def parse():
@@ -62,6 +61,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cap", type=int, default=60, help="Krylov basis capacity")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-full-solve", action="store_true",
+                    help="reference arm: run the oracle's complete solve once and print its iteration count")
+    ap.add_argument("--skip-sweep", action="store_true")
     # smaller cases for profiling runs (the default is the benchmark workload)
     ap.add_argument("--m1", type=int, default=255)
     ap.add_argument("--nt", type=int, default=256)
@@ -196,45 +198,162 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_iteration_seconds(gamma=1e-4, m1=M1, nt=NT):
-    """Time one right-preconditioned (flexible) GMRES iteration of the CPU oracle on
-    the full workload: P_eps^{-1} v (FFT, one V-cycle per shifted system, inverse
-    FFT), A z, and the Gram-Schmidt step against the first basis vector."""
+# The oracle's own iteration count for the benchmark workload at gamma = 1e-4
+# (its full right-preconditioned GMRES to rtol 1e-8; `--oracle-full-solve`
+# reruns that solve and prints the count).  The GPU FP64 solve takes the same
+# count (iteration-count parity is tested).
+ORACLE_GAMMA = 1e-4
+ORACLE_ITERS = 37
+ORACLE_SAMPLE_ITERS = 3
+
+
+def host_description():
+    """Logical CPUs of this host and its lscpu summary (model, sockets, cores)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            k = k.strip()
+            if k in ("Architecture", "Model name", "Socket(s)", "Core(s) per socket", "Thread(s) per core",
+                     "CPU(s)", "CPU max MHz", "L3 cache"):
+                info[k] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        info["lscpu"] = "unavailable"
+    return info
+
+
+class _PlaneThreads:
+    """Wraps an oracle spatial solver: its independent shifted systems (one per
+    frequency plane) are split into contiguous chunks solved on a thread pool
+    (numpy releases the GIL inside the array operations).  The solver's own
+    arithmetic is unchanged."""
+
+    def __init__(self, inner, threads):
+        import concurrent.futures as cf
+        self.inner, self.threads = inner, threads
+        self.pool = cf.ThreadPoolExecutor(threads) if threads > 1 else None
+
+    def __call__(self, sigma, R):
+        if self.pool is None:
+            return self.inner(sigma, R)
+        k = R.shape[0]
+        cuts = np.linspace(0, k, self.threads + 1).astype(int)
+        futs = [self.pool.submit(self.inner, sigma[a:b], R[a:b]) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        return np.concatenate([f.result() for f in futs], axis=0)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+
+
+def _oracle_problem(gamma, m1, nt):
     import synthetic as S
     from oracle import precond as opc, system as osy
     prob = S.variable_2d_problem(gamma=gamma, m1=m1, n=nt)
     tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, gamma)
     b = osy.build_rhs(prob.f, prob.g, prob.y0, tau, gamma)
     mg = opc.MGSpatialSolver(prob.a_nodes, tau)
+    return prob, tau, alpha, b, mg
+
+
+def oracle_solve_seconds(threads, m1=M1, nt=NT, gamma=ORACLE_GAMMA, iters=ORACLE_ITERS,
+                         sample_iters=ORACLE_SAMPLE_ITERS):
+    """Seconds of one oracle GMRES solve of the workload, from a bounded sample.
+
+    The oracle's own flexible GMRES (unchanged; the spatial solves of the
+    frequency planes on `threads` host threads) runs the first `sample_iters`
+    iterations of the solve; its cost splits into a per-iteration part (the
+    preconditioner apply and the matvec) and a modified Gram-Schmidt part that
+    grows with the basis (iteration j projects against j+1 vectors).  The
+    Gram-Schmidt cost per basis vector is timed on the same vectors (the
+    oracle's dot and update).  The solve of `iters` iterations then costs
+        iters * base + gs * iters (iters + 1) / 2.
+    Returns (seconds, details)."""
+    from oracle import krylov as okr, precond as opc, system as osy
+    prob, tau, alpha, b, mg = _oracle_problem(gamma, m1, nt)
+    sp = _PlaneThreads(mg, threads)
+    A = lambda v: osy.apply_A(v, prob.a_nodes, tau, alpha)
+    Pi = lambda v: opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, sp)
     t0 = time.perf_counter()
-    v = b / np.linalg.norm(b)
-    z = opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, mg)
-    w = osy.apply_A(z, prob.a_nodes, tau, alpha)
-    h = float(np.vdot(w.ravel(), v.ravel()))
-    w = w - h * v
-    _ = np.linalg.norm(w)
-    return time.perf_counter() - t0
+    r = okr.gmres(A, Pi, b, rtol=1e-8, maxit=sample_iters, mode="right")
+    t_sample = time.perf_counter() - t0
+    k_s = r.iters
+    # one modified Gram-Schmidt projection against one basis vector, as the oracle forms it
+    w = b.ravel().copy()
+    v = w / np.linalg.norm(w)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        h = np.dot(w, v)
+        w = w - h * v
+    t_gs = (time.perf_counter() - t0) / reps
+    sp.close()
+    gs_sample = t_gs * k_s * (k_s + 1) / 2
+    base = max(t_sample - gs_sample, 0.0) / max(k_s, 1)
+    total = iters * base + t_gs * iters * (iters + 1) / 2
+    return total, {"iters": iters, "sample_iterations": k_s, "sample_seconds": t_sample,
+                   "per_iteration_base_s": base, "gram_schmidt_per_vector_s": t_gs, "threads": threads}
+
+
+def cpu_baseline_record(m1=M1, nt=NT, single=True):
+    """The oracle on this host's cores: all cores (the value) and one core."""
+    cores = os.cpu_count() or 1
+    t_all, det_all = oracle_solve_seconds(cores, m1, nt)
+    rec = {"value": t_all, "unit": "s/solve", "cores": cores, "kind": "oracle",
+           "sample": (f"the oracle's own flexible GMRES on the full workload at gamma={ORACLE_GAMMA:g} (rtol 1e-8): "
+                      f"its first {det_all['sample_iterations']} iterations timed, spatial solves of the frequency "
+                      f"planes on {cores} threads, plus the modified Gram-Schmidt projection timed per basis "
+                      f"vector; a solve of the oracle's own {ORACLE_ITERS} iterations costs "
+                      f"iters*base + gs*iters*(iters+1)/2"),
+           "all_cores": det_all, "host": host_description()}
+    if single:
+        t_one, det_one = oracle_solve_seconds(1, m1, nt)
+        rec["single_core"] = {"value": t_one, **det_one}
+    return rec
+
+
+def oracle_full_solve(m1=M1, nt=NT, gamma=ORACLE_GAMMA):
+    """The oracle's complete solve (all host cores): its iteration count and time."""
+    from oracle import krylov as okr, precond as opc, system as osy
+    prob, tau, alpha, b, mg = _oracle_problem(gamma, m1, nt)
+    sp = _PlaneThreads(mg, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    r = okr.gmres(lambda v: osy.apply_A(v, prob.a_nodes, tau, alpha),
+                  lambda v: opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, sp), b, rtol=1e-8, maxit=200,
+                  mode="right")
+    sp.close()
+    return {"iters": r.iters, "converged": r.converged, "seconds": time.perf_counter() - t0,
+            "threads": os.cpu_count(), "gamma": gamma, "m1": m1, "n": nt}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.oracle_full_solve:
+        print(json.dumps({"impl": "reference", "oracle_full_solve": oracle_full_solve(args.m1, args.nt)}), flush=True)
+        return 0
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_iteration_seconds(m1=args.m1, nt=args.nt)
-    times = [oracle_iteration_seconds(m1=args.m1, nt=args.nt) for _ in range(args.steps)]
-    per_iter = statistics.median(times)
-    value = per_iter * PAPER_ITERS_H8
+        oracle_solve_seconds(cores, m1=args.m1, nt=args.nt)
+    t0 = time.perf_counter()
+    runs = [oracle_solve_seconds(cores, m1=args.m1, nt=args.nt) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    value = statistics.median(t for t, _ in runs)
+    det = runs[len(runs) // 2][1]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": False, "scaling": "weak",
+        "ms_per_step": 1000 * wall / max(args.steps, 1), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.m1, args.nt, args.gammas),
-        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": 1, "kind": "oracle",
-                         "sample": f"one oracle GMRES iteration (preconditioner apply, matvec, one Gram-Schmidt "
-                                   f"step) on the full workload at gamma=1e-4 per step, median of {args.steps}, "
-                                   f"times {PAPER_ITERS_H8} iterations (the paper's count at this size)"},
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle",
+                         "sample": (f"per step: the oracle's own flexible GMRES on the full workload at "
+                                    f"gamma={ORACLE_GAMMA:g}, its first {det['sample_iterations']} iterations timed "
+                                    f"on {cores} threads plus the Gram-Schmidt cost per basis vector, scaled to "
+                                    f"the oracle's {ORACLE_ITERS} iterations; median of {args.steps} steps"),
+                         "all_cores": det, "host": host_description()},
         "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -407,12 +526,90 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
     return out
 
 
+def iteration_sweep(args, torch, dev, m1=M1, ns=(32, 64, 128, 256, 512), gammas=GAMMAS):
+    """GMRES iteration counts of the mixed path (FP32 preconditioner, flexible GMRES,
+    rtol 1e-8) over n and gamma at m1^2, for eps = sqrt(tau) (the benchmark's choice)
+    and for eps = c_tau(1/2) = (sqrt(tau)/2) / (sqrt(tau)/2 + 2 sqrt(T)), the largest
+    eps Theorem 2.13 covers with delta = 1/2 (also in FP64)."""
+    import synthetic as S
+    from paper_2410_22686_gb300 import Solver
+    out = {"m1": m1, "n": list(ns), "gammas": list(gammas), "rtol": RTOL}
+    rows = {"sqrt_tau_fp32": {}, "c_tau_half_fp32": {}, "c_tau_half_fp64": {}}
+    for nt in ns:
+        for key in rows:
+            rows[key][str(nt)] = []
+        for g in gammas:
+            p = S.variable_2d_problem(gamma=g, m1=m1, n=nt)
+            f = torch.from_numpy(p.f).to(dev)
+            gg = torch.from_numpy(p.g).to(dev)
+            y0 = torch.from_numpy(p.y0).to(dev)
+            c_tau = 0.5 * math.sqrt(p.tau) / (0.5 * math.sqrt(p.tau) + 2.0 * math.sqrt(p.T))
+            for key, eps, prec in (("sqrt_tau_fp32", p.eps, "fp32"), ("c_tau_half_fp32", c_tau, "fp32"),
+                                   ("c_tau_half_fp64", c_tau, "fp64")):
+                s = Solver(2, m1, nt, p.T, g, eps, p.a_nodes, spatial="mg", precision=prec, max_iter=args.cap)
+                b = s.build_rhs(f, gg, y0)
+                _, it, rr = s.solve(b, rtol=RTOL, raise_on_nonconv=False)
+                rows[key][str(nt)].append(it if rr <= RTOL else None)
+                s.close()
+                del b
+            del f, gg, y0
+            torch.cuda.empty_cache()
+    out.update(rows)
+    for key, tab in rows.items():
+        vals = [v for r in tab.values() for v in r if v is not None]
+        out[key + "_range"] = [min(vals), max(vals)] if vals else None
+    return out
+
+
+# process-group backend and device of a rank (one GPU per rank)
+BACKEND = "nccl"
+
+
+def rank_device(local):
+    import torch
+    torch.cuda.set_device(local)
+    return torch.device("cuda", local)
+
+
+def free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_local_ranks(nprocs, argv, script=None, capture=False, timeout=None):
+    """Run `nprocs` copies of the benchmark (or `script`) as ranks 0..nprocs-1 of
+    one job on this node: RANK, LOCAL_RANK, WORLD_SIZE and a free MASTER_PORT on
+    127.0.0.1 in each environment, as torchrun would set them.  Returns the first
+    nonzero exit code (0 if all ranks succeeded) and, with `capture`, each rank's
+    combined output."""
+    port = free_port()
+    procs = []
+    for r in range(nprocs):
+        env = dict(os.environ, WORLD_SIZE=str(nprocs), RANK=str(r), LOCAL_RANK=str(r), LOCAL_WORLD_SIZE=str(nprocs),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, script or os.path.abspath(__file__), *argv], env=env,
+                                      stdout=subprocess.PIPE if capture else None,
+                                      stderr=subprocess.STDOUT if capture else None, text=True))
+    rcs, outs = [], []
+    for p in procs:
+        try:
+            out, _ = p.communicate(timeout=timeout)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            out, _ = p.communicate()
+        rcs.append(p.returncode)
+        outs.append(out)
+    rc = next((c for c in rcs if c), 0)
+    return (rc, outs) if capture else rc
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = dist_init("nccl")
+    dev = rank_device(local)
+    dist = dist_init(BACKEND)
     import synthetic as S
     from paper_2410_22686_gb300 import Solver
     from paper_2410_22686_gb300 import build as pbuild
@@ -468,7 +665,7 @@ def run_ours(args):
     # ---------------- mixed precision (the timed headline)
     sols, rhs = make("fp32")
     ms_mixed, rec_mixed, clocks = timed(sols, rhs, args.steps, args.warmup, profile=True)
-    launches = sum(s.launch_count() for s in sols)
+    launches = int(dist_sum(dist, float(sum(s.launch_count() for s in sols)), dev))  # whole job
     stats = {}
     for s in sols:
         for k, v in s.stats().items():
@@ -559,11 +756,14 @@ def run_ours(args):
     # ---------------- the other workloads of the path
     extras = _extra_workloads(args, torch, dev, dist, ws, rank)
 
+    # ---------------- iteration counts over n and gamma (the iteration-count target)
+    sweep = None if (args.skip_sweep or rank != 0) else iteration_sweep(args, torch, dev, m1=args.m1)
+
     # ---------------- roofline of the dominant kernel class
-    # DRAM bytes (read + write) over algorithmic bytes of one launch, from the ncu
-    # capture summarised in profiles/kernels_gmres_mixed_255x255_n128.md (255^2 x 128,
-    # four basis vectors); a full-size launch moves the same bytes per unknown, so the
-    # traffic of the average timed launch is this ratio times its algorithmic bytes
+    # DRAM bytes (read + write) over algorithmic bytes of one launch, from an ncu
+    # capture of the same kernels at 255^2 x 128 with a four-vector basis; a
+    # full-size launch moves the same bytes per unknown, so the traffic of the
+    # average timed launch is this ratio times its algorithmic bytes
     ncu_traffic_ratio = {"arnoldi_dot": (665.9 + 4.0) / 665.8, "arnoldi_update_norm": (665.9 + 176.8) / 865.6}
     tot_ms = sum(v["ms"] for v in stats.values())
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
@@ -575,26 +775,32 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12     # 2 FP64 FMA/clk/SM at 2070 MHz
+    from paper_2410_22686_gb300 import measure_peaks
+    fp64_peak_tflops, fp32_peak_tflops = measure_peaks()
     dom_avg_ms = dom["ms"] / max(dom["launches"], 1)
     dom_bytes = dom["bytes"] / max(dom["launches"], 1)
     dom_flops = dom["flops"] / max(dom["launches"], 1)
     gbs = dom_bytes / (dom_avg_ms * 1e-3) / 1e9
     tfl = dom_flops / (dom_avg_ms * 1e-3) / 1e12
-    if dom_name in ("arnoldi_dot", "arnoldi_update_norm", "matvec", "x_update") and tfl / fp64_peak_tflops > gbs / hbm_peak:
+    fp64_kernels = ("arnoldi_dot", "arnoldi_update_norm", "matvec", "x_update")
+    if dom_name in fp64_kernels and tfl / fp64_peak_tflops > gbs / hbm_peak:
         roof = {"bound": "alu", "achieved": tfl, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": tfl / fp64_peak_tflops, "traffic": None, "kernel": dom_name,
-                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
-                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+                "peak_source": "FP64 FMA rate measured on this GPU in this run (pc_measure_peaks: "
+                               "register-only FMA chains, best of 5 launches) (of measured)",
+                "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": gbs / hbm_peak,
+                "hbm_peak_source": peak_src}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": None, "kernel": dom_name, "peak_source": peak_src}
     if dom_name in ncu_traffic_ratio:
         roof["traffic"] = ncu_traffic_ratio[dom_name] * dom_bytes
-        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel at "
-                                  "255^2 x 128 (profiles/kernels_gmres_mixed_255x255_n128.md), scaled to "
-                                  "this launch by its algorithmic bytes")
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel in a "
+                                  "capture at 255^2 x 128, scaled to this launch by its algorithmic bytes")
     roof["share_of_kernel_time"] = dom["ms"] / tot_ms if tot_ms else None
+    measured_rates = {"fp64_fma_tflops": fp64_peak_tflops, "fp32_fma_tflops": fp32_peak_tflops,
+                      "hbm_copy_gbs": hbm_peak, "hbm_source": peak_src,
+                      "fp_source": "pc_measure_peaks in this run"}
     breakdown = {k: {"share": v["ms"] / tot_ms if tot_ms else None, "launches": v["launches"],
                      "avg_us": 1000 * v["ms"] / v["launches"] if v["launches"] else None,
                      "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None}
@@ -613,7 +819,8 @@ def run_ours(args):
         "unknowns_iters_per_s": ws * sum(U * it for it in iters_mixed) / (ms_mixed / 1000.0 / args.steps),
         "precond_apply": {"gbs": precond_gbs, "ms": p_ms, "frac_of_hbm": precond_gbs / hbm_peak,
                           "bytes": p_bytes, "precision": "fp32"},
-        "roofline": roof, "kernel_breakdown": breakdown, "other_workloads": extras,
+        "roofline": roof, "measured_peaks": measured_rates, "kernel_breakdown": breakdown,
+        "other_workloads": extras, "iters_sweep": sweep,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 8 * U * len(GAM) * ws,
@@ -623,12 +830,7 @@ def run_ours(args):
                        "during the current solve"},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        t_iter = oracle_iteration_seconds(m1=args.m1, nt=args.nt)
-        mean_it = sum(iters_mixed) / len(iters_mixed)
-        line["cpu_baseline"] = {"value": t_iter * mean_it, "unit": "s/solve", "cores": 1, "kind": "oracle",
-                                "sample": "one oracle GMRES iteration (preconditioner apply, matvec, one "
-                                          "Gram-Schmidt step) on the full workload at gamma=1e-4, times the "
-                                          f"mean GPU iteration count {mean_it:.1f}"}
+        line["cpu_baseline"] = cpu_baseline_record(args.m1, args.nt)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -639,6 +841,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # not started by torchrun: start one rank per GPU here
+        return launch_local_ranks(args.gpus, sys.argv[1:])
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

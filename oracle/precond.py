@@ -312,6 +312,37 @@ def apply_Peps_inv(v: np.ndarray, n: int, alpha: float, eps: float, spatial) -> 
     return np.stack([wt1 - wt2, wt1 + wt2])
 
 
+# ----------------------------------------------------------------------------
+# the ideal RBD preconditioner P by block substitution in time     (Eq. matrix_P)
+# ----------------------------------------------------------------------------
+
+
+def apply_P_inv(v: np.ndarray, n: int, alpha: float, spatial) -> np.ndarray:
+    """w = P^{-1} v for the rotated block-diagonal preconditioner of Eq. matrix_P,
+    P = 1/2 blockdiag(T^T + alpha I, T + alpha I) [[I, I], [-I, I]] (M = I).
+    Its inverse is [[I, -I], [I, I]] blockdiag((T^T + alpha I)^{-1}, (T + alpha I)^{-1}):
+    * (T + alpha I) w2 = v2, T block lower bidiagonal (Eq. matrix_T): forward in time,
+      ((1 + alpha) I + tau K) w2_j = v2_j + w2_{j-1}, w2_0 = 0;
+    * (T^T + alpha I) w1 = v1: backward in time,
+      ((1 + alpha) I + tau K) w1_j = v1_j + w1_{j+1}, w1_{n+1} = 0;
+    then w = [w1 - w2; w1 + w2].  Each step is one spatial solve with the real shift
+    1 + alpha by `spatial` (exact for the dense and sine-transform solvers, one
+    V(1,0) cycle for multigrid): n sequential solves per half, the cost the
+    eps-circulant P_eps removes."""
+    shift = np.array([1.0 + alpha])
+    w1 = np.zeros(v[0].shape)
+    w2 = np.zeros(v[1].shape)
+    prev = np.zeros(v[1].shape[1:])
+    for j in range(n):
+        w2[j] = np.real(spatial(shift, (v[1][j] + prev)[None]))[0]
+        prev = w2[j]
+    nxt = np.zeros(v[0].shape[1:])
+    for j in reversed(range(n)):
+        w1[j] = np.real(spatial(shift, (v[0][j] + nxt)[None]))[0]
+        nxt = w1[j]
+    return np.stack([w1 - w2, w1 + w2])
+
+
 def make_spatial_solver(kind: str, a_nodes, m1: int, d: int, tau: float, smoother: str = "red-black"):
     """'dense' | 'fst' (a constant; a_nodes None means a = 1) | 'mg' (with the given smoother)."""
     if a_nodes is None:

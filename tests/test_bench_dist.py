@@ -195,3 +195,40 @@ def test_batched_extra_logic_with_fake_solvers(monkeypatch):
     assert out["problems"] == 64 and out["ranks"] == 1 and out["converged"] == 64 and out["max_iters"] == 7
     assert out["waves"] >= 1 and out["batch_seconds"] >= 0.0
     assert out["total_unknowns"] == sum(q.unknowns for q in synthetic.batched_problems(64))
+
+
+def test_gpus_flag_starts_the_ranks_itself():
+    """`bench.py --gpus 2` without a torchrun environment starts two ranks of one job;
+    each runs its replica, rank 0 alone prints the line, n_gpus is 2 and the value is
+    the whole job's seconds per solve (slowest rank's time over both ranks' solves)."""
+    import json
+    env_keep = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK") if k in os.environ}
+    try:
+        argv = ["--gpus", "2", "--steps", "2", "--warmup", "3", "--m1", "7", "--nt", "4", "--skip-fp64",
+                "--skip-e2e", "--skip-bf16", "--skip-3d", "--skip-grad", "--skip-batched", "--skip-fst",
+                "--skip-graph", "--skip-sweep", "--no-cpu-baseline"]
+        rc, outs = bench.launch_local_ranks(2, argv, script=os.path.join(ROOT, "tests", "bench_fake_rank.py"),
+                                            capture=True, timeout=240)
+    finally:
+        os.environ.update(env_keep)
+    assert rc == 0, outs
+    assert "fake rank 0 of 2" in outs[0] and "fake rank 1 of 2" in outs[1]
+    lines = [ln for out in outs for ln in out.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1 and lines[0] in outs[0]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["scaling"] == "weak" and d["steps"] == 2
+    # rank 1 sleeps 20 ms per solve: 2 steps x 4 solves = 160 ms at least, over 16 solves
+    assert d["value"] >= 0.160 / 16 * 0.99
+    assert abs(d["value"] - d["ms_per_step"] * 2 / 1000.0 / 16) <= 1e-12
+    assert d["gpu_launches"] == 2 * (2 * 4 * 10)  # both ranks
+
+
+def test_gpus_flag_under_torchrun_environment_does_not_relaunch(monkeypatch):
+    called = []
+    monkeypatch.setattr(bench, "launch_local_ranks", lambda *a, **k: called.append(a) or 0)
+    monkeypatch.setattr(bench, "run_reference", lambda args: 0)
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--gpus", "2", "--impl", "reference"])
+    assert bench.main() == 0 and not called
+    monkeypatch.delenv("WORLD_SIZE")
+    assert bench.main() == 0 and called and called[0][0] == 2

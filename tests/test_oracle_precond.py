@@ -79,6 +79,37 @@ def test_P_eps_tends_to_ideal_P_linearly_in_eps():
     assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8
 
 
+@pytest.mark.parametrize("d,m1,n", [(2, 3, 5), (2, 4, 1), (2, 2, 3), (3, 2, 3), (2, 3, 8)])
+def test_ideal_P_block_substitution_matches_dense_P(d, m1, n):
+    # Eq. matrix_P assembled densely and solved by LU, against the sequential
+    # forward / backward substitution in time with exact spatial solves
+    a, K, tau, alpha = _setup(d, m1, n, seed=3 * d + m1 + n)
+    v = S.random_vector((2, n) + (m1,) * d, 31)
+    ref = np.linalg.solve(pc.P_dense(K, n, tau, alpha), v.ravel())
+    got = pc.apply_P_inv(v, n, alpha, pc.DenseSpatialSolver(a, tau))
+    assert np.linalg.norm(got.ravel() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_ideal_P_with_sine_transforms_equals_dense_solves():
+    a, K, tau, alpha = _setup(2, 7, 6, const=True)
+    v = S.random_vector((2, 6, 7, 7), 32)
+    got = pc.apply_P_inv(v, 6, alpha, pc.FSTSpatialSolver(7, 2, tau))
+    ref = pc.apply_P_inv(v, 6, alpha, pc.DenseSpatialSolver(a, tau))
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_ideal_P_is_the_eps_to_zero_limit_of_the_four_step_apply():
+    # P_eps -> P as eps -> 0 (the eps-circulant corner entry vanishes): the two
+    # independent routes (FFT diagonalisation vs block substitution) meet linearly
+    a, K, tau, alpha = _setup(2, 3, 8)
+    v = S.random_vector((2, 8, 3, 3), 33)
+    sp = pc.DenseSpatialSolver(a, tau)
+    ref = pc.apply_P_inv(v, 8, alpha, sp)
+    errs = [np.linalg.norm(pc.apply_Peps_inv(v, 8, alpha, e, sp) - ref) / np.linalg.norm(ref)
+            for e in (1e-3, 1e-4, 1e-5)]
+    assert errs[0] / errs[1] > 8 and errs[1] / errs[2] > 8 and errs[2] < 1e-4
+
+
 @pytest.mark.parametrize("gamma", [1e-8, 1e-4, 1.0])
 def test_theorem_ideal_spectrum_on_the_line_re_1(gamma):
     # Theorem 2.3 (M = I): sigma(P^{-1} A) lies in {1 + i x, |x| <= 1}
