@@ -84,6 +84,16 @@ typedef enum pc_smoother {
                                     Table 7 exactly; sequential along the grid diagonals, much slower) */
 } pc_smoother;
 
+/* Preconditioner of a handle (pc_set_preconditioner).
+ *   PC_PRECOND_EPS_CIRCULANT: P_eps of Eq. matrix_P_eps, applied by the four
+ *     steps of Section 2.1 (all time blocks in parallel; the default).
+ *   PC_PRECOND_IDEAL_RBD: P of Eq. matrix_P (the paper's comparison, Tables 4
+ *     and 8), applied by block substitution in time: n sequential steps, each
+ *     one spatial solve ((1 + alpha) I + tau K) z = r per half by the handle's
+ *     spatial solver (exact sine transforms or one V(1,0) cycle), half 2 forward
+ *     and half 1 backward in time, then w = [[I, -I], [I, I]] [w1; w2]. */
+typedef enum { PC_PRECOND_EPS_CIRCULANT = 0, PC_PRECOND_IDEAL_RBD = 1 } pc_precond_kind;
+
 typedef struct pc_params {
   int dim;          /* 2 or 3 */
   int m1;           /* interior grid points per dimension, h = 1/(m1+1); multigrid needs m1 = 2^k-1 */
@@ -139,6 +149,13 @@ int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
  * Errors: PC_ERR_ARG (null), PC_ERR_UNSUPPORTED (sine-transform or finite-element
  * handles, whose coefficient must stay constant). */
 int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream);
+
+/* Select the preconditioner used by pc_apply_precond, pc_gmres_solve and
+ * pc_adjoint_solve (pc_precond_kind).  The graph-launched and batched solves
+ * take the eps-circulant one only (PC_ERR_UNSUPPORTED otherwise).  Errors:
+ * PC_ERR_ARG (unknown kind), PC_ERR_UNSUPPORTED (ideal RBD on a finite-element
+ * handle). */
+int pc_set_preconditioner(pc_handle* h, int kind);
 
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
 int pc_destroy(pc_handle* h);

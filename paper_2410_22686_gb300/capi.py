@@ -22,6 +22,7 @@ PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S = 0, 1, 2
 PC_GMRES_RIGHT, PC_GMRES_LEFT = 0, 1
 PC_SPACE_FD, PC_SPACE_FE = 0, 1
 PC_SMOOTHER_RED_BLACK, PC_SMOOTHER_LEXICOGRAPHIC = 0, 1
+PC_PRECOND_EPS_CIRCULANT, PC_PRECOND_IDEAL_RBD = 0, 1
 
 
 class pc_params(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGNATURES = {
     "pc_grad_log_a": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
     "pc_set_log_coefficient": (_i, [_vp, _dp, _vp]),
+    "pc_set_preconditioner": (_i, [_vp, _i]),
     "pc_grad_g": (_i, [_vp, _dp, _dp, _vp]),
     "pc_objective": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_objective_grad": (_i, [_vp, _dp, _dp, _dp, _dp, _dp, _vp]),

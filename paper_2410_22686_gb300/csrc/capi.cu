@@ -52,7 +52,7 @@ const char* kernel_class_name(int kc) {
                                         "normalize",     "givens",       "x_update",
                                         "axpby",         "build_rhs",    "grad_stencil",
                                         "arnoldi_reorth", "mg_coarse_cycle", "mg_down",
-                                        "fe_apply"};
+                                        "fe_apply",      "ideal_rbd_step"};
   return (kc >= 0 && kc < KC_COUNT) ? names[kc] : "?";
 }
 
@@ -183,6 +183,10 @@ struct pc_handle {
   double2* sig1_64 = nullptr;  // the shift 1 (end-point solves)
   float2* sig1_32 = nullptr;
   float2* sig32 = nullptr;
+  // ideal RBD preconditioner (Eq. matrix_P): the real shift 1 + alpha of both planes
+  int precond_kind = PC_PRECOND_EPS_CIRCULANT;
+  double2* sigP64 = nullptr;
+  float2* sigP32 = nullptr;
   // FST tables
   double* S64 = nullptr;
   float* S32 = nullptr;
@@ -259,6 +263,7 @@ static void release(pc_handle* h) {
 }
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static void drop_graphs(pc_handle* h);
 
 // a must be finite, > 0 at interior nodes and >= 0 at boundary nodes (faces to the
 // boundary then carry a_f = (a_P + a_Q)/2 > 0, so K stays symmetric positive definite)
@@ -612,6 +617,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     const std::vector<double> one{1.0}, zero{0.0};
     if ((rc = upload_c(h, (void**)&h->sig1_64, one, zero, false, st))) goto fail_out;
     if ((rc = upload_c(h, (void**)&h->sig1_32, one, zero, true, st))) goto fail_out;
+    const std::vector<double> shiftP(2, 1.0 + h->alpha), zero2(2, 0.0);
+    if ((rc = upload_c(h, (void**)&h->sigP64, shiftP, zero2, false, st))) goto fail_out;
+    if ((rc = upload_c(h, (void**)&h->sigP32, shiftP, zero2, true, st))) goto fail_out;
   }
   // ---- FST tables (constant a)
   if (spatial == PC_SPATIAL_FST) {
@@ -781,6 +789,17 @@ extern "C" int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* s
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_set_log_coefficient");
 }
 
+extern "C" int pc_set_preconditioner(pc_handle* h, int kind) {
+  if (!h) return fail(PC_ERR_ARG, "pc_set_preconditioner: null handle");
+  if (kind != PC_PRECOND_EPS_CIRCULANT && kind != PC_PRECOND_IDEAL_RBD)
+    return fail(PC_ERR_ARG, "pc_set_preconditioner: unknown kind");
+  if (kind == PC_PRECOND_IDEAL_RBD && h->fe)
+    return fail(PC_ERR_UNSUPPORTED, "pc_set_preconditioner: the ideal RBD preconditioner needs finite differences");
+  if (kind != h->precond_kind) drop_graphs(h);
+  h->precond_kind = kind;
+  return PC_OK;
+}
+
 extern "C" int pc_destroy(pc_handle* h) {
   if (!h) return PC_OK;
   cudaDeviceSynchronize();
@@ -829,6 +848,7 @@ struct Tables<double> {
   static const double2* tw(const pc_handle* h) { return h->tw64; }
   static const double2* sig(const pc_handle* h) { return h->sig64; }
   static const double2* sig1(const pc_handle* h) { return h->sig1_64; }
+  static const double2* sigP(const pc_handle* h) { return h->sigP64; }
   static const double* S(const pc_handle* h) { return h->S64; }
   static const double* lamK(const pc_handle* h) { return h->lamK64; }
   static const double* rmass(const pc_handle* h) { return h->rmass64; }
@@ -841,6 +861,7 @@ struct Tables<float> {
   static const float2* tw(const pc_handle* h) { return h->tw32; }
   static const float2* sig(const pc_handle* h) { return h->sig32; }
   static const float2* sig1(const pc_handle* h) { return h->sig1_32; }
+  static const float2* sigP(const pc_handle* h) { return h->sigP32; }
   static const float* S(const pc_handle* h) { return h->S32; }
   static const float* lamK(const pc_handle* h) { return h->lamK32; }
   static const float* rmass(const pc_handle* h) { return h->rmass32; }
@@ -973,10 +994,31 @@ static FineCorrection<TU> fine_correction(const pc_handle* h) {
 
 // w = P^{-1} v; with jdev != nullptr the output is w + j*stride and, when index_input,
 // the input v + j*stride (an FP32 input is the single rounded copy of the basis vector)
+// w = P^{-1} v for the ideal RBD preconditioner of Eq. matrix_P: n sequential
+// steps, each one spatial solve of two planes with the real shift 1 + alpha (half 2
+// forward in time, half 1 backward), then the rotation [[I, -I], [I, I]]
+template <typename Tc, typename TU, typename Tout, typename Tin>
+static cudaError_t precond_ideal_t(pc_handle* h, Launch& L, const Tin* v, Tout* w) {
+  typedef typename Cx<Tc>::t C;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j <= h->n; ++j) {
+    if ((e = launch_ideal_step<Tc, TU, Tin, Tout>(L, v, (const TU*)h->lv[0].u, (C*)h->lv[0].r, w, h->ms, h->n, j)) !=
+        cudaSuccess)
+      return e;
+    if (j == h->n) break;
+    if ((e = spatial_solve<Tc, TU>(h, L, 2, Tables<Tc>::sigP(h), true)) != cudaSuccess) return e;
+  }
+  return launch_rbd_butterfly<Tout>(L, w, (int64_t)h->n * h->ms);
+}
+
 template <typename Tc, typename TU, typename Tout, typename Tin = double>
 static cudaError_t precond_t(pc_handle* h, Launch& L, const Tin* v, Tout* w, size_t stride = 0,
                              const int* jdev = nullptr, bool index_input = true) {
   typedef typename Cx<Tc>::t C;
+  if (h->precond_kind == PC_PRECOND_IDEAL_RBD) {
+    if (stride != 0 || jdev != nullptr) return cudaErrorNotSupported;  // graph solves reject it first
+    return precond_ideal_t<Tc, TU, Tout, Tin>(h, L, v, w);
+  }
   cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::dinv(h),
                                           Tables<Tc>::tw(h), (C*)h->lv[0].r, index_input ? stride : 0,
                                           index_input ? jdev : nullptr);
@@ -1362,6 +1404,8 @@ extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, doub
 
 static int graph_supported(const pc_handle* h, int maxit) {
   if (maxit < 1 || maxit > h->cap) return fail(PC_ERR_ARG, "graph solve: maxit must be in [1, max_iter]");
+  if (h->precond_kind != PC_PRECOND_EPS_CIRCULANT)
+    return fail(PC_ERR_UNSUPPORTED, "graph solve: the eps-circulant preconditioner only");
   if (!is_pow2(h->n)) return fail(PC_ERR_UNSUPPORTED, "graph solve: n must be a power of two");
   const int nmax = h->fp32 ? 1024 : 256;
   if (h->n > nmax) return fail(PC_ERR_UNSUPPORTED, "graph solve: n too large for the register FFT");

@@ -140,6 +140,7 @@ enum KernelClass {
   KC_MG_COARSE,
   KC_MG_DOWN,  // fused smooth + residual + restriction of one level
   KC_FE_APPLY, // finite-element mass / stiffness product of single fields
+  KC_IDEAL_STEP,  // ideal RBD preconditioner: per-time-step right-hand sides and the final rotation
   KC_COUNT
 };
 const char* kernel_class_name(int kc);
@@ -416,6 +417,12 @@ cudaError_t launch_objective(Launch& L, const double* x, const double* g, int64_
                              double* partial, int max_partial, double* J);
 cudaError_t launch_objective_grad(Launch& L, const double* x, const double* g, int64_t half, double gamma, double c,
                                   const double* gJ, double* gx, double* gg);
+// ideal RBD preconditioner (Eq. matrix_P): step j of the two block substitutions in time
+template <typename Tc, typename TU, typename Tin, typename Tout>
+cudaError_t launch_ideal_step(Launch& L, const Tin* v, const TU* u, typename Cx<Tc>::t* r, Tout* w, int64_t ms, int n,
+                              int j);
+template <typename T>
+cudaError_t launch_rbd_butterfly(Launch& L, T* w, int64_t half);
 cudaError_t launch_grad_chunked(Launch& L, const Grid& g, int n, double scale, const double* a_int, const double* x,
                                 const double* lam, double* partial, int tj, double* grad);
 

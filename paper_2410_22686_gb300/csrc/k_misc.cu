@@ -267,6 +267,44 @@ __global__ void objective_grad_kernel(const double* __restrict__ x, const double
   }
 }
 
+// One step of the ideal RBD apply (Eq. matrix_P) by block substitution in time.
+// The solutions of step j-1 -- spectral planes 0 and 1 of u, real parts: half 2
+// at time j-1 (forward substitution for T + alpha I) and half 1 at time n-j
+// (backward substitution for T^T + alpha I) -- are stored into w, and the
+// right-hand sides of step j are formed as real planes 0 and 1 of r:
+//   v2_j + w2_{j-1}  and  v1_{n-1-j} + w1_{n-j}  (zero predecessors at j = 0).
+template <typename Tc, typename TU, typename Tin, typename Tout>
+__global__ void ideal_step_kernel(const Tin* __restrict__ v, const TU* __restrict__ u,
+                                  typename Cx<Tc>::t* __restrict__ r, Tout* __restrict__ w, int64_t ms, int n,
+                                  int j) {
+  const int64_t half = (int64_t)n * ms;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += stride) {
+    Tc u2 = Tc(0), u1 = Tc(0);
+    if (j > 0) {
+      u2 = ldc(u, s).x;
+      u1 = ldc(u, ms + s).x;
+      w[half + (int64_t)(j - 1) * ms + s] = cvt<Tout>(u2);
+      w[(int64_t)(n - j) * ms + s] = cvt<Tout>(u1);
+    }
+    if (j < n) {
+      r[s] = cmk<Tc>(cvt<Tc>(v[half + (int64_t)j * ms + s]) + u2, Tc(0));
+      r[ms + s] = cmk<Tc>(cvt<Tc>(v[(int64_t)(n - 1 - j) * ms + s]) + u1, Tc(0));
+    }
+  }
+}
+
+// w = [[I, -I], [I, I]] [w1; w2] in place (the last factor of P^{-1})
+template <typename T>
+__global__ void rbd_butterfly_kernel(T* __restrict__ w, int64_t half) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < half; e += stride) {
+    const T a = w[e], b = w[half + e];
+    w[e] = a - b;
+    w[half + e] = a + b;
+  }
+}
+
 static unsigned grid_for(int64_t len) {
   int64_t b = (len + 255) / 256;
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -353,6 +391,34 @@ cudaError_t launch_objective_grad(Launch& L, const double* x, const double* g, i
                                                              gg);
   return L.end(KC_GRAD, (24.0 + (gx ? 16.0 : 0.0) + (gg ? 8.0 : 0.0)) * half, 6.0 * half);
 }
+
+template <typename Tc, typename TU, typename Tin, typename Tout>
+cudaError_t launch_ideal_step(Launch& L, const Tin* v, const TU* u, typename Cx<Tc>::t* r, Tout* w, int64_t ms, int n,
+                              int j) {
+  L.begin(KC_IDEAL_STEP);
+  ideal_step_kernel<Tc, TU, Tin, Tout><<<grid_for(ms), 256, 0, L.stream>>>(v, u, r, w, ms, n, j);
+  const double rd = j > 0 ? 2.0 * sizeof(TU) + 2.0 * sizeof(Tout) : 0.0;
+  const double wr = j < n ? 2.0 * sizeof(Tin) + 2.0 * sizeof(typename Cx<Tc>::t) : 0.0;
+  return L.end(KC_IDEAL_STEP, (rd + wr) * ms, 2.0 * ms);
+}
+#define PCOPT_IDEAL_STEP(TC, TU, TIN, TOUT)                                                                   \
+  template cudaError_t launch_ideal_step<TC, TU, TIN, TOUT>(Launch&, const TIN*, const TU*, Cx<TC>::t*, TOUT*, \
+                                                            int64_t, int, int);
+PCOPT_IDEAL_STEP(double, double2, double, double)
+PCOPT_IDEAL_STEP(float, float2, double, double)
+PCOPT_IDEAL_STEP(float, float2, float, float)
+PCOPT_IDEAL_STEP(float, __nv_bfloat162, double, double)
+PCOPT_IDEAL_STEP(float, __nv_bfloat162, float, float)
+#undef PCOPT_IDEAL_STEP
+
+template <typename T>
+cudaError_t launch_rbd_butterfly(Launch& L, T* w, int64_t half) {
+  L.begin(KC_IDEAL_STEP);
+  rbd_butterfly_kernel<T><<<grid_for(half), 256, 0, L.stream>>>(w, half);
+  return L.end(KC_IDEAL_STEP, 4.0 * sizeof(T) * half, 2.0 * half);
+}
+template cudaError_t launch_rbd_butterfly<double>(Launch&, double*, int64_t);
+template cudaError_t launch_rbd_butterfly<float>(Launch&, float*, int64_t);
 
 cudaError_t launch_endpoint_rhs(Launch& L, const double* x, int64_t ms, int n, double tau, double gamma,
                                 const double* fT, const double* g0, const double* y0, const double* pN, double* rhs_y,

@@ -19,6 +19,7 @@ _PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": ca
 _MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
 _SPACE = {"fd": capi.PC_SPACE_FD, "fe": capi.PC_SPACE_FE}
 _SMOOTHER = {"red-black": capi.PC_SMOOTHER_RED_BLACK, "lexicographic": capi.PC_SMOOTHER_LEXICOGRAPHIC}
+_PRECOND = {"eps-circulant": capi.PC_PRECOND_EPS_CIRCULANT, "ideal": capi.PC_PRECOND_IDEAL_RBD}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -121,6 +122,14 @@ class Solver:
         if log_a.numel() != self.ms:
             raise ValueError(f"log_a must hold {self.ms} values")
         capi.check(self.lib.pc_set_log_coefficient(self.h, _ptr(log_a), _stream()))
+
+    def set_preconditioner(self, kind: str):
+        """"eps-circulant" (P_eps, the default) or "ideal" (P of Eq. matrix_P by block
+        substitution in time: the paper's comparison preconditioner)."""
+        if kind not in _PRECOND:
+            raise ValueError(f"kind must be one of {sorted(_PRECOND)}, got {kind!r}")
+        capi.check(self.lib.pc_set_preconditioner(self.h, _PRECOND[kind]))
+        self.precond_kind = kind
 
     # ---------------------------------------------------------------- helpers
     def empty_vector(self):
