@@ -51,7 +51,8 @@ typedef enum pc_status {
   PC_ERR_OOM = 3,            /* device allocation failed in pc_setup */
   PC_ERR_NOT_CONVERGED = 4,  /* Krylov solver hit max_iter; x holds the last iterate */
   PC_ERR_BREAKDOWN = 5,      /* NaN/Inf in a residual or Arnoldi coefficient */
-  PC_ERR_UNSUPPORTED = 6     /* valid request outside what this build implements */
+  PC_ERR_UNSUPPORTED = 6,    /* valid request outside what this build implements */
+  PC_ERR_TIMEOUT = 7         /* a bounded device-side wait (streamed copy) ran out; the result is invalid */
 } pc_status;
 
 typedef enum pc_spatial {
@@ -93,6 +94,28 @@ typedef enum pc_smoother {
  *     spatial solver (exact sine transforms or one V(1,0) cycle), half 2 forward
  *     and half 1 backward in time, then w = [[I, -I], [I, I]] [w1; w2]. */
 typedef enum { PC_PRECOND_EPS_CIRCULANT = 0, PC_PRECOND_IDEAL_RBD = 1 } pc_precond_kind;
+
+/* Arnoldi precision of GMRES (pc_set_arnoldi).  The paper fixes none (Section 3
+ * runs MATLAB's FP64 gmres); these choose how the orthogonalisation of flexible
+ * GMRES with the FP32 preconditioner uses GB300's small FP64 unit.
+ *   PC_ARNOLDI_AUTO: FP64 handles as PC_ARNOLDI_FP64, mixed handles as
+ *     PC_ARNOLDI_DOUBLE_FLOAT.
+ *   PC_ARNOLDI_FP64: FP64 basis and FP64 products in the first Gram-Schmidt
+ *     pass; on mixed handles the selective second pass takes FP32 products of
+ *     20-bit truncations and the inner matvec of the FP32 basis is double-float.
+ *   PC_ARNOLDI_FP64_STRICT: FP64 basis and FP64 products everywhere, the second
+ *     pass and the inner matvec (FP32 input, FP64 arithmetic) included.
+ *   PC_ARNOLDI_DOUBLE_FLOAT (mixed handles): each basis vector stored as two FP32
+ *     planes, v = hi + lo to ~2^-48 relative (hi is the FP32 rounding the
+ *     preconditioner reads); dot products and updates as error-free FP32
+ *     transformations (FMA product errors, TwoSum), scalars and reductions in
+ *     FP64; the second pass takes FP32 products of the hi planes. */
+typedef enum {
+  PC_ARNOLDI_AUTO = 0,
+  PC_ARNOLDI_FP64 = 1,
+  PC_ARNOLDI_FP64_STRICT = 2,
+  PC_ARNOLDI_DOUBLE_FLOAT = 3
+} pc_arnoldi;
 
 typedef struct pc_params {
   int dim;          /* 2 or 3 */
@@ -156,6 +179,11 @@ int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream);
  * PC_ERR_ARG (unknown kind), PC_ERR_UNSUPPORTED (ideal RBD on a finite-element
  * handle). */
 int pc_set_preconditioner(pc_handle* h, int kind);
+
+/* Select the Arnoldi precision (pc_arnoldi) of later solves on the handle.
+ * Errors: PC_ERR_ARG (unknown mode), PC_ERR_UNSUPPORTED (double-float basis on an
+ * FP64 handle). */
+int pc_set_arnoldi(pc_handle* h, int mode);
 
 /* Release the handle and its workspace (waits for its work to finish).  NULL is a no-op. */
 int pc_destroy(pc_handle* h);

@@ -16,13 +16,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpcopt.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pcopt.h")
 
-PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_NOT_CONVERGED, PC_ERR_BREAKDOWN, PC_ERR_UNSUPPORTED = range(7)
+(PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_NOT_CONVERGED, PC_ERR_BREAKDOWN, PC_ERR_UNSUPPORTED,
+ PC_ERR_TIMEOUT) = range(8)
 PC_SPATIAL_AUTO, PC_SPATIAL_FST, PC_SPATIAL_MG = 0, 1, 2
 PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S = 0, 1, 2
 PC_GMRES_RIGHT, PC_GMRES_LEFT = 0, 1
 PC_SPACE_FD, PC_SPACE_FE = 0, 1
 PC_SMOOTHER_RED_BLACK, PC_SMOOTHER_LEXICOGRAPHIC = 0, 1
 PC_PRECOND_EPS_CIRCULANT, PC_PRECOND_IDEAL_RBD = 0, 1
+PC_ARNOLDI_AUTO, PC_ARNOLDI_FP64, PC_ARNOLDI_FP64_STRICT, PC_ARNOLDI_DOUBLE_FLOAT = 0, 1, 2, 3
 
 
 class pc_params(ctypes.Structure):
@@ -78,6 +80,7 @@ _SIGNATURES = {
     "pc_grad_log_a_noalloc": (_i, [_i, _i, _i, _d, _dp, _dp, _dp, _dp, _vp]),
     "pc_set_log_coefficient": (_i, [_vp, _dp, _vp]),
     "pc_set_preconditioner": (_i, [_vp, _i]),
+    "pc_set_arnoldi": (_i, [_vp, _i]),
     "pc_grad_g": (_i, [_vp, _dp, _dp, _vp]),
     "pc_objective": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_objective_grad": (_i, [_vp, _dp, _dp, _dp, _dp, _dp, _vp]),

@@ -185,6 +185,8 @@ struct pc_handle {
   float2* sig32 = nullptr;
   // ideal RBD preconditioner (Eq. matrix_P): the real shift 1 + alpha of both planes
   int precond_kind = PC_PRECOND_EPS_CIRCULANT;
+  int arnoldi = PC_ARNOLDI_AUTO;  // pc_arnoldi: basis storage and product precision of flexible GMRES
+  size_t pl = 0;                  // plane stride of a double-float basis vector (floats)
   double2* sigP64 = nullptr;
   float2* sigP32 = nullptr;
   // FST tables
@@ -660,7 +662,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     const size_t U = h->U;
     const int cap = h->cap;
     h->nblocks = num_sms() * kMaxBlocksPerSM;
-    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * U))) goto fail_out;
+    // basis: cap + 1 vectors; a double-float basis stores each as two FP32 planes of
+    // pl = U rounded up to 64 floats (aligned bulk copies), i.e. pl doubles per vector
+    h->pl = (U + 63) & ~(size_t)63;
+    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * h->pl))) goto fail_out;
     if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
     if (h->fp32 && (rc = dev_alloc_t(h, &h->vf32, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
@@ -673,6 +678,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = dev_alloc_t(h, &h->hcol, (size_t)2 * (cap + 1)))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->ycoef, (size_t)cap + 1))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->scal, 16))) goto fail_out;
+    if (cudaMemsetAsync(h->scal, 0, 16 * sizeof(double), st) != cudaSuccess) {
+      rc = fail(PC_ERR_CUDA, "pc_setup: scalar workspace");
+      goto fail_out;
+    }
     if ((rc = dev_alloc_t(h, &h->partial, (size_t)h->nblocks * (cap + 2)))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->idx, 4))) goto fail_out;
     // scalars come back through mapped pinned memory written by a kernel, so the
@@ -797,6 +806,16 @@ extern "C" int pc_set_preconditioner(pc_handle* h, int kind) {
     return fail(PC_ERR_UNSUPPORTED, "pc_set_preconditioner: the ideal RBD preconditioner needs finite differences");
   if (kind != h->precond_kind) drop_graphs(h);
   h->precond_kind = kind;
+  return PC_OK;
+}
+
+extern "C" int pc_set_arnoldi(pc_handle* h, int mode) {
+  if (!h) return fail(PC_ERR_ARG, "pc_set_arnoldi: null handle");
+  if (mode < PC_ARNOLDI_AUTO || mode > PC_ARNOLDI_DOUBLE_FLOAT) return fail(PC_ERR_ARG, "pc_set_arnoldi: unknown mode");
+  if (mode == PC_ARNOLDI_DOUBLE_FLOAT && !h->fp32)
+    return fail(PC_ERR_UNSUPPORTED, "pc_set_arnoldi: the double-float basis serves the FP32 preconditioner");
+  if (mode != h->arnoldi) drop_graphs(h);
+  h->arnoldi = mode;
   return PC_OK;
 }
 
@@ -1011,16 +1030,19 @@ static cudaError_t precond_ideal_t(pc_handle* h, Launch& L, const Tin* v, Tout* 
   return launch_rbd_butterfly<Tout>(L, w, (int64_t)h->n * h->ms);
 }
 
+// (in_stride, when nonzero, indexes the input instead of stride: the hi planes of a
+// double-float basis lie 2 U apart)
 template <typename Tc, typename TU, typename Tout, typename Tin = double>
 static cudaError_t precond_t(pc_handle* h, Launch& L, const Tin* v, Tout* w, size_t stride = 0,
-                             const int* jdev = nullptr, bool index_input = true) {
+                             const int* jdev = nullptr, bool index_input = true, size_t in_stride = 0) {
   typedef typename Cx<Tc>::t C;
   if (h->precond_kind == PC_PRECOND_IDEAL_RBD) {
     if (stride != 0 || jdev != nullptr) return cudaErrorNotSupported;  // graph solves reject it first
     return precond_ideal_t<Tc, TU, Tout, Tin>(h, L, v, w);
   }
   cudaError_t e = launch_tfft_forward<Tc>(L, h->ms, h->n, v, Tables<Tc>::dpow(h), Tables<Tc>::dinv(h),
-                                          Tables<Tc>::tw(h), (C*)h->lv[0].r, index_input ? stride : 0,
+                                          Tables<Tc>::tw(h), (C*)h->lv[0].r,
+                                          index_input ? (in_stride ? in_stride : stride) : 0,
                                           index_input ? jdev : nullptr);
   if (e != cudaSuccess) return e;
   if ((e = spatial_solve<Tc, TU>(h, L)) != cudaSuccess) return e;
@@ -1032,10 +1054,18 @@ static cudaError_t precond_t(pc_handle* h, Launch& L, const Tin* v, Tout* w, siz
 // FP32 preconditioner into Tout, with the handle's iterate storage
 template <typename Tout, typename Tin = double>
 static cudaError_t precond32(pc_handle* h, Launch& L, const Tin* v, Tout* w, size_t stride = 0,
-                             const int* jdev = nullptr, bool index_input = true) {
-  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout, Tin>(h, L, v, w, stride, jdev, index_input)
-                  : precond_t<float, float2, Tout, Tin>(h, L, v, w, stride, jdev, index_input);
+                             const int* jdev = nullptr, bool index_input = true, size_t in_stride = 0) {
+  return h->bf16s ? precond_t<float, __nv_bfloat162, Tout, Tin>(h, L, v, w, stride, jdev, index_input, in_stride)
+                  : precond_t<float, float2, Tout, Tin>(h, L, v, w, stride, jdev, index_input, in_stride);
 }
+
+// Arnoldi precision of flexible GMRES with the FP32 preconditioner: a double-float
+// basis (the default) or an FP64 one; strict: FP64 products everywhere, including the
+// re-orthogonalisation pass and the inner matvec of the FP32 basis
+static bool arnoldi_df(const pc_handle* h) {
+  return h->fp32 && (h->arnoldi == PC_ARNOLDI_AUTO || h->arnoldi == PC_ARNOLDI_DOUBLE_FLOAT);
+}
+static bool arnoldi_strict(const pc_handle* h) { return h->arnoldi == PC_ARNOLDI_FP64_STRICT; }
 
 // w (FP64) = P^{-1} v in the handle's precision
 static cudaError_t precond64(pc_handle* h, Launch& L, const double* v, double* w) {
@@ -1064,6 +1094,9 @@ static cudaError_t matvec_basis(pc_handle* h, Launch& L, const void* z, double* 
                                              jdev)
                    : launch_matvec_fe<double>(L, g, h->n, h->alpha, h->fes, h->tau, (const double*)z, y, false, zs,
                                               ys, jdev);
+  if (h->fp32 && arnoldi_strict(h))
+    return launch_matvec<float>(L, g, h->n, Stencil<double>{h->lv[0].w64, h->lv[0].d64}, h->alpha, (const float*)z,
+                                y, false, zs, ys, jdev);
   if (h->fp32) return launch_matvec_df(L, g, h->n, h->wdf, h->ddf, h->alpha_df, (const float*)z, y, zs, ys, jdev);
   return launch_matvec<double>(L, g, h->n, Stencil<double>{h->lv[0].w64, h->lv[0].d64}, h->alpha,
                                (const double*)z, y, false, zs, ys, jdev);
@@ -1187,9 +1220,11 @@ static int fetch_scalars(pc_handle* h, cudaStream_t st, const double* src, int n
   return PC_OK;
 }
 
-// host[0] = est, host[1] = ref, host[8] = re-orthogonalisation flag of the last step
+// host[0] = est, host[1] = ref, host[8] = re-orthogonalisation flag of the last step,
+// host[9] = error word of the bounded waits (scal[10]; nonzero: a wait ran out)
 static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref, bool* reorth = nullptr) {
-  if (int rc = fetch_scalars(h, st, h->scal + 1, 9, 0)) return rc;
+  if (int rc = fetch_scalars(h, st, h->scal + 1, 10, 0)) return rc;
+  if (h->host[9] != 0.0) return fail(PC_ERR_TIMEOUT, "a bounded device wait ran out (streamed basis copy)");
   if (est) *est = h->host[0];
   if (ref) *ref = h->host[1];
   if (reorth) *reorth = h->host[8] != 0.0;
@@ -1224,18 +1259,32 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   PC_CUDA(cudaStreamSynchronize(st));
   const bool x0_zero = h->host[2] == 0.0;
 
+  // double-float basis: vector i = FP32 planes hi, lo at Vf + i * ldf (flexible GMRES only)
+  const bool df = mode == PC_GMRES_RIGHT && arnoldi_df(h);
+  const bool lp_reorth = !arnoldi_strict(h);
+  float* Vf = reinterpret_cast<float*>(V);
+  const size_t pl = h->pl, ldf = 2 * pl;
+  double* werr = h->scal + 10;
+  PC_CUDA(cudaMemsetAsync(werr, 0, sizeof(double), st));
+  const double* r0 = V;  // r0 before normalisation (double-float basis: b itself or tbuf)
+
   // reference norm and r0 (stored unnormalised in V_0)
   if (mode == PC_GMRES_RIGHT) {
     GM_CUDA(launch_norm2(L, b, U, h->partial, nrm2));
     GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 1));  // ref = ||b||
+    double* r0w = df ? h->tbuf : V;
     if (x0_zero) {
-      PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (df)
+        r0 = b;
+      else
+        PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
       GM_CUDA(matvec_any(h, L, x, false, h->wbuf, false));
-      PC_CUDA(cudaMemcpyAsync(V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, V, U));
+      PC_CUDA(cudaMemcpyAsync(r0w, b, U * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GM_CUDA(launch_axpby<double>(L, -1.0, h->wbuf, 1.0, r0w, U));
+      r0 = r0w;
     }
-    GM_CUDA(launch_norm2(L, V, U, h->partial, nrm2));
+    GM_CUDA(launch_norm2(L, r0, U, h->partial, nrm2));
     GM_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, est, ref, 0));
   } else {
     GM_CUDA(precond64(h, L, b, V));  // P^{-1} b
@@ -1270,15 +1319,36 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   }
   // flexible GMRES with the FP32 preconditioner reads the FP32 rounding of each new
   // basis vector, written by the kernels that finish it (scale / update)
-  float* vf = (mode == PC_GMRES_RIGHT && h->fp32) ? h->vf32 : nullptr;
-  GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr, vf));
+  float* vf = (mode == PC_GMRES_RIGHT && h->fp32 && !df) ? h->vf32 : nullptr;
+  if (df)
+    GM_CUDA(launch_split_scale(L, r0, Vf, pl, U, nrm2));
+  else
+    GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr, vf));
 
   int k = 0;
   bool converged = false;
   for (int j = 0; j < maxit; ++j) {
     double* vj = V + (size_t)j * U;
     double* vn = V + (size_t)(j + 1) * U;
-    if (mode == PC_GMRES_RIGHT) {
+    if (df) {
+      // double-float basis: the preconditioner reads the hi plane of v_j, A z_j goes to
+      // wbuf (FP64), the new vector's planes are written by the update
+      float* zj = (float*)h->Z + (size_t)j * U;
+      float* vnf = Vf + (size_t)(j + 1) * ldf;
+      GM_CUDA(precond32<float, float>(h, L, Vf + (size_t)j * ldf, zj));
+      GM_CUDA(matvec_basis(h, L, zj, h->wbuf));
+      GM_CUDA(launch_multidot_df(L, Vf, ldf, pl, j + 1, h->wbuf, nullptr, U, h->partial, h->hcol, AS.ww, nullptr,
+                                 werr));
+      GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
+      GM_CUDA(launch_update_df(L, Vf, ldf, pl, j + 1, h->hcol, h->wbuf, vnf, U, AS.inv, h->partial, AS.q, nullptr,
+                               werr));
+      GM_CUDA(launch_arnoldi_check(L, AS));
+      GM_CUDA(launch_multidot_df(L, Vf, ldf, pl, j + 1, nullptr, vnf, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
+                                 werr));
+      GM_CUDA(launch_update_df(L, Vf, ldf, pl, j + 1, h->hcol + ldh, nullptr, vnf, U, nullptr, h->partial, AS.rho2,
+                               AS.flag, werr));
+      GM_CUDA(launch_scale_df(L, vnf, pl, U, AS.rho2, AS.flag));
+    } else if (mode == PC_GMRES_RIGHT) {
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
         GM_CUDA(precond32<float, float>(h, L, vf, zj));
@@ -1292,20 +1362,25 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       GM_CUDA(matvec_any(h, L, vj, false, h->wbuf, false));
       GM_CUDA(precond64(h, L, h->wbuf, vn));
     }
-    // classical Gram-Schmidt with Pythagorean normalisation, re-orthogonalised only
-    // when the check flags cancellation (the gated kernels then do the work)
-    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol, AS.ww, nullptr));
-    GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
-    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol, vn, U, AS.inv, h->partial, AS.q, nullptr, vf));
-    GM_CUDA(launch_arnoldi_check(L, AS));
-    GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
-    GM_CUDA(launch_update(L, V, U, j + 1, h->hcol + ldh, vn, U, nullptr, h->partial, AS.rho2, AS.flag));
-    GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag, vf));
+    if (!df) {
+      // classical Gram-Schmidt with Pythagorean normalisation, re-orthogonalised only
+      // when the check flags cancellation (the gated kernels then do the work)
+      GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol, AS.ww, nullptr));
+      GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
+      GM_CUDA(launch_update(L, V, U, j + 1, h->hcol, vn, U, AS.inv, h->partial, AS.q, nullptr, vf));
+      GM_CUDA(launch_arnoldi_check(L, AS));
+      GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol + ldh, nullptr, AS.flag, lp_reorth));
+      GM_CUDA(launch_update(L, V, U, j + 1, h->hcol + ldh, vn, U, nullptr, h->partial, AS.rho2, AS.flag, nullptr,
+                            lp_reorth));
+      GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag, vf));
+    }
     GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, est, ref));
     bool reorth = false;
     if (int rc = read_scalars(h, st, &est_h, nullptr, &reorth)) return rc;
     if (reorth) {  // book the second Gram-Schmidt pass that ran
-      h->prof.bytes[KC_REORTH] += 8.0 * U * (2.0 * (j + 1) + 6.0);
+      // double-float basis: hi planes read twice (4 B each), the new vector's planes read
+      // three times and written twice; FP64 basis: 8 B per basis read, 6 vector passes
+      h->prof.bytes[KC_REORTH] += df ? 4.0 * U * (2.0 * (j + 1) + 11.0) : 8.0 * U * (2.0 * (j + 1) + 6.0);
       h->prof.flops[KC_REORTH] += 4.0 * U * (j + 1);
       h->prof.launches[KC_REORTH]++;
     }
@@ -1420,8 +1495,13 @@ static int enqueue_pre(pc_handle* h, Launch& L, const double* b, double* x, doub
   GR_CUDA(cudaMemsetAsync(x, 0, U * sizeof(double), L.stream));
   GR_CUDA(launch_norm2(L, b, U, h->partial, nrm2));
   GR_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, h->scal + 1, h->scal + 2, 1));
-  GR_CUDA(cudaMemcpyAsync(h->V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, L.stream));
-  GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr, h->fp32 ? h->vf32 : nullptr));
+  if (arnoldi_df(h)) {
+    GR_CUDA(cudaMemsetAsync(h->scal + 10, 0, sizeof(double), L.stream));
+    GR_CUDA(launch_split_scale(L, b, reinterpret_cast<float*>(h->V), h->pl, U, nrm2));
+  } else {
+    GR_CUDA(cudaMemcpyAsync(h->V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, L.stream));
+    GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr, h->fp32 ? h->vf32 : nullptr));
+  }
   GR_CUDA(launch_loop_start(L, h->idx, h->idx + 1, h->scal + 1, rtol, hc));
   return PC_OK;
 }
@@ -1432,6 +1512,30 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   const int ldh = h->cap + 1;
   const int* j = h->idx;
   const ArnoldiScalars AS{h->scal + 4, h->scal + 5, h->scal + 6, h->scal + 7, h->scal + 8, h->scal + 9};
+  if (arnoldi_df(h)) {
+    // double-float basis (vectors 2 pl floats apart): see gmres_impl
+    float* Z = (float*)h->Z;
+    float* Vf = reinterpret_cast<float*>(h->V);
+    const size_t pl = h->pl, ldf = 2 * pl;
+    double* werr = h->scal + 10;
+    GR_CUDA((precond32<float, float>(h, L, Vf, Z, U, j, true, ldf)));
+    GR_CUDA(matvec_basis(h, L, Z, h->wbuf, U, 0, j));
+    GR_CUDA(launch_multidot_df_dev(L, Vf, ldf, pl, maxit, j, h->wbuf, U, h->partial, h->hcol, AS.ww, nullptr, werr));
+    GR_CUDA(launch_arnoldi_prep_dev(L, j, h->hcol, AS));
+    GR_CUDA(launch_update_df_dev(L, Vf, ldf, pl, maxit, j, h->hcol, h->wbuf, U, AS.inv, h->partial, AS.q, nullptr,
+                                 werr));
+    GR_CUDA(launch_arnoldi_check(L, AS));
+    GR_CUDA(launch_multidot_df_dev(L, Vf, ldf, pl, maxit, j, nullptr, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
+                                   werr));
+    GR_CUDA(launch_update_df_dev(L, Vf, ldf, pl, maxit, j, h->hcol + ldh, nullptr, U, nullptr, h->partial, AS.rho2,
+                                 AS.flag, werr));
+    GR_CUDA(launch_scale_df_dev(L, Vf, ldf, pl, j, U, AS.rho2, AS.flag));
+    GR_CUDA(launch_givens_dev(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, h->scal + 1,
+                              h->scal + 2));
+    GR_CUDA(launch_loop_control(L, h->idx, h->idx + 1, h->scal + 1, rtol, maxit, hc));
+    return PC_OK;
+  }
+  const bool lp_reorth = !arnoldi_strict(h);
   if (h->fp32) {
     float* Z = (float*)h->Z;
     GR_CUDA((precond32<float, float>(h, L, h->vf32, Z, U, j, false)));
@@ -1446,8 +1550,10 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   float* vf = h->fp32 ? h->vf32 : nullptr;
   GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol, h->V, U, U, AS.inv, h->partial, AS.q, nullptr, vf));
   GR_CUDA(launch_arnoldi_check(L, AS));
-  GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol + ldh, nullptr, AS.flag));
-  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol + ldh, h->V, U, U, nullptr, h->partial, AS.rho2, AS.flag));
+  GR_CUDA(launch_multidot_dev(L, h->V, U, maxit, j, h->V, U, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
+                              lp_reorth));
+  GR_CUDA(launch_update_dev(L, h->V, U, maxit, j, h->hcol + ldh, h->V, U, U, nullptr, h->partial, AS.rho2, AS.flag,
+                            nullptr, lp_reorth));
   GR_CUDA(launch_scale_dev(L, h->V, U, j, U, AS.rho2, AS.flag, vf));
   GR_CUDA(launch_givens_dev(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, h->scal + 1,
                             h->scal + 2));
@@ -1510,6 +1616,10 @@ static int capture_solve(pc_handle* h, const double* b, double* x, double rtol, 
 
 // read iterations and the true relative residual of a finished graph solve
 static int graph_results(pc_handle* h, cudaStream_t st, double rtol, int* iters, double* relres) {
+  if (arnoldi_df(h)) {
+    if (int rc = fetch_scalars(h, st, h->scal + 10, 1, 12)) return rc;
+    if (h->host[12] != 0.0) return fail(PC_ERR_TIMEOUT, "graph solve: a bounded device wait ran out");
+  }
   if (int rc = fetch_scalars(h, st, h->scal + 1, 3, 0, h->idx + 1)) return rc;
   const int kdone = (int)h->host[3];
   const double ref = h->host[1], r2 = h->host[2];
@@ -1701,6 +1811,7 @@ extern "C" const char* pc_status_string(int s) {
     case PC_ERR_NOT_CONVERGED: return "not converged";
     case PC_ERR_BREAKDOWN: return "breakdown (non-finite value)";
     case PC_ERR_UNSUPPORTED: return "unsupported";
+    case PC_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
   }
 }

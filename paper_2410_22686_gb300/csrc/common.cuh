@@ -342,11 +342,14 @@ struct ArnoldiScalars {
 constexpr int kMaxBlocksPerSM = 8;  // 256-thread blocks: partial-sum buffers hold SMs*8 rows
 // out = V^T w for nv vectors (stride ldv); optionally *ww = ||w||^2; skipped when gate && *gate == 0
 // (gated launches are booked under KC_REORTH with zero bytes; the caller adds them if they ran)
+// lp_reorth: gated (re-orthogonalisation) launches take FP32 products of 20-bit truncations;
+// false keeps FP64 products there too
 cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, const double* w, size_t len,
-                            double* partial, double* out, double* ww, const double* gate);
+                            double* partial, double* out, double* ww, const double* gate, bool lp_reorth = true);
 // v = (v - sum_i coef_i V_i) * (*scale or 1); *q = ||v - sum_i coef_i V_i||^2 (before scaling); gated
 cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
-                          const double* scale, double* partial, double* q, const double* gate, float* vf = nullptr);
+                          const double* scale, double* partial, double* q, const double* gate, float* vf = nullptr,
+                          bool lp_reorth = true);
 cudaError_t launch_norm2(Launch& L, const double* w, size_t len, double* partial, double* nrm2);
 // v *= 1/sqrt(*nrm2); gated
 cudaError_t launch_scale_by_inv_norm(Launch& L, double* v, size_t len, const double* nrm2, const double* gate,
@@ -368,10 +371,10 @@ cudaError_t launch_xupdate(Launch& L, const Tz* Z, size_t ldz, int k, const doub
 // can be recorded inside a conditional graph body).
 cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev,
                                 const double* wbase, size_t wstride, size_t len, double* partial, double* out,
-                                double* ww, const double* gate);
+                                double* ww, const double* gate, bool lp_reorth = true);
 cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
                               double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
-                              double* q, const double* gate, float* vf = nullptr);
+                              double* q, const double* gate, float* vf = nullptr, bool lp_reorth = true);
 cudaError_t launch_scale_dev(Launch& L, double* vbase, size_t vstride, const int* jdev, size_t len,
                              const double* nrm2, const double* gate, float* vf = nullptr);
 cudaError_t launch_arnoldi_prep_dev(Launch& L, const int* jdev, const double* d, ArnoldiScalars s);
@@ -392,6 +395,27 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
                                  int set_ref);
 
 // RHS assembly and gradient
+// double-float basis: vector i = FP32 planes hi at Vf + i*ldv, lo at + pl (ldv = 2 pl,
+// pl >= len rounded up to 64, len even).  The first pass streams the basis through
+// shared memory with bulk copies; a wait that runs out of its budget writes a nonzero
+// value into *err (device) and the kernel returns early.  gate != nullptr selects
+// the (gated) second pass on the hi planes.
+cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* w,
+                               const float* xh, size_t len, double* partial, double* out, double* ww,
+                               const double* gate, double* err);
+cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* coef,
+                             const double* w, float* out, size_t len, const double* scale, double* partial, double* q,
+                             const double* gate, double* err);
+cudaError_t launch_split_scale(Launch& L, const double* src, float* out, size_t pl, size_t len, const double* nrm2);
+cudaError_t launch_scale_df(Launch& L, float* v, size_t pl, size_t len, const double* nrm2, const double* gate);
+cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
+                                   const double* w, size_t len, double* partial, double* out, double* ww,
+                                   const double* gate, double* err);
+cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
+                                 const double* coef, const double* w, size_t len, const double* scale,
+                                 double* partial, double* q, const double* gate, double* err);
+cudaError_t launch_scale_df_dev(Launch& L, float* Vf, size_t ldv, size_t pl, const int* jdev, size_t len,
+                                const double* nrm2, const double* gate);
 cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
                              const double* g, const double* y0, double* b);
 

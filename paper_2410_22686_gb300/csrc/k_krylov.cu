@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace pcopt {
 
@@ -437,6 +438,468 @@ __global__ void loop_start_kernel(int* jdev, int* kdev, const double* est, doubl
   cudaGraphSetConditional(hc, (isfinite(e) && e > rtol) ? 1u : 0u);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float basis (flexible GMRES with the FP32 preconditioner).  Basis
+// vector i is two FP32 planes, hi at Vf + i*ldv and lo at Vf + i*ldv + pl
+// (ldv = 2 pl, pl >= len rounded up to a multiple of 64), v = hi + lo to about
+// 2^-48 relative; hi is the FP32 rounding of v and is what the FP32
+// preconditioner reads.  The Arnoldi products and sums run on the FP32 units as
+// error-free transformations (the product's rounding error by FMA, Knuth's
+// TwoSum for the running sums), so the passes over the basis are bound by HBM
+// instead of by GB300's FP64 unit.  Scalars (h_ij, norms) and the per-block
+// reductions stay FP64.
+//
+// The first pass (multi-dot and update) streams tiles of the basis into shared
+// memory with bulk asynchronous copies (several stages in flight per SM on
+// mbarriers), so the bytes in flight do not compete with the accumulators for
+// registers; the selective second pass reads the hi planes directly.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 512;             // elements per streamed tile (two per thread)
+constexpr int kGroup = 16;             // basis vectors per stage of the update
+constexpr int kBarBytes = 256;         // mbarriers (16 full, 16 empty) at the start of the dynamic shared memory
+constexpr size_t kStreamSmem = 220 * 1024;  // dynamic shared-memory budget of a streaming CTA
+
+__device__ __forceinline__ float neg_f(float x) { return -x; }
+
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  hi = f64_to_f32(x);
+  lo = f64_to_f32(x - f32_to_f64(hi));
+}
+
+// s + e += (ah + al)(bh + bl), the product's low-order term al*bl dropped
+__device__ __forceinline__ void df_dot_acc(float ah, float al, float bh, float bl, float& s, float& e) {
+  const float p = __fmul_rn(ah, bh);
+  float t = fmaf(ah, bh, -p);
+  t = fmaf(ah, bl, t);
+  t = fmaf(al, bh, t);
+  const float s2 = __fadd_rn(s, p);
+  const float bb = __fsub_rn(s2, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+  e = __fadd_rn(e, __fadd_rn(err, t));
+  s = s2;
+}
+
+// (ah, al) -= (ch + cl)(vh + vl)
+__device__ __forceinline__ void df_sub_prod(float ch, float cl, float vh, float vl, float& ah, float& al) {
+  const float p = __fmul_rn(ch, vh);
+  float t = fmaf(ch, vh, -p);
+  t = fmaf(ch, vl, t);
+  t = fmaf(cl, vh, t);
+  const float s = __fsub_rn(ah, p);
+  const float bb = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(neg_f(p), bb));
+  al = __fadd_rn(al, __fsub_rn(err, t));
+  ah = s;
+}
+
+// (hi, lo) with |lo| <= ulp(hi)/2 from an unnormalised pair
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+
+// (hi, lo) *= (sh + sl)
+__device__ __forceinline__ void df_scale(float& hi, float& lo, float sh, float sl) {
+  const float p = __fmul_rn(hi, sh);
+  float t = fmaf(hi, sh, -p);
+  t = fmaf(hi, sl, t);
+  t = fmaf(lo, sh, t);
+  hi = p;
+  lo = t;
+  df_renorm(hi, lo);
+}
+
+__device__ __forceinline__ size_t round4(size_t x) { return (x + 3) & ~(size_t)3; }
+
+// nv basis vectors in ceil(nv / 16) chunks of nearly equal size (no small tail chunk,
+// whose stages would be mostly overhead): chunk c covers [i0, i0 + cnt)
+__host__ __device__ __forceinline__ void balanced_chunk(int nv, int c, int* i0, int* cnt) {
+  const int nch = (nv + kChunk - 1) / kChunk;
+  const int base = nv / nch, rem = nv % nch;
+  *cnt = base + (c < rem ? 1 : 0);
+  *i0 = c * base + (c < rem ? c : rem);
+}
+
+// Producer/consumer stream of a CTA's items through S shared-memory stages.
+// The CTA has kThreads consumer threads (warps 0..7) and one producer warp (warp
+// 8).  Stage q has a "full" mbarrier (one arrival with the copies' byte count,
+// completed by the copy engine) and an "empty" one (one arrival per consumer
+// warp once it has read the stage).  The producer's lanes issue an item's copies
+// together: issue(k, stage, full, lane).  consume(k, stage) runs on every consumer
+// thread.  No CTA-wide barrier inside the stream.  Every wait is bounded; one that
+// runs out sets *err, ends that thread's loop, and the producer then drains the
+// copies it has in flight (bounded) before the CTA leaves.
+constexpr int kConsumerWarps = kThreads / 32;
+constexpr int kStreamThreads = kThreads + 32;
+
+template <typename Issue, typename Consume>
+__device__ __forceinline__ void stream_items(size_t nitems, int S, size_t stage_stride, Issue issue, Consume consume,
+                                             double* err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm);
+  uint64_t* empty = full + 16;
+  unsigned char* buf = dsm + kBarBytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kConsumerWarps);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (warp == kConsumerWarps) {  // producer
+    size_t k = 0;
+    bool ok = true;
+    for (; k < nitems; ++k) {
+      const int q = (int)(k % S);
+      if (k >= (size_t)S) {
+        // the consumers released this stage's previous item (use k / S - 1)
+        bool got = mbar_wait_bounded(&empty[q], (uint32_t)((k / S - 1) & 1), nullptr, 0.0);
+        got = __all_sync(0xffffffffu, got);
+        if (!got) {
+          ok = false;
+          break;
+        }
+      }
+      issue(k, buf + q * stage_stride, &full[q], lane);
+    }
+    if (!ok) {
+      if (lane == 0) *err = kErrWaitTimeout;
+      // items k - S + 1 .. k - 1 may still be in flight: wait for their copies
+      const size_t lo = k >= (size_t)S ? k - S + 1 : 0;
+      for (size_t m = lo; m < k; ++m) mbar_wait_bounded(&full[m % S], (uint32_t)((m / S) & 1), nullptr, 0.0);
+    }
+  } else {  // consumers
+    for (size_t k = 0; k < nitems; ++k) {
+      const int q = (int)(k % S);
+      if (!mbar_wait_bounded(&full[q], (uint32_t)((k / S) & 1), err, kErrWaitTimeout)) break;
+      consume(k, buf + q * stage_stride);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[q]);
+    }
+  }
+  __syncthreads();
+}
+
+// the producer lanes' share of an item: lane 0 announces the bytes, then copy c
+// (of ncopies) is issued by lane c % 32
+template <typename CopyAt>
+__device__ __forceinline__ void issue_copies(uint64_t* bar, uint32_t bytes, int ncopies, int lane, CopyAt copy_at) {
+  if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+  __syncwarp();
+  for (int c = lane; c < ncopies; c += 32) copy_at(c);
+}
+
+// First pass, multi-dot: partial[b*ld + i0 + c] = sum over CTA b of V_{i0+c} . w
+// (w FP64, split on use) and, WITH_NORM, partial[b*ld + ncol_norm] = w . w.
+template <int CNT, bool WITH_NORM>
+__device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf, size_t ldv, size_t pl, int i0,
+                                                   const double* __restrict__ w, size_t len,
+                                                   double* __restrict__ partial, int ncol_norm, int ld, int S,
+                                                   size_t stage_stride, double* err) {
+  float s[CNT], er[CNT];
+  double ww = 0.0;
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) s[c] = er[c] = 0.0f;
+  const size_t ntiles = (len + kTile - 1) / kTile;
+  const size_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto issue = [&](size_t k, unsigned char* st, uint64_t* bar, int lane) {
+    const size_t e0 = (blockIdx.x + k * gridDim.x) * (size_t)kTile;
+    const size_t n = len - e0 < (size_t)kTile ? len - e0 : (size_t)kTile;  // even: len is even
+    const uint32_t fb = (uint32_t)(round4(n) * 4), db = (uint32_t)(n * 8);
+    // copies 0 .. 2 CNT - 1: plane c % 2 of vector i0 + c / 2; copy 2 CNT: w
+    issue_copies(bar, 2u * CNT * fb + db, 2 * CNT + 1, lane, [&](int c) {
+      if (c < 2 * CNT)
+        bulk_copy_g2s(st + (size_t)c * kTile * 4, Vf + (size_t)(i0 + c / 2) * ldv + (c & 1) * pl + e0, fb, bar);
+      else
+        bulk_copy_g2s(st + (size_t)2 * CNT * kTile * 4, w + e0, db, bar);
+    });
+  };
+  auto consume = [&](size_t k, const unsigned char* st) {
+    const size_t e0 = (blockIdx.x + k * gridDim.x) * (size_t)kTile;
+    const float* sv = reinterpret_cast<const float*>(st);
+    const double* sw = reinterpret_cast<const double*>(st + (size_t)2 * CNT * kTile * 4);
+#pragma unroll
+    for (int q = 0; q < kTile / kThreads; ++q) {
+      const int el = threadIdx.x + q * kThreads;
+      if (e0 + el < len) {
+        const double we = sw[el];
+        float wh, wl;
+        split_f64(we, wh, wl);
+        if (WITH_NORM) ww = fma(we, we, ww);
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) df_dot_acc(sv[(2 * c) * kTile + el], sv[(2 * c + 1) * kTile + el], wh, wl, s[c], er[c]);
+      }
+    }
+  };
+  stream_items(mine, S, stage_stride, issue, consume, err);
+  __shared__ double red[kStreamThreads / 32][CNT + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    const double v = warp_sum(f32_to_f64(s[c]) + f32_to_f64(er[c]));
+    if (lane == 0) red[wid][c] = v;
+  }
+  if (WITH_NORM) {
+    const double v = warp_sum(ww);
+    if (lane == 0) red[wid][CNT] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < CNT + (WITH_NORM ? 1 : 0)) {
+    double t = 0.0;
+    for (int q = 0; q < kStreamThreads / 32; ++q) t += red[q][threadIdx.x];
+    const int col = threadIdx.x < CNT ? i0 + threadIdx.x : ncol_norm;
+    partial[(size_t)blockIdx.x * ld + col] = t;
+  }
+}
+
+template <int CNT, bool WITH_NORM>
+__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
+                                                                  int i0, const double* __restrict__ w, size_t len,
+                                                                  double* __restrict__ partial, int nv, int ld, int S,
+                                                                  size_t stage_stride, double* err) {
+  multidot_df_stream<CNT, WITH_NORM>(Vf, ldv, pl, i0, w, len, partial, nv, ld, S, stage_stride, err);
+}
+
+// device-resident index: nv = *jdev + 1 vectors; launch `chunk` of the balanced split
+// (exits when nv needs fewer chunks)
+template <bool WITH_NORM>
+__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_dyn_kernel(const float* __restrict__ Vf, size_t ldv,
+                                                                      size_t pl, int chunk,
+                                                                      const double* __restrict__ w,
+                                                                      const int* __restrict__ jdev, size_t len,
+                                                                      double* __restrict__ partial, int ld, int S,
+                                                                      size_t stage_stride, double* err) {
+  const int nv = *jdev + 1;
+  if (chunk >= (nv + kChunk - 1) / kChunk) return;
+  int i0, cnt;
+  balanced_chunk(nv, chunk, &i0, &cnt);
+  switch (cnt) {
+#define PCOPT_DYN(k) \
+  case k: multidot_df_stream<k, WITH_NORM>(Vf, ldv, pl, i0, w, len, partial, ld - 1, ld, S, stage_stride, err); break;
+    PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
+    PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
+#undef PCOPT_DYN
+    default: break;
+  }
+}
+
+// First pass, update: out = (w - sum_{i < nv} coef_i V_i) * scale (double-float
+// planes of out), partial[b] = CTA sum of |w - sum|^2 (FP64, before scaling).  The
+// stream walks (tile, group of 16 vectors) items; w is copied with a tile's first group.
+// With jdev: nv = *jdev + 1 and out = Vf + nv * ldv.
+__global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
+                                                                int nv, const double* __restrict__ coef,
+                                                                const double* __restrict__ w, float* out, size_t len,
+                                                                const double* __restrict__ scale,
+                                                                double* __restrict__ partial,
+                                                                const int* __restrict__ jdev, int S,
+                                                                size_t stage_stride, double* err) {
+  if (jdev) {
+    nv = *jdev + 1;
+    out = const_cast<float*>(Vf) + (size_t)nv * ldv;
+  }
+  __shared__ float2 cf[1024];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    float hi, lo;
+    split_f64(coef[i], hi, lo);
+    cf[i] = make_float2(hi, lo);
+  }
+  float sh = 1.0f, sl = 0.0f;
+  if (scale) split_f64(scale[0], sh, sl);
+  const int G = (nv + kGroup - 1) / kGroup;  // groups of 16 (the last one holds the rest)
+  const size_t ntiles = (len + kTile - 1) / kTile;
+  const size_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  float ah[kTile / kThreads], al[kTile / kThreads];
+  double acc = 0.0;
+  auto issue = [&](size_t k, unsigned char* st, uint64_t* bar, int lane) {
+    const size_t e0 = (blockIdx.x + (k / G) * gridDim.x) * (size_t)kTile;
+    const int g = (int)(k % G);
+    const int i0 = g * kGroup, cnt = nv - i0 < kGroup ? nv - i0 : kGroup;
+    const size_t n = len - e0 < (size_t)kTile ? len - e0 : (size_t)kTile;
+    const uint32_t fb = (uint32_t)(round4(n) * 4), db = (uint32_t)(n * 8);
+    // copies 0 .. 2 cnt - 1: plane c % 2 of vector i0 + c / 2; copy 2 cnt (first group only): w
+    issue_copies(bar, 2u * cnt * fb + (g == 0 ? db : 0u), 2 * cnt + (g == 0 ? 1 : 0), lane, [&](int c) {
+      if (c < 2 * cnt)
+        bulk_copy_g2s(st + (size_t)c * kTile * 4, Vf + (size_t)(i0 + c / 2) * ldv + (c & 1) * pl + e0, fb, bar);
+      else
+        bulk_copy_g2s(st + (size_t)2 * kGroup * kTile * 4, w + e0, db, bar);
+    });
+  };
+  auto consume = [&](size_t k, const unsigned char* st) {
+    const size_t e0 = (blockIdx.x + (k / G) * gridDim.x) * (size_t)kTile;
+    const int g = (int)(k % G);
+    const int i0 = g * kGroup, cnt = nv - i0 < kGroup ? nv - i0 : kGroup;
+    const float* sv = reinterpret_cast<const float*>(st);
+    const double* sw = reinterpret_cast<const double*>(st + (size_t)2 * kGroup * kTile * 4);
+#pragma unroll
+    for (int q = 0; q < kTile / kThreads; ++q) {
+      const int el = threadIdx.x + q * kThreads;
+      if (e0 + el >= len) continue;
+      if (g == 0) split_f64(sw[el], ah[q], al[q]);
+      for (int c = 0; c < cnt; ++c) {
+        const float2 cc = cf[i0 + c];
+        df_sub_prod(cc.x, cc.y, sv[(2 * c) * kTile + el], sv[(2 * c + 1) * kTile + el], ah[q], al[q]);
+      }
+      if (g == G - 1) {
+        float hi = ah[q], lo = al[q];
+        df_renorm(hi, lo);
+        const double x = f32_to_f64(hi) + f32_to_f64(lo);
+        acc = fma(x, x, acc);
+        if (scale) df_scale(hi, lo, sh, sl);
+        out[e0 + el] = hi;
+        out[pl + e0 + el] = lo;
+      }
+    }
+  };
+  __syncthreads();  // coefficients staged
+  stream_items(mine * (size_t)G, S, stage_stride, issue, consume, err);
+  __shared__ double red[kStreamThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kStreamThreads / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Second pass (re-orthogonalisation, gated): e_c = hi_{i0+c} . x with x the hi plane of
+// the new vector (FP32 products of hi planes: the coefficients removed here are ~1e-6).
+template <int CNT>
+__device__ __forceinline__ void multidot_lp_body(const float* __restrict__ Vf, size_t ldv, int i0,
+                                                 const float* __restrict__ xh, size_t len,
+                                                 double* __restrict__ partial, int ld) {
+  float s[CNT];
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) s[c] = 0.0f;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const float* Vb = Vf + (size_t)i0 * ldv;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    const float x = xh[e];
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) s[c] = fmaf(__ldg(Vb + (size_t)c * ldv + e), x, s[c]);
+  }
+  __shared__ double red[kThreads / 32][CNT];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < CNT; ++c) {
+    const double v = warp_sum(f32_to_f64(s[c]));
+    if (lane == 0) red[wid][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < CNT) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q][threadIdx.x];
+    partial[(size_t)blockIdx.x * ld + i0 + threadIdx.x] = t;
+  }
+}
+
+template <int CNT>
+__global__ void __launch_bounds__(kThreads) multidot_lp_kernel(const float* __restrict__ Vf, size_t ldv, int i0,
+                                                               const float* __restrict__ xh, size_t len,
+                                                               double* __restrict__ partial, int ld,
+                                                               const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
+  multidot_lp_body<CNT>(Vf, ldv, i0, xh, len, partial, ld);
+}
+
+__global__ void __launch_bounds__(kThreads) multidot_lp_dyn_kernel(const float* __restrict__ Vf, size_t ldv, int i0,
+                                                                   const int* __restrict__ jdev, size_t len,
+                                                                   double* __restrict__ partial, int ld,
+                                                                   const double* __restrict__ gate) {
+  if (gated_off(gate)) return;
+  const int nv = *jdev + 1;
+  if (i0 >= nv) return;
+  const float* xh = Vf + (size_t)nv * ldv;
+  const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
+  switch (cnt) {
+#define PCOPT_DYN(k) \
+  case k: multidot_lp_body<k>(Vf, ldv, i0, xh, len, partial, ld); break;
+    PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
+    PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
+#undef PCOPT_DYN
+    default: break;
+  }
+}
+
+// Second pass update (gated): v -= sum_i e_i hi_i (FP32 sum of hi planes) on the
+// double-float vector `out` in place; partial[b] = block sum of |v|^2.
+// With jdev: nv = *jdev + 1 and out = Vf + nv * ldv.
+__global__ void __launch_bounds__(kThreads) update_lp_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
+                                                             int nv, const double* __restrict__ coef, float* out,
+                                                             size_t len, double* __restrict__ partial,
+                                                             const double* __restrict__ gate,
+                                                             const int* __restrict__ jdev) {
+  if (gated_off(gate)) return;
+  if (jdev) {
+    nv = *jdev + 1;
+    out = const_cast<float*>(Vf) + (size_t)nv * ldv;
+  }
+  __shared__ float cf[1024];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (float)coef[i];
+  __syncthreads();
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    float ah = out[e], al = out[pl + e];
+    float sf = 0.0f;
+    for (int i = 0; i < nv; ++i) sf = fmaf(cf[i], __ldg(Vf + (size_t)i * ldv + e), sf);
+    const float s2 = __fsub_rn(ah, sf);
+    const float bb = __fsub_rn(s2, ah);
+    al = __fadd_rn(al, __fadd_rn(__fsub_rn(ah, __fsub_rn(s2, bb)), __fsub_rn(neg_f(sf), bb)));
+    ah = s2;
+    df_renorm(ah, al);
+    const double x = f32_to_f64(ah) + f32_to_f64(al);
+    acc = fma(x, x, acc);
+    out[e] = ah;
+    out[pl + e] = al;
+  }
+  __shared__ double red[kThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) t += red[q];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// planes of `out` = src / sqrt(nrm2[0]) (src FP64; a zero norm copies src unscaled)
+__global__ void split_scale_kernel(const double* __restrict__ src, float* __restrict__ out, size_t pl, size_t len,
+                                   const double* __restrict__ nrm2) {
+  const bool nz = nrm2[0] > 0.0;
+  const double q = nz ? 1.0 / sqrt(nrm2[0]) : 1.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    float hi, lo;
+    split_f64(src[e] * q, hi, lo);
+    out[e] = hi;
+    out[pl + e] = lo;
+  }
+}
+
+// double-float vector *= 1/sqrt(nrm2[0]) (gated; with jdev the vector is v + (*jdev+1) ldv)
+__global__ void scale_df_kernel(float* v, size_t ldv, size_t pl, size_t len, const double* __restrict__ nrm2,
+                                const double* __restrict__ gate, const int* __restrict__ jdev) {
+  if (gated_off(gate)) return;
+  if (jdev) v += (size_t)(*jdev + 1) * ldv;
+  if (!(nrm2[0] > 0.0)) return;
+  float sh, sl;
+  split_f64(1.0 / sqrt(nrm2[0]), sh, sl);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
+    float hi = v[e], lo = v[pl + e];
+    df_scale(hi, lo, sh, sl);
+    v[e] = hi;
+    v[pl + e] = lo;
+  }
+}
+
 // blocks that fit the device at once for kernel `fn` (one wave), capped by the work size
 template <typename K>
 unsigned wave_blocks(K fn, size_t smem, size_t len) {
@@ -464,9 +927,10 @@ ChunkGrids one_grid(unsigned nb) {
 
 template <int CNT, bool N>
 cudaError_t multidot_chunk(Launch& L, const double* V, size_t ldv, int i0, const double* w, size_t len,
-                           double* partial, int nv, int ld, const double* gate, unsigned* blocks_out) {
+                           double* partial, int nv, int ld, const double* gate, unsigned* blocks_out, bool lp) {
   // gated launches are the re-orthogonalisation pass: FP32 products (see the file header)
-  auto kern = gate ? multidot_kernel<CNT, N, true> : multidot_kernel<CNT, N, false>;
+  // unless lp is false (FP64 products throughout)
+  auto kern = (gate && lp) ? multidot_kernel<CNT, N, true> : multidot_kernel<CNT, N, false>;
   const unsigned nb = wave_blocks(kern, 0, len);
   *blocks_out = nb;
   const int kc = gate ? KC_REORTH : KC_DOT;
@@ -477,10 +941,84 @@ cudaError_t multidot_chunk(Launch& L, const double* V, size_t ldv, int i0, const
 
 template <bool N>
 cudaError_t multidot_dispatch(int cnt, Launch& L, const double* V, size_t ldv, int i0, const double* w, size_t len,
-                              double* partial, int nv, int ld, const double* gate, unsigned* nb) {
+                              double* partial, int nv, int ld, const double* gate, unsigned* nb, bool lp) {
   switch (cnt) {
 #define PCOPT_CASE(k) \
-  case k: return multidot_chunk<k, N>(L, V, ldv, i0, w, len, partial, nv, ld, gate, nb);
+  case k: return multidot_chunk<k, N>(L, V, ldv, i0, w, len, partial, nv, ld, gate, nb, lp);
+    PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
+    PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
+    PCOPT_CASE(15) PCOPT_CASE(16)
+#undef PCOPT_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t round128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+// stages of `stride` bytes that fit the streaming CTA's shared-memory budget
+int stream_stages_for(size_t stride) {
+  const size_t s = (kStreamSmem - kBarBytes) / stride;
+  return (int)(s < 2 ? 2 : (s > 12 ? 12 : s));
+}
+
+// one streaming CTA per SM (the stages fill its shared memory), at most one per tile
+unsigned stream_grid(size_t len) {
+  const size_t ntiles = (len + kTile - 1) / kTile;
+  const size_t sms = (size_t)num_sms();
+  return (unsigned)(ntiles < sms ? (ntiles ? ntiles : 1) : sms);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kern, size_t smem) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int CNT, bool N>
+cudaError_t multidot_df_chunk(Launch& L, const float* Vf, size_t ldv, size_t pl, int i0, const double* w, size_t len,
+                              double* partial, int nv, int ld, double* err, unsigned* blocks_out) {
+  const size_t stride = round128((size_t)2 * CNT * kTile * 4 + (size_t)kTile * 8);
+  const int S = stream_stages_for(stride);
+  const size_t smem = kBarBytes + S * stride;
+  auto kern = multidot_df_kernel<CNT, N>;
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = stream_grid(len);
+  *blocks_out = nb;
+  L.begin(KC_DOT);
+  kern<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, i0, w, len, partial, nv, ld, S, stride, err);
+  return L.end(KC_DOT, 8.0 * len * (CNT + 1), 2.0 * len * (CNT + (N ? 1 : 0)));
+}
+
+template <bool N>
+cudaError_t multidot_df_dispatch(int cnt, Launch& L, const float* Vf, size_t ldv, size_t pl, int i0, const double* w,
+                                 size_t len, double* partial, int nv, int ld, double* err, unsigned* nb) {
+  switch (cnt) {
+#define PCOPT_CASE(k) \
+  case k: return multidot_df_chunk<k, N>(L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, nb);
+    PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
+    PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
+    PCOPT_CASE(15) PCOPT_CASE(16)
+#undef PCOPT_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int CNT>
+cudaError_t multidot_lp_chunk(Launch& L, const float* Vf, size_t ldv, int i0, const float* xh, size_t len,
+                              double* partial, int ld, const double* gate, unsigned* blocks_out) {
+  auto kern = multidot_lp_kernel<CNT>;
+  const unsigned nb = wave_blocks(kern, 0, len);
+  *blocks_out = nb;
+  L.begin(KC_REORTH);
+  kern<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, i0, xh, len, partial, ld, gate);
+  return L.end(KC_REORTH, 0.0, 0.0);
+}
+
+cudaError_t multidot_lp_dispatch(int cnt, Launch& L, const float* Vf, size_t ldv, int i0, const float* xh, size_t len,
+                                 double* partial, int ld, const double* gate, unsigned* nb) {
+  switch (cnt) {
+#define PCOPT_CASE(k) \
+  case k: return multidot_lp_chunk<k>(L, Vf, ldv, i0, xh, len, partial, ld, gate, nb);
     PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
     PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
     PCOPT_CASE(15) PCOPT_CASE(16)
@@ -492,7 +1030,7 @@ cudaError_t multidot_dispatch(int cnt, Launch& L, const double* V, size_t ldv, i
 }  // namespace
 
 cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, const double* w, size_t len,
-                            double* partial, double* out, double* ww, const double* gate) {
+                            double* partial, double* out, double* ww, const double* gate, bool lp_reorth) {
   if (nv < 1 || nv > kChunk * kMaxChunks) return cudaErrorInvalidValue;
   const int ld = nv + 1;
   ChunkGrids cg = one_grid(1);
@@ -500,8 +1038,9 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
   for (int i0 = 0, c = 0; i0 < nv; i0 += kChunk, ++c) {
     const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
     unsigned nb = 0;
-    cudaError_t e = (i0 == 0 && ww) ? multidot_dispatch<true>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb)
-                                    : multidot_dispatch<false>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb);
+    cudaError_t e =
+        (i0 == 0 && ww) ? multidot_dispatch<true>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb, lp_reorth)
+                        : multidot_dispatch<false>(cnt, L, V, ldv, i0, w, len, partial, nv, ld, gate, &nb, lp_reorth);
     if (e != cudaSuccess) return e;
     cg.nb[c] = nb;
     nb_sum += nb * (double)cnt;
@@ -514,9 +1053,10 @@ cudaError_t launch_multidot(Launch& L, const double* V, size_t ldv, int nv, cons
 }
 
 cudaError_t launch_update(Launch& L, const double* V, size_t ldv, int nv, const double* coef, double* v, size_t len,
-                          const double* scale, double* partial, double* q, const double* gate, float* vf) {
+                          const double* scale, double* partial, double* q, const double* gate, float* vf,
+                          bool lp_reorth) {
   const size_t smem = sizeof(double) * (nv > 0 ? nv : 1);
-  auto kern = gate ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
+  auto kern = (gate && lp_reorth) ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
   const unsigned nb = wave_blocks(kern, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);
@@ -603,15 +1143,183 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
 }
 
 // ---------------------------------------------------------------------------
+// double-float basis: vector i = planes hi at Vf + i*ldv, lo at + pl (ldv = 2 pl)
+cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* w,
+                               const float* xh, size_t len, double* partial, double* out, double* ww,
+                               const double* gate, double* err) {
+  if (nv < 1 || nv > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+  if (len & 1) return cudaErrorInvalidValue;  // the streamed tiles need an even length
+  const bool lp = gate != nullptr;  // gated launches are the re-orthogonalisation pass
+  const int ld = nv + 1;
+  ChunkGrids cg = one_grid(1);
+  double nb_sum = 0;
+  if (lp) {  // fixed chunks of 16 (their grids differ with the chunk's register use)
+    for (int i0 = 0, c = 0; i0 < nv; i0 += kChunk, ++c) {
+      const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
+      unsigned nb = 0;
+      cudaError_t e = multidot_lp_dispatch(cnt, L, Vf, ldv, i0, xh, len, partial, ld, gate, &nb);
+      if (e != cudaSuccess) return e;
+      cg.nb[c] = nb;
+      nb_sum += nb * (double)cnt;
+    }
+  } else {  // balanced chunks, every one on the same streaming grid
+    const int nch = (nv + kChunk - 1) / kChunk;
+    unsigned nb = 0;
+    for (int c = 0; c < nch; ++c) {
+      int i0, cnt;
+      balanced_chunk(nv, c, &i0, &cnt);
+      cudaError_t e = (i0 == 0 && ww)
+                          ? multidot_df_dispatch<true>(cnt, L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, &nb)
+                          : multidot_df_dispatch<false>(cnt, L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, &nb);
+      if (e != cudaSuccess) return e;
+      nb_sum += nb * (double)cnt;
+    }
+    cg = one_grid(nb);
+  }
+  const int ncols = nv + (ww && !lp ? 1 : 0);
+  const int kc = lp ? KC_REORTH : KC_REDUCE;
+  L.begin(kc);
+  reduce_partials_kernel<<<ncols, kThreads, 0, L.stream>>>(partial, cg, ld, out, lp ? nullptr : ww, nv, gate,
+                                                          nullptr);
+  return lp ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * nb_sum, nb_sum);
+}
+
+cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* coef,
+                             const double* w, float* out, size_t len, const double* scale, double* partial, double* q,
+                             const double* gate, double* err) {
+  if (nv < 1 || nv > 1024) return cudaErrorInvalidValue;
+  if (len & 1) return cudaErrorInvalidValue;
+  const bool lp = gate != nullptr;
+  unsigned nb;
+  cudaError_t e;
+  if (lp) {
+    nb = wave_blocks(update_lp_kernel, 0, len);
+    L.begin(KC_REORTH);
+    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, pl, nv, coef, out, len, partial, gate, nullptr);
+    e = L.end(KC_REORTH, 0.0, 0.0);
+  } else {
+    const size_t stride = round128((size_t)2 * kGroup * kTile * 4 + (size_t)kTile * 8);
+    const int S = stream_stages_for(stride);
+    const size_t smem = kBarBytes + S * stride;
+    if ((e = allow_smem(update_df_kernel, smem)) != cudaSuccess) return e;
+    nb = stream_grid(len);
+    L.begin(KC_UPDATE);
+    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, nv, coef, w, out, len, scale, partial, nullptr,
+                                                            S, stride, err);
+    e = L.end(KC_UPDATE, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
+  }
+  if (e != cudaSuccess) return e;
+  const int kr = lp ? KC_REORTH : KC_REDUCE;
+  L.begin(kr);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate, nullptr);
+  return lp ? L.end(kr, 0.0, 0.0) : L.end(kr, 8.0 * nb, 1.0 * nb);
+}
+
+cudaError_t launch_split_scale(Launch& L, const double* src, float* out, size_t pl, size_t len, const double* nrm2) {
+  L.begin(KC_SCALE);
+  split_scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(src, out, pl, len, nrm2);
+  return L.end(KC_SCALE, 16.0 * len, 2.0 * len);
+}
+
+cudaError_t launch_scale_df(Launch& L, float* v, size_t pl, size_t len, const double* nrm2, const double* gate) {
+  const int kc = gate ? KC_REORTH : KC_SCALE;
+  L.begin(kc);
+  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, 2 * pl, pl, len, nrm2, gate, nullptr);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len, 1.0 * len);
+}
+
+cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
+                                   const double* w, size_t len, double* partial, double* out, double* ww,
+                                   const double* gate, double* err) {
+  if (nv_max < 1 || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+  if (len & 1) return cudaErrorInvalidValue;
+  const bool lp = gate != nullptr;
+  const int ld = nv_max + 1;
+  const int kc = lp ? KC_REORTH : KC_DOT;
+  ChunkGrids cg;
+  if (lp) {
+    const unsigned nb = wave_blocks(multidot_lp_dyn_kernel, 0, len);
+    cg = one_grid(nb);
+    for (int i0 = 0; i0 < nv_max; i0 += kChunk) {
+      L.begin(kc);
+      multidot_lp_dyn_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, i0, jdev, len, partial, ld, gate);
+      cudaError_t e = L.end(kc, 0.0, 0.0);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    const size_t stride = round128((size_t)2 * kChunk * kTile * 4 + (size_t)kTile * 8);
+    const int S = stream_stages_for(stride);
+    const size_t smem = kBarBytes + S * stride;
+    cudaError_t e = allow_smem(multidot_df_dyn_kernel<true>, smem);
+    if (e == cudaSuccess) e = allow_smem(multidot_df_dyn_kernel<false>, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = stream_grid(len);
+    cg = one_grid(nb);
+    for (int c = 0; c < (nv_max + kChunk - 1) / kChunk; ++c) {
+      L.begin(kc);
+      if (c == 0 && ww)
+        multidot_df_dyn_kernel<true><<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, c, w, jdev, len, partial,
+                                                                            ld, S, stride, err);
+      else
+        multidot_df_dyn_kernel<false><<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, c, w, jdev, len, partial,
+                                                                             ld, S, stride, err);
+      e = L.end(kc, 0.0, 0.0);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  L.begin(kc);
+  reduce_partials_kernel<<<nv_max + (ww && !lp ? 1 : 0), kThreads, 0, L.stream>>>(partial, cg, ld, out,
+                                                                                 lp ? nullptr : ww, nv_max, gate,
+                                                                                 jdev);
+  return L.end(kc, 0.0, 0.0);
+}
+
+cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
+                                 const double* coef, const double* w, size_t len, const double* scale,
+                                 double* partial, double* q, const double* gate, double* err) {
+  if (nv_max < 1 || nv_max > 1024) return cudaErrorInvalidValue;
+  if (len & 1) return cudaErrorInvalidValue;
+  const bool lp = gate != nullptr;
+  const int kc = lp ? KC_REORTH : KC_UPDATE;
+  unsigned nb;
+  cudaError_t e;
+  L.begin(kc);
+  if (lp) {
+    nb = wave_blocks(update_lp_kernel, 0, len);
+    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, pl, nv_max, coef, nullptr, len, partial, gate, jdev);
+  } else {
+    const size_t stride = round128((size_t)2 * kGroup * kTile * 4 + (size_t)kTile * 8);
+    const int S = stream_stages_for(stride);
+    const size_t smem = kBarBytes + S * stride;
+    if ((e = allow_smem(update_df_kernel, smem)) != cudaSuccess) return e;
+    nb = stream_grid(len);
+    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, nv_max, coef, w, nullptr, len, scale,
+                                                            partial, jdev, S, stride, err);
+  }
+  e = L.end(kc, 0.0, 0.0);
+  if (e != cudaSuccess) return e;
+  L.begin(kc);
+  reduce_partials_kernel<<<1, kThreads, 0, L.stream>>>(partial, one_grid(nb), 1, q, q, 1, gate, nullptr);
+  return L.end(kc, 0.0, 0.0);
+}
+
+cudaError_t launch_scale_df_dev(Launch& L, float* Vf, size_t ldv, size_t pl, const int* jdev, size_t len,
+                                const double* nrm2, const double* gate) {
+  L.begin(KC_REORTH);
+  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(Vf, ldv, pl, len, nrm2, gate, jdev);
+  return L.end(KC_REORTH, 0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------
 // device-index launchers: every launch below is independent of the iteration
 // index, which the kernels read from `jdev`, so one captured iteration serves all
 cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev,
                                 const double* wbase, size_t wstride, size_t len, double* partial, double* out,
-                                double* ww, const double* gate) {
+                                double* ww, const double* gate, bool lp_reorth) {
   if (nv_max < 1 || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
   const int ld = nv_max + 1;
   // gated launches are the re-orthogonalisation pass: FP32 products (see the file header)
-  auto plain = gate ? multidot_dyn_kernel<false, true> : multidot_dyn_kernel<false, false>;
+  auto plain = (gate && lp_reorth) ? multidot_dyn_kernel<false, true> : multidot_dyn_kernel<false, false>;
   const unsigned nb_norm = wave_blocks(multidot_dyn_kernel<true>, 0, len);
   const unsigned nb_plain = wave_blocks(plain, 0, len);
   ChunkGrids cg = one_grid(nb_plain);
@@ -636,9 +1344,9 @@ cudaError_t launch_multidot_dev(Launch& L, const double* V, size_t ldv, int nv_m
 
 cudaError_t launch_update_dev(Launch& L, const double* V, size_t ldv, int nv_max, const int* jdev, const double* coef,
                               double* vbase, size_t vstride, size_t len, const double* scale, double* partial,
-                              double* q, const double* gate, float* vf) {
+                              double* q, const double* gate, float* vf, bool lp_reorth) {
   const size_t smem = sizeof(double) * nv_max;
-  auto kern = gate ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
+  auto kern = (gate && lp_reorth) ? update_kernel<true> : update_kernel<false>;  // gated: re-orthogonalisation
   const unsigned nb = wave_blocks(kern, smem, len);
   const int kc = gate ? KC_REORTH : KC_UPDATE;
   L.begin(kc);

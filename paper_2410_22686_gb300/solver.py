@@ -20,6 +20,8 @@ _MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
 _SPACE = {"fd": capi.PC_SPACE_FD, "fe": capi.PC_SPACE_FE}
 _SMOOTHER = {"red-black": capi.PC_SMOOTHER_RED_BLACK, "lexicographic": capi.PC_SMOOTHER_LEXICOGRAPHIC}
 _PRECOND = {"eps-circulant": capi.PC_PRECOND_EPS_CIRCULANT, "ideal": capi.PC_PRECOND_IDEAL_RBD}
+_ARNOLDI = {"auto": capi.PC_ARNOLDI_AUTO, "fp64": capi.PC_ARNOLDI_FP64, "fp64-strict": capi.PC_ARNOLDI_FP64_STRICT,
+            "double-float": capi.PC_ARNOLDI_DOUBLE_FLOAT}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -122,6 +124,15 @@ class Solver:
         if log_a.numel() != self.ms:
             raise ValueError(f"log_a must hold {self.ms} values")
         capi.check(self.lib.pc_set_log_coefficient(self.h, _ptr(log_a), _stream()))
+
+    def set_arnoldi(self, mode: str):
+        """Arnoldi precision of later solves: "auto" (FP64 handles FP64, mixed handles
+        a double-float basis), "fp64", "fp64-strict" (FP64 products everywhere) or
+        "double-float" (pc_set_arnoldi)."""
+        if mode not in _ARNOLDI:
+            raise ValueError(f"mode must be one of {sorted(_ARNOLDI)}, got {mode!r}")
+        capi.check(self.lib.pc_set_arnoldi(self.h, _ARNOLDI[mode]))
+        self.arnoldi = mode
 
     def set_preconditioner(self, kind: str):
         """"eps-circulant" (P_eps, the default) or "ideal" (P of Eq. matrix_P by block

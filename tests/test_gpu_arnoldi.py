@@ -1,0 +1,113 @@
+"""Arnoldi precision of flexible GMRES with the FP32 preconditioner (pc_set_arnoldi):
+the double-float basis (the mixed handles' default), the FP64 basis with FP32
+re-orthogonalisation products, and the strict FP64 scheme give the FP64 oracle's
+solution within the mixed path's 1e-7 and the same iteration counts; the graph-
+launched solve agrees with the host-driven one in every mode."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import krylov as okr, precond as opc, system as osy
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["double-float", "fp64", "fp64-strict"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_22686_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _oracle(prob):
+    tau, alpha = prob.tau, osy.alpha_weight(prob.T, prob.n, prob.gamma)
+    b = osy.build_rhs(prob.f, prob.g, prob.y0, tau, prob.gamma)
+    mg = opc.MGSpatialSolver(prob.a_nodes, tau)
+    A = lambda v: osy.apply_A(v, prob.a_nodes, tau, alpha)
+    Pi = lambda v: opc.apply_Peps_inv(v, prob.n, alpha, prob.eps, mg)
+    return b, A, okr.gmres(A, Pi, b, rtol=1e-13, maxit=200, mode="right")
+
+
+@pytest.mark.parametrize("case", [("2d", 1e-4, 63, 64), ("2d", 1e-8, 31, 32), ("3d", 1e-4, 15, 16)])
+def test_every_arnoldi_mode_matches_the_fp64_oracle_with_equal_counts(case):
+    from paper_2410_22686_gb300 import Solver
+    kind, gamma, m1, n = case
+    prob = (S.variable_2d_problem(gamma=gamma, m1=m1, n=n) if kind == "2d"
+            else S.gaussian_field_3d_problem(m1=m1, n=n))
+    b, A, ref = _oracle(prob)
+    counts = {}
+    for mode in MODES:
+        sol = Solver(prob.d, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg",
+                     precision="fp32", max_iter=80)
+        sol.set_arnoldi(mode)
+        x, _, rel = sol.solve(_dev(b), rtol=1e-11)
+        xg = x.cpu().numpy()
+        assert rel <= 1e-11
+        err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-7, (mode, err)
+        # the reported residual is the true one
+        r = b - A(xg)
+        assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rel) <= 1e-12
+        _, counts[mode], rel8 = sol.solve(_dev(b), rtol=1e-8)
+        assert rel8 <= 1e-8
+        sol.close()
+    assert len(set(counts.values())) == 1, counts
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_graph_solve_agrees_with_host_solve_in_every_mode(mode):
+    from paper_2410_22686_gb300 import Solver
+    prob = S.variable_2d_problem(gamma=1e-4, m1=63, n=64)
+    sol = Solver(2, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg", precision="fp32",
+                 max_iter=60)
+    sol.set_arnoldi(mode)
+    b = sol.build_rhs(_dev(prob.f), _dev(prob.g), _dev(prob.y0))
+    xh, ih, rh = sol.solve(b, rtol=1e-10)
+    xg, ig, rg = sol.solve_graph(b, rtol=1e-10)
+    assert ih == ig
+    assert rg <= 1e-10 and rh <= 1e-10
+    assert (xg - xh).norm().item() <= 1e-9 * xh.norm().item()
+    # repeated graph solves are bitwise reproducible
+    xg2, _, _ = sol.solve_graph(b, rtol=1e-10)
+    assert torch.equal(xg, xg2)
+    sol.close()
+
+
+def test_long_solve_with_second_pass_in_double_float():
+    # 63^2 x 64, gamma 1e-4 to 1e-11: long enough that the selective second
+    # Gram-Schmidt pass runs on the double-float basis; the solution stays within the
+    # mixed tolerance
+    from paper_2410_22686_gb300 import Solver
+    prob = S.variable_2d_problem(gamma=1e-4, m1=63, n=64)
+    b, A, ref = _oracle(prob)
+    sol = Solver(2, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg", precision="fp32",
+                 max_iter=90)
+    sol.profile(True)
+    sol.stats_reset()
+    x, it, rel = sol.solve(_dev(b), rtol=1e-11)
+    st = sol.stats()
+    sol.profile(False)
+    assert rel <= 1e-11
+    assert st.get("arnoldi_reorth", {"launches": 0})["launches"] >= 1
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    sol.close()
+
+
+def test_arnoldi_mode_arguments():
+    from paper_2410_22686_gb300 import Solver, capi
+    s64 = Solver(2, 15, 8, 1.0, 1e-3, 0.3, None, spatial="fst", precision="fp64", max_iter=10)
+    with pytest.raises(capi.PCError) as e:
+        s64.set_arnoldi("double-float")
+    assert e.value.status == capi.PC_ERR_UNSUPPORTED
+    assert s64.lib.pc_set_arnoldi(s64.h, 9) == capi.PC_ERR_ARG
+    with pytest.raises(ValueError):
+        s64.set_arnoldi("fp16")
+    s64.set_arnoldi("fp64-strict")
+    s64.close()
