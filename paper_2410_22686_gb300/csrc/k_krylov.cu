@@ -617,21 +617,22 @@ __device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf,
         bulk_copy_g2s(st + (size_t)2 * CNT * kTile * 4, w + e0, db, bar);
     });
   };
+  // thread t takes elements 2t and 2t + 1 of a tile (8-byte and 16-byte shared loads;
+  // both lie inside or both beyond len, which is even)
   auto consume = [&](size_t k, const unsigned char* st) {
     const size_t e0 = (blockIdx.x + k * gridDim.x) * (size_t)kTile;
-    const float* sv = reinterpret_cast<const float*>(st);
-    const double* sw = reinterpret_cast<const double*>(st + (size_t)2 * CNT * kTile * 4);
+    if (e0 + 2 * threadIdx.x >= len) return;
+    const float2* sv = reinterpret_cast<const float2*>(st);
+    const double2 w2 = reinterpret_cast<const double2*>(st + (size_t)2 * CNT * kTile * 4)[threadIdx.x];
+    float wh0, wl0, wh1, wl1;
+    split_f64(w2.x, wh0, wl0);
+    split_f64(w2.y, wh1, wl1);
+    if (WITH_NORM) ww = fma(w2.y, w2.y, fma(w2.x, w2.x, ww));
 #pragma unroll
-    for (int q = 0; q < kTile / kThreads; ++q) {
-      const int el = threadIdx.x + q * kThreads;
-      if (e0 + el < len) {
-        const double we = sw[el];
-        float wh, wl;
-        split_f64(we, wh, wl);
-        if (WITH_NORM) ww = fma(we, we, ww);
-#pragma unroll
-        for (int c = 0; c < CNT; ++c) df_dot_acc(sv[(2 * c) * kTile + el], sv[(2 * c + 1) * kTile + el], wh, wl, s[c], er[c]);
-      }
+    for (int c = 0; c < CNT; ++c) {
+      const float2 h = sv[(2 * c) * (kTile / 2) + threadIdx.x], l = sv[(2 * c + 1) * (kTile / 2) + threadIdx.x];
+      df_dot_acc(h.x, l.x, wh0, wl0, s[c], er[c]);
+      df_dot_acc(h.y, l.y, wh1, wl1, s[c], er[c]);
     }
   };
   stream_items(mine, S, stage_stride, issue, consume, err);
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const floa
   const int G = (nv + kGroup - 1) / kGroup;  // groups of 16 (the last one holds the rest)
   const size_t ntiles = (len + kTile - 1) / kTile;
   const size_t mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  float ah[kTile / kThreads], al[kTile / kThreads];
+  float ah[2], al[2], bh[2], bl[2];  // two elements x (even, odd) double-float partial sums
   double acc = 0.0;
   auto issue = [&](size_t k, unsigned char* st, uint64_t* bar, int lane) {
     const size_t e0 = (blockIdx.x + (k / G) * gridDim.x) * (size_t)kTile;
@@ -728,30 +729,54 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const floa
         bulk_copy_g2s(st + (size_t)2 * kGroup * kTile * 4, w + e0, db, bar);
     });
   };
+  // thread t takes elements 2t and 2t + 1 of a tile; each element's sum runs in two
+  // double-float accumulators (even and odd vectors) for four independent chains
   auto consume = [&](size_t k, const unsigned char* st) {
     const size_t e0 = (blockIdx.x + (k / G) * gridDim.x) * (size_t)kTile;
+    if (e0 + 2 * threadIdx.x >= len) return;
     const int g = (int)(k % G);
     const int i0 = g * kGroup, cnt = nv - i0 < kGroup ? nv - i0 : kGroup;
-    const float* sv = reinterpret_cast<const float*>(st);
-    const double* sw = reinterpret_cast<const double*>(st + (size_t)2 * kGroup * kTile * 4);
+    const float2* sv = reinterpret_cast<const float2*>(st);
+    if (g == 0) {
+      const double2 w2 = reinterpret_cast<const double2*>(st + (size_t)2 * kGroup * kTile * 4)[threadIdx.x];
+      split_f64(w2.x, ah[0], al[0]);
+      split_f64(w2.y, ah[1], al[1]);
+      bh[0] = bl[0] = bh[1] = bl[1] = 0.0f;
+    }
+    int c = 0;
+    for (; c + 1 < cnt; c += 2) {
+      const float2 c0 = cf[i0 + c], c1 = cf[i0 + c + 1];
+      const float2 h0 = sv[(2 * c) * (kTile / 2) + threadIdx.x], l0 = sv[(2 * c + 1) * (kTile / 2) + threadIdx.x];
+      const float2 h1 = sv[(2 * c + 2) * (kTile / 2) + threadIdx.x], l1 = sv[(2 * c + 3) * (kTile / 2) + threadIdx.x];
+      df_sub_prod(c0.x, c0.y, h0.x, l0.x, ah[0], al[0]);
+      df_sub_prod(c0.x, c0.y, h0.y, l0.y, ah[1], al[1]);
+      df_sub_prod(c1.x, c1.y, h1.x, l1.x, bh[0], bl[0]);
+      df_sub_prod(c1.x, c1.y, h1.y, l1.y, bh[1], bl[1]);
+    }
+    if (c < cnt) {
+      const float2 c0 = cf[i0 + c];
+      const float2 h0 = sv[(2 * c) * (kTile / 2) + threadIdx.x], l0 = sv[(2 * c + 1) * (kTile / 2) + threadIdx.x];
+      df_sub_prod(c0.x, c0.y, h0.x, l0.x, ah[0], al[0]);
+      df_sub_prod(c0.x, c0.y, h0.y, l0.y, ah[1], al[1]);
+    }
+    if (g == G - 1) {
+      float hv[2], lv[2];
 #pragma unroll
-    for (int q = 0; q < kTile / kThreads; ++q) {
-      const int el = threadIdx.x + q * kThreads;
-      if (e0 + el >= len) continue;
-      if (g == 0) split_f64(sw[el], ah[q], al[q]);
-      for (int c = 0; c < cnt; ++c) {
-        const float2 cc = cf[i0 + c];
-        df_sub_prod(cc.x, cc.y, sv[(2 * c) * kTile + el], sv[(2 * c + 1) * kTile + el], ah[q], al[q]);
-      }
-      if (g == G - 1) {
-        float hi = ah[q], lo = al[q];
+      for (int q = 0; q < 2; ++q) {
+        // (ah, al) + (bh, bl) in double-float, then normalised
+        float hi = __fadd_rn(ah[q], bh[q]);
+        const float bb = __fsub_rn(hi, ah[q]);
+        float lo = __fadd_rn(__fsub_rn(ah[q], __fsub_rn(hi, bb)), __fsub_rn(bh[q], bb));
+        lo = __fadd_rn(lo, __fadd_rn(al[q], bl[q]));
         df_renorm(hi, lo);
         const double x = f32_to_f64(hi) + f32_to_f64(lo);
         acc = fma(x, x, acc);
         if (scale) df_scale(hi, lo, sh, sl);
-        out[e0 + el] = hi;
-        out[pl + e0 + el] = lo;
+        hv[q] = hi;
+        lv[q] = lo;
       }
+      reinterpret_cast<float2*>(out + e0)[threadIdx.x] = make_float2(hv[0], hv[1]);
+      reinterpret_cast<float2*>(out + pl + e0)[threadIdx.x] = make_float2(lv[0], lv[1]);
     }
   };
   __syncthreads();  // coefficients staged
