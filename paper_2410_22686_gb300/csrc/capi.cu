@@ -186,7 +186,6 @@ struct pc_handle {
   // ideal RBD preconditioner (Eq. matrix_P): the real shift 1 + alpha of both planes
   int precond_kind = PC_PRECOND_EPS_CIRCULANT;
   int arnoldi = PC_ARNOLDI_AUTO;  // pc_arnoldi: basis storage and product precision of flexible GMRES
-  size_t pl = 0;                  // plane stride of a double-float basis vector (floats)
   double2* sigP64 = nullptr;
   float2* sigP32 = nullptr;
   // FST tables
@@ -662,10 +661,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     const size_t U = h->U;
     const int cap = h->cap;
     h->nblocks = num_sms() * kMaxBlocksPerSM;
-    // basis: cap + 1 vectors; a double-float basis stores each as two FP32 planes of
-    // pl = U rounded up to 64 floats (aligned bulk copies), i.e. pl doubles per vector
-    h->pl = (U + 63) & ~(size_t)63;
-    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * h->pl))) goto fail_out;
+    // basis: cap + 1 vectors; a double-float basis stores each as two FP32 planes in
+    // tiles of 512 unknowns (the last tile padded), i.e. ceil(U/512) * 512 doubles per vector
+    const size_t tiled = (U + 511) / 512 * 512;
+    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * tiled))) goto fail_out;
     if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
     if (h->fp32 && (rc = dev_alloc_t(h, &h->vf32, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
@@ -1259,11 +1258,11 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   PC_CUDA(cudaStreamSynchronize(st));
   const bool x0_zero = h->host[2] == 0.0;
 
-  // double-float basis: vector i = FP32 planes hi, lo at Vf + i * ldf (flexible GMRES only)
+  // double-float basis: two FP32 planes per vector, tiled layout (flexible GMRES only)
   const bool df = mode == PC_GMRES_RIGHT && arnoldi_df(h);
   const bool lp_reorth = !arnoldi_strict(h);
   float* Vf = reinterpret_cast<float*>(V);
-  const size_t pl = h->pl, ldf = 2 * pl;
+  const int nvt = h->cap + 1;  // vectors per tile block of the double-float layout
   double* werr = h->scal + 10;
   PC_CUDA(cudaMemsetAsync(werr, 0, sizeof(double), st));
   const double* r0 = V;  // r0 before normalisation (double-float basis: b itself or tbuf)
@@ -1319,9 +1318,9 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   }
   // flexible GMRES with the FP32 preconditioner reads the FP32 rounding of each new
   // basis vector, written by the kernels that finish it (scale / update)
-  float* vf = (mode == PC_GMRES_RIGHT && h->fp32 && !df) ? h->vf32 : nullptr;
+  float* vf = (mode == PC_GMRES_RIGHT && h->fp32) ? h->vf32 : nullptr;
   if (df)
-    GM_CUDA(launch_split_scale(L, r0, Vf, pl, U, nrm2));
+    GM_CUDA(launch_split_scale(L, r0, Vf, nvt, vf, U, nrm2));
   else
     GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr, vf));
 
@@ -1331,23 +1330,19 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
     double* vj = V + (size_t)j * U;
     double* vn = V + (size_t)(j + 1) * U;
     if (df) {
-      // double-float basis: the preconditioner reads the hi plane of v_j, A z_j goes to
-      // wbuf (FP64), the new vector's planes are written by the update
+      // double-float basis: the preconditioner reads the FP32 rounding of v_j (vf32),
+      // A z_j goes to wbuf (FP64), the update writes v_{j+1} and its FP32 rounding
       float* zj = (float*)h->Z + (size_t)j * U;
-      float* vnf = Vf + (size_t)(j + 1) * ldf;
-      GM_CUDA(precond32<float, float>(h, L, Vf + (size_t)j * ldf, zj));
+      GM_CUDA(precond32<float, float>(h, L, vf, zj));
       GM_CUDA(matvec_basis(h, L, zj, h->wbuf));
-      GM_CUDA(launch_multidot_df(L, Vf, ldf, pl, j + 1, h->wbuf, nullptr, U, h->partial, h->hcol, AS.ww, nullptr,
-                                 werr));
+      GM_CUDA(launch_multidot_df(L, Vf, nvt, j + 1, h->wbuf, U, h->partial, h->hcol, AS.ww, nullptr, werr));
       GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
-      GM_CUDA(launch_update_df(L, Vf, ldf, pl, j + 1, h->hcol, h->wbuf, vnf, U, AS.inv, h->partial, AS.q, nullptr,
-                               werr));
+      GM_CUDA(launch_update_df(L, Vf, nvt, j + 1, h->hcol, h->wbuf, vf, U, AS.inv, h->partial, AS.q, nullptr, werr));
       GM_CUDA(launch_arnoldi_check(L, AS));
-      GM_CUDA(launch_multidot_df(L, Vf, ldf, pl, j + 1, nullptr, vnf, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
-                                 werr));
-      GM_CUDA(launch_update_df(L, Vf, ldf, pl, j + 1, h->hcol + ldh, nullptr, vnf, U, nullptr, h->partial, AS.rho2,
+      GM_CUDA(launch_multidot_df(L, Vf, nvt, j + 1, nullptr, U, h->partial, h->hcol + ldh, nullptr, AS.flag, werr));
+      GM_CUDA(launch_update_df(L, Vf, nvt, j + 1, h->hcol + ldh, nullptr, vf, U, nullptr, h->partial, AS.rho2,
                                AS.flag, werr));
-      GM_CUDA(launch_scale_df(L, vnf, pl, U, AS.rho2, AS.flag));
+      GM_CUDA(launch_scale_df(L, Vf, nvt, j + 1, vf, U, AS.rho2, AS.flag));
     } else if (mode == PC_GMRES_RIGHT) {
       if (h->fp32) {
         float* zj = (float*)h->Z + (size_t)j * U;
@@ -1497,7 +1492,7 @@ static int enqueue_pre(pc_handle* h, Launch& L, const double* b, double* x, doub
   GR_CUDA(launch_arnoldi_start(L, h->gvec, nrm2, h->scal + 1, h->scal + 2, 1));
   if (arnoldi_df(h)) {
     GR_CUDA(cudaMemsetAsync(h->scal + 10, 0, sizeof(double), L.stream));
-    GR_CUDA(launch_split_scale(L, b, reinterpret_cast<float*>(h->V), h->pl, U, nrm2));
+    GR_CUDA(launch_split_scale(L, b, reinterpret_cast<float*>(h->V), h->cap + 1, h->vf32, U, nrm2));
   } else {
     GR_CUDA(cudaMemcpyAsync(h->V, b, U * sizeof(double), cudaMemcpyDeviceToDevice, L.stream));
     GR_CUDA(launch_scale_by_inv_norm(L, h->V, U, nrm2, nullptr, h->fp32 ? h->vf32 : nullptr));
@@ -1513,23 +1508,23 @@ static int enqueue_body(pc_handle* h, Launch& L, double rtol, int maxit, cudaGra
   const int* j = h->idx;
   const ArnoldiScalars AS{h->scal + 4, h->scal + 5, h->scal + 6, h->scal + 7, h->scal + 8, h->scal + 9};
   if (arnoldi_df(h)) {
-    // double-float basis (vectors 2 pl floats apart): see gmres_impl
+    // double-float basis (tiled layout): see gmres_impl
     float* Z = (float*)h->Z;
     float* Vf = reinterpret_cast<float*>(h->V);
-    const size_t pl = h->pl, ldf = 2 * pl;
+    const int nvt = h->cap + 1;
     double* werr = h->scal + 10;
-    GR_CUDA((precond32<float, float>(h, L, Vf, Z, U, j, true, ldf)));
+    GR_CUDA((precond32<float, float>(h, L, h->vf32, Z, U, j, false)));
     GR_CUDA(matvec_basis(h, L, Z, h->wbuf, U, 0, j));
-    GR_CUDA(launch_multidot_df_dev(L, Vf, ldf, pl, maxit, j, h->wbuf, U, h->partial, h->hcol, AS.ww, nullptr, werr));
+    GR_CUDA(launch_multidot_df_dev(L, Vf, nvt, maxit, j, h->wbuf, U, h->partial, h->hcol, AS.ww, nullptr, werr));
     GR_CUDA(launch_arnoldi_prep_dev(L, j, h->hcol, AS));
-    GR_CUDA(launch_update_df_dev(L, Vf, ldf, pl, maxit, j, h->hcol, h->wbuf, U, AS.inv, h->partial, AS.q, nullptr,
-                                 werr));
+    GR_CUDA(launch_update_df_dev(L, Vf, nvt, maxit, j, h->hcol, h->wbuf, h->vf32, U, AS.inv, h->partial, AS.q,
+                                 nullptr, werr));
     GR_CUDA(launch_arnoldi_check(L, AS));
-    GR_CUDA(launch_multidot_df_dev(L, Vf, ldf, pl, maxit, j, nullptr, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
+    GR_CUDA(launch_multidot_df_dev(L, Vf, nvt, maxit, j, nullptr, U, h->partial, h->hcol + ldh, nullptr, AS.flag,
                                    werr));
-    GR_CUDA(launch_update_df_dev(L, Vf, ldf, pl, maxit, j, h->hcol + ldh, nullptr, U, nullptr, h->partial, AS.rho2,
-                                 AS.flag, werr));
-    GR_CUDA(launch_scale_df_dev(L, Vf, ldf, pl, j, U, AS.rho2, AS.flag));
+    GR_CUDA(launch_update_df_dev(L, Vf, nvt, maxit, j, h->hcol + ldh, nullptr, h->vf32, U, nullptr, h->partial,
+                                 AS.rho2, AS.flag, werr));
+    GR_CUDA(launch_scale_df_dev(L, Vf, nvt, j, h->vf32, U, AS.rho2, AS.flag));
     GR_CUDA(launch_givens_dev(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, h->scal + 1,
                               h->scal + 2));
     GR_CUDA(launch_loop_control(L, h->idx, h->idx + 1, h->scal + 1, rtol, maxit, hc));

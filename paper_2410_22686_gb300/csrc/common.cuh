@@ -395,26 +395,29 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
                                  int set_ref);
 
 // RHS assembly and gradient
-// double-float basis: vector i = FP32 planes hi at Vf + i*ldv, lo at + pl (ldv = 2 pl,
-// pl >= len rounded up to 64, len even).  The first pass streams the basis through
-// shared memory with bulk copies; a wait that runs out of its budget writes a nonzero
-// value into *err (device) and the kernel returns early.  gate != nullptr selects
-// the (gated) second pass on the hi planes.
-cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* w,
-                               const float* xh, size_t len, double* partial, double* out, double* ww,
-                               const double* gate, double* err);
-cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* coef,
-                             const double* w, float* out, size_t len, const double* scale, double* partial, double* q,
-                             const double* gate, double* err);
-cudaError_t launch_split_scale(Launch& L, const double* src, float* out, size_t pl, size_t len, const double* nrm2);
-cudaError_t launch_scale_df(Launch& L, float* v, size_t pl, size_t len, const double* nrm2, const double* gate);
-cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
-                                   const double* w, size_t len, double* partial, double* out, double* ww,
-                                   const double* gate, double* err);
-cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
-                                 const double* coef, const double* w, size_t len, const double* scale,
-                                 double* partial, double* q, const double* gate, double* err);
-cudaError_t launch_scale_df_dev(Launch& L, float* Vf, size_t ldv, size_t pl, const int* jdev, size_t len,
+// double-float basis: each vector two FP32 planes (hi, lo) in a layout tiled by 512
+// unknowns, nvt vectors per tile block (vector nv is the new one; len even; the
+// allocation holds ceil(len/512) * nvt * 1024 floats).  The first pass streams the
+// basis through shared memory with bulk copies; a wait that runs out of its budget
+// writes a nonzero value into *err (device) and the kernel returns early.
+// gate != nullptr selects the (gated) second pass on the hi planes.  vf receives the
+// contiguous hi plane (FP32 rounding) of the vector a kernel finishes.
+cudaError_t launch_multidot_df(Launch& L, const float* Vf, int nvt, int nv, const double* w, size_t len,
+                               double* partial, double* out, double* ww, const double* gate, double* err);
+cudaError_t launch_update_df(Launch& L, float* Vf, int nvt, int nv, const double* coef, const double* w, float* vf,
+                             size_t len, const double* scale, double* partial, double* q, const double* gate,
+                             double* err);
+cudaError_t launch_split_scale(Launch& L, const double* src, float* Vf, int nvt, float* vf, size_t len,
+                               const double* nrm2);
+cudaError_t launch_scale_df(Launch& L, float* Vf, int nvt, int nv, float* vf, size_t len, const double* nrm2,
+                            const double* gate);
+cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, int nvt, int nv_max, const int* jdev, const double* w,
+                                   size_t len, double* partial, double* out, double* ww, const double* gate,
+                                   double* err);
+cudaError_t launch_update_df_dev(Launch& L, float* Vf, int nvt, int nv_max, const int* jdev, const double* coef,
+                                 const double* w, float* vf, size_t len, const double* scale, double* partial,
+                                 double* q, const double* gate, double* err);
+cudaError_t launch_scale_df_dev(Launch& L, float* Vf, int nvt, const int* jdev, float* vf, size_t len,
                                 const double* nrm2, const double* gate);
 cudaError_t launch_build_rhs(Launch& L, int64_t ms, int n, double tau, double sqrt_gamma, const double* f,
                              const double* g, const double* y0, double* b);

@@ -439,22 +439,24 @@ __global__ void loop_start_kernel(int* jdev, int* kdev, const double* est, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Double-float basis (flexible GMRES with the FP32 preconditioner).  Basis
-// vector i is two FP32 planes, hi at Vf + i*ldv and lo at Vf + i*ldv + pl
-// (ldv = 2 pl, pl >= len rounded up to a multiple of 64), v = hi + lo to about
-// 2^-48 relative; hi is the FP32 rounding of v and is what the FP32
-// preconditioner reads.  The Arnoldi products and sums run on the FP32 units as
-// error-free transformations (the product's rounding error by FMA, Knuth's
-// TwoSum for the running sums), so the passes over the basis are bound by HBM
-// instead of by GB300's FP64 unit.  Scalars (h_ij, norms) and the per-block
-// reductions stay FP64.
+// Double-float basis (flexible GMRES with the FP32 preconditioner).  Each basis
+// vector is held as two FP32 planes, v = hi + lo to about 2^-48 relative, in a
+// tiled layout: the planes of element tile t (kTile consecutive unknowns) of
+// every vector are stored together, vector by vector,
+//   offset(i, e, plane) = ((t nvt + i) 2 + plane) kTile + e mod kTile,  t = e / kTile,
+// (nvt = vectors per tile block), so the tile of a group of vectors is one
+// contiguous block: one bulk copy fills a stage.  The FP32 rounding of the newest
+// vector (its hi plane) is also written contiguously for the FP32 preconditioner.
+// The Arnoldi products and sums run on the FP32 units as error-free
+// transformations (the product's rounding error by FMA, Knuth's TwoSum for the
+// running sums), so the passes over the basis are bound by HBM instead of by
+// GB300's FP64 unit.  Scalars (h_ij, norms) and the per-block reductions stay FP64.
 //
-// The first pass (multi-dot and update) streams tiles of the basis into shared
-// memory with bulk asynchronous copies (several stages in flight per SM on
-// mbarriers), so the bytes in flight do not compete with the accumulators for
-// registers; the selective second pass reads the hi planes directly.
+// The first pass (multi-dot and update) streams the basis through shared memory
+// (a producer warp issues the bulk asynchronous copies of several stages ahead on
+// mbarriers); the selective second pass reads the hi planes directly.
 // ---------------------------------------------------------------------------
-constexpr int kTile = 512;             // elements per streamed tile (two per thread)
+constexpr int kTile = 512;             // elements per tile of the layout and per streamed stage (two per thread)
 constexpr int kGroup = 16;             // basis vectors per stage of the update
 constexpr int kBarBytes = 256;         // mbarriers (16 full, 16 empty) at the start of the dynamic shared memory
 constexpr size_t kStreamSmem = 220 * 1024;  // dynamic shared-memory budget of a streaming CTA
@@ -511,6 +513,11 @@ __device__ __forceinline__ void df_scale(float& hi, float& lo, float sh, float s
 }
 
 __device__ __forceinline__ size_t round4(size_t x) { return (x + 3) & ~(size_t)3; }
+
+// offset of element e of plane p (0 hi, 1 lo) of basis vector i in the tiled layout
+__host__ __device__ __forceinline__ size_t df_at(int nvt, int i, size_t e, int p) {
+  return (((e / kTile) * (size_t)nvt + (size_t)i) * 2 + p) * kTile + e % kTile;
+}
 
 // nv basis vectors in ceil(nv / 16) chunks of nearly equal size (no small tail chunk,
 // whose stages would be mostly overhead): chunk c covers [i0, i0 + cnt)
@@ -595,7 +602,7 @@ __device__ __forceinline__ void issue_copies(uint64_t* bar, uint32_t bytes, int 
 // First pass, multi-dot: partial[b*ld + i0 + c] = sum over CTA b of V_{i0+c} . w
 // (w FP64, split on use) and, WITH_NORM, partial[b*ld + ncol_norm] = w . w.
 template <int CNT, bool WITH_NORM>
-__device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf, size_t ldv, size_t pl, int i0,
+__device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf, int nvt, int i0,
                                                    const double* __restrict__ w, size_t len,
                                                    double* __restrict__ partial, int ncol_norm, int ld, int S,
                                                    size_t stage_stride, double* err) {
@@ -608,13 +615,13 @@ __device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf,
   auto issue = [&](size_t k, unsigned char* st, uint64_t* bar, int lane) {
     const size_t e0 = (blockIdx.x + k * gridDim.x) * (size_t)kTile;
     const size_t n = len - e0 < (size_t)kTile ? len - e0 : (size_t)kTile;  // even: len is even
-    const uint32_t fb = (uint32_t)(round4(n) * 4), db = (uint32_t)(n * 8);
-    // copies 0 .. 2 CNT - 1: plane c % 2 of vector i0 + c / 2; copy 2 CNT: w
-    issue_copies(bar, 2u * CNT * fb + db, 2 * CNT + 1, lane, [&](int c) {
-      if (c < 2 * CNT)
-        bulk_copy_g2s(st + (size_t)c * kTile * 4, Vf + (size_t)(i0 + c / 2) * ldv + (c & 1) * pl + e0, fb, bar);
+    const uint32_t vb = (uint32_t)CNT * 2 * kTile * 4, db = (uint32_t)(n * 8);
+    // copy 0: the tile of vectors i0 .. i0 + CNT - 1 (contiguous); copy 1: w
+    issue_copies(bar, vb + db, 2, lane, [&](int c) {
+      if (c == 0)
+        bulk_copy_g2s(st, Vf + df_at(nvt, i0, e0, 0), vb, bar);
       else
-        bulk_copy_g2s(st + (size_t)2 * CNT * kTile * 4, w + e0, db, bar);
+        bulk_copy_g2s(st + vb, w + e0, db, bar);
     });
   };
   // thread t takes elements 2t and 2t + 1 of a tile (8-byte and 16-byte shared loads;
@@ -657,29 +664,28 @@ __device__ __forceinline__ void multidot_df_stream(const float* __restrict__ Vf,
 }
 
 template <int CNT, bool WITH_NORM>
-__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
-                                                                  int i0, const double* __restrict__ w, size_t len,
-                                                                  double* __restrict__ partial, int nv, int ld, int S,
-                                                                  size_t stage_stride, double* err) {
-  multidot_df_stream<CNT, WITH_NORM>(Vf, ldv, pl, i0, w, len, partial, nv, ld, S, stage_stride, err);
+__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_kernel(const float* __restrict__ Vf, int nvt, int i0,
+                                                                        const double* __restrict__ w, size_t len,
+                                                                        double* __restrict__ partial, int nv, int ld,
+                                                                        int S, size_t stage_stride, double* err) {
+  multidot_df_stream<CNT, WITH_NORM>(Vf, nvt, i0, w, len, partial, nv, ld, S, stage_stride, err);
 }
 
 // device-resident index: nv = *jdev + 1 vectors; launch `chunk` of the balanced split
 // (exits when nv needs fewer chunks)
 template <bool WITH_NORM>
-__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_dyn_kernel(const float* __restrict__ Vf, size_t ldv,
-                                                                      size_t pl, int chunk,
-                                                                      const double* __restrict__ w,
-                                                                      const int* __restrict__ jdev, size_t len,
-                                                                      double* __restrict__ partial, int ld, int S,
-                                                                      size_t stage_stride, double* err) {
+__global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_dyn_kernel(const float* __restrict__ Vf, int nvt,
+                                                                            int chunk, const double* __restrict__ w,
+                                                                            const int* __restrict__ jdev, size_t len,
+                                                                            double* __restrict__ partial, int ld,
+                                                                            int S, size_t stage_stride, double* err) {
   const int nv = *jdev + 1;
   if (chunk >= (nv + kChunk - 1) / kChunk) return;
   int i0, cnt;
   balanced_chunk(nv, chunk, &i0, &cnt);
   switch (cnt) {
 #define PCOPT_DYN(k) \
-  case k: multidot_df_stream<k, WITH_NORM>(Vf, ldv, pl, i0, w, len, partial, ld - 1, ld, S, stage_stride, err); break;
+  case k: multidot_df_stream<k, WITH_NORM>(Vf, nvt, i0, w, len, partial, ld - 1, ld, S, stage_stride, err); break;
     PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
     PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
 #undef PCOPT_DYN
@@ -687,21 +693,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_dyn_kernel(cons
   }
 }
 
-// First pass, update: out = (w - sum_{i < nv} coef_i V_i) * scale (double-float
-// planes of out), partial[b] = CTA sum of |w - sum|^2 (FP64, before scaling).  The
-// stream walks (tile, group of 16 vectors) items; w is copied with a tile's first group.
-// With jdev: nv = *jdev + 1 and out = Vf + nv * ldv.
-__global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
-                                                                int nv, const double* __restrict__ coef,
-                                                                const double* __restrict__ w, float* out, size_t len,
-                                                                const double* __restrict__ scale,
-                                                                double* __restrict__ partial,
-                                                                const int* __restrict__ jdev, int S,
-                                                                size_t stage_stride, double* err) {
-  if (jdev) {
-    nv = *jdev + 1;
-    out = const_cast<float*>(Vf) + (size_t)nv * ldv;
-  }
+// First pass, update: vector nv = (w - sum_{i < nv} coef_i V_i) * scale (double-float),
+// vf = its hi plane (contiguous), partial[b] = CTA sum of |w - sum|^2 (FP64, before
+// scaling).  The stream walks (tile, group of 16 vectors) items; w is copied with a
+// tile's first group.  With jdev: nv = *jdev + 1.
+__global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(float* Vf, int nvt, int nv,
+                                                                      const double* __restrict__ coef,
+                                                                      const double* __restrict__ w, float* vf,
+                                                                      size_t len, const double* __restrict__ scale,
+                                                                      double* __restrict__ partial,
+                                                                      const int* __restrict__ jdev, int S,
+                                                                      size_t stage_stride, double* err) {
+  if (jdev) nv = *jdev + 1;
   __shared__ float2 cf[1024];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     float hi, lo;
@@ -720,11 +723,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const floa
     const int g = (int)(k % G);
     const int i0 = g * kGroup, cnt = nv - i0 < kGroup ? nv - i0 : kGroup;
     const size_t n = len - e0 < (size_t)kTile ? len - e0 : (size_t)kTile;
-    const uint32_t fb = (uint32_t)(round4(n) * 4), db = (uint32_t)(n * 8);
-    // copies 0 .. 2 cnt - 1: plane c % 2 of vector i0 + c / 2; copy 2 cnt (first group only): w
-    issue_copies(bar, 2u * cnt * fb + (g == 0 ? db : 0u), 2 * cnt + (g == 0 ? 1 : 0), lane, [&](int c) {
-      if (c < 2 * cnt)
-        bulk_copy_g2s(st + (size_t)c * kTile * 4, Vf + (size_t)(i0 + c / 2) * ldv + (c & 1) * pl + e0, fb, bar);
+    const uint32_t vb = (uint32_t)cnt * 2 * kTile * 4, db = (uint32_t)(n * 8);
+    // copy 0: the tile of vectors i0 .. i0 + cnt - 1 (contiguous); copy 1 (first group): w
+    issue_copies(bar, vb + (g == 0 ? db : 0u), g == 0 ? 2 : 1, lane, [&](int c) {
+      if (c == 0)
+        bulk_copy_g2s(st, Vf + df_at(nvt, i0, e0, 0), vb, bar);
       else
         bulk_copy_g2s(st + (size_t)2 * kGroup * kTile * 4, w + e0, db, bar);
     });
@@ -775,8 +778,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const floa
         hv[q] = hi;
         lv[q] = lo;
       }
-      reinterpret_cast<float2*>(out + e0)[threadIdx.x] = make_float2(hv[0], hv[1]);
-      reinterpret_cast<float2*>(out + pl + e0)[threadIdx.x] = make_float2(lv[0], lv[1]);
+      float* o = Vf + df_at(nvt, nv, e0, 0);
+      reinterpret_cast<float2*>(o)[threadIdx.x] = make_float2(hv[0], hv[1]);
+      reinterpret_cast<float2*>(o + kTile)[threadIdx.x] = make_float2(lv[0], lv[1]);
+      reinterpret_cast<float2*>(vf + e0)[threadIdx.x] = make_float2(hv[0], hv[1]);
     }
   };
   __syncthreads();  // coefficients staged
@@ -793,20 +798,19 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(const floa
 }
 
 // Second pass (re-orthogonalisation, gated): e_c = hi_{i0+c} . x with x the hi plane of
-// the new vector (FP32 products of hi planes: the coefficients removed here are ~1e-6).
+// the new vector nv (FP32 products of hi planes: the coefficients removed here are ~1e-6).
 template <int CNT>
-__device__ __forceinline__ void multidot_lp_body(const float* __restrict__ Vf, size_t ldv, int i0,
-                                                 const float* __restrict__ xh, size_t len,
+__device__ __forceinline__ void multidot_lp_body(const float* __restrict__ Vf, int nvt, int i0, int nv, size_t len,
                                                  double* __restrict__ partial, int ld) {
   float s[CNT];
 #pragma unroll
   for (int c = 0; c < CNT; ++c) s[c] = 0.0f;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const float* Vb = Vf + (size_t)i0 * ldv;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    const float x = xh[e];
+    const float x = Vf[df_at(nvt, nv, e, 0)];
+    const float* vb = Vf + df_at(nvt, i0, e, 0);  // vector i0 + c at vb + 2 c kTile
 #pragma unroll
-    for (int c = 0; c < CNT; ++c) s[c] = fmaf(__ldg(Vb + (size_t)c * ldv + e), x, s[c]);
+    for (int c = 0; c < CNT; ++c) s[c] = fmaf(__ldg(vb + (size_t)2 * c * kTile), x, s[c]);
   }
   __shared__ double red[kThreads / 32][CNT];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -824,26 +828,24 @@ __device__ __forceinline__ void multidot_lp_body(const float* __restrict__ Vf, s
 }
 
 template <int CNT>
-__global__ void __launch_bounds__(kThreads) multidot_lp_kernel(const float* __restrict__ Vf, size_t ldv, int i0,
-                                                               const float* __restrict__ xh, size_t len,
-                                                               double* __restrict__ partial, int ld,
+__global__ void __launch_bounds__(kThreads) multidot_lp_kernel(const float* __restrict__ Vf, int nvt, int i0, int nv,
+                                                               size_t len, double* __restrict__ partial, int ld,
                                                                const double* __restrict__ gate) {
   if (gated_off(gate)) return;
-  multidot_lp_body<CNT>(Vf, ldv, i0, xh, len, partial, ld);
+  multidot_lp_body<CNT>(Vf, nvt, i0, nv, len, partial, ld);
 }
 
-__global__ void __launch_bounds__(kThreads) multidot_lp_dyn_kernel(const float* __restrict__ Vf, size_t ldv, int i0,
+__global__ void __launch_bounds__(kThreads) multidot_lp_dyn_kernel(const float* __restrict__ Vf, int nvt, int i0,
                                                                    const int* __restrict__ jdev, size_t len,
                                                                    double* __restrict__ partial, int ld,
                                                                    const double* __restrict__ gate) {
   if (gated_off(gate)) return;
   const int nv = *jdev + 1;
   if (i0 >= nv) return;
-  const float* xh = Vf + (size_t)nv * ldv;
   const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
   switch (cnt) {
 #define PCOPT_DYN(k) \
-  case k: multidot_lp_body<k>(Vf, ldv, i0, xh, len, partial, ld); break;
+  case k: multidot_lp_body<k>(Vf, nvt, i0, nv, len, partial, ld); break;
     PCOPT_DYN(1) PCOPT_DYN(2) PCOPT_DYN(3) PCOPT_DYN(4) PCOPT_DYN(5) PCOPT_DYN(6) PCOPT_DYN(7) PCOPT_DYN(8)
     PCOPT_DYN(9) PCOPT_DYN(10) PCOPT_DYN(11) PCOPT_DYN(12) PCOPT_DYN(13) PCOPT_DYN(14) PCOPT_DYN(15) PCOPT_DYN(16)
 #undef PCOPT_DYN
@@ -851,28 +853,26 @@ __global__ void __launch_bounds__(kThreads) multidot_lp_dyn_kernel(const float* 
   }
 }
 
-// Second pass update (gated): v -= sum_i e_i hi_i (FP32 sum of hi planes) on the
-// double-float vector `out` in place; partial[b] = block sum of |v|^2.
-// With jdev: nv = *jdev + 1 and out = Vf + nv * ldv.
-__global__ void __launch_bounds__(kThreads) update_lp_kernel(const float* __restrict__ Vf, size_t ldv, size_t pl,
-                                                             int nv, const double* __restrict__ coef, float* out,
-                                                             size_t len, double* __restrict__ partial,
+// Second pass update (gated): vector nv -= sum_i e_i hi_i (FP32 sum of hi planes) in
+// place; partial[b] = block sum of |v|^2.  With jdev: nv = *jdev + 1.
+__global__ void __launch_bounds__(kThreads) update_lp_kernel(float* Vf, int nvt, int nv,
+                                                             const double* __restrict__ coef, size_t len,
+                                                             double* __restrict__ partial,
                                                              const double* __restrict__ gate,
                                                              const int* __restrict__ jdev) {
   if (gated_off(gate)) return;
-  if (jdev) {
-    nv = *jdev + 1;
-    out = const_cast<float*>(Vf) + (size_t)nv * ldv;
-  }
+  if (jdev) nv = *jdev + 1;
   __shared__ float cf[1024];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (float)coef[i];
   __syncthreads();
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    float ah = out[e], al = out[pl + e];
+    float* o = Vf + df_at(nvt, nv, e, 0);
+    float ah = o[0], al = o[kTile];
+    const float* vb = Vf + df_at(nvt, 0, e, 0);  // vector i at vb + 2 i kTile
     float sf = 0.0f;
-    for (int i = 0; i < nv; ++i) sf = fmaf(cf[i], __ldg(Vf + (size_t)i * ldv + e), sf);
+    for (int i = 0; i < nv; ++i) sf = fmaf(cf[i], __ldg(vb + (size_t)2 * i * kTile), sf);
     const float s2 = __fsub_rn(ah, sf);
     const float bb = __fsub_rn(s2, ah);
     al = __fadd_rn(al, __fadd_rn(__fsub_rn(ah, __fsub_rn(s2, bb)), __fsub_rn(neg_f(sf), bb)));
@@ -880,8 +880,8 @@ __global__ void __launch_bounds__(kThreads) update_lp_kernel(const float* __rest
     df_renorm(ah, al);
     const double x = f32_to_f64(ah) + f32_to_f64(al);
     acc = fma(x, x, acc);
-    out[e] = ah;
-    out[pl + e] = al;
+    o[0] = ah;
+    o[kTile] = al;
   }
   __shared__ double red[kThreads / 32];
   acc = warp_sum(acc);
@@ -894,34 +894,39 @@ __global__ void __launch_bounds__(kThreads) update_lp_kernel(const float* __rest
   }
 }
 
-// planes of `out` = src / sqrt(nrm2[0]) (src FP64; a zero norm copies src unscaled)
-__global__ void split_scale_kernel(const double* __restrict__ src, float* __restrict__ out, size_t pl, size_t len,
-                                   const double* __restrict__ nrm2) {
+// vector 0 = src / sqrt(nrm2[0]) in double-float (a zero norm copies src unscaled), vf = hi
+__global__ void split_scale_kernel(const double* __restrict__ src, float* __restrict__ Vf, int nvt, float* vf,
+                                   size_t len, const double* __restrict__ nrm2) {
   const bool nz = nrm2[0] > 0.0;
   const double q = nz ? 1.0 / sqrt(nrm2[0]) : 1.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
     float hi, lo;
     split_f64(src[e] * q, hi, lo);
-    out[e] = hi;
-    out[pl + e] = lo;
+    float* o = Vf + df_at(nvt, 0, e, 0);
+    o[0] = hi;
+    o[kTile] = lo;
+    vf[e] = hi;
   }
 }
 
-// double-float vector *= 1/sqrt(nrm2[0]) (gated; with jdev the vector is v + (*jdev+1) ldv)
-__global__ void scale_df_kernel(float* v, size_t ldv, size_t pl, size_t len, const double* __restrict__ nrm2,
+// vector nv *= 1/sqrt(nrm2[0]) in double-float, vf = its hi plane (gated; with jdev
+// nv = *jdev + 1)
+__global__ void scale_df_kernel(float* Vf, int nvt, int nv, float* vf, size_t len, const double* __restrict__ nrm2,
                                 const double* __restrict__ gate, const int* __restrict__ jdev) {
   if (gated_off(gate)) return;
-  if (jdev) v += (size_t)(*jdev + 1) * ldv;
+  if (jdev) nv = *jdev + 1;
   if (!(nrm2[0] > 0.0)) return;
   float sh, sl;
   split_f64(1.0 / sqrt(nrm2[0]), sh, sl);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += stride) {
-    float hi = v[e], lo = v[pl + e];
+    float* o = Vf + df_at(nvt, nv, e, 0);
+    float hi = o[0], lo = o[kTile];
     df_scale(hi, lo, sh, sl);
-    v[e] = hi;
-    v[pl + e] = lo;
+    o[0] = hi;
+    o[kTile] = lo;
+    vf[e] = hi;
   }
 }
 
@@ -999,7 +1004,7 @@ cudaError_t allow_smem(K kern, size_t smem) {
 }
 
 template <int CNT, bool N>
-cudaError_t multidot_df_chunk(Launch& L, const float* Vf, size_t ldv, size_t pl, int i0, const double* w, size_t len,
+cudaError_t multidot_df_chunk(Launch& L, const float* Vf, int nvt, int i0, const double* w, size_t len,
                               double* partial, int nv, int ld, double* err, unsigned* blocks_out) {
   const size_t stride = round128((size_t)2 * CNT * kTile * 4 + (size_t)kTile * 8);
   const int S = stream_stages_for(stride);
@@ -1010,16 +1015,16 @@ cudaError_t multidot_df_chunk(Launch& L, const float* Vf, size_t ldv, size_t pl,
   const unsigned nb = stream_grid(len);
   *blocks_out = nb;
   L.begin(KC_DOT);
-  kern<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, i0, w, len, partial, nv, ld, S, stride, err);
+  kern<<<nb, kStreamThreads, smem, L.stream>>>(Vf, nvt, i0, w, len, partial, nv, ld, S, stride, err);
   return L.end(KC_DOT, 8.0 * len * (CNT + 1), 2.0 * len * (CNT + (N ? 1 : 0)));
 }
 
 template <bool N>
-cudaError_t multidot_df_dispatch(int cnt, Launch& L, const float* Vf, size_t ldv, size_t pl, int i0, const double* w,
+cudaError_t multidot_df_dispatch(int cnt, Launch& L, const float* Vf, int nvt, int i0, const double* w,
                                  size_t len, double* partial, int nv, int ld, double* err, unsigned* nb) {
   switch (cnt) {
 #define PCOPT_CASE(k) \
-  case k: return multidot_df_chunk<k, N>(L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, nb);
+  case k: return multidot_df_chunk<k, N>(L, Vf, nvt, i0, w, len, partial, nv, ld, err, nb);
     PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
     PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
     PCOPT_CASE(15) PCOPT_CASE(16)
@@ -1029,21 +1034,21 @@ cudaError_t multidot_df_dispatch(int cnt, Launch& L, const float* Vf, size_t ldv
 }
 
 template <int CNT>
-cudaError_t multidot_lp_chunk(Launch& L, const float* Vf, size_t ldv, int i0, const float* xh, size_t len,
-                              double* partial, int ld, const double* gate, unsigned* blocks_out) {
+cudaError_t multidot_lp_chunk(Launch& L, const float* Vf, int nvt, int i0, int nv, size_t len, double* partial, int ld,
+                              const double* gate, unsigned* blocks_out) {
   auto kern = multidot_lp_kernel<CNT>;
   const unsigned nb = wave_blocks(kern, 0, len);
   *blocks_out = nb;
   L.begin(KC_REORTH);
-  kern<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, i0, xh, len, partial, ld, gate);
+  kern<<<nb, kThreads, 0, L.stream>>>(Vf, nvt, i0, nv, len, partial, ld, gate);
   return L.end(KC_REORTH, 0.0, 0.0);
 }
 
-cudaError_t multidot_lp_dispatch(int cnt, Launch& L, const float* Vf, size_t ldv, int i0, const float* xh, size_t len,
+cudaError_t multidot_lp_dispatch(int cnt, Launch& L, const float* Vf, int nvt, int i0, int nv, size_t len,
                                  double* partial, int ld, const double* gate, unsigned* nb) {
   switch (cnt) {
 #define PCOPT_CASE(k) \
-  case k: return multidot_lp_chunk<k>(L, Vf, ldv, i0, xh, len, partial, ld, gate, nb);
+  case k: return multidot_lp_chunk<k>(L, Vf, nvt, i0, nv, len, partial, ld, gate, nb);
     PCOPT_CASE(1) PCOPT_CASE(2) PCOPT_CASE(3) PCOPT_CASE(4) PCOPT_CASE(5) PCOPT_CASE(6) PCOPT_CASE(7)
     PCOPT_CASE(8) PCOPT_CASE(9) PCOPT_CASE(10) PCOPT_CASE(11) PCOPT_CASE(12) PCOPT_CASE(13) PCOPT_CASE(14)
     PCOPT_CASE(15) PCOPT_CASE(16)
@@ -1168,11 +1173,10 @@ cudaError_t launch_arnoldi_start(Launch& L, double* gvec, const double* nrm2, do
 }
 
 // ---------------------------------------------------------------------------
-// double-float basis: vector i = planes hi at Vf + i*ldv, lo at + pl (ldv = 2 pl)
-cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* w,
-                               const float* xh, size_t len, double* partial, double* out, double* ww,
-                               const double* gate, double* err) {
-  if (nv < 1 || nv > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+// double-float basis in the tiled layout (df_at); vector nv is the new one
+cudaError_t launch_multidot_df(Launch& L, const float* Vf, int nvt, int nv, const double* w, size_t len,
+                               double* partial, double* out, double* ww, const double* gate, double* err) {
+  if (nv < 1 || nv >= nvt || nv > kChunk * kMaxChunks) return cudaErrorInvalidValue;
   if (len & 1) return cudaErrorInvalidValue;  // the streamed tiles need an even length
   const bool lp = gate != nullptr;  // gated launches are the re-orthogonalisation pass
   const int ld = nv + 1;
@@ -1182,7 +1186,7 @@ cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl
     for (int i0 = 0, c = 0; i0 < nv; i0 += kChunk, ++c) {
       const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
       unsigned nb = 0;
-      cudaError_t e = multidot_lp_dispatch(cnt, L, Vf, ldv, i0, xh, len, partial, ld, gate, &nb);
+      cudaError_t e = multidot_lp_dispatch(cnt, L, Vf, nvt, i0, nv, len, partial, ld, gate, &nb);
       if (e != cudaSuccess) return e;
       cg.nb[c] = nb;
       nb_sum += nb * (double)cnt;
@@ -1193,9 +1197,8 @@ cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl
     for (int c = 0; c < nch; ++c) {
       int i0, cnt;
       balanced_chunk(nv, c, &i0, &cnt);
-      cudaError_t e = (i0 == 0 && ww)
-                          ? multidot_df_dispatch<true>(cnt, L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, &nb)
-                          : multidot_df_dispatch<false>(cnt, L, Vf, ldv, pl, i0, w, len, partial, nv, ld, err, &nb);
+      cudaError_t e = (i0 == 0 && ww) ? multidot_df_dispatch<true>(cnt, L, Vf, nvt, i0, w, len, partial, nv, ld, err, &nb)
+                                      : multidot_df_dispatch<false>(cnt, L, Vf, nvt, i0, w, len, partial, nv, ld, err, &nb);
       if (e != cudaSuccess) return e;
       nb_sum += nb * (double)cnt;
     }
@@ -1209,10 +1212,10 @@ cudaError_t launch_multidot_df(Launch& L, const float* Vf, size_t ldv, size_t pl
   return lp ? L.end(kc, 0.0, 0.0) : L.end(kc, 8.0 * nb_sum, nb_sum);
 }
 
-cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv, const double* coef,
-                             const double* w, float* out, size_t len, const double* scale, double* partial, double* q,
-                             const double* gate, double* err) {
-  if (nv < 1 || nv > 1024) return cudaErrorInvalidValue;
+cudaError_t launch_update_df(Launch& L, float* Vf, int nvt, int nv, const double* coef, const double* w, float* vf,
+                             size_t len, const double* scale, double* partial, double* q, const double* gate,
+                             double* err) {
+  if (nv < 1 || nv >= nvt || nv > 1024) return cudaErrorInvalidValue;
   if (len & 1) return cudaErrorInvalidValue;
   const bool lp = gate != nullptr;
   unsigned nb;
@@ -1220,7 +1223,7 @@ cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, 
   if (lp) {
     nb = wave_blocks(update_lp_kernel, 0, len);
     L.begin(KC_REORTH);
-    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, pl, nv, coef, out, len, partial, gate, nullptr);
+    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, nvt, nv, coef, len, partial, gate, nullptr);
     e = L.end(KC_REORTH, 0.0, 0.0);
   } else {
     const size_t stride = round128((size_t)2 * kGroup * kTile * 4 + (size_t)kTile * 8);
@@ -1229,9 +1232,9 @@ cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, 
     if ((e = allow_smem(update_df_kernel, smem)) != cudaSuccess) return e;
     nb = stream_grid(len);
     L.begin(KC_UPDATE);
-    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, nv, coef, w, out, len, scale, partial, nullptr,
-                                                            S, stride, err);
-    e = L.end(KC_UPDATE, 8.0 * len * (nv + 2), 2.0 * len * (nv + 1));
+    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, nvt, nv, coef, w, vf, len, scale, partial, nullptr, S,
+                                                            stride, err);
+    e = L.end(KC_UPDATE, 8.0 * len * (nv + 2) + 4.0 * len, 2.0 * len * (nv + 1));
   }
   if (e != cudaSuccess) return e;
   const int kr = lp ? KC_REORTH : KC_REDUCE;
@@ -1240,23 +1243,25 @@ cudaError_t launch_update_df(Launch& L, const float* Vf, size_t ldv, size_t pl, 
   return lp ? L.end(kr, 0.0, 0.0) : L.end(kr, 8.0 * nb, 1.0 * nb);
 }
 
-cudaError_t launch_split_scale(Launch& L, const double* src, float* out, size_t pl, size_t len, const double* nrm2) {
+cudaError_t launch_split_scale(Launch& L, const double* src, float* Vf, int nvt, float* vf, size_t len,
+                               const double* nrm2) {
   L.begin(KC_SCALE);
-  split_scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(src, out, pl, len, nrm2);
-  return L.end(KC_SCALE, 16.0 * len, 2.0 * len);
+  split_scale_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(src, Vf, nvt, vf, len, nrm2);
+  return L.end(KC_SCALE, 20.0 * len, 2.0 * len);
 }
 
-cudaError_t launch_scale_df(Launch& L, float* v, size_t pl, size_t len, const double* nrm2, const double* gate) {
+cudaError_t launch_scale_df(Launch& L, float* Vf, int nvt, int nv, float* vf, size_t len, const double* nrm2,
+                            const double* gate) {
   const int kc = gate ? KC_REORTH : KC_SCALE;
   L.begin(kc);
-  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(v, 2 * pl, pl, len, nrm2, gate, nullptr);
-  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 16.0 * len, 1.0 * len);
+  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(Vf, nvt, nv, vf, len, nrm2, gate, nullptr);
+  return gate ? L.end(kc, 0.0, 0.0) : L.end(kc, 20.0 * len, 1.0 * len);
 }
 
-cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
-                                   const double* w, size_t len, double* partial, double* out, double* ww,
-                                   const double* gate, double* err) {
-  if (nv_max < 1 || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
+cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, int nvt, int nv_max, const int* jdev, const double* w,
+                                   size_t len, double* partial, double* out, double* ww, const double* gate,
+                                   double* err) {
+  if (nv_max < 1 || nv_max >= nvt || nv_max > kChunk * kMaxChunks) return cudaErrorInvalidValue;
   if (len & 1) return cudaErrorInvalidValue;
   const bool lp = gate != nullptr;
   const int ld = nv_max + 1;
@@ -1267,7 +1272,7 @@ cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_
     cg = one_grid(nb);
     for (int i0 = 0; i0 < nv_max; i0 += kChunk) {
       L.begin(kc);
-      multidot_lp_dyn_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, i0, jdev, len, partial, ld, gate);
+      multidot_lp_dyn_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, nvt, i0, jdev, len, partial, ld, gate);
       cudaError_t e = L.end(kc, 0.0, 0.0);
       if (e != cudaSuccess) return e;
     }
@@ -1283,11 +1288,11 @@ cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_
     for (int c = 0; c < (nv_max + kChunk - 1) / kChunk; ++c) {
       L.begin(kc);
       if (c == 0 && ww)
-        multidot_df_dyn_kernel<true><<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, c, w, jdev, len, partial,
-                                                                            ld, S, stride, err);
+        multidot_df_dyn_kernel<true><<<nb, kStreamThreads, smem, L.stream>>>(Vf, nvt, c, w, jdev, len, partial, ld,
+                                                                            S, stride, err);
       else
-        multidot_df_dyn_kernel<false><<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, c, w, jdev, len, partial,
-                                                                             ld, S, stride, err);
+        multidot_df_dyn_kernel<false><<<nb, kStreamThreads, smem, L.stream>>>(Vf, nvt, c, w, jdev, len, partial, ld,
+                                                                             S, stride, err);
       e = L.end(kc, 0.0, 0.0);
       if (e != cudaSuccess) return e;
     }
@@ -1299,10 +1304,10 @@ cudaError_t launch_multidot_df_dev(Launch& L, const float* Vf, size_t ldv, size_
   return L.end(kc, 0.0, 0.0);
 }
 
-cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t pl, int nv_max, const int* jdev,
-                                 const double* coef, const double* w, size_t len, const double* scale,
-                                 double* partial, double* q, const double* gate, double* err) {
-  if (nv_max < 1 || nv_max > 1024) return cudaErrorInvalidValue;
+cudaError_t launch_update_df_dev(Launch& L, float* Vf, int nvt, int nv_max, const int* jdev, const double* coef,
+                                 const double* w, float* vf, size_t len, const double* scale, double* partial,
+                                 double* q, const double* gate, double* err) {
+  if (nv_max < 1 || nv_max >= nvt || nv_max > 1024) return cudaErrorInvalidValue;
   if (len & 1) return cudaErrorInvalidValue;
   const bool lp = gate != nullptr;
   const int kc = lp ? KC_REORTH : KC_UPDATE;
@@ -1311,15 +1316,15 @@ cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t 
   L.begin(kc);
   if (lp) {
     nb = wave_blocks(update_lp_kernel, 0, len);
-    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, ldv, pl, nv_max, coef, nullptr, len, partial, gate, jdev);
+    update_lp_kernel<<<nb, kThreads, 0, L.stream>>>(Vf, nvt, nv_max, coef, len, partial, gate, jdev);
   } else {
     const size_t stride = round128((size_t)2 * kGroup * kTile * 4 + (size_t)kTile * 8);
     const int S = stream_stages_for(stride);
     const size_t smem = kBarBytes + S * stride;
     if ((e = allow_smem(update_df_kernel, smem)) != cudaSuccess) return e;
     nb = stream_grid(len);
-    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, ldv, pl, nv_max, coef, w, nullptr, len, scale,
-                                                            partial, jdev, S, stride, err);
+    update_df_kernel<<<nb, kStreamThreads, smem, L.stream>>>(Vf, nvt, nv_max, coef, w, vf, len, scale, partial, jdev,
+                                                            S, stride, err);
   }
   e = L.end(kc, 0.0, 0.0);
   if (e != cudaSuccess) return e;
@@ -1328,10 +1333,10 @@ cudaError_t launch_update_df_dev(Launch& L, const float* Vf, size_t ldv, size_t 
   return L.end(kc, 0.0, 0.0);
 }
 
-cudaError_t launch_scale_df_dev(Launch& L, float* Vf, size_t ldv, size_t pl, const int* jdev, size_t len,
+cudaError_t launch_scale_df_dev(Launch& L, float* Vf, int nvt, const int* jdev, float* vf, size_t len,
                                 const double* nrm2, const double* gate) {
   L.begin(KC_REORTH);
-  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(Vf, ldv, pl, len, nrm2, gate, jdev);
+  scale_df_kernel<<<stream_blocks(len), kThreads, 0, L.stream>>>(Vf, nvt, 0, vf, len, nrm2, gate, jdev);
   return L.end(KC_REORTH, 0.0, 0.0);
 }
 
