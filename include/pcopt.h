@@ -439,6 +439,24 @@ int64_t pc_launch_count(const pc_handle* h);
  * `stream`; takes tens of milliseconds. */
 int pc_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
 
+/* Self-test of the bounded device waits (no paper counterpart): one CTA waits on
+ * an mbarrier phase that cannot complete (64 bytes announced, 32 copied), gives
+ * up after budget_ms (0 < budget_ms <= 10000) of SM clock, records the timeout
+ * and returns, as the streamed Arnoldi kernels do if a copy never arrives.
+ * Returns PC_ERR_TIMEOUT when the wait ran out as intended (the CUDA context stays
+ * usable); PC_ERR_CUDA on a CUDA error.  Allocates nothing.  Synchronises `stream`. */
+int pc_selftest_wait_timeout(double budget_ms, void* stream);
+
+/* Debug build only (compiled with -DPCOPT_DEBUG, libpcopt_debug.so; no paper
+ * counterpart): kernels check their index arithmetic (neighbour indices of the
+ * stencils, basis-vector and tile indices of the Krylov kernels, time and column
+ * indices of the time transforms), record the first failing check's code in a
+ * device word and skip the access instead of trapping.  *code = that code (0: no
+ * check failed; 1xx matvec, 2xx Krylov, 3xx time FFT); reset != 0 clears it.
+ * Returns PC_OK in the debug build, PC_ERR_UNSUPPORTED (and *code = 0) in the
+ * release build. */
+int pc_debug_status(int reset, int* code);
+
 /* Message of the calling thread's last error (never NULL). */
 const char* pc_last_error(void);
 const char* pc_status_string(int status);

@@ -14,6 +14,8 @@ import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpcopt.so")
+# the checked build (compiled with -DPCOPT_DEBUG); PCOPT_LIBRARY=debug selects it
+DEBUG_LIB_PATH = os.path.join(HERE, "libpcopt_debug.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pcopt.h")
 
 (PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_NOT_CONVERGED, PC_ERR_BREAKDOWN, PC_ERR_UNSUPPORTED,
@@ -94,6 +96,8 @@ _SIGNATURES = {
     "pc_stats_reset": (_i, [_vp]),
     "pc_launch_count": (ctypes.c_int64, [_vp]),
     "pc_measure_peaks": (_i, [_dpp, _dpp, _vp]),
+    "pc_selftest_wait_timeout": (_i, [_d, _vp]),
+    "pc_debug_status": (_i, [_i, _ip]),
     "pc_last_error": (ctypes.c_char_p, []),
     "pc_status_string": (ctypes.c_char_p, [_i]),
 }
@@ -112,7 +116,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (DEBUG_LIB_PATH if os.environ.get("PCOPT_LIBRARY") == "debug" else LIB_PATH)
     if not os.path.exists(p):
         raise RuntimeError(f"{p} not found: the CUDA library must be built (python -c 'import __graft_entry__ as g; g.build()')")
     lib = ctypes.CDLL(p)

@@ -1795,6 +1795,17 @@ extern "C" int pc_stats_reset(pc_handle* h) {
 
 extern "C" int64_t pc_launch_count(const pc_handle* h) { return h ? h->prof.total : 0; }
 
+extern "C" int pc_debug_status(int reset, int* code) {
+  if (!code) return fail(PC_ERR_ARG, "pc_debug_status: null code");
+  const int a = pcopt_debug_matvec(reset), b = pcopt_debug_krylov(reset), c = pcopt_debug_tfft(reset);
+  *code = a ? a : (b ? b : c);
+#ifdef PCOPT_DEBUG
+  return PC_OK;
+#else
+  return PC_ERR_UNSUPPORTED;  // release build: no checks compiled in, *code is 0
+#endif
+}
+
 extern "C" const char* pc_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* pc_status_string(int s) {

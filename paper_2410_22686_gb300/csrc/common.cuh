@@ -115,6 +115,39 @@ __device__ __forceinline__ void stc(double2* p, int64_t i, double2 v) { p[i] = v
 __device__ __forceinline__ void stc(__nv_bfloat162* p, int64_t i, float2 v) { p[i] = __float22bfloat162_rn(v); }
 
 // ---------------------------------------------------------------------------
+// Debug build (-DPCOPT_DEBUG): explicit checks of index arithmetic that record the
+// first failing check's code in a device word of the translation unit and let the
+// caller skip the access, instead of trapping.  In the release build PC_DOK(c, code)
+// is `true` and costs nothing.  Codes: 1xx matvec, 2xx Krylov, 3xx time FFT.
+// ---------------------------------------------------------------------------
+#ifdef PCOPT_DEBUG
+static __device__ int pcopt_dbg_err = 0;
+__device__ __forceinline__ bool pcopt_dok(bool ok, int code) {
+  if (!ok) atomicCAS(&pcopt_dbg_err, 0, code);
+  return ok;
+}
+#define PC_DOK(cond, code) (pcopt_dok((cond), (code)))
+#define PCOPT_DEBUG_READER(fn)                                                    \
+  int fn(int reset) {                                                             \
+    int v = 0;                                                                    \
+    if (cudaMemcpyFromSymbol(&v, pcopt_dbg_err, sizeof(int)) != cudaSuccess) v = -1; \
+    if (reset) {                                                                  \
+      const int z = 0;                                                            \
+      cudaMemcpyToSymbol(pcopt_dbg_err, &z, sizeof(int));                         \
+    }                                                                             \
+    return v;                                                                     \
+  }
+#else
+#define PC_DOK(cond, code) (true)
+#define PCOPT_DEBUG_READER(fn) \
+  int fn(int) { return 0; }
+#endif
+// per translation unit: the recorded code (0 none, -1 unreadable); reset clears it
+int pcopt_debug_matvec(int reset);
+int pcopt_debug_krylov(int reset);
+int pcopt_debug_tfft(int reset);
+
+// ---------------------------------------------------------------------------
 // kernel classes (instrumentation buckets)
 // ---------------------------------------------------------------------------
 enum KernelClass {

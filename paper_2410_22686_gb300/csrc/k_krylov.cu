@@ -681,6 +681,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) multidot_df_dyn_kernel(cons
                                                                             int S, size_t stage_stride, double* err) {
   const int nv = *jdev + 1;
   if (chunk >= (nv + kChunk - 1) / kChunk) return;
+  if (!PC_DOK(nv < nvt && (len & 1) == 0, 201)) return;  // vector nv and the tiles exist
   int i0, cnt;
   balanced_chunk(nv, chunk, &i0, &cnt);
   switch (cnt) {
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(float* Vf,
                                                                       const int* __restrict__ jdev, int S,
                                                                       size_t stage_stride, double* err) {
   if (jdev) nv = *jdev + 1;
+  if (!PC_DOK(nv >= 1 && nv < nvt && nv <= 1024 && (len & 1) == 0, 202)) return;
   __shared__ float2 cf[1024];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     float hi, lo;
@@ -842,6 +844,7 @@ __global__ void __launch_bounds__(kThreads) multidot_lp_dyn_kernel(const float* 
   if (gated_off(gate)) return;
   const int nv = *jdev + 1;
   if (i0 >= nv) return;
+  if (!PC_DOK(nv < nvt, 205)) return;
   const int cnt = nv - i0 < kChunk ? nv - i0 : kChunk;
   switch (cnt) {
 #define PCOPT_DYN(k) \
@@ -862,6 +865,7 @@ __global__ void __launch_bounds__(kThreads) update_lp_kernel(float* Vf, int nvt,
                                                              const int* __restrict__ jdev) {
   if (gated_off(gate)) return;
   if (jdev) nv = *jdev + 1;
+  if (!PC_DOK(nv >= 1 && nv < nvt && nv <= 1024, 203)) return;
   __shared__ float cf[1024];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cf[i] = (float)coef[i];
   __syncthreads();
@@ -916,6 +920,7 @@ __global__ void scale_df_kernel(float* Vf, int nvt, int nv, float* vf, size_t le
                                 const double* __restrict__ gate, const int* __restrict__ jdev) {
   if (gated_off(gate)) return;
   if (jdev) nv = *jdev + 1;
+  if (!PC_DOK(nv >= 0 && nv < nvt, 204)) return;
   if (!(nrm2[0] > 0.0)) return;
   float sh, sl;
   split_f64(1.0 / sqrt(nrm2[0]), sh, sl);
@@ -1453,5 +1458,7 @@ int num_sms() {
   }
   return cached;
 }
+
+PCOPT_DEBUG_READER(pcopt_debug_krylov)
 
 }  // namespace pcopt

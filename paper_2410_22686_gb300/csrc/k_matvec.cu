@@ -200,9 +200,11 @@ __global__ void __launch_bounds__(256) matvec_df_kernel(const float* __restrict_
   }
 #pragma unroll
   for (int k = 0; k < 2 * DIM; ++k) {
+    if (!PC_DOK(!ex[k] || (s + off[k] >= 0 && s + off[k] < ms), 101)) return;  // neighbour inside the grid
     const float2 c = w[(int64_t)k * ms + s];
     wv[k] = make_float2(-c.x, -c.y);  // off-diagonal entries of tau K are -w
   }
+  if (!PC_DOK(j1 <= n && j0 >= 0, 102)) return;
   const float2 d = dg[s];
   const float* x1 = x;
   const float* x2 = x + (int64_t)n * ms;
@@ -276,5 +278,7 @@ cudaError_t launch_matvec_df(Launch& L, const Grid& g, int n, const float2* w, c
     matvec_df_kernel<3><<<grid, threads, 0, L.stream>>>(x, y, w, diag, alpha, g.m, g.np, n, tj, xstride, ystride, jdev);
   return L.end(KC_MATVEC, jdev ? 0.0 : bytes, jdev ? 0.0 : U * (4.0 * g.dim + 5.0));
 }
+
+PCOPT_DEBUG_READER(pcopt_debug_matvec)
 
 }  // namespace pcopt

@@ -227,6 +227,7 @@ __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, 
   for (int j2 = 0; j2 < N2; ++j2) {
     const int j = r + N1 * j2;
     Tc a, b;
+    PC_DOK(j < n && c < COLS && (!valid || s < ms), 301);
     ld(j, a, b);
     x[j2] = cmk<Tc>(a * dinv[j], b * dpow[j]);
   }
@@ -914,5 +915,7 @@ PCOPT_INV(float, float2, float)
 PCOPT_INV(float, __nv_bfloat162, double)
 PCOPT_INV(float, __nv_bfloat162, float)
 #undef PCOPT_INV
+
+PCOPT_DEBUG_READER(pcopt_debug_tfft)
 
 }  // namespace pcopt

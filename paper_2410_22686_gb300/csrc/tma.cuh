@@ -70,11 +70,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // wait for the phase of `parity` to complete; false (and *err = code) after the budget
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, double* err, double code) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, double* err, double code,
+                                                  long long budget = kWaitBudgetCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudgetCycles) {
+    if (clock64() - t0 > budget) {
       if (err) *err = code;
       return false;
     }

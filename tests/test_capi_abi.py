@@ -88,3 +88,18 @@ def test_noalloc_gradient_rejects_bad_sizes_without_gpu():
         assert len(l.pc_last_error()) > 0
     assert l.pc_grad_log_a_noalloc(2, 7, 8, 1.0, nul, one, one, one, nul) == capi.PC_ERR_ARG
     assert b"null" in l.pc_last_error()
+
+
+def test_debug_build_compiles_and_exports_the_boundary():
+    """The checked build (-DPCOPT_DEBUG: index checks that record a code instead of
+    trapping) compiles for sm_103a and exports the same C ABI; the release build
+    answers pc_debug_status with PC_ERR_UNSUPPORTED and code 0 (no GPU needed)."""
+    path = pbuild.build(debug=True)
+    assert path.endswith("libpcopt_debug.so")
+    dbg = ctypes.CDLL(path)
+    for name in capi.header_functions():
+        assert hasattr(dbg, name), name
+    l = capi.load()
+    code = ctypes.c_int(-7)
+    assert l.pc_debug_status(0, ctypes.byref(code)) == capi.PC_ERR_UNSUPPORTED
+    assert code.value == 0

@@ -111,3 +111,24 @@ def test_arnoldi_mode_arguments():
         s64.set_arnoldi("fp16")
     s64.set_arnoldi("fp64-strict")
     s64.close()
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """A wait whose mbarrier phase cannot complete gives up after its budget and reports
+    PC_ERR_TIMEOUT; solves on the same context work afterwards."""
+    import time
+
+    from paper_2410_22686_gb300 import Solver, capi
+    lib = capi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    assert lib.pc_selftest_wait_timeout(50.0, stream) == capi.PC_ERR_TIMEOUT
+    assert b"ran out" in lib.pc_last_error()
+    assert time.perf_counter() - t0 >= 0.03
+    assert lib.pc_selftest_wait_timeout(0.0, stream) == capi.PC_ERR_ARG
+    prob = S.variable_2d_problem(gamma=1e-4, m1=31, n=32)
+    sol = Solver(2, 31, 32, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg", precision="fp32", max_iter=60)
+    b = sol.build_rhs(_dev(prob.f), _dev(prob.g), _dev(prob.y0))
+    _, it, rel = sol.solve(b, rtol=1e-8)
+    assert rel <= 1e-8 and it > 0
+    sol.close()
