@@ -426,6 +426,12 @@ typedef struct pc_kernel_stat {
 } pc_kernel_stat;
 
 int pc_profile(pc_handle* h, int on);
+/* Restrict the timing of pc_profile to the named kernel classes (comma-separated,
+ * as pc_stats names them, e.g. "arnoldi_dot,arnoldi_update_norm"; NULL or "" times
+ * every class).  Untimed classes still count launches, bytes and flops.  Fewer
+ * event pairs leave the timed work closer to an unprofiled run.  PC_ERR_ARG for an
+ * unknown name. */
+int pc_profile_classes(pc_handle* h, const char* names);
 int pc_stats(pc_handle* h, pc_kernel_stat* out, int cap, int* count);
 int pc_stats_reset(pc_handle* h);
 int64_t pc_launch_count(const pc_handle* h);

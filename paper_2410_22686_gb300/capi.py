@@ -94,6 +94,7 @@ _SIGNATURES = {
     "pc_profile": (_i, [_vp, _i]),
     "pc_stats": (_i, [_vp, ctypes.POINTER(pc_kernel_stat), _i, _ip]),
     "pc_stats_reset": (_i, [_vp]),
+    "pc_profile_classes": (_i, [_vp, ctypes.c_char_p]),
     "pc_launch_count": (ctypes.c_int64, [_vp]),
     "pc_measure_peaks": (_i, [_dpp, _dpp, _vp]),
     "pc_selftest_wait_timeout": (_i, [_d, _vp]),

@@ -57,9 +57,8 @@ const char* kernel_class_name(int kc) {
 }
 
 void Launch::begin(int kc) {
-  (void)kc;
   ev_a = nullptr;
-  if (prof && prof->on) {
+  if (prof && prof->on && (prof->mask >> kc & 1ull)) {
     if (prof->pool.empty()) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) == cudaSuccess) prof->pool.push_back(e);
@@ -229,6 +228,7 @@ struct pc_handle {
   int* idx = nullptr;                 // device: [0] Arnoldi index j, [1] iterations done k
   cudaStream_t cap_stream = nullptr;  // capture streams (a batch captures each problem on its own)
   cudaStream_t aux_stream = nullptr;
+  cudaEvent_t scal_ev = nullptr;      // marks the copy of the per-iteration scalars
   cudaGraphExec_t gexec = nullptr;    // single-problem solve graph and what it was built for
   const double* g_b = nullptr;
   double* g_x = nullptr;
@@ -254,6 +254,8 @@ static int dev_alloc_t(pc_handle* h, T** p, size_t count) {
 static void release(pc_handle* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   h->gexec = nullptr;
+  if (h->scal_ev) cudaEventDestroy(h->scal_ev);
+  h->scal_ev = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   h->cap_stream = h->aux_stream = nullptr;
@@ -700,6 +702,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     }
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->scal_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "pc_setup");
@@ -1230,6 +1233,27 @@ static int read_scalars(pc_handle* h, cudaStream_t st, double* est, double* ref,
   return PC_OK;
 }
 
+// the same scalars as read_scalars, in two halves: post_scalars queues their copy into
+// mapped host memory and records the handle's event; take_scalars waits for that event
+// only (work queued after it keeps running) and reads them
+static int post_scalars(pc_handle* h, cudaStream_t st) {
+  Launch L{st, &h->prof, &h->tiles};
+  L.begin(KC_REDUCE);
+  to_mapped_kernel<<<1, 32, 0, st>>>(h->scal + 1, 10, nullptr, h->host_dev);
+  PC_CUDA(L.end(KC_REDUCE, 80.0, 0.0));
+  PC_CUDA(cudaEventRecord(h->scal_ev, st));
+  return PC_OK;
+}
+
+static int take_scalars(pc_handle* h, double* est, double* ref, bool* reorth) {
+  PC_CUDA(cudaEventSynchronize(h->scal_ev));
+  if (h->host[9] != 0.0) return fail(PC_ERR_TIMEOUT, "a bounded device wait ran out (streamed basis copy)");
+  if (est) *est = h->host[0];
+  if (ref) *ref = h->host[1];
+  if (reorth) *reorth = h->host[8] != 0.0;
+  return PC_OK;
+}
+
 static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int maxit, int mode, int* iters,
                       double* relres, cudaStream_t st) {
   if (!h || !b || !x) return fail(PC_ERR_ARG, "gmres: null argument");
@@ -1324,17 +1348,42 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
   else
     GM_CUDA(launch_scale_by_inv_norm(L, V, U, nrm2, nullptr, vf));
 
-  int k = 0;
-  bool converged = false;
-  for (int j = 0; j < maxit; ++j) {
+  // Iteration j = front (z_j = P^{-1} v_j and w = A z_j, or the left-preconditioned
+  // pair; it needs only v_j) + back (Arnoldi passes, Givens, the estimate copied to
+  // mapped host memory behind an event, which the host waits for).  Queuing the next
+  // front before that wait was tried: the GPU never idled long enough for it to pay
+  // (0.0852 vs 0.0849 s per solve at 255^2 x 256), so the next front waits for the decision.
+  auto front = [&](int j) -> cudaError_t {
     double* vj = V + (size_t)j * U;
     double* vn = V + (size_t)(j + 1) * U;
+    cudaError_t e2;
     if (df) {
       // double-float basis: the preconditioner reads the FP32 rounding of v_j (vf32),
-      // A z_j goes to wbuf (FP64), the update writes v_{j+1} and its FP32 rounding
+      // A z_j goes to wbuf (FP64)
       float* zj = (float*)h->Z + (size_t)j * U;
-      GM_CUDA(precond32<float, float>(h, L, vf, zj));
-      GM_CUDA(matvec_basis(h, L, zj, h->wbuf));
+      if ((e2 = precond32<float, float>(h, L, vf, zj)) != cudaSuccess) return e2;
+      return matvec_basis(h, L, zj, h->wbuf);
+    }
+    if (mode == PC_GMRES_RIGHT) {
+      if (h->fp32) {
+        float* zj = (float*)h->Z + (size_t)j * U;
+        if ((e2 = precond32<float, float>(h, L, vf, zj)) != cudaSuccess) return e2;
+        return matvec_basis(h, L, zj, vn);
+      }
+      double* zj = (double*)h->Z + (size_t)j * U;
+      if ((e2 = precond_t<double, double2, double>(h, L, vj, zj)) != cudaSuccess) return e2;
+      return matvec_any(h, L, zj, false, vn, false);
+    }
+    if ((e2 = matvec_any(h, L, vj, false, h->wbuf, false)) != cudaSuccess) return e2;
+    return precond64(h, L, h->wbuf, vn);
+  };
+  int k = 0;
+  bool converged = false;
+  GM_CUDA(front(0));
+  for (int j = 0; j < maxit; ++j) {
+    double* vn = V + (size_t)(j + 1) * U;
+    if (df) {
+      // the update writes v_{j+1} and its FP32 rounding
       GM_CUDA(launch_multidot_df(L, Vf, nvt, j + 1, h->wbuf, U, h->partial, h->hcol, AS.ww, nullptr, werr));
       GM_CUDA(launch_arnoldi_prep(L, j + 1, h->hcol, AS));
       GM_CUDA(launch_update_df(L, Vf, nvt, j + 1, h->hcol, h->wbuf, vf, U, AS.inv, h->partial, AS.q, nullptr, werr));
@@ -1343,21 +1392,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       GM_CUDA(launch_update_df(L, Vf, nvt, j + 1, h->hcol + ldh, nullptr, vf, U, nullptr, h->partial, AS.rho2,
                                AS.flag, werr));
       GM_CUDA(launch_scale_df(L, Vf, nvt, j + 1, vf, U, AS.rho2, AS.flag));
-    } else if (mode == PC_GMRES_RIGHT) {
-      if (h->fp32) {
-        float* zj = (float*)h->Z + (size_t)j * U;
-        GM_CUDA(precond32<float, float>(h, L, vf, zj));
-        GM_CUDA(matvec_basis(h, L, zj, vn));
-      } else {
-        double* zj = (double*)h->Z + (size_t)j * U;
-        GM_CUDA(precond_t<double, double2, double>(h, L, vj, zj));
-        GM_CUDA(matvec_any(h, L, zj, false, vn, false));
-      }
     } else {
-      GM_CUDA(matvec_any(h, L, vj, false, h->wbuf, false));
-      GM_CUDA(precond64(h, L, h->wbuf, vn));
-    }
-    if (!df) {
       // classical Gram-Schmidt with Pythagorean normalisation, re-orthogonalised only
       // when the check flags cancellation (the gated kernels then do the work)
       GM_CUDA(launch_multidot(L, V, U, j + 1, vn, U, h->partial, h->hcol, AS.ww, nullptr));
@@ -1370,8 +1405,9 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       GM_CUDA(launch_scale_by_inv_norm(L, vn, U, AS.rho2, AS.flag, vf));
     }
     GM_CUDA(launch_givens(L, j, ldh, h->H, h->cs, h->sn, h->gvec, h->hcol, h->hcol + ldh, AS, est, ref));
+    if (int rc = post_scalars(h, st)) return rc;
     bool reorth = false;
-    if (int rc = read_scalars(h, st, &est_h, nullptr, &reorth)) return rc;
+    if (int rc = take_scalars(h, &est_h, nullptr, &reorth)) return rc;
     if (reorth) {  // book the second Gram-Schmidt pass that ran
       // double-float basis: hi planes read twice (4 B each), the new vector's planes read
       // three times and written twice; FP64 basis: 8 B per basis read, 6 vector passes
@@ -1386,6 +1422,7 @@ static int gmres_impl(pc_handle* h, const double* b, double* x, double rtol, int
       converged = true;
       break;
     }
+    if (j + 1 < maxit) GM_CUDA(front(j + 1));
   }
   GM_CUDA(launch_backsolve(L, k, ldh, h->H, h->gvec, h->ycoef));
   if (mode == PC_GMRES_RIGHT) {
@@ -1764,6 +1801,30 @@ extern "C" int pc_batch_destroy(pc_batch* bt) {
 extern "C" int pc_profile(pc_handle* h, int on) {
   if (!h) return fail(PC_ERR_ARG, "null handle");
   h->prof.on = on != 0;
+  return PC_OK;
+}
+
+extern "C" int pc_profile_classes(pc_handle* h, const char* names) {
+  if (!h) return fail(PC_ERR_ARG, "null handle");
+  if (!names || !*names) {
+    h->prof.mask = ~0ull;
+    return PC_OK;
+  }
+  uint64_t mask = 0;
+  std::string list(names);
+  size_t pos = 0;
+  while (pos <= list.size()) {
+    size_t end = list.find(',', pos);
+    if (end == std::string::npos) end = list.size();
+    const std::string nm = list.substr(pos, end - pos);
+    int found = -1;
+    for (int kc = 0; kc < KC_COUNT; ++kc)
+      if (nm == kernel_class_name(kc)) found = kc;
+    if (found < 0) return fail(PC_ERR_ARG, "pc_profile_classes: unknown kernel class '" + nm + "'");
+    mask |= 1ull << found;
+    pos = end + 1;
+  }
+  h->prof.mask = mask;
   return PC_OK;
 }
 

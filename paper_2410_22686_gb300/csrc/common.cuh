@@ -183,6 +183,7 @@ const char* kernel_class_name(int kc);
 // ---------------------------------------------------------------------------
 struct Prof {
   bool on = false;
+  uint64_t mask = ~0ull;  // kernel classes timed while on (bit kc)
   int64_t launches[KC_COUNT] = {0};
   double bytes[KC_COUNT] = {0};
   double flops[KC_COUNT] = {0};

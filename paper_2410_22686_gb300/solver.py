@@ -314,7 +314,10 @@ class Solver:
         return {f: getattr(t, f) for f, _ in capi.pc_tiles._fields_}
 
     # ---------------------------------------------------------------- instrumentation
-    def profile(self, on=True):
+    def profile(self, on=True, classes=None):
+        """Time kernels with CUDA events (pc_profile); classes: names of the kernel classes
+        to time (pc_profile_classes), None for all."""
+        capi.check(self.lib.pc_profile_classes(self.h, ",".join(classes).encode() if classes else None))
         capi.check(self.lib.pc_profile(self.h, 1 if on else 0))
 
     def stats(self):

@@ -49,14 +49,15 @@ class FakeSolver:
     def stats_reset(self):
         self.launches = 0
 
-    def profile(self, on=True):
+    def profile(self, on=True, classes=None):
         pass
 
     def launch_count(self):
         return self.launches
 
     def stats(self):
-        return {"arnoldi_dot": {"launches": 7, "ms": 1.0, "bytes": 8.0e9, "flops": 1.0e9}}
+        return {"arnoldi_dot": {"launches": 7, "ms": 1.0, "bytes": 8.0e9, "flops": 1.0e9},
+                "arnoldi_update_norm": {"launches": 7, "ms": 0.5, "bytes": 8.0e9, "flops": 1.0e9}}
 
     def residual_history(self):
         return [1.0, 1e-9]
