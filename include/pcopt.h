@@ -64,8 +64,14 @@ typedef enum pc_spatial {
 typedef enum pc_precision {
   PC_PREC_FP64 = 0,         /* preconditioner in FP64 */
   PC_PREC_MIXED_FP32 = 1,   /* preconditioner in FP32 (flexible GMRES keeps FP64 outside) */
-  PC_PREC_MIXED_BF16S = 2   /* as FP32, multigrid smoother iterates stored as BF16 */
+  PC_PREC_MIXED_BF16S = 2,  /* as FP32, multigrid smoother iterates stored as BF16 */
+  PC_PREC_AUTO = 3          /* FP32 when eps >= PC_AUTO_FP32_MIN_EPS, else FP64: the time
+                               scaling D = diag(eps^{j/n}) amplifies the FP32 rounding of the
+                               apply by up to 1/eps, and below this eps (e.g. the paper's
+                               eps = tau/2) the FP32 preconditioner needs several times the
+                               FP64 iterations; pc_precision_of reports the choice */
 } pc_precision;
+#define PC_AUTO_FP32_MIN_EPS 1e-2
 
 typedef enum pc_gmres_mode {
   PC_GMRES_RIGHT = 0,  /* flexible GMRES, right preconditioning, stops on ||b-Ax||/||b|| */
@@ -151,6 +157,10 @@ typedef struct pc_handle pc_handle;
  * MG with m1 != 2^k-1, unknown space), PC_ERR_UNSUPPORTED (finite elements with a
  * non-constant a or multigrid), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
+
+/* The precision a handle resolved to (PC_PREC_FP64, PC_PREC_MIXED_FP32 or
+ * PC_PREC_MIXED_BF16S; PC_PREC_AUTO is resolved at setup). */
+int pc_precision_of(const pc_handle* h, int* precision);
 
 /* Replace the coefficient a(x) of an existing handle without reallocating:
  * the stencil of every level (and the FST eigenvalues) is recomputed on the

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pcopt.h")
 (PC_OK, PC_ERR_ARG, PC_ERR_CUDA, PC_ERR_OOM, PC_ERR_NOT_CONVERGED, PC_ERR_BREAKDOWN, PC_ERR_UNSUPPORTED,
  PC_ERR_TIMEOUT) = range(8)
 PC_SPATIAL_AUTO, PC_SPATIAL_FST, PC_SPATIAL_MG = 0, 1, 2
-PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S = 0, 1, 2
+PC_PREC_FP64, PC_PREC_MIXED_FP32, PC_PREC_MIXED_BF16S, PC_PREC_AUTO = 0, 1, 2, 3
 PC_GMRES_RIGHT, PC_GMRES_LEFT = 0, 1
 PC_SPACE_FD, PC_SPACE_FE = 0, 1
 PC_SMOOTHER_RED_BLACK, PC_SMOOTHER_LEXICOGRAPHIC = 0, 1
@@ -87,6 +87,7 @@ _SIGNATURES = {
     "pc_objective": (_i, [_vp, _dp, _dp, _dp, _vp]),
     "pc_objective_grad": (_i, [_vp, _dp, _dp, _dp, _dp, _dp, _vp]),
     "pc_sizes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "pc_precision_of": (_i, [_vp, _ip]),
     "pc_end_point_solves": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, _i, _ip, _vp]),
     "pc_get_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),
     "pc_set_tiles": (_i, [_vp, ctypes.POINTER(pc_tiles)]),

@@ -456,7 +456,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   if (!(p->T > 0) || !std::isfinite(p->T)) return fail(PC_ERR_ARG, "T must be finite and > 0");
   if (!(p->gamma > 0) || !std::isfinite(p->gamma)) return fail(PC_ERR_ARG, "gamma must be finite and > 0");
   if (!(p->eps > 0) || !(p->eps <= 1.0)) return fail(PC_ERR_ARG, "eps must lie in (0, 1]");
-  if (p->precision != PC_PREC_FP64 && p->precision != PC_PREC_MIXED_FP32 && p->precision != PC_PREC_MIXED_BF16S)
+  if (p->precision != PC_PREC_FP64 && p->precision != PC_PREC_MIXED_FP32 && p->precision != PC_PREC_MIXED_BF16S &&
+      p->precision != PC_PREC_AUTO)
     return fail(PC_ERR_ARG, "unknown precision");
   if (p->spatial < 0 || p->spatial > 2) return fail(PC_ERR_ARG, "unknown spatial solver");
   if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
@@ -501,8 +502,11 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->sqrtg = std::sqrt(p->gamma);
   h->h = 1.0 / (m1 + 1);
   h->spatial = spatial;
-  h->fp32 = p->precision != PC_PREC_FP64;
-  h->bf16s = p->precision == PC_PREC_MIXED_BF16S && spatial == PC_SPATIAL_MG;
+  const int prec = p->precision == PC_PREC_AUTO ? (p->eps >= PC_AUTO_FP32_MIN_EPS ? PC_PREC_MIXED_FP32 : PC_PREC_FP64)
+                                                : p->precision;
+  h->prm.precision = prec;
+  h->fp32 = prec != PC_PREC_FP64;
+  h->bf16s = prec == PC_PREC_MIXED_BF16S && spatial == PC_SPATIAL_MG;
   h->cap = p->max_iter;
   h->a_const = a[0];
   h->fe = fe;
@@ -826,6 +830,12 @@ extern "C" int pc_destroy(pc_handle* h) {
   cudaDeviceSynchronize();
   release(h);
   delete h;
+  return PC_OK;
+}
+
+extern "C" int pc_precision_of(const pc_handle* h, int* precision) {
+  if (!h || !precision) return fail(PC_ERR_ARG, "pc_precision_of: null argument");
+  *precision = h->prm.precision;
   return PC_OK;
 }
 

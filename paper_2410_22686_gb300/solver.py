@@ -15,7 +15,8 @@ from . import capi, tuning
 
 _SPATIAL = {"auto": capi.PC_SPATIAL_AUTO, "fst": capi.PC_SPATIAL_FST, "mg": capi.PC_SPATIAL_MG}
 _PREC = {"fp64": capi.PC_PREC_FP64, "fp32": capi.PC_PREC_MIXED_FP32, "mixed": capi.PC_PREC_MIXED_FP32,
-         "bf16s": capi.PC_PREC_MIXED_BF16S}
+         "bf16s": capi.PC_PREC_MIXED_BF16S, "auto": capi.PC_PREC_AUTO}
+_PREC_NAME = {capi.PC_PREC_FP64: "fp64", capi.PC_PREC_MIXED_FP32: "fp32", capi.PC_PREC_MIXED_BF16S: "bf16s"}
 _MODE = {"right": capi.PC_GMRES_RIGHT, "left": capi.PC_GMRES_LEFT}
 _SPACE = {"fd": capi.PC_SPACE_FD, "fe": capi.PC_SPACE_FE}
 _SMOOTHER = {"red-black": capi.PC_SMOOTHER_RED_BLACK, "lexicographic": capi.PC_SMOOTHER_LEXICOGRAPHIC}
@@ -76,11 +77,13 @@ class Solver:
         self.ms = m1 ** dim
         self.vec_len = 2 * n * self.ms
         self.tau = T / (n + 1)
-        self.precision = precision
+        resolved = ctypes.c_int(0)
+        capi.check(self.lib.pc_precision_of(self.h, ctypes.byref(resolved)))
+        self.precision = _PREC_NAME[resolved.value]  # "auto" resolved by eps (pc_precision)
         self.spatial = spatial
         self.space = space
         if tiles == "table":
-            entry = tuning.lookup(dim, m1, n, precision, spatial) if space == "fd" else None
+            entry = tuning.lookup(dim, m1, n, self.precision, spatial) if space == "fd" else None
             if entry:
                 self.set_tiles(**entry)
         elif tiles == "auto":

@@ -132,3 +132,17 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable():
     _, it, rel = sol.solve(b, rtol=1e-8)
     assert rel <= 1e-8 and it > 0
     sol.close()
+
+
+def test_auto_precision_follows_eps():
+    """precision="auto": the FP32 preconditioner for eps >= 1e-2 (the benchmark's
+    eps = sqrt(tau)), FP64 below (the paper's eps = tau/2, where the FP32 apply's rounding,
+    amplified by 1/eps through D = diag(eps^{j/n}), costs several times the iterations)."""
+    from paper_2410_22686_gb300 import Solver
+    m1, n = 7, 256
+    tau = 1.0 / (n + 1)  # sqrt(tau) = 0.062, tau / 2 = 0.0019
+    s1 = Solver(2, m1, n, 1.0, 1e-4, tau ** 0.5, None, spatial="fst", precision="auto")
+    s2 = Solver(2, m1, n, 1.0, 1e-4, tau / 2, None, spatial="fst", precision="auto")
+    assert s1.precision == "fp32" and s2.precision == "fp64"
+    s1.close()
+    s2.close()
