@@ -749,14 +749,21 @@ __global__ void __launch_bounds__(kStreamThreads, 1) update_df_kernel(float* Vf,
       bh[0] = bl[0] = bh[1] = bl[1] = 0.0f;
     }
     int c = 0;
-    for (; c + 1 < cnt; c += 2) {
-      const float2 c0 = cf[i0 + c], c1 = cf[i0 + c + 1];
-      const float2 h0 = sv[(2 * c) * (kTile / 2) + threadIdx.x], l0 = sv[(2 * c + 1) * (kTile / 2) + threadIdx.x];
-      const float2 h1 = sv[(2 * c + 2) * (kTile / 2) + threadIdx.x], l1 = sv[(2 * c + 3) * (kTile / 2) + threadIdx.x];
+    auto pair = [&](int cc) {
+      const float2 c0 = cf[i0 + cc], c1 = cf[i0 + cc + 1];
+      const float2 h0 = sv[(2 * cc) * (kTile / 2) + threadIdx.x], l0 = sv[(2 * cc + 1) * (kTile / 2) + threadIdx.x];
+      const float2 h1 = sv[(2 * cc + 2) * (kTile / 2) + threadIdx.x], l1 = sv[(2 * cc + 3) * (kTile / 2) + threadIdx.x];
       df_sub_prod(c0.x, c0.y, h0.x, l0.x, ah[0], al[0]);
       df_sub_prod(c0.x, c0.y, h0.y, l0.y, ah[1], al[1]);
       df_sub_prod(c1.x, c1.y, h1.x, l1.x, bh[0], bl[0]);
       df_sub_prod(c1.x, c1.y, h1.y, l1.y, bh[1], bl[1]);
+    };
+    if (cnt == kGroup) {  // a full group: unrolled, so the shared loads run ahead of the sums
+#pragma unroll
+      for (int cc = 0; cc < kGroup; cc += 2) pair(cc);
+      c = kGroup;
+    } else {
+      for (; c + 1 < cnt; c += 2) pair(c);
     }
     if (c < cnt) {
       const float2 c0 = cf[i0 + c];
