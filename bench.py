@@ -820,10 +820,10 @@ def run_ours(args):
     # DRAM bytes (read + write) over algorithmic bytes of one launch, from an ncu
     # capture of the double-float Arnoldi kernels (tiled basis, bulk-copy streams) of
     # the mixed solve at 255^2 x 128: multi-dot over a chunk of 9 basis vectors
-    # 1331.8 + 4.0 MB for 1326.4 MB, update over 17 vectors 2397.2 + 195.7 MB for
+    # 1331.8 + 4.0 MB for 1326.4 MB, update over 17 vectors 2397.2 + 195.6 MB for
     # 2586.4 MB; a full-size launch moves the same bytes per unknown, so the traffic of
     # the average timed launch is this ratio times its algorithmic bytes
-    ncu_traffic_ratio = {"arnoldi_dot": (1331.8 + 4.0) / 1326.4, "arnoldi_update_norm": (2397.2 + 195.7) / 2586.4}
+    ncu_traffic_ratio = {"arnoldi_dot": (1331.8 + 4.0) / 1326.4, "arnoldi_update_norm": (2397.2 + 195.6) / 2586.4}
     tot_ms = sum(v["ms"] for v in all_stats.values())
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])  # among the classes timed in the region
     peaks, peak_src = {}, "fallback 6.8 TB/s (of fallback)"

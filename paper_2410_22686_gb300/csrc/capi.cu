@@ -573,8 +573,9 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       const float ah = (float)h->alpha;
       h->alpha_df = make_float2(ah, (float)(h->alpha - (double)ah));
     }
-    // the fused coarse cycle takes every level from the first with m <= 31 (2D) / 15 (3D)
-    const int mthr = dim == 2 ? 31 : 15;
+    // the fused lower cycle takes every level from the first with m <= 63 (2D, FP32 or
+    // FP64 iterates: one in-place array per level), 31 (2D, BF16 storage) or 15 (3D)
+    const int mthr = dim == 2 ? (h->bf16s ? 31 : kMgTailMaxM) : 15;
     int l0 = (int)h->lv.size() - 1;
     while (l0 > 0 && h->lv[l0 - 1].m <= mthr) --l0;
     if ((int)h->lv.size() - l0 > kMaxCoarseLevels) l0 = (int)h->lv.size() - kMaxCoarseLevels;
@@ -995,9 +996,17 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
   }
   {
     const CoarseLevels<Tc>& cl = coarse_of<Tc>(h);
-    if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r, (TU*)h->lv[l0].u)) !=
-        cudaSuccess)
+    if constexpr (std::is_same<TU, C>::value) {
+      if (h->dim == 2) {
+        if ((e = launch_mg_tail2<Tc>(L, P, cl, sig, (const C*)h->lv[l0].r, (C*)h->lv[l0].u)) != cudaSuccess) return e;
+      } else if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r,
+                                                     (TU*)h->lv[l0].u)) != cudaSuccess) {
+        return e;
+      }
+    } else if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r,
+                                                   (TU*)h->lv[l0].u)) != cudaSuccess) {
       return e;
+    }
   }
   // in 2D the finest level's correction is added by the inverse time transform
   // (fine_correction); in 3D (eight coarse parents per point) by the prolongation kernel

@@ -27,7 +27,8 @@ SHAPES = [dict(mg_cx=8, mg_ctas=2, mv_tj=8, pro_pch=2, fft_stream=1, mg_march=0,
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5), ("bf16s", 3e-2)])
-@pytest.mark.parametrize("d,m1,n", [(2, 63, 16), (2, 127, 8), (3, 15, 8), (2, 31, 256), (2, 15, 512)])
+@pytest.mark.parametrize("d,m1,n", [(2, 63, 16), (2, 127, 8), (3, 15, 8), (2, 31, 256), (2, 15, 512), (2, 31, 128),
+                                    (2, 7, 1024)])
 def test_precond_and_matvec_match_oracle_for_every_tile_shape(precision, tol, d, m1, n):
     from paper_2410_22686_gb300 import Solver
     a = np.exp(0.4 * S.random_vector((m1 + 2,) * d, 5))
@@ -66,7 +67,9 @@ def test_invalid_tile_shapes_are_rejected():
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_autotune_picks_valid_shapes_and_keeps_the_solution(precision):
     from paper_2410_22686_gb300 import Solver
-    prob = S.variable_2d_problem(gamma=1e-4, m1=63, n=32)
+    # 127^2: one fine level with a fused down leg (the levels from 63^2 down run in
+    # one kernel), so the down-leg shape is tuned
+    prob = S.variable_2d_problem(gamma=1e-4, m1=127, n=32)
     sol = Solver(2, prob.m1, prob.n, prob.T, prob.gamma, prob.eps, prob.a_nodes, spatial="mg",
                  precision=precision, max_iter=60, tiles=None)
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -75,7 +78,7 @@ def test_autotune_picks_valid_shapes_and_keeps_the_solution(precision):
     t = sol.autotune(reps=2)
     assert t["mg_cx"] in (8, 16) and 1 <= t["mg_ctas"] <= 64
     # pro_pch stays 0 (default) when the handle launches no prolongation kernel:
-    # at 63^2 the only fine level's correction is fused into the inverse FFT
+    # at 127^2 the only fine level's correction is fused into the inverse FFT
     assert 1 <= t["mv_tj"] <= 4096 and 0 <= t["pro_pch"] <= 64 and t["fft_stream"] in (0, 1)
     assert sol.get_tiles() == t
     x1, it1, rr1 = sol.solve(b, rtol=1e-8)
