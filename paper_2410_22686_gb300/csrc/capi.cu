@@ -165,6 +165,7 @@ struct pc_handle {
 
   std::vector<LevelBuf> lv;
   int coarse_l0 = 0;                 // first level run by the fused coarse-cycle kernel
+  bool tail2 = false;                // 2D FP32 iterates: that kernel is mg_tail2 (from 63^2)
   Tiles tiles;                       // tile shapes of the tunable kernels (0 = default)
   float2* wdf = nullptr;             // level-0 face weights and diagonal as (hi, lo) float pairs
   float2* ddf = nullptr;
@@ -573,9 +574,13 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       const float ah = (float)h->alpha;
       h->alpha_df = make_float2(ah, (float)(h->alpha - (double)ah));
     }
-    // the fused lower cycle takes every level from the first with m <= 63 (2D, FP32 or
-    // FP64 iterates: one in-place array per level), 31 (2D, BF16 storage) or 15 (3D)
-    const int mthr = dim == 2 ? (h->bf16s ? 31 : kMgTailMaxM) : 15;
+    // the fused lower cycle takes every level from the first with m <= 63 (2D, FP32
+    // iterates: one in-place array per level), 31 (2D, FP64 iterates or BF16 storage)
+    // or 15 (3D).  (The in-place kernel also runs FP64 iterates, but one CTA of 133 KB
+    // per plane made the ideal preconditioner's two-plane steps slower: 29.6 -> 34.8
+    // ms per apply at 255^2 x 256.)
+    h->tail2 = dim == 2 && h->fp32 && !h->bf16s;
+    const int mthr = h->tail2 ? kMgTailMaxM : (dim == 2 ? 31 : 15);
     int l0 = (int)h->lv.size() - 1;
     while (l0 > 0 && h->lv[l0 - 1].m <= mthr) --l0;
     if ((int)h->lv.size() - l0 > kMaxCoarseLevels) l0 = (int)h->lv.size() - kMaxCoarseLevels;
@@ -996,17 +1001,16 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
   }
   {
     const CoarseLevels<Tc>& cl = coarse_of<Tc>(h);
-    if constexpr (std::is_same<TU, C>::value) {
-      if (h->dim == 2) {
-        if ((e = launch_mg_tail2<Tc>(L, P, cl, sig, (const C*)h->lv[l0].r, (C*)h->lv[l0].u)) != cudaSuccess) return e;
-      } else if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r,
-                                                     (TU*)h->lv[l0].u)) != cudaSuccess) {
-        return e;
+    bool done = false;
+    if constexpr (std::is_same<Tc, float>::value && std::is_same<TU, float2>::value) {
+      if (h->tail2) {
+        if ((e = launch_mg_tail2(L, P, cl, sig, (const C*)h->lv[l0].r, (C*)h->lv[l0].u)) != cudaSuccess) return e;
+        done = true;
       }
-    } else if ((e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r,
-                                                   (TU*)h->lv[l0].u)) != cudaSuccess) {
-      return e;
     }
+    if (!done && (e = launch_mg_coarse_cycle<Tc, TU>(L, h->dim, P, cl, sig, (const C*)h->lv[l0].r,
+                                                     (TU*)h->lv[l0].u)) != cudaSuccess)
+      return e;
   }
   // in 2D the finest level's correction is added by the inverse time transform
   // (fine_correction); in 3D (eight coarse parents per point) by the prolongation kernel

@@ -358,14 +358,12 @@ struct CoarseLevels {
   const T* w[kMaxCoarseLevels];
   const T* diag[kMaxCoarseLevels];
 };
-// 2D FP32 / FP64 iterates: the lower part of the cycle from the first level with
+// 2D FP32 iterates: the lower part of the cycle from the first level with
 // m <= kMgTailMaxM, one array per level updated in place (k_mgtail.cu)
 constexpr int kMgTailMaxM = 63;
-template <typename Tc>
-bool mg_tail2_supported(const CoarseLevels<Tc>& lv);
-template <typename Tc>
-cudaError_t launch_mg_tail2(Launch& L, int planes, const CoarseLevels<Tc>& lv, const typename Cx<Tc>::t* sigma,
-                            const typename Cx<Tc>::t* r0, typename Cx<Tc>::t* u0);
+bool mg_tail2_supported(const CoarseLevels<float>& lv);
+cudaError_t launch_mg_tail2(Launch& L, int planes, const CoarseLevels<float>& lv, const float2* sigma, const float2* r0,
+                            float2* u0);
 template <typename Tc, typename TU>
 size_t mg_coarse_cycle_smem(const CoarseLevels<Tc>& lv);
 template <typename Tc, typename TU>

@@ -1,6 +1,8 @@
 // Lower part of the 2D V(1,0) cycle (Section 2.1, step 2 of the apply of
 // P_eps^{-1}, variable a) in one launch: from the first level with at most 63^2
-// points down to the one-point level and back, for FP32 or FP64 iterates.
+// points down to the one-point level and back, for FP32 iterates (FP64 handles keep
+// the coarse-cycle kernel from 31^2: with FP64 values a plane needs one 133 KB CTA,
+// which made the two-plane steps of the ideal preconditioner slower).
 //
 // One CTA owns one spectral plane and keeps ONE array per level in shared memory,
 // updated in place:
@@ -44,7 +46,6 @@ __device__ __forceinline__ float2 tail_inv(float2 sig, float d) {
   const float q = __fdividef(1.0f, fmaf(a, a, sig.y * sig.y));
   return make_float2(a * q, -sig.y * q);
 }
-__device__ __forceinline__ double2 tail_inv(double2 sig, double d) { return inv_diag<double>(sig, d); }
 
 template <typename C, typename T>
 __device__ __forceinline__ void tail_fma(C& acc, T w, C v) {
@@ -292,8 +293,7 @@ size_t tail_coef_smem(const CoarseLevels<Tc>& lv, int from) {
 }  // namespace
 
 // levels it takes: 2D, odd m halving down to one point, first level at most 63^2
-template <typename Tc>
-bool mg_tail2_supported(const CoarseLevels<Tc>& lv) {
+bool mg_tail2_supported(const CoarseLevels<float>& lv) {
   if (lv.count < 1 || lv.count > kMaxCoarseLevels || lv.m[0] > kMgTailMaxM) return false;
   for (int l = 0; l < lv.count; ++l) {
     if (lv.m[l] < 1 || (lv.m[l] & 1) == 0 || lv.np[l] != (int64_t)lv.m[l] * lv.m[l]) return false;
@@ -302,10 +302,10 @@ bool mg_tail2_supported(const CoarseLevels<Tc>& lv) {
   return lv.m[lv.count - 1] == 1;
 }
 
-template <typename Tc>
-cudaError_t launch_mg_tail2(Launch& L, int planes, const CoarseLevels<Tc>& lv, const typename Cx<Tc>::t* sigma,
-                            const typename Cx<Tc>::t* r0, typename Cx<Tc>::t* u0) {
-  if (!mg_tail2_supported<Tc>(lv) || planes < 1) return cudaErrorInvalidValue;
+cudaError_t launch_mg_tail2(Launch& L, int planes, const CoarseLevels<float>& lv, const float2* sigma, const float2* r0,
+                            float2* u0) {
+  typedef float Tc;
+  if (!mg_tail2_supported(lv) || planes < 1) return cudaErrorInvalidValue;
   // stage the first level's coefficients too when two CTAs still fit on an SM
   const size_t base = tail_arrays_smem<Tc>(lv) + tail_coef_smem<Tc>(lv, 1);
   const size_t all = base + tail_coef_smem<Tc>(lv, 0) - tail_coef_smem<Tc>(lv, 1);
@@ -315,17 +315,10 @@ cudaError_t launch_mg_tail2(Launch& L, int planes, const CoarseLevels<Tc>& lv, c
   if (e != cudaSuccess) return e;
   double pts = 0;
   for (int l = 0; l < lv.count; ++l) pts += (double)lv.np[l];
-  const double cs = sizeof(typename Cx<Tc>::t);
+  const double cs = sizeof(float2);
   L.begin(KC_MG_COARSE);
   mg_tail2_kernel<Tc><<<planes, tail_threads<Tc>(), smem, L.stream>>>(lv, r0, u0, sigma, stage0);
   return L.end(KC_MG_COARSE, (double)planes * lv.np[0] * 2.0 * cs, (double)planes * pts * 60.0);
 }
-
-template bool mg_tail2_supported<float>(const CoarseLevels<float>&);
-template bool mg_tail2_supported<double>(const CoarseLevels<double>&);
-template cudaError_t launch_mg_tail2<float>(Launch&, int, const CoarseLevels<float>&, const float2*, const float2*,
-                                            float2*);
-template cudaError_t launch_mg_tail2<double>(Launch&, int, const CoarseLevels<double>&, const double2*,
-                                             const double2*, double2*);
 
 }  // namespace pcopt
