@@ -135,6 +135,9 @@ Prof::~Prof() {
 // ---------------------------------------------------------------------------
 // the handle
 // ---------------------------------------------------------------------------
+// time chunks of the element stiffness-derivative partial sums
+constexpr int kFeGradChunks = 16;
+
 struct LevelBuf {
   int m = 0;
   int64_t np = 0;
@@ -146,6 +149,8 @@ struct LevelBuf {
   void* r = nullptr;       // complex spectral planes (Tc)
   void* u = nullptr;
   void* res = nullptr;
+  double* e64 = nullptr;   // 2D elements with a nodal coefficient: one value per element ((m+1)^2)
+  float* e32 = nullptr;
 };
 
 struct pc_handle {
@@ -159,7 +164,9 @@ struct pc_handle {
   bool bf16s = false;  // multigrid iterates stored as BF16 pairs (FP32 arithmetic)
   int cap = 0;
   double a_const = 1.0;
-  bool fe = false;  // finite elements in space (mass matrix M): constant a, FST
+  bool fe = false;  // finite elements in space (mass matrix M)
+  bool fevar = false;  // 2D elements solved by the element multigrid (any nodal coefficient)
+  double* fe_gpart = nullptr;  // 2D elements: per-element partial sums of the stiffness derivative
   bool lex = false;  // multigrid smoother in the natural order (per-level kernels on every level)
   FeScale fes;
 
@@ -419,6 +426,31 @@ static int upload(pc_handle* h, T** dst, const std::vector<double>& src, cudaStr
 }
 
 // face weights [4][np] (2D) packed per point for one-load access
+// element coefficients of every multigrid level (2D): level l+1 takes level l's nodal
+// values at even grid nodes (injection); an element gets the mean of its corner values
+static std::vector<std::vector<double>> fe_level_elements(const std::vector<double>& a, int m1, int nlev) {
+  std::vector<std::vector<double>> out;
+  std::vector<double> acur = a;  // (m+2)^2 nodes, x1 fastest
+  int m = m1;
+  for (int l = 0; l < nlev; ++l) {
+    const int Mn = m + 2, me = m + 1;
+    std::vector<double> E((size_t)me * me);
+    for (int k2 = 0; k2 < me; ++k2)
+      for (int k1 = 0; k1 < me; ++k1)
+        E[(size_t)k2 * me + k1] = 0.25 * (acur[(size_t)k2 * Mn + k1] + acur[(size_t)k2 * Mn + k1 + 1] +
+                                          acur[(size_t)(k2 + 1) * Mn + k1] + acur[(size_t)(k2 + 1) * Mn + k1 + 1]);
+    out.push_back(std::move(E));
+    if (l + 1 == nlev) break;
+    const int mc = (m - 1) / 2, Mc = mc + 2;
+    std::vector<double> ac((size_t)Mc * Mc);
+    for (int J = 0; J < Mc; ++J)
+      for (int I = 0; I < Mc; ++I) ac[(size_t)J * Mc + I] = acur[(size_t)(2 * J) * Mn + 2 * I];
+    acur.swap(ac);
+    m = mc;
+  }
+  return out;
+}
+
 static std::vector<float4> pack_w4(const std::vector<double>& w, int64_t np) {
   std::vector<float4> t((size_t)np);
   for (int64_t i = 0; i < np; ++i)
@@ -480,8 +512,13 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   }
   int spatial = p->spatial;
   const bool fe = p->space == PC_SPACE_FE;
-  if (fe && (!constant || spatial == PC_SPATIAL_MG))
-    return fail(PC_ERR_UNSUPPORTED, "finite elements: implemented for a constant coefficient with sine-transform solves");
+  if (fe && dim == 3 && (!constant || spatial == PC_SPATIAL_MG))
+    return fail(PC_ERR_UNSUPPORTED, "3D finite elements: implemented for a constant coefficient with sine-transform "
+                                    "solves");
+  if (fe && p->smoother == PC_SMOOTHER_LEXICOGRAPHIC)
+    return fail(PC_ERR_UNSUPPORTED, "finite elements: the element multigrid smooths in colour order only");
+  if (fe && p->precision == PC_PREC_MIXED_BF16S && (!constant || spatial == PC_SPATIAL_MG))
+    return fail(PC_ERR_UNSUPPORTED, "finite elements: no BF16-storage element multigrid");
   if (spatial == PC_SPATIAL_AUTO) spatial = constant ? PC_SPATIAL_FST : PC_SPATIAL_MG;
   if (spatial == PC_SPATIAL_FST && !constant) return fail(PC_ERR_ARG, "FST needs a constant coefficient a");
   if (spatial == PC_SPATIAL_MG && ((m1 + 1) & m1) != 0) return fail(PC_ERR_ARG, "multigrid needs m1 = 2^k - 1");
@@ -511,6 +548,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->cap = p->max_iter;
   h->a_const = a[0];
   h->fe = fe;
+  h->fevar = fe && spatial == PC_SPATIAL_MG;
   h->fes = fe_scale(dim, m1, h->a_const);
   h->lex = spatial == PC_SPATIAL_MG && p->smoother == PC_SMOOTHER_LEXICOGRAPHIC;
   h->prof.on = false;
@@ -524,6 +562,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     std::vector<std::vector<double>> ws, ds;
     std::vector<int> mlev;
     all_level_stencils(a, m1, dim, h->tau, spatial == PC_SPATIAL_MG, ws, ds, mlev);
+    const std::vector<std::vector<double>> els =
+        h->fevar ? fe_level_elements(a, m1, (int)mlev.size()) : std::vector<std::vector<double>>();
     for (size_t l = 0; l < mlev.size(); ++l) {
       LevelBuf L;
       L.m = mlev[l];
@@ -532,6 +572,10 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       if ((rc = upload(h, &L.d64, ds[l], st))) goto fail_out;
       if ((rc = upload(h, &L.w32, ws[l], st))) goto fail_out;
       if ((rc = upload(h, &L.d32, ds[l], st))) goto fail_out;
+      if (h->fevar) {
+        if ((rc = upload(h, &L.e64, els[l], st))) goto fail_out;
+        if ((rc = upload(h, &L.e32, els[l], st))) goto fail_out;
+      }
       if (dim == 2 && h->fp32) {
         const std::vector<float4> w4 = pack_w4(ws[l], L.np);
         if ((rc = dev_alloc_t(h, &L.w4, w4.size()))) goto fail_out;
@@ -545,7 +589,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
       if ((rc = dev_alloc(h, &L.u, (size_t)h->planes * L.np * ub))) goto fail_out;
       // per-level residual planes: the 3D path and the natural-order smoother write them
       // (the 2D red-black down leg fuses the residual away)
-      if ((dim == 3 || h->lex) && l + 1 < mlev.size() &&
+      if ((dim == 3 || h->lex || h->fevar) && l + 1 < mlev.size() &&
           (rc = dev_alloc(h, &L.res, (size_t)h->planes * L.np * cb)))
         goto fail_out;
       h->lv.push_back(L);
@@ -579,7 +623,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     // or 15 (3D).  (The in-place kernel also runs FP64 iterates, but one CTA of 133 KB
     // per plane made the ideal preconditioner's two-plane steps slower: 29.6 -> 34.8
     // ms per apply at 255^2 x 256.)
-    h->tail2 = dim == 2 && h->fp32 && !h->bf16s;
+    h->tail2 = dim == 2 && h->fp32 && !h->bf16s && !h->fevar;
     const int mthr = h->tail2 ? kMgTailMaxM : (dim == 2 ? 31 : 15);
     int l0 = (int)h->lv.size() - 1;
     while (l0 > 0 && h->lv[l0 - 1].m <= mthr) --l0;
@@ -667,6 +711,8 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     if ((rc = upload(h, &h->a_nodes_dev, a, st))) goto fail_out;
     const int nch = (h->n + h->grad_tj - 1) / h->grad_tj;
     if ((rc = dev_alloc_t(h, &h->grad_partial, (size_t)nch * h->ms))) goto fail_out;
+    if (fe && dim == 2 && (rc = dev_alloc_t(h, &h->fe_gpart, (size_t)kFeGradChunks * (m1 + 1) * (m1 + 1))))
+      goto fail_out;
   }
   // ---- Krylov workspace
   {
@@ -768,6 +814,13 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
       PC_CUDA(cudaStreamSynchronize(st));
     }
   }
+  if (h->fevar) {
+    const std::vector<std::vector<double>> els = fe_level_elements(a, m1, (int)mlev.size());
+    for (size_t l = 0; l < mlev.size(); ++l) {
+      if ((rc = refill(h->lv[l].e64, els[l], st, s64))) return rc;
+      if ((rc = refill(h->lv[l].e32, els[l], st, s32))) return rc;
+    }
+  }
   {
     std::vector<float2> wsp(ws[0].size()), dsp(ds[0].size());
     for (size_t i = 0; i < wsp.size(); ++i) {
@@ -796,11 +849,16 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
 
 extern "C" int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream) {
   if (!h || !log_a) return fail(PC_ERR_ARG, "pc_set_log_coefficient: null argument");
-  if (h->spatial != PC_SPATIAL_MG || h->fe)
-    return fail(PC_ERR_UNSUPPORTED, "pc_set_log_coefficient: variable-coefficient (multigrid, finite-difference) "
-                                    "handles only");
+  if (h->spatial != PC_SPATIAL_MG)
+    return fail(PC_ERR_UNSUPPORTED, "pc_set_log_coefficient: variable-coefficient (multigrid) handles only");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   cudaError_t e = launch_set_log_coefficient(L, h->dim, h->m1, log_a, h->a_nodes_dev, h->a_int);
+  if (h->fevar) {
+    int st = 1;
+    for (size_t l = 0; l < h->lv.size() && e == cudaSuccess; ++l, st *= 2)
+      e = launch_fevar_level_elements(L, h->a_nodes_dev, h->m1 + 2, st, h->lv[l].m, h->lv[l].e64, h->lv[l].e32);
+    return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_set_log_coefficient");
+  }
   int stride = 1;
   for (size_t l = 0; l < h->lv.size() && e == cudaSuccess; ++l, stride *= 2) {
     LevelBuf& B = h->lv[l];
@@ -875,6 +933,39 @@ template <>
 const double* lvd<double>(const LevelBuf& L) { return L.d64; }
 template <>
 const float* lvd<float>(const LevelBuf& L) { return L.d32; }
+
+template <typename Tc>
+static const Tc* lve(const LevelBuf& L);
+template <>
+const double* lve<double>(const LevelBuf& L) { return L.e64; }
+template <>
+const float* lve<float>(const LevelBuf& L) { return L.e32; }
+
+// element multigrid, 2D (k_fevar.cu): on every level a colour-ordered Gauss-Seidel
+// sweep from zero, residual and restriction by P^T; the one-point level is solved by
+// its sweep; then the bilinear corrections from the coarsest level up
+template <typename Tc>
+static cudaError_t fevar_spatial(pc_handle* h, Launch& L, int P, const typename Cx<Tc>::t* sig) {
+  typedef typename Cx<Tc>::t C;
+  const int nl = (int)h->lv.size();
+  const Tc tau = (Tc)h->tau;
+  cudaError_t e;
+  for (int l = 0; l < nl; ++l) {
+    const LevelBuf& B = h->lv[l];
+    const Tc hl = Tc(1) / Tc(B.m + 1);
+    const Tc* E = lve<Tc>(B);
+    if ((e = launch_fevar_smooth<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r, (C*)B.u)) != cudaSuccess)
+      return e;
+    if (l + 1 == nl) break;
+    if ((e = launch_fevar_resid_restrict<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r, (const C*)B.u,
+                                             (C*)B.res, (C*)h->lv[l + 1].r)) != cudaSuccess)
+      return e;
+  }
+  for (int l = nl - 2; l >= 0; --l)
+    if ((e = launch_mg_prolong<Tc, C>(L, grid_of(h, l), P, (const C*)h->lv[l + 1].u, (C*)h->lv[l].u)) != cudaSuccess)
+      return e;
+  return cudaSuccess;
+}
 
 template <typename Tc>
 struct Tables;
@@ -960,6 +1051,10 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
       return cudaSuccess;
     }
   }
+  if (h->fevar) {
+    if constexpr (std::is_same<TU, C>::value) return fevar_spatial<Tc>(h, L, P, sig);
+    return cudaErrorNotSupported;
+  }
   // multigrid V(1,0): per-level kernels on the fine levels, one fused kernel for the rest
   const int nl = (int)h->lv.size();
   const int l0 = h->coarse_l0;
@@ -1026,7 +1121,7 @@ static cudaError_t spatial_solve(pc_handle* h, Launch& L, int nplanes = 0,
 template <typename TU>
 static FineCorrection<TU> fine_correction(const pc_handle* h) {
   FineCorrection<TU> fc;
-  if (h->spatial == PC_SPATIAL_FST || h->lex || h->coarse_l0 < 1 || h->dim != 2) return fc;
+  if (h->spatial == PC_SPATIAL_FST || h->lex || h->fevar || h->coarse_l0 < 1 || h->dim != 2) return fc;
   const Grid g0 = grid_of(h, 0), g1 = grid_of(h, 1);
   fc.ec = (const TU*)h->lv[1].u;
   fc.dim = h->dim;
@@ -1100,6 +1195,14 @@ static cudaError_t precond64(pc_handle* h, Launch& L, const double* v, double* w
 static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32, double* y, bool transpose) {
   Stencil<double> st{h->lv[0].w64, h->lv[0].d64};
   const Grid g = grid_of(h, 0);
+  if (h->fevar) {
+    const double h2 = h->h * h->h;
+    if (x_f32)
+      return launch_matvec_fevar<float>(L, h->m1, h->n, h2, h->alpha, h->tau, h->lv[0].e64, (const float*)x, y,
+                                        transpose);
+    return launch_matvec_fevar<double>(L, h->m1, h->n, h2, h->alpha, h->tau, h->lv[0].e64, (const double*)x, y,
+                                       transpose);
+  }
   if (h->fe) {
     if (x_f32) return launch_matvec_fe<float>(L, g, h->n, h->alpha, h->fes, h->tau, (const float*)x, y, transpose);
     return launch_matvec_fe<double>(L, g, h->n, h->alpha, h->fes, h->tau, (const double*)x, y, transpose);
@@ -1114,6 +1217,11 @@ static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32
 static cudaError_t matvec_basis(pc_handle* h, Launch& L, const void* z, double* y, size_t zs = 0, size_t ys = 0,
                                 const int* jdev = nullptr) {
   const Grid g = grid_of(h, 0);
+  if (h->fevar)
+    return h->fp32 ? launch_matvec_fevar<float>(L, h->m1, h->n, h->h * h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                (const float*)z, y, false, zs, ys, jdev)
+                   : launch_matvec_fevar<double>(L, h->m1, h->n, h->h * h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                 (const double*)z, y, false, zs, ys, jdev);
   if (h->fe)
     return h->fp32 ? launch_matvec_fe<float>(L, g, h->n, h->alpha, h->fes, h->tau, (const float*)z, y, false, zs, ys,
                                              jdev)
@@ -1183,8 +1291,13 @@ extern "C" int pc_build_rhs(pc_handle* h, const double* f, const double* g, cons
 
 extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream) {
   if (!h || !x || !lam || !grad) return fail(PC_ERR_ARG, "pc_grad_log_a: null argument");
-  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_grad_log_a: finite-difference handles only");
+  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_grad_log_a: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  if (h->fe) {
+    // -tau a_P / 4 sum over P's elements and the time blocks of (lam1^T K_e x2 - lam2^T K_e x1)
+    cudaError_t e = launch_fevar_grad(L, h->m1, h->n, h->tau, h->a_int, x, lam, h->fe_gpart, kFeGradChunks, grad);
+    return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_log_a");
+  }
   // -tau * a_P / (2 h^2) * sum_j sum_faces [...]
   const double scale = -h->tau * 0.5 / (h->h * h->h);
   cudaError_t e =
@@ -1194,8 +1307,11 @@ extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, d
 
 extern "C" int pc_grad_g(pc_handle* h, const double* lam, double* grad_g, void* stream) {
   if (!h || !lam || !grad_g) return fail(PC_ERR_ARG, "pc_grad_g: null argument");
-  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_grad_g: finite-difference handles only");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  if (h->fe) {  // b1_j = tau M g_j: the gradient is tau M lam1_j
+    cudaError_t e = launch_fe_apply(L, grid_of(h, 0), h->n, h->tau * h->fes.wM, 0.0, lam, 0.0, grad_g);
+    return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_g");
+  }
   cudaError_t e = launch_grad_g(L, lam, (int64_t)h->n * h->ms, h->tau, grad_g);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_g");
 }
@@ -1205,8 +1321,13 @@ static double objective_weight(const pc_handle* h) { return std::pow(h->h, h->di
 
 extern "C" int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void* stream) {
   if (!h || !x || !g || !J) return fail(PC_ERR_ARG, "pc_objective: null argument");
-  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_objective: finite-difference handles only");
+  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_objective: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  if (h->fe) {  // tau [1/2 sum e^T M e + 1/(2 gamma) sum p^T M p]
+    cudaError_t e = launch_fevar_objective(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g, h->partial,
+                                           h->nblocks * (h->cap + 2), J);
+    return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective");
+  }
   cudaError_t e = launch_objective(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), h->partial,
                                    h->nblocks * (h->cap + 2), J);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective");
@@ -1215,8 +1336,12 @@ extern "C" int pc_objective(pc_handle* h, const double* x, const double* g, doub
 extern "C" int pc_objective_grad(pc_handle* h, const double* x, const double* g, const double* gJ, double* gx,
                                  double* gg, void* stream) {
   if (!h || !x || !g || (!gx && !gg)) return fail(PC_ERR_ARG, "pc_objective_grad: null argument");
-  if (h->fe) return fail(PC_ERR_UNSUPPORTED, "pc_objective_grad: finite-difference handles only");
+  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_objective_grad: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
+  if (h->fe) {
+    cudaError_t e = launch_fevar_objective_grad(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g, gJ, gx, gg);
+    return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective_grad");
+  }
   cudaError_t e = launch_objective_grad(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), gJ, gx, gg);
   return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective_grad");
 }
@@ -2172,7 +2297,9 @@ static int pcg_E(pc_handle* h, Launch& L, const double* b, double* u, double rto
   if (bnorm == 0.0) return PC_OK;
   if (!std::isfinite(bnorm) || !std::isfinite(rz)) return fail(PC_ERR_BREAKDOWN, "end-point solve: non-finite input");
   for (int it = 1; it <= maxit; ++it) {
-    if (h->fe)
+    if (h->fevar)
+      PC_CUDA(launch_fevar_apply(L, h->m1, 1, h->h * h->h, h->lv[0].e64, 1.0, h->tau, p, 0.0, q));  // (M + tau K) p
+    else if (h->fe)
       PC_CUDA(launch_fe_apply(L, g, 1, h->fes.wM, h->tau * h->fes.wK, p, 0.0, q));  // (M + tau K) p
     else
       PC_CUDA(launch_apply_E(L, g, st, p, q));

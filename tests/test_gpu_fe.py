@@ -167,8 +167,9 @@ def test_fe_adjoint_solve_matches_oracle():
 
 
 def test_fe_unsupported_requests_fail_loudly():
+    # the element gradient is built for 2D grids (tests/test_gpu_fe_var.py)
     from paper_2410_22686_gb300 import capi
-    sol = _solver(2, 7, 4)
+    sol = _solver(3, 7, 4)
     x = torch.zeros(sol.vec_len, dtype=torch.float64, device="cuda")
     with pytest.raises(capi.PCError) as ei:
         sol.grad_log_a(x, x)
