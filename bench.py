@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--gammas", default=",".join(str(g) for g in GAMMAS))
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fe-var", action="store_true")
     ap.add_argument("--skip-bf16", action="store_true")
     ap.add_argument("--skip-3d", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
@@ -445,6 +446,24 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
         out["const_a_fst_255sq_n256"] = {"data": "Example 1 fields, a = 1, gamma 1e-4, eps = sqrt(tau)",
                                          "fd": "finite differences (M = I)",
                                          "fe": "bilinear finite elements (mass matrix M)", **res}
+
+    if not args.skip_fe_var:
+        # variable a with bilinear elements: the element multigrid inside P_eps^{-1}
+        p = S.variable_2d_problem(gamma=1e-4, m1=M1, n=NT)
+        res = {}
+        for prec in ("fp32", "fp64"):
+            sol = Solver(2, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision=prec, max_iter=80,
+                         space="fe")
+            b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
+                              torch.from_numpy(p.y0).to(dev))
+            t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
+            res[prec] = {"solve_s": t, "iters": r[1], "relres": r[2]}
+            sol.close()
+            del b
+            torch.cuda.empty_cache()
+        out["fe_var_255sq_n256"] = {"data": "benchmark fields (variable a), gamma 1e-4, eps = sqrt(tau)",
+                                    "discretisation": "bilinear elements, element coefficient = mean of its "
+                                                      "corner values; colour-ordered element multigrid", **res}
 
     if not args.skip_grad:
         p = S.gradient_problem()

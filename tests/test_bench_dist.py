@@ -190,7 +190,7 @@ def test_batched_extra_logic_with_fake_solvers(monkeypatch):
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
-    args = types.SimpleNamespace(skip_3d=True, skip_fst=True, skip_grad=True, skip_batched=False, skip_ideal=True,
+    args = types.SimpleNamespace(skip_3d=True, skip_fst=True, skip_fe_var=True, skip_grad=True, skip_batched=False, skip_ideal=True,
                                  batch_gb=110.0)
     out = bench._extra_workloads(args, torch, "cpu")["batched_64"]
     assert out["problems"] == 64 and out["ranks"] == 1 and out["converged"] == 64 and out["max_iters"] == 7
@@ -206,7 +206,7 @@ def test_gpus_flag_starts_the_ranks_itself():
     env_keep = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK") if k in os.environ}
     try:
         argv = ["--gpus", "2", "--steps", "2", "--warmup", "3", "--m1", "7", "--nt", "4", "--skip-fp64",
-                "--skip-e2e", "--skip-bf16", "--skip-3d", "--skip-grad", "--skip-batched", "--skip-fst",
+                "--skip-e2e", "--skip-bf16", "--skip-3d", "--skip-grad", "--skip-batched", "--skip-fst", "--skip-fe-var",
                 "--skip-graph", "--skip-sweep", "--skip-ideal", "--no-cpu-baseline"]
         rc, outs = bench.launch_local_ranks(2, argv, script=os.path.join(ROOT, "tests", "bench_fake_rank.py"),
                                             capture=True, timeout=240)
