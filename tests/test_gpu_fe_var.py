@@ -197,3 +197,31 @@ def test_element_requests_outside_the_built_path_fail_loudly():
         with pytest.raises(capi.PCError) as ei:
             Solver(2, 7, 4, 1.0, 1e-3, 0.3, a, spatial="mg", space="fe", **kw)
         assert ei.value.status == capi.PC_ERR_UNSUPPORTED
+
+
+def test_element_graph_and_batched_solves_match_host_solves():
+    """The element multigrid under CUDA-graph capture: one graph launch per solve and one
+    batch of element, difference and constant-coefficient handles give the host-driven
+    solves' iterates."""
+    from paper_2410_22686_gb300 import Batch, Solver
+    m1, n, gamma = 31, 32, 1e-3
+    eps = math.sqrt(osy.time_step(1.0, n))
+    a = _coef(m1, 25)
+    sols = [_solver(m1, n, a, precision="fp64", gamma=gamma, eps=eps),
+            _solver(m1, n, a, precision="mixed", gamma=gamma, eps=eps),
+            Solver(2, m1, n, 1.0, gamma, eps, a, spatial="mg", precision="fp64", max_iter=80, tiles=None)]
+    f, g, y0 = (_dev(S.random_vector(sh, k)) for sh, k in (((n, m1, m1), 26), ((n, m1, m1), 27), ((m1, m1), 28)))
+    bs = [s.build_rhs(f, g, y0) for s in sols]
+    singles = [s.solve(b, rtol=1e-10) for s, b in zip(sols, bs)]
+    for s, b, (x_ref, it_ref, _) in zip(sols, bs, singles):
+        x, it, rr = s.solve_graph(b, rtol=1e-10)
+        assert it == it_ref and rr <= 1e-10
+        assert (x - x_ref).norm().item() <= 1e-9 * x_ref.norm().item()
+    batch = Batch(sols, bs, rtol=1e-10, maxit=80)
+    iters, rel = batch.solve()
+    for k, (x_ref, it_ref, _) in enumerate(singles):
+        assert iters[k] == it_ref and rel[k] <= 1e-10
+        assert (batch.xs[k] - x_ref).norm().item() <= 1e-9 * x_ref.norm().item()
+    batch.close()
+    for s in sols:
+        s.close()
