@@ -458,6 +458,18 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
                               torch.from_numpy(p.y0).to(dev))
             t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
             res[prec] = {"solve_s": t, "iters": r[1], "relres": r[2]}
+            if prec == "fp32":  # per-kernel CUDA-event breakdown of one more solve
+                sol.stats_reset()
+                sol.profile(True)
+                sol.solve(b, rtol=RTOL, raise_on_nonconv=False)
+                torch.cuda.synchronize()
+                sol.profile(False)
+                st = sol.stats()
+                tot = sum(v["ms"] for v in st.values()) or 1.0
+                res[prec]["kernel_breakdown"] = {
+                    k: {"share": v["ms"] / tot, "avg_us": 1000 * v["ms"] / v["launches"],
+                        "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None}
+                    for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8] if v["launches"]}
             sol.close()
             del b
             torch.cuda.empty_cache()

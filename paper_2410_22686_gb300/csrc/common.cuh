@@ -279,6 +279,7 @@ cudaError_t launch_fe_apply(Launch& L, const Grid& g, int planes, double cM, dou
 // element ((m+1)^2, the mean of its corner values), h2 = h^2 of the level
 cudaError_t launch_fevar_apply(Launch& L, int m, int planes, double h2, const double* E, double cM, double cK,
                                const double* in, double beta, double* out);
+// (strides / jdev as launch_matvec)
 template <typename Tin>
 cudaError_t launch_matvec_fevar(Launch& L, int m, int n, double h2, double alpha, double tau, const double* E,
                                 const Tin* x, double* y, bool transpose, size_t xstride = 0, size_t ystride = 0,

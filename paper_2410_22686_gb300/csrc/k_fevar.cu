@@ -51,11 +51,12 @@ __device__ __forceinline__ void mk_apply(const Tin* __restrict__ u, const KStenc
                                          T& mu36, T& ku) {
   const int s = i2 * m + i1;
   const bool w = i1 > 0, e = i1 < m - 1, so = i2 > 0, no = i2 < m - 1;
-  const T uc = (T)u[s];
-  const T uw = w ? (T)u[s - 1] : T(0), ue = e ? (T)u[s + 1] : T(0);
-  const T us = so ? (T)u[s - m] : T(0), un = no ? (T)u[s + m] : T(0);
-  const T usw = (so && w) ? (T)u[s - m - 1] : T(0), use = (so && e) ? (T)u[s - m + 1] : T(0);
-  const T unw = (no && w) ? (T)u[s + m - 1] : T(0), une = (no && e) ? (T)u[s + m + 1] : T(0);
+  // FP32 inputs widen on the integer pipes (cvt): GB300 runs F2F on its FP64 unit
+  const T uc = cvt<T>(u[s]);
+  const T uw = w ? cvt<T>(u[s - 1]) : T(0), ue = e ? cvt<T>(u[s + 1]) : T(0);
+  const T us = so ? cvt<T>(u[s - m]) : T(0), un = no ? cvt<T>(u[s + m]) : T(0);
+  const T usw = (so && w) ? cvt<T>(u[s - m - 1]) : T(0), use = (so && e) ? cvt<T>(u[s - m + 1]) : T(0);
+  const T unw = (no && w) ? cvt<T>(u[s + m - 1]) : T(0), une = (no && e) ? cvt<T>(u[s + m + 1]) : T(0);
   mu36 = T(16) * uc + T(4) * (uw + ue + us + un) + (usw + use + unw + une);
   ku = k.c * uc + k.e * ue + k.w * uw + k.n * un + k.s * us + k.ne * une + k.nw * unw + k.se * use + k.sw * usw;
 }
@@ -90,9 +91,9 @@ __global__ void __launch_bounds__(256) fevar_matvec_kernel(const Tin* __restrict
   const int64_t np = (int64_t)m * m;
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= np) return;
-  if (jdev) {
+  if (jdev) {  // device-resident Arnoldi index: x = Z_j, y = V_{j+1}
     x += (size_t)(*jdev) * xstride;
-    y += (size_t)(*jdev) * ystride;
+    y += (size_t)(*jdev + 1) * ystride;
   }
   const int j0 = blockIdx.y * tj, j1 = min(n, j0 + tj);
   if (j0 >= n) return;
