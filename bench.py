@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-fst", action="store_true")
     ap.add_argument("--skip-graph", action="store_true")
-    ap.add_argument("--batch-gb", type=float, default=110.0, help="device memory per batched wave (GB)")
+    ap.add_argument("--batch-gb", type=float, default=200.0, help="device memory per batched wave (GB)")
     a = ap.parse_args()
     a.gammas = tuple(float(x) for x in a.gammas.split(","))
     return a

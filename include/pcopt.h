@@ -239,7 +239,13 @@ int pc_build_rhs(pc_handle* h, const double* f, const double* g, const double* y
  *   relative residual (true residual for RIGHT, preconditioned for LEFT).
  * Arnoldi (classical Gram-Schmidt with one re-orthogonalisation), the Givens
  * least-squares update, the matvec and the true residual are FP64 in every
- * precision mode.  Synchronises `stream`.
+ * precision mode.  RIGHT mode stops on the least-squares estimate of the
+ * residual and then forms the true residual ||b - A x|| / ||b||; if that misses
+ * rtol (an FP32 preconditioner can leave it just above the estimate) and
+ * iterations remain, the solve continues from x in a fresh Krylov space until
+ * the true residual meets rtol or maxit iterations in total are spent; iters
+ * counts every iteration.  PC_OK therefore means relres <= rtol.
+ * Synchronises `stream`.
  * Errors: PC_ERR_NOT_CONVERGED (x holds the maxit-th iterate), PC_ERR_BREAKDOWN. */
 int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit,
                    int mode, int* iters, double* relres, void* stream);
@@ -253,6 +259,8 @@ int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int ma
  *   iterations + 1); 0 before any solve, or after one that failed before its
  *   first residual.  Copies the sines from the device on `stream` and
  *   synchronises it.
+ * After a continuation (pc_gmres_solve) the history is that of the last Krylov
+ * space, out[0] being its initial residual.
  * Errors: PC_ERR_ARG (null h or count, cap < 0, out NULL with cap > 0). */
 int pc_residual_history(pc_handle* h, double* out, int cap, int* count, void* stream);
 
@@ -262,7 +270,8 @@ int pc_residual_history(pc_handle* h, double* out, int cap, int* count, void* st
  * estimate, so no host round trip happens per iteration.  The graph is built
  * on the first call and reused while (b, x, rtol, maxit) are unchanged.
  *   x: device, overwritten (the initial guess is zero).  iters/relres as in
- *   pc_gmres_solve (relres is the true relative residual).  Synchronises `stream`.
+ *   pc_gmres_solve (relres is the true relative residual; a true residual above
+ *   rtol is continued host-driven as in pc_gmres_solve).  Synchronises `stream`.
  * Errors: as pc_gmres_solve; PC_ERR_UNSUPPORTED for n not a power of two,
  * n > 1024 (FP32 preconditioner) or n > 256 (FP64 preconditioner). */
 int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, int maxit, int* iters,
@@ -276,7 +285,9 @@ int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, 
  * (HOST arrays, may be NULL).  hs: distinct handles; b[i], x[i]: device
  * vectors of handle i (x overwritten, zero initial guess).  The batch keeps
  * pointers to everything it was created with; destroy it before those.
- * pc_batch_solve returns the worst status over the problems. */
+ * A problem whose true residual misses rtol after the launch is continued
+ * host-driven as in pc_gmres_solve.  pc_batch_solve returns the worst status
+ * over the problems. */
 typedef struct pc_batch pc_batch;
 int pc_batch_create(pc_handle* const* hs, int count, const double* const* b, double* const* x, double rtol,
                     int maxit, pc_batch** out);

@@ -1618,9 +1618,39 @@ extern "C" int pc_residual_history(pc_handle* h, double* out, int cap, int* coun
   return PC_OK;
 }
 
+// Right-preconditioned GMRES stops on the least-squares estimate of ||b - A x||; with
+// an FP32 preconditioner and a double-float basis the true residual formed at exit can
+// sit just above that estimate.  When it misses rtol and iterations remain, the solve
+// continues from the current x in a fresh Krylov space (r0 = b - A x, the remaining
+// iteration budget) until the true residual meets rtol or the budget is spent; `done`
+// holds the iterations already spent (a graph solve's), and *iters counts all of them.
+static int gmres_confirm(pc_handle* h, const double* b, double* x, double rtol, int maxit, int mode, int rc,
+                         int done, double rr, int* iters, double* relres, cudaStream_t st) {
+  while (rc == PC_OK && mode == PC_GMRES_RIGHT && rr > rtol && done < maxit) {
+    int k = 0;
+    rc = gmres_impl(h, b, x, rtol, maxit - done, mode, &k, &rr, st);
+    done += k;
+    if (k == 0) break;
+  }
+  if (iters) *iters = done;
+  if (relres) *relres = rr;
+  if (rc == PC_OK && mode == PC_GMRES_RIGHT && rr > rtol)
+    return fail(PC_ERR_NOT_CONVERGED, "gmres: true residual above rtol after maxit iterations");
+  return rc;
+}
+
 extern "C" int pc_gmres_solve(pc_handle* h, const double* b, double* x, double rtol, int maxit, int mode, int* iters,
                               double* relres, void* stream) {
-  return gmres_impl(h, b, x, rtol, maxit, mode, iters, relres, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  int k = 0;
+  double rr = 0.0;
+  const int rc = gmres_impl(h, b, x, rtol, maxit, mode, &k, &rr, st);
+  if (rc != PC_OK && rc != PC_ERR_NOT_CONVERGED) {
+    if (iters) *iters = k;
+    if (relres) *relres = rr;
+    return rc;
+  }
+  return gmres_confirm(h, b, x, rtol, maxit, mode, rc, k, rr, iters, relres, st);
 }
 
 extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, int maxit, int mode,
@@ -1636,7 +1666,11 @@ extern "C" int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, doub
   if (e != cudaSuccess) return cuda_fail(e, "pc_adjoint_solve");
   if ((e = launch_axpby<double>(L, -1.0, lam + half, 0.0, lam + half, half)) != cudaSuccess)
     return cuda_fail(e, "pc_adjoint_solve");
-  const int rc = gmres_impl(h, h->adjbuf, lam, rtol, maxit, mode, iters, relres, st);
+  int k = 0;
+  double rr = 0.0;
+  int rc = gmres_impl(h, h->adjbuf, lam, rtol, maxit, mode, &k, &rr, st);
+  if (rc == PC_OK || rc == PC_ERR_NOT_CONVERGED)
+    rc = gmres_confirm(h, h->adjbuf, lam, rtol, maxit, mode, rc, k, rr, iters, relres, st);
   if ((e = launch_axpby<double>(L, -1.0, lam + half, 0.0, lam + half, half)) != cudaSuccess)
     return cuda_fail(e, "pc_adjoint_solve");
   cudaError_t se = cudaStreamSynchronize(st);
@@ -1842,7 +1876,14 @@ extern "C" int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, do
     h->g_maxit = maxit;
   }
   GR_CUDA(cudaGraphLaunch(h->gexec, st));
-  return graph_results(h, st, rtol, iters, relres);
+  int k = 0;
+  double rr = 0.0;
+  const int rc = graph_results(h, st, rtol, &k, &rr);
+  if (iters) *iters = k;
+  if (relres) *relres = rr;
+  if (rc != PC_OK) return rc;
+  // a true residual above rtol continues host-driven from x (gmres_confirm)
+  return gmres_confirm(h, b, x, rtol, maxit, PC_GMRES_RIGHT, rc, k, rr, iters, relres, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1851,6 +1892,8 @@ extern "C" int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, do
 // ---------------------------------------------------------------------------
 struct pc_batch {
   std::vector<pc_handle*> hs;
+  std::vector<const double*> b;  // right-hand sides and solutions of the problems
+  std::vector<double*> x;
   double rtol = 0.0;
   int maxit = 0;
   cudaGraphExec_t exec = nullptr;
@@ -1880,6 +1923,8 @@ extern "C" int pc_batch_create(pc_handle* const* hs, int count, const double* co
   bt->hs.assign(hs, hs + count);
   bt->rtol = rtol;
   bt->maxit = maxit;
+  bt->b.assign(b, b + count);
+  bt->x.assign(x, x + count);
   int rc = PC_OK;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&bt->origin, cudaStreamNonBlocking);
@@ -1928,7 +1973,13 @@ extern "C" int pc_batch_solve(pc_batch* bt, int* iters, double* relres, void* st
   GR_CUDA(cudaGraphLaunch(bt->exec, st));
   int worst = PC_OK;
   for (size_t i = 0; i < bt->hs.size(); ++i) {
-    const int rc = graph_results(bt->hs[i], st, bt->rtol, iters ? iters + i : nullptr, relres ? relres + i : nullptr);
+    int k = 0;
+    double rr = 0.0;
+    int rc = graph_results(bt->hs[i], st, bt->rtol, &k, &rr);
+    if (rc == PC_OK)  // a true residual above rtol continues host-driven from x[i] (gmres_confirm)
+      rc = gmres_confirm(bt->hs[i], bt->b[i], bt->x[i], bt->rtol, bt->maxit, PC_GMRES_RIGHT, rc, k, rr, &k, &rr, st);
+    if (iters) iters[i] = k;
+    if (relres) relres[i] = rr;
     if (rc == PC_ERR_CUDA) return rc;
     if (rc != PC_OK && worst == PC_OK) worst = rc;
   }
