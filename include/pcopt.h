@@ -158,6 +158,30 @@ typedef struct pc_handle pc_handle;
  * non-constant a or multigrid), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
 
+/* Bytes of the Krylov storage a handle built from `params` needs: the basis of
+ * max_iter + 1 vectors (8 bytes per unknown each, double-float or FP64) and the
+ * max_iter preconditioned vectors of flexible GMRES (4 bytes per unknown with an
+ * FP32 preconditioner, 8 with FP64), each part rounded up to 256 bytes.  This
+ * storage is what full GMRES (Section 3: no restarts) needs to hold, and it
+ * dominates a handle's memory.  Host arithmetic only.
+ * Errors: PC_ERR_ARG (null argument; dim, m1, n, max_iter, eps or precision as
+ * in pc_setup). */
+int pc_krylov_bytes(const pc_params* params, size_t* bytes);
+
+/* pc_setup with the Krylov storage in caller-provided device memory instead of
+ * the handle's own: krylov (device, 256-byte aligned, at least
+ * pc_krylov_bytes(params) bytes) holds the basis and then the preconditioned
+ * vectors.  The caller owns that memory, keeps it alive while the handle exists
+ * and may give overlapping ranges to several handles, which then must not solve
+ * at the same time: a batch (pc_batch_create) starts a problem whose range
+ * overlaps an earlier problem's after that problem has finished, so more
+ * problems than fit in memory at once run in one graph launch.  Every
+ * solve overwrites the range.
+ * Errors: as pc_setup; PC_ERR_ARG also for a null, misaligned or too small
+ * workspace (checked before any device work). */
+int pc_setup_shared(const pc_params* params, const double* a_nodes, void* krylov, size_t krylov_bytes,
+                    void* stream, pc_handle** out);
+
 /* The precision a handle resolved to (PC_PREC_FP64, PC_PREC_MIXED_FP32 or
  * PC_PREC_MIXED_BF16S; PC_PREC_AUTO is resolved at setup). */
 int pc_precision_of(const pc_handle* h, int* precision);
@@ -285,9 +309,11 @@ int pc_gmres_solve_graph(pc_handle* h, const double* b, double* x, double rtol, 
  * (HOST arrays, may be NULL).  hs: distinct handles; b[i], x[i]: device
  * vectors of handle i (x overwritten, zero initial guess).  The batch keeps
  * pointers to everything it was created with; destroy it before those.
- * A problem whose true residual misses rtol after the launch is continued
- * host-driven as in pc_gmres_solve.  pc_batch_solve returns the worst status
- * over the problems. */
+ * Problems whose Krylov storage overlaps (pc_setup_shared) are ordered: the
+ * later one in hs starts when the earlier one has finished; all others run
+ * concurrently.  A problem whose true residual misses rtol after the launch is
+ * continued host-driven as in pc_gmres_solve.  pc_batch_solve returns the worst
+ * status over the problems. */
 typedef struct pc_batch pc_batch;
 int pc_batch_create(pc_handle* const* hs, int count, const double* const* b, double* const* x, double rtol,
                     int maxit, pc_batch** out);

@@ -6,6 +6,6 @@ this package only binds it (``capi``), wraps a handle (``Solver``) and adds a
 ``torch.autograd.Function`` over the solve (``autograd``).
 """
 from . import capi  # noqa: F401
-from .solver import Batch, Solver, measure_peaks, solve_host_pipelined  # noqa: F401
+from .solver import Batch, Solver, krylov_bytes, measure_peaks, pack_krylov, solve_host_pipelined  # noqa: F401
 
-__all__ = ["capi", "Solver", "Batch", "measure_peaks", "solve_host_pipelined"]
+__all__ = ["capi", "Solver", "Batch", "krylov_bytes", "measure_peaks", "pack_krylov", "solve_host_pipelined"]

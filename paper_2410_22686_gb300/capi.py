@@ -63,6 +63,8 @@ _dpp = ctypes.POINTER(ctypes.c_double)
 
 _SIGNATURES = {
     "pc_setup": (_i, [ctypes.POINTER(pc_params), _vp, _vp, ctypes.POINTER(_vp)]),
+    "pc_krylov_bytes": (_i, [ctypes.POINTER(pc_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "pc_setup_shared": (_i, [ctypes.POINTER(pc_params), _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "pc_destroy": (_i, [_vp]),
     "pc_set_coefficient": (_i, [_vp, _vp, _vp]),
     "pc_matvec": (_i, [_vp, _dp, _dp, _vp]),

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -155,6 +156,9 @@ struct LevelBuf {
 
 struct pc_handle {
   pc_params prm;
+  // caller-provided device memory holding V and Z (pc_setup_shared), else null
+  const unsigned char* kws = nullptr;
+  size_t kws_bytes = 0;
   int dim = 2, m1 = 0, n = 0, nf = 0, planes = 0, logn = 0;
   int64_t ms = 0;
   size_t U = 0;
@@ -479,7 +483,58 @@ static int upload_c(pc_handle* h, void** dst, const std::vector<double>& re, con
   return PC_OK;
 }
 
+// bytes of the Krylov basis V (cap + 1 vectors of the tiled layout, 8 bytes per
+// unknown) and of the preconditioned vectors Z (cap vectors, FP32 or FP64), each
+// part rounded up to 256 bytes; Z follows V
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+static size_t krylov_v_bytes(size_t U, int cap) { return round256((size_t)(cap + 1) * ((U + 511) / 512 * 512) * 8); }
+static size_t krylov_bytes_of(size_t U, int cap, bool fp32) {
+  return krylov_v_bytes(U, cap) + round256((size_t)cap * U * (fp32 ? sizeof(float) : sizeof(double)));
+}
+static int resolved_precision(const pc_params* p) {
+  return p->precision == PC_PREC_AUTO ? (p->eps >= PC_AUTO_FP32_MIN_EPS ? PC_PREC_MIXED_FP32 : PC_PREC_FP64)
+                                      : p->precision;
+}
+
+static int setup_impl(const pc_params* p, const double* a_nodes, void* krylov, size_t krylov_bytes, void* stream,
+                      pc_handle** out);
+
 extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream, pc_handle** out) {
+  return setup_impl(p, a_nodes, nullptr, 0, stream, out);
+}
+
+extern "C" int pc_krylov_bytes(const pc_params* p, size_t* bytes) {
+  if (!p || !bytes) return fail(PC_ERR_ARG, "pc_krylov_bytes: null argument");
+  if (p->dim != 2 && p->dim != 3) return fail(PC_ERR_ARG, "dim must be 2 or 3");
+  if (p->m1 < 1 || p->m1 > 4095) return fail(PC_ERR_ARG, "m1 must be in [1, 4095]");
+  if (p->n < 1 || p->n > 4096) return fail(PC_ERR_ARG, "n must be in [1, 4096]");
+  if (p->max_iter < 1 || p->max_iter > 1000) return fail(PC_ERR_ARG, "max_iter must be in [1, 1000]");
+  if (!(p->eps > 0) || !(p->eps <= 1.0)) return fail(PC_ERR_ARG, "eps must lie in (0, 1]");
+  const int prec = resolved_precision(p);
+  if (prec != PC_PREC_FP64 && prec != PC_PREC_MIXED_FP32 && prec != PC_PREC_MIXED_BF16S)
+    return fail(PC_ERR_ARG, "unknown precision");
+  const size_t ms = p->dim == 2 ? (size_t)p->m1 * p->m1 : (size_t)p->m1 * p->m1 * p->m1;
+  *bytes = krylov_bytes_of(2 * (size_t)p->n * ms, p->max_iter, prec != PC_PREC_FP64);
+  return PC_OK;
+}
+
+extern "C" int pc_setup_shared(const pc_params* p, const double* a_nodes, void* krylov, size_t krylov_bytes,
+                               void* stream, pc_handle** out) {
+  if (!out) return fail(PC_ERR_ARG, "pc_setup_shared: null out pointer");
+  *out = nullptr;
+  if (!krylov) return fail(PC_ERR_ARG, "pc_setup_shared: null workspace");
+  if (reinterpret_cast<uintptr_t>(krylov) % 256 != 0)
+    return fail(PC_ERR_ARG, "pc_setup_shared: the workspace must be 256-byte aligned");
+  size_t need = 0;
+  if (int rc = pc_krylov_bytes(p, &need)) return rc;
+  if (krylov_bytes < need)
+    return fail(PC_ERR_ARG, "pc_setup_shared: workspace of " + std::to_string(krylov_bytes) + " bytes, " +
+                                std::to_string(need) + " needed");
+  return setup_impl(p, a_nodes, krylov, krylov_bytes, stream, out);
+}
+
+static int setup_impl(const pc_params* p, const double* a_nodes, void* krylov, size_t krylov_bytes, void* stream,
+                      pc_handle** out) {
   if (!p || !out) return fail(PC_ERR_ARG, "pc_setup: null params or out pointer");
   *out = nullptr;
   if (p->dim != 2 && p->dim != 3) return fail(PC_ERR_ARG, "dim must be 2 or 3");
@@ -540,8 +595,7 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
   h->sqrtg = std::sqrt(p->gamma);
   h->h = 1.0 / (m1 + 1);
   h->spatial = spatial;
-  const int prec = p->precision == PC_PREC_AUTO ? (p->eps >= PC_AUTO_FP32_MIN_EPS ? PC_PREC_MIXED_FP32 : PC_PREC_FP64)
-                                                : p->precision;
+  const int prec = resolved_precision(p);
   h->prm.precision = prec;
   h->fp32 = prec != PC_PREC_FP64;
   h->bf16s = prec == PC_PREC_MIXED_BF16S && spatial == PC_SPATIAL_MG;
@@ -722,8 +776,16 @@ extern "C" int pc_setup(const pc_params* p, const double* a_nodes, void* stream,
     // basis: cap + 1 vectors; a double-float basis stores each as two FP32 planes in
     // tiles of 512 unknowns (the last tile padded), i.e. ceil(U/512) * 512 doubles per vector
     const size_t tiled = (U + 511) / 512 * 512;
-    if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * tiled))) goto fail_out;
-    if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
+    if (krylov) {
+      // V and Z in the caller's memory (checked by pc_setup_shared), Z after V
+      h->kws = static_cast<const unsigned char*>(krylov);
+      h->kws_bytes = krylov_bytes_of(U, cap, h->fp32);
+      h->V = static_cast<double*>(krylov);
+      h->Z = static_cast<unsigned char*>(krylov) + krylov_v_bytes(U, cap);
+    } else {
+      if ((rc = dev_alloc_t(h, &h->V, (size_t)(cap + 1) * tiled))) goto fail_out;
+      if ((rc = dev_alloc(h, &h->Z, (size_t)cap * U * (h->fp32 ? sizeof(float) : sizeof(double))))) goto fail_out;
+    }
     if (h->fp32 && (rc = dev_alloc_t(h, &h->vf32, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->wbuf, U))) goto fail_out;
     if ((rc = dev_alloc_t(h, &h->tbuf, U))) goto fail_out;
@@ -1901,6 +1963,12 @@ struct pc_batch {
   std::vector<cudaEvent_t> events;
 };
 
+// do two handles' Krylov workspaces (pc_setup_shared) share any byte?
+static bool krylov_overlap(const pc_handle* a, const pc_handle* b) {
+  if (!a->kws || !b->kws) return false;
+  return a->kws < b->kws + b->kws_bytes && b->kws < a->kws + a->kws_bytes;
+}
+
 static void batch_release(pc_batch* bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   for (auto e : bt->events) cudaEventDestroy(e);
@@ -1943,6 +2011,9 @@ extern "C" int pc_batch_create(pc_handle* const* hs, int count, const double* co
   for (int i = 0; e == cudaSuccess && rc == PC_OK && i < count; ++i) {
     // fork: the problem's capture stream joins the capture, then runs its own solve
     e = cudaStreamWaitEvent(hs[i]->cap_stream, bt->events[0], 0);
+    // a problem whose Krylov workspace overlaps an earlier problem's starts after it
+    for (int q = 0; e == cudaSuccess && q < i; ++q)
+      if (krylov_overlap(hs[q], hs[i])) e = cudaStreamWaitEvent(hs[i]->cap_stream, bt->events[1 + q], 0);
     if (e != cudaSuccess) break;
     rc = capture_solve(hs[i], b[i], x[i], rtol, maxit, hs[i]->cap_stream);
     if (rc) break;

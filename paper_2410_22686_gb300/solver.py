@@ -43,14 +43,18 @@ class Solver:
     def __init__(self, dim: int, m1: int, n: int, T: float, gamma: float, eps: float,
                  a_nodes: np.ndarray | None = None, spatial: str = "auto", precision: str = "fp64",
                  max_iter: int = 60, tiles: str | dict | None = "table", space: str = "fd",
-                 smoother: str = "red-black"):
+                 smoother: str = "red-black", krylov: torch.Tensor | None = None):
         """space: "fd" finite differences (M = I) or "fe" bilinear / trilinear finite
         elements (mass matrix M; constant a, sine-transform solves).
         smoother: Gauss-Seidel ordering of the multigrid pre-smoother, "red-black"
         (parallel) or "lexicographic" (the natural order: the paper's Table 7 counts).
         tiles: "table" applies the stored autotune table's entry for this shape
         (if any), "auto" runs the autotuner now, a dict sets the shapes, None keeps
-        the built-in defaults."""
+        the built-in defaults.
+        krylov: a CUDA uint8 tensor (view) holding the Krylov storage instead of the
+        handle's own (pc_setup_shared; at least krylov_bytes(...) bytes, 256-byte
+        aligned).  Handles whose storage overlaps must not solve at the same time; a
+        Batch orders them."""
         for name, val, table in (("spatial", spatial, _SPATIAL), ("precision", precision, _PREC),
                                  ("space", space, _SPACE), ("smoother", smoother, _SMOOTHER)):
             if val not in table:
@@ -72,7 +76,14 @@ class Solver:
                 raise ValueError("a_nodes must have (m1+2)^dim entries")
             a_ptr = self._a.ctypes.data_as(ctypes.c_void_p)
         h = ctypes.c_void_p()
-        capi.check(self.lib.pc_setup(ctypes.byref(prm), a_ptr, _stream(), ctypes.byref(h)))
+        if krylov is None:
+            capi.check(self.lib.pc_setup(ctypes.byref(prm), a_ptr, _stream(), ctypes.byref(h)))
+        else:
+            if not (krylov.is_cuda and krylov.dtype == torch.uint8 and krylov.dim() == 1 and krylov.is_contiguous()):
+                raise ValueError("krylov must be a contiguous 1-D uint8 CUDA tensor")
+            self._krylov = krylov  # the handle borrows it
+            capi.check(self.lib.pc_setup_shared(ctypes.byref(prm), a_ptr, ctypes.c_void_p(krylov.data_ptr()),
+                                                krylov.numel(), _stream(), ctypes.byref(h)))
         self.h = h
         self.ms = m1 ** dim
         self.vec_len = 2 * n * self.ms
@@ -338,6 +349,35 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.pc_launch_count(self.h))
+
+
+def krylov_bytes(dim: int, m1: int, n: int, eps: float, precision: str = "fp64", max_iter: int = 60) -> int:
+    """Bytes of the Krylov storage of a handle with these parameters (pc_krylov_bytes)."""
+    if precision not in _PREC:
+        raise ValueError(f"precision must be one of {sorted(_PREC)}, got {precision!r}")
+    lib = capi.load()
+    prm = capi.pc_params(dim, m1, n, 1.0, 1.0, eps, capi.PC_SPATIAL_AUTO, _PREC[precision], max_iter,
+                         capi.PC_SPACE_FD, capi.PC_SMOOTHER_RED_BLACK)
+    out = ctypes.c_size_t(0)
+    capi.check(lib.pc_krylov_bytes(ctypes.byref(prm), ctypes.byref(out)))
+    return int(out.value)
+
+
+def pack_krylov(sizes, pool_bytes: int, align: int = 256):
+    """Offsets of Krylov storages of the given sizes in one pool: in order, side by
+    side until the pool is full, then again from the start (the next memory wave).
+    Storages of one wave never overlap; a storage of a later wave overlaps those of
+    earlier waves that share its bytes, and a Batch runs it after them."""
+    offsets, cur = [], 0
+    for b in sizes:
+        need = (int(b) + align - 1) // align * align
+        if need > pool_bytes:
+            raise ValueError(f"a Krylov storage of {b} bytes does not fit a pool of {pool_bytes}")
+        if cur + need > pool_bytes:
+            cur = 0
+        offsets.append(cur)
+        cur += need
+    return offsets
 
 
 def measure_peaks():

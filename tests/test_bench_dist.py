@@ -187,14 +187,19 @@ def test_batched_extra_logic_with_fake_solvers(monkeypatch):
 
     monkeypatch.setattr(pkg, "Solver", FakeSolver)
     monkeypatch.setattr(pkg, "Batch", FakeBatch)
+    # Krylov storage of 1000 bytes per problem in a pool of 10 KB: several memory waves
+    monkeypatch.setattr(pkg, "krylov_bytes", lambda *a, **k: 1000)
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a, **k: (400e9, 400e9))
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
     args = types.SimpleNamespace(skip_3d=True, skip_fst=True, skip_fe_var=True, skip_grad=True, skip_batched=False, skip_ideal=True,
-                                 batch_gb=110.0)
+                                 batch_gb=1e-5)
     out = bench._extra_workloads(args, torch, "cpu")["batched_64"]
     assert out["problems"] == 64 and out["ranks"] == 1 and out["converged"] == 64 and out["max_iters"] == 7
-    assert out["waves"] >= 1 and out["batch_seconds"] >= 0.0
+    assert out["graph_launches"] == 1 and out["batch_seconds"] >= 0.0
+    # 64 storages of 1024 bytes (256-byte aligned) in a 10000-byte pool: 9 per wave
+    assert out["memory_waves"] == 8 and out["krylov_pool_gb"] == 1e-5
     assert out["total_unknowns"] == sum(q.unknowns for q in synthetic.batched_problems(64))
 
 
