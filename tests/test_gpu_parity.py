@@ -144,6 +144,41 @@ def _oracle_solution(prob, spatial, rtol=1e-13):
     return b, A, Pi, okr.gmres(A, Pi, b, rtol=rtol, maxit=200, mode="right")
 
 
+# The largest lengths and grids the library takes: n = 2048 and 4096 time blocks (the
+# time transforms beyond the register FFTs: FP32 above 1024, FP64 above 256), a
+# 1023^2 multigrid (ten levels) and a 2047^2 sine-transform grid
+LARGEST_CASES = [(2, 3, 4096, "var", "mg"), (2, 7, 2048, "const", "fst"), (3, 3, 4096, "var", "mg"),
+                 (2, 1023, 2, "var", "mg"), (2, 2047, 1, "const", "fst")]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("d,m1,n,kind,spatial", LARGEST_CASES)
+def test_precond_and_matvec_at_the_largest_sizes(d, m1, n, kind, spatial, precision, tol):
+    a = _coef(d, m1, kind, seed=7 * m1 + n)
+    gamma, eps = 1e-4, 0.25
+    sol = _solver(d, m1, n, a, spatial, precision=precision, gamma=gamma, eps=eps, max_iter=4)
+    v = S.random_vector((2, n) + (m1,) * d, 17)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, opc.make_spatial_solver(spatial, a, m1, d, tau))
+    assert _rel(w, ref) <= tol
+    y = sol.matvec(_dev(v)).cpu().numpy()
+    assert _rel(y, osy.apply_A(v, _a_or_one(a, d, m1), tau, alpha)) <= 1e-12
+    sol.close()
+
+
+def test_solve_at_the_largest_n_matches_oracle():
+    prob = S.variable_2d_problem(gamma=1e-4, m1=3, n=4096)
+    b, A, Pi, ref = _oracle_solution(prob, "mg")
+    for precision, rtol, tol in (("fp64", 1e-12, 1e-10), ("fp32", 1e-10, 1e-7)):
+        sol = _solver(2, 3, 4096, prob.a_nodes, "mg", precision=precision, gamma=prob.gamma, eps=prob.eps,
+                      max_iter=60)
+        x, iters, rel = sol.solve(_dev(b), rtol=rtol)
+        assert rel <= rtol
+        assert np.linalg.norm(x.cpu().numpy() - ref.x) <= tol * np.linalg.norm(ref.x)
+        sol.close()
+
+
 @pytest.mark.parametrize("case", ["plain", "variable", "variable3d"])
 def test_fp64_gmres_solution_matches_oracle(case):
     if case == "plain":
