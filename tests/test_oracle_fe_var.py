@@ -228,3 +228,114 @@ def test_gradient_routes_agree_with_finite_differences_of_the_optimum():
     dg = S.random_vector(g0.shape, 31)
     fd = (J(a0, g0 + h * dg) - J(a0, g0 - h * dg)) / (2 * h)
     assert abs(fd - float(np.sum(eg * dg))) <= 1e-6 * abs(fd)
+
+
+# ---------------------------------------------------------------------------
+# trilinear elements with a nodal coefficient (3D)
+# ---------------------------------------------------------------------------
+
+def test_trilinear_element_matrices_have_the_closed_form_entries():
+    # K_e = h/12 [4, 0, -1, -1] and M_e = h^3/216 [8, 4, 2, 1] for corners differing in
+    # 0, 1, 2, 3 coordinates (the tensor products of the 1D element matrices)
+    m1 = 3
+    h = 1 / (m1 + 1)
+    corners, Me, Ke = fe.reference_element(m1, 3)
+    kv, mv = [4.0, 0.0, -1.0, -1.0], [8.0, 4.0, 2.0, 1.0]
+    for p, cp in enumerate(corners):
+        for q, cq in enumerate(corners):
+            t = sum(a != b for a, b in zip(cp, cq))
+            assert abs(Ke[p, q] - h / 12 * kv[t]) < 1e-15
+            assert abs(Me[p, q] - h ** 3 / 216 * mv[t]) < 1e-17
+
+
+def test_variable_coefficient_solution_is_second_order_in_3d():
+    # -div(a grad u) = f, u = sin(pi x1) sin(pi x2) sin(pi x3), a = 1 + x1 x3 + x2^2 / 2
+    def err(m1):
+        h = 1 / (m1 + 1)
+        xn = np.arange(m1 + 2) * h
+        X3, X2, X1 = np.meshgrid(xn, xn, xn, indexing="ij")
+        a = 1 + X1 * X3 + 0.5 * X2 ** 2
+        xi = xn[1:-1]
+        Y3, Y2, Y1 = np.meshgrid(xi, xi, xi, indexing="ij")
+        s = [np.sin(np.pi * Y) for Y in (Y1, Y2, Y3)]
+        c = [np.cos(np.pi * Y) for Y in (Y1, Y2, Y3)]
+        aa = 1 + Y1 * Y3 + 0.5 * Y2 ** 2
+        da = (Y3, Y2, Y1)                        # da/dx1, da/dx2, da/dx3
+        u = s[0] * s[1] * s[2]
+        grad = (np.pi * c[0] * s[1] * s[2], np.pi * s[0] * c[1] * s[2], np.pi * s[0] * s[1] * c[2])
+        f = 3 * np.pi ** 2 * aa * u - sum(dk * gk for dk, gk in zip(da, grad))
+        M, K = fe.fe_matrices_var(a)
+        uh = spla.spsolve(K.tocsc(), M @ f.ravel())
+        return np.abs(uh - u.ravel()).max()
+
+    e1, e2 = err(7), err(15)
+    assert 3.3 < e1 / e2 < 4.8, (e1, e2)
+
+
+def test_stiffness_derivative_equals_central_differences_in_3d():
+    m1, d = 3, 3
+    a = np.exp(0.3 * S.random_vector((m1 + 2,) * d, 32))
+    u = S.random_vector((2, m1, m1, m1), 33)
+    v = S.random_vector((2, m1, m1, m1), 34)
+    Sd = fe.stiffness_derivative(u, v, a)
+
+    def form(ax):
+        _, K = fe.fe_matrices_var(ax)
+        return sum(float(u[t].ravel() @ (K @ v[t].ravel())) for t in range(2))
+
+    h = 1e-6
+    for P in [(1, 1, 1), (2, 3, 1), (3, 3, 3), (1, 2, 3)]:
+        ap, am = a.copy(), a.copy()
+        ap[P] *= math.exp(h)
+        am[P] *= math.exp(-h)
+        fd = (form(ap) - form(am)) / (2 * h)
+        assert abs(fd - Sd[P[0] - 1, P[1] - 1, P[2] - 1]) <= 1e-7 * abs(fd)
+
+
+def _vcycle_by_loops_d(a_nodes, tau, sigma, r):
+    """_vcycle_by_loops for any dimension: Gauss-Seidel over the 2^d colours in order."""
+    d = a_nodes.ndim
+    m = a_nodes.shape[0] - 2
+    M, K = fe.fe_matrices_var(a_nodes)
+    A = sigma * M.toarray() + tau * K.toarray()
+    N = m ** d
+    if m == 1:
+        return r / A[0, 0]
+    col = fe.colour_of(m, d).ravel()
+    u = np.zeros(N, dtype=complex)
+    for c in range(2 ** d):
+        for pnt in range(N):
+            if col[pnt] != c:
+                continue
+            u[pnt] = (r[pnt] - sum(A[pnt, q] * u[q] for q in range(N) if q != pnt)) / A[pnt, pnt]
+    res = r - A @ u
+    P = _prolongation_matrix((m - 1) // 2, d)
+    ec = _vcycle_by_loops_d(a_nodes[(slice(None, None, 2),) * d], tau, sigma, P.T @ res)
+    return u + P @ ec
+
+
+def test_vcycle_equals_the_point_by_point_cycle_in_3d():
+    m1 = 3
+    a = np.exp(0.4 * S.random_vector((m1 + 2,) * 3, 35))
+    tau = 0.05
+    mg = fe.MGSpatialSolverFE(a, tau)
+    sig = np.array([0.7 + 0.4j, 1e-2 + 0.3j])
+    r = S.random_vector((2, m1, m1, m1), 36) + 1j * S.random_vector((2, m1, m1, m1), 37)
+    got = mg(sig, r)
+    for k in range(2):
+        ref = _vcycle_by_loops_d(a, tau, sig[k], r[k].ravel())
+        assert np.abs(got[k].ravel() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_preconditioned_gmres_converges_in_few_iterations_in_3d():
+    m1, n, gamma = 7, 8, 1e-3
+    a = np.exp(0.4 * S.random_vector((m1 + 2,) * 3, 38))
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    M, K = fe.fe_matrices_var(a)
+    mg = fe.MGSpatialSolverFE(a, tau)
+    b = fe.build_rhs(S.random_vector((n, m1, m1, m1), 39), S.random_vector((n, m1, m1, m1), 40),
+                     S.random_vector((m1, m1, m1), 41), tau, gamma, M)
+    res = okr.gmres(lambda v: fe.apply_A(v, M, K, tau, alpha),
+                    lambda v: opc.apply_Peps_inv(v, n, alpha, math.sqrt(tau), mg), b, rtol=1e-10, maxit=80,
+                    mode="right")
+    assert res.converged and res.iters <= 40
