@@ -448,34 +448,41 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
                                          "fe": "bilinear finite elements (mass matrix M)", **res}
 
     if not args.skip_fe_var:
-        # variable a with bilinear elements: the element multigrid inside P_eps^{-1}
-        p = S.variable_2d_problem(gamma=1e-4, m1=M1, n=NT)
-        res = {}
-        for prec in ("fp32", "fp64"):
-            sol = Solver(2, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision=prec, max_iter=80,
-                         space="fe")
-            b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
-                              torch.from_numpy(p.y0).to(dev))
-            t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
-            res[prec] = {"solve_s": t, "iters": r[1], "relres": r[2]}
-            if prec == "fp32":  # per-kernel CUDA-event breakdown of one more solve
-                sol.stats_reset()
-                sol.profile(True)
-                sol.solve(b, rtol=RTOL, raise_on_nonconv=False)
-                torch.cuda.synchronize()
-                sol.profile(False)
-                st = sol.stats()
-                tot = sum(v["ms"] for v in st.values()) or 1.0
-                res[prec]["kernel_breakdown"] = {
-                    k: {"share": v["ms"] / tot, "avg_us": 1000 * v["ms"] / v["launches"],
-                        "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None}
-                    for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8] if v["launches"]}
-            sol.close()
-            del b
-            torch.cuda.empty_cache()
-        out["fe_var_255sq_n256"] = {"data": "benchmark fields (variable a), gamma 1e-4, eps = sqrt(tau)",
-                                    "discretisation": "bilinear elements, element coefficient = mean of its "
-                                                      "corner values; colour-ordered element multigrid", **res}
+        # a nodal coefficient with bilinear (2D) and trilinear (3D) elements: the element
+        # multigrid inside P_eps^{-1}, on the benchmark fields and on the 3D random field
+        cases = (("fe_var_255sq_n256", S.variable_2d_problem(gamma=1e-4, m1=M1, n=NT),
+                  "benchmark fields (variable a), gamma 1e-4, eps = sqrt(tau)",
+                  "bilinear elements, element coefficient = mean of its corner values; colour-ordered element "
+                  "multigrid (4 colours)"),
+                 ("fe_var_3d_63cubed_n128", S.gaussian_field_3d_problem(),
+                  "3D random-field coefficient of the 63^3 x 128 workload, gamma 1e-4, eps = sqrt(tau)",
+                  "trilinear elements, element coefficient = mean of its corner values; colour-ordered element "
+                  "multigrid (8 colours); element products in FP64 arithmetic"))
+        for key, p, data, disc in cases:
+            res = {}
+            for prec in ("fp32", "fp64"):
+                sol = Solver(p.d, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision=prec,
+                             max_iter=80, space="fe")
+                b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
+                                  torch.from_numpy(p.y0).to(dev))
+                t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 2)
+                res[prec] = {"solve_s": t, "iters": r[1], "relres": r[2]}
+                if prec == "fp32":  # per-kernel CUDA-event breakdown of one more solve
+                    sol.stats_reset()
+                    sol.profile(True)
+                    sol.solve(b, rtol=RTOL, raise_on_nonconv=False)
+                    torch.cuda.synchronize()
+                    sol.profile(False)
+                    st = sol.stats()
+                    tot = sum(v["ms"] for v in st.values()) or 1.0
+                    res[prec]["kernel_breakdown"] = {
+                        k: {"share": v["ms"] / tot, "avg_us": 1000 * v["ms"] / v["launches"],
+                            "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None}
+                        for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8] if v["launches"]}
+                sol.close()
+                del b
+                torch.cuda.empty_cache()
+            out[key] = {"data": data, "discretisation": disc, **res}
 
     if not args.skip_grad:
         p = S.gradient_problem()

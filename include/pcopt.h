@@ -148,14 +148,18 @@ typedef struct pc_handle pc_handle;
  *            and >= 0 at boundary nodes.
  *   stream:  stream used for the coefficient upload.
  *   out:     receives the handle (caller releases it with pc_destroy).
- * With space = PC_SPACE_FE the matrices are the bilinear / trilinear element
- * matrices of the uniform grid (M = (h/6)^dim [1 4 1]^(x)dim,
- * K = a (h/6)^(dim-1)/h sum_axes [-1 2 -1] (x) [1 4 1]..), every spatial solve
- * (sigma M + tau K) z = r is exact by sine transforms, and a must be constant.
+ * With space = PC_SPACE_FE the matrices are the bilinear (2D) / trilinear (3D)
+ * element matrices of the uniform grid with the consistent mass matrix
+ * (M = (h/6)^dim [1 4 1]^(x)dim).  A constant a gives
+ * K = a (h/6)^(dim-1)/h sum_axes [-1 2 -1] (x) [1 4 1].., and with the
+ * sine-transform solver every spatial solve (sigma M + tau K) z = r is exact; a
+ * nodal a gives K(a) = sum_e a_e K_e (a_e the mean of element e's corner values,
+ * a 9-point stencil in 2D, 27-point in 3D), solved inside P_eps^{-1} by one
+ * V(1,0) cycle of the element multigrid (Gauss-Seidel in 2^dim colours).
  * Errors: PC_ERR_ARG (dim not 2/3, m1 < 1, n outside 1..4096,
  * T <= 0, gamma <= 0, eps outside (0,1], a not as above, FST with non-constant a,
- * MG with m1 != 2^k-1, unknown space), PC_ERR_UNSUPPORTED (finite elements with a
- * non-constant a or multigrid), PC_ERR_OOM, PC_ERR_CUDA. */
+ * MG with m1 != 2^k-1, unknown space), PC_ERR_UNSUPPORTED (finite elements with
+ * the natural-order smoother or BF16 storage), PC_ERR_OOM, PC_ERR_CUDA. */
 int pc_setup(const pc_params* params, const double* a_nodes, void* stream, pc_handle** out);
 
 /* Bytes of the Krylov storage a handle built from `params` needs: the basis of
@@ -203,8 +207,8 @@ int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* stream);
  *   log_a: device, ms = m1^dim FP64, interior nodes in vector ordering.  The
  *          values must be finite (exp of them is the coefficient; no device-side
  *          check: NaN or Inf surfaces later as PC_ERR_BREAKDOWN of a solve).
- * Errors: PC_ERR_ARG (null), PC_ERR_UNSUPPORTED (sine-transform or finite-element
- * handles, whose coefficient must stay constant). */
+ * Errors: PC_ERR_ARG (null), PC_ERR_UNSUPPORTED (sine-transform handles, whose
+ * coefficient must stay constant). */
 int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* stream);
 
 /* Select the preconditioner used by pc_apply_precond, pc_gmres_solve and
@@ -331,23 +335,26 @@ int pc_adjoint_solve(pc_handle* h, const double* c, double* lam, double rtol, in
  *   grad_P = -tau * sum_j [ lam1_j^T (dK/dlog a_P) x2_j - lam2_j^T (dK/dlog a_P) x1_j ],
  *   u^T (dK/dlog a_P) v = a_P/(2h^2) sum_{faces (P,Q)} (u_P-u_Q)(v_P-v_Q),
  * i.e. -lam^T (dA/dlog a_P) x for interior nodes P (boundary nodes fixed).
- * Finite-difference handles only (PC_ERR_UNSUPPORTED for finite elements).
+ * Finite elements: u^T (dK/dlog a_P) v = a_P / 2^dim sum over the 2^dim elements
+ * e around P of u_e^T K_e v_e (K_e the element stiffness of a = 1).
  *   x, lam: device all-at-once vectors; grad: device, ms FP64 (interior nodes,
  *   same spatial ordering), overwritten. */
 int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream);
 
 /* Gradient with respect to the target g of a scalar L(x) through the solve
  * (b1_j = tau g_j in Eq. main_system): given the adjoint lam = A^{-T} dL/dx,
- *   grad_g[j][s] = tau * lam1[j][s],  j = 1..n (the first half of lam).
- *   lam: device all-at-once vector; grad_g: device, n*ms FP64, overwritten.
- * Finite-difference handles only (PC_ERR_UNSUPPORTED for finite elements). */
+ *   grad_g[j][s] = tau * lam1[j][s],  j = 1..n (the first half of lam);
+ * finite elements (b1_j = tau M g_j): grad_g[j] = tau M lam1[j].
+ *   lam: device all-at-once vector; grad_g: device, n*ms FP64, overwritten. */
 int pc_grad_g(pc_handle* h, const double* lam, double* grad_g, void* stream);
 
 /* The discrete tracking objective (Eq. Cost_functional_heat on the grid, with
  * u = p/gamma):
  *   J_h = h^d tau [ 1/2 sum_{j=1..n} ||y_j - g_j||^2 + 1/(2 gamma) sum_{j=1..n} ||p_j||^2 ],
  * y = x1/sqrt(gamma), p = x2; the optimality system of Eq. main_system is its
- * KKT system.  x: device all-at-once vector; g: device, n*ms; J: device, one
+ * KKT system.  Finite elements: h^d I replaced by the mass matrix M,
+ * J_h = tau [1/2 sum (y_j - g_j)^T M (y_j - g_j) + 1/(2 gamma) sum p_j^T M p_j].
+ * x: device all-at-once vector; g: device, n*ms; J: device, one
  * FP64, written asynchronously (deterministic reduction order).  Uses the
  * handle's reduction scratch: do not overlap with a solve on the same handle. */
 int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void* stream);
@@ -355,6 +362,7 @@ int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void
 /* Gradient of J_h (pc_objective) times the scalar *gJ (device; NULL means 1):
  *   gx1 = gJ h^d tau (y - g)/sqrt(gamma),  gx2 = gJ h^d tau p/gamma   (dJ/dx)
  *   gg  = -gJ h^d tau (y - g)                                          (explicit dJ/dg)
+ * (finite elements: h^d replaced by M applied to each time block).
  * gx: device all-at-once vector or NULL; gg: device n*ms or NULL (not both). */
 int pc_objective_grad(pc_handle* h, const double* x, const double* g, const double* gJ, double* gx, double* gg,
                       void* stream);

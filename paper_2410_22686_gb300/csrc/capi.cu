@@ -169,8 +169,8 @@ struct pc_handle {
   int cap = 0;
   double a_const = 1.0;
   bool fe = false;  // finite elements in space (mass matrix M)
-  bool fevar = false;  // 2D elements solved by the element multigrid (any nodal coefficient)
-  double* fe_gpart = nullptr;  // 2D elements: per-element partial sums of the stiffness derivative
+  bool fevar = false;  // elements solved by the element multigrid (any nodal coefficient)
+  double* fe_gpart = nullptr;  // elements: per-element partial sums of the stiffness derivative
   bool lex = false;  // multigrid smoother in the natural order (per-level kernels on every level)
   FeScale fes;
 
@@ -432,25 +432,34 @@ static int upload(pc_handle* h, T** dst, const std::vector<double>& src, cudaStr
 // face weights [4][np] (2D) packed per point for one-load access
 // element coefficients of every multigrid level (2D): level l+1 takes level l's nodal
 // values at even grid nodes (injection); an element gets the mean of its corner values
-static std::vector<std::vector<double>> fe_level_elements(const std::vector<double>& a, int m1, int nlev) {
+static std::vector<std::vector<double>> fe_level_elements(const std::vector<double>& a, int m1, int dim, int nlev) {
+  // element value = mean of its 2^dim corner values; a: (m+2)^dim nodes, x1 fastest
   std::vector<std::vector<double>> out;
-  std::vector<double> acur = a;  // (m+2)^2 nodes, x1 fastest
+  std::vector<double> acur = a;
   int m = m1;
   for (int l = 0; l < nlev; ++l) {
-    const int Mn = m + 2, me = m + 1;
-    std::vector<double> E((size_t)me * me);
-    for (int k2 = 0; k2 < me; ++k2)
-      for (int k1 = 0; k1 < me; ++k1)
-        E[(size_t)k2 * me + k1] = 0.25 * (acur[(size_t)k2 * Mn + k1] + acur[(size_t)k2 * Mn + k1 + 1] +
-                                          acur[(size_t)(k2 + 1) * Mn + k1] + acur[(size_t)(k2 + 1) * Mn + k1 + 1]);
+    const size_t Mn = (size_t)m + 2, me = (size_t)m + 1;
+    const size_t ne = dim == 2 ? me * me : me * me * me;
+    std::vector<double> E(ne);
+    for (size_t el = 0; el < ne; ++el) {
+      const size_t k1 = el % me, k2 = (el / me) % me, k3 = dim == 2 ? 0 : el / (me * me);
+      double v = 0.0;
+      for (int c = 0; c < (1 << dim); ++c) {
+        const size_t n1 = k1 + (c & 1), n2 = k2 + ((c >> 1) & 1), n3 = dim == 2 ? 0 : k3 + (c >> 2);
+        v += acur[(n3 * Mn + n2) * Mn + n1];
+      }
+      E[el] = v / (1 << dim);
+    }
     out.push_back(std::move(E));
     if (l + 1 == nlev) break;
-    const int mc = (m - 1) / 2, Mc = mc + 2;
-    std::vector<double> ac((size_t)Mc * Mc);
-    for (int J = 0; J < Mc; ++J)
-      for (int I = 0; I < Mc; ++I) ac[(size_t)J * Mc + I] = acur[(size_t)(2 * J) * Mn + 2 * I];
+    const size_t mc = ((size_t)m - 1) / 2, Mc = mc + 2;
+    std::vector<double> ac(dim == 2 ? Mc * Mc : Mc * Mc * Mc);
+    for (size_t q = 0; q < ac.size(); ++q) {
+      const size_t I = q % Mc, J = (q / Mc) % Mc, K = dim == 2 ? 0 : q / (Mc * Mc);
+      ac[q] = acur[((2 * K) * Mn + 2 * J) * Mn + 2 * I];
+    }
     acur.swap(ac);
-    m = mc;
+    m = (int)mc;
   }
   return out;
 }
@@ -567,9 +576,6 @@ static int setup_impl(const pc_params* p, const double* a_nodes, void* krylov, s
   }
   int spatial = p->spatial;
   const bool fe = p->space == PC_SPACE_FE;
-  if (fe && dim == 3 && (!constant || spatial == PC_SPATIAL_MG))
-    return fail(PC_ERR_UNSUPPORTED, "3D finite elements: implemented for a constant coefficient with sine-transform "
-                                    "solves");
   if (fe && p->smoother == PC_SMOOTHER_LEXICOGRAPHIC)
     return fail(PC_ERR_UNSUPPORTED, "finite elements: the element multigrid smooths in colour order only");
   if (fe && p->precision == PC_PREC_MIXED_BF16S && (!constant || spatial == PC_SPATIAL_MG))
@@ -617,7 +623,7 @@ static int setup_impl(const pc_params* p, const double* a_nodes, void* krylov, s
     std::vector<int> mlev;
     all_level_stencils(a, m1, dim, h->tau, spatial == PC_SPATIAL_MG, ws, ds, mlev);
     const std::vector<std::vector<double>> els =
-        h->fevar ? fe_level_elements(a, m1, (int)mlev.size()) : std::vector<std::vector<double>>();
+        h->fevar ? fe_level_elements(a, m1, dim, (int)mlev.size()) : std::vector<std::vector<double>>();
     for (size_t l = 0; l < mlev.size(); ++l) {
       LevelBuf L;
       L.m = mlev[l];
@@ -765,7 +771,8 @@ static int setup_impl(const pc_params* p, const double* a_nodes, void* krylov, s
     if ((rc = upload(h, &h->a_nodes_dev, a, st))) goto fail_out;
     const int nch = (h->n + h->grad_tj - 1) / h->grad_tj;
     if ((rc = dev_alloc_t(h, &h->grad_partial, (size_t)nch * h->ms))) goto fail_out;
-    if (fe && dim == 2 && (rc = dev_alloc_t(h, &h->fe_gpart, (size_t)kFeGradChunks * (m1 + 1) * (m1 + 1))))
+    if (fe && (rc = dev_alloc_t(h, &h->fe_gpart, (size_t)kFeGradChunks * (m1 + 1) * (m1 + 1) *
+                                                   (dim == 3 ? (size_t)(m1 + 1) : 1))))
       goto fail_out;
   }
   // ---- Krylov workspace
@@ -877,7 +884,7 @@ extern "C" int pc_set_coefficient(pc_handle* h, const double* a_nodes, void* str
     }
   }
   if (h->fevar) {
-    const std::vector<std::vector<double>> els = fe_level_elements(a, m1, (int)mlev.size());
+    const std::vector<std::vector<double>> els = fe_level_elements(a, m1, dim, (int)mlev.size());
     for (size_t l = 0; l < mlev.size(); ++l) {
       if ((rc = refill(h->lv[l].e64, els[l], st, s64))) return rc;
       if ((rc = refill(h->lv[l].e32, els[l], st, s32))) return rc;
@@ -918,7 +925,9 @@ extern "C" int pc_set_log_coefficient(pc_handle* h, const double* log_a, void* s
   if (h->fevar) {
     int st = 1;
     for (size_t l = 0; l < h->lv.size() && e == cudaSuccess; ++l, st *= 2)
-      e = launch_fevar_level_elements(L, h->a_nodes_dev, h->m1 + 2, st, h->lv[l].m, h->lv[l].e64, h->lv[l].e32);
+      e = h->dim == 3
+              ? launch_fevar3_level_elements(L, h->a_nodes_dev, h->m1 + 2, st, h->lv[l].m, h->lv[l].e64, h->lv[l].e32)
+              : launch_fevar_level_elements(L, h->a_nodes_dev, h->m1 + 2, st, h->lv[l].m, h->lv[l].e64, h->lv[l].e32);
     return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_set_log_coefficient");
   }
   int stride = 1;
@@ -1003,9 +1012,10 @@ const double* lve<double>(const LevelBuf& L) { return L.e64; }
 template <>
 const float* lve<float>(const LevelBuf& L) { return L.e32; }
 
-// element multigrid, 2D (k_fevar.cu): on every level a colour-ordered Gauss-Seidel
-// sweep from zero, residual and restriction by P^T; the one-point level is solved by
-// its sweep; then the bilinear corrections from the coarsest level up
+// element multigrid (k_fevar.cu in 2D, k_fevar3.cu in 3D): on every level a
+// colour-ordered Gauss-Seidel sweep from zero, residual and restriction by P^T; the
+// one-point level is solved by its sweep; then the (bi/tri)linear corrections from the
+// coarsest level up
 template <typename Tc>
 static cudaError_t fevar_spatial(pc_handle* h, Launch& L, int P, const typename Cx<Tc>::t* sig) {
   typedef typename Cx<Tc>::t C;
@@ -1016,12 +1026,15 @@ static cudaError_t fevar_spatial(pc_handle* h, Launch& L, int P, const typename 
     const LevelBuf& B = h->lv[l];
     const Tc hl = Tc(1) / Tc(B.m + 1);
     const Tc* E = lve<Tc>(B);
-    if ((e = launch_fevar_smooth<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r, (C*)B.u)) != cudaSuccess)
-      return e;
+    e = h->dim == 3 ? launch_fevar3_smooth<Tc>(L, B.m, P, hl, tau, E, sig, (const C*)B.r, (C*)B.u)
+                    : launch_fevar_smooth<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r, (C*)B.u);
+    if (e != cudaSuccess) return e;
     if (l + 1 == nl) break;
-    if ((e = launch_fevar_resid_restrict<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r, (const C*)B.u,
-                                             (C*)B.res, (C*)h->lv[l + 1].r)) != cudaSuccess)
-      return e;
+    e = h->dim == 3 ? launch_fevar3_resid_restrict<Tc>(L, B.m, P, hl, tau, E, sig, (const C*)B.r, (const C*)B.u,
+                                                       (C*)B.res, (C*)h->lv[l + 1].r)
+                    : launch_fevar_resid_restrict<Tc>(L, B.m, P, hl * hl, tau, E, sig, (const C*)B.r,
+                                                      (const C*)B.u, (C*)B.res, (C*)h->lv[l + 1].r);
+    if (e != cudaSuccess) return e;
   }
   for (int l = nl - 2; l >= 0; --l)
     if ((e = launch_mg_prolong<Tc, C>(L, grid_of(h, l), P, (const C*)h->lv[l + 1].u, (C*)h->lv[l].u)) != cudaSuccess)
@@ -1259,6 +1272,11 @@ static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32
   const Grid g = grid_of(h, 0);
   if (h->fevar) {
     const double h2 = h->h * h->h;
+    if (h->dim == 3)
+      return x_f32 ? launch_matvec_fevar3<float>(L, h->m1, h->n, h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                 (const float*)x, y, transpose)
+                   : launch_matvec_fevar3<double>(L, h->m1, h->n, h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                  (const double*)x, y, transpose);
     if (x_f32)
       return launch_matvec_fevar<float>(L, h->m1, h->n, h2, h->alpha, h->tau, h->lv[0].e64, (const float*)x, y,
                                         transpose);
@@ -1279,6 +1297,11 @@ static cudaError_t matvec_any(pc_handle* h, Launch& L, const void* x, bool x_f32
 static cudaError_t matvec_basis(pc_handle* h, Launch& L, const void* z, double* y, size_t zs = 0, size_t ys = 0,
                                 const int* jdev = nullptr) {
   const Grid g = grid_of(h, 0);
+  if (h->fevar && h->dim == 3)
+    return h->fp32 ? launch_matvec_fevar3<float>(L, h->m1, h->n, h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                 (const float*)z, y, false, zs, ys, jdev)
+                   : launch_matvec_fevar3<double>(L, h->m1, h->n, h->h, h->alpha, h->tau, h->lv[0].e64,
+                                                  (const double*)z, y, false, zs, ys, jdev);
   if (h->fevar)
     return h->fp32 ? launch_matvec_fevar<float>(L, h->m1, h->n, h->h * h->h, h->alpha, h->tau, h->lv[0].e64,
                                                 (const float*)z, y, false, zs, ys, jdev)
@@ -1353,11 +1376,13 @@ extern "C" int pc_build_rhs(pc_handle* h, const double* f, const double* g, cons
 
 extern "C" int pc_grad_log_a(pc_handle* h, const double* x, const double* lam, double* grad, void* stream) {
   if (!h || !x || !lam || !grad) return fail(PC_ERR_ARG, "pc_grad_log_a: null argument");
-  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_grad_log_a: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   if (h->fe) {
-    // -tau a_P / 4 sum over P's elements and the time blocks of (lam1^T K_e x2 - lam2^T K_e x1)
-    cudaError_t e = launch_fevar_grad(L, h->m1, h->n, h->tau, h->a_int, x, lam, h->fe_gpart, kFeGradChunks, grad);
+    // -tau a_P / 2^d sum over P's elements and the time blocks of (lam1^T K_e x2 - lam2^T K_e x1)
+    cudaError_t e =
+        h->dim == 3
+            ? launch_fevar3_grad(L, h->m1, h->n, h->h, h->tau, h->a_int, x, lam, h->fe_gpart, kFeGradChunks, grad)
+            : launch_fevar_grad(L, h->m1, h->n, h->tau, h->a_int, x, lam, h->fe_gpart, kFeGradChunks, grad);
     return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_grad_log_a");
   }
   // -tau * a_P / (2 h^2) * sum_j sum_faces [...]
@@ -1383,11 +1408,12 @@ static double objective_weight(const pc_handle* h) { return std::pow(h->h, h->di
 
 extern "C" int pc_objective(pc_handle* h, const double* x, const double* g, double* J, void* stream) {
   if (!h || !x || !g || !J) return fail(PC_ERR_ARG, "pc_objective: null argument");
-  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_objective: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   if (h->fe) {  // tau [1/2 sum e^T M e + 1/(2 gamma) sum p^T M p]
-    cudaError_t e = launch_fevar_objective(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g, h->partial,
-                                           h->nblocks * (h->cap + 2), J);
+    cudaError_t e = h->dim == 3 ? launch_fevar3_objective(L, h->m1, h->n, h->h, h->tau, h->prm.gamma, x, g,
+                                                          h->partial, h->nblocks * (h->cap + 2), J)
+                                : launch_fevar_objective(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g,
+                                                         h->partial, h->nblocks * (h->cap + 2), J);
     return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective");
   }
   cudaError_t e = launch_objective(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), h->partial,
@@ -1398,10 +1424,11 @@ extern "C" int pc_objective(pc_handle* h, const double* x, const double* g, doub
 extern "C" int pc_objective_grad(pc_handle* h, const double* x, const double* g, const double* gJ, double* gx,
                                  double* gg, void* stream) {
   if (!h || !x || !g || (!gx && !gg)) return fail(PC_ERR_ARG, "pc_objective_grad: null argument");
-  if (h->fe && h->dim != 2) return fail(PC_ERR_UNSUPPORTED, "pc_objective_grad: 3D finite elements");
   Launch L{(cudaStream_t)stream, &h->prof, &h->tiles};
   if (h->fe) {
-    cudaError_t e = launch_fevar_objective_grad(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g, gJ, gx, gg);
+    cudaError_t e =
+        h->dim == 3 ? launch_fevar3_objective_grad(L, h->m1, h->n, h->h, h->tau, h->prm.gamma, x, g, gJ, gx, gg)
+                    : launch_fevar_objective_grad(L, h->m1, h->n, h->h * h->h, h->tau, h->prm.gamma, x, g, gJ, gx, gg);
     return e == cudaSuccess ? PC_OK : cuda_fail(e, "pc_objective_grad");
   }
   cudaError_t e = launch_objective_grad(L, x, g, (int64_t)h->n * h->ms, h->prm.gamma, objective_weight(h), gJ, gx, gg);
@@ -2419,7 +2446,9 @@ static int pcg_E(pc_handle* h, Launch& L, const double* b, double* u, double rto
   if (bnorm == 0.0) return PC_OK;
   if (!std::isfinite(bnorm) || !std::isfinite(rz)) return fail(PC_ERR_BREAKDOWN, "end-point solve: non-finite input");
   for (int it = 1; it <= maxit; ++it) {
-    if (h->fevar)
+    if (h->fevar && h->dim == 3)
+      PC_CUDA(launch_fevar3_apply(L, h->m1, 1, h->h, h->lv[0].e64, 1.0, h->tau, p, 0.0, q));  // (M + tau K) p
+    else if (h->fevar)
       PC_CUDA(launch_fevar_apply(L, h->m1, 1, h->h * h->h, h->lv[0].e64, 1.0, h->tau, p, 0.0, q));  // (M + tau K) p
     else if (h->fe)
       PC_CUDA(launch_fe_apply(L, g, 1, h->fes.wM, h->tau * h->fes.wK, p, 0.0, q));  // (M + tau K) p

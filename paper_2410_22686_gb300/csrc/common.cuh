@@ -301,6 +301,32 @@ cudaError_t launch_fevar_objective(Launch& L, int m, int n, double h2, double ta
 cudaError_t launch_fevar_objective_grad(Launch& L, int m, int n, double h2, double tau, double gamma,
                                         const double* x, const double* g, const double* gJ, double* gx, double* gg);
 
+// 3D trilinear elements with a nodal coefficient (k_fevar3.cu): E holds one value per
+// element ((m+1)^3, the mean of its eight corner values), h = the level's mesh width
+cudaError_t launch_fevar3_apply(Launch& L, int m, int planes, double h, const double* E, double cM, double cK,
+                                const double* in, double beta, double* out);
+template <typename Tin>
+cudaError_t launch_matvec_fevar3(Launch& L, int m, int n, double h, double alpha, double tau, const double* E,
+                                 const Tin* x, double* y, bool transpose, size_t xstride = 0, size_t ystride = 0,
+                                 const int* jdev = nullptr);
+template <typename Tc>
+cudaError_t launch_fevar3_smooth(Launch& L, int m, int planes, Tc h, Tc tau, const Tc* E,
+                                 const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r, typename Cx<Tc>::t* u);
+template <typename Tc>
+cudaError_t launch_fevar3_resid_restrict(Launch& L, int m, int planes, Tc h, Tc tau, const Tc* E,
+                                         const typename Cx<Tc>::t* sigma, const typename Cx<Tc>::t* r,
+                                         const typename Cx<Tc>::t* u, typename Cx<Tc>::t* res,
+                                         typename Cx<Tc>::t* rc);
+cudaError_t launch_fevar3_level_elements(Launch& L, const double* a_nodes, int M0, int stride, int m, double* e64,
+                                         float* e32);
+cudaError_t launch_fevar3_grad(Launch& L, int m, int n, double h, double tau, const double* a_int, const double* x,
+                               const double* lam, double* part, int max_chunks, double* grad);
+cudaError_t launch_fevar3_objective(Launch& L, int m, int n, double h, double tau, double gamma, const double* x,
+                                    const double* g, double* partial, int max_partial, double* J);
+cudaError_t launch_fevar3_objective_grad(Launch& L, int m, int n, double h, double tau, double gamma,
+                                         const double* x, const double* g, const double* gJ, double* gx,
+                                         double* gg);
+
 // forward scaled time FFT: v (FP64 [2][n][ms]) -> spectral planes [2*nfreq][ms]
 // dpow[j] = eps^{j/n}, dinv[j] = eps^{-j/n}, tw[k] = exp(-2 pi i k/n) for k = 0..n-1
 // With jdev != nullptr the input is v + (*jdev) * vstride (device-resident Arnoldi index).

@@ -66,14 +66,14 @@ def test_status_strings_and_argument_errors_without_gpu():
         assert l.pc_setup(ctypes.byref(p), a.ctypes.data_as(ctypes.c_void_p), None,
                           ctypes.byref(h)) == capi.PC_ERR_ARG, (i, j, v)
         assert b"boundary" in l.pc_last_error()
-    # finite elements: the element multigrid is 2D, smooths in colour order only and has
-    # no BF16 storage; 3D elements take a constant coefficient and sine transforms
+    # finite elements: the element multigrid (2D and 3D) smooths in colour order only and
+    # has no BF16 storage
     a = np.ones((9, 9, 9))
     a[4, 4, 4] = 2.0
     a2 = np.ones((9, 9))
     a2[4, 4] = 2.0
-    for p, a_ptr in [(capi.pc_params(3, 7, 8, 1.0, 1e-2, 0.5, 2, 0, 10, 1), None),
-                     (capi.pc_params(3, 7, 8, 1.0, 1e-2, 0.5, 0, 0, 10, 1), a.ctypes.data_as(ctypes.c_void_p)),
+    for p, a_ptr in [(capi.pc_params(3, 7, 8, 1.0, 1e-2, 0.5, 2, 2, 10, 1), a.ctypes.data_as(ctypes.c_void_p)),
+                     (capi.pc_params(3, 7, 8, 1.0, 1e-2, 0.5, 2, 0, 10, 1, 1), a.ctypes.data_as(ctypes.c_void_p)),
                      (capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 2, 2, 10, 1), a2.ctypes.data_as(ctypes.c_void_p)),
                      (capi.pc_params(2, 7, 8, 1.0, 1e-2, 0.5, 2, 0, 10, 1, 1), a2.ctypes.data_as(ctypes.c_void_p))]:
         assert l.pc_setup(ctypes.byref(p), a_ptr, None, ctypes.byref(h)) == capi.PC_ERR_UNSUPPORTED

@@ -166,13 +166,27 @@ def test_fe_adjoint_solve_matches_oracle():
     sol.close()
 
 
-def test_fe_unsupported_requests_fail_loudly():
-    # the element gradient is built for 2D grids (tests/test_gpu_fe_var.py)
+def test_fe_3d_gradient_pieces_match_oracle_and_fixed_coefficient_fails_loudly():
+    """A 3D constant-coefficient element handle (sine transforms): the stiffness
+    derivative of the gradient and the element objective match the oracle; its
+    coefficient cannot be changed on the device."""
     from paper_2410_22686_gb300 import capi
-    sol = _solver(3, 7, 4)
-    x = torch.zeros(sol.vec_len, dtype=torch.float64, device="cuda")
+    d, m1, n, gamma = 3, 7, 4, 1e-3
+    sol = _solver(d, m1, n, gamma=gamma)
+    a = np.ones((m1 + 2,) * d)
+    M, _ = fe.fe_matrices(m1, d)
+    tau = osy.time_step(1.0, n)
+    xh = S.random_vector((2, n) + (m1,) * d, 31)
+    lam = S.random_vector((2, n) + (m1,) * d, 32)
+    gh = S.random_vector((n,) + (m1,) * d, 33)
+    ga = sol.grad_log_a(_dev(xh), _dev(lam)).cpu().numpy().reshape((m1,) * d)
+    ref_ga, _ = fe.adjoint_gradient(xh, lam, gh, a, M, tau, gamma)
+    assert _rel(ga, ref_ga) <= 1e-12
+    J = sol.objective(_dev(xh), _dev(gh)).item()
+    ref = fe.objective(xh, gh, M, tau, gamma)
+    assert abs(J - ref) <= 1e-13 * abs(ref)
     with pytest.raises(capi.PCError) as ei:
-        sol.grad_log_a(x, x)
+        sol.set_log_coefficient(torch.zeros((m1,) * d, dtype=torch.float64, device="cuda"))
     assert ei.value.status == capi.PC_ERR_UNSUPPORTED
     sol.close()
 
