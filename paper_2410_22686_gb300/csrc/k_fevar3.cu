@@ -16,6 +16,7 @@
 // (sigma M + tau K(a)) (eight colours: the 27-point stencils never couple two points of
 // one colour), the stiffness derivative of the gradient and the element objective.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -114,8 +115,9 @@ __global__ void __launch_bounds__(256) fevar3_apply_kernel(const double* __restr
 }
 
 // All-at-once product A x (or A^T x), A = [[alpha I(x)M, T^T], [-T, alpha I(x)M]],
-// (T v)_j = M v_j - M v_{j-1} + tau K v_j, in FP64 arithmetic (FP32 inputs widened
-// exactly).  One thread per spatial point and chunk of time blocks [j0, j1):
+// (T v)_j = M v_j - M v_{j-1} + tau K v_j, in FP64 arithmetic for FP64 inputs (FP32
+// inputs take the double-float kernel below).  One thread per spatial point and chunk
+// of time blocks [j0, j1):
 //   y1_j = alpha M x1_j + sg (M x2_j - M x2_{j+1} + tau K x2_j)
 //   y2_j = alpha M x2_j - sg (M x1_j - M x1_{j-1} + tau K x1_j),   sg = -1 for A^T.
 template <typename Tin, bool TRANSPOSE>
@@ -164,6 +166,135 @@ __global__ void __launch_bounds__(256) fevar3_matvec_kernel(const Tin* __restric
   if (j1 < n) {
     double mu, ku;
     mk_apply3(x2 + (int64_t)j1 * np, A, m, i1, i2, i3, mu, ku);
+    Mx2n = mh * mu;
+  }
+  y1[(int64_t)(j1 - 1) * np + s] = alpha * pMx1 + sg * (pMx2 - Mx2n + tk * pKx2);
+}
+
+// ---------------------------------------------------------------------------
+// Element product of an FP32 vector (the inner product of flexible GMRES) in
+// double-float arithmetic, as the 2D kernel: the 21 K entries of a point that can be
+// nonzero are split once into FP32 (hi, lo) pairs and kept for all its time blocks;
+// per time block and half, M u (power-of-two weights on FP32 values, every term
+// exact) and K u (exact products hi * u by FMA, lo * u rounded) are summed with
+// Knuth's TwoSum into (sum, error) pairs, widened on the integer pipes and combined
+// in FP64.  Relative error of a sum: about 2^-44 of the sum of the magnitudes of its
+// terms, against ~100 FP64 operations per point and time block otherwise.
+// ---------------------------------------------------------------------------
+struct DF3 {
+  float hi, lo;
+};
+
+// (hi, lo) += x exactly (TwoSum; no contraction into FMA)
+__device__ __forceinline__ void df3_add(DF3& a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, err);
+}
+
+// (hi, lo) += (kh + kl) u
+__device__ __forceinline__ void df3_add_prod(DF3& a, float kh, float kl, float u) {
+  const float p = __fmul_rn(kh, u);
+  const float e = fmaf(kh, u, -p);
+  df3_add(a, p);
+  a.lo = __fadd_rn(a.lo, fmaf(kl, u, e));
+}
+
+__device__ __forceinline__ double df3_val(const DF3& a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+
+// the K entries of the 21 offsets not in a single coordinate, in loop order
+struct KSplit3 {
+  float h[21], l[21];
+};
+
+__device__ __forceinline__ void mk_apply3_df(const float* __restrict__ u, const KSplit3& k, int m, int i1, int i2,
+                                             int i3, double& mu, double& ku) {
+  const int64_t s = ((int64_t)i3 * m + i2) * m + i1;
+  DF3 am{0.0f, 0.0f}, ak{0.0f, 0.0f};
+  int q = 0;
+#pragma unroll
+  for (int o3 = -1; o3 <= 1; ++o3)
+#pragma unroll
+    for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+      for (int o1 = -1; o1 <= 1; ++o1) {
+        const int q1 = i1 + o1, q2 = i2 + o2, q3 = i3 + o3;
+        const bool in = q1 >= 0 && q1 < m && q2 >= 0 && q2 < m && q3 >= 0 && q3 < m;
+        const float v = in ? u[s + ((int64_t)o3 * m + o2) * m + o1] : 0.0f;
+        df3_add(am, __fmul_rn((float)m_weight(o1, o2, o3), v));  // a power of two: exact
+        if ((o1 != 0) + (o2 != 0) + (o3 != 0) != 1) {
+          df3_add_prod(ak, k.h[q], k.l[q], v);
+          ++q;
+        }
+      }
+  mu = df3_val(am);
+  ku = df3_val(ak);
+}
+
+template <bool TRANSPOSE>
+__global__ void __launch_bounds__(256, 2) fevar3_matvec_df_kernel(const float* __restrict__ x, double* __restrict__ y,
+                                                               const double* __restrict__ E, int m, int n, int tj,
+                                                               double mh, double kh, double alpha, double tau,
+                                                               size_t xstride, size_t ystride,
+                                                               const int* __restrict__ jdev) {
+  const int64_t np = (int64_t)m * m * m;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= np) return;
+  if (jdev) {  // device-resident Arnoldi index: x = Z_j, y = V_{j+1}
+    x += (size_t)(*jdev) * xstride;
+    y += (size_t)(*jdev + 1) * ystride;
+  }
+  const int j0 = blockIdx.y * tj, j1 = min(n, j0 + tj);
+  if (j0 >= n) return;
+  int i1, i2, i3;
+  coords3(s, m, i1, i2, i3);
+  KSplit3 k;
+  {
+    const Around<double> A = around(E, m, i1, i2, i3);
+    int q = 0;
+#pragma unroll
+    for (int o3 = -1; o3 <= 1; ++o3)
+#pragma unroll
+      for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+        for (int o1 = -1; o1 <= 1; ++o1) {
+          if ((o1 != 0) + (o2 != 0) + (o3 != 0) == 1) continue;
+          const double kv = k_entry(A, o1, o2, o3);
+          k.h[q] = f64_to_f32(kv);
+          k.l[q] = f64_to_f32(kv - f32_to_f64(k.h[q]));
+          ++q;
+        }
+  }
+  const double sg = TRANSPOSE ? -1.0 : 1.0, tk = tau * kh;
+  const float* x1 = x;
+  const float* x2 = x + (int64_t)n * np;
+  double* y1 = y;
+  double* y2 = y + (int64_t)n * np;
+  double Mx1p = 0.0;
+  if (j0 > 0) {
+    double mu, ku;
+    mk_apply3_df(x1 + (int64_t)(j0 - 1) * np, k, m, i1, i2, i3, mu, ku);
+    Mx1p = mh * mu;
+  }
+  double pMx1 = 0.0, pMx2 = 0.0, pKx2 = 0.0;
+  for (int j = j0; j < j1; ++j) {
+    double mu1, ku1, mu2, ku2;
+    mk_apply3_df(x1 + (int64_t)j * np, k, m, i1, i2, i3, mu1, ku1);
+    mk_apply3_df(x2 + (int64_t)j * np, k, m, i1, i2, i3, mu2, ku2);
+    const double Mx1 = mh * mu1, Mx2 = mh * mu2;
+    y2[(int64_t)j * np + s] = alpha * Mx2 - sg * (Mx1 - Mx1p + tk * ku1);
+    if (j > j0) y1[(int64_t)(j - 1) * np + s] = alpha * pMx1 + sg * (pMx2 - Mx2 + tk * pKx2);
+    Mx1p = Mx1;
+    pMx1 = Mx1;
+    pMx2 = Mx2;
+    pKx2 = ku2;
+  }
+  double Mx2n = 0.0;
+  if (j1 < n) {
+    double mu, ku;
+    mk_apply3_df(x2 + (int64_t)j1 * np, k, m, i1, i2, i3, mu, ku);
     Mx2n = mh * mu;
   }
   y1[(int64_t)(j1 - 1) * np + s] = alpha * pMx1 + sg * (pMx2 - Mx2n + tk * pKx2);
@@ -517,13 +648,23 @@ cudaError_t launch_matvec_fevar3(Launch& L, int m, int n, double h, double alpha
   const dim3 grid = grid3(np, (n + tj - 1) / tj);
   const double tot = 2.0 * n * (double)np, mh = h * h * h / 216.0, kh = h / 12.0;
   L.begin(KC_MATVEC);
-  if (transpose)
-    fevar3_matvec_kernel<Tin, true><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
+  if constexpr (std::is_same<Tin, float>::value) {
+    if (transpose)
+      fevar3_matvec_df_kernel<true><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
                                                                 ystride, jdev);
-  else
-    fevar3_matvec_kernel<Tin, false><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
+    else
+      fevar3_matvec_df_kernel<false><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
                                                                  ystride, jdev);
-  return L.end(KC_MATVEC, tot * (sizeof(Tin) + 8.0), tot * 100.0);
+    return L.end(KC_MATVEC, tot * (sizeof(Tin) + 8.0), tot * 400.0);
+  } else {
+    if (transpose)
+      fevar3_matvec_kernel<Tin, true><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
+                                                                  ystride, jdev);
+    else
+      fevar3_matvec_kernel<Tin, false><<<grid, 256, 0, L.stream>>>(x, y, E, m, n, tj, mh, kh, alpha, tau, xstride,
+                                                                   ystride, jdev);
+    return L.end(KC_MATVEC, tot * (sizeof(Tin) + 8.0), tot * 100.0);
+  }
 }
 
 template <typename Tc>
