@@ -205,3 +205,21 @@ def test_element_graph_and_batched_solves_match_host_solves_3d():
     batch.close()
     for s in sols:
         s.close()
+
+
+def test_double_float_product_equals_fp64_product_on_the_full_grid():
+    """On the 63^3 grid of the 3D workload (n = 32): the product of an FP32 vector in
+    double-float arithmetic equals the FP64-arithmetic product of the same (widened)
+    vector, which the tests above check against the oracle, to 1e-12."""
+    from paper_2410_22686_gb300 import Solver
+    p = S.gaussian_field_3d_problem(m1=63, n=32)
+    s32 = Solver(3, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision="fp32", max_iter=4,
+                 space="fe")
+    s64 = Solver(3, p.m1, p.n, p.T, p.gamma, p.eps, p.a_nodes, spatial="mg", precision="fp64", max_iter=4,
+                 space="fe")
+    x32 = torch.from_numpy(S.random_vector((2 * p.n * p.m1 ** 3,), 3).astype(np.float32)).cuda()
+    y32 = s32.matvec_f32(x32)
+    y64 = s64.matvec(x32.double())
+    assert (y32 - y64).abs().max().item() <= 1e-12 * y64.abs().max().item()
+    s32.close()
+    s64.close()
