@@ -447,6 +447,23 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
                                          "fd": "finite differences (M = I)",
                                          "fe": "bilinear finite elements (mass matrix M)", **res}
 
+    if not args.skip_fst:
+        # the plain FP64 configuration: a = 1, 31^2 interior grid, n = 32, gamma = 1e-2,
+        # eps = 0.5 sqrt(tau), g = sin(pi x1) sin(pi x2) t (61,504 unknowns; launch-bound)
+        p = S.plain_fp64_problem()
+        res = {}
+        for prec in ("fp64", "fp32"):
+            sol = Solver(2, p.m1, p.n, p.T, p.gamma, p.eps, None, spatial="fst", precision=prec, max_iter=60)
+            b = sol.build_rhs(torch.from_numpy(p.f).to(dev), torch.from_numpy(p.g).to(dev),
+                              torch.from_numpy(p.y0).to(dev))
+            t, r = sync_time(lambda: sol.solve(b, rtol=RTOL, raise_on_nonconv=False), 5)
+            tg, rg = sync_time(lambda: sol.solve_graph(b, rtol=RTOL, raise_on_nonconv=False), 5)
+            res[prec] = {"solve_s": t, "graph_solve_s": tg, "iters": r[1], "relres": r[2]}
+            sol.close()
+            del b
+        out["plain_31sq_n32"] = {"data": "a = 1, 31^2, n = 32, gamma 1e-2, eps = 0.5 sqrt(tau), "
+                                         "g = sin(pi x1) sin(pi x2) t", "unknowns": p.unknowns, **res}
+
     if not args.skip_fe_var:
         # a nodal coefficient with bilinear (2D) and trilinear (3D) elements: the element
         # multigrid inside P_eps^{-1}, on the benchmark fields and on the 3D random field
@@ -457,7 +474,8 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
                  ("fe_var_3d_63cubed_n128", S.gaussian_field_3d_problem(),
                   "3D random-field coefficient of the 63^3 x 128 workload, gamma 1e-4, eps = sqrt(tau)",
                   "trilinear elements, element coefficient = mean of its corner values; colour-ordered element "
-                  "multigrid (8 colours); element products in FP64 arithmetic"))
+                  "multigrid (8 colours); element products in FP64 arithmetic on FP64 handles, in double-float "
+                  "arithmetic for the FP32 basis"))
         for key, p, data, disc in cases:
             res = {}
             for prec in ("fp32", "fp64"):
