@@ -180,7 +180,7 @@ int pc_krylov_bytes(const pc_params* params, size_t* bytes);
  * at the same time: a batch (pc_batch_create) starts a problem whose range
  * overlaps an earlier problem's after that problem has finished, so more
  * problems than fit in memory at once run in one graph launch.  Every
- * solve overwrites the range.
+ * solve (and pc_autotune) overwrites the range.
  * Errors: as pc_setup; PC_ERR_ARG also for a null, misaligned or too small
  * workspace (checked before any device work). */
 int pc_setup_shared(const pc_params* params, const double* a_nodes, void* krylov, size_t krylov_bytes,
