@@ -67,11 +67,12 @@ typedef enum pc_precision {
   PC_PREC_MIXED_BF16S = 2,  /* as FP32, multigrid smoother iterates stored as BF16 */
   PC_PREC_AUTO = 3          /* FP32 when eps >= PC_AUTO_FP32_MIN_EPS, else FP64: the time
                                scaling D = diag(eps^{j/n}) amplifies the FP32 rounding of the
-                               apply by up to 1/eps, and below this eps (e.g. the paper's
-                               eps = tau/2) the FP32 preconditioner needs several times the
-                               FP64 iterations; pc_precision_of reports the choice */
+                               apply by up to 1/eps; down to this eps (the paper's eps = tau/2
+                               included for n up to a few thousand) the FP32 preconditioner
+                               needs at most about one iteration more than FP64;
+                               pc_precision_of reports the choice */
 } pc_precision;
-#define PC_AUTO_FP32_MIN_EPS 1e-2
+#define PC_AUTO_FP32_MIN_EPS 1e-4
 
 typedef enum pc_gmres_mode {
   PC_GMRES_RIGHT = 0,  /* flexible GMRES, right preconditioning, stops on ||b-Ax||/||b|| */

@@ -2,15 +2,20 @@
 // P_eps^{-1} (Section 2.1), with C_{eps,n} = D^{-1} F Lambda F^* D
 // (Eq. decomposition_eps), D = diag(eps^{j/n}), lambda_k = 1 - eps^{1/n} theta^{-k}.
 //
-// Because C_{eps,n} is real, C^T = D F conj(Lambda) F^* D^{-1}, so
-//   half 1 (block C_eps^T + alpha I):  hat v1 = fft(D^{-1} v1), shifts conj(lambda_k) + alpha,
-//   half 2 (block C_eps   + alpha I):  hat v2 = fft(D v2),      shifts lambda_k + alpha,
-// and both are inverted by D^{+-1} ifft(.).  The two real halves are packed
-// into one complex sequence z = D^{-1} v1 + i D v2 (two-for-one), and only the
-// Hermitian half k = 0..n/2 is kept.  Since conj(lambda_{n-k}) = lambda_k,
-// frequency n-k of half 1 has the same shifted operator as frequency k of
-// half 2, so spectral plane 2k holds hat v2[k] and plane 2k+1 holds
-// conj(hat v1[k]) = hat v1[n-k]: both planes of a pair share sigma_k = lambda_k + alpha.
+// C_{eps,n} is Toeplitz, so its transpose is C^T = J C J with J the reversal of the
+// time index, and (C^T + alpha I)^{-1} v1 = J (C + alpha I)^{-1} J v1: both halves go
+// through the same transform,
+//   half 1 (block C_eps^T + alpha I):  hat v1 = fft(D J v1), shifts lambda_k + alpha,
+//   half 2 (block C_eps   + alpha I):  hat v2 = fft(D v2),   shifts lambda_k + alpha,
+// inverted by D^{-1} ifft(.) (and J again for half 1).  The two real halves are
+// packed into one complex sequence z = D J v1 + i D v2 (two-for-one) and only the
+// Hermitian half k = 0..n/2 is kept: spectral plane 2k holds hat v2[k], plane 2k+1
+// hat v1[k], and both planes of a pair share sigma_k = lambda_k + alpha.  The two
+// parts of z carry the same scaling eps^{j/n} at every j, so the packing costs no
+// accuracy.  (Packing D^{-1} v1 with D v2 instead, the form C^T = D F conj(Lambda)
+// F^* D^{-1} suggests, mixes parts whose ratio reaches eps^{-2}: the smaller part then
+// keeps only about u / eps^2 of relative accuracy, which ruins an FP32 transform at
+// the paper's eps = tau/2.)
 //
 // One CTA owns TS consecutive spatial points and the whole time axis: it
 // reads n rows of TS values per half (coalesced along space), runs an
@@ -127,8 +132,8 @@ __global__ void __launch_bounds__(256) tfft_forward_kernel(const Tin* __restrict
     Tc a = Tc(0), b = Tc(0);
     if (s < ms) {
       const Tc d = dpow[j];
-      a = cvt<Tc>(v1[(int64_t)j * ms + s]) / d;   // D^{-1} v1
-      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * d;   // D v2
+      a = cvt<Tc>(v1[(int64_t)(n - 1 - j) * ms + s]) * d;  // D J v1
+      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * d;            // D v2
     }
     z[bitrev(j, logn) * TS + c] = cmk<Tc>(a, b);
   }
@@ -143,9 +148,9 @@ __global__ void __launch_bounds__(256) tfft_forward_kernel(const Tin* __restrict
     if (s >= ms) continue;
     const C Z = z[k * TS + c];
     const C W = z[((n - k) & (n - 1)) * TS + c];
-    // hat v2[k] = (Z[k] - conj Z[n-k]) / (2i);  conj(hat v1[k]) = (conj Z[k] + Z[n-k]) / 2
+    // hat v2[k] = (Z[k] - conj Z[n-k]) / (2i);  hat v1[k] = (Z[k] + conj Z[n-k]) / 2
     spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
-    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (Z.y - W.y) * hf);
   }
 }
 
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
     C sa = czero<Tc>(), sb = czero<Tc>();
     if (s < ms) {
       sa = ldc(spec, (int64_t)(2 * k) * ms + s);      // hat w2[k]
-      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);  // hat w1[n-k] = conj(hat w1[k])
+      sb = ldc(spec, (int64_t)(2 * k + 1) * ms + s);  // hat w1[k]
       if (fc.ec) {
         Parents<Tc, TU> par;
         par.init(fc, s);
@@ -175,11 +180,11 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
         sb = sb + par.at(fc, 2 * k + 1);
       }
     }
-    // Y[k] = hat w1[k] + i hat w2[k] with hat w1[k] = conj(sb), hat w2[k] = sa
-    z[bitrev(k, logn) * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
+    // Y[k] = hat w1[k] + i hat w2[k] with hat w1[k] = sb, hat w2[k] = sa
+    z[bitrev(k, logn) * TS + c] = cmk<Tc>(sb.x - sa.y, sb.y + sa.x);
     if (k > 0 && 2 * k < n) {
-      // Y[n-k] = hat w1[n-k] + i hat w2[n-k] with hat w1[n-k] = sb, hat w2[n-k] = conj(sa)
-      z[bitrev(n - k, logn) * TS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+      // Y[n-k] = conj(hat w1[k]) + i conj(hat w2[k]) (real halves)
+      z[bitrev(n - k, logn) * TS + c] = cmk<Tc>(sb.x + sa.y, sa.x - sb.y);
     }
   }
   __syncthreads();
@@ -192,10 +197,9 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
     const int c = e - j * TS;
     const int64_t s = s0 + c;
     if (s >= ms) continue;
-    const C y = z[j * TS + c];
-    const Tc d = dpow[j];
-    const Tc wt1 = d * (y.x * inv_n);   // D ifft(hat w1)
-    const Tc wt2 = (y.y * inv_n) / d;   // D^{-1} ifft(hat w2)
+    const int jr = n - 1 - j;
+    const Tc wt1 = (z[jr * TS + c].x * inv_n) / dpow[jr];  // J D^{-1} ifft(hat w1)
+    const Tc wt2 = (z[j * TS + c].y * inv_n) / dpow[j];    // D^{-1} ifft(hat w2)
     w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);   // step 4: [[I, -I], [I, I]]
     w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
   }
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(256) tfft_inverse_kernel(const TU* __restrict_
 // spatial columns: two register FFTs and one shared-memory exchange instead of
 // log2(n) shared-memory radix-2 stages.
 // Forward transform of one tile of COLS = 256 / N1 columns.  ld(j, a, b) gives
-// v1[j] and v2[j] of the thread's column (zero outside the grid).  Returns after
+// v1[n-1-j] and v2[j] of the thread's column (zero outside the grid).  Returns after
 // the spectrum stores; the caller's barrier orders the reuse of `sm`.
 template <typename Tc, int N1, int N2, typename Ld>
 __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, const Tc* __restrict__ dinv,
@@ -221,7 +225,7 @@ __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, 
   typedef typename Cx<Tc>::t C;
   constexpr int n = N1 * N2;
   constexpr int COLS = 256 / N1;
-  // (A) rows j = r + N1 j2: z = D^{-1} v1 + i D v2, N2-point DFT over j2
+  // (A) rows j = r + N1 j2: z = D J v1 + i D v2, N2-point DFT over j2
   C x[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) {
@@ -229,7 +233,7 @@ __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, 
     Tc a, b;
     PC_DOK(j < n && c < COLS && (!valid || s < ms), 301);
     ld(j, a, b);
-    x[j2] = cmk<Tc>(a * dinv[j], b * dpow[j]);
+    x[j2] = cmk<Tc>(a * dpow[j], b * dpow[j]);
   }
   reg_fft<N2, false>(x, tw, N1);
   // (B) twiddle w^{j1 k2}, stored as Y[k2][j1]
@@ -262,8 +266,9 @@ __device__ __forceinline__ void fwd4_body(Ld&& ld, const Tc* __restrict__ dpow, 
       if (k <= n / 2) {
         const C Z = sm[k * COLS + c];
         const C W = sm[((n - k) & (n - 1)) * COLS + c];
+        // hat v2[k] = (Z[k] - conj Z[n-k]) / (2i),  hat v1[k] = (Z[k] + conj Z[n-k]) / 2
         spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
-        spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+        spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (Z.y - W.y) * hf);
       }
     }
   }
@@ -289,8 +294,10 @@ __device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, 
     if (k <= n / 2) {
       C sa, sb;
       ld(k, sa, sb);
-      sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
-      if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+      // Y[k] = hat w1[k] + i hat w2[k] (sb = hat w1[k], sa = hat w2[k]);
+      // Y[n-k] = conj(hat w1[k]) + i conj(hat w2[k]) (real halves)
+      sm[k * COLS + c] = cmk<Tc>(sb.x - sa.y, sb.y + sa.x);
+      if (k > 0 && 2 * k < n) sm[(n - k) * COLS + c] = cmk<Tc>(sb.x + sa.y, sa.x - sb.y);
     }
   }
   __syncthreads();
@@ -307,22 +314,35 @@ __device__ __forceinline__ void inv4_body(Ld&& ld, const Tc* __restrict__ dpow, 
     sm[(j2 * N1 + r) * COLS + c] = (j2 == 0 || r == 0) ? x[j2] : cmul(t, x[j2]);
   }
   __syncthreads();
-  if (r < N2 && valid) {
-    // (C) row j2 = r: N1-point inverse DFT over k1 -> x[j2 + N2 j1]
-    C y[N1];
+  // (C) row j2 = r: N1-point inverse DFT over k1 -> z[j2 + N2 j1]
+  C y[N1];
+  if (r < N2) {
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) y[k1] = sm[(r * N1 + k1) * COLS + c];
+  }
+  __syncthreads();  // every read of the exchange is done before sm is rewritten
+  if (r < N2) {
     reg_fft<N1, true>(y, tw, N2);
     const Tc inv_n = Tc(1) / Tc(n);
+    // half 1 belongs to time n-1-j (J D^{-1} ifft(hat w1)), half 2 to time j
+    // (D^{-1} ifft(hat w2)): meet in shared memory for the butterfly
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const int j = r + N2 * j1;
+      sm[(n - 1 - j) * COLS + c].x = dinv[j] * (y[j1].x * inv_n);
+      sm[j * COLS + c].y = dinv[j] * (y[j1].y * inv_n);
+    }
+  }
+  __syncthreads();
+  if (r < N2 && valid) {
     Tout* w1 = w;
     Tout* w2 = w + (int64_t)n * ms;
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       const int j = r + N2 * j1;
-      const Tc wt1 = dpow[j] * (y[j1].x * inv_n);  // D ifft(hat w1)
-      const Tc wt2 = dinv[j] * (y[j1].y * inv_n);  // D^{-1} ifft(hat w2)
-      w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);  // step 4: [[I, -I], [I, I]]
-      w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+      const C t = sm[j * COLS + c];
+      w1[(int64_t)j * ms + s] = cvt<Tout>(t.x - t.y);  // step 4: [[I, -I], [I, I]]
+      w2[(int64_t)j * ms + s] = cvt<Tout>(t.x + t.y);
     }
   }
 }
@@ -355,7 +375,7 @@ __global__ void __launch_bounds__(256) tfft4_forward_kernel(const Tin* __restric
   const Tin* v2 = v + (int64_t)n * ms;
   fwd4_body<Tc, N1, N2>(
       [&](int j, Tc& a, Tc& b) {
-        a = valid ? cvt<Tc>(v1[(int64_t)j * ms + s]) : Tc(0);
+        a = valid ? cvt<Tc>(v1[(int64_t)(n - 1 - j) * ms + s]) : Tc(0);
         b = valid ? cvt<Tc>(v2[(int64_t)j * ms + s]) : Tc(0);
       },
       dpow, dinv, tw, spec, sm, ms, s, valid, r, c);
@@ -383,7 +403,7 @@ __global__ void __launch_bounds__(256, 2) tfft4_forward_f64_kernel(const Tin* __
   const Tin* v2 = v + (int64_t)n * ms;
   fwd4_body<double, N1, N2>(
       [&](int j, double& a, double& b) {
-        a = valid ? cvt<double>(v1[(int64_t)j * ms + s]) : 0.0;
+        a = valid ? cvt<double>(v1[(int64_t)(n - 1 - j) * ms + s]) : 0.0;
         b = valid ? cvt<double>(v2[(int64_t)j * ms + s]) : 0.0;
       },
       dpow, dinv, tw, spec, sm, ms, s, valid, r, c);
@@ -432,7 +452,7 @@ __global__ void __launch_bounds__(256) tfft4s_forward_kernel(const Tin* __restri
     const int64_t s = (int64_t)t * COLS + c;
     fwd4_body<Tc, N1, N2>(
         [&](int j, Tc& a, Tc& b) {
-          a = cvt<Tc>(st[j * COLS + c]);
+          a = cvt<Tc>(st[(n - 1 - j) * COLS + c]);
           b = cvt<Tc>(st[(n + j) * COLS + c]);
         },
         dpow, dinv, tw, spec, sm, ms, s, s < ms, r, c);
@@ -556,8 +576,8 @@ __global__ void __launch_bounds__(256) tdft_forward_kernel(const Tin* __restrict
     const int64_t s = s0 + c;
     Tc a = Tc(0), b = Tc(0);
     if (s < ms) {
-      a = cvt<Tc>(v1[(int64_t)j * ms + s]) * dinv[j];
-      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * dpow[j];
+      a = cvt<Tc>(v1[(int64_t)(n - 1 - j) * ms + s]) * dpow[j];  // D J v1
+      b = cvt<Tc>(v2[(int64_t)j * ms + s]) * dpow[j];            // D v2
     }
     z[j * TS + c] = cmk<Tc>(a, b);
   }
@@ -583,8 +603,8 @@ __global__ void __launch_bounds__(256) tdft_forward_kernel(const Tin* __restrict
       if (ikn >= n) ikn -= n;
     }
     if (s >= ms) continue;
-    spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);
-    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (W.y - Z.y) * hf);
+    spec[(int64_t)(2 * k) * ms + s] = cmk<Tc>((Z.y + W.y) * hf, (W.x - Z.x) * hf);  // hat v2[k]
+    spec[(int64_t)(2 * k + 1) * ms + s] = cmk<Tc>((Z.x + W.x) * hf, (Z.y - W.y) * hf);  // hat v1[k]
   }
 }
 
@@ -613,16 +633,15 @@ __global__ void __launch_bounds__(256) tdft_inverse_kernel(const TU* __restrict_
         sb = sb + par.at(fc, 2 * k + 1);
       }
     }
-    z[k * TS + c] = cmk<Tc>(sb.x - sa.y, sa.x - sb.y);
-    if (k > 0 && 2 * k < n) z[(n - k) * TS + c] = cmk<Tc>(sb.x + sa.y, sb.y + sa.x);
+    // Y[k] = hat w1[k] + i hat w2[k], Y[n-k] = conj(hat w1[k]) + i conj(hat w2[k])
+    z[k * TS + c] = cmk<Tc>(sb.x - sa.y, sb.y + sa.x);
+    if (k > 0 && 2 * k < n) z[(n - k) * TS + c] = cmk<Tc>(sb.x + sa.y, sa.x - sb.y);
   }
   __syncthreads();
   const Tc inv_n = Tc(1) / Tc(n);
-  Tout* w1 = w;
-  Tout* w2 = w + (int64_t)n * ms;
+  C* o = z + (size_t)n * TS;  // [n][TS]: half 1 in .x, half 2 in .y, both at their own time
   for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
     const int j = e / TS, c = e - (e / TS) * TS;
-    const int64_t s = s0 + c;
     C y = czero<Tc>();
     int ij = 0;  // (j k) mod n, conjugate twiddles
     for (int k = 0; k < n; ++k) {
@@ -633,11 +652,19 @@ __global__ void __launch_bounds__(256) tdft_inverse_kernel(const TU* __restrict_
       ij += j;
       if (ij >= n) ij -= n;
     }
+    o[(n - 1 - j) * TS + c].x = dinv[j] * (y.x * inv_n);  // J D^{-1} ifft(hat w1)
+    o[j * TS + c].y = dinv[j] * (y.y * inv_n);            // D^{-1} ifft(hat w2)
+  }
+  __syncthreads();
+  Tout* w1 = w;
+  Tout* w2 = w + (int64_t)n * ms;
+  for (int e = threadIdx.x; e < n * TS; e += blockDim.x) {
+    const int j = e / TS, c = e - (e / TS) * TS;
+    const int64_t s = s0 + c;
     if (s >= ms) continue;
-    const Tc wt1 = dpow[j] * (y.x * inv_n);
-    const Tc wt2 = dinv[j] * (y.y * inv_n);
-    w1[(int64_t)j * ms + s] = cvt<Tout>(wt1 - wt2);
-    w2[(int64_t)j * ms + s] = cvt<Tout>(wt1 + wt2);
+    const C t = o[j * TS + c];
+    w1[(int64_t)j * ms + s] = cvt<Tout>(t.x - t.y);  // step 4: [[I, -I], [I, I]]
+    w2[(int64_t)j * ms + s] = cvt<Tout>(t.x + t.y);
   }
 }
 
@@ -866,7 +893,8 @@ cudaError_t launch_tfft_inverse(Launch& L, int64_t ms, int n, const TU* spec, co
   if (jdev && (n > four_step_max<Tc>() || !pow2)) return cudaErrorNotSupported;
   if (!pow2) {
     const int TS = pick_ts_dft<Tc>(n);
-    const size_t smem = (size_t)n * TS * sizeof(typename Cx<Tc>::t);
+    // the spectrum and, after the sums, both halves at their own times: two [n][TS] arrays
+    const size_t smem = 2 * (size_t)n * TS * sizeof(typename Cx<Tc>::t);
     cudaError_t e =
         cudaFuncSetAttribute(tdft_inverse_kernel<Tc, TU, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

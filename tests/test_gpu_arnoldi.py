@@ -135,14 +135,15 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable():
 
 
 def test_auto_precision_follows_eps():
-    """precision="auto": the FP32 preconditioner for eps >= 1e-2 (the benchmark's
-    eps = sqrt(tau)), FP64 below (the paper's eps = tau/2, where the FP32 apply's rounding,
-    amplified by 1/eps through D = diag(eps^{j/n}), costs several times the iterations)."""
+    """precision="auto": the FP32 preconditioner for eps >= 1e-4 (the benchmark's
+    eps = sqrt(tau), the paper's eps = tau/2), FP64 below, where the FP32 apply's rounding,
+    amplified by up to 1/eps through D = diag(eps^{j/n}), would cost iterations."""
     from paper_2410_22686_gb300 import Solver
     m1, n = 7, 256
     tau = 1.0 / (n + 1)  # sqrt(tau) = 0.062, tau / 2 = 0.0019
     s1 = Solver(2, m1, n, 1.0, 1e-4, tau ** 0.5, None, spatial="fst", precision="auto")
     s2 = Solver(2, m1, n, 1.0, 1e-4, tau / 2, None, spatial="fst", precision="auto")
-    assert s1.precision == "fp32" and s2.precision == "fp64"
-    s1.close()
-    s2.close()
+    s3 = Solver(2, m1, n, 1.0, 1e-4, 1e-5, None, spatial="fst", precision="auto")
+    assert s1.precision == "fp32" and s2.precision == "fp32" and s3.precision == "fp64"
+    for s in (s1, s2, s3):
+        s.close()

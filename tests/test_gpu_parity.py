@@ -151,6 +151,26 @@ LARGEST_CASES = [(2, 3, 4096, "var", "mg"), (2, 7, 2048, "const", "fst"), (3, 3,
                  (2, 1023, 2, "var", "mg"), (2, 2047, 1, "const", "fst")]
 
 
+# the ends of the admissible eps range (0, 1]: eps = 1 is the plain circulant (D = I);
+# a small eps makes D = diag(eps^{j/n}) span a factor 1/eps, and the four steps then
+# lose up to ~u/eps of relative accuracy on either side (the oracle takes the same steps),
+# so the tolerance scales with 1/eps
+@pytest.mark.parametrize("eps,precision,tol", [(1.0, "fp64", 1e-12), (1.0, "fp32", 1e-5), (1e-3, "fp64", 1e-10),
+                                               (1e-5, "fp64", 1e-8), (1e-3, "fp32", 1e-3)])
+@pytest.mark.parametrize("d,m1,n,kind,spatial", [(2, 15, 32, "var", "mg"), (2, 31, 16, "const", "fst"),
+                                                (3, 7, 8, "var", "mg")])
+def test_precond_apply_at_the_ends_of_the_eps_range(d, m1, n, kind, spatial, eps, precision, tol):
+    a = _coef(d, m1, kind, seed=5 * m1 + n)
+    gamma = 1e-4
+    sol = _solver(d, m1, n, a, spatial, precision=precision, gamma=gamma, eps=eps, max_iter=4)
+    v = S.random_vector((2, n) + (m1,) * d, 19)
+    w = sol.apply_precond(_dev(v)).cpu().numpy()
+    tau, alpha = osy.time_step(1.0, n), osy.alpha_weight(1.0, n, gamma)
+    ref = opc.apply_Peps_inv(v, n, alpha, eps, opc.make_spatial_solver(spatial, a, m1, d, tau))
+    assert _rel(w, ref) <= tol
+    sol.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("d,m1,n,kind,spatial", LARGEST_CASES)
 def test_precond_and_matvec_at_the_largest_sizes(d, m1, n, kind, spatial, precision, tol):
