@@ -350,3 +350,23 @@ def test_theorem_gmres_rate_bound(gamma, n):
     assert res.converged
     for k, rk in enumerate(res.resid_history):
         assert rk <= rho ** k * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("n,eps", [(1, 0.5), (4, 0.3), (8, 1e-3), (31, 0.01), (32, 1.0)])
+def test_transposed_block_is_the_time_reversal_of_the_block(n, eps):
+    # C_eps is Toeplitz, so C^T = J C J with J the reversal of the time index, and the
+    # transposed block of P_eps can be solved through the block itself:
+    # (C^T + alpha I)^{-1} v = J (C + alpha I)^{-1} J v
+    C = pc.C_eps_matrix(n, eps)
+    J = np.eye(n)[::-1]
+    assert np.array_equal(C.T, J @ C @ J)
+    alpha = 0.37
+    v = S.random_vector((n,), 40)
+    lhs = np.linalg.solve(C.T + alpha * np.eye(n), v)
+    rhs = J @ np.linalg.solve(C + alpha * np.eye(n), J @ v)
+    assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(lhs).max()
+    # and through the diagonalisation of C: J D^{-1} F (Lambda + alpha)^{-1} F^* D J v
+    D = pc.D_eps_diag(n, eps)
+    lam = pc.eigenvalues_lambda(n, eps)
+    via = J @ ((np.fft.ifft(np.fft.fft(D * (J @ v)) / (lam + alpha)) / D).real)
+    assert np.abs(via - lhs).max() <= 1e-12 / min(eps, 1.0) * np.abs(lhs).max()
