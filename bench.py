@@ -580,6 +580,9 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
         other = 64.0 * sum(q.unknowns for q in probs)  # the handles' other workspace, b and x
         free = torch.cuda.mem_get_info(dev)[0]
         pool = int(min(need, args.batch_gb * 1e9, free - other - 16e9))
+        largest = max(-(-b // 256) * 256 for b in sizes)
+        if pool < largest:  # one problem's storage must fit (a device with little free memory)
+            pool = largest
         offs = pack_krylov(sizes, pool)
         waves = 1 + sum(1 for i, o in enumerate(offs) if i > 0 and o == 0)
         buf = torch.empty(pool, dtype=torch.uint8, device=dev)
