@@ -632,13 +632,15 @@ def _extra_workloads(args, torch, dev, dist=None, ws=1, rank=0):
 
 def iteration_sweep(args, torch, dev, m1=M1, ns=(32, 64, 128, 256, 512), gammas=GAMMAS):
     """GMRES iteration counts of the mixed path (FP32 preconditioner, flexible GMRES,
-    rtol 1e-8) over n and gamma at m1^2, for eps = sqrt(tau) (the benchmark's choice)
-    and for eps = c_tau(1/2) = (sqrt(tau)/2) / (sqrt(tau)/2 + 2 sqrt(T)), the largest
-    eps Theorem 2.13 covers with delta = 1/2 (also in FP64)."""
+    rtol 1e-8) over n and gamma at m1^2, for eps = sqrt(tau) (the benchmark's choice),
+    for eps = c_tau(1/2) = (sqrt(tau)/2) / (sqrt(tau)/2 + 2 sqrt(T)), the largest eps
+    Theorem 2.13 covers with delta = 1/2, and for the paper's eps = tau/2 (both also in
+    FP64)."""
     import synthetic as S
     from paper_2410_22686_gb300 import Solver
     out = {"m1": m1, "n": list(ns), "gammas": list(gammas), "rtol": RTOL}
-    rows = {"sqrt_tau_fp32": {}, "c_tau_half_fp32": {}, "c_tau_half_fp64": {}}
+    rows = {"sqrt_tau_fp32": {}, "c_tau_half_fp32": {}, "c_tau_half_fp64": {}, "tau_half_fp32": {},
+            "tau_half_fp64": {}}
     for nt in ns:
         for key in rows:
             rows[key][str(nt)] = []
@@ -649,7 +651,8 @@ def iteration_sweep(args, torch, dev, m1=M1, ns=(32, 64, 128, 256, 512), gammas=
             y0 = torch.from_numpy(p.y0).to(dev)
             c_tau = 0.5 * math.sqrt(p.tau) / (0.5 * math.sqrt(p.tau) + 2.0 * math.sqrt(p.T))
             for key, eps, prec in (("sqrt_tau_fp32", p.eps, "fp32"), ("c_tau_half_fp32", c_tau, "fp32"),
-                                   ("c_tau_half_fp64", c_tau, "fp64")):
+                                   ("c_tau_half_fp64", c_tau, "fp64"), ("tau_half_fp32", p.tau / 2, "fp32"),
+                                   ("tau_half_fp64", p.tau / 2, "fp64")):
                 s = Solver(2, m1, nt, p.T, g, eps, p.a_nodes, spatial="mg", precision=prec, max_iter=args.cap)
                 b = s.build_rhs(f, gg, y0)
                 _, it, rr = s.solve(b, rtol=RTOL, raise_on_nonconv=False)
